@@ -1,0 +1,174 @@
+/*
+ * yy.h - C ABI of the Yin-Yang multipole gravity solver (GB300, sm_103a).
+ *
+ * Computes the Newtonian potential Phi and the field -grad(Phi) of a
+ * cell-averaged density given on the two patches of a Yin-Yang grid, by the
+ * multipole method of Almanstotter, Melson, Janka & Mueller (2018),
+ * "Parallelized solution method of the three-dimensional gravitational
+ * potential on the Yin-Yang grid" (arXiv:1806.04593), which builds on
+ * Mueller & Steinmetz (1995).
+ *
+ * Per solve, on the caller's CUDA stream and without host synchronisation:
+ *   analysis   A_p[i][lm] = sum_jk rho_p[i][jk] w_jk K_lm T_j^(lm) {C_k^(m), S_k^(m)}
+ *              (§3 Eqs. ac/as with the overlap weight of §4), both patches;
+ *   radial     inner / outer sums of Eqs. phiin/phiout at the interfaces
+ *              r_n^+, as scaled prefix / suffix scans over r;
+ *   synthesis  Phi(r_q) = Phi_q(r_q) + Phi_p(r_q) on both patches (§4), the
+ *              other patch's moments evaluated at the target points expressed
+ *              in that patch's angles (Eqs. trafotheta/trafophi); optionally
+ *              -grad(Phi) in the target patch's local spherical basis.
+ *
+ * Conventions (all functions):
+ *  - Arrays are C-contiguous float64.  A patch field is [n_r][n_theta][n_phi]
+ *    (radius slowest, phi fastest); a gradient is [3][n_r][n_theta][n_phi]
+ *    holding (g_r, g_theta, g_phi).
+ *  - Zone i (0-based) spans r_edges[i]..r_edges[i+1]; output row n is the
+ *    outer interface r = r_edges[n+1] (the paper evaluates at interfaces).
+ *    Density is zero inside r_edges[0].
+ *  - Patch cells: theta_j = pi/4 - delta_theta + (j + 1/2) d_theta with
+ *    d_theta = (pi/2 + 2 delta_theta)/n_theta, phi_k = -3pi/4 - delta_phi +
+ *    (k + 1/2) d_phi with d_phi = (3pi/2 + 2 delta_phi)/n_phi (§4 intervals).
+ *    Outputs are at the cell-centre angles of the target patch.
+ *  - The Yang patch's local Cartesian frame is (x,y,z) -> (-x,z,y) of Yin's.
+ *  - Device pointers must be 16-byte aligned.  Input and output buffers are
+ *    owned by the caller; the handle owns its tables and workspace.
+ *  - A handle is not thread-safe and must be used from one stream at a time.
+ *  - Arguments are validated on the host; a failed check returns
+ *    YY_ERR_INVALID_ARG before any device work.  The library never aborts,
+ *    never uses device assert or trap, and never synchronises inside
+ *    yy_potential.  Kernels that detect a bad condition set a device error
+ *    word that yy_last_device_status reports.
+ */
+#ifndef YY_H
+#define YY_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct yy_grid yy_grid;
+
+typedef enum {
+  YY_OK = 0,
+  YY_ERR_INVALID_ARG = 1,
+  YY_ERR_OOM = 2,
+  YY_ERR_CUDA = 3,
+  YY_ERR_NOT_SUPPORTED = 4,
+  YY_ERR_TIMEOUT = 5,
+  YY_ERR_DEVICE_CHECK = 6
+} yy_status;
+
+/* Arithmetic of the two contractions (analysis and synthesis).  Tables and
+ * the radial scans are float64 in every form.
+ *   YY_FP64   float64 operands and accumulation (CUDA-core DFMA).
+ *   YY_FP32   float32 operands and accumulation (CUDA-core FFMA).
+ *   YY_TF32   one tf32 product per term on tcgen05 tensor cores, fp32 accumulation.
+ *   YY_BF16X3 operands split into 3 bf16 terms, 6 cross products, fp32
+ *             accumulation per K chunk, chunks summed in float64.
+ *   YY_FP16X2 operands split into 2 scaled fp16 terms, 3 cross products,
+ *             fp32 accumulation per K chunk, chunks summed in float64.       */
+typedef enum {
+  YY_FP64 = 0,
+  YY_FP32 = 1,
+  YY_TF32 = 2,
+  YY_BF16X3 = 3,
+  YY_FP16X2 = 4
+} yy_precision;
+
+/* Tables and intermediates readable through yy_grid_copy_table (tests and
+ * diagnostics).  Mode index: idx(l,0) = l^2, idx(l,m,cos) = l^2 + 2m - 1,
+ * idx(l,m,sin) = l^2 + 2m (m >= 1), n_lm = (l_max+1)^2.
+ *   YY_TABLE_WEIGHTS  [n_theta][n_phi]       overlap weights w_jk (§4)
+ *   YY_TABLE_TBAR     [n_theta][n_lm]        K_lm T_j^(lm) (Eq. tlm), cos and sin slots equal
+ *   YY_TABLE_ANALYSIS [n_lm][n_theta*n_phi]  w_jk K_lm T_j^(lm) {C_k^(m), S_k^(m)}
+ *   YY_TABLE_SYNTH    [n_theta*n_phi][2 n_lm] K_lm P_l^m {cos, sin}(m phi) at the cell
+ *                     centre (first n_lm) and at the centre seen from the
+ *                     other patch (last n_lm)
+ *   YY_TABLE_SYNTH_T  same layout: d/dtheta, rotated into the target basis
+ *   YY_TABLE_SYNTH_P  same layout: (1/sin theta) d/dphi, rotated likewise
+ *   YY_TABLE_MOMENTS  [2 n_r][n_lm]          normalised A of the last solve (Yin rows first)
+ *   YY_TABLE_COEFF    [2 n_r][2 n_lm]        synthesis coefficients of the last solve */
+typedef enum {
+  YY_TABLE_WEIGHTS = 0,
+  YY_TABLE_TBAR = 1,
+  YY_TABLE_ANALYSIS = 2,
+  YY_TABLE_SYNTH = 3,
+  YY_TABLE_SYNTH_T = 4,
+  YY_TABLE_SYNTH_P = 5,
+  YY_TABLE_MOMENTS = 6,
+  YY_TABLE_COEFF = 7
+} yy_table;
+
+/* Create a grid handle on the current CUDA device and build every
+ * density-independent term once (§3: the constant terms are computed only
+ * while the grid is fixed): overlap weights, polar / azimuthal integrals,
+ * normalised Legendre tables at the own and the other patch's angles, their
+ * angular derivatives, and the radial scan coefficients, all in float64 on
+ * the GPU.  Synchronises the device before returning.
+ *   r_edges      host, n_r + 1 values, r_edges[0] >= 0, strictly increasing
+ *   n_r          radial zones, 1 <= n_r <= 1<<20
+ *   n_theta/phi  cells per patch, >= 1 each, n_theta * n_phi <= 1<<24
+ *   delta_theta  buffer widths (radians), 0 <= delta < pi/4
+ *   delta_phi
+ *   l_max        0 <= l_max <= 80
+ *   G            gravitational constant (finite)
+ *   out          receives the handle (set to NULL on failure)
+ * Errors: YY_ERR_INVALID_ARG, YY_ERR_OOM, YY_ERR_CUDA. */
+yy_status yy_grid_create(const double *r_edges, int n_r, int n_theta, int n_phi,
+                         double delta_theta, double delta_phi, int l_max, double G,
+                         yy_grid **out);
+
+/* Build the operand tables of a reduced-precision form (allocates device
+ * memory; synchronises).  YY_FP64 is always ready.  Returns
+ * YY_ERR_NOT_SUPPORTED if the device cannot run the form. */
+yy_status yy_grid_prepare(yy_grid *g, yy_precision prec);
+
+/* One solve on `cuda_stream` (a cudaStream_t, NULL = legacy default stream).
+ *   rho_yin, rho_yang   device, [n_r][n_theta][n_phi] float64 (read)
+ *   phi_yin, phi_yang   device, same shape (written)
+ *   grad_yin, grad_yang device, [3][n_r][n_theta][n_phi] or both NULL
+ * Asynchronous; no host synchronisation.  Errors: YY_ERR_INVALID_ARG (NULL
+ * or misaligned pointer, one gradient pointer NULL), YY_ERR_NOT_SUPPORTED
+ * (precision not prepared), YY_ERR_CUDA (launch failure). */
+yy_status yy_potential(yy_grid *g, const double *rho_yin, const double *rho_yang,
+                       double *phi_yin, double *phi_yang,
+                       double *grad_yin, double *grad_yang,
+                       yy_precision prec, void *cuda_stream);
+
+/* yy_potential with HOST buffers: copies rho to the handle's device staging
+ * buffers, solves, copies Phi (and the gradient) back, and synchronises the
+ * stream before returning.  Host buffers should be page-locked for full
+ * copy bandwidth.  The first call allocates the staging buffers. */
+yy_status yy_potential_host(yy_grid *g, const double *rho_yin, const double *rho_yang,
+                            double *phi_yin, double *phi_yang,
+                            double *grad_yin, double *grad_yang,
+                            yy_precision prec, void *cuda_stream);
+
+/* Copy a table or intermediate (see yy_table) into host memory; `count` is
+ * the number of float64 values the caller's buffer holds and must equal the
+ * table's size (query it with host_dst = NULL: *count receives the size).
+ * Synchronises the device. */
+yy_status yy_grid_copy_table(yy_grid *g, yy_table which, double *host_dst, size_t *count);
+
+/* Device error word of the handle (synchronises the device).  YY_OK or
+ * YY_ERR_DEVICE_CHECK / YY_ERR_TIMEOUT; reading clears it. */
+yy_status yy_last_device_status(yy_grid *g);
+
+/* Release the handle and all its device memory (NULL-safe; synchronises). */
+void yy_destroy(yy_grid *g);
+
+/* Static description of a status code. */
+const char *yy_status_string(yy_status s);
+
+/* Dense flop count of one solve: 2 M N K of the analysis plus one or four
+ * synthesis contractions (with_gradient = 0 / 1), in floating-point
+ * operations (the algorithmic count, before any operand splitting). */
+double yy_solve_flops(const yy_grid *g, int with_gradient);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* YY_H */

@@ -1,0 +1,302 @@
+// C ABI of libyy: handle life cycle, argument checks and the solve pipeline.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "yy_debug.h"
+#include "yy_internal.h"
+
+namespace yy {
+
+static int g_fail_alloc_countdown = -1;   // test hook: < 0 disabled
+
+cudaError_t dmalloc(void **p, size_t bytes) {
+  *p = nullptr;
+  if (g_fail_alloc_countdown == 0) return cudaErrorMemoryAllocation;
+  if (g_fail_alloc_countdown > 0) --g_fail_alloc_countdown;
+  return cudaMalloc(p, bytes == 0 ? 16 : bytes);
+}
+
+int choose_split_k(int M, int N, int K);
+
+// Gauss-Legendre nodes and weights on [0, 1] (weights sum to 1), by Newton
+// iteration on P_n with the three-term recurrence.
+static void gauss_legendre01(int n, double *x, double *w) {
+  const double pi = 3.141592653589793238462643383279502884;
+  for (int i = 0; i < n; ++i) {
+    double z = cos(pi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = 0.0;
+      for (int k = 1; k <= n; ++k) {
+        const double p2 = p1;
+        p1 = p0;
+        p0 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p2) / k;
+      }
+      dp = n * (z * p0 - p1) / (z * z - 1.0);
+      const double dz = p0 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-17) break;
+    }
+    x[i] = 0.5 * (1.0 - z);
+    w[i] = 1.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+static yy_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return YY_OK;
+  if (e == cudaErrorMemoryAllocation) return YY_ERR_OOM;
+  return YY_ERR_CUDA;
+}
+
+static void free_all(yy_grid *g) {
+  if (!g) return;
+  double *dbufs[] = {g->r_edges, g->w,    g->tbar, g->ban,       g->ysyn,      g->ysyn_t,
+                     g->ysyn_p,  g->scan, g->gl_nodes, g->A,     g->part,      g->cin,
+                     g->Q,       g->stage_rho, g->stage_phi, g->stage_grad};
+  for (double *p : dbufs)
+    if (p) cudaFree(p);
+  float *fbufs[] = {g->ban32, g->ysyn32, g->ysyn_t32, g->ysyn_p32, g->rho32, g->Q32};
+  for (float *p : fbufs)
+    if (p) cudaFree(p);
+  if (g->err) cudaFree(g->err);
+  tc_free(g);
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace yy
+
+using namespace yy;
+
+extern "C" {
+
+void yy_debug_fail_alloc_after(int n) { g_fail_alloc_countdown = n; }
+
+const char *yy_status_string(yy_status s) {
+  switch (s) {
+    case YY_OK: return "ok";
+    case YY_ERR_INVALID_ARG: return "invalid argument";
+    case YY_ERR_OOM: return "device memory allocation failed";
+    case YY_ERR_CUDA: return "CUDA error";
+    case YY_ERR_NOT_SUPPORTED: return "not supported (precision not prepared or device lacks it)";
+    case YY_ERR_TIMEOUT: return "device-side wait timed out";
+    case YY_ERR_DEVICE_CHECK: return "device-side check failed";
+  }
+  return "unknown status";
+}
+
+yy_status yy_grid_create(const double *r_edges, int n_r, int n_theta, int n_phi, double delta_theta,
+                         double delta_phi, int l_max, double G, yy_grid **out) {
+  if (out == nullptr) return YY_ERR_INVALID_ARG;
+  *out = nullptr;
+  const double quarter_pi = 0.78539816339744830962;
+  if (r_edges == nullptr || n_r < 1 || n_r > (1 << 20) || n_theta < 1 || n_phi < 1 ||
+      (long long)n_theta * n_phi > (1 << 24) || l_max < 0 || l_max > YY_LMAX_CAP)
+    return YY_ERR_INVALID_ARG;
+  if (!(delta_theta >= 0.0 && delta_theta < quarter_pi) || !(delta_phi >= 0.0 && delta_phi < quarter_pi))
+    return YY_ERR_INVALID_ARG;
+  if (!isfinite(G)) return YY_ERR_INVALID_ARG;
+  if (!(r_edges[0] >= 0.0) || !isfinite(r_edges[0])) return YY_ERR_INVALID_ARG;
+  for (int i = 0; i < n_r; ++i)
+    if (!(r_edges[i + 1] > r_edges[i]) || !isfinite(r_edges[i + 1])) return YY_ERR_INVALID_ARG;
+
+  yy_grid *g = new (std::nothrow) yy_grid();
+  if (!g) return YY_ERR_OOM;
+  memset((void *)g, 0, sizeof(yy_grid));
+  cudaGetDevice(&g->device);
+  g->n_r = n_r;
+  g->n_theta = n_theta;
+  g->n_phi = n_phi;
+  g->n_ang = n_theta * n_phi;
+  g->lmax = l_max;
+  g->n_lm = (l_max + 1) * (l_max + 1);
+  g->delta_theta = delta_theta;
+  g->delta_phi = delta_phi;
+  g->G = G;
+  g->th0 = quarter_pi - delta_theta;
+  g->ph0 = -3.0 * quarter_pi - delta_phi;
+  g->dth = (2.0 * quarter_pi + 2.0 * delta_theta) / n_theta;
+  g->dph = (6.0 * quarter_pi + 2.0 * delta_phi) / n_phi;
+
+  const size_t n_ang = g->n_ang, n_lm = g->n_lm, M = 2 * (size_t)n_r;
+  g->split_k = choose_split_k((int)M, (int)n_lm, (int)n_ang);
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void **p, size_t bytes) {
+    if (e == cudaSuccess) e = dmalloc(p, bytes);
+  };
+  A((void **)&g->r_edges, (n_r + 1) * sizeof(double));
+  A((void **)&g->w, n_ang * sizeof(double));
+  A((void **)&g->tbar, (size_t)n_theta * n_lm * sizeof(double));
+  A((void **)&g->ban, n_lm * n_ang * sizeof(double));
+  A((void **)&g->ysyn, n_ang * 2 * n_lm * sizeof(double));
+  A((void **)&g->ysyn_t, n_ang * 2 * n_lm * sizeof(double));
+  A((void **)&g->ysyn_p, n_ang * 2 * n_lm * sizeof(double));
+  A((void **)&g->scan, (size_t)n_r * (l_max + 1) * 4 * sizeof(double));
+  A((void **)&g->A, M * n_lm * sizeof(double));
+  if (g->split_k > 1) A((void **)&g->part, (size_t)g->split_k * M * n_lm * sizeof(double));
+  A((void **)&g->cin, M * n_lm * sizeof(double));
+  A((void **)&g->Q, 3 * M * 2 * n_lm * sizeof(double));
+  A((void **)&g->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(g->r_edges, r_edges, (n_r + 1) * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(g->err, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    const int n_gl = l_max + 32;
+    std::vector<double> gl(2 * YY_GL_WEIGHT_NODES + 2 * n_gl);
+    gauss_legendre01(YY_GL_WEIGHT_NODES, gl.data(), gl.data() + YY_GL_WEIGHT_NODES);
+    gauss_legendre01(n_gl, gl.data() + 2 * YY_GL_WEIGHT_NODES, gl.data() + 2 * YY_GL_WEIGHT_NODES + n_gl);
+    e = build_tables(g, gl.data(), n_gl);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    const yy_status st = from_cuda(e);
+    cudaGetLastError();
+    free_all(g);
+    delete g;
+    return st;
+  }
+  *out = g;
+  return YY_OK;
+}
+
+yy_status yy_grid_prepare(yy_grid *g, yy_precision prec) {
+  if (!g) return YY_ERR_INVALID_ARG;
+  switch (prec) {
+    case YY_FP64: return YY_OK;
+    case YY_FP32: {
+      if (g->ban32) return YY_OK;
+      cudaError_t e = convert_tables_f32(g);
+      if (e == cudaSuccess) e = cudaDeviceSynchronize();
+      return from_cuda(e);
+    }
+    case YY_TF32:
+    case YY_BF16X3:
+    case YY_FP16X2: return tc_prepare(g, prec);
+  }
+  return YY_ERR_INVALID_ARG;
+}
+
+static yy_status check_solve_args(yy_grid *g, const double *rho_yin, const double *rho_yang,
+                                  double *phi_yin, double *phi_yang, double *grad_yin,
+                                  double *grad_yang, yy_precision prec) {
+  if (!g || !rho_yin || !rho_yang || !phi_yin || !phi_yang) return YY_ERR_INVALID_ARG;
+  if ((grad_yin == nullptr) != (grad_yang == nullptr)) return YY_ERR_INVALID_ARG;
+  const void *ptrs[] = {rho_yin, rho_yang, phi_yin, phi_yang, grad_yin, grad_yang};
+  for (const void *p : ptrs)
+    if (p && !aligned16(p)) return YY_ERR_INVALID_ARG;
+  if ((int)prec < 0 || (int)prec > (int)YY_FP16X2) return YY_ERR_INVALID_ARG;
+  if (prec == YY_FP32 && !g->ban32) return YY_ERR_NOT_SUPPORTED;
+  if ((prec == YY_TF32 || prec == YY_BF16X3 || prec == YY_FP16X2) && !g->tc[prec]) return YY_ERR_NOT_SUPPORTED;
+  return YY_OK;
+}
+
+yy_status yy_potential(yy_grid *g, const double *rho_yin, const double *rho_yang, double *phi_yin,
+                       double *phi_yang, double *grad_yin, double *grad_yang, yy_precision prec,
+                       void *cuda_stream) {
+  yy_status st = check_solve_args(g, rho_yin, rho_yang, phi_yin, phi_yang, grad_yin, grad_yang, prec);
+  if (st != YY_OK) return st;
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != g->device) return YY_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaError_t e;
+  if (prec == YY_FP64 || prec == YY_FP32) {
+    const bool f32 = (prec == YY_FP32);
+    e = analysis_simt(g, rho_yin, rho_yang, f32, s);
+    if (e == cudaSuccess) e = radial_scan(g, f32, s);
+    if (e == cudaSuccess) e = synthesis_simt(g, phi_yin, phi_yang, grad_yin, grad_yang, f32, s);
+  } else {
+    e = tc_analysis(g, prec, rho_yin, rho_yang, s);
+    if (e == cudaSuccess) e = radial_scan(g, false, s);
+    if (e == cudaSuccess) e = tc_pack_coefficients(g, prec, s);
+    if (e == cudaSuccess) e = tc_synthesis(g, prec, phi_yin, phi_yang, grad_yin, grad_yang, s);
+  }
+  return from_cuda(e);
+}
+
+yy_status yy_potential_host(yy_grid *g, const double *rho_yin, const double *rho_yang, double *phi_yin,
+                            double *phi_yang, double *grad_yin, double *grad_yang, yy_precision prec,
+                            void *cuda_stream) {
+  if (!g || !rho_yin || !rho_yang || !phi_yin || !phi_yang) return YY_ERR_INVALID_ARG;
+  if ((grad_yin == nullptr) != (grad_yang == nullptr)) return YY_ERR_INVALID_ARG;
+  const size_t field = (size_t)g->n_r * g->n_ang;
+  cudaError_t e = cudaSuccess;
+  if (!g->stage_rho) e = dmalloc((void **)&g->stage_rho, 2 * field * sizeof(double));
+  if (e == cudaSuccess && !g->stage_phi) e = dmalloc((void **)&g->stage_phi, 2 * field * sizeof(double));
+  if (e == cudaSuccess && grad_yin && !g->stage_grad) e = dmalloc((void **)&g->stage_grad, 6 * field * sizeof(double));
+  if (e != cudaSuccess) return from_cuda(e);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const size_t bytes = field * sizeof(double);
+  e = cudaMemcpyAsync(g->stage_rho, rho_yin, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g->stage_rho + field, rho_yang, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  double *gy = grad_yin ? g->stage_grad : nullptr;
+  double *gg = grad_yin ? g->stage_grad + 3 * field : nullptr;
+  yy_status st = yy_potential(g, g->stage_rho, g->stage_rho + field, g->stage_phi, g->stage_phi + field, gy, gg,
+                              prec, cuda_stream);
+  if (st != YY_OK) return st;
+  e = cudaMemcpyAsync(phi_yin, g->stage_phi, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(phi_yang, g->stage_phi + field, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && grad_yin) e = cudaMemcpyAsync(grad_yin, gy, 3 * bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && grad_yin) e = cudaMemcpyAsync(grad_yang, gg, 3 * bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return from_cuda(e);
+}
+
+yy_status yy_grid_copy_table(yy_grid *g, yy_table which, double *host_dst, size_t *count) {
+  if (!g || !count) return YY_ERR_INVALID_ARG;
+  const size_t n_ang = g->n_ang, n_lm = g->n_lm, M = 2 * (size_t)g->n_r;
+  const double *src = nullptr;
+  size_t n = 0;
+  switch (which) {
+    case YY_TABLE_WEIGHTS: src = g->w; n = n_ang; break;
+    case YY_TABLE_TBAR: src = g->tbar; n = (size_t)g->n_theta * n_lm; break;
+    case YY_TABLE_ANALYSIS: src = g->ban; n = n_lm * n_ang; break;
+    case YY_TABLE_SYNTH: src = g->ysyn; n = n_ang * 2 * n_lm; break;
+    case YY_TABLE_SYNTH_T: src = g->ysyn_t; n = n_ang * 2 * n_lm; break;
+    case YY_TABLE_SYNTH_P: src = g->ysyn_p; n = n_ang * 2 * n_lm; break;
+    case YY_TABLE_MOMENTS: src = g->A; n = M * n_lm; break;
+    case YY_TABLE_COEFF: src = g->Q; n = M * 2 * n_lm; break;
+    default: return YY_ERR_INVALID_ARG;
+  }
+  if (host_dst == nullptr) {
+    *count = n;
+    return YY_OK;
+  }
+  if (*count != n) return YY_ERR_INVALID_ARG;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(host_dst, src, n * sizeof(double), cudaMemcpyDeviceToHost);
+  return from_cuda(e);
+}
+
+yy_status yy_last_device_status(yy_grid *g) {
+  if (!g) return YY_ERR_INVALID_ARG;
+  int h = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&h, g->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(g->err, 0, sizeof(int));
+  if (e != cudaSuccess) return from_cuda(e);
+  if (h & YY_DEVERR_TIMEOUT) return YY_ERR_TIMEOUT;
+  if (h & YY_DEVERR_CHECK) return YY_ERR_DEVICE_CHECK;
+  return YY_OK;
+}
+
+void yy_destroy(yy_grid *g) {
+  if (!g) return;
+  cudaDeviceSynchronize();
+  free_all(g);
+  delete g;
+}
+
+double yy_solve_flops(const yy_grid *g, int with_gradient) {
+  if (!g) return 0.0;
+  const double M = 2.0 * g->n_r, K_an = g->n_ang, N_an = g->n_lm;
+  const double analysis = 2.0 * M * N_an * K_an;
+  const double synth = 2.0 * M * (2.0 * g->n_lm) * g->n_ang;
+  return analysis + (with_gradient ? 4.0 : 1.0) * synth;
+}
+
+}  // extern "C"

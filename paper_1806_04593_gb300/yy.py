@@ -1,0 +1,233 @@
+"""Thin ctypes binding of libyy (include/yy.h), same names as the C ABI.
+
+Argument marshalling only: every step of a solve runs in the library's CUDA
+kernels.  Arrays are passed as torch tensors (device memory, float64,
+C-contiguous) or as raw integer addresses; streams as torch.cuda.Stream or
+raw cudaStream_t integers.  Loading fails loudly when libyy.so is missing:
+there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libyy.so")
+
+YY_OK = 0
+YY_ERR_INVALID_ARG = 1
+YY_ERR_OOM = 2
+YY_ERR_CUDA = 3
+YY_ERR_NOT_SUPPORTED = 4
+YY_ERR_TIMEOUT = 5
+YY_ERR_DEVICE_CHECK = 6
+
+YY_FP64 = 0
+YY_FP32 = 1
+YY_TF32 = 2
+YY_BF16X3 = 3
+YY_FP16X2 = 4
+PRECISIONS = {"fp64": YY_FP64, "fp32": YY_FP32, "tf32": YY_TF32, "bf16x3": YY_BF16X3, "fp16x2": YY_FP16X2}
+
+YY_TABLE_WEIGHTS = 0
+YY_TABLE_TBAR = 1
+YY_TABLE_ANALYSIS = 2
+YY_TABLE_SYNTH = 3
+YY_TABLE_SYNTH_T = 4
+YY_TABLE_SYNTH_P = 5
+YY_TABLE_MOMENTS = 6
+YY_TABLE_COEFF = 7
+
+_lib = None
+
+
+class YYError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {yy_status_string(status)} (status {status})")
+
+
+def load():
+    """Load libyy.so (build it first with paper_1806_04593_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libyy.so not found at {LIB_PATH}; run paper_1806_04593_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    D = ctypes.c_double
+    I = ctypes.c_int
+    lib.yy_grid_create.argtypes = [P, I, I, I, D, D, I, D, ctypes.POINTER(P)]
+    lib.yy_grid_create.restype = I
+    lib.yy_grid_prepare.argtypes = [P, I]
+    lib.yy_grid_prepare.restype = I
+    lib.yy_potential.argtypes = [P, P, P, P, P, P, P, I, P]
+    lib.yy_potential.restype = I
+    lib.yy_potential_host.argtypes = [P, P, P, P, P, P, P, I, P]
+    lib.yy_potential_host.restype = I
+    lib.yy_grid_copy_table.argtypes = [P, I, P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.yy_grid_copy_table.restype = I
+    lib.yy_last_device_status.argtypes = [P]
+    lib.yy_last_device_status.restype = I
+    lib.yy_destroy.argtypes = [P]
+    lib.yy_destroy.restype = None
+    lib.yy_status_string.argtypes = [I]
+    lib.yy_status_string.restype = ctypes.c_char_p
+    lib.yy_solve_flops.argtypes = [P, I]
+    lib.yy_solve_flops.restype = D
+    lib.yy_debug_fail_alloc_after.argtypes = [I]
+    lib.yy_debug_fail_alloc_after.restype = None
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def yy_status_string(status):
+    return load().yy_status_string(int(status)).decode()
+
+
+def yy_grid_create(r_edges, n_theta, n_phi, delta_theta, delta_phi, l_max, G=1.0):
+    """Returns (status, handle)."""
+    r = np.ascontiguousarray(r_edges, dtype=np.float64)
+    h = ctypes.c_void_p()
+    st = load().yy_grid_create(r.ctypes.data, int(r.size - 1), int(n_theta), int(n_phi),
+                               float(delta_theta), float(delta_phi), int(l_max), float(G),
+                               ctypes.byref(h))
+    return st, h.value
+
+
+def yy_grid_prepare(handle, prec):
+    return load().yy_grid_prepare(handle, int(prec))
+
+
+def yy_potential(handle, rho_yin, rho_yang, phi_yin, phi_yang, grad_yin=None, grad_yang=None,
+                 prec=YY_FP64, stream=None):
+    return load().yy_potential(handle, _ptr(rho_yin), _ptr(rho_yang), _ptr(phi_yin), _ptr(phi_yang),
+                               _ptr(grad_yin), _ptr(grad_yang), int(prec), _stream(stream))
+
+
+def yy_potential_host(handle, rho_yin, rho_yang, phi_yin, phi_yang, grad_yin=None, grad_yang=None,
+                      prec=YY_FP64, stream=None):
+    return load().yy_potential_host(handle, _ptr(rho_yin), _ptr(rho_yang), _ptr(phi_yin),
+                                    _ptr(phi_yang), _ptr(grad_yin), _ptr(grad_yang), int(prec),
+                                    _stream(stream))
+
+
+def yy_grid_copy_table(handle, which):
+    """Returns (status, numpy float64 array)."""
+    lib = load()
+    n = ctypes.c_size_t(0)
+    st = lib.yy_grid_copy_table(handle, int(which), None, ctypes.byref(n))
+    if st != YY_OK:
+        return st, None
+    out = np.empty(n.value, dtype=np.float64)
+    st = lib.yy_grid_copy_table(handle, int(which), out.ctypes.data, ctypes.byref(n))
+    return st, out
+
+
+def yy_last_device_status(handle):
+    return load().yy_last_device_status(handle)
+
+
+def yy_destroy(handle):
+    load().yy_destroy(handle)
+
+
+def yy_solve_flops(handle, with_gradient):
+    return load().yy_solve_flops(handle, int(bool(with_gradient)))
+
+
+def yy_debug_fail_alloc_after(n):
+    load().yy_debug_fail_alloc_after(int(n))
+
+
+class Grid:
+    """Owning wrapper of a yy_grid handle with torch-tensor conveniences."""
+
+    def __init__(self, r_edges, n_theta, n_phi, delta_theta, delta_phi, l_max, G=1.0):
+        st, h = yy_grid_create(r_edges, n_theta, n_phi, delta_theta, delta_phi, l_max, G)
+        if st != YY_OK:
+            raise YYError(st, "yy_grid_create")
+        self.handle = h
+        self.n_r = int(np.asarray(r_edges).size - 1)
+        self.n_theta, self.n_phi, self.l_max = int(n_theta), int(n_phi), int(l_max)
+        self.n_lm = (self.l_max + 1) ** 2
+
+    @classmethod
+    def from_spec(cls, spec):
+        return cls(spec.r_edges, spec.n_theta, spec.n_phi, spec.delta_theta, spec.delta_phi,
+                   spec.lmax, spec.G)
+
+    @property
+    def field_shape(self):
+        return (self.n_r, self.n_theta, self.n_phi)
+
+    def prepare(self, prec):
+        st = yy_grid_prepare(self.handle, PRECISIONS.get(prec, prec))
+        if st != YY_OK:
+            raise YYError(st, "yy_grid_prepare")
+
+    def potential(self, rho_yin, rho_yang, phi_yin, phi_yang, grad_yin=None, grad_yang=None,
+                  prec=YY_FP64, stream=None):
+        st = yy_potential(self.handle, rho_yin, rho_yang, phi_yin, phi_yang, grad_yin, grad_yang,
+                          PRECISIONS.get(prec, prec), stream)
+        if st != YY_OK:
+            raise YYError(st, "yy_potential")
+
+    def solve(self, rho_yin, rho_yang, gradient=False, prec=YY_FP64, stream=None):
+        """Allocate outputs (torch, same device) and solve; returns a dict."""
+        import torch
+        phi_yin = torch.empty_like(rho_yin)
+        phi_yang = torch.empty_like(rho_yang)
+        g_yin = g_yang = None
+        if gradient:
+            g_yin = torch.empty((3,) + tuple(rho_yin.shape), dtype=torch.float64, device=rho_yin.device)
+            g_yang = torch.empty_like(g_yin)
+        self.potential(rho_yin, rho_yang, phi_yin, phi_yang, g_yin, g_yang, prec, stream)
+        out = {"phi_yin": phi_yin, "phi_yang": phi_yang}
+        if gradient:
+            out["grad_yin"], out["grad_yang"] = g_yin, g_yang
+        return out
+
+    def table(self, which):
+        st, arr = yy_grid_copy_table(self.handle, which)
+        if st != YY_OK:
+            raise YYError(st, "yy_grid_copy_table")
+        return arr
+
+    def flops(self, gradient):
+        return yy_solve_flops(self.handle, gradient)
+
+    def close(self):
+        if self.handle:
+            yy_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,262 @@
+"""GPU path (through the C ABI) against the CPU oracle.
+
+Tolerance of the float64 path: 1e-12 relative (max-norm over the field) for
+Phi and -grad Phi, the bar the solver is specified to; tables 1e-13.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from paper_1806_04593_gb300 import inputs
+
+from .gpu_common import K_lm, gpu_solve, lib, mode_index, rel_l2, rel_max, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def yy():
+    require_gpu()
+    return lib()
+
+
+_GRIDS = {}
+
+
+def _grid(yy, spec):
+    key = spec.name
+    if key not in _GRIDS:
+        _GRIDS[key] = yy.Grid.from_spec(spec)
+    return _GRIDS[key]
+
+
+# ---------------------------------------------------------------------------
+# tables
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["tiny", "mid"])
+def test_weight_table(yy, oracle_grid, name):
+    spec = inputs.GRIDS[name]()
+    g = _grid(yy, spec)
+    w = g.table(yy.YY_TABLE_WEIGHTS).reshape(spec.n_theta, spec.n_phi)
+    og = oracle_grid(spec)
+    assert np.abs(w - og.w).max() <= 1e-13
+    te, pe = og.theta_edges, og.phi_edges
+    dO = (np.cos(te[:-1]) - np.cos(te[1:]))[:, None] * (pe[1:] - pe[:-1])[None, :]
+    assert abs((dO * w).sum() - 2 * math.pi) <= 1e-12
+
+
+def test_weight_table_production(yy, oracle_grid):
+    spec = inputs.production_grid()
+    g = _grid(yy, spec)
+    w = g.table(yy.YY_TABLE_WEIGHTS).reshape(spec.n_theta, spec.n_phi)
+    assert np.abs(w - oracle_grid(spec).w).max() <= 1e-13
+
+
+@pytest.mark.parametrize("name", ["tiny", "mid"])
+def test_polar_and_analysis_tables(yy, oracle_grid, name):
+    spec = inputs.GRIDS[name]()
+    g = _grid(yy, spec)
+    og = oracle_grid(spec)
+    L = spec.lmax
+    K = K_lm(og.N)
+    modes = mode_index(L)
+    tb = g.table(yy.YY_TABLE_TBAR).reshape(spec.n_theta, len(modes))
+    ban = g.table(yy.YY_TABLE_ANALYSIS).reshape(len(modes), spec.n_ang)
+    for idx, (l, m, kind) in enumerate(modes):
+        ref = K[l, m] * og.T[l, m]
+        assert np.abs(tb[:, idx] - ref).max() <= 1e-13 * max(np.abs(ref).max(), 1e-300), (l, m)
+        cs = og.C[m] if kind == "c" else og.S[m]
+        ref_b = (og.w * ref[:, None] * cs[None, :]).reshape(-1)
+        scale = max(np.abs(ref_b).max(), 1e-300)
+        assert np.abs(ban[idx] - ref_b).max() <= 1e-13 * scale, (l, m, kind)
+
+
+@pytest.mark.parametrize("name", ["tiny", "mid"])
+def test_synthesis_tables_same_and_cross(yy, oracle_grid, name):
+    from oracle import assoc_legendre, other_patch_angles
+    spec = inputs.GRIDS[name]()
+    g = _grid(yy, spec)
+    og = oracle_grid(spec)
+    L = spec.lmax
+    K = K_lm(og.N)
+    modes = mode_index(L)
+    n_lm = len(modes)
+    ys = g.table(yy.YY_TABLE_SYNTH).reshape(spec.n_ang, 2 * n_lm)
+    th, ph = og.target_theta, og.target_phi
+    tx, px = other_patch_angles(th, ph)
+    for half, (t, p) in enumerate(((th, ph), (tx, px))):
+        P = assoc_legendre(L, np.cos(t), np.sin(t))
+        for idx, (l, m, kind) in enumerate(modes):
+            f = np.cos(m * p) if kind == "c" else np.sin(m * p)
+            ref = K[l, m] * P[l, m] * f
+            got = ys[:, half * n_lm + idx]
+            assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max()), (half, l, m, kind)
+
+
+# ---------------------------------------------------------------------------
+# solves
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["tiny", "mid"])
+def test_fp64_potential_and_gradient_match_oracle(yy, oracle_grid, name):
+    spec = inputs.GRIDS[name]()
+    g = _grid(yy, spec)
+    ry, rg = inputs.density_for(spec)
+    out = gpu_solve(g, ry, rg, gradient=True)
+    ref = oracle_grid(spec).solve(ry, rg, gradient=True)
+    for q in ("yin", "yang"):
+        assert rel_max(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64, q
+        assert rel_l2(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64, q
+        assert rel_max(out["grad_" + q], ref["grad_" + q]) <= TOL_FP64, q
+
+
+def test_fp64_production_sampled_cells(yy, oracle_grid):
+    """Full 1-degree, l_max = 25 grid in the launch configuration of the
+    benchmark; every radius at a sample of target cells."""
+    spec = inputs.production_grid()
+    g = _grid(yy, spec)
+    ry, rg = inputs.density_for(spec)
+    out = gpu_solve(g, ry, rg, gradient=True)
+    rng = np.random.default_rng(31)
+    cells = np.sort(rng.choice(spec.n_ang, 64, replace=False))
+    ref = oracle_grid(spec).solve(ry, rg, gradient=True, cells=cells)
+    j, k = np.divmod(cells, spec.n_phi)
+    for q in ("yin", "yang"):
+        got = out["phi_" + q][:, j, k]
+        assert rel_max(got, ref["phi_" + q]) <= TOL_FP64, q
+        gg = out["grad_" + q][:, :, j, k]
+        assert rel_max(gg, ref["grad_" + q]) <= TOL_FP64, q
+
+
+def test_ragged_small_grid(yy):
+    """Odd sizes that leave ragged tiles everywhere (n_r, n_ang, n_lm not
+    multiples of any tile), r_edges[0] = 0, unequal buffers."""
+    from oracle import OracleGrid
+    spec = inputs.GridSpec("ragged", np.concatenate([[0.0], np.logspace(-2, 0, 70)]), 13, 37,
+                           0.06, 0.02, 11, 0.5)
+    rng = np.random.default_rng(32)
+    ry = rng.uniform(0.0, 1.0, (spec.n_r, 13, 37))
+    rg = rng.uniform(0.0, 1.0, (spec.n_r, 13, 37))
+    g = yy.Grid.from_spec(spec)
+    out = gpu_solve(g, ry, rg, gradient=True)
+    ref = OracleGrid(spec.r_edges, 13, 37, 0.06, 0.02, 11, 0.5).solve(ry, rg, gradient=True)
+    for q in ("yin", "yang"):
+        assert rel_max(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64
+        assert rel_max(out["grad_" + q], ref["grad_" + q]) <= TOL_FP64
+    g.close()
+
+
+def test_degenerate_lmax0_single_zone(yy):
+    """l_max = 0 (monopole only), one radial zone, a 1 x 1 patch."""
+    from oracle import OracleGrid
+    r = np.array([0.1, 1.0])
+    g = yy.Grid(r, 1, 1, 0.0, 0.0, 0, 1.0)
+    ry = np.full((1, 1, 1), 2.0)
+    rg = np.full((1, 1, 1), 3.0)
+    out = gpu_solve(g, ry, rg, gradient=True)
+    ref = OracleGrid(r, 1, 1, 0.0, 0.0, 0, 1.0).solve(ry, rg, gradient=True)
+    for q in ("yin", "yang"):
+        assert rel_max(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64
+        assert rel_max(out["grad_" + q][0], ref["grad_" + q][0]) <= TOL_FP64
+    g.close()
+
+
+def test_zero_density_gives_zero(yy):
+    spec = inputs.tiny_grid()
+    g = _grid(yy, spec)
+    z = np.zeros((spec.n_r, spec.n_theta, spec.n_phi))
+    out = gpu_solve(g, z, z, gradient=True)
+    for v in out.values():
+        assert np.all(v == 0.0)
+
+
+def test_swap_symmetry_bitwise_and_determinism(yy):
+    spec = inputs.mid_grid()
+    g = _grid(yy, spec)
+    ry, rg = inputs.density_for(spec)
+    a = gpu_solve(g, ry, rg, gradient=True)
+    b = gpu_solve(g, rg, ry, gradient=True)
+    c = gpu_solve(g, ry, rg, gradient=True)
+    assert np.array_equal(a["phi_yin"], b["phi_yang"])
+    assert np.array_equal(a["phi_yang"], b["phi_yin"])
+    assert np.array_equal(a["grad_yin"], b["grad_yang"])
+    for key in a:
+        assert np.array_equal(a[key], c[key])
+
+
+def test_linearity(yy):
+    spec = inputs.tiny_grid()
+    g = _grid(yy, spec)
+    rng = np.random.default_rng(33)
+    shape = (spec.n_r, spec.n_theta, spec.n_phi)
+    r1 = [rng.uniform(0, 1, shape) for _ in range(2)]
+    r2 = [rng.uniform(0, 1, shape) for _ in range(2)]
+    a = gpu_solve(g, *r1)["phi_yin"]
+    b = gpu_solve(g, *r2)["phi_yin"]
+    c = gpu_solve(g, 2 * r1[0] - 3 * r2[0], 2 * r1[1] - 3 * r2[1])["phi_yin"]
+    assert np.abs(c - (2 * a - 3 * b)).max() <= 1e-13 * np.abs(c).max()
+
+
+def test_host_entry_point_matches_device_path(yy):
+    import torch
+    spec = inputs.tiny_grid()
+    g = _grid(yy, spec)
+    ry, rg = inputs.density_for(spec)
+    dev = gpu_solve(g, ry, rg, gradient=True)
+    shape = (spec.n_r, spec.n_theta, spec.n_phi)
+    h = {k: torch.empty(s, dtype=torch.float64).pin_memory()
+         for k, s in (("py", shape), ("pg", shape), ("gy", (3,) + shape), ("gg", (3,) + shape))}
+    ryt = torch.from_numpy(np.ascontiguousarray(ry)).pin_memory()
+    rgt = torch.from_numpy(np.ascontiguousarray(rg)).pin_memory()
+    st = yy.yy_potential_host(g.handle, ryt, rgt, h["py"], h["pg"], h["gy"], h["gg"], yy.YY_FP64,
+                              torch.cuda.current_stream())
+    assert st == yy.YY_OK
+    assert np.array_equal(h["py"].numpy(), dev["phi_yin"])
+    assert np.array_equal(h["gg"].numpy(), dev["grad_yang"])
+
+
+def test_error_paths(yy):
+    import torch
+    spec = inputs.tiny_grid()
+    g = _grid(yy, spec)
+    x = torch.zeros((spec.n_r, spec.n_theta, spec.n_phi), dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(x)
+    # one gradient pointer only
+    assert yy.yy_potential(g.handle, x, x, y, y, y, None) == yy.YY_ERR_INVALID_ARG
+    # misaligned pointer
+    assert yy.yy_potential(g.handle, x.data_ptr() + 8, x, y, y) == yy.YY_ERR_INVALID_ARG
+    # unknown precision
+    assert yy.yy_potential(g.handle, x, x, y, y, prec=9) == yy.YY_ERR_INVALID_ARG
+    assert yy.yy_last_device_status(g.handle) == yy.YY_OK
+
+
+def test_allocation_failure_is_reported_cleanly(yy):
+    spec = inputs.tiny_grid()
+    for n in (0, 3, 7):
+        yy.yy_debug_fail_alloc_after(n)
+        st, h = yy.yy_grid_create(spec.r_edges, spec.n_theta, spec.n_phi, spec.delta_theta,
+                                  spec.delta_phi, spec.lmax)
+        yy.yy_debug_fail_alloc_after(-1)
+        assert st == yy.YY_ERR_OOM and not h
+    # the library still works afterwards
+    g = yy.Grid.from_spec(spec)
+    g.close()
+
+
+def test_fp32_path_tolerance(yy, oracle_grid):
+    """float32 contractions (float64 tables cast once, float64 scans):
+    rounding of the operands, 2^-24 relative, accumulated over K terms."""
+    spec = inputs.mid_grid()
+    g = _grid(yy, spec)
+    g.prepare("fp32")
+    ry, rg = inputs.density_for(spec)
+    out = gpu_solve(g, ry, rg, gradient=True, prec="fp32")
+    ref = oracle_grid(spec).solve(ry, rg, gradient=True)
+    for q in ("yin", "yang"):
+        assert rel_max(out["phi_" + q], ref["phi_" + q]) <= 1e-5
+        assert rel_max(out["grad_" + q], ref["grad_" + q]) <= 1e-4
