@@ -1,0 +1,392 @@
+#!/usr/bin/env python3
+"""Benchmark of the Yin-Yang multipole gravity solver on GB300.
+
+Workload: the 1-degree Yin-Yang grid (90 x 270 cells per patch), 550
+log-spaced zones in [1e-4, 1], l_max = 25, with the seeded proto-neutron-star
+density; tables prebuilt.  One step = one solve of Phi and -grad Phi on both
+patches (analysis, radial scans, four synthesis contractions).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec P] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is solves/s over all ranks from
+device-side CUDA events; `e2e` is the same metric through yy_potential_host
+(host buffers, host<->device copies inside the timed region).  With several
+GPUs every rank solves its own field (replicas, weak scaling).  The reference
+arm times the CPU float64 oracle on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "YY Poisson solves/s and GEMM TFLOP/s (1° grid, l_max=25) at stated rel. error vs FP64"
+UNIT = "solves/s"
+L2_BYTES = 126 * 1024 * 1024
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="auto")
+    ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=4, help="oracle evaluates 1/S of the cells")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only: a barrier and a max over ranks)
+# ---------------------------------------------------------------------------
+
+class Dist:
+    def __init__(self, init=True):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1 and init:
+            import torch.distributed as dist
+            backend = "nccl" if self._cuda() else "gloo"
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    @staticmethod
+    def _cuda():
+        import torch
+        return torch.cuda.is_available()
+
+    def barrier(self):
+        if self.pg:
+            import torch
+            if self._cuda():
+                self.pg.barrier(device_ids=[self.local])
+            else:
+                self.pg.barrier()
+
+    def max(self, x):
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([float(x)], device="cuda" if self._cuda() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on a bounded sample (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_solve(og, ry, rg, cells, gradient):
+    t0 = time.perf_counter()
+    res = og.solve(ry, rg, gradient=gradient, cells=cells)
+    return res, time.perf_counter() - t0
+
+
+def oracle_fixed_cost(og, ry, rg):
+    """Time of the density-dependent part that does not scale with the
+    number of target cells (analysis and radial sums of both patches)."""
+    t0 = time.perf_counter()
+    for rho in (ry, rg):
+        og.radial_sums(*og.analysis(rho))
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(spec, ry, rg, gradient, sample_div):
+    import numpy as np
+    from oracle import OracleGrid
+    og = OracleGrid(spec.r_edges, spec.n_theta, spec.n_phi, spec.delta_theta, spec.delta_phi,
+                    spec.lmax, spec.G)
+    cells = np.arange(0, spec.n_ang, sample_div)
+    fixed = oracle_fixed_cost(og, ry, rg)
+    res, t_sample = oracle_sample_solve(og, ry, rg, cells, gradient)
+    t_full = fixed + (t_sample - fixed) * (spec.n_ang / cells.size)
+    info = {"value": 1.0 / t_full, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"numpy float64 oracle: analysis + radial sums of both patches in full "
+                       f"({fixed:.2f} s), Phi{' and -grad Phi' if gradient else ''} at 1/{sample_div} "
+                       f"of the target cells ({cells.size} cells x {spec.n_r} radii, "
+                       f"{t_sample - fixed:.2f} s), evaluation time scaled x{spec.n_ang / cells.size:.1f}; "
+                       f"tables prebuilt; numpy BLAS threading")}
+    return info, res, cells
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, dist):
+    import numpy as np
+    import torch
+
+    from paper_1806_04593_gb300 import build as yybuild
+    from paper_1806_04593_gb300 import inputs, yy
+
+    if dist.rank == 0:
+        yybuild.build()
+    dist.barrier()
+    yy.load()
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    stream = torch.cuda.current_stream(dev)
+    gradient = not args.no_grad
+
+    spec = inputs.production_grid()
+    grid = yy.Grid.from_spec(spec)
+    prec = args.prec
+    if prec == "auto":
+        prec = "fp64"
+    grid.prepare(prec)
+    ry_np, rg_np = inputs.density_for(spec)
+    ry = torch.from_numpy(ry_np).to(dev)
+    rg = torch.from_numpy(rg_np).to(dev)
+    shape = grid.field_shape
+    phi_y = torch.empty(shape, dtype=torch.float64, device=dev)
+    phi_g = torch.empty_like(phi_y)
+    g_y = torch.empty((3,) + shape, dtype=torch.float64, device=dev) if gradient else None
+    g_g = torch.empty_like(g_y) if gradient else None
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def solve():
+        grid.potential(ry, rg, phi_y, phi_g, g_y, g_g, prec=prec, stream=stream)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    launches = yy.yy_last_launch_count(grid.handle)
+
+    # ---- device-timed region
+    yy.yy_grid_set_profiling(grid.handle, 1)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage_tot = {k: 0.0 for k in yy.STAGES}
+    clocks = ClockSampler(dist.local)
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    w0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()                              # evict L2 between steps (outside the events)
+        starts[i].record(stream)
+        solve()
+        ends[i].record(stream)
+        st, stages = yy.yy_grid_stage_ms(grid.handle)
+        for k in stage_tot:
+            stage_tot[k] += stages[k]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    dist.barrier()
+    clk = clocks.stop()
+    yy.yy_grid_set_profiling(grid.handle, 0)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    dev_s = sum(step_ms) / 1e3
+    dev_s_max = dist.max(dev_s)
+    value = dist.world * args.steps / dev_s_max
+
+    # ---- end to end through the host-buffer entry point
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_ry, h_rg = pin(ry_np), pin(rg_np)
+    h_py = torch.empty(shape, dtype=torch.float64).pin_memory()
+    h_pg = torch.empty(shape, dtype=torch.float64).pin_memory()
+    h_gy = torch.empty((3,) + shape, dtype=torch.float64).pin_memory() if gradient else None
+    h_gg = torch.empty((3,) + shape, dtype=torch.float64).pin_memory() if gradient else None
+    pcode = yy.PRECISIONS[prec]
+    for _ in range(max(1, args.warmup // 2)):
+        yy.yy_potential_host(grid.handle, h_ry, h_rg, h_py, h_pg, h_gy, h_gg, pcode, stream)
+    dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st = yy.yy_potential_host(grid.handle, h_ry, h_rg, h_py, h_pg, h_gy, h_gg, pcode, stream)
+        assert st == yy.YY_OK, yy.yy_status_string(st)
+    e2e_s = dist.max(time.perf_counter() - t0)
+    field_bytes = ry_np.nbytes
+    h2d = 2 * field_bytes
+    d2h = 2 * field_bytes + (6 * field_bytes if gradient else 0)
+
+    # ---- roofline of the dominant kernel (the synthesis contraction)
+    n_synth = 4 if gradient else 1
+    synth_ms = (stage_tot["synth_phi"] + stage_tot["synth_grad"]) / args.steps / n_synth
+    synth_flop = 2.0 * (2 * spec.n_r) * (2 * grid.n_lm) * spec.n_ang
+    total_flop = grid.flops(gradient)
+    if prec in ("fp64",):
+        roof = {"bound": "alu", "kernel": "k_gemm_tn<double> (synthesis, FP64 DFMA)",
+                "achieved": synth_flop / (synth_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz"}
+    else:
+        roof = {"bound": "alu", "kernel": "k_gemm_tn<float> (synthesis, FP32 FFMA)",
+                "achieved": synth_flop / (synth_ms / 1e3) / 1e12,
+                "peak": 152 * 128 * 2 * 2.070e9 / 1e12, "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dev_s_max * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32"}.get(prec, prec),
+        "data": "synthetic (seeded proto-neutron-star density, l<=4 angular perturbation)",
+        "config": {"workload": "1-degree Yin-Yang grid, 2 x 90 x 270 cells, n_r=550 log r in [1e-4,1], "
+                               "l_max=25, Phi and -grad Phi per solve" if gradient else
+                               "1-degree Yin-Yang grid, 2 x 90 x 270 cells, n_r=550, l_max=25, Phi only",
+                   "n_r": spec.n_r, "n_theta": spec.n_theta, "n_phi": spec.n_phi, "l_max": spec.lmax,
+                   "gradient": gradient, "precision": prec, "parallelism": f"replicas x{dist.world}",
+                   "l2": "L2 flushed (256 MB write) before every timed step"},
+        "gemm_tflops": total_flop / (dev_s_max / args.steps) / 1e12,
+        "stage_ms": {k: v / args.steps for k, v in stage_tot.items()},
+        "wall_s": wall,
+        "roofline": roof,
+        "e2e": {"value": dist.world * args.steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches * args.steps,
+        "clocks": clk,
+    }
+
+    # ---- CPU baseline (oracle) and error vs the float64 oracle, rank 0 at N=1
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        info, ref, cells = cpu_baseline(spec, ry_np, rg_np, gradient, args.cpu_sample)
+        out["cpu_baseline"] = info
+        j, k = np.divmod(cells, spec.n_phi)
+        err = {}
+        got = {"phi_yin": phi_y, "phi_yang": phi_g, "grad_yin": g_y, "grad_yang": g_g}
+        for key in ("phi_yin", "phi_yang") + (("grad_yin", "grad_yang") if gradient else ()):
+            a = got[key].cpu().numpy()
+            a = a[:, j, k] if key.startswith("phi") else a[:, :, j, k]
+            r = ref[key]
+            err[key] = {"rel_max": float(np.abs(a - r).max() / np.abs(r).max()),
+                        "rel_l2": float(np.linalg.norm(a - r) / np.linalg.norm(r))}
+        out["error_vs_fp64_oracle"] = err
+    grid.close()
+    return out
+
+
+def run_reference(args, dist):
+    """CPU float64 oracle on a bounded sample of the same workload."""
+    if dist.rank != 0:
+        return None
+    from oracle import OracleGrid
+    import numpy as np
+    from paper_1806_04593_gb300 import inputs
+    gradient = not args.no_grad
+    spec = inputs.production_grid()
+    ry, rg = inputs.density_for(spec)
+    og = OracleGrid(spec.r_edges, spec.n_theta, spec.n_phi, spec.delta_theta, spec.delta_phi,
+                    spec.lmax, spec.G)
+    cells = np.arange(0, spec.n_ang, args.cpu_sample)
+    scale = spec.n_ang / cells.size
+    for _ in range(args.warmup):
+        oracle_sample_solve(og, ry, rg, cells, gradient)
+    per = []
+    for _ in range(args.steps):
+        fixed = oracle_fixed_cost(og, ry, rg)
+        _, t = oracle_sample_solve(og, ry, rg, cells, gradient)
+        per.append(fixed + (t - fixed) * scale)
+    value = args.steps / sum(per)
+    sample = (f"float64 oracle; per step: analysis + radial sums of both patches in full, "
+              f"Phi{' and -grad Phi' if gradient else ''} at 1/{args.cpu_sample} of the cells, "
+              f"evaluation time scaled x{scale:.1f}")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "1-degree Yin-Yang grid, 2 x 90 x 270 cells, n_r=550, l_max=25, "
+                                   + ("Phi and -grad Phi" if gradient else "Phi only"),
+                       "n_r": spec.n_r, "n_theta": spec.n_theta, "n_phi": spec.n_phi,
+                       "l_max": spec.lmax, "gradient": gradient},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    dist = Dist(init=(args.impl == "ours"))
+    try:
+        out = run_reference(args, dist) if args.impl == "reference" else run_ours(args, dist)
+        if out is not None and dist.rank == 0:
+            print(json.dumps(out))
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -162,6 +162,27 @@ void yy_destroy(yy_grid *g);
 /* Static description of a status code. */
 const char *yy_status_string(yy_status s);
 
+/* Stage timing (diagnostics).  When enabled, yy_potential records CUDA
+ * events on its stream at the stage boundaries; yy_grid_stage_ms synchronises
+ * and returns the durations of the last solve in milliseconds:
+ *   ms[YY_STAGE_ANALYSIS]   analysis contraction (operand packing included)
+ *   ms[YY_STAGE_SCAN]       radial scans (coefficient packing included)
+ *   ms[YY_STAGE_SYNTH_PHI]  synthesis of Phi (one contraction)
+ *   ms[YY_STAGE_SYNTH_GRAD] synthesis of -grad Phi (three contractions; 0
+ *                           without gradient)                              */
+typedef enum {
+  YY_STAGE_ANALYSIS = 0,
+  YY_STAGE_SCAN = 1,
+  YY_STAGE_SYNTH_PHI = 2,
+  YY_STAGE_SYNTH_GRAD = 3,
+  YY_STAGE_COUNT = 4
+} yy_stage;
+yy_status yy_grid_set_profiling(yy_grid *g, int enable);
+yy_status yy_grid_stage_ms(yy_grid *g, double *ms);
+
+/* Number of CUDA kernels the last yy_potential call launched (-1 for NULL). */
+int yy_last_launch_count(const yy_grid *g);
+
 /* Dense flop count of one solve: 2 M N K of the analysis plus one or four
  * synthesis contractions (with_gradient = 0 / 1), in floating-point
  * operations (the algorithmic count, before any operand splitting). */

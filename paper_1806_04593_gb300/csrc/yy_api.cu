@@ -202,18 +202,30 @@ yy_status yy_potential(yy_grid *g, const double *rho_yin, const double *rho_yang
   cudaGetDevice(&dev);
   if (dev != g->device) return YY_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  cudaError_t e;
-  if (prec == YY_FP64 || prec == YY_FP32) {
-    const bool f32 = (prec == YY_FP32);
-    e = analysis_simt(g, rho_yin, rho_yang, f32, s);
-    if (e == cudaSuccess) e = radial_scan(g, f32, s);
-    if (e == cudaSuccess) e = synthesis_simt(g, phi_yin, phi_yang, grad_yin, grad_yang, f32, s);
-  } else {
-    e = tc_analysis(g, prec, rho_yin, rho_yang, s);
-    if (e == cudaSuccess) e = radial_scan(g, false, s);
-    if (e == cudaSuccess) e = tc_pack_coefficients(g, prec, s);
-    if (e == cudaSuccess) e = tc_synthesis(g, prec, phi_yin, phi_yang, grad_yin, grad_yang, s);
-  }
+  const bool prof = g->profiling != 0;
+  cudaError_t e = cudaSuccess;
+  auto mark = [&](int i) {
+    if (prof && e == cudaSuccess) e = cudaEventRecord(g->ev[i], s);
+  };
+  const bool simt = (prec == YY_FP64 || prec == YY_FP32);
+  const bool f32 = (prec == YY_FP32);
+  g->launches = 0;
+  mark(0);
+  if (e == cudaSuccess)
+    e = simt ? analysis_simt(g, rho_yin, rho_yang, f32, s) : tc_analysis(g, prec, rho_yin, rho_yang, s);
+  mark(1);
+  if (e == cudaSuccess) e = radial_scan(g, f32, s);
+  if (e == cudaSuccess && !simt) e = tc_pack_coefficients(g, prec, s);
+  mark(2);
+  if (e == cudaSuccess)
+    e = simt ? synthesis_simt(g, 0, phi_yin, phi_yang, grad_yin, grad_yang, f32, s)
+             : tc_synthesis(g, prec, 0, phi_yin, phi_yang, grad_yin, grad_yang, s);
+  mark(3);
+  if (e == cudaSuccess && grad_yin != nullptr)
+    e = simt ? synthesis_simt(g, 1, phi_yin, phi_yang, grad_yin, grad_yang, f32, s)
+             : tc_synthesis(g, prec, 1, phi_yin, phi_yang, grad_yin, grad_yang, s);
+  mark(4);
+  g->last_had_grad = grad_yin != nullptr;
   return from_cuda(e);
 }
 
@@ -287,9 +299,38 @@ yy_status yy_last_device_status(yy_grid *g) {
 void yy_destroy(yy_grid *g) {
   if (!g) return;
   cudaDeviceSynchronize();
+  if (g->profiling) yy_grid_set_profiling(g, 0);
   free_all(g);
   delete g;
 }
+
+yy_status yy_grid_set_profiling(yy_grid *g, int enable) {
+  if (!g) return YY_ERR_INVALID_ARG;
+  if (enable && !g->profiling) {
+    for (int i = 0; i < 5; ++i) {
+      cudaError_t e = cudaEventCreate(&g->ev[i]);
+      if (e != cudaSuccess) return from_cuda(e);
+    }
+  } else if (!enable && g->profiling) {
+    cudaDeviceSynchronize();
+    for (int i = 0; i < 5; ++i) cudaEventDestroy(g->ev[i]);
+  }
+  g->profiling = enable ? 1 : 0;
+  return YY_OK;
+}
+
+yy_status yy_grid_stage_ms(yy_grid *g, double *ms) {
+  if (!g || !ms || !g->profiling) return YY_ERR_INVALID_ARG;
+  cudaError_t e = cudaEventSynchronize(g->ev[4]);
+  float t[4] = {0, 0, 0, 0};
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&t[i], g->ev[i], g->ev[i + 1]);
+  if (e != cudaSuccess) return from_cuda(e);
+  for (int i = 0; i < 4; ++i) ms[i] = t[i];
+  if (!g->last_had_grad) ms[YY_STAGE_SYNTH_GRAD] = 0.0;
+  return YY_OK;
+}
+
+int yy_last_launch_count(const yy_grid *g) { return g ? g->launches : -1; }
 
 double yy_solve_flops(const yy_grid *g, int with_gradient) {
   if (!g) return 0.0;

@@ -159,6 +159,7 @@ cudaError_t analysis_simt(yy_grid *g, const double *rho_yin, const double *rho_y
   if (fp32) {
     const size_t pp = (size_t)g->n_r * g->n_ang;
     k_rho_to_f32<<<(unsigned)((pp + 255) / 256), 256, 0, s>>>(pp, rho_yin, rho_yang, g->rho32);
+    g->launches++;
     err = launch_gemm<float, float>(M, N, K, splits, g->rho32, g->rho32 + pp, g->n_r, K, g->ban32, K,
                                     out, out, M, N, s);
   } else {
@@ -166,15 +167,17 @@ cudaError_t analysis_simt(yy_grid *g, const double *rho_yin, const double *rho_y
                                       out, M, N, s);
   }
   if (err != cudaSuccess) return err;
+  g->launches++;
   if (splits > 1) {
     const size_t count = (size_t)M * N;
     k_sum_partials<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(count, splits, g->part, g->A);
+    g->launches++;
     err = cudaGetLastError();
   }
   return err;
 }
 
-cudaError_t synthesis_simt(yy_grid *g, double *phi_yin, double *phi_yang, double *grad_yin,
+cudaError_t synthesis_simt(yy_grid *g, int which, double *phi_yin, double *phi_yang, double *grad_yin,
                            double *grad_yang, bool fp32, cudaStream_t s) {
   const int M = 2 * g->n_r, N = g->n_ang, K = 2 * g->n_lm;
   const size_t qsz = (size_t)M * K;
@@ -189,8 +192,9 @@ cudaError_t synthesis_simt(yy_grid *g, double *phi_yin, double *phi_yang, double
                {1, 0, grad_yin, grad_yang},
                {2, 1, grad_yin ? grad_yin + comp : nullptr, grad_yang ? grad_yang + comp : nullptr},
                {2, 2, grad_yin ? grad_yin + 2 * comp : nullptr, grad_yang ? grad_yang + 2 * comp : nullptr}};
-  const int n_jobs = (grad_yin != nullptr) ? 4 : 1;
-  for (int t = 0; t < n_jobs; ++t) {
+  const int t0 = (which == 0) ? 0 : 1;
+  const int t1 = (which == 0) ? 1 : 4;
+  for (int t = t0; t < t1; ++t) {
     const Job &jb = jobs[t];
     if (fp32) {
       const float *tabs[3] = {g->ysyn32, g->ysyn_t32, g->ysyn_p32};
@@ -204,6 +208,7 @@ cudaError_t synthesis_simt(yy_grid *g, double *phi_yin, double *phi_yang, double
                                         g->n_r, N, s);
     }
     if (err != cudaSuccess) return err;
+    g->launches++;
   }
   return cudaSuccess;
 }

@@ -122,6 +122,7 @@ cudaError_t radial_scan(yy_grid *g, bool want_f32, cudaStream_t s) {
   const int blocks = (warps * 32 + 255) / 256;
   k_radial_scan<<<blocks, 256, 0, s>>>(g->n_r, g->lmax, g->n_lm, g->G, g->A, g->scan, g->r_edges,
                                        g->cin, g->Q, want_f32 ? g->Q32 : nullptr);
+  g->launches++;
   return cudaGetLastError();
 }
 

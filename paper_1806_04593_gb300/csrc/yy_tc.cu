@@ -9,7 +9,7 @@ cudaError_t tc_analysis(yy_grid *, yy_precision, const double *, const double *,
   return cudaErrorNotSupported;
 }
 cudaError_t tc_pack_coefficients(yy_grid *, yy_precision, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t tc_synthesis(yy_grid *, yy_precision, double *, double *, double *, double *, cudaStream_t) {
+cudaError_t tc_synthesis(yy_grid *, yy_precision, int, double *, double *, double *, double *, cudaStream_t) {
   return cudaErrorNotSupported;
 }
 

@@ -79,6 +79,12 @@ def load():
     lib.yy_status_string.restype = ctypes.c_char_p
     lib.yy_solve_flops.argtypes = [P, I]
     lib.yy_solve_flops.restype = D
+    lib.yy_last_launch_count.argtypes = [P]
+    lib.yy_last_launch_count.restype = I
+    lib.yy_grid_set_profiling.argtypes = [P, I]
+    lib.yy_grid_set_profiling.restype = I
+    lib.yy_grid_stage_ms.argtypes = [P, ctypes.POINTER(D)]
+    lib.yy_grid_stage_ms.restype = I
     lib.yy_debug_fail_alloc_after.argtypes = [I]
     lib.yy_debug_fail_alloc_after.restype = None
     _lib = lib
@@ -158,6 +164,25 @@ def yy_destroy(handle):
 
 def yy_solve_flops(handle, with_gradient):
     return load().yy_solve_flops(handle, int(bool(with_gradient)))
+
+
+def yy_last_launch_count(handle):
+    return load().yy_last_launch_count(handle)
+
+
+YY_STAGE_COUNT = 4
+STAGES = ("analysis", "scan", "synth_phi", "synth_grad")
+
+
+def yy_grid_set_profiling(handle, enable):
+    return load().yy_grid_set_profiling(handle, int(bool(enable)))
+
+
+def yy_grid_stage_ms(handle):
+    """Returns (status, dict stage -> ms of the last solve)."""
+    buf = (ctypes.c_double * YY_STAGE_COUNT)()
+    st = load().yy_grid_stage_ms(handle, buf)
+    return st, dict(zip(STAGES, list(buf)))
 
 
 def yy_debug_fail_alloc_after(n):
