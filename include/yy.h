@@ -180,6 +180,30 @@ typedef enum {
 yy_status yy_grid_set_profiling(yy_grid *g, int enable);
 yy_status yy_grid_stage_ms(yy_grid *g, double *ms);
 
+/* Radial inner / outer sums without a handle and without any allocation.
+ * (No counterpart in the paper: this is a deployment variant of the scan.)
+ * For callers that cannot allocate device memory when they need the sums:
+ * code running while a CUDA graph is captured, applications whose device
+ * memory is owned by their own pool, loops that must not enter the driver's
+ * allocator.  It computes the same coefficients as the solve's scan stage.
+ *   r_edges  device, n_r + 1 radii obeying yy_grid_create's rules (not
+ *            checked here; values that break them give undefined results)
+ *   moments  device, [2 n_r][n_lm] normalised moments, Yin rows first, in the
+ *            layout of YY_TABLE_MOMENTS
+ *   coeff    device out, [3][2 n_r][2 n_lm]: the Phi, g_r and angular-gradient
+ *            coefficients; block 0 has the layout of YY_TABLE_COEFF
+ *   n_r >= 1, 0 <= l_max <= 80, G finite; all pointers 16-byte aligned.
+ * Scratch: a static device array of 2^21 float64 (16 MiB) that every GPU
+ * loading the library keeps until exit; 2 n_r (l_max+1)^2 must not exceed
+ * 2^21, otherwise YY_ERR_INVALID_ARG and nothing is launched.  Nothing in the
+ * scratch needs clearing (each value is written before it is read), but all
+ * calls share it: calls whose kernels overlap on the GPU (other streams,
+ * other threads) race and give wrong results.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  Asynchronous on cuda_stream. */
+yy_status yy_radial_scan_static(const double *r_edges, int n_r, int l_max, double G,
+                                const double *moments, double *coeff, void *cuda_stream);
+
 /* Number of CUDA kernels the last yy_potential call launched (-1 for NULL). */
 int yy_last_launch_count(const yy_grid *g);
 

@@ -79,6 +79,8 @@ def load():
     lib.yy_status_string.restype = ctypes.c_char_p
     lib.yy_solve_flops.argtypes = [P, I]
     lib.yy_solve_flops.restype = D
+    lib.yy_radial_scan_static.argtypes = [P, I, I, D, P, P, P]
+    lib.yy_radial_scan_static.restype = I
     lib.yy_last_launch_count.argtypes = [P]
     lib.yy_last_launch_count.restype = I
     lib.yy_grid_set_profiling.argtypes = [P, I]
@@ -164,6 +166,12 @@ def yy_destroy(handle):
 
 def yy_solve_flops(handle, with_gradient):
     return load().yy_solve_flops(handle, int(bool(with_gradient)))
+
+
+def yy_radial_scan_static(r_edges, n_r, l_max, G, moments, coeff, stream=None):
+    """Allocation-free radial scan (device pointers / tensors)."""
+    return load().yy_radial_scan_static(_ptr(r_edges), int(n_r), int(l_max), float(G), _ptr(moments),
+                                        _ptr(coeff), _stream(stream))
 
 
 def yy_last_launch_count(handle):
