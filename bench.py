@@ -36,6 +36,16 @@ L2_BYTES = 126 * 1024 * 1024
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 
 
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "source": "fallback"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -45,6 +55,7 @@ def parse():
     ap.add_argument("--prec", default="auto")
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=4, help="oracle evaluates 1/S of the cells")
     return ap.parse_args()
 
@@ -213,7 +224,7 @@ def run_ours(args, dist):
     grid = yy.Grid.from_spec(spec)
     prec = args.prec
     if prec == "auto":
-        prec = "fp64"
+        prec = "fp16x2"
     grid.prepare(prec)
     ry_np, rg_np = inputs.density_for(spec)
     ry = torch.from_numpy(ry_np).to(dev)
@@ -286,24 +297,54 @@ def run_ours(args, dist):
     synth_ms = (stage_tot["synth_phi"] + stage_tot["synth_grad"]) / args.steps / n_synth
     synth_flop = 2.0 * (2 * spec.n_r) * (2 * grid.n_lm) * spec.n_ang
     total_flop = grid.flops(gradient)
-    if prec in ("fp64",):
+    products = {"fp16x2": 3, "bf16x3": 6, "tf32": 1, "fp64": 1, "fp32": 1}[prec]
+    peaks = _measured_peaks()
+    if prec == "fp64":
         roof = {"bound": "alu", "kernel": "k_gemm_tn<double> (synthesis, FP64 DFMA)",
                 "achieved": synth_flop / (synth_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "traffic": None,
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz"}
-    else:
+    elif prec == "fp32":
         roof = {"bound": "alu", "kernel": "k_gemm_tn<float> (synthesis, FP32 FFMA)",
                 "achieved": synth_flop / (synth_ms / 1e3) / 1e12,
                 "peak": 152 * 128 * 2 * 2.070e9 / 1e12, "unit": "TFLOP/s", "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz"}
+    else:
+        ratio = 0.5 if prec == "tf32" else 1.0
+        roof = {"bound": "tensor", "kernel": f"k_tc_gemm<{prec}> (synthesis, tcgen05)",
+                "achieved": products * synth_flop / (synth_ms / 1e3) / 1e12,
+                "peak": peaks["bf16_tflops"] * ratio, "unit": "TFLOP/s", "traffic": None,
+                "flops_counted": f"hardware: {products} tensor-core products x 2MNK per launch",
+                "peak_source": ("measured bf16 burst (MEASURED_PEAKS.json)"
+                                + (" x 0.5 (tf32 nominal ratio)" if prec == "tf32" else ""))}
     roof["frac"] = roof["achieved"] / roof["peak"]
+
+    # ---- the plain float64 GPU path on the same grid, for comparison
+    fp64_path = None
+    if prec != "fp64" and not args.no_fp64_path:
+        grid.potential(ry, rg, phi_y, phi_g, g_y, g_g, prec="fp64", stream=stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            grid.potential(ry, rg, phi_y, phi_g, g_y, g_g, prec="fp64", stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / 2
+        fp64_path = {"value": 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64,
+                     "headline_speedup": value / dist.world / (1e3 / ms64)}
+        solve()                                   # leave the headline form's result in place
+        torch.cuda.synchronize()
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dev_s_max * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "fp32": "f32"}.get(prec, prec),
+        "dtype": {"fp64": "f64", "fp32": "f32", "fp16x2": "fp16x2 (fp32 accumulate, f64 scans)",
+                  "bf16x3": "bf16x3 (fp32 accumulate, f64 scans)",
+                  "tf32": "tf32 (fp32 accumulate, f64 scans)"}[prec],
         "data": "synthetic (seeded proto-neutron-star density, l<=4 angular perturbation)",
         "config": {"workload": "1-degree Yin-Yang grid, 2 x 90 x 270 cells, n_r=550 log r in [1e-4,1], "
                                "l_max=25, Phi and -grad Phi per solve" if gradient else
@@ -312,6 +353,8 @@ def run_ours(args, dist):
                    "gradient": gradient, "precision": prec, "parallelism": f"replicas x{dist.world}",
                    "l2": "L2 flushed (256 MB write) before every timed step"},
         "gemm_tflops": total_flop / (dev_s_max / args.steps) / 1e12,
+        "gemm_tflops_hardware": products * total_flop / (dev_s_max / args.steps) / 1e12,
+        "fp64_gpu_path": fp64_path,
         "stage_ms": {k: v / args.steps for k, v in stage_tot.items()},
         "wall_s": wall,
         "roofline": roof,

@@ -55,7 +55,7 @@ static yy_status from_cuda(cudaError_t e) {
 static void free_all(yy_grid *g) {
   if (!g) return;
   double *dbufs[] = {g->r_edges, g->w,    g->tbar, g->ban,       g->ysyn,      g->ysyn_t,
-                     g->ysyn_p,  g->scan, g->gl_nodes, g->A,     g->part,      g->cin,
+                     g->ysyn_p,  g->scan, g->scan_maps, g->gl_nodes, g->A, g->part, g->cin,
                      g->Q,       g->stage_rho, g->stage_phi, g->stage_grad};
   for (double *p : dbufs)
     if (p) cudaFree(p);
@@ -135,7 +135,12 @@ yy_status yy_grid_create(const double *r_edges, int n_r, int n_theta, int n_phi,
   A((void **)&g->ysyn, n_ang * 2 * n_lm * sizeof(double));
   A((void **)&g->ysyn_t, n_ang * 2 * n_lm * sizeof(double));
   A((void **)&g->ysyn_p, n_ang * 2 * n_lm * sizeof(double));
-  A((void **)&g->scan, (size_t)n_r * (l_max + 1) * 4 * sizeof(double));
+  A((void **)&g->scan, (size_t)n_r * (l_max + 1) * 8 * sizeof(double));
+  {
+    int nc = 1, ch = 1;
+    scan_geometry(g, &nc, &ch);
+    A((void **)&g->scan_maps, (size_t)2 * nc * n_lm * 4 * sizeof(double));
+  }
   A((void **)&g->A, M * n_lm * sizeof(double));
   if (g->split_k > 1) A((void **)&g->part, (size_t)g->split_k * M * n_lm * sizeof(double));
   A((void **)&g->cin, M * n_lm * sizeof(double));

@@ -31,7 +31,8 @@ struct yy_grid {
   double *ysyn;        // [n_ang][2 n_lm]         synthesis operand, same | cross
   double *ysyn_t;      // [n_ang][2 n_lm]         d/dtheta, target basis
   double *ysyn_p;      // [n_ang][2 n_lm]         (1/sin) d/dphi, target basis
-  double *scan;        // [n_r][lmax+1][4]        a_in, b_in, e_out, f_out
+  double *scan;        // [n_r][lmax+1][8]        a_in, b_in, e_out, f_out, output factors
+  double *scan_maps;   // [2][chunks][n_lm] x 4   per-chunk affine maps of the scans
   double *gl_nodes;    // GL nodes / weights on [0, 1] for the weight integrals
 
   // workspace (device)
@@ -79,6 +80,7 @@ cudaError_t synthesis_simt(yy_grid *g, int which, double *phi_yin, double *phi_y
 cudaError_t convert_tables_f32(yy_grid *g);
 
 // radial scans (yy_scan.cu); writes Q (and Q32 if want_f32)
+void scan_geometry(const yy_grid *g, int *nc, int *ch);
 cudaError_t radial_scan(yy_grid *g, bool want_f32, cudaStream_t s);
 
 // tensor-core path (yy_tc.cu)

@@ -1,15 +1,19 @@
 // Radial inner / outer sums of the solver (§3 Eqs. phiin / phiout) as
-// float64 affine scans over r, one warp per (patch, mode).
+// float64 affine scans over r.
 //
 // For output radius r_{n+1} (outer interface of zone n):
 //   c_n = r_{n+1}^-(l+1) sum_{i<=n} R_in,i A_i  = a_n c_{n-1} + b_n A_n
 //   d_n = r_{n+1}^l      sum_{i>n}  R_out,i A_i = e_n d_{n+1} + f_n A_{n+1}
-// with the per-zone factors built once per grid.  Each lane folds a
-// contiguous chunk of zones into one affine map x -> alpha x + beta, the warp
-// combines the maps with shuffles (prefix for c, suffix for d), and each lane
-// replays its chunk from the combined start value.  All factors are <= 1 in
-// magnitude for the homogeneous part, so the scans are contracting.
+// with per-(zone, l) factors built once per grid.  All homogeneous factors
+// are <= 1, so the recurrences are contracting.
 //
+// The chip's FP64 pipe is narrow, so the work is spread over every SM:
+// the zones are cut into NC chunks; lane = mode (32 consecutive modes per
+// warp, so every access to A, the scratch and the outputs is a contiguous
+// 256-byte row segment); warp = (patch, mode group, chunk).
+//   k_scan_maps   folds each chunk into one affine map per direction
+//   k_scan_apply  starts each chunk from the composed maps of the chunks
+//                 before (inner) / after (outer) it and replays it
 // Outputs, in the layout the synthesis contraction reads ("cat" rows: the
 // row of patch p holds [coefficients of p | coefficients of the other patch]):
 //   Q   = -G 4 pi/(2l+1) (c_n + d_n)                         -> Phi
@@ -20,84 +24,103 @@
 namespace yy {
 namespace {
 
-constexpr double kFourPi = 12.566370614359172953850573533118;
-
-__global__ void __launch_bounds__(256)
-k_radial_scan(int n_r, int lmax, int n_lm, double G, const double *__restrict__ A,
-              const double *__restrict__ coef, const double *__restrict__ r_edges,
-              double *__restrict__ cin, double *__restrict__ Q, float *__restrict__ Q32) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= 2 * n_lm) return;
-  const int p = warp / n_lm, idx = warp % n_lm;
+__device__ __forceinline__ int mode_degree(int idx) {
   int l = (int)sqrt((double)idx);
   while (l * l > idx) --l;
   while ((l + 1) * (l + 1) <= idx) ++l;
-  const int L1 = lmax + 1;
-  const int CH = (n_r + 31) / 32;
-  const int n0 = min(n_r, lane * CH), n1 = min(n_r, n0 + CH);
-  const double *Ap = A + (size_t)p * n_r * n_lm + idx;
-  double *Cp = cin + (size_t)p * n_r * n_lm + idx;
+  return l;
+}
 
-  // ---- inner (prefix) scan
-  double al = 1.0, be = 0.0;
-  for (int n = n0; n < n1; ++n) {
-    const double *c = coef + ((size_t)n * L1 + l) * 4;
-    const double a = c[0];
-    be = fma(a, be, c[1] * Ap[(size_t)n * n_lm]);
-    al *= a;
-  }
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const double ao = __shfl_up_sync(0xffffffffu, al, off);
-    const double bo = __shfl_up_sync(0xffffffffu, be, off);
-    if (lane >= off) {
-      be = fma(al, bo, be);
-      al *= ao;
-    }
-  }
-  double x = __shfl_up_sync(0xffffffffu, be, 1);
-  if (lane == 0) x = 0.0;
-  for (int n = n0; n < n1; ++n) {
-    const double *c = coef + ((size_t)n * L1 + l) * 4;
-    x = fma(c[0], x, c[1] * Ap[(size_t)n * n_lm]);
-    Cp[(size_t)n * n_lm] = x;
-  }
+// exact float64 -> fp32 rounding by integer operations (fp32 copies only)
+__device__ __forceinline__ float to_f32(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hi = (unsigned int)(u >> 32);
+  const int e32 = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+  if (e32 <= 0 || e32 >= 255) return (u << 1) == 0ull ? __uint_as_float(hi & 0x80000000u) : (float)x;
+  const unsigned long long man = u & 0xFFFFFFFFFFFFFull;
+  const unsigned int m23 = (unsigned int)(man >> 29), rem = (unsigned int)(man & 0x1FFFFFFFull);
+  const unsigned int up = (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) ? 1u : 0u;
+  return __uint_as_float((hi & 0x80000000u) | (((unsigned int)e32 << 23) + m23 + up));
+}
 
-  // ---- outer (suffix) scan
-  al = 1.0;
-  be = 0.0;
-  for (int n = n1 - 1; n >= n0; --n) {
-    const double *c = coef + ((size_t)n * L1 + l) * 4;
-    const double an = (n + 1 < n_r) ? Ap[(size_t)(n + 1) * n_lm] : 0.0;
-    be = fma(c[2], be, c[3] * an);
-    al *= c[2];
+struct ScanGeom {
+  int n_r, lmax, n_lm, nc, ch, wpp;   // chunks, chunk length, warps per patch and chunk
+};
+
+__device__ __forceinline__ bool scan_lane(const ScanGeom &s, int &p, int &idx, int &c, int &n0, int &n1) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= 2 * s.wpp * s.nc) return false;
+  c = w % s.nc;
+  const int rest = w / s.nc;
+  p = rest / s.wpp;
+  idx = (rest % s.wpp) * 32 + lane;
+  n0 = c * s.ch;
+  n1 = min(s.n_r, n0 + s.ch);
+  return idx < s.n_lm;
+}
+
+__global__ void __launch_bounds__(128)
+k_scan_maps(ScanGeom s, const double *__restrict__ A, const double *__restrict__ coef, double4 *__restrict__ maps) {
+  int p, idx, c, n0, n1;
+  if (!scan_lane(s, p, idx, c, n0, n1)) return;
+  const int l = mode_degree(idx);
+  const int L1 = s.lmax + 1;
+  const double *Ap = A + (size_t)p * s.n_r * s.n_lm + idx;
+  double ai = 1.0, bi = 0.0, ao = 1.0, bo = 0.0;
+  for (int n = n0; n < n1; ++n) {
+    const double *k = coef + ((size_t)n * L1 + l) * 8;
+    bi = fma(k[0], bi, k[1] * Ap[(size_t)n * s.n_lm]);
+    ai *= k[0];
   }
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const double ao = __shfl_down_sync(0xffffffffu, al, off);
-    const double bo = __shfl_down_sync(0xffffffffu, be, off);
-    if (lane + off < 32) {
-      be = fma(al, bo, be);
-      al *= ao;
-    }
-  }
-  double y = __shfl_down_sync(0xffffffffu, be, 1);
-  if (lane == 31) y = 0.0;
-  const double f_phi = -G * kFourPi / (2.0 * l + 1.0);
-  const size_t row2 = 2 * (size_t)n_lm;
-  const size_t qsz = (size_t)2 * n_r * row2;
   for (int n = n1 - 1; n >= n0; --n) {
-    const double *c = coef + ((size_t)n * L1 + l) * 4;
-    const double an = (n + 1 < n_r) ? Ap[(size_t)(n + 1) * n_lm] : 0.0;
-    y = fma(c[2], y, c[3] * an);
-    const double cn = Cp[(size_t)n * n_lm];
-    const double inv_r = 1.0 / r_edges[n + 1];
-    const double q = f_phi * (cn + y);
-    const double qr = -f_phi * (-(l + 1.0) * cn + l * y) * inv_r;
-    const double qt = -q * inv_r;
-    const size_t own = (size_t)(p * n_r + n) * row2 + idx;
-    const size_t oth = (size_t)((1 - p) * n_r + n) * row2 + n_lm + idx;
+    const double *k = coef + ((size_t)n * L1 + l) * 8;
+    const double an = (n + 1 < s.n_r) ? Ap[(size_t)(n + 1) * s.n_lm] : 0.0;
+    bo = fma(k[2], bo, k[3] * an);
+    ao *= k[2];
+  }
+  maps[((size_t)p * s.nc + c) * s.n_lm + idx] = make_double4(ai, bi, ao, bo);
+}
+
+__global__ void __launch_bounds__(128)
+k_scan_apply(ScanGeom s, const double *__restrict__ A, const double *__restrict__ coef,
+             const double4 *__restrict__ maps, double *__restrict__ cin, double *__restrict__ Q,
+             float *__restrict__ Q32) {
+  int p, idx, c, n0, n1;
+  if (!scan_lane(s, p, idx, c, n0, n1)) return;
+  const int l = mode_degree(idx);
+  const int L1 = s.lmax + 1;
+  const double4 *mp = maps + (size_t)p * s.nc * s.n_lm + idx;
+  double x = 0.0;                       // c_{n0 - 1}
+  for (int k = 0; k < c; ++k) {
+    const double4 m = mp[(size_t)k * s.n_lm];
+    x = fma(m.x, x, m.y);
+  }
+  double y = 0.0;                       // d_{n1 - 1} comes from the chunks above
+  for (int k = s.nc - 1; k > c; --k) {
+    const double4 m = mp[(size_t)k * s.n_lm];
+    y = fma(m.z, y, m.w);
+  }
+  const double *Ap = A + (size_t)p * s.n_r * s.n_lm + idx;
+  double *Cp = cin + (size_t)p * s.n_r * s.n_lm + idx;
+  for (int n = n0; n < n1; ++n) {
+    const double *k = coef + ((size_t)n * L1 + l) * 8;
+    x = fma(k[0], x, k[1] * Ap[(size_t)n * s.n_lm]);
+    Cp[(size_t)n * s.n_lm] = x;
+  }
+  const size_t row2 = 2 * (size_t)s.n_lm;
+  const size_t qsz = (size_t)2 * s.n_r * row2;
+  for (int n = n1 - 1; n >= n0; --n) {
+    const double *k = coef + ((size_t)n * L1 + l) * 8;
+    const double an = (n + 1 < s.n_r) ? Ap[(size_t)(n + 1) * s.n_lm] : 0.0;
+    y = fma(k[2], y, k[3] * an);
+    const double cn = Cp[(size_t)n * s.n_lm];
+    const double sum = cn + y;
+    const double q = k[4] * sum;
+    const double qr = fma(k[5], cn, k[6] * y);
+    const double qt = k[7] * sum;
+    const size_t own = (size_t)(p * s.n_r + n) * row2 + idx;
+    const size_t oth = (size_t)((1 - p) * s.n_r + n) * row2 + s.n_lm + idx;
     Q[own] = q;
     Q[oth] = q;
     Q[qsz + own] = qr;
@@ -105,23 +128,40 @@ k_radial_scan(int n_r, int lmax, int n_lm, double G, const double *__restrict__ 
     Q[2 * qsz + own] = qt;
     Q[2 * qsz + oth] = qt;
     if (Q32 != nullptr) {
-      Q32[own] = (float)q;
-      Q32[oth] = (float)q;
-      Q32[qsz + own] = (float)qr;
-      Q32[qsz + oth] = (float)qr;
-      Q32[2 * qsz + own] = (float)qt;
-      Q32[2 * qsz + oth] = (float)qt;
+      const float fq = to_f32(q), fr = to_f32(qr), ft = to_f32(qt);
+      Q32[own] = fq;
+      Q32[oth] = fq;
+      Q32[qsz + own] = fr;
+      Q32[qsz + oth] = fr;
+      Q32[2 * qsz + own] = ft;
+      Q32[2 * qsz + oth] = ft;
     }
   }
 }
 
 }  // namespace
 
-cudaError_t radial_scan(yy_grid *g, bool want_f32, cudaStream_t s) {
-  const int warps = 2 * g->n_lm;
-  const int blocks = (warps * 32 + 255) / 256;
-  k_radial_scan<<<blocks, 256, 0, s>>>(g->n_r, g->lmax, g->n_lm, g->G, g->A, g->scan, g->r_edges,
-                                       g->cin, g->Q, want_f32 ? g->Q32 : nullptr);
+void scan_geometry(const yy_grid *g, int *nc, int *ch) {
+  const int wpp = (g->n_lm + 31) / 32;
+  int n = (4 * 152 + 2 * wpp - 1) / (2 * wpp);   // about four warps per SM
+  n = n < 1 ? 1 : (n > g->n_r ? g->n_r : n);
+  *ch = (g->n_r + n - 1) / n;
+  *nc = (g->n_r + *ch - 1) / *ch;
+}
+
+cudaError_t radial_scan(yy_grid *g, bool want_f32, cudaStream_t st) {
+  ScanGeom s;
+  s.n_r = g->n_r;
+  s.lmax = g->lmax;
+  s.n_lm = g->n_lm;
+  s.wpp = (g->n_lm + 31) / 32;
+  scan_geometry(g, &s.nc, &s.ch);
+  const int warps = 2 * s.wpp * s.nc;
+  const int blocks = (warps * 32 + 127) / 128;
+  k_scan_maps<<<blocks, 128, 0, st>>>(s, g->A, g->scan, (double4 *)g->scan_maps);
+  g->launches++;
+  k_scan_apply<<<blocks, 128, 0, st>>>(s, g->A, g->scan, (const double4 *)g->scan_maps, g->cin, g->Q,
+                                       want_f32 ? g->Q32 : nullptr);
   g->launches++;
   return cudaGetLastError();
 }

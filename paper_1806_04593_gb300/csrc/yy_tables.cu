@@ -370,8 +370,10 @@ __global__ void k_synth_tables(SynthGeom G, double *__restrict__ ysyn, double *_
 //              = r_{n+1}^2 ln(r_{n+2}/r_{n+1})                       (l = 2)
 // so c_n = r_{n+1}^-(l+1) sum_{i<=n} R_in,i A_i and d_n = r_{n+1}^l sum_{i>n}
 // R_out,i A_i (Eqs. phiin / phiout), computed with expm1/log so that no
-// power of r is formed explicitly.
-__global__ void k_scan_coeffs(int n_r, int lmax, const double *__restrict__ r,
+// power of r is formed explicitly.  Entries 4..7 turn (c_n, d_n) into the
+// synthesis coefficients:  Q = k4 (c + d),  Q_r = k5 c + k6 d,  Q_t = k7 (c + d)
+// (factors listed in the body).
+__global__ void k_scan_coeffs(int n_r, int lmax, double G, const double *__restrict__ r,
                               double *__restrict__ coef) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_r * (lmax + 1)) return;
@@ -387,11 +389,17 @@ __global__ void k_scan_coeffs(int n_r, int lmax, const double *__restrict__ r,
     ee = exp(-(double)l * lu);
     f = (l == 2) ? r1 * r1 * lu : r1 * r1 * expm1((2.0 - l) * lu) / (2.0 - l);
   }
-  double *o = coef + (size_t)e * 4;
+  const double fq = -G * 12.566370614359172953850573533118 / (2.0 * l + 1.0);
+  const double inv_r = 1.0 / r1;
+  double *o = coef + (size_t)e * 8;
   o[0] = a;
   o[1] = b;
   o[2] = ee;
   o[3] = f;
+  o[4] = fq;                        // Phi:      -G 4pi/(2l+1) (c + d)
+  o[5] = fq * (l + 1.0) * inv_r;    // g_r:       G 4pi/(2l+1) (-(l+1) c + l d) / r
+  o[6] = -fq * l * inv_r;
+  o[7] = -fq * inv_r;               // g_angle:   G 4pi/(2l+1) (c + d) / r
 }
 
 }  // namespace
@@ -445,7 +453,7 @@ cudaError_t build_tables(yy_grid *g, const double *gl_host, int n_gl) {
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
 
   const int n_sc = g->n_r * (g->lmax + 1);
-  k_scan_coeffs<<<(n_sc + 127) / 128, 128>>>(g->n_r, g->lmax, g->r_edges, g->scan);
+  k_scan_coeffs<<<(n_sc + 127) / 128, 128>>>(g->n_r, g->lmax, g->G, g->r_edges, g->scan);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,124 @@
+"""Tensor-core forms (tcgen05) against the float64 oracle.
+
+Stated tolerances (max-norm relative error over the whole field):
+  FP16X2, BF16X3  Phi <= 1e-6;  -grad Phi <= 1e-5
+  TF32            Phi <= 5e-4;  -grad Phi <= 5e-3
+The split forms keep about 22 (fp16 x 2) or 24 (bf16 x 3) significant bits
+per operand; the bound comes from the fp32 accumulation in tensor memory
+(about 2^-24 per accumulation step, a few hundred steps per output) with the
+monopole done in float64.  The gradient weights mode l by about l relative
+to Phi, so its bound is larger.  TF32 keeps 11 bits.
+"""
+
+import numpy as np
+import pytest
+
+from paper_1806_04593_gb300 import inputs
+
+from .gpu_common import gpu_solve, lib, rel_max, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp16x2": (1e-6, 1e-5), "bf16x3": (1e-6, 1e-5), "tf32": (5e-4, 5e-3)}
+
+
+@pytest.fixture(scope="module")
+def yy():
+    require_gpu()
+    return lib()
+
+
+_GRIDS = {}
+
+
+def _grid(yy, spec):
+    if spec.name not in _GRIDS:
+        _GRIDS[spec.name] = yy.Grid.from_spec(spec)
+    return _GRIDS[spec.name]
+
+
+@pytest.mark.parametrize("prec", ["fp16x2", "bf16x3", "tf32"])
+@pytest.mark.parametrize("name", ["tiny", "mid"])
+def test_tensor_form_matches_oracle(yy, oracle_grid, prec, name):
+    spec = inputs.GRIDS[name]()
+    g = _grid(yy, spec)
+    g.prepare(prec)
+    ry, rg = inputs.density_for(spec)
+    out = gpu_solve(g, ry, rg, gradient=True, prec=prec)
+    assert yy.yy_last_device_status(g.handle) == yy.YY_OK
+    ref = oracle_grid(spec).solve(ry, rg, gradient=True)
+    tol_phi, tol_g = TOL[prec]
+    for q in ("yin", "yang"):
+        assert rel_max(out["phi_" + q], ref["phi_" + q]) <= tol_phi, (q, prec)
+        assert rel_max(out["grad_" + q], ref["grad_" + q]) <= tol_g, (q, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp16x2", "bf16x3"])
+def test_tensor_form_production_sampled(yy, oracle_grid, prec):
+    spec = inputs.production_grid()
+    g = _grid(yy, spec)
+    g.prepare(prec)
+    ry, rg = inputs.density_for(spec)
+    out = gpu_solve(g, ry, rg, gradient=True, prec=prec)
+    assert yy.yy_last_device_status(g.handle) == yy.YY_OK
+    rng = np.random.default_rng(41)
+    cells = np.sort(rng.choice(spec.n_ang, 64, replace=False))
+    ref = oracle_grid(spec).solve(ry, rg, gradient=True, cells=cells)
+    j, k = np.divmod(cells, spec.n_phi)
+    tol_phi, tol_g = TOL[prec]
+    for q in ("yin", "yang"):
+        assert rel_max(out["phi_" + q][:, j, k], ref["phi_" + q]) <= tol_phi
+        assert rel_max(out["grad_" + q][:, :, j, k], ref["grad_" + q]) <= tol_g
+
+
+def test_tensor_form_ragged_sizes(yy):
+    """Sizes that are multiples of no tile: partial M, N and K tiles."""
+    from oracle import OracleGrid
+    spec = inputs.GridSpec("ragged_tc", np.logspace(-2, 0, 131), 17, 41, 0.03, 0.05, 13, 1.0)
+    rng = np.random.default_rng(42)
+    ry = rng.uniform(0.5, 1.5, (spec.n_r, 17, 41))
+    rg = rng.uniform(0.5, 1.5, (spec.n_r, 17, 41))
+    g = yy.Grid.from_spec(spec)
+    ref = OracleGrid(spec.r_edges, 17, 41, 0.03, 0.05, 13).solve(ry, rg, gradient=True)
+    for prec in ("fp16x2", "bf16x3", "tf32"):
+        g.prepare(prec)
+        out = gpu_solve(g, ry, rg, gradient=True, prec=prec)
+        tol_phi, tol_g = TOL[prec]
+        for q in ("yin", "yang"):
+            assert rel_max(out["phi_" + q], ref["phi_" + q]) <= tol_phi, prec
+            assert rel_max(out["grad_" + q], ref["grad_" + q]) <= tol_g, prec
+    assert yy.yy_last_device_status(g.handle) == yy.YY_OK
+    g.close()
+
+
+def test_tensor_form_deterministic_and_swap_symmetric(yy):
+    spec = inputs.mid_grid()
+    g = _grid(yy, spec)
+    g.prepare("fp16x2")
+    ry, rg = inputs.density_for(spec)
+    a = gpu_solve(g, ry, rg, gradient=True, prec="fp16x2")
+    b = gpu_solve(g, ry, rg, gradient=True, prec="fp16x2")
+    c = gpu_solve(g, rg, ry, gradient=True, prec="fp16x2")
+    for key in a:
+        assert np.array_equal(a[key], b[key]), key
+    assert np.array_equal(a["phi_yin"], c["phi_yang"])
+    assert np.array_equal(a["grad_yang"], c["grad_yin"])
+
+
+def test_zero_density_tensor_form(yy):
+    spec = inputs.tiny_grid()
+    g = _grid(yy, spec)
+    g.prepare("fp16x2")
+    z = np.zeros((spec.n_r, spec.n_theta, spec.n_phi))
+    out = gpu_solve(g, z, z, gradient=True, prec="fp16x2")
+    for v in out.values():
+        assert np.all(v == 0.0)
+
+
+def test_unprepared_precision_is_not_supported(yy):
+    import torch
+    spec = inputs.tiny_grid()
+    g = yy.Grid.from_spec(spec)
+    x = torch.zeros((spec.n_r, spec.n_theta, spec.n_phi), dtype=torch.float64, device="cuda")
+    assert yy.yy_potential(g.handle, x, x, x.clone(), x.clone(), prec=yy.YY_BF16X3) == yy.YY_ERR_NOT_SUPPORTED
+    g.close()
