@@ -1,16 +1,1129 @@
-// Tensor-core (tcgen05) forms of the two contractions.
+// Tensor-core (tcgen05) forms of the two contractions of the solver:
+//   analysis   A[2 n_r][n_lm]    = rho . B_an^T   (§3 Eqs. ac/as with the §4 weights)
+//   synthesis  Phi[2 n_r][n_ang] = Q . Y^T        (§4 sum of the four potentials)
+//
+// Operands are float64 on entry.  Each is split into pieces of a narrower
+// type with a power-of-two scale per row (A) or per column (B):
+//   FP16X2  x = s (h + l), h, l fp16;        products h.h + h.l + l.h
+//   BF16X3  x = s (h + m + l), bf16;         products hh hm mh hl lh mm
+//   TF32    x = s t, t tf32 (round to nearest);  one product
+// The products run on tcgen05.mma (kind::f16 / kind::tf32) from shared memory
+// tiles loaded by TMA (64-byte swizzle, K-major), accumulating in fp32 in
+// tensor memory; the epilogue warps read TMEM and apply the scales.  The
+// analysis is split over K and its fp32 partial sums are added in a fixed
+// order.  The monopole (l = 0) column of each contraction is taken out of
+// the tensor-core product and done in float64 (it dominates Phi and A;
+// keeping it exact keeps the error of the narrow products relative to the
+// small l >= 1 part), and the analysis runs on rho minus its row mean, the
+// mean's contribution being added back in float64.
+//
+// The FP64 pipe of this chip retires about two operations per clock per SM,
+// so the packing, reduction and epilogue code uses fp32 arithmetic and
+// exact integer conversions between fp32 and float64.
+//
+// Kernel layout (persistent, 6 warps per CTA, one CTA per SM):
+//   warp 0  lane 0: TMA producer over a ring of STAGES shared-memory stages
+//   warp 1  allocates TMEM; lane 0 issues the MMAs and the commits
+//   warps 2-5: epilogue, TMEM lanes 32 (w % 4) .. + 31
+// Every mbarrier wait gives up after ~2 s, sets the device error word and
+// lets the CTA finish (TMEM is always released).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
 #include "yy_internal.h"
 
 namespace yy {
 
-yy_status tc_prepare(yy_grid *, yy_precision) { return YY_ERR_NOT_SUPPORTED; }
-void tc_free(yy_grid *) {}
-cudaError_t tc_analysis(yy_grid *, yy_precision, const double *, const double *, cudaStream_t) {
-  return cudaErrorNotSupported;
+// ---------------------------------------------------------------------------
+// precision forms
+// ---------------------------------------------------------------------------
+
+enum { KIND_F16 = 0, KIND_BF16 = 1, KIND_TF32 = 2 };
+
+struct FormFP16x2 {
+  typedef __half elem;
+  static constexpr int kKind = KIND_F16, kElem = 2, kPA = 2, kPB = 2, kPairs = 3, kBN = 256, kStages = 4;
+  __host__ __device__ static constexpr int pa(int i) { return i == 2 ? 1 : 0; }
+  __host__ __device__ static constexpr int pb(int i) { return i == 1 ? 1 : 0; }
+};
+
+struct FormBF16x3 {
+  typedef __nv_bfloat16 elem;
+  static constexpr int kKind = KIND_BF16, kElem = 2, kPA = 3, kPB = 3, kPairs = 6, kBN = 128, kStages = 4;
+  // (0,0) (0,1) (1,0) (0,2) (2,0) (1,1)
+  __host__ __device__ static constexpr int pa(int i) { return i == 2 ? 1 : (i == 4 ? 2 : (i == 5 ? 1 : 0)); }
+  __host__ __device__ static constexpr int pb(int i) { return i == 1 ? 1 : (i == 3 ? 2 : (i == 5 ? 1 : 0)); }
+};
+
+struct FormTF32 {
+  typedef float elem;
+  static constexpr int kKind = KIND_TF32, kElem = 4, kPA = 1, kPB = 1, kPairs = 1, kBN = 256, kStages = 8;
+  __host__ __device__ static constexpr int pa(int) { return 0; }
+  __host__ __device__ static constexpr int pb(int) { return 0; }
+};
+
+constexpr int kBM = 128;
+constexpr int kRowBytes = 64;        // K bytes per tile row and stage: one 64-byte swizzle atom
+constexpr int kPadK = 64;            // K padding (elements) of every packed operand
+constexpr int kBChunk = 32;          // rows of one B box; B tiles are loaded in 32-row chunks
+constexpr double kY00 = 0.28209479177387814347403972578039;   // K_00 P_0^0 = 1/sqrt(4 pi)
+
+template <class F>
+constexpr int stage_bytes() {
+  return F::kPA * kBM * kRowBytes + F::kPB * F::kBN * kRowBytes;
 }
-cudaError_t tc_pack_coefficients(yy_grid *, yy_precision, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t tc_synthesis(yy_grid *, yy_precision, int, double *, double *, double *, double *, cudaStream_t) {
-  return cudaErrorNotSupported;
+template <class F>
+constexpr int smem_bytes() {
+  return F::kStages * stage_bytes<F>() + 1024 /*align*/ + 512 /*barriers*/;
+}
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait: ~2 s of wall time, then the error word gets YY_DEVERR_TIMEOUT.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
+  const uint32_t addr = smem_u32(bar);
+  for (int i = 0; i < 256; ++i)
+    if (mbar_try_wait(addr, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (true) {
+    if (mbar_try_wait(addr, parity)) return true;
+    if (globaltimer() - t0 > 2000000000ull) {
+      atomicOr(err, YY_DEVERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap *map, uint32_t dst, uint64_t *bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Multicast variant: the same shared-memory offset and barrier in every CTA
+// of the cluster named by the mask receive the box.
+__device__ __forceinline__ void tma_load_2d_mc(const CUtensorMap *map, uint32_t dst, uint64_t *bar, int x, int y,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%4, %5}], [%2], %3;" ::"r"(dst),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "h"(mask), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t base, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols) : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle (layout type 4),
+// 8-row groups 512 bytes apart (stride byte offset), descriptor version 1.
+// The tile base must be 512-byte aligned; advancing K by 32 bytes inside the
+// swizzle atom advances the start address.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
+// Instruction descriptor: fp32 accumulator, A/B format, both K-major, N, M = 128.
+template <class F>
+__host__ __device__ constexpr uint32_t instr_desc() {
+  return (1u << 4) | ((uint32_t)F::kKind << 7) | ((uint32_t)F::kKind << 10) | ((uint32_t)(F::kBN >> 3) << 17) |
+         ((uint32_t)(kBM >> 4) << 24);
+}
+
+template <class F>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (F::kKind == KIND_TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// fp32 <-> float64 with integer operations only: exact widening, and
+// round-to-nearest-even narrowing (the same result as the conversion
+// instruction); zero / subnormal / overflow / NaN take the instruction.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t ex = (u >> 23) & 0xFFu;
+  if (ex == 0u || ex == 255u) {
+    if ((u << 1) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    return (double)f;
+  }
+  const uint32_t hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const uint32_t hi = (uint32_t)(u >> 32);
+  const int ex = (int)((hi >> 20) & 0x7FFu);
+  const int e32 = ex - 1023 + 127;
+  if (e32 <= 0 || e32 >= 255) {
+    if ((u << 1) == 0ull) return __uint_as_float(hi & 0x80000000u);
+    return (float)x;
+  }
+  const unsigned long long man = u & 0xFFFFFFFFFFFFFull;
+  const uint32_t m23 = (uint32_t)(man >> 29);
+  const uint32_t rem = (uint32_t)(man & 0x1FFFFFFFull);
+  const uint32_t up = (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) ? 1u : 0u;
+  return __uint_as_float((hi & 0x80000000u) | (((uint32_t)e32 << 23) + m23 + up));
+}
+
+// ---------------------------------------------------------------------------
+// the contraction kernel
+// ---------------------------------------------------------------------------
+
+struct TcArgs {
+  int M, N;              // valid output rows / columns
+  int kb_total;          // K blocks (kRowBytes per row) in the packed operands
+  int kb_per_tile;       // K blocks per tile (the K split)
+  int m_tiles, n_tiles, k_splits;   // tile space, M fastest, then N, then K split
+  int a_rows, b_rows;    // rows of one piece in the stacked A / B operands
+  int mode;              // 0: fp32 partials [z][M][N]; 1: float64 output
+  float *part;
+  double *out0, *out1;   // rows < out_split -> out0, others -> out1
+  int out_split;
+  long long ldo;
+  const float *row_scale, *col_scale, *row_add;   // powers of two / fp32 monopole term
+  int *err;
+};
+
+// Persistent.  CTAs form clusters of C (C = 1 or 3) along M: the C CTAs of a
+// cluster compute C vertically adjacent 128 x BN tiles that share one B tile,
+// and each loads 1/C of that B tile (32-row chunks r, r + C, ...) with TMA
+// multicast into the shared memory of all C CTAs.  A consumer frees a stage
+// in all C CTAs at once (multicast tcgen05.commit), so each CTA's "empty"
+// barrier counts C arrivals.  Cluster c handles cluster tiles c,
+// c + #clusters, ...; the producer and the MMA issuer run ahead across tiles
+// through the shared-memory ring, and the accumulator is double-buffered in
+// TMEM (2 x BN columns) so the epilogue of one tile overlaps the MMAs of the
+// next.
+template <class F, int C>
+__global__ void __launch_bounds__(192, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
+  constexpr int BN = F::kBN, S = F::kStages;
+  constexpr int A_TILE = kBM * kRowBytes, B_TILE = BN * kRowBytes;
+  constexpr int STAGE = stage_bytes<F>();
+  constexpr int KSTEP_BYTES = 32;                   // one MMA consumes 32 bytes of K per row
+  constexpr int KSTEPS = kRowBytes / KSTEP_BYTES;   // MMAs per K block and product
+  constexpr int BK = kRowBytes / F::kElem;          // elements of K per block
+  constexpr int NCHUNK = BN / kBChunk;
+  constexpr uint16_t MASK = (uint16_t)((1u << C) - 1u);
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *full = (uint64_t *)(smem + S * STAGE);
+  uint64_t *empty = full + S;
+  uint64_t *tfull = empty + S;      // [2]
+  uint64_t *tempty = tfull + 2;     // [2]
+  uint32_t *tmem_slot = (uint32_t *)(tempty + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rank = (C > 1) ? (int)cluster_rank() : 0;
+  const int cluster = (int)blockIdx.x / C, n_clusters = (int)gridDim.x / C;
+  const int m_groups = a.m_tiles / C;
+  const int total = m_groups * a.n_tiles * a.k_splits;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], C);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 2 * BN);
+    tc_fence_before();
+  }
+  __syncthreads();
+  if constexpr (C > 1) cluster_sync();   // peers' barriers exist before any multicast
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int gk = 0;
+      bool ok = true;
+      for (int t = cluster; t < total && ok; t += n_clusters) {
+        const int mt = (t % m_groups) * C + rank;
+        const int nt = (t / m_groups) % a.n_tiles, z = t / (m_groups * a.n_tiles);
+        const int kb0 = z * a.kb_per_tile;
+        const int nkb = min(a.kb_total, kb0 + a.kb_per_tile) - kb0;
+        for (int i = 0; i < nkb; ++i, ++gk) {
+          const int s = gk % S;
+          if (gk >= S && !mbar_wait(&empty[s], ((gk / S) & 1) ^ 1, a.err)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], STAGE);
+          const uint32_t base = smem_u32(smem + s * STAGE);
+          const int kx = (kb0 + i) * BK;
+#pragma unroll
+          for (int p = 0; p < F::kPA; ++p)
+            tma_load_2d(&tmA, base + p * A_TILE, &full[s], kx, p * a.a_rows + mt * kBM);
+#pragma unroll
+          for (int p = 0; p < F::kPB; ++p) {
+            const uint32_t bdst = base + F::kPA * A_TILE + p * B_TILE;
+            const int brow = p * a.b_rows + nt * BN;
+            for (int c = rank; c < NCHUNK; c += C) {
+              if constexpr (C > 1)
+                tma_load_2d_mc(&tmB, bdst + c * kBChunk * kRowBytes, &full[s], kx, brow + c * kBChunk, MASK);
+              else
+                tma_load_2d(&tmB, bdst + c * kBChunk * kRowBytes, &full[s], kx, brow + c * kBChunk);
+            }
+          }
+        }
+      }
+      // every stage's last use must be released by all C consumers before
+      // this CTA may leave (peers' commits still land on our barriers)
+      if (ok)
+        for (int i = max(0, gk - S); i < gk; ++i)
+          if (!mbar_wait(&empty[i % S], (i / S) & 1, a.err)) break;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = instr_desc<F>();
+      int gk = 0, it = 0;
+      bool ok = true;
+      for (int t = cluster; t < total && ok; t += n_clusters, ++it) {
+        const int b = it & 1;
+        if (it >= 2) {
+          if (!mbar_wait(&tempty[b], ((it >> 1) & 1) ^ 1, a.err)) break;
+          tc_fence_after();
+        }
+        const int z = t / (m_groups * a.n_tiles);
+        const int kb0 = z * a.kb_per_tile;
+        const int nkb = min(a.kb_total, kb0 + a.kb_per_tile) - kb0;
+        const uint32_t dacc = tmem_base + (uint32_t)(b * BN);
+        for (int i = 0; i < nkb; ++i, ++gk) {
+          const int s = gk % S;
+          if (!mbar_wait(&full[s], (gk / S) & 1, a.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + s * STAGE);
+          const uint32_t sb = sa + F::kPA * A_TILE;
+#pragma unroll
+          for (int q = 0; q < F::kPairs; ++q) {
+#pragma unroll
+            for (int kk = 0; kk < KSTEPS; ++kk) {
+              const uint64_t da = smem_desc(sa + F::pa(q) * A_TILE + kk * KSTEP_BYTES);
+              const uint64_t db = smem_desc(sb + F::pb(q) * B_TILE + kk * KSTEP_BYTES);
+              mma<F>(dacc, da, db, idesc, (i | q | kk) != 0 ? 1u : 0u);
+            }
+          }
+          if constexpr (C > 1)
+            mma_commit_mc(&empty[s], MASK);
+          else
+            mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(&tfull[b]);
+      }
+    }
+  } else {
+    // epilogue: TMEM lane quarter of this warp
+    const int quarter = warp & 3;
+    int it = 0;
+    for (int t = cluster; t < total; t += n_clusters, ++it) {
+      const int b = it & 1;
+      if (!mbar_wait(&tfull[b], (it >> 1) & 1, a.err)) break;
+      tc_fence_after();
+      const int mt = (t % m_groups) * C + rank;
+      const int nt = (t / m_groups) % a.n_tiles, z = t / (m_groups * a.n_tiles);
+      const int row = mt * kBM + quarter * 32 + lane;
+      const bool live = row < a.M;
+      float rs = 0.0f, ra = 0.0f;
+      double *orow = nullptr;
+      if (a.mode == 1 && live) {
+        rs = a.row_scale[row];
+        ra = a.row_add[row];
+        orow = (row < a.out_split) ? a.out0 + (size_t)row * a.ldo : a.out1 + (size_t)(row - a.out_split) * a.ldo;
+      }
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0), v);
+        if (!live) continue;
+        const int col0 = nt * BN + c0;
+        if (a.mode == 0) {
+          float *dst = a.part + ((size_t)z * a.M + row) * a.N + col0;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (col0 + j < a.N) dst[j] = __uint_as_float(v[j]);
+        } else {
+          // result = acc * row scale * column scale (powers of two: exact) +
+          // monopole term, rounded once in fp32, widened exactly to float64
+          double *dst = orow + col0;
+          const bool vec = (col0 + 32 <= a.N) && (((uintptr_t)dst & 15u) == 0);
+          if (vec) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+              double2 o;
+              o.x = f32_to_f64(fmaf(__uint_as_float(v[j]) * rs, a.col_scale[col0 + j], ra));
+              o.y = f32_to_f64(fmaf(__uint_as_float(v[j + 1]) * rs, a.col_scale[col0 + j + 1], ra));
+              *(double2 *)(dst + j) = o;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (col0 + j < a.N) dst[j] = f32_to_f64(fmaf(__uint_as_float(v[j]) * rs, a.col_scale[col0 + j], ra));
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
+    }
+  }
+  __syncthreads();
+  if constexpr (C > 1) cluster_sync();   // no CTA leaves while peers may still reach its barriers
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, 2 * BN);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// operand packing: float64 rows -> scaled narrow pieces [P][rows_pad][k_pad]
+// ---------------------------------------------------------------------------
+//
+// One CTA per row.  Pass 1 converts the row to fp32 (cached in shared memory
+// when it is short) and gathers, with compensated fp32 sums: the row sum (for
+// the optional mean subtraction), the minimum / maximum, and an optional dot
+// product with an fp32 vector (the float64 monopole of the analysis).  Pass 2
+// scales (x - mean) by a power of two so that the row maximum lies in
+// [2^14, 2^15) and splits it into the form's pieces, 8 elements per store.
+
+struct PackArgs {
+  int rows;              // valid rows
+  int rows_pad;          // rows of one piece
+  int K, k_pad;          // valid / padded row length
+  const double *src0, *src1;
+  int split_row;         // rows < split_row from src0
+  long long ld;          // source row stride
+  int zero_k0, zero_k1;  // source columns left out (-1: none)
+  int zero_row;          // source row left out (-1: none)
+  const float *dot_vec;  // optional: dot_out[row] = sum_k x[k] dot_vec[k]
+  double *dot_out;
+  double add_factor;     // optional: row_add[row] = add_factor (x[zero_k0] + x[zero_k1])
+  float *row_add;
+  double *mean_out;      // optional: pack x - mean, store the mean used
+  double *scale_out;     // [rows_pad] power of two undoing the scaling (float64)
+  float *scale_out_f;    // the same in fp32 (optional)
+  void *out;             // pieces
+  int cache;             // 1: row cached in shared memory (K floats)
+};
+
+struct PackBatch {
+  PackArgs job[3];       // blockIdx.y selects the job
+};
+
+// compensated accumulation (Neumaier) in fp32
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+  const float t = s + x;
+  c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+  s = t;
+}
+
+template <class F>
+__device__ __forceinline__ void split8(const float (&y)[8], typename F::elem *base, size_t piece_stride) {
+  if constexpr (F::kKind == KIND_F16) {
+    __align__(16) __half h[8], l[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      h[i] = __float2half_rn(y[i]);
+      l[i] = __float2half_rn(y[i] - __half2float(h[i]));
+    }
+    *(uint4 *)base = *(const uint4 *)h;
+    *(uint4 *)(base + piece_stride) = *(const uint4 *)l;
+  } else if constexpr (F::kKind == KIND_BF16) {
+    __align__(16) __nv_bfloat16 h[8], m[8], l[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      h[i] = __float2bfloat16_rn(y[i]);
+      const float r = y[i] - __bfloat162float(h[i]);
+      m[i] = __float2bfloat16_rn(r);
+      l[i] = __float2bfloat16_rn(r - __bfloat162float(m[i]));
+    }
+    *(uint4 *)base = *(const uint4 *)h;
+    *(uint4 *)(base + piece_stride) = *(const uint4 *)m;
+    *(uint4 *)(base + 2 * piece_stride) = *(const uint4 *)l;
+  } else {
+    __align__(16) uint32_t t[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t[i]) : "f"(y[i]));
+    *(uint4 *)base = *(const uint4 *)t;
+    *(uint4 *)(base + 4) = *(const uint4 *)(t + 4);
+  }
+}
+
+template <class F>
+__global__ void __launch_bounds__(256) k_pack_rows(PackBatch batch) {
+  extern __shared__ float rowbuf[];
+  __shared__ double red[4][256];
+  const PackArgs &p = batch.job[blockIdx.y];
+  const int row = blockIdx.x;
+  if (row >= p.rows_pad) return;
+  typedef typename F::elem E;
+  const size_t piece_stride = (size_t)p.rows_pad * p.k_pad;
+  E *orow = (E *)p.out + (size_t)row * p.k_pad;
+  const bool valid = row < p.rows && row != p.zero_row;
+  const double *src = nullptr;
+  if (valid) src = (row < p.split_row) ? p.src0 + (size_t)row * p.ld : p.src1 + (size_t)(row - p.split_row) * p.ld;
+
+  float s = 0.f, sc_ = 0.f, d = 0.f, dc = 0.f, mn = INFINITY, mx = -INFINITY;
+  if (valid) {
+    // 4 consecutive values per thread and step, all loads issued before use
+#pragma unroll 2
+    for (int k0 = threadIdx.x * 4; k0 < p.K; k0 += blockDim.x * 4) {
+      double xv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xv[i] = (k0 + i < p.K) ? src[k0 + i] : 0.0;
+      float bv[4] = {0.f, 0.f, 0.f, 0.f};
+      if (p.dot_vec) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) bv[i] = (k0 + i < p.K) ? p.dot_vec[k0 + i] : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int k = k0 + i;
+        if (k >= p.K) break;
+        const bool used = (k != p.zero_k0 && k != p.zero_k1);
+        const float x = used ? f64_to_f32(xv[i]) : 0.0f;
+        if (p.cache) rowbuf[k] = x;
+        if (!used) continue;
+        kahan_add(s, sc_, x);
+        mn = fminf(mn, x);
+        mx = fmaxf(mx, x);
+        if (p.dot_vec) {
+          const float pr = x * bv[i];
+          kahan_add(d, dc, pr);
+          kahan_add(d, dc, fmaf(x, bv[i], -pr));
+        }
+      }
+    }
+  }
+  red[0][threadIdx.x] = (double)s + (double)sc_;
+  red[1][threadIdx.x] = (double)d + (double)dc;
+  red[2][threadIdx.x] = (double)mn;
+  red[3][threadIdx.x] = (double)mx;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + w];
+      red[1][threadIdx.x] += red[1][threadIdx.x + w];
+      red[2][threadIdx.x] = fmin(red[2][threadIdx.x], red[2][threadIdx.x + w]);
+      red[3][threadIdx.x] = fmax(red[3][threadIdx.x], red[3][threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  const int n_used = p.K - (p.zero_k0 >= 0 ? 1 : 0) - ((p.zero_k1 >= 0 && p.zero_k1 != p.zero_k0) ? 1 : 0);
+  float mean = 0.0f;
+  if (p.mean_out && valid && n_used > 0) mean = (float)(red[0][0] / n_used);
+  float amax = 0.0f;
+  if (valid && n_used > 0) amax = fmaxf((float)red[3][0] - mean, mean - (float)red[2][0]);
+  float scf = 1.0f;
+  if (amax > 0.0f && isfinite(amax)) scf = ldexpf(1.0f, 14 - ilogbf(amax));
+  if (threadIdx.x == 0) {
+    p.scale_out[row] = 1.0 / (double)scf;
+    if (p.scale_out_f) p.scale_out_f[row] = 1.0f / scf;
+    if (p.mean_out) p.mean_out[row] = (double)mean;
+    if (p.dot_vec && row < p.rows) p.dot_out[row] = valid ? red[1][0] : 0.0;
+    if (p.row_add && row < p.rows)
+      p.row_add[row] = (valid && p.zero_k0 >= 0) ? (float)(p.add_factor * (src[p.zero_k0] + src[p.zero_k1])) : 0.0f;
+  }
+  if (p.cache) __syncthreads();
+  for (int k0 = threadIdx.x * 8; k0 < p.k_pad; k0 += blockDim.x * 8) {
+    float xs[8];
+    if (p.cache) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) xs[i] = (valid && k0 + i < p.K) ? rowbuf[k0 + i] : 0.0f;
+    } else {
+      double xv[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) xv[i] = (valid && k0 + i < p.K) ? src[k0 + i] : 0.0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) xs[i] = f64_to_f32(xv[i]);
+    }
+    float y[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int k = k0 + i;
+      const bool used = valid && k < p.K && k != p.zero_k0 && k != p.zero_k1;
+      y[i] = used ? (xs[i] - mean) * scf : 0.0f;
+    }
+    split8<F>(y, orow + k0, piece_stride);
+  }
+}
+
+// A[row][col] = (sum_z part[z][row][col]) row_scale col_scale + mean[row] colsum[col]
+// (the tensor cores saw rho - mean); column 0 is the float64 monopole.
+__global__ void k_reduce_partials(int M, int N, int S, const float *__restrict__ part,
+                                  const double *__restrict__ rs, const double *__restrict__ cs,
+                                  const double *__restrict__ mono, const double *__restrict__ mean,
+                                  const double *__restrict__ colsum, double *__restrict__ A) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)M * N) return;
+  const int row = (int)(e / N), col = (int)(e % N);
+  if (col == 0) {
+    A[e] = mono[row];
+    return;
+  }
+  float s = 0.f, c = 0.f;
+  for (int z = 0; z < S; ++z) kahan_add(s, c, part[(size_t)z * M * N + e]);
+  const double sum = f32_to_f64(s) + f32_to_f64(c);
+  A[e] = fma(sum * rs[row], cs[col], mean[row] * colsum[col]);
+}
+
+// colsum[row] = sum_k table[row][k] (float64, fixed order); b0[k] = fp32(table[0][k])
+__global__ void __launch_bounds__(256) k_row_sums(int K, const double *__restrict__ table, double *__restrict__ out,
+                                                  float *__restrict__ b0) {
+  __shared__ double red[256];
+  const double *src = table + (size_t)blockIdx.x * K;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    s += src[k];
+    if (blockIdx.x == 0) b0[k] = (float)src[k];
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void *ptr = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+  }
+  return fn;
+}
+
+template <class F>
+static bool make_map(CUtensorMap *map, void *base, int k_pad, int rows_total, int box_rows) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  const CUtensorMapDataType dt = (F::kKind == KIND_F16)    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                 : (F::kKind == KIND_BF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const cuuint64_t dims[2] = {(cuuint64_t)k_pad, (cuuint64_t)rows_total};
+  const cuuint64_t strides[1] = {(cuuint64_t)k_pad * F::kElem};
+  const cuuint32_t box[2] = {(cuuint32_t)(kRowBytes / F::kElem), (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+}  // namespace yy
+
+struct yy_tc_tables {
+  yy_precision prec;
+  int sms;
+  int cluster;           // CTAs per cluster along M (1 or 3)
+  int max_clusters;      // co-resident clusters of the contraction kernel
+  // analysis
+  int an_rows_a, an_kpad, an_rows_b;      // M_pad, K_pad, N_pad
+  void *an_A, *an_B;
+  double *an_rs, *an_cs, *an_mono, *an_mean, *an_colsum;
+  float *an_b0;                           // fp32 copy of the monopole row of the analysis table
+  float *part;
+  int an_splits, an_kb_per;
+  CUtensorMap an_mapA, an_mapB;
+  // synthesis (3 coefficient sets, 3 tables)
+  int sy_kpad, sy_rows_b;
+  void *sy_A[3], *sy_B[3];
+  double *sy_rs[3], *sy_cs[3];
+  float *sy_rsf[3], *sy_csf[3], *sy_add[3];
+  CUtensorMap sy_mapA[3], sy_mapB[3];
+};
+
+namespace yy {
+
+// Rows up to this many values are cached in shared memory during packing.
+constexpr int kPackCacheMax = 16 * 1024 / 4;
+
+static size_t pack_smem(const PackBatch &b, int n) {
+  size_t m = 0;
+  for (int i = 0; i < n; ++i)
+    if (b.job[i].cache) m = std::max(m, (size_t)b.job[i].K * sizeof(float));
+  return m;
+}
+
+template <class F>
+static cudaError_t launch_pack(PackBatch &b, int n, cudaStream_t s) {
+  int rows = 0;
+  for (int i = 0; i < n; ++i) {
+    b.job[i].cache = b.job[i].K <= kPackCacheMax ? 1 : 0;
+    rows = std::max(rows, b.job[i].rows_pad);
+  }
+  k_pack_rows<F><<<dim3(rows, n), 256, pack_smem(b, n), s>>>(b);
+  return cudaGetLastError();
+}
+
+template <class F>
+static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
+  const int M = 2 * g->n_r;
+  cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, g->device);
+  for (int c : {1, 3}) {
+    auto kern = (c == 1) ? k_tc_gemm<F, 1> : k_tc_gemm<F, 3>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<F>()) != cudaSuccess)
+      return YY_ERR_NOT_SUPPORTED;
+  }
+  // Clusters of 3 CTAs along M share B tiles by multicast.  Measured on the
+  // 1-degree grid they cut L2 reads but not the time per tile, and fewer
+  // clusters than SMs can be resident, so single CTAs are the default;
+  // YY_TC_CLUSTER=3 selects clusters (when M needs little extra padding).
+  const char *cenv = getenv("YY_TC_CLUSTER");
+  t->cluster = (cenv && atoi(cenv) == 3 && round_up(M, 3 * kBM) * 100 <= round_up(M, kBM) * 115) ? 3 : 1;
+  t->max_clusters = t->sms;
+  if (t->cluster == 3) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 3;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(3 * 64);
+    cfg.blockDim = dim3(192);
+    cfg.dynamicSmemBytes = smem_bytes<F>();
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (void *)k_tc_gemm<F, 3>, &cfg) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      t->cluster = 1;
+    } else {
+      t->max_clusters = n;
+    }
+  }
+  t->an_rows_a = round_up(M, kBM * t->cluster);
+  t->an_kpad = round_up(g->n_ang, kPadK);
+  t->an_rows_b = round_up(g->n_lm, F::kBN);
+  t->sy_kpad = round_up(2 * g->n_lm, kPadK);
+  t->sy_rows_b = round_up(g->n_ang, F::kBN);
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void **ptr, size_t bytes) {
+    if (e == cudaSuccess) e = dmalloc(ptr, bytes);
+  };
+  A(&t->an_A, (size_t)F::kPA * t->an_rows_a * t->an_kpad * F::kElem);
+  A(&t->an_B, (size_t)F::kPB * t->an_rows_b * t->an_kpad * F::kElem);
+  A((void **)&t->an_rs, t->an_rows_a * sizeof(double));
+  A((void **)&t->an_cs, t->an_rows_b * sizeof(double));
+  A((void **)&t->an_mono, t->an_rows_a * sizeof(double));
+  A((void **)&t->an_mean, t->an_rows_a * sizeof(double));
+  A((void **)&t->an_colsum, g->n_lm * sizeof(double));
+  A((void **)&t->an_b0, g->n_ang * sizeof(float));
+  for (int c = 0; c < 3; ++c) {
+    A(&t->sy_A[c], (size_t)F::kPA * t->an_rows_a * t->sy_kpad * F::kElem);
+    A(&t->sy_B[c], (size_t)F::kPB * t->sy_rows_b * t->sy_kpad * F::kElem);
+    A((void **)&t->sy_rs[c], t->an_rows_a * sizeof(double));
+    A((void **)&t->sy_cs[c], t->sy_rows_b * sizeof(double));
+    A((void **)&t->sy_rsf[c], t->an_rows_a * sizeof(float));
+    A((void **)&t->sy_csf[c], t->sy_rows_b * sizeof(float));
+    A((void **)&t->sy_add[c], t->an_rows_a * sizeof(float));
+  }
+  // split K of the analysis: about three rounds of the persistent CTAs; the
+  // split also bounds the fp32 accumulation length of each partial sum
+  const int tiles = (t->an_rows_b / F::kBN) * (t->an_rows_a / kBM) / t->cluster;   // cluster tiles
+  const int kb_total = t->an_kpad * F::kElem / kRowBytes;
+  const int slots = t->cluster == 3 ? t->max_clusters : t->sms;
+  int splits = (3 * slots + tiles - 1) / tiles;
+  splits = splits < 1 ? 1 : (splits > kb_total ? kb_total : splits);
+  t->an_kb_per = (kb_total + splits - 1) / splits;
+  t->an_splits = (kb_total + t->an_kb_per - 1) / t->an_kb_per;
+  A((void **)&t->part, (size_t)t->an_splits * M * g->n_lm * sizeof(float));
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? YY_ERR_OOM : YY_ERR_CUDA;
+
+  if (cudaFuncSetAttribute(k_pack_rows<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kPackCacheMax * (int)sizeof(float)) != cudaSuccess)
+    return YY_ERR_NOT_SUPPORTED;
+  // static operands: the analysis table (mode 0 left out: done in float64)
+  // and the three synthesis tables, each row scaled separately
+  k_row_sums<<<g->n_lm, 256>>>(g->n_ang, g->ban, t->an_colsum, t->an_b0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return YY_ERR_CUDA;
+  PackBatch b = {};
+  PackArgs &p = b.job[0];
+  p.rows = g->n_lm;
+  p.rows_pad = t->an_rows_b;
+  p.K = g->n_ang;
+  p.k_pad = t->an_kpad;
+  p.src0 = p.src1 = g->ban;
+  p.split_row = g->n_lm;
+  p.ld = g->n_ang;
+  p.zero_k0 = p.zero_k1 = -1;
+  p.zero_row = 0;
+  p.scale_out = t->an_cs;
+  p.out = t->an_B;
+  if ((e = launch_pack<F>(b, 1, 0)) != cudaSuccess) return YY_ERR_CUDA;
+  const double *tabs[3] = {g->ysyn, g->ysyn_t, g->ysyn_p};
+  PackBatch bs = {};
+  for (int c = 0; c < 3; ++c) {
+    PackArgs &q = bs.job[c];
+    q.rows = g->n_ang;
+    q.rows_pad = t->sy_rows_b;
+    q.K = 2 * g->n_lm;
+    q.k_pad = t->sy_kpad;
+    q.src0 = q.src1 = tabs[c];
+    q.split_row = g->n_ang;
+    q.ld = 2 * g->n_lm;
+    q.zero_k0 = q.zero_k1 = -1;
+    q.zero_row = -1;
+    q.scale_out = t->sy_cs[c];
+    q.scale_out_f = t->sy_csf[c];
+    q.out = t->sy_B[c];
+  }
+  if ((e = launch_pack<F>(bs, 3, 0)) != cudaSuccess) return YY_ERR_CUDA;
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return YY_ERR_CUDA;
+
+  bool ok = make_map<F>(&t->an_mapA, t->an_A, t->an_kpad, F::kPA * t->an_rows_a, kBM) &&
+            make_map<F>(&t->an_mapB, t->an_B, t->an_kpad, F::kPB * t->an_rows_b, kBChunk);
+  for (int c = 0; c < 3 && ok; ++c)
+    ok = make_map<F>(&t->sy_mapA[c], t->sy_A[c], t->sy_kpad, F::kPA * t->an_rows_a, kBM) &&
+         make_map<F>(&t->sy_mapB[c], t->sy_B[c], t->sy_kpad, F::kPB * t->sy_rows_b, kBChunk);
+  if (!ok) return YY_ERR_NOT_SUPPORTED;
+  return YY_OK;
+}
+
+static void free_tables(yy_tc_tables *t) {
+  if (!t) return;
+  void *ptrs[] = {t->an_A, t->an_B, t->an_rs, t->an_cs, t->an_mono, t->an_mean, t->an_colsum, t->an_b0, t->part};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  for (int c = 0; c < 3; ++c) {
+    void *q[] = {t->sy_A[c], t->sy_B[c], t->sy_rs[c], t->sy_cs[c], t->sy_rsf[c], t->sy_csf[c], t->sy_add[c]};
+    for (void *p : q)
+      if (p) cudaFree(p);
+  }
+  delete t;
+}
+
+yy_status tc_prepare(yy_grid *g, yy_precision prec) {
+  if (g->tc[prec]) return YY_OK;
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, g->device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, g->device);
+  if (major != 10 || minor != 3) return YY_ERR_NOT_SUPPORTED;   // built for sm_103a only
+  yy_tc_tables *t = new (std::nothrow) yy_tc_tables();
+  if (!t) return YY_ERR_OOM;
+  memset((void *)t, 0, sizeof(*t));
+  t->prec = prec;
+  yy_status st;
+  switch (prec) {
+    case YY_FP16X2: st = prepare_form<FormFP16x2>(g, t); break;
+    case YY_BF16X3: st = prepare_form<FormBF16x3>(g, t); break;
+    case YY_TF32: st = prepare_form<FormTF32>(g, t); break;
+    default: st = YY_ERR_INVALID_ARG;
+  }
+  if (st != YY_OK) {
+    cudaGetLastError();
+    free_tables(t);
+    return st;
+  }
+  g->tc[prec] = t;
+  return YY_OK;
+}
+
+void tc_free(yy_grid *g) {
+  for (int i = 0; i < 5; ++i) {
+    free_tables(g->tc[i]);
+    g->tc[i] = nullptr;
+  }
+}
+
+template <class F>
+static cudaError_t launch_gemm(yy_grid *g, yy_tc_tables *t, const CUtensorMap &ma, const CUtensorMap &mb,
+                               const TcArgs &args, int n_tiles, int m_tiles, int splits, cudaStream_t s) {
+  TcArgs a = args;
+  a.n_tiles = n_tiles;
+  a.m_tiles = m_tiles;
+  a.k_splits = splits;
+  const int C = t->cluster;
+  const int ctiles = n_tiles * (m_tiles / C) * splits;
+  const int slots = C == 3 ? t->max_clusters : t->sms;
+  const int clusters = ctiles < slots ? ctiles : slots;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(clusters * C);
+  cfg.blockDim = dim3(192);
+  cfg.dynamicSmemBytes = smem_bytes<F>();
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = (C == 3) ? cudaLaunchKernelEx(&cfg, k_tc_gemm<F, 3>, ma, mb, a)
+                           : cudaLaunchKernelEx(&cfg, k_tc_gemm<F, 1>, ma, mb, a);
+  g->launches++;
+  return e;
+}
+
+template <class F>
+static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, const double *rg, cudaStream_t s) {
+  const int M = 2 * g->n_r;
+  PackBatch b = {};
+  PackArgs &p = b.job[0];
+  p.rows = M;
+  p.rows_pad = t->an_rows_a;
+  p.K = g->n_ang;
+  p.k_pad = t->an_kpad;
+  p.src0 = ry;
+  p.src1 = rg;
+  p.split_row = g->n_r;
+  p.ld = g->n_ang;
+  p.zero_k0 = p.zero_k1 = -1;
+  p.zero_row = -1;
+  p.dot_vec = t->an_b0;         // monopole row of the analysis table
+  p.dot_out = t->an_mono;
+  p.mean_out = t->an_mean;      // the tensor cores see rho - (row mean)
+  p.scale_out = t->an_rs;
+  p.out = t->an_A;
+  cudaError_t e = launch_pack<F>(b, 1, s);
+  g->launches++;
+  if (e != cudaSuccess) return e;
+  TcArgs a = {};
+  a.M = M;
+  a.N = g->n_lm;
+  a.kb_total = t->an_kpad * F::kElem / kRowBytes;
+  a.kb_per_tile = t->an_kb_per;
+  a.a_rows = t->an_rows_a;
+  a.b_rows = t->an_rows_b;
+  a.mode = 0;
+  a.part = t->part;
+  a.err = g->err;
+  e = launch_gemm<F>(g, t, t->an_mapA, t->an_mapB, a, t->an_rows_b / F::kBN, t->an_rows_a / kBM, t->an_splits, s);
+  if (e != cudaSuccess) return e;
+  const size_t cnt = (size_t)M * g->n_lm;
+  k_reduce_partials<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(M, g->n_lm, t->an_splits, t->part, t->an_rs,
+                                                                  t->an_cs, t->an_mono, t->an_mean, t->an_colsum,
+                                                                  g->A);
+  g->launches++;
+  return cudaGetLastError();
+}
+
+template <class F>
+static cudaError_t pack_coefficients_form(yy_grid *g, yy_tc_tables *t, cudaStream_t s) {
+  const int M = 2 * g->n_r;
+  const size_t qsz = (size_t)M * 2 * g->n_lm;
+  // Phi and g_r: the monopole pair (columns 0 and n_lm) is added in the epilogue
+  const double add[3] = {kY00, kY00, 0.0};
+  PackBatch b = {};
+  for (int c = 0; c < 3; ++c) {
+    PackArgs &p = b.job[c];
+    p.rows = M;
+    p.rows_pad = t->an_rows_a;
+    p.K = 2 * g->n_lm;
+    p.k_pad = t->sy_kpad;
+    p.src0 = p.src1 = g->Q + c * qsz;
+    p.split_row = M;
+    p.ld = 2 * g->n_lm;
+    p.zero_k0 = 0;
+    p.zero_k1 = g->n_lm;
+    p.zero_row = -1;
+    p.add_factor = add[c];
+    p.row_add = t->sy_add[c];
+    p.scale_out = t->sy_rs[c];
+    p.scale_out_f = t->sy_rsf[c];
+    p.out = t->sy_A[c];
+  }
+  cudaError_t e = launch_pack<F>(b, 3, s);
+  g->launches++;
+  return e;
+}
+
+template <class F>
+static cudaError_t synthesis_form(yy_grid *g, yy_tc_tables *t, int which, double *py, double *pg, double *gy,
+                                  double *gg, cudaStream_t s) {
+  const size_t comp = (size_t)g->n_r * g->n_ang;
+  // (coefficient set, table, outputs)
+  struct Job {
+    int q, tab;
+    double *o0, *o1;
+  } jobs[4] = {{0, 0, py, pg},
+               {1, 0, gy, gg},
+               {2, 1, gy ? gy + comp : nullptr, gg ? gg + comp : nullptr},
+               {2, 2, gy ? gy + 2 * comp : nullptr, gg ? gg + 2 * comp : nullptr}};
+  const int j0 = which == 0 ? 0 : 1, j1 = which == 0 ? 1 : 4;
+  for (int j = j0; j < j1; ++j) {
+    TcArgs a = {};
+    a.M = 2 * g->n_r;
+    a.N = g->n_ang;
+    a.kb_total = t->sy_kpad * F::kElem / kRowBytes;
+    a.kb_per_tile = a.kb_total;
+    a.a_rows = t->an_rows_a;
+    a.b_rows = t->sy_rows_b;
+    a.mode = 1;
+    a.out0 = jobs[j].o0;
+    a.out1 = jobs[j].o1;
+    a.out_split = g->n_r;
+    a.ldo = g->n_ang;
+    a.row_scale = t->sy_rsf[jobs[j].q];
+    a.col_scale = t->sy_csf[jobs[j].tab];
+    a.row_add = t->sy_add[jobs[j].q];
+    a.err = g->err;
+    cudaError_t e = launch_gemm<F>(g, t, t->sy_mapA[jobs[j].q], t->sy_mapB[jobs[j].tab], a, t->sy_rows_b / F::kBN,
+                                   t->an_rows_a / kBM, 1, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t tc_analysis(yy_grid *g, yy_precision prec, const double *ry, const double *rg, cudaStream_t s) {
+  yy_tc_tables *t = g->tc[prec];
+  switch (prec) {
+    case YY_FP16X2: return analysis_form<FormFP16x2>(g, t, ry, rg, s);
+    case YY_BF16X3: return analysis_form<FormBF16x3>(g, t, ry, rg, s);
+    case YY_TF32: return analysis_form<FormTF32>(g, t, ry, rg, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t tc_pack_coefficients(yy_grid *g, yy_precision prec, cudaStream_t s) {
+  yy_tc_tables *t = g->tc[prec];
+  switch (prec) {
+    case YY_FP16X2: return pack_coefficients_form<FormFP16x2>(g, t, s);
+    case YY_BF16X3: return pack_coefficients_form<FormBF16x3>(g, t, s);
+    case YY_TF32: return pack_coefficients_form<FormTF32>(g, t, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t tc_synthesis(yy_grid *g, yy_precision prec, int which, double *py, double *pg, double *gy, double *gg,
+                         cudaStream_t s) {
+  yy_tc_tables *t = g->tc[prec];
+  switch (prec) {
+    case YY_FP16X2: return synthesis_form<FormFP16x2>(g, t, which, py, pg, gy, gg, s);
+    case YY_BF16X3: return synthesis_form<FormBF16x3>(g, t, which, py, pg, gy, gg, s);
+    case YY_TF32: return synthesis_form<FormTF32>(g, t, which, py, pg, gy, gg, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace yy
