@@ -74,7 +74,7 @@ struct FormTF32 {
 constexpr int kBM = 128;
 constexpr int kRowBytes = 64;        // K bytes per tile row and stage: one 64-byte swizzle atom
 constexpr int kPadK = 64;            // K padding (elements) of every packed operand
-constexpr int kBChunk = 32;          // rows of one B box; B tiles are loaded in 32-row chunks
+constexpr int kBChunk = 32;          // rows of one B box when clusters share B tiles
 constexpr double kY00 = 0.28209479177387814347403972578039;   // K_00 P_0^0 = 1/sqrt(4 pi)
 
 template <class F>
@@ -314,7 +314,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   constexpr int KSTEP_BYTES = 32;                   // one MMA consumes 32 bytes of K per row
   constexpr int KSTEPS = kRowBytes / KSTEP_BYTES;   // MMAs per K block and product
   constexpr int BK = kRowBytes / F::kElem;          // elements of K per block
-  constexpr int NCHUNK = BN / kBChunk;
+  constexpr int BROWS = (C > 1) ? kBChunk : BN;     // rows per B load (one box without clusters)
+  constexpr int NCHUNK = BN / BROWS;
   constexpr uint16_t MASK = (uint16_t)((1u << C) - 1u);
 
   extern __shared__ uint8_t smem_raw[];
@@ -378,9 +379,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             const int brow = p * a.b_rows + nt * BN;
             for (int c = rank; c < NCHUNK; c += C) {
               if constexpr (C > 1)
-                tma_load_2d_mc(&tmB, bdst + c * kBChunk * kRowBytes, &full[s], kx, brow + c * kBChunk, MASK);
+                tma_load_2d_mc(&tmB, bdst + c * BROWS * kRowBytes, &full[s], kx, brow + c * BROWS, MASK);
               else
-                tma_load_2d(&tmB, bdst + c * kBChunk * kRowBytes, &full[s], kx, brow + c * kBChunk);
+                tma_load_2d(&tmB, bdst + c * BROWS * kRowBytes, &full[s], kx, brow + c * BROWS);
             }
           }
         }
@@ -901,11 +902,12 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
   if ((e = launch_pack<F>(bs, 3, 0)) != cudaSuccess) return YY_ERR_CUDA;
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return YY_ERR_CUDA;
 
+  const int brows = t->cluster > 1 ? kBChunk : F::kBN;   // B box rows, as the kernel loads them
   bool ok = make_map<F>(&t->an_mapA, t->an_A, t->an_kpad, F::kPA * t->an_rows_a, kBM) &&
-            make_map<F>(&t->an_mapB, t->an_B, t->an_kpad, F::kPB * t->an_rows_b, kBChunk);
+            make_map<F>(&t->an_mapB, t->an_B, t->an_kpad, F::kPB * t->an_rows_b, brows);
   for (int c = 0; c < 3 && ok; ++c)
     ok = make_map<F>(&t->sy_mapA[c], t->sy_A[c], t->sy_kpad, F::kPA * t->an_rows_a, kBM) &&
-         make_map<F>(&t->sy_mapB[c], t->sy_B[c], t->sy_kpad, F::kPB * t->sy_rows_b, kBChunk);
+         make_map<F>(&t->sy_mapB[c], t->sy_B[c], t->sy_kpad, F::kPB * t->sy_rows_b, brows);
   if (!ok) return YY_ERR_NOT_SUPPORTED;
   return YY_OK;
 }
