@@ -21,10 +21,10 @@
 // so the packing, reduction and epilogue code uses fp32 arithmetic and
 // exact integer conversions between fp32 and float64.
 //
-// Kernel layout (persistent, 6 warps per CTA, one CTA per SM):
+// Kernel layout (persistent, 10 warps per CTA, one CTA per SM):
 //   warp 0  lane 0: TMA producer over a ring of STAGES shared-memory stages
 //   warp 1  allocates TMEM; lane 0 issues the MMAs and the commits
-//   warps 2-5: epilogue, TMEM lanes 32 (w % 4) .. + 31
+//   warps 2-9: epilogue, TMEM lanes 32 (w % 4) .. + 31, alternate column chunks
 // Every mbarrier wait gives up after ~2 s, sets the device error word and
 // lets the CTA finish (TMEM is always released).
 #include <cuda.h>
@@ -81,9 +81,14 @@ template <class F>
 constexpr int stage_bytes() {
   return F::kPA * kBM * kRowBytes + F::kPB * F::kBN * kRowBytes;
 }
+constexpr int kEpiWarps = 16;        // four epilogue warps per TMEM lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kEpiCols = 16;         // columns per TMEM load / staged fragment
+constexpr int kStgBytes = kEpiWarps * 32 * kEpiCols * 4;   // one 32 x 16 fp32 fragment per epilogue warp
+
 template <class F>
 constexpr int smem_bytes() {
-  return F::kStages * stage_bytes<F>() + 1024 /*align*/ + 512 /*barriers*/;
+  return F::kStages * stage_bytes<F>() + kStgBytes + 1024 /*align*/ + 256 /*barriers*/;
 }
 
 // ---------------------------------------------------------------------------
@@ -246,6 +251,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // fp32 <-> float64 with integer operations only: exact widening, and
 // round-to-nearest-even narrowing (the same result as the conversion
 // instruction); zero / subnormal / overflow / NaN take the instruction.
@@ -306,7 +321,7 @@ struct TcArgs {
 // TMEM (2 x BN columns) so the epilogue of one tile overlaps the MMAs of the
 // next.
 template <class F, int C>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kThreads, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
   constexpr int BN = F::kBN, S = F::kStages;
   constexpr int A_TILE = kBM * kRowBytes, B_TILE = BN * kRowBytes;
@@ -320,7 +335,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t *full = (uint64_t *)(smem + S * STAGE);
+  float *staging = (float *)(smem + S * STAGE);   // [kEpiWarps][32][kEpiCols], XOR-swizzled columns
+  uint64_t *full = (uint64_t *)(smem + S * STAGE + kStgBytes);
   uint64_t *empty = full + S;
   uint64_t *tfull = empty + S;      // [2]
   uint64_t *tempty = tfull + 2;     // [2]
@@ -339,7 +355,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4);
+      mbar_init(&tempty[b], kEpiWarps);
     }
     fence_barrier_init();
   }
@@ -434,8 +450,14 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       }
     }
   } else {
-    // epilogue: TMEM lane quarter of this warp
+    // epilogue: TMEM lane quarter of this warp; the four warps of a quarter
+    // take alternate 16-column chunks.  Each 32 x 16 fragment is scaled in
+    // fp32 (lane = row), staged in shared memory, and written out as row
+    // segments by the whole warp (half-warp = row, lane = column), so the
+    // global stores are coalesced.
     const int quarter = warp & 3;
+    const int sub = (warp - 2) >> 2;                    // 0..3 within the quarter
+    float *stg = staging + (warp - 2) * 32 * kEpiCols;
     int it = 0;
     for (int t = cluster; t < total; t += n_clusters, ++it) {
       const int b = it & 1;
@@ -443,45 +465,48 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       tc_fence_after();
       const int mt = (t % m_groups) * C + rank;
       const int nt = (t / m_groups) % a.n_tiles, z = t / (m_groups * a.n_tiles);
-      const int row = mt * kBM + quarter * 32 + lane;
-      const bool live = row < a.M;
-      float rs = 0.0f, ra = 0.0f;
-      double *orow = nullptr;
-      if (a.mode == 1 && live) {
-        rs = a.row_scale[row];
-        ra = a.row_add[row];
-        orow = (row < a.out_split) ? a.out0 + (size_t)row * a.ldo : a.out1 + (size_t)(row - a.out_split) * a.ldo;
+      const int row0 = mt * kBM + quarter * 32;          // first row of this warp's fragment
+      const int myrow = row0 + lane;
+      float rs = 1.0f, ra = 0.0f;
+      unsigned long long optr = 0ull;                    // this lane's output row (mode 1)
+      if (a.mode == 1 && myrow < a.M) {
+        rs = a.row_scale[myrow];
+        ra = a.row_add[myrow];
+        optr = (unsigned long long)((myrow < a.out_split) ? a.out0 + (size_t)myrow * a.ldo
+                                                          : a.out1 + (size_t)(myrow - a.out_split) * a.ldo);
       }
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        uint32_t v[32];
-        tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0), v);
-        if (!live) continue;
-        const int col0 = nt * BN + c0;
-        if (a.mode == 0) {
-          float *dst = a.part + ((size_t)z * a.M + row) * a.N + col0;
+      for (int c0 = kEpiCols * sub; c0 < BN; c0 += kEpiCols * (kEpiWarps / 4)) {
+        uint32_t v[16];
+        tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0), v);
+        const int colbase = nt * BN + c0;
+        // column scales of this chunk, one per lane of the lower half-warp
+        float csl = 0.0f;
+        if (a.mode == 1 && lane < kEpiCols && colbase + lane < a.N) csl = a.col_scale[colbase + lane];
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (col0 + j < a.N) dst[j] = __uint_as_float(v[j]);
-        } else {
-          // result = acc * row scale * column scale (powers of two: exact) +
-          // monopole term, rounded once in fp32, widened exactly to float64
-          double *dst = orow + col0;
-          const bool vec = (col0 + 32 <= a.N) && (((uintptr_t)dst & 15u) == 0);
-          if (vec) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-              double2 o;
-              o.x = f32_to_f64(fmaf(__uint_as_float(v[j]) * rs, a.col_scale[col0 + j], ra));
-              o.y = f32_to_f64(fmaf(__uint_as_float(v[j + 1]) * rs, a.col_scale[col0 + j + 1], ra));
-              *(double2 *)(dst + j) = o;
-            }
+        for (int j = 0; j < kEpiCols; ++j) {
+          const float cs = __shfl_sync(0xffffffffu, csl, j);
+          const float x = __uint_as_float(v[j]);
+          const float y = (a.mode == 1) ? fmaf(x * rs, cs, ra) : x;
+          stg[lane * kEpiCols + (j ^ (lane & 15))] = y;
+        }
+        __syncwarp();
+        const int hl = lane >> 4, cl = lane & 15;
+        const int col = colbase + cl;
+        const bool col_ok = col < a.N;
+#pragma unroll 4
+        for (int r = 0; r < 32; r += 2) {
+          const int rr = r + hl;                          // row of this half-warp
+          const int row = row0 + rr;
+          const float y = stg[rr * kEpiCols + (cl ^ (rr & 15))];
+          if (a.mode == 0) {
+            if (row < a.M && col_ok) a.part[((size_t)z * a.M + row) * a.N + col] = y;
           } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (col0 + j < a.N) dst[j] = f32_to_f64(fmaf(__uint_as_float(v[j]) * rs, a.col_scale[col0 + j], ra));
+            const unsigned long long rp = __shfl_sync(0xffffffffu, optr, rr);
+            if (row < a.M && col_ok) ((double *)rp)[col] = f32_to_f64(y);
           }
         }
+        __syncwarp();
       }
       tc_fence_before();
       __syncwarp();
@@ -811,7 +836,7 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(3 * 64);
-    cfg.blockDim = dim3(192);
+    cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = smem_bytes<F>();
     cfg.attrs = attr;
     cfg.numAttrs = 1;
@@ -976,7 +1001,7 @@ static cudaError_t launch_gemm(yy_grid *g, yy_tc_tables *t, const CUtensorMap &m
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(clusters * C);
-  cfg.blockDim = dim3(192);
+  cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem_bytes<F>();
   cfg.stream = s;
   cfg.attrs = attr;
