@@ -13,10 +13,15 @@
  *              (§3 Eqs. ac/as with the overlap weight of §4), both patches;
  *   radial     inner / outer sums of Eqs. phiin/phiout at the interfaces
  *              r_n^+, as scaled prefix / suffix scans over r;
- *   synthesis  Phi(r_q) = Phi_q(r_q) + Phi_p(r_q) on both patches (§4), the
- *              other patch's moments evaluated at the target points expressed
- *              in that patch's angles (Eqs. trafotheta/trafophi); optionally
- *              -grad(Phi) in the target patch's local spherical basis.
+ *   combine    the other patch's moments re-expressed in each patch's frame
+ *              (a fixed rotation within each degree l) and added to its own,
+ *              so that one set of coefficients per patch gives the §4 sum
+ *              Phi(r_q) = Phi_q(r_q) + Phi_p(r_q) (the other patch's terms are
+ *              its harmonics at the target points in its own angles,
+ *              Eqs. trafotheta/trafophi);
+ *   synthesis  Phi on both patches from the combined coefficients and the
+ *              own-frame harmonics; optionally -grad(Phi) in the target
+ *              patch's local spherical basis.
  *
  * Conventions (all functions):
  *  - Arrays are C-contiguous float64.  A patch field is [n_r][n_theta][n_phi]
@@ -83,13 +88,19 @@ typedef enum {
  *   YY_TABLE_WEIGHTS  [n_theta][n_phi]       overlap weights w_jk (§4)
  *   YY_TABLE_TBAR     [n_theta][n_lm]        K_lm T_j^(lm) (Eq. tlm), cos and sin slots equal
  *   YY_TABLE_ANALYSIS [n_lm][n_theta*n_phi]  w_jk K_lm T_j^(lm) {C_k^(m), S_k^(m)}
- *   YY_TABLE_SYNTH    [n_theta*n_phi][2 n_lm] K_lm P_l^m {cos, sin}(m phi) at the cell
- *                     centre (first n_lm) and at the centre seen from the
- *                     other patch (last n_lm)
- *   YY_TABLE_SYNTH_T  same layout: d/dtheta, rotated into the target basis
- *   YY_TABLE_SYNTH_P  same layout: (1/sin theta) d/dphi, rotated likewise
- *   YY_TABLE_MOMENTS  [2 n_r][n_lm]          normalised A of the last solve (Yin rows first)
- *   YY_TABLE_COEFF    [2 n_r][2 n_lm]        synthesis coefficients of the last solve */
+ *   YY_TABLE_SYNTH    [n_theta*n_phi][n_lm]  K_lm P_l^m {cos, sin}(m phi) at the cell centre
+ *   YY_TABLE_SYNTH_T  same layout: d/dtheta
+ *   YY_TABLE_SYNTH_P  same layout: (1/sin theta) d/dphi
+ *   YY_TABLE_MOMENTS  [2 n_r][n_lm]          normalised A of each patch's own cells in
+ *                                            its own frame, last solve (Yin rows first)
+ *   YY_TABLE_COEFF    [3][2 n_r][n_lm]       synthesis coefficients of the last solve:
+ *                                            Phi, g_r, angular gradient
+ *   YY_TABLE_ROTATION [sum_l (2l+1)^2]       per degree l, the (2l+1) x (2l+1) matrix D^l
+ *                                            (row-major, at offset l (4l^2-1)/3) with
+ *                                            Y_i(other-patch angles) = sum_j D^l_ij Y_j(own
+ *                                            angles); modes of degree l in index order
+ *   YY_TABLE_MOMENTS_TOTAL [2 n_r][n_lm]     moments of both patches in each patch's
+ *                                            frame: A_p + D^T A_(other), last solve */
 typedef enum {
   YY_TABLE_WEIGHTS = 0,
   YY_TABLE_TBAR = 1,
@@ -98,15 +109,17 @@ typedef enum {
   YY_TABLE_SYNTH_T = 4,
   YY_TABLE_SYNTH_P = 5,
   YY_TABLE_MOMENTS = 6,
-  YY_TABLE_COEFF = 7
+  YY_TABLE_COEFF = 7,
+  YY_TABLE_ROTATION = 8,
+  YY_TABLE_MOMENTS_TOTAL = 9
 } yy_table;
 
 /* Create a grid handle on the current CUDA device and build every
  * density-independent term once (§3: the constant terms are computed only
  * while the grid is fixed): overlap weights, polar / azimuthal integrals,
- * normalised Legendre tables at the own and the other patch's angles, their
- * angular derivatives, and the radial scan coefficients, all in float64 on
- * the GPU.  Synchronises the device before returning.
+ * normalised harmonic tables at the cell centres and their angular
+ * derivatives, the per-degree rotation between the two patches' harmonics,
+ * and the radial scan coefficients, all in float64 on the GPU.  Synchronises the device before returning.
  *   r_edges      host, n_r + 1 values, r_edges[0] >= 0, strictly increasing
  *   n_r          radial zones, 1 <= n_r <= 1<<20
  *   n_theta/phi  cells per patch, >= 1 each, n_theta * n_phi <= 1<<24
@@ -166,7 +179,8 @@ const char *yy_status_string(yy_status s);
  * events on its stream at the stage boundaries; yy_grid_stage_ms synchronises
  * and returns the durations of the last solve in milliseconds:
  *   ms[YY_STAGE_ANALYSIS]   analysis contraction (operand packing included)
- *   ms[YY_STAGE_SCAN]       radial scans (coefficient packing included)
+ *   ms[YY_STAGE_SCAN]       moment combination and radial scans (coefficient
+ *                           packing included)
  *   ms[YY_STAGE_SYNTH_PHI]  synthesis of Phi (one contraction)
  *   ms[YY_STAGE_SYNTH_GRAD] synthesis of -grad Phi (three contractions; 0
  *                           without gradient)                              */
@@ -188,10 +202,10 @@ yy_status yy_grid_stage_ms(yy_grid *g, double *ms);
  * allocator.  It computes the same coefficients as the solve's scan stage.
  *   r_edges  device, n_r + 1 radii obeying yy_grid_create's rules (not
  *            checked here; values that break them give undefined results)
- *   moments  device, [2 n_r][n_lm] normalised moments, Yin rows first, in the
- *            layout of YY_TABLE_MOMENTS
- *   coeff    device out, [3][2 n_r][2 n_lm]: the Phi, g_r and angular-gradient
- *            coefficients; block 0 has the layout of YY_TABLE_COEFF
+ *   moments  device, [2 n_r][n_lm] normalised moments, Yin rows first: the
+ *            combined moments of YY_TABLE_MOMENTS_TOTAL
+ *   coeff    device out, [3][2 n_r][n_lm]: the Phi, g_r and angular-gradient
+ *            coefficients, in the layout of YY_TABLE_COEFF
  *   n_r >= 1, 0 <= l_max <= 80, G finite; all pointers 16-byte aligned.
  * Scratch: a static device array of 2^21 float64 (16 MiB) that every GPU
  * loading the library keeps until exit; 2 n_r (l_max+1)^2 must not exceed
@@ -207,9 +221,10 @@ yy_status yy_radial_scan_static(const double *r_edges, int n_r, int l_max, doubl
 /* Number of CUDA kernels the last yy_potential call launched (-1 for NULL). */
 int yy_last_launch_count(const yy_grid *g);
 
-/* Dense flop count of one solve: 2 M N K of the analysis plus one or four
- * synthesis contractions (with_gradient = 0 / 1), in floating-point
- * operations (the algorithmic count, before any operand splitting). */
+/* Dense flop count of one solve: 2 M N K of the analysis, the moment
+ * combination, and one or four synthesis contractions (with_gradient = 0 / 1;
+ * K = n_lm each), in floating-point operations (the algorithmic count,
+ * before any operand splitting). */
 double yy_solve_flops(const yy_grid *g, int with_gradient);
 
 #ifdef __cplusplus

@@ -54,12 +54,13 @@ static yy_status from_cuda(cudaError_t e) {
 
 static void free_all(yy_grid *g) {
   if (!g) return;
-  double *dbufs[] = {g->r_edges, g->w,    g->tbar, g->ban,       g->ysyn,      g->ysyn_t,
-                     g->ysyn_p,  g->scan, g->scan_maps, g->gl_nodes, g->A, g->part, g->cin,
-                     g->Q,       g->stage_rho, g->stage_phi, g->stage_grad};
+  double *dbufs[] = {g->r_edges, g->w,      g->tbar,      g->ban,       g->ysyn,  g->ysyn_t,
+                     g->ysyn_p,  g->rot,    g->scan,      g->scan_maps, g->gl_nodes, g->A,
+                     g->Atot,    g->part,   g->cin,       g->Q,         g->stage_rho, g->stage_phi,
+                     g->stage_grad};
   for (double *p : dbufs)
     if (p) cudaFree(p);
-  float *fbufs[] = {g->ban32, g->ysyn32, g->ysyn_t32, g->ysyn_p32, g->rho32, g->Q32};
+  float *fbufs[] = {g->rot32, g->ban32, g->ysyn32, g->ysyn_t32, g->ysyn_p32, g->rho32, g->Q32};
   for (float *p : fbufs)
     if (p) cudaFree(p);
   if (g->err) cudaFree(g->err);
@@ -132,9 +133,11 @@ yy_status yy_grid_create(const double *r_edges, int n_r, int n_theta, int n_phi,
   A((void **)&g->w, n_ang * sizeof(double));
   A((void **)&g->tbar, (size_t)n_theta * n_lm * sizeof(double));
   A((void **)&g->ban, n_lm * n_ang * sizeof(double));
-  A((void **)&g->ysyn, n_ang * 2 * n_lm * sizeof(double));
-  A((void **)&g->ysyn_t, n_ang * 2 * n_lm * sizeof(double));
-  A((void **)&g->ysyn_p, n_ang * 2 * n_lm * sizeof(double));
+  A((void **)&g->ysyn, n_ang * n_lm * sizeof(double));
+  A((void **)&g->ysyn_t, n_ang * n_lm * sizeof(double));
+  A((void **)&g->ysyn_p, n_ang * n_lm * sizeof(double));
+  A((void **)&g->rot, rotation_table_size(l_max) * sizeof(double));
+  A((void **)&g->rot32, rotation_table_size(l_max) * sizeof(float));
   A((void **)&g->scan, (size_t)n_r * (l_max + 1) * 8 * sizeof(double));
   {
     int nc = 1, ch = 1;
@@ -142,9 +145,10 @@ yy_status yy_grid_create(const double *r_edges, int n_r, int n_theta, int n_phi,
     A((void **)&g->scan_maps, (size_t)2 * nc * n_lm * 4 * sizeof(double));
   }
   A((void **)&g->A, M * n_lm * sizeof(double));
+  A((void **)&g->Atot, M * n_lm * sizeof(double));
   if (g->split_k > 1) A((void **)&g->part, (size_t)g->split_k * M * n_lm * sizeof(double));
   A((void **)&g->cin, M * n_lm * sizeof(double));
-  A((void **)&g->Q, 3 * M * 2 * n_lm * sizeof(double));
+  A((void **)&g->Q, 3 * M * n_lm * sizeof(double));
   A((void **)&g->err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(g->r_edges, r_edges, (n_r + 1) * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(g->err, 0, sizeof(int));
@@ -219,6 +223,7 @@ yy_status yy_potential(yy_grid *g, const double *rho_yin, const double *rho_yang
   if (e == cudaSuccess)
     e = simt ? analysis_simt(g, rho_yin, rho_yang, f32, s) : tc_analysis(g, prec, rho_yin, rho_yang, s);
   mark(1);
+  if (e == cudaSuccess) e = rotate_moments(g, prec == YY_FP64, s);
   if (e == cudaSuccess) e = radial_scan(g, f32, s);
   if (e == cudaSuccess && !simt) e = tc_pack_coefficients(g, prec, s);
   mark(2);
@@ -272,11 +277,13 @@ yy_status yy_grid_copy_table(yy_grid *g, yy_table which, double *host_dst, size_
     case YY_TABLE_WEIGHTS: src = g->w; n = n_ang; break;
     case YY_TABLE_TBAR: src = g->tbar; n = (size_t)g->n_theta * n_lm; break;
     case YY_TABLE_ANALYSIS: src = g->ban; n = n_lm * n_ang; break;
-    case YY_TABLE_SYNTH: src = g->ysyn; n = n_ang * 2 * n_lm; break;
-    case YY_TABLE_SYNTH_T: src = g->ysyn_t; n = n_ang * 2 * n_lm; break;
-    case YY_TABLE_SYNTH_P: src = g->ysyn_p; n = n_ang * 2 * n_lm; break;
+    case YY_TABLE_SYNTH: src = g->ysyn; n = n_ang * n_lm; break;
+    case YY_TABLE_SYNTH_T: src = g->ysyn_t; n = n_ang * n_lm; break;
+    case YY_TABLE_SYNTH_P: src = g->ysyn_p; n = n_ang * n_lm; break;
     case YY_TABLE_MOMENTS: src = g->A; n = M * n_lm; break;
-    case YY_TABLE_COEFF: src = g->Q; n = M * 2 * n_lm; break;
+    case YY_TABLE_COEFF: src = g->Q; n = 3 * M * n_lm; break;
+    case YY_TABLE_ROTATION: src = g->rot; n = (size_t)rotation_table_size(g->lmax); break;
+    case YY_TABLE_MOMENTS_TOTAL: src = g->Atot; n = M * n_lm; break;
     default: return YY_ERR_INVALID_ARG;
   }
   if (host_dst == nullptr) {
@@ -341,8 +348,10 @@ double yy_solve_flops(const yy_grid *g, int with_gradient) {
   if (!g) return 0.0;
   const double M = 2.0 * g->n_r, K_an = g->n_ang, N_an = g->n_lm;
   const double analysis = 2.0 * M * N_an * K_an;
-  const double synth = 2.0 * M * (2.0 * g->n_lm) * g->n_ang;
-  return analysis + (with_gradient ? 4.0 : 1.0) * synth;
+  const double synth = 2.0 * M * g->n_lm * g->n_ang;
+  double rotation = 0.0;
+  for (int l = 0; l <= g->lmax; ++l) rotation += 2.0 * M * (2.0 * l + 1.0) * (2.0 * l + 1.0);
+  return analysis + rotation + (with_gradient ? 4.0 : 1.0) * synth;
 }
 
 }  // extern "C"

@@ -1,7 +1,8 @@
 // CUDA-core contractions of the solver: float64 (DFMA) and float32 (FFMA).
 //
 //  analysis   A[2 n_r][n_lm]  = rho[2 n_r][n_ang] . B_an^T      (§3 Eqs. ac/as, §4 weights)
-//  synthesis  Phi[2 n_r][n_ang] = Qcat[2 n_r][2 n_lm] . Ysyn^T   (§4 sum of four potentials)
+//  synthesis  Phi[2 n_r][n_ang] = Q[2 n_r][n_lm] . Ysyn^T   (§4 sum of four potentials, with
+//             the other patch's moments already rotated into each patch's frame)
 //
 // Both operands are K-major (row m of A and row n of B are contiguous in k),
 // rows of A may come from two arrays (Yin rows then Yang rows) and rows of C
@@ -179,7 +180,7 @@ cudaError_t analysis_simt(yy_grid *g, const double *rho_yin, const double *rho_y
 
 cudaError_t synthesis_simt(yy_grid *g, int which, double *phi_yin, double *phi_yang, double *grad_yin,
                            double *grad_yang, bool fp32, cudaStream_t s) {
-  const int M = 2 * g->n_r, N = g->n_ang, K = 2 * g->n_lm;
+  const int M = 2 * g->n_r, N = g->n_ang, K = g->n_lm;
   const size_t qsz = (size_t)M * K;
   const size_t comp = (size_t)g->n_r * g->n_ang;
   cudaError_t err;
@@ -215,7 +216,7 @@ cudaError_t synthesis_simt(yy_grid *g, int which, double *phi_yin, double *phi_y
 
 cudaError_t convert_tables_f32(yy_grid *g) {
   const size_t n_ban = (size_t)g->n_lm * g->n_ang;
-  const size_t n_syn = (size_t)g->n_ang * 2 * g->n_lm;
+  const size_t n_syn = (size_t)g->n_ang * g->n_lm;
   cudaError_t err;
   if ((err = dmalloc((void **)&g->ban32, n_ban * sizeof(float))) != cudaSuccess) return err;
   if ((err = dmalloc((void **)&g->ysyn32, n_syn * sizeof(float))) != cudaSuccess) return err;
@@ -223,7 +224,7 @@ cudaError_t convert_tables_f32(yy_grid *g) {
   if ((err = dmalloc((void **)&g->ysyn_p32, n_syn * sizeof(float))) != cudaSuccess) return err;
   if ((err = dmalloc((void **)&g->rho32, 2 * (size_t)g->n_r * g->n_ang * sizeof(float))) != cudaSuccess)
     return err;
-  if ((err = dmalloc((void **)&g->Q32, 3 * (size_t)2 * g->n_r * 2 * g->n_lm * sizeof(float))) != cudaSuccess)
+  if ((err = dmalloc((void **)&g->Q32, 3 * (size_t)2 * g->n_r * g->n_lm * sizeof(float))) != cudaSuccess)
     return err;
   k_to_f32<<<(unsigned)((n_ban + 255) / 256), 256>>>(n_ban, g->ban, g->ban32);
   k_to_f32<<<(unsigned)((n_syn + 255) / 256), 256>>>(n_syn, g->ysyn, g->ysyn32);

@@ -28,25 +28,28 @@ struct yy_grid {
   double *w;           // [n_theta][n_phi]        overlap weights
   double *tbar;        // [n_theta][n_lm]         K_lm T_j^(lm)
   double *ban;         // [n_lm][n_ang]           analysis operand (K-major)
-  double *ysyn;        // [n_ang][2 n_lm]         synthesis operand, same | cross
-  double *ysyn_t;      // [n_ang][2 n_lm]         d/dtheta, target basis
-  double *ysyn_p;      // [n_ang][2 n_lm]         (1/sin) d/dphi, target basis
+  double *ysyn;        // [n_ang][n_lm]           synthesis operand (own frame)
+  double *ysyn_t;      // [n_ang][n_lm]           d/dtheta
+  double *ysyn_p;      // [n_ang][n_lm]           (1/sin) d/dphi
+  double *rot;         // [sum_l (2l+1)^2]        D^l, other-frame harmonics in own-frame ones
+  float *rot32;        // same, rounded to float32
   double *scan;        // [n_r][lmax+1][8]        a_in, b_in, e_out, f_out, output factors
   double *scan_maps;   // [2][chunks][n_lm] x 4   per-chunk affine maps of the scans
   double *gl_nodes;    // GL nodes / weights on [0, 1] for the weight integrals
 
   // workspace (device)
-  double *A;           // [2 n_r][n_lm]
+  double *A;           // [2 n_r][n_lm]           moments of each patch's own cells
+  double *Atot;        // [2 n_r][n_lm]           both patches' moments in each patch's frame
   double *part;        // split-K partials [split][2 n_r][n_lm]
   int split_k;
   double *cin;         // [2 n_r][n_lm] inner scan values
-  double *Q;           // [3][2 n_r][2 n_lm]  Phi, g_r and g_angle coefficients
+  double *Q;           // [3][2 n_r][n_lm]    Phi, g_r and g_angle coefficients
   int *err;            // device error word
 
   // float32 form
   float *ban32, *ysyn32, *ysyn_t32, *ysyn_p32;   // same layouts as float64
   float *rho32;        // [2 n_r][n_ang]
-  float *Q32;          // [3][2 n_r][2 n_lm]
+  float *Q32;          // [3][2 n_r][n_lm]
 
   // tensor-core forms
   yy_tc_tables *tc[5];
@@ -70,6 +73,8 @@ cudaError_t dmalloc(void **p, size_t bytes);
 
 // tables (yy_tables.cu)
 cudaError_t build_tables(yy_grid *g, const double *gl_host, int n_gl);
+// entries of the rotation table: sum_{l <= lmax} (2l+1)^2
+inline int rotation_table_size(int lmax) { return (lmax + 1) * (4 * (lmax + 1) * (lmax + 1) - 1) / 3; }
 
 // float64 / float32 CUDA-core contractions (yy_gemm_simt.cu)
 cudaError_t analysis_simt(yy_grid *g, const double *rho_yin, const double *rho_yang,
@@ -79,7 +84,9 @@ cudaError_t synthesis_simt(yy_grid *g, int which, double *phi_yin, double *phi_y
                            double *grad_yin, double *grad_yang, bool fp32, cudaStream_t s);
 cudaError_t convert_tables_f32(yy_grid *g);
 
-// radial scans (yy_scan.cu); writes Q (and Q32 if want_f32)
+// Atot = A + D^T A(other patch), float32 products unless fp64 (yy_scan.cu)
+cudaError_t rotate_moments(yy_grid *g, bool fp64, cudaStream_t s);
+// radial scans (yy_scan.cu): Atot -> Q (and Q32 if want_f32)
 void scan_geometry(const yy_grid *g, int *nc, int *ch);
 cudaError_t radial_scan(yy_grid *g, bool want_f32, cudaStream_t s);
 

@@ -14,8 +14,9 @@
 //   k_scan_maps   folds each chunk into one affine map per direction
 //   k_scan_apply  starts each chunk from the composed maps of the chunks
 //                 before (inner) / after (outer) it and replays it
-// Outputs, in the layout the synthesis contraction reads ("cat" rows: the
-// row of patch p holds [coefficients of p | coefficients of the other patch]):
+// The scans read Atot, the moments of both patches expressed in the frame of
+// the patch a row belongs to (k_rotate_moments, below), so each output row
+// holds the complete coefficients of its patch.  Outputs [3][2 n_r][n_lm]:
 //   Q   = -G 4 pi/(2l+1) (c_n + d_n)                         -> Phi
 //   Q_r =  G 4 pi/(2l+1) (-(l+1) c_n + l d_n) / r_{n+1}      -> g_r
 //   Q_t =  G 4 pi/(2l+1) (c_n + d_n) / r_{n+1}               -> g_theta, g_phi
@@ -108,8 +109,7 @@ k_scan_apply(ScanGeom s, const double *__restrict__ A, const double *__restrict_
     x = fma(k[0], x, k[1] * Ap[(size_t)n * s.n_lm]);
     Cp[(size_t)n * s.n_lm] = x;
   }
-  const size_t row2 = 2 * (size_t)s.n_lm;
-  const size_t qsz = (size_t)2 * s.n_r * row2;
+  const size_t qsz = (size_t)2 * s.n_r * s.n_lm;
   for (int n = n1 - 1; n >= n0; --n) {
     const double *k = coef + ((size_t)n * L1 + l) * 8;
     const double an = (n + 1 < s.n_r) ? Ap[(size_t)(n + 1) * s.n_lm] : 0.0;
@@ -119,27 +119,70 @@ k_scan_apply(ScanGeom s, const double *__restrict__ A, const double *__restrict_
     const double q = k[4] * sum;
     const double qr = fma(k[5], cn, k[6] * y);
     const double qt = k[7] * sum;
-    const size_t own = (size_t)(p * s.n_r + n) * row2 + idx;
-    const size_t oth = (size_t)((1 - p) * s.n_r + n) * row2 + s.n_lm + idx;
-    Q[own] = q;
-    Q[oth] = q;
-    Q[qsz + own] = qr;
-    Q[qsz + oth] = qr;
-    Q[2 * qsz + own] = qt;
-    Q[2 * qsz + oth] = qt;
+    const size_t o = (size_t)(p * s.n_r + n) * s.n_lm + idx;
+    Q[o] = q;
+    Q[qsz + o] = qr;
+    Q[2 * qsz + o] = qt;
     if (Q32 != nullptr) {
-      const float fq = to_f32(q), fr = to_f32(qr), ft = to_f32(qt);
-      Q32[own] = fq;
-      Q32[oth] = fq;
-      Q32[qsz + own] = fr;
-      Q32[qsz + oth] = fr;
-      Q32[2 * qsz + own] = ft;
-      Q32[2 * qsz + oth] = ft;
+      Q32[o] = to_f32(q);
+      Q32[qsz + o] = to_f32(qr);
+      Q32[2 * qsz + o] = to_f32(qt);
     }
   }
 }
 
+// Combination of the two patches' moments (§4: the potential of a patch is the
+// sum of the potentials of both patches' moments, each taken in the target
+// patch's angles).  Y_i(M v) = sum_j D^l_ij Y_j(v) turns the other patch's
+// moments into own-frame ones of the same degree:
+//   Atot[p][n][j] = A[p][n][j] + sum_i D^l_ij A[1-p][n][i],  i, j of degree l.
+// The scans and the synthesis are linear and act on each degree alone, so this
+// gives the same potential as summing four separate ones.  One block per
+// radius; T is the type of the products (float64, or float32 with a float64
+// sum onto the own-patch moment).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_rotate_moments(int n_r, int n_lm, const T *__restrict__ rot, const double *__restrict__ A,
+                 double *__restrict__ Atot) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *a = reinterpret_cast<T *>(smraw);   // [2][n_lm]
+  const int n = blockIdx.x;
+  for (int e = threadIdx.x; e < 2 * n_lm; e += blockDim.x) {
+    const int p = e / n_lm, j = e % n_lm;
+    a[e] = (T)A[((size_t)p * n_r + n) * n_lm + j];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * n_lm; e += blockDim.x) {
+    const int p = e / n_lm, j = e % n_lm;
+    const int l = mode_degree(j);
+    const int w = 2 * l + 1, jj = j - l * l;
+    const T *D = rot + (size_t)l * (4 * l * l - 1) / 3 + jj;
+    const T *x = a + (1 - p) * n_lm + l * l;
+    T acc = 0;
+    for (int i = 0; i < w; ++i) acc = fma(D[(size_t)i * w], x[i], acc);
+    const size_t o = ((size_t)p * n_r + n) * n_lm + j;
+    Atot[o] = A[o] + (double)acc;
+  }
+}
+
 }  // namespace
+
+cudaError_t rotate_moments(yy_grid *g, bool fp64, cudaStream_t st) {
+  const size_t smem = 2 * (size_t)g->n_lm * (fp64 ? sizeof(double) : sizeof(float));
+  if (smem > 48 * 1024) {
+    const cudaError_t e = fp64 ? cudaFuncSetAttribute(k_rotate_moments<double>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                               : cudaFuncSetAttribute(k_rotate_moments<float>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (fp64)
+    k_rotate_moments<double><<<g->n_r, 256, smem, st>>>(g->n_r, g->n_lm, g->rot, g->A, g->Atot);
+  else
+    k_rotate_moments<float><<<g->n_r, 256, smem, st>>>(g->n_r, g->n_lm, g->rot32, g->A, g->Atot);
+  g->launches++;
+  return cudaGetLastError();
+}
 
 void scan_geometry(const yy_grid *g, int *nc, int *ch) {
   const int wpp = (g->n_lm + 31) / 32;
@@ -158,9 +201,9 @@ cudaError_t radial_scan(yy_grid *g, bool want_f32, cudaStream_t st) {
   scan_geometry(g, &s.nc, &s.ch);
   const int warps = 2 * s.wpp * s.nc;
   const int blocks = (warps * 32 + 127) / 128;
-  k_scan_maps<<<blocks, 128, 0, st>>>(s, g->A, g->scan, (double4 *)g->scan_maps);
+  k_scan_maps<<<blocks, 128, 0, st>>>(s, g->Atot, g->scan, (double4 *)g->scan_maps);
   g->launches++;
-  k_scan_apply<<<blocks, 128, 0, st>>>(s, g->A, g->scan, (const double4 *)g->scan_maps, g->cin, g->Q,
+  k_scan_apply<<<blocks, 128, 0, st>>>(s, g->Atot, g->scan, (const double4 *)g->scan_maps, g->cin, g->Q,
                                        want_f32 ? g->Q32 : nullptr);
   g->launches++;
   return cudaGetLastError();

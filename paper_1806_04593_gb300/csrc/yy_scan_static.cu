@@ -107,8 +107,7 @@ k_radial_scan_static(int n_r, int lmax, int n_lm, double G, const double *__rest
   double y = __shfl_down_sync(0xffffffffu, be, 1);
   if (lane == 31) y = 0.0;
   const double f_phi = -G * kFourPi / (2.0 * l + 1.0);
-  const size_t row2 = 2 * (size_t)n_lm;
-  const size_t qsz = (size_t)2 * n_r * row2;
+  const size_t qsz = (size_t)2 * n_r * n_lm;
   for (int n = n1 - 1; n >= n0; --n) {
     zone_factors(n, l, n_r, r, a, b, e, f);
     const double an = (n + 1 < n_r) ? Ap[(size_t)(n + 1) * n_lm] : 0.0;
@@ -118,14 +117,10 @@ k_radial_scan_static(int n_r, int lmax, int n_lm, double G, const double *__rest
     const double q = f_phi * (cn + y);
     const double qr = -f_phi * (-(l + 1.0) * cn + l * y) * inv_r;
     const double qt = -q * inv_r;
-    const size_t own = (size_t)(p * n_r + n) * row2 + idx;
-    const size_t oth = (size_t)((1 - p) * n_r + n) * row2 + n_lm + idx;
-    Q[own] = q;
-    Q[oth] = q;
-    Q[qsz + own] = qr;
-    Q[qsz + oth] = qr;
-    Q[2 * qsz + own] = qt;
-    Q[2 * qsz + oth] = qt;
+    const size_t o = (size_t)(p * n_r + n) * n_lm + idx;
+    Q[o] = q;
+    Q[qsz + o] = qr;
+    Q[2 * qsz + o] = qt;
   }
 }
 

@@ -6,10 +6,11 @@
 //  k_tbar           K_lm T_j^(lm), T of Eq. tlm, by Gauss-Legendre quadrature
 //                   of the normalised Legendre functions
 //  k_analysis_table w_jk K_lm T_j^(lm) {C_k^(m), S_k^(m)} (§2 closed forms for C, S)
-//  k_synth_tables   K_lm P_l^m {cos, sin}(m phi) at the own cell centre and at
-//                   the centre expressed in the other patch's angles
-//                   (Eqs. trafotheta / trafophi), plus the angular derivatives
-//                   rotated into the target patch's spherical basis
+//  k_synth_tables   K_lm P_l^m {cos, sin}(m phi) at the cell centre and its
+//                   angular derivatives in the patch's own spherical basis
+//  k_rotation_table per degree l, the matrix D^l that expresses a harmonic
+//                   taken in the other patch's angles (Eqs. trafotheta /
+//                   trafophi) through the own-frame harmonics of the same l
 //  k_scan_coeffs    per-zone factors of the scaled radial recurrences
 //                   (Eqs. rin / rout, phiin / phiout)
 #include <math.h>
@@ -283,77 +284,97 @@ struct SynthGeom {
 __global__ void k_synth_tables(SynthGeom G, double *__restrict__ ysyn, double *__restrict__ ysyn_t,
                                double *__restrict__ ysyn_p) {
   extern __shared__ double sm[];
-  const int ntri = (G.lmax + 1) * (G.lmax + 2) / 2;
-  double *Pown = sm;
-  double *Poth = sm + ntri;
+  double *P = sm;
   const int cell = blockIdx.x;
   const int j = cell / G.n_phi, k = cell % G.n_phi;
   const double th = G.th0 + G.dth * (j + 0.5);
   const double ph = G.ph0 + G.dph * (k + 0.5);
-  // own-frame point and its Cartesian direction
-  const double st = sin(th), ct = cos(th), sp = sin(ph), cp = cos(ph);
-  const double vx = st * cp, vy = st * sp, vz = ct;
-  // the same direction in the other patch's frame: (x, y, z) -> (-x, z, y)
-  const double ox = -vx, oy = vz, oz = vy;
-  const double so = sqrt(ox * ox + oy * oy);
-  const double co = oz;
-  const double pho = atan2(oy, ox);
-  // rotation of the other frame's (e_theta, e_phi) into the target basis
-  const double spo = sin(pho), cpo = cos(pho);
-  const double et_o[3] = {co * cpo, co * spo, -so};      // other-frame components
-  const double ep_o[3] = {-spo, cpo, 0.0};
-  const double et_t[3] = {-et_o[0], et_o[2], et_o[1]};   // mapped to own frame
-  const double ep_t[3] = {-ep_o[0], ep_o[2], ep_o[1]};
-  const double e_th[3] = {ct * cp, ct * sp, -st};
-  const double e_ph[3] = {-sp, cp, 0.0};
-  const double Rtt = e_th[0] * et_t[0] + e_th[1] * et_t[1] + e_th[2] * et_t[2];
-  const double Rtp = e_th[0] * ep_t[0] + e_th[1] * ep_t[1] + e_th[2] * ep_t[2];
-  const double Rpt = e_ph[0] * et_t[0] + e_ph[1] * et_t[1] + e_ph[2] * et_t[2];
-  const double Rpp = e_ph[0] * ep_t[0] + e_ph[1] * ep_t[1] + e_ph[2] * ep_t[2];
-
-  for (int m = threadIdx.x; m <= G.lmax; m += blockDim.x) {
-    pbar_column(m, G.lmax, ct, st, [&](int l, double p) { Pown[tri(l, m)] = p; });
-    pbar_column(m, G.lmax, co, so, [&](int l, double p) { Poth[tri(l, m)] = p; });
-  }
+  const double st = sin(th), ct = cos(th);
+  for (int m = threadIdx.x; m <= G.lmax; m += blockDim.x)
+    pbar_column(m, G.lmax, ct, st, [&](int l, double p) { P[tri(l, m)] = p; });
   __syncthreads();
 
-  const size_t row = (size_t)cell * 2 * G.n_lm;
+  const size_t row = (size_t)cell * G.n_lm;
   for (int m = threadIdx.x; m <= G.lmax; m += blockDim.x) {
     const double cm = cos(m * ph), sm_ = sin(m * ph);
-    const double cmo = cos(m * pho), smo = sin(m * pho);
     for (int l = m; l <= G.lmax; ++l) {
-      const double p = Pown[tri(l, m)], po = Poth[tri(l, m)];
-      const double dp = dpbar(Pown, l, m, G.lmax), dpo = dpbar(Poth, l, m, G.lmax);
-      const double qs = mpbar_over_sin(Pown, l, m, G.lmax);
-      const double qso = mpbar_over_sin(Poth, l, m, G.lmax);
+      const double p = P[tri(l, m)];
+      const double dp = dpbar(P, l, m, G.lmax);
+      const double qs = mpbar_over_sin(P, l, m, G.lmax);
       if (m == 0) {
         const int idx = l * l;
         ysyn[row + idx] = p;
-        ysyn[row + G.n_lm + idx] = po;
         ysyn_t[row + idx] = dp;
-        ysyn_t[row + G.n_lm + idx] = Rtt * dpo;
         ysyn_p[row + idx] = 0.0;
-        ysyn_p[row + G.n_lm + idx] = Rpt * dpo;
       } else {
         const int ic = l * l + 2 * m - 1, is = l * l + 2 * m;
         ysyn[row + ic] = p * cm;
         ysyn[row + is] = p * sm_;
-        ysyn[row + G.n_lm + ic] = po * cmo;
-        ysyn[row + G.n_lm + is] = po * smo;
         // d/dtheta, and (1/sin) d/dphi of cos(m phi) -> -m sin, sin(m phi) -> m cos
         ysyn_t[row + ic] = dp * cm;
         ysyn_t[row + is] = dp * sm_;
         ysyn_p[row + ic] = -qs * sm_;
         ysyn_p[row + is] = qs * cm;
-        const double gt_c = dpo * cmo, gt_s = dpo * smo;     // other frame, theta'
-        const double gp_c = -qso * smo, gp_s = qso * cmo;    // other frame, phi'
-        ysyn_t[row + G.n_lm + ic] = Rtt * gt_c + Rtp * gp_c;
-        ysyn_t[row + G.n_lm + is] = Rtt * gt_s + Rtp * gp_s;
-        ysyn_p[row + G.n_lm + ic] = Rpt * gt_c + Rpp * gp_c;
-        ysyn_p[row + G.n_lm + is] = Rpt * gt_s + Rpp * gp_s;
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// rotation of the other patch's harmonics, one block per degree l
+// ---------------------------------------------------------------------------
+//
+// A point with own-frame Cartesian direction v has direction M v in the other
+// patch's frame, M (x, y, z) = (-x, z, y) (Eqs. trafotheta / trafophi); M is a
+// rotation (by pi about (0, 1, 1) / sqrt 2) and its own inverse, so the same
+// matrices serve both patches.  The real harmonics Y_i = K_lm P_l^m {cos, sin}
+// are orthonormal on the sphere and a rotation keeps the degree, hence
+//   Y_i(M v) = sum_j D^l_ij Y_j(v),   D^l_ij = int Y_i(M v) Y_j(v) dOmega,
+// i, j over the 2l+1 modes of degree l in the order m = 0, (1, c), (1, s), ...
+// The integrand is a polynomial of degree 2l on the sphere: Gauss-Legendre in
+// cos(theta) with at least lmax + 1 nodes times 2 lmax + 2 equispaced azimuths
+// integrates it to rounding.  Storage: D^l row-major at offset l (4l^2 - 1) / 3.
+__global__ void k_rotation_table(int lmax, const double *__restrict__ gx, const double *__restrict__ gw,
+                                 int n_mu, double *__restrict__ rot) {
+  const int l = blockIdx.x;
+  const int n = 2 * l + 1;
+  const int n_az = 2 * lmax + 2;
+  __shared__ double y_own[2 * YY_LMAX_CAP + 1], y_oth[2 * YY_LMAX_CAP + 1];
+  constexpr int kPer = (2 * YY_LMAX_CAP + 1) * (2 * YY_LMAX_CAP + 1) / 128 + 1;   // blockDim.x = 128
+  double acc[kPer];
+  for (int q = 0; q < kPer; ++q) acc[q] = 0.0;
+  for (int pt = 0; pt < n_mu * n_az; ++pt) {
+    const int a = pt / n_az, b = pt % n_az;
+    const double mu = 2.0 * gx[a] - 1.0;                  // nodes on [0, 1] mapped to [-1, 1]
+    const double wq = 2.0 * gw[a] * (2.0 * kPi / n_az);
+    const double ph = 2.0 * kPi * (b + 0.5) / n_az;
+    const double s = sqrt(fmax(0.0, 1.0 - mu * mu));
+    const double vx = s * cos(ph), vy = s * sin(ph), vz = mu;
+    const double ox = -vx, oy = vz, oz = vy;
+    const double so = sqrt(ox * ox + oy * oy);
+    const double pho = atan2(oy, ox);
+    __syncthreads();
+    for (int m = threadIdx.x; m <= l; m += blockDim.x) {
+      double po = 0.0, px = 0.0;
+      pbar_column(m, l, mu, s, [&](int ll, double v) { if (ll == l) po = v; });
+      pbar_column(m, l, oz, so, [&](int ll, double v) { if (ll == l) px = v; });
+      if (m == 0) {
+        y_own[0] = po;
+        y_oth[0] = px;
+      } else {
+        y_own[2 * m - 1] = po * cos(m * ph);
+        y_own[2 * m] = po * sin(m * ph);
+        y_oth[2 * m - 1] = px * cos(m * pho);
+        y_oth[2 * m] = px * sin(m * pho);
+      }
+    }
+    __syncthreads();
+    int q = 0;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x, ++q) acc[q] += wq * y_oth[e / n] * y_own[e % n];
+  }
+  double *D = rot + (size_t)l * (4 * l * l - 1) / 3;
+  int q = 0;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x, ++q) D[e] = acc[q];
 }
 
 // ---------------------------------------------------------------------------
@@ -402,6 +423,11 @@ __global__ void k_scan_coeffs(int n_r, int lmax, double G, const double *__restr
   o[7] = -fq * inv_r;               // g_angle:   G 4pi/(2l+1) (c + d) / r
 }
 
+__global__ void k_round_f32(int n, const double *__restrict__ src, float *__restrict__ dst) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) dst[e] = (float)src[e];
+}
+
 }  // namespace
 
 cudaError_t build_tables(yy_grid *g, const double *gl_host, int n_gl) {
@@ -445,11 +471,17 @@ cudaError_t build_tables(yy_grid *g, const double *gl_host, int n_gl) {
   sg.n_phi = g->n_phi;
   sg.lmax = g->lmax;
   sg.n_lm = g->n_lm;
-  const size_t smem = 2 * (size_t)(g->lmax + 1) * (g->lmax + 2) / 2 * sizeof(double);
+  const size_t smem = (size_t)(g->lmax + 1) * (g->lmax + 2) / 2 * sizeof(double);
   if ((err = cudaFuncSetAttribute(k_synth_tables, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
     return err;
   k_synth_tables<<<g->n_ang, 96, smem>>>(sg, g->ysyn, g->ysyn_t, g->ysyn_p);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+
+  k_rotation_table<<<g->lmax + 1, 128>>>(g->lmax, gx, gw, n_gl, g->rot);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  const int n_rot = rotation_table_size(g->lmax);
+  k_round_f32<<<(n_rot + 255) / 256, 256>>>(n_rot, g->rot, g->rot32);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
 
   const int n_sc = g->n_r * (g->lmax + 1);

@@ -543,7 +543,7 @@ struct PackArgs {
   int zero_row;          // source row left out (-1: none)
   const float *dot_vec;  // optional: dot_out[row] = sum_k x[k] dot_vec[k]
   double *dot_out;
-  double add_factor;     // optional: row_add[row] = add_factor (x[zero_k0] + x[zero_k1])
+  double add_factor;     // optional: row_add[row] = add_factor x[zero_k0]
   float *row_add;
   double *mean_out;      // optional: pack x - mean, store the mean used
   double *scale_out;     // [rows_pad] power of two undoing the scaling (float64)
@@ -668,7 +668,7 @@ __global__ void __launch_bounds__(256) k_pack_rows(PackBatch batch) {
     if (p.mean_out) p.mean_out[row] = (double)mean;
     if (p.dot_vec && row < p.rows) p.dot_out[row] = valid ? red[1][0] : 0.0;
     if (p.row_add && row < p.rows)
-      p.row_add[row] = (valid && p.zero_k0 >= 0) ? (float)(p.add_factor * (src[p.zero_k0] + src[p.zero_k1])) : 0.0f;
+      p.row_add[row] = (valid && p.zero_k0 >= 0) ? (float)(p.add_factor * src[p.zero_k0]) : 0.0f;
   }
   if (p.cache) __syncthreads();
   for (int k0 = threadIdx.x * 8; k0 < p.k_pad; k0 += blockDim.x * 8) {
@@ -851,7 +851,7 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
   t->an_rows_a = round_up(M, kBM * t->cluster);
   t->an_kpad = round_up(g->n_ang, kPadK);
   t->an_rows_b = round_up(g->n_lm, F::kBN);
-  t->sy_kpad = round_up(2 * g->n_lm, kPadK);
+  t->sy_kpad = round_up(g->n_lm, kPadK);
   t->sy_rows_b = round_up(g->n_ang, F::kBN);
   cudaError_t e = cudaSuccess;
   auto A = [&](void **ptr, size_t bytes) {
@@ -913,11 +913,11 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
     PackArgs &q = bs.job[c];
     q.rows = g->n_ang;
     q.rows_pad = t->sy_rows_b;
-    q.K = 2 * g->n_lm;
+    q.K = g->n_lm;
     q.k_pad = t->sy_kpad;
     q.src0 = q.src1 = tabs[c];
     q.split_row = g->n_ang;
-    q.ld = 2 * g->n_lm;
+    q.ld = g->n_lm;
     q.zero_k0 = q.zero_k1 = -1;
     q.zero_row = -1;
     q.scale_out = t->sy_cs[c];
@@ -1058,21 +1058,21 @@ static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, 
 template <class F>
 static cudaError_t pack_coefficients_form(yy_grid *g, yy_tc_tables *t, cudaStream_t s) {
   const int M = 2 * g->n_r;
-  const size_t qsz = (size_t)M * 2 * g->n_lm;
-  // Phi and g_r: the monopole pair (columns 0 and n_lm) is added in the epilogue
+  const size_t qsz = (size_t)M * g->n_lm;
+  // Phi and g_r: the monopole (column 0) is added in the epilogue
   const double add[3] = {kY00, kY00, 0.0};
   PackBatch b = {};
   for (int c = 0; c < 3; ++c) {
     PackArgs &p = b.job[c];
     p.rows = M;
     p.rows_pad = t->an_rows_a;
-    p.K = 2 * g->n_lm;
+    p.K = g->n_lm;
     p.k_pad = t->sy_kpad;
     p.src0 = p.src1 = g->Q + c * qsz;
     p.split_row = M;
-    p.ld = 2 * g->n_lm;
+    p.ld = g->n_lm;
     p.zero_k0 = 0;
-    p.zero_k1 = g->n_lm;
+    p.zero_k1 = -1;
     p.zero_row = -1;
     p.add_factor = add[c];
     p.row_add = t->sy_add[c];

@@ -40,6 +40,8 @@ YY_TABLE_SYNTH_T = 4
 YY_TABLE_SYNTH_P = 5
 YY_TABLE_MOMENTS = 6
 YY_TABLE_COEFF = 7
+YY_TABLE_ROTATION = 8
+YY_TABLE_MOMENTS_TOTAL = 9
 
 _lib = None
 

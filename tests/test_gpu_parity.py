@@ -77,8 +77,8 @@ def test_polar_and_analysis_tables(yy, oracle_grid, name):
 
 
 @pytest.mark.parametrize("name", ["tiny", "mid"])
-def test_synthesis_tables_same_and_cross(yy, oracle_grid, name):
-    from oracle import assoc_legendre, other_patch_angles
+def test_synthesis_tables_own_frame(yy, oracle_grid, name):
+    from oracle import assoc_legendre
     spec = inputs.GRIDS[name]()
     g = _grid(yy, spec)
     og = oracle_grid(spec)
@@ -86,16 +86,52 @@ def test_synthesis_tables_same_and_cross(yy, oracle_grid, name):
     K = K_lm(og.N)
     modes = mode_index(L)
     n_lm = len(modes)
-    ys = g.table(yy.YY_TABLE_SYNTH).reshape(spec.n_ang, 2 * n_lm)
+    ys = g.table(yy.YY_TABLE_SYNTH).reshape(spec.n_ang, n_lm)
     th, ph = og.target_theta, og.target_phi
+    P = assoc_legendre(L, np.cos(th), np.sin(th))
+    for idx, (l, m, kind) in enumerate(modes):
+        f = np.cos(m * ph) if kind == "c" else np.sin(m * ph)
+        ref = K[l, m] * P[l, m] * f
+        assert np.abs(ys[:, idx] - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max()), (l, m, kind)
+
+
+def _harmonics(L, K, modes, th, ph):
+    from oracle import assoc_legendre
+    P = assoc_legendre(L, np.cos(th), np.sin(th))
+    out = np.empty((len(modes),) + np.shape(th))
+    for idx, (l, m, kind) in enumerate(modes):
+        out[idx] = K[l, m] * P[l, m] * (np.cos(m * ph) if kind == "c" else np.sin(m * ph))
+    return out
+
+
+@pytest.mark.parametrize("name", ["tiny", "mid"])
+def test_rotation_table_maps_other_frame_harmonics(yy, oracle_grid, name):
+    """Y_i(angles in the other patch) = sum_j D^l_ij Y_j(own angles) at random
+    points (oracle harmonics, oracle angle transform); D^l orthogonal and its
+    own inverse (the Yin-Yang map is an involution)."""
+    from oracle import other_patch_angles
+    spec = inputs.GRIDS[name]()
+    g = _grid(yy, spec)
+    og = oracle_grid(spec)
+    L = spec.lmax
+    K = K_lm(og.N)
+    modes = mode_index(L)
+    rot = g.table(yy.YY_TABLE_ROTATION)
+    assert rot.size == sum((2 * l + 1) ** 2 for l in range(L + 1))
+    rng = np.random.default_rng(11)
+    th = np.arccos(rng.uniform(-1.0, 1.0, 400))
+    ph = rng.uniform(-math.pi, math.pi, 400)
     tx, px = other_patch_angles(th, ph)
-    for half, (t, p) in enumerate(((th, ph), (tx, px))):
-        P = assoc_legendre(L, np.cos(t), np.sin(t))
-        for idx, (l, m, kind) in enumerate(modes):
-            f = np.cos(m * p) if kind == "c" else np.sin(m * p)
-            ref = K[l, m] * P[l, m] * f
-            got = ys[:, half * n_lm + idx]
-            assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max()), (half, l, m, kind)
+    y_own = _harmonics(L, K, modes, th, ph)
+    y_oth = _harmonics(L, K, modes, tx, px)
+    for l in range(L + 1):
+        w = 2 * l + 1
+        off = l * (4 * l * l - 1) // 3
+        D = rot[off:off + w * w].reshape(w, w)
+        sl = slice(l * l, l * l + w)
+        assert np.abs(D @ y_own[sl] - y_oth[sl]).max() <= 1e-12, l
+        assert np.abs(D @ D.T - np.eye(w)).max() <= 1e-13, l
+        assert np.abs(D @ D - np.eye(w)).max() <= 1e-13, l
 
 
 # ---------------------------------------------------------------------------

@@ -28,19 +28,19 @@ def test_static_scan_matches_solve_coefficients_twice():
     ry, rg = inputs.density_for(spec)
     grid.solve(torch.from_numpy(ry).to(dev), torch.from_numpy(rg).to(dev))
     torch.cuda.synchronize()
-    moments = grid.table(yy.YY_TABLE_MOMENTS)          # existing entry point's intermediate
-    expected = grid.table(yy.YY_TABLE_COEFF)           # existing entry point's output
+    moments = grid.table(yy.YY_TABLE_MOMENTS_TOTAL)    # existing entry point's scan input
+    expected = grid.table(yy.YY_TABLE_COEFF)           # existing entry point's scan output
     n_lm = grid.n_lm
     r_dev = torch.from_numpy(np.ascontiguousarray(spec.r_edges)).to(dev)
     m_dev = torch.from_numpy(moments).to(dev)
     outs = []
     for _ in range(2):
-        coeff = torch.full((3, 2 * spec.n_r, 2 * n_lm), float("nan"), dtype=torch.float64, device=dev)
+        coeff = torch.full((3, 2 * spec.n_r, n_lm), float("nan"), dtype=torch.float64, device=dev)
         st = yy.yy_radial_scan_static(r_dev, spec.n_r, spec.lmax, spec.G, m_dev, coeff,
                                       torch.cuda.current_stream())
         assert st == yy.YY_OK, yy.yy_status_string(st)
         torch.cuda.synchronize()
-        got = coeff[0].cpu().numpy().reshape(-1)
+        got = coeff.cpu().numpy().reshape(-1)
         err = np.abs(got - expected).max() / np.abs(expected).max()
         assert err <= 1e-12, err
         outs.append(coeff.cpu().numpy())
