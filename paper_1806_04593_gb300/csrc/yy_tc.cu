@@ -52,6 +52,7 @@ enum { KIND_F16 = 0, KIND_BF16 = 1, KIND_TF32 = 2 };
 struct FormFP16x2 {
   typedef __half elem;
   static constexpr int kKind = KIND_F16, kElem = 2, kPA = 2, kPB = 2, kPairs = 3, kBN = 256, kStages = 4;
+  static constexpr int kPairStages = 6;
   __host__ __device__ static constexpr int pa(int i) { return i == 2 ? 1 : 0; }
   __host__ __device__ static constexpr int pb(int i) { return i == 1 ? 1 : 0; }
 };
@@ -59,6 +60,7 @@ struct FormFP16x2 {
 struct FormBF16x3 {
   typedef __nv_bfloat16 elem;
   static constexpr int kKind = KIND_BF16, kElem = 2, kPA = 3, kPB = 3, kPairs = 6, kBN = 128, kStages = 4;
+  static constexpr int kPairStages = 4;
   // (0,0) (0,1) (1,0) (0,2) (2,0) (1,1)
   __host__ __device__ static constexpr int pa(int i) { return i == 2 ? 1 : (i == 4 ? 2 : (i == 5 ? 1 : 0)); }
   __host__ __device__ static constexpr int pb(int i) { return i == 1 ? 1 : (i == 3 ? 2 : (i == 5 ? 1 : 0)); }
@@ -67,6 +69,7 @@ struct FormBF16x3 {
 struct FormTF32 {
   typedef float elem;
   static constexpr int kKind = KIND_TF32, kElem = 4, kPA = 1, kPB = 1, kPairs = 1, kBN = 256, kStages = 8;
+  static constexpr int kPairStages = 12;
   __host__ __device__ static constexpr int pa(int) { return 0; }
   __host__ __device__ static constexpr int pb(int) { return 0; }
 };
@@ -89,6 +92,19 @@ constexpr int kStgBytes = kEpiWarps * 32 * kEpiCols * 4;   // one 32 x 16 fp32 f
 template <class F>
 constexpr int smem_bytes() {
   return F::kStages * stage_bytes<F>() + kStgBytes + 1024 /*align*/ + 256 /*barriers*/;
+}
+
+// CTA-pair synthesis kernel: per CTA 128 rows of A and up to 128 rows of B
+// (half of the pair's N) in every stage.
+constexpr int kPairRows = 128;
+constexpr int kPairTmemCols = 512;   // two accumulators of up to 256 columns
+template <class F>
+constexpr int pair_stage_bytes() {
+  return (F::kPA + F::kPB) * kPairRows * kRowBytes;
+}
+template <class F>
+constexpr int pair_smem_bytes() {
+  return F::kPairStages * pair_stage_bytes<F>() + 1024 /*align*/ + 256 /*barriers*/;
 }
 
 // ---------------------------------------------------------------------------
@@ -259,6 +275,106 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---- CTA-pair (cta_group::2) forms -------------------------------------
+//
+// Two CTAs of a cluster share one MMA of M = 256: the even CTA issues it; each
+// CTA holds 128 rows of A and half the columns of B in its own shared memory
+// and 128 lanes of the accumulator in its own TMEM.
+
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+// Bounded wait with cluster-scope acquire (arrivals may come from the peer).
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity, int *err) {
+  const uint32_t addr = smem_u32(bar);
+  for (int i = 0; i < 256; ++i)
+    if (mbar_try_wait_cluster(addr, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (true) {
+    if (mbar_try_wait_cluster(addr, parity)) return true;
+    if (globaltimer() - t0 > 2000000000ull) {
+      atomicOr(err, YY_DEVERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+// Arrive on a barrier given by its shared::cluster address (own or peer CTA).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+// TMA load into this CTA's shared memory that completes on a barrier of
+// either CTA of the pair (cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(const CUtensorMap *map, uint32_t dst, uint32_t bar_cluster, int x,
+                                                 int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(bar_cluster), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t base, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols) : "memory");
+}
+
+template <class F>
+__device__ __forceinline__ void mma_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (F::kKind == KIND_TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
+
+// Arrive on the barrier at this offset in both CTAs of the pair once the
+// MMAs issued before it have completed.
+__device__ __forceinline__ void mma_commit_pair(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"((uint16_t)3)
+      : "memory");
+}
+
+// Instruction descriptor of the pair MMA: M = 256, N = n (multiple of 16, <= 256).
+template <class F>
+__host__ __device__ constexpr uint32_t instr_desc_pair(int n) {
+  return (1u << 4) | ((uint32_t)F::kKind << 7) | ((uint32_t)F::kKind << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(256 >> 4) << 24);
 }
 
 // fp32 <-> float64 with integer operations only: exact widening, and
@@ -518,6 +634,193 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem_base, 2 * BN);
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// the synthesis kernel: CTA pairs, M = 256 cells x N = bn coefficient rows
+// ---------------------------------------------------------------------------
+//
+// out[row][cell] = (sum_k Y[cell][k] Q[row][k]) cell_scale[cell] row_scale[row] + row_add[row]
+// with Y the packed table (operand A, one row per cell) and Q the packed
+// coefficients (operand B).  Clusters of two CTAs; pair p handles tiles
+// p, p + #pairs, ... (coefficient-row tiles fastest, so the pairs working at
+// the same time share table tiles in L2).  Per stage each CTA loads its 128
+// table rows and its bn / 2 coefficient rows; both CTAs' loads complete on
+// the even CTA's "full" barrier, whose thread 32 issues the M = 256 MMAs and
+// releases each stage in both CTAs with a multicast commit.  Each CTA's TMEM
+// holds its 128 cells x bn accumulator (double-buffered), so a lane of an
+// epilogue warp owns one cell and a 16-column TMEM load gives it 16 rows:
+// every store is 32 consecutive cells of one output row.  The epilogue warps
+// of both CTAs release a buffer on the even CTA's "tempty" barrier.
+struct PairArgs {
+  int cells, cell_tiles;        // valid cells; tiles of 256 cells
+  int rows, row_tiles, bn;      // valid coefficient rows; tiles of bn rows (multiple of 16, <= 256)
+  int kb_total;                 // K blocks (kRowBytes per row)
+  int a_rows, b_rows;           // rows of one piece in the stacked A (table) / B (coefficient) operands
+  double *out0, *out1;          // row r < out_split -> out0 + r ldo, else out1 + (r - out_split) ldo
+  int out_split;
+  long long ldo;
+  const float *cell_scale, *row_scale, *row_add;
+  int *err;
+};
+
+template <class F>
+__global__ void __launch_bounds__(kThreads, 1)
+k_tc_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, PairArgs a) {
+  constexpr int S = F::kPairStages;
+  constexpr int SLOT = kPairRows * kRowBytes;
+  constexpr int STAGE = pair_stage_bytes<F>();
+  constexpr int KSTEP_BYTES = 32;
+  constexpr int KSTEPS = kRowBytes / KSTEP_BYTES;
+  constexpr int BK = kRowBytes / F::kElem;
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *full = (uint64_t *)(smem + S * STAGE);
+  uint64_t *empty = full + S;
+  uint64_t *tfull = empty + S;      // [2]
+  uint64_t *tempty = tfull + 2;     // [2], counted in the even CTA
+  uint32_t *tmem_slot = (uint32_t *)(tempty + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rank = (int)cluster_rank();
+  const int pair = (int)blockIdx.x >> 1, n_pairs = (int)gridDim.x >> 1;
+  const int total = a.cell_tiles * a.row_tiles;
+  const int bh = a.bn >> 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 2 * kEpiWarps);
+    }
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc_pair(tmem_slot, kPairTmemCols);
+    tc_fence_before();
+  }
+  __syncthreads();
+  cluster_sync();   // both CTAs' barriers and TMEM exist before any remote use
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const uint32_t tx_bytes = 2u * (uint32_t)(F::kPA * kPairRows + F::kPB * bh) * kRowBytes;
+      int gk = 0;
+      bool ok = true;
+      for (int t = pair; t < total && ok; t += n_pairs) {
+        const int rt = t % a.row_tiles, ct = t / a.row_tiles;
+        const int arow = (2 * ct + rank) * kPairRows;
+        const int brow = rt * a.bn + rank * bh;
+        for (int i = 0; i < a.kb_total; ++i, ++gk) {
+          const int s = gk % S;
+          if (gk >= S && !mbar_wait(&empty[s], ((gk / S) & 1) ^ 1, a.err)) {
+            ok = false;
+            break;
+          }
+          if (rank == 0) mbar_expect_tx(&full[s], tx_bytes);
+          const uint32_t fbar = mapa_rank(smem_u32(&full[s]), 0);
+          const uint32_t base = smem_u32(smem + s * STAGE);
+          const int kx = i * BK;
+#pragma unroll
+          for (int p = 0; p < F::kPA; ++p) tma_load_2d_pair(&tmA, base + p * SLOT, fbar, kx, p * a.a_rows + arow);
+#pragma unroll
+          for (int p = 0; p < F::kPB; ++p)
+            tma_load_2d_pair(&tmB, base + (F::kPA + p) * SLOT, fbar, kx, p * a.b_rows + brow);
+        }
+      }
+      // the last uses of every stage must be complete before this CTA leaves
+      if (ok)
+        for (int i = max(0, gk - S); i < gk; ++i)
+          if (!mbar_wait(&empty[i % S], (i / S) & 1, a.err)) break;
+    }
+  } else if (warp == 1) {
+    if (rank == 0 && lane == 0) {
+      const uint32_t idesc = instr_desc_pair<F>(a.bn);
+      int gk = 0, it = 0;
+      bool ok = true;
+      for (int t = pair; t < total && ok; t += n_pairs, ++it) {
+        const int b = it & 1;
+        if (it >= 2) {
+          if (!mbar_wait_cluster(&tempty[b], ((it >> 1) & 1) ^ 1, a.err)) break;
+          tc_fence_after();
+        }
+        const uint32_t dacc = tmem_base + (uint32_t)(b * 256);
+        for (int i = 0; i < a.kb_total; ++i, ++gk) {
+          const int s = gk % S;
+          if (!mbar_wait_cluster(&full[s], (gk / S) & 1, a.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + s * STAGE);
+          const uint32_t sb = sa + F::kPA * SLOT;
+#pragma unroll
+          for (int q = 0; q < F::kPairs; ++q) {
+#pragma unroll
+            for (int kk = 0; kk < KSTEPS; ++kk) {
+              const uint64_t da = smem_desc(sa + F::pa(q) * SLOT + kk * KSTEP_BYTES);
+              const uint64_t db = smem_desc(sb + F::pb(q) * SLOT + kk * KSTEP_BYTES);
+              mma_pair<F>(dacc, da, db, idesc, (i | q | kk) != 0 ? 1u : 0u);
+            }
+          }
+          mma_commit_pair(&empty[s]);
+        }
+        if (ok) mma_commit_pair(&tfull[b]);
+      }
+    }
+  } else {
+    const int quarter = warp & 3;
+    const int sub = (warp - 2) >> 2;    // 0..3 within the lane quarter
+    const uint32_t tempty_even = mapa_rank(smem_u32(&tempty[0]), 0);
+    int it = 0;
+    for (int t = pair; t < total; t += n_pairs, ++it) {
+      const int b = it & 1;
+      if (!mbar_wait_cluster(&tfull[b], (it >> 1) & 1, a.err)) break;
+      tc_fence_after();
+      const int rt = t % a.row_tiles, ct = t / a.row_tiles;
+      const int cell = (2 * ct + rank) * kPairRows + quarter * 32 + lane;
+      const bool cell_ok = cell < a.cells;
+      const float cs = cell_ok ? a.cell_scale[cell] : 0.0f;
+#pragma unroll 1
+      for (int c0 = kEpiCols * sub; c0 < a.bn; c0 += kEpiCols * 4) {
+        uint32_t v[16];
+        tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + c0), v);
+        const int row0 = rt * a.bn + c0;
+        float rsl = 0.0f, ral = 0.0f;
+        if (lane < kEpiCols && row0 + lane < a.rows) {
+          rsl = a.row_scale[row0 + lane];
+          ral = a.row_add[row0 + lane];
+        }
+#pragma unroll
+        for (int j = 0; j < kEpiCols; ++j) {
+          const float rs = __shfl_sync(0xffffffffu, rsl, j);
+          const float ra = __shfl_sync(0xffffffffu, ral, j);
+          const int row = row0 + j;
+          if (row < a.rows && cell_ok) {
+            double *orow = (row < a.out_split) ? a.out0 + (size_t)row * a.ldo
+                                               : a.out1 + (size_t)(row - a.out_split) * a.ldo;
+            orow[cell] = f32_to_f64(fmaf(__uint_as_float(v[j]) * cs, rs, ra));
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(tempty_even + (uint32_t)(b * sizeof(uint64_t)));
+    }
+  }
+  __syncthreads();
+  cluster_sync();   // no CTA leaves while its peer may still reach its barriers or TMEM
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc_pair(tmem_base, kPairTmemCols);
   }
 }
 
@@ -781,12 +1084,15 @@ struct yy_tc_tables {
   float *part;
   int an_splits, an_kb_per;
   CUtensorMap an_mapA, an_mapB;
-  // synthesis (3 coefficient sets, 3 tables)
-  int sy_kpad, sy_rows_b;
-  void *sy_A[3], *sy_B[3];
-  double *sy_rs[3], *sy_cs[3];
-  float *sy_rsf[3], *sy_csf[3], *sy_add[3];
-  CUtensorMap sy_mapA[3], sy_mapB[3];
+  // synthesis (3 coefficient sets, 3 tables), CTA-pair kernel
+  int sy_kpad;
+  int sy_cells_pad, sy_cell_tiles;        // table rows (multiple of 256), tiles of 256 cells
+  int sy_bn, sy_row_tiles, sy_rows_pad;   // coefficient rows per tile, tiles, padded rows
+  int pair_slots;                         // co-resident CTA pairs
+  void *sy_q[3], *sy_tab[3];              // packed coefficients / tables
+  double *sy_qs[3], *sy_tabs[3];          // their scales (float64 copies)
+  float *sy_qsf[3], *sy_tabsf[3], *sy_add[3];
+  CUtensorMap sy_qmap[3], sy_tabmap[3];
 };
 
 namespace yy {
@@ -821,6 +1127,28 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<F>()) != cudaSuccess)
       return YY_ERR_NOT_SUPPORTED;
   }
+  if (cudaFuncSetAttribute(k_tc_pair<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, pair_smem_bytes<F>()) !=
+      cudaSuccess)
+    return YY_ERR_NOT_SUPPORTED;
+  {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * 64);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = pair_smem_bytes<F>();
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (void *)k_tc_pair<F>, &cfg) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      return YY_ERR_NOT_SUPPORTED;
+    }
+    t->pair_slots = n;
+  }
   // Clusters of 3 CTAs along M share B tiles by multicast.  Measured on the
   // 1-degree grid they cut L2 reads but not the time per tile, and fewer
   // clusters than SMs can be resident, so single CTAs are the default;
@@ -852,7 +1180,11 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
   t->an_kpad = round_up(g->n_ang, kPadK);
   t->an_rows_b = round_up(g->n_lm, F::kBN);
   t->sy_kpad = round_up(g->n_lm, kPadK);
-  t->sy_rows_b = round_up(g->n_ang, F::kBN);
+  t->sy_cells_pad = round_up(g->n_ang, 2 * kPairRows);
+  t->sy_cell_tiles = t->sy_cells_pad / (2 * kPairRows);
+  t->sy_row_tiles = (M + 255) / 256;
+  t->sy_bn = round_up((M + t->sy_row_tiles - 1) / t->sy_row_tiles, 16);
+  t->sy_rows_pad = t->sy_row_tiles * t->sy_bn;
   cudaError_t e = cudaSuccess;
   auto A = [&](void **ptr, size_t bytes) {
     if (e == cudaSuccess) e = dmalloc(ptr, bytes);
@@ -866,13 +1198,13 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
   A((void **)&t->an_colsum, g->n_lm * sizeof(double));
   A((void **)&t->an_b0, g->n_ang * sizeof(float));
   for (int c = 0; c < 3; ++c) {
-    A(&t->sy_A[c], (size_t)F::kPA * t->an_rows_a * t->sy_kpad * F::kElem);
-    A(&t->sy_B[c], (size_t)F::kPB * t->sy_rows_b * t->sy_kpad * F::kElem);
-    A((void **)&t->sy_rs[c], t->an_rows_a * sizeof(double));
-    A((void **)&t->sy_cs[c], t->sy_rows_b * sizeof(double));
-    A((void **)&t->sy_rsf[c], t->an_rows_a * sizeof(float));
-    A((void **)&t->sy_csf[c], t->sy_rows_b * sizeof(float));
-    A((void **)&t->sy_add[c], t->an_rows_a * sizeof(float));
+    A(&t->sy_q[c], (size_t)F::kPB * t->sy_rows_pad * t->sy_kpad * F::kElem);
+    A(&t->sy_tab[c], (size_t)F::kPA * t->sy_cells_pad * t->sy_kpad * F::kElem);
+    A((void **)&t->sy_qs[c], t->sy_rows_pad * sizeof(double));
+    A((void **)&t->sy_tabs[c], t->sy_cells_pad * sizeof(double));
+    A((void **)&t->sy_qsf[c], t->sy_rows_pad * sizeof(float));
+    A((void **)&t->sy_tabsf[c], t->sy_cells_pad * sizeof(float));
+    A((void **)&t->sy_add[c], t->sy_rows_pad * sizeof(float));
   }
   // split K of the analysis: about three rounds of the persistent CTAs; the
   // split also bounds the fp32 accumulation length of each partial sum
@@ -912,7 +1244,7 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
   for (int c = 0; c < 3; ++c) {
     PackArgs &q = bs.job[c];
     q.rows = g->n_ang;
-    q.rows_pad = t->sy_rows_b;
+    q.rows_pad = t->sy_cells_pad;
     q.K = g->n_lm;
     q.k_pad = t->sy_kpad;
     q.src0 = q.src1 = tabs[c];
@@ -920,9 +1252,9 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
     q.ld = g->n_lm;
     q.zero_k0 = q.zero_k1 = -1;
     q.zero_row = -1;
-    q.scale_out = t->sy_cs[c];
-    q.scale_out_f = t->sy_csf[c];
-    q.out = t->sy_B[c];
+    q.scale_out = t->sy_tabs[c];
+    q.scale_out_f = t->sy_tabsf[c];
+    q.out = t->sy_tab[c];
   }
   if ((e = launch_pack<F>(bs, 3, 0)) != cudaSuccess) return YY_ERR_CUDA;
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return YY_ERR_CUDA;
@@ -931,8 +1263,8 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
   bool ok = make_map<F>(&t->an_mapA, t->an_A, t->an_kpad, F::kPA * t->an_rows_a, kBM) &&
             make_map<F>(&t->an_mapB, t->an_B, t->an_kpad, F::kPB * t->an_rows_b, brows);
   for (int c = 0; c < 3 && ok; ++c)
-    ok = make_map<F>(&t->sy_mapA[c], t->sy_A[c], t->sy_kpad, F::kPA * t->an_rows_a, kBM) &&
-         make_map<F>(&t->sy_mapB[c], t->sy_B[c], t->sy_kpad, F::kPB * t->sy_rows_b, brows);
+    ok = make_map<F>(&t->sy_tabmap[c], t->sy_tab[c], t->sy_kpad, F::kPA * t->sy_cells_pad, kPairRows) &&
+         make_map<F>(&t->sy_qmap[c], t->sy_q[c], t->sy_kpad, F::kPB * t->sy_rows_pad, t->sy_bn / 2);
   if (!ok) return YY_ERR_NOT_SUPPORTED;
   return YY_OK;
 }
@@ -943,7 +1275,7 @@ static void free_tables(yy_tc_tables *t) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (int c = 0; c < 3; ++c) {
-    void *q[] = {t->sy_A[c], t->sy_B[c], t->sy_rs[c], t->sy_cs[c], t->sy_rsf[c], t->sy_csf[c], t->sy_add[c]};
+    void *q[] = {t->sy_q[c], t->sy_tab[c], t->sy_qs[c], t->sy_tabs[c], t->sy_qsf[c], t->sy_tabsf[c], t->sy_add[c]};
     for (void *p : q)
       if (p) cudaFree(p);
   }
@@ -1065,7 +1397,7 @@ static cudaError_t pack_coefficients_form(yy_grid *g, yy_tc_tables *t, cudaStrea
   for (int c = 0; c < 3; ++c) {
     PackArgs &p = b.job[c];
     p.rows = M;
-    p.rows_pad = t->an_rows_a;
+    p.rows_pad = t->sy_rows_pad;
     p.K = g->n_lm;
     p.k_pad = t->sy_kpad;
     p.src0 = p.src1 = g->Q + c * qsz;
@@ -1076,9 +1408,9 @@ static cudaError_t pack_coefficients_form(yy_grid *g, yy_tc_tables *t, cudaStrea
     p.zero_row = -1;
     p.add_factor = add[c];
     p.row_add = t->sy_add[c];
-    p.scale_out = t->sy_rs[c];
-    p.scale_out_f = t->sy_rsf[c];
-    p.out = t->sy_A[c];
+    p.scale_out = t->sy_qs[c];
+    p.scale_out_f = t->sy_qsf[c];
+    p.out = t->sy_q[c];
   }
   cudaError_t e = launch_pack<F>(b, 3, s);
   g->launches++;
@@ -1099,24 +1431,39 @@ static cudaError_t synthesis_form(yy_grid *g, yy_tc_tables *t, int which, double
                {2, 2, gy ? gy + 2 * comp : nullptr, gg ? gg + 2 * comp : nullptr}};
   const int j0 = which == 0 ? 0 : 1, j1 = which == 0 ? 1 : 4;
   for (int j = j0; j < j1; ++j) {
-    TcArgs a = {};
-    a.M = 2 * g->n_r;
-    a.N = g->n_ang;
+    PairArgs a = {};
+    a.cells = g->n_ang;
+    a.cell_tiles = t->sy_cell_tiles;
+    a.rows = 2 * g->n_r;
+    a.row_tiles = t->sy_row_tiles;
+    a.bn = t->sy_bn;
     a.kb_total = t->sy_kpad * F::kElem / kRowBytes;
-    a.kb_per_tile = a.kb_total;
-    a.a_rows = t->an_rows_a;
-    a.b_rows = t->sy_rows_b;
-    a.mode = 1;
+    a.a_rows = t->sy_cells_pad;
+    a.b_rows = t->sy_rows_pad;
     a.out0 = jobs[j].o0;
     a.out1 = jobs[j].o1;
     a.out_split = g->n_r;
     a.ldo = g->n_ang;
-    a.row_scale = t->sy_rsf[jobs[j].q];
-    a.col_scale = t->sy_csf[jobs[j].tab];
+    a.cell_scale = t->sy_tabsf[jobs[j].tab];
+    a.row_scale = t->sy_qsf[jobs[j].q];
     a.row_add = t->sy_add[jobs[j].q];
     a.err = g->err;
-    cudaError_t e = launch_gemm<F>(g, t, t->sy_mapA[jobs[j].q], t->sy_mapB[jobs[j].tab], a, t->sy_rows_b / F::kBN,
-                                   t->an_rows_a / kBM, 1, s);
+    const int tiles = a.cell_tiles * a.row_tiles;
+    const int pairs = tiles < t->pair_slots ? tiles : t->pair_slots;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * pairs);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = pair_smem_bytes<F>();
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_pair<F>, t->sy_tabmap[jobs[j].tab], t->sy_qmap[jobs[j].q], a);
+    g->launches++;
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
