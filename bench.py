@@ -294,7 +294,7 @@ def run_ours(args, dist):
 
     # ---- roofline of the dominant kernel (the synthesis contraction)
     n_synth = 4 if gradient else 1
-    synth_ms = (stage_tot["synth_phi"] + stage_tot["synth_grad"]) / args.steps / n_synth
+    synth_ms = stage_tot["synthesis"] / args.steps / n_synth
     synth_flop = 2.0 * (2 * spec.n_r) * grid.n_lm * spec.n_ang
     total_flop = grid.flops(gradient)
     products = {"fp16x2": 3, "bf16x3": 6, "tf32": 1, "fp64": 1, "fp32": 1}[prec]

@@ -181,15 +181,13 @@ const char *yy_status_string(yy_status s);
  *   ms[YY_STAGE_ANALYSIS]   analysis contraction (operand packing included)
  *   ms[YY_STAGE_SCAN]       moment combination and radial scans (coefficient
  *                           packing included)
- *   ms[YY_STAGE_SYNTH_PHI]  synthesis of Phi (one contraction)
- *   ms[YY_STAGE_SYNTH_GRAD] synthesis of -grad Phi (three contractions; 0
- *                           without gradient)                              */
+ *   ms[YY_STAGE_SYNTHESIS]  synthesis of Phi and, when requested, -grad Phi
+ *                           (one or four contractions)                      */
 typedef enum {
   YY_STAGE_ANALYSIS = 0,
   YY_STAGE_SCAN = 1,
-  YY_STAGE_SYNTH_PHI = 2,
-  YY_STAGE_SYNTH_GRAD = 3,
-  YY_STAGE_COUNT = 4
+  YY_STAGE_SYNTHESIS = 2,
+  YY_STAGE_COUNT = 3
 } yy_stage;
 yy_status yy_grid_set_profiling(yy_grid *g, int enable);
 yy_status yy_grid_stage_ms(yy_grid *g, double *ms);

@@ -228,14 +228,9 @@ yy_status yy_potential(yy_grid *g, const double *rho_yin, const double *rho_yang
   if (e == cudaSuccess && !simt) e = tc_pack_coefficients(g, prec, s);
   mark(2);
   if (e == cudaSuccess)
-    e = simt ? synthesis_simt(g, 0, phi_yin, phi_yang, grad_yin, grad_yang, f32, s)
-             : tc_synthesis(g, prec, 0, phi_yin, phi_yang, grad_yin, grad_yang, s);
+    e = simt ? synthesis_simt(g, phi_yin, phi_yang, grad_yin, grad_yang, f32, s)
+             : tc_synthesis(g, prec, phi_yin, phi_yang, grad_yin, grad_yang, s);
   mark(3);
-  if (e == cudaSuccess && grad_yin != nullptr)
-    e = simt ? synthesis_simt(g, 1, phi_yin, phi_yang, grad_yin, grad_yang, f32, s)
-             : tc_synthesis(g, prec, 1, phi_yin, phi_yang, grad_yin, grad_yang, s);
-  mark(4);
-  g->last_had_grad = grad_yin != nullptr;
   return from_cuda(e);
 }
 
@@ -319,13 +314,13 @@ void yy_destroy(yy_grid *g) {
 yy_status yy_grid_set_profiling(yy_grid *g, int enable) {
   if (!g) return YY_ERR_INVALID_ARG;
   if (enable && !g->profiling) {
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i <= YY_STAGE_COUNT; ++i) {
       cudaError_t e = cudaEventCreate(&g->ev[i]);
       if (e != cudaSuccess) return from_cuda(e);
     }
   } else if (!enable && g->profiling) {
     cudaDeviceSynchronize();
-    for (int i = 0; i < 5; ++i) cudaEventDestroy(g->ev[i]);
+    for (int i = 0; i <= YY_STAGE_COUNT; ++i) cudaEventDestroy(g->ev[i]);
   }
   g->profiling = enable ? 1 : 0;
   return YY_OK;
@@ -333,12 +328,12 @@ yy_status yy_grid_set_profiling(yy_grid *g, int enable) {
 
 yy_status yy_grid_stage_ms(yy_grid *g, double *ms) {
   if (!g || !ms || !g->profiling) return YY_ERR_INVALID_ARG;
-  cudaError_t e = cudaEventSynchronize(g->ev[4]);
-  float t[4] = {0, 0, 0, 0};
-  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&t[i], g->ev[i], g->ev[i + 1]);
+  cudaError_t e = cudaEventSynchronize(g->ev[YY_STAGE_COUNT]);
+  float t[YY_STAGE_COUNT] = {};
+  for (int i = 0; i < YY_STAGE_COUNT && e == cudaSuccess; ++i)
+    e = cudaEventElapsedTime(&t[i], g->ev[i], g->ev[i + 1]);
   if (e != cudaSuccess) return from_cuda(e);
-  for (int i = 0; i < 4; ++i) ms[i] = t[i];
-  if (!g->last_had_grad) ms[YY_STAGE_SYNTH_GRAD] = 0.0;
+  for (int i = 0; i < YY_STAGE_COUNT; ++i) ms[i] = t[i];
   return YY_OK;
 }
 

@@ -178,7 +178,7 @@ cudaError_t analysis_simt(yy_grid *g, const double *rho_yin, const double *rho_y
   return err;
 }
 
-cudaError_t synthesis_simt(yy_grid *g, int which, double *phi_yin, double *phi_yang, double *grad_yin,
+cudaError_t synthesis_simt(yy_grid *g, double *phi_yin, double *phi_yang, double *grad_yin,
                            double *grad_yang, bool fp32, cudaStream_t s) {
   const int M = 2 * g->n_r, N = g->n_ang, K = g->n_lm;
   const size_t qsz = (size_t)M * K;
@@ -193,9 +193,8 @@ cudaError_t synthesis_simt(yy_grid *g, int which, double *phi_yin, double *phi_y
                {1, 0, grad_yin, grad_yang},
                {2, 1, grad_yin ? grad_yin + comp : nullptr, grad_yang ? grad_yang + comp : nullptr},
                {2, 2, grad_yin ? grad_yin + 2 * comp : nullptr, grad_yang ? grad_yang + 2 * comp : nullptr}};
-  const int t0 = (which == 0) ? 0 : 1;
-  const int t1 = (which == 0) ? 1 : 4;
-  for (int t = t0; t < t1; ++t) {
+  const int n_jobs = grad_yin ? 4 : 1;
+  for (int t = 0; t < n_jobs; ++t) {
     const Job &jb = jobs[t];
     if (fp32) {
       const float *tabs[3] = {g->ysyn32, g->ysyn_t32, g->ysyn_p32};

@@ -59,8 +59,7 @@ struct yy_grid {
 
   // stage timing
   int profiling;
-  int last_had_grad;
-  cudaEvent_t ev[5];
+  cudaEvent_t ev[YY_STAGE_COUNT + 1];
 
   // host-buffer staging (yy_potential_host)
   double *stage_rho, *stage_phi, *stage_grad;
@@ -79,8 +78,8 @@ inline int rotation_table_size(int lmax) { return (lmax + 1) * (4 * (lmax + 1) *
 // float64 / float32 CUDA-core contractions (yy_gemm_simt.cu)
 cudaError_t analysis_simt(yy_grid *g, const double *rho_yin, const double *rho_yang,
                           bool fp32, cudaStream_t s);
-// which = 0: Phi only; which = 1: the three gradient components only
-cudaError_t synthesis_simt(yy_grid *g, int which, double *phi_yin, double *phi_yang,
+// Phi, and the three gradient components when grad_yin != NULL
+cudaError_t synthesis_simt(yy_grid *g, double *phi_yin, double *phi_yang,
                            double *grad_yin, double *grad_yang, bool fp32, cudaStream_t s);
 cudaError_t convert_tables_f32(yy_grid *g);
 
@@ -96,7 +95,7 @@ void tc_free(yy_grid *g);
 cudaError_t tc_analysis(yy_grid *g, yy_precision prec, const double *rho_yin,
                         const double *rho_yang, cudaStream_t s);
 cudaError_t tc_pack_coefficients(yy_grid *g, yy_precision prec, cudaStream_t s);
-cudaError_t tc_synthesis(yy_grid *g, yy_precision prec, int which, double *phi_yin,
+cudaError_t tc_synthesis(yy_grid *g, yy_precision prec, double *phi_yin,
                          double *phi_yang, double *grad_yin, double *grad_yang, cudaStream_t s);
 
 }  // namespace yy

@@ -267,6 +267,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 16 columns of this warp's 32 TMEM lanes, without waiting (tmem_wait_ld).
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -643,10 +655,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 // ---------------------------------------------------------------------------
 //
 // out[row][cell] = (sum_k Y[cell][k] Q[row][k]) cell_scale[cell] row_scale[row] + row_add[row]
-// with Y the packed table (operand A, one row per cell) and Q the packed
-// coefficients (operand B).  Clusters of two CTAs; pair p handles tiles
-// p, p + #pairs, ... (coefficient-row tiles fastest, so the pairs working at
-// the same time share table tiles in L2).  Per stage each CTA loads its 128
+// with Y a packed table (operand A, one row per cell) and Q packed
+// coefficients (operand B), for up to four jobs (Phi, g_r, g_theta, g_phi)
+// in one launch.  Clusters of two CTAs; pair p handles tiles p, p + #pairs,
+// ... of the job-major tile list (coefficient-row tiles fastest, so the
+// pairs working at the same time share table tiles in L2).  Per stage each CTA loads its 128
 // table rows and its bn / 2 coefficient rows; both CTAs' loads complete on
 // the even CTA's "full" barrier, whose thread 32 issues the M = 256 MMAs and
 // releases each stage in both CTAs with a multicast commit.  Each CTA's TMEM
@@ -654,21 +667,31 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 // epilogue warp owns one cell and a 16-column TMEM load gives it 16 rows:
 // every store is 32 consecutive cells of one output row.  The epilogue warps
 // of both CTAs release a buffer on the even CTA's "tempty" barrier.
+struct PairJob {
+  double *out0, *out1;          // row r < out_split -> out0 + r ldo, else out1 + (r - out_split) ldo
+  const float *cell_scale, *row_scale, *row_add;
+  int ta, tb;                   // operand maps of this job
+};
+
 struct PairArgs {
   int cells, cell_tiles;        // valid cells; tiles of 256 cells
   int rows, row_tiles, bn;      // valid coefficient rows; tiles of bn rows (multiple of 16, <= 256)
   int kb_total;                 // K blocks (kRowBytes per row)
   int a_rows, b_rows;           // rows of one piece in the stacked A (table) / B (coefficient) operands
-  double *out0, *out1;          // row r < out_split -> out0 + r ldo, else out1 + (r - out_split) ldo
   int out_split;
   long long ldo;
-  const float *cell_scale, *row_scale, *row_add;
+  int n_jobs;
+  PairJob job[4];
   int *err;
+};
+
+struct PairMaps {
+  CUtensorMap a[3], b[3];       // tables (operand A), coefficient sets (operand B)
 };
 
 template <class F>
 __global__ void __launch_bounds__(kThreads, 1)
-k_tc_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, PairArgs a) {
+k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArgs a) {
   constexpr int S = F::kPairStages;
   constexpr int SLOT = kPairRows * kRowBytes;
   constexpr int STAGE = pair_stage_bytes<F>();
@@ -687,7 +710,8 @@ k_tc_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rank = (int)cluster_rank();
   const int pair = (int)blockIdx.x >> 1, n_pairs = (int)gridDim.x >> 1;
-  const int total = a.cell_tiles * a.row_tiles;
+  const int per_job = a.cell_tiles * a.row_tiles;
+  const int total = per_job * a.n_jobs;
   const int bh = a.bn >> 1;
 
   if (threadIdx.x == 0) {
@@ -716,9 +740,12 @@ k_tc_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       int gk = 0;
       bool ok = true;
       for (int t = pair; t < total && ok; t += n_pairs) {
-        const int rt = t % a.row_tiles, ct = t / a.row_tiles;
+        const int jb = t / per_job, tl = t % per_job;
+        const int rt = tl % a.row_tiles, ct = tl / a.row_tiles;
         const int arow = (2 * ct + rank) * kPairRows;
         const int brow = rt * a.bn + rank * bh;
+        const CUtensorMap *tmA = &maps.a[a.job[jb].ta];
+        const CUtensorMap *tmB = &maps.b[a.job[jb].tb];
         for (int i = 0; i < a.kb_total; ++i, ++gk) {
           const int s = gk % S;
           if (gk >= S && !mbar_wait(&empty[s], ((gk / S) & 1) ^ 1, a.err)) {
@@ -730,10 +757,10 @@ k_tc_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           const uint32_t base = smem_u32(smem + s * STAGE);
           const int kx = i * BK;
 #pragma unroll
-          for (int p = 0; p < F::kPA; ++p) tma_load_2d_pair(&tmA, base + p * SLOT, fbar, kx, p * a.a_rows + arow);
+          for (int p = 0; p < F::kPA; ++p) tma_load_2d_pair(tmA, base + p * SLOT, fbar, kx, p * a.a_rows + arow);
 #pragma unroll
           for (int p = 0; p < F::kPB; ++p)
-            tma_load_2d_pair(&tmB, base + (F::kPA + p) * SLOT, fbar, kx, p * a.b_rows + brow);
+            tma_load_2d_pair(tmB, base + (F::kPA + p) * SLOT, fbar, kx, p * a.b_rows + brow);
         }
       }
       // the last uses of every stage must be complete before this CTA leaves
@@ -777,37 +804,62 @@ k_tc_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       }
     }
   } else {
+    // Lane quarter of this warp's TMEM lanes; the four warps of a quarter take
+    // 16-column chunks sub, sub + 4, sub + 8, sub + 12.  The scales of a tile
+    // are loaded before its accumulator is ready; the chunks are read from
+    // TMEM two at a time.
     const int quarter = warp & 3;
     const int sub = (warp - 2) >> 2;    // 0..3 within the lane quarter
     const uint32_t tempty_even = mapa_rank(smem_u32(&tempty[0]), 0);
+    const int n_chunks = a.bn / kEpiCols;
     int it = 0;
     for (int t = pair; t < total; t += n_pairs, ++it) {
       const int b = it & 1;
-      if (!mbar_wait_cluster(&tfull[b], (it >> 1) & 1, a.err)) break;
-      tc_fence_after();
-      const int rt = t % a.row_tiles, ct = t / a.row_tiles;
+      const PairJob &J = a.job[t / per_job];
+      const int tl = t % per_job;
+      const int rt = tl % a.row_tiles, ct = tl / a.row_tiles;
       const int cell = (2 * ct + rank) * kPairRows + quarter * 32 + lane;
       const bool cell_ok = cell < a.cells;
-      const float cs = cell_ok ? a.cell_scale[cell] : 0.0f;
-#pragma unroll 1
-      for (int c0 = kEpiCols * sub; c0 < a.bn; c0 += kEpiCols * 4) {
-        uint32_t v[16];
-        tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + c0), v);
-        const int row0 = rt * a.bn + c0;
-        float rsl = 0.0f, ral = 0.0f;
-        if (lane < kEpiCols && row0 + lane < a.rows) {
-          rsl = a.row_scale[row0 + lane];
-          ral = a.row_add[row0 + lane];
-        }
+      const float cs = cell_ok ? J.cell_scale[cell] : 0.0f;
+      // lanes 0..15: scales of row (chunk i, lane) for chunk i = sub + 4 (i')
+      float rsv[4], rav[4];
 #pragma unroll
-        for (int j = 0; j < kEpiCols; ++j) {
-          const float rs = __shfl_sync(0xffffffffu, rsl, j);
-          const float ra = __shfl_sync(0xffffffffu, ral, j);
-          const int row = row0 + j;
-          if (row < a.rows && cell_ok) {
-            double *orow = (row < a.out_split) ? a.out0 + (size_t)row * a.ldo
-                                               : a.out1 + (size_t)(row - a.out_split) * a.ldo;
-            orow[cell] = f32_to_f64(fmaf(__uint_as_float(v[j]) * cs, rs, ra));
+      for (int i = 0; i < 4; ++i) {
+        const int row = rt * a.bn + (sub + 4 * i) * kEpiCols + (lane & 15);
+        const bool ok = (sub + 4 * i) < n_chunks && row < a.rows;
+        rsv[i] = ok ? J.row_scale[row] : 0.0f;
+        rav[i] = ok ? J.row_add[row] : 0.0f;
+      }
+      if (!mbar_wait_cluster(&tfull[b], (it >> 1) & 1, a.err)) break;
+      tc_fence_after();
+      const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i0 = 2 * h, i1 = 2 * h + 1;
+        const int k0 = sub + 4 * i0, k1 = sub + 4 * i1;
+        if (k0 >= n_chunks) break;
+        uint32_t v0[16], v1[16];
+        tmem_ld16_async(tbase + (uint32_t)(k0 * kEpiCols), v0);
+        if (k1 < n_chunks) tmem_ld16_async(tbase + (uint32_t)(k1 * kEpiCols), v1);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int k = c == 0 ? k0 : k1;
+          if (k >= n_chunks) break;
+          const float rsl = c == 0 ? rsv[i0] : rsv[i1];
+          const float ral = c == 0 ? rav[i0] : rav[i1];
+          const int row0 = rt * a.bn + k * kEpiCols;
+#pragma unroll
+          for (int j = 0; j < kEpiCols; ++j) {
+            const float rs = __shfl_sync(0xffffffffu, rsl, j);
+            const float ra = __shfl_sync(0xffffffffu, ral, j);
+            const int row = row0 + j;
+            const float x = __uint_as_float(c == 0 ? v0[j] : v1[j]);
+            if (row < a.rows && cell_ok) {
+              double *orow = (row < a.out_split) ? J.out0 + (size_t)row * a.ldo
+                                                 : J.out1 + (size_t)(row - a.out_split) * a.ldo;
+              orow[cell] = f32_to_f64(fmaf(x * cs, rs, ra));
+            }
           }
         }
       }
@@ -1092,7 +1144,7 @@ struct yy_tc_tables {
   void *sy_q[3], *sy_tab[3];              // packed coefficients / tables
   double *sy_qs[3], *sy_tabs[3];          // their scales (float64 copies)
   float *sy_qsf[3], *sy_tabsf[3], *sy_add[3];
-  CUtensorMap sy_qmap[3], sy_tabmap[3];
+  yy::PairMaps sy_maps;                     // a: tables, b: coefficient sets
 };
 
 namespace yy {
@@ -1263,8 +1315,8 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
   bool ok = make_map<F>(&t->an_mapA, t->an_A, t->an_kpad, F::kPA * t->an_rows_a, kBM) &&
             make_map<F>(&t->an_mapB, t->an_B, t->an_kpad, F::kPB * t->an_rows_b, brows);
   for (int c = 0; c < 3 && ok; ++c)
-    ok = make_map<F>(&t->sy_tabmap[c], t->sy_tab[c], t->sy_kpad, F::kPA * t->sy_cells_pad, kPairRows) &&
-         make_map<F>(&t->sy_qmap[c], t->sy_q[c], t->sy_kpad, F::kPB * t->sy_rows_pad, t->sy_bn / 2);
+    ok = make_map<F>(&t->sy_maps.a[c], t->sy_tab[c], t->sy_kpad, F::kPA * t->sy_cells_pad, kPairRows) &&
+         make_map<F>(&t->sy_maps.b[c], t->sy_q[c], t->sy_kpad, F::kPB * t->sy_rows_pad, t->sy_bn / 2);
   if (!ok) return YY_ERR_NOT_SUPPORTED;
   return YY_OK;
 }
@@ -1418,55 +1470,57 @@ static cudaError_t pack_coefficients_form(yy_grid *g, yy_tc_tables *t, cudaStrea
 }
 
 template <class F>
-static cudaError_t synthesis_form(yy_grid *g, yy_tc_tables *t, int which, double *py, double *pg, double *gy,
-                                  double *gg, cudaStream_t s) {
+static cudaError_t synthesis_form(yy_grid *g, yy_tc_tables *t, double *py, double *pg, double *gy, double *gg,
+                                  cudaStream_t s) {
   const size_t comp = (size_t)g->n_r * g->n_ang;
-  // (coefficient set, table, outputs)
-  struct Job {
+  // (coefficient set, table, outputs): Phi = Q.Y, g_r = Q_r.Y, g_theta = Q_t.Y_t, g_phi = Q_t.Y_p
+  const struct {
     int q, tab;
     double *o0, *o1;
   } jobs[4] = {{0, 0, py, pg},
                {1, 0, gy, gg},
                {2, 1, gy ? gy + comp : nullptr, gg ? gg + comp : nullptr},
                {2, 2, gy ? gy + 2 * comp : nullptr, gg ? gg + 2 * comp : nullptr}};
-  const int j0 = which == 0 ? 0 : 1, j1 = which == 0 ? 1 : 4;
-  for (int j = j0; j < j1; ++j) {
-    PairArgs a = {};
-    a.cells = g->n_ang;
-    a.cell_tiles = t->sy_cell_tiles;
-    a.rows = 2 * g->n_r;
-    a.row_tiles = t->sy_row_tiles;
-    a.bn = t->sy_bn;
-    a.kb_total = t->sy_kpad * F::kElem / kRowBytes;
-    a.a_rows = t->sy_cells_pad;
-    a.b_rows = t->sy_rows_pad;
-    a.out0 = jobs[j].o0;
-    a.out1 = jobs[j].o1;
-    a.out_split = g->n_r;
-    a.ldo = g->n_ang;
-    a.cell_scale = t->sy_tabsf[jobs[j].tab];
-    a.row_scale = t->sy_qsf[jobs[j].q];
-    a.row_add = t->sy_add[jobs[j].q];
-    a.err = g->err;
-    const int tiles = a.cell_tiles * a.row_tiles;
-    const int pairs = tiles < t->pair_slots ? tiles : t->pair_slots;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(2 * pairs);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = pair_smem_bytes<F>();
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_pair<F>, t->sy_tabmap[jobs[j].tab], t->sy_qmap[jobs[j].q], a);
-    g->launches++;
-    if (e != cudaSuccess) return e;
+  PairArgs a = {};
+  a.cells = g->n_ang;
+  a.cell_tiles = t->sy_cell_tiles;
+  a.rows = 2 * g->n_r;
+  a.row_tiles = t->sy_row_tiles;
+  a.bn = t->sy_bn;
+  a.kb_total = t->sy_kpad * F::kElem / kRowBytes;
+  a.a_rows = t->sy_cells_pad;
+  a.b_rows = t->sy_rows_pad;
+  a.out_split = g->n_r;
+  a.ldo = g->n_ang;
+  a.n_jobs = gy ? 4 : 1;
+  a.err = g->err;
+  for (int j = 0; j < a.n_jobs; ++j) {
+    PairJob &J = a.job[j];
+    J.out0 = jobs[j].o0;
+    J.out1 = jobs[j].o1;
+    J.cell_scale = t->sy_tabsf[jobs[j].tab];
+    J.row_scale = t->sy_qsf[jobs[j].q];
+    J.row_add = t->sy_add[jobs[j].q];
+    J.ta = jobs[j].tab;
+    J.tb = jobs[j].q;
   }
-  return cudaSuccess;
+  const int tiles = a.cell_tiles * a.row_tiles * a.n_jobs;
+  const int pairs = tiles < t->pair_slots ? tiles : t->pair_slots;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(2 * pairs);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = pair_smem_bytes<F>();
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_pair<F>, t->sy_maps, a);
+  g->launches++;
+  return e;
 }
 
 cudaError_t tc_analysis(yy_grid *g, yy_precision prec, const double *ry, const double *rg, cudaStream_t s) {
@@ -1489,13 +1543,13 @@ cudaError_t tc_pack_coefficients(yy_grid *g, yy_precision prec, cudaStream_t s) 
   }
 }
 
-cudaError_t tc_synthesis(yy_grid *g, yy_precision prec, int which, double *py, double *pg, double *gy, double *gg,
+cudaError_t tc_synthesis(yy_grid *g, yy_precision prec, double *py, double *pg, double *gy, double *gg,
                          cudaStream_t s) {
   yy_tc_tables *t = g->tc[prec];
   switch (prec) {
-    case YY_FP16X2: return synthesis_form<FormFP16x2>(g, t, which, py, pg, gy, gg, s);
-    case YY_BF16X3: return synthesis_form<FormBF16x3>(g, t, which, py, pg, gy, gg, s);
-    case YY_TF32: return synthesis_form<FormTF32>(g, t, which, py, pg, gy, gg, s);
+    case YY_FP16X2: return synthesis_form<FormFP16x2>(g, t, py, pg, gy, gg, s);
+    case YY_BF16X3: return synthesis_form<FormBF16x3>(g, t, py, pg, gy, gg, s);
+    case YY_TF32: return synthesis_form<FormTF32>(g, t, py, pg, gy, gg, s);
     default: return cudaErrorInvalidValue;
   }
 }

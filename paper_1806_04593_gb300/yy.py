@@ -180,8 +180,8 @@ def yy_last_launch_count(handle):
     return load().yy_last_launch_count(handle)
 
 
-YY_STAGE_COUNT = 4
-STAGES = ("analysis", "scan", "synth_phi", "synth_grad")
+YY_STAGE_COUNT = 3
+STAGES = ("analysis", "scan", "synthesis")
 
 
 def yy_grid_set_profiling(handle, enable):
