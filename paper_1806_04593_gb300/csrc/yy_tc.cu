@@ -1049,6 +1049,168 @@ __global__ void __launch_bounds__(256) k_pack_rows(PackBatch batch) {
   }
 }
 
+// Two adjacent elements split into the form's pieces (piece p at base + p
+// piece_stride); base is 4-byte aligned (8-byte for tf32).
+template <class F>
+__device__ __forceinline__ void split2(float y0, float y1, typename F::elem *base, size_t piece_stride) {
+  if constexpr (F::kKind == KIND_F16) {
+    const __half2 h = __floats2half2_rn(y0, y1);
+    const float2 hb = __half22float2(h);
+    *(__half2 *)base = h;
+    *(__half2 *)(base + piece_stride) = __floats2half2_rn(y0 - hb.x, y1 - hb.y);
+  } else if constexpr (F::kKind == KIND_BF16) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(y0, y1);
+    const float2 hb = __bfloat1622float2(h);
+    const float r0 = y0 - hb.x, r1 = y1 - hb.y;
+    const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
+    const float2 mb = __bfloat1622float2(m);
+    *(__nv_bfloat162 *)base = h;
+    *(__nv_bfloat162 *)(base + piece_stride) = m;
+    *(__nv_bfloat162 *)(base + 2 * piece_stride) = __floats2bfloat162_rn(r0 - mb.x, r1 - mb.y);
+  } else {
+    uint2 t;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t.x) : "f"(y0));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t.y) : "f"(y1));
+    *(uint2 *)base = t;
+  }
+}
+
+// Register-resident form of the packing: TPR threads per row, each holding 2P
+// values (pair c: elements 2 (c TPR + thread) + {0, 1}), so the row is read
+// once, every load and store instruction covers consecutive elements across
+// the threads, and the statistics need only shuffles (plus shared memory
+// across warps when TPR > 32).  TPR = 32: one warp per row, 8 rows per block
+// (short rows); TPR = 1024: one block per row (long rows).  Requires
+// k_pad <= 2 P TPR.  The chip's float64 pipe is narrow, so all per-thread
+// arithmetic is fp32: the row sum (it only fixes the centring value; the
+// same float is used again in the correction), the minimum and maximum, and
+// the optional dot product as an unevaluated fp32 pair (hi + lo, Knuth's
+// two-sum); one thread forms the float64 results.
+
+struct RowStats {
+  float s, dh, dl, mn, mx;
+};
+
+__device__ __forceinline__ void two_sum_add(float &h, float &l, float bh, float bl) {
+  const float s = h + bh;
+  const float bb = s - h;
+  const float e = (h - (s - bb)) + (bh - bb);
+  const float t = l + bl + e;
+  h = s + t;
+  l = t - (h - s);
+}
+
+__device__ __forceinline__ void warp_stats(RowStats &r) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    r.s += __shfl_xor_sync(0xffffffffu, r.s, off);
+    const float oh = __shfl_xor_sync(0xffffffffu, r.dh, off);
+    const float ol = __shfl_xor_sync(0xffffffffu, r.dl, off);
+    two_sum_add(r.dh, r.dl, oh, ol);
+    r.mn = fminf(r.mn, __shfl_xor_sync(0xffffffffu, r.mn, off));
+    r.mx = fmaxf(r.mx, __shfl_xor_sync(0xffffffffu, r.mx, off));
+  }
+}
+
+template <int TPR>
+__device__ __forceinline__ void row_stats(RowStats &r, RowStats *red) {
+  warp_stats(r);
+  if constexpr (TPR > 32) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = r;
+    __syncthreads();
+    if (w == 0) {
+      r = (lane < TPR / 32) ? red[lane] : RowStats{0.f, 0.f, 0.f, INFINITY, -INFINITY};
+      warp_stats(r);
+      if (lane == 0) red[0] = r;
+    }
+    __syncthreads();
+    r = red[0];
+  }
+}
+
+template <class F, int TPR, int P>
+__global__ void __launch_bounds__(TPR > 256 ? TPR : 256, 1)
+k_pack_reg(PackBatch batch) {
+  constexpr int TPB = TPR > 256 ? TPR : 256;
+  __shared__ RowStats red[32];
+  const PackArgs &p = batch.job[blockIdx.y];
+  const int tid = threadIdx.x % TPR;
+  const int row = blockIdx.x * (TPB / TPR) + threadIdx.x / TPR;
+  if (row >= p.rows_pad) return;   // whole rows (and, for TPR > 32, whole blocks) leave together
+  typedef typename F::elem E;
+  const size_t piece_stride = (size_t)p.rows_pad * p.k_pad;
+  E *orow = (E *)p.out + (size_t)row * p.k_pad;
+  const bool valid = row < p.rows && row != p.zero_row;
+  const double *src = nullptr;
+  if (valid) src = (row < p.split_row) ? p.src0 + (size_t)row * p.ld : p.src1 + (size_t)(row - p.split_row) * p.ld;
+  const int K = p.K, z0 = p.zero_k0, z1 = p.zero_k1;
+  const bool vec = ((uintptr_t)src & 15u) == 0;
+
+  // loads in runs of 4 pairs; the dot product adds fp32 runs of 8 products
+  float x[2 * P];
+  RowStats st = {0.f, 0.f, 0.f, INFINITY, -INFINITY};
+#pragma unroll
+  for (int c0 = 0; c0 < P; c0 += 4) {
+    double xv[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = 2 * ((c0 + i) * TPR + tid);
+      if (valid && k + 1 < K && vec) {
+        const double2 t = *(const double2 *)(src + k);
+        xv[2 * i] = t.x;
+        xv[2 * i + 1] = t.y;
+      } else {
+        xv[2 * i] = (valid && k < K) ? src[k] : 0.0;
+        xv[2 * i + 1] = (valid && k + 1 < K) ? src[k + 1] : 0.0;
+      }
+    }
+    float run = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int c = 2 * c0 + i;
+      const int k = 2 * ((c0 + i / 2) * TPR + tid) + (i & 1);
+      const bool used = valid && k < K && k != z0 && k != z1;
+      const float v = used ? f64_to_f32(xv[i]) : 0.0f;
+      x[c] = v;
+      st.s += v;
+      if (used) {
+        st.mn = fminf(st.mn, v);
+        st.mx = fmaxf(st.mx, v);
+      }
+      if (p.dot_vec) run = fmaf(v, (k < K) ? p.dot_vec[k] : 0.0f, run);
+    }
+    if (p.dot_vec) two_sum_add(st.dh, st.dl, run, 0.0f);
+  }
+  row_stats<TPR>(st, red);
+  const int n_used = K - (z0 >= 0 ? 1 : 0) - ((z1 >= 0 && z1 != z0) ? 1 : 0);
+  float mean = 0.0f;
+  if (p.mean_out && valid && n_used > 0) mean = st.s / (float)n_used;
+  float amax = 0.0f;
+  if (valid && n_used > 0) amax = fmaxf(st.mx - mean, mean - st.mn);
+  float scf = 1.0f;
+  if (amax > 0.0f && isfinite(amax)) scf = ldexpf(1.0f, 14 - ilogbf(amax));
+  if (tid == 0) {
+    p.scale_out[row] = (double)(1.0f / scf);   // a power of two: exact in fp32
+    if (p.scale_out_f) p.scale_out_f[row] = 1.0f / scf;
+    if (p.mean_out) p.mean_out[row] = (double)mean;
+    if (p.dot_vec && row < p.rows) p.dot_out[row] = valid ? (double)st.dh + (double)st.dl : 0.0;
+    if (p.row_add && row < p.rows)
+      p.row_add[row] = (valid && z0 >= 0) ? (float)(p.add_factor * src[z0]) : 0.0f;
+  }
+  // (x - mean) scf as one rounding: scf is a power of two
+  const float off = -mean * scf;
+#pragma unroll
+  for (int c = 0; c < P; ++c) {
+    const int k = 2 * (c * TPR + tid);
+    if (k >= p.k_pad) break;
+    const bool u0 = valid && k < K && k != z0 && k != z1;
+    const bool u1 = valid && k + 1 < K && k + 1 != z0 && k + 1 != z1;
+    split2<F>(u0 ? fmaf(x[2 * c], scf, off) : 0.0f, u1 ? fmaf(x[2 * c + 1], scf, off) : 0.0f, orow + k,
+              piece_stride);
+  }
+}
+
 // A[row][col] = (sum_z part[z][row][col]) row_scale col_scale + mean[row] colsum[col]
 // (the tensor cores saw rho - mean); column 0 is the float64 monopole.
 __global__ void k_reduce_partials(int M, int N, int S, const float *__restrict__ part,
@@ -1161,12 +1323,28 @@ static size_t pack_smem(const PackBatch &b, int n) {
 
 template <class F>
 static cudaError_t launch_pack(PackBatch &b, int n, cudaStream_t s) {
-  int rows = 0;
+  int rows = 0, kp = 0;
   for (int i = 0; i < n; ++i) {
     b.job[i].cache = b.job[i].K <= kPackCacheMax ? 1 : 0;
     rows = std::max(rows, b.job[i].rows_pad);
+    kp = std::max(kp, b.job[i].k_pad);
   }
-  k_pack_rows<F><<<dim3(rows, n), 256, pack_smem(b, n), s>>>(b);
+  // register-resident forms where the row fits, else the two-pass kernel
+  const unsigned wblocks = (unsigned)((rows + 7) / 8);
+  if (kp <= 32 * 8)
+    k_pack_reg<F, 32, 4><<<dim3(wblocks, n), 256, 0, s>>>(b);
+  else if (kp <= 32 * 24)
+    k_pack_reg<F, 32, 12><<<dim3(wblocks, n), 256, 0, s>>>(b);
+  else if (kp <= 32 * 64)
+    k_pack_reg<F, 32, 32><<<dim3(wblocks, n), 256, 0, s>>>(b);
+  else if (kp <= 1024 * 8)
+    k_pack_reg<F, 1024, 4><<<dim3(rows, n), 1024, 0, s>>>(b);
+  else if (kp <= 1024 * 16)
+    k_pack_reg<F, 1024, 8><<<dim3(rows, n), 1024, 0, s>>>(b);
+  else if (kp <= 1024 * 24)
+    k_pack_reg<F, 1024, 12><<<dim3(rows, n), 1024, 0, s>>>(b);
+  else
+    k_pack_rows<F><<<dim3(rows, n), 256, pack_smem(b, n), s>>>(b);
   return cudaGetLastError();
 }
 
