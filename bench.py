@@ -311,7 +311,7 @@ def run_ours(args, dist):
                 "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz"}
     else:
         ratio = 0.5 if prec == "tf32" else 1.0
-        roof = {"bound": "tensor", "kernel": f"k_tc_gemm<{prec}> (synthesis, tcgen05)",
+        roof = {"bound": "tensor", "kernel": f"k_tc_pair<{prec}> (synthesis, tcgen05 cta_group::2)",
                 "achieved": products * synth_flop / (synth_ms / 1e3) / 1e12,
                 "peak": peaks["bf16_tflops"] * ratio, "unit": "TFLOP/s", "traffic": None,
                 "flops_counted": f"hardware: {products} tensor-core products x 2MNK per launch",

@@ -224,7 +224,7 @@ yy_status yy_potential(yy_grid *g, const double *rho_yin, const double *rho_yang
     e = simt ? analysis_simt(g, rho_yin, rho_yang, f32, s) : tc_analysis(g, prec, rho_yin, rho_yang, s);
   mark(1);
   if (e == cudaSuccess) e = rotate_moments(g, prec == YY_FP64, s);
-  if (e == cudaSuccess) e = radial_scan(g, f32, s);
+  if (e == cudaSuccess) e = radial_scan(g, f32, true, s);
   if (e == cudaSuccess && !simt) e = tc_pack_coefficients(g, prec, s);
   mark(2);
   if (e == cudaSuccess)

@@ -85,9 +85,10 @@ cudaError_t convert_tables_f32(yy_grid *g);
 
 // Atot = A + D^T A(other patch), float32 products unless fp64 (yy_scan.cu)
 cudaError_t rotate_moments(yy_grid *g, bool fp64, cudaStream_t s);
-// radial scans (yy_scan.cu): Atot -> Q (and Q32 if want_f32)
+// radial scans (yy_scan.cu): Atot -> Q (and Q32 if want_f32); f64_out: output
+// factors applied in float64 (else in fp32, for the reduced-precision forms)
 void scan_geometry(const yy_grid *g, int *nc, int *ch);
-cudaError_t radial_scan(yy_grid *g, bool want_f32, cudaStream_t s);
+cudaError_t radial_scan(yy_grid *g, bool want_f32, bool f64_out, cudaStream_t s);
 
 // tensor-core path (yy_tc.cu)
 yy_status tc_prepare(yy_grid *g, yy_precision prec);

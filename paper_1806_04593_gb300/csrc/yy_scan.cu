@@ -20,13 +20,15 @@
 //   Q   = -G 4 pi/(2l+1) (c_n + d_n)                         -> Phi
 //   Q_r =  G 4 pi/(2l+1) (-(l+1) c_n + l d_n) / r_{n+1}      -> g_r
 //   Q_t =  G 4 pi/(2l+1) (c_n + d_n) / r_{n+1}               -> g_theta, g_phi
+#include <algorithm>
+
 #include "yy_internal.h"
 
 namespace yy {
 namespace {
 
 __device__ __forceinline__ int mode_degree(int idx) {
-  int l = (int)sqrt((double)idx);
+  int l = (int)sqrtf((float)idx);   // corrected below; exact for idx < 2^24
   while (l * l > idx) --l;
   while ((l + 1) * (l + 1) <= idx) ++l;
   return l;
@@ -43,6 +45,22 @@ __device__ __forceinline__ float to_f32(double x) {
   const unsigned int up = (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) ? 1u : 0u;
   return __uint_as_float((hi & 0x80000000u) | (((unsigned int)e32 << 23) + m23 + up));
 }
+
+// exact float32 -> float64 widening by integer operations
+__device__ __forceinline__ double to_f64(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int ex = (u >> 23) & 0xFFu;
+  if (ex == 0u || ex == 255u) {
+    if ((u << 1) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    return (double)f;
+  }
+  const unsigned int hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+struct __align__(32) Map4 {
+  double a_in, b_in, a_out, b_out;   // inner c -> a_in c + b_in, outer d -> a_out d + b_out
+};
 
 struct ScanGeom {
   int n_r, lmax, n_lm, nc, ch, wpp;   // chunks, chunk length, warps per patch and chunk
@@ -62,7 +80,7 @@ __device__ __forceinline__ bool scan_lane(const ScanGeom &s, int &p, int &idx, i
 }
 
 __global__ void __launch_bounds__(128)
-k_scan_maps(ScanGeom s, const double *__restrict__ A, const double *__restrict__ coef, double4 *__restrict__ maps) {
+k_scan_maps(ScanGeom s, const double *__restrict__ A, const double *__restrict__ coef, Map4 *__restrict__ maps) {
   int p, idx, c, n0, n1;
   if (!scan_lane(s, p, idx, c, n0, n1)) return;
   const int l = mode_degree(idx);
@@ -80,27 +98,27 @@ k_scan_maps(ScanGeom s, const double *__restrict__ A, const double *__restrict__
     bo = fma(k[2], bo, k[3] * an);
     ao *= k[2];
   }
-  maps[((size_t)p * s.nc + c) * s.n_lm + idx] = make_double4(ai, bi, ao, bo);
+  maps[((size_t)p * s.nc + c) * s.n_lm + idx] = Map4{ai, bi, ao, bo};
 }
 
 __global__ void __launch_bounds__(128)
 k_scan_apply(ScanGeom s, const double *__restrict__ A, const double *__restrict__ coef,
-             const double4 *__restrict__ maps, double *__restrict__ cin, double *__restrict__ Q,
+             const Map4 *__restrict__ maps, double *__restrict__ cin, double *__restrict__ Q,
              float *__restrict__ Q32) {
   int p, idx, c, n0, n1;
   if (!scan_lane(s, p, idx, c, n0, n1)) return;
   const int l = mode_degree(idx);
   const int L1 = s.lmax + 1;
-  const double4 *mp = maps + (size_t)p * s.nc * s.n_lm + idx;
+  const Map4 *mp = maps + (size_t)p * s.nc * s.n_lm + idx;
   double x = 0.0;                       // c_{n0 - 1}
   for (int k = 0; k < c; ++k) {
-    const double4 m = mp[(size_t)k * s.n_lm];
-    x = fma(m.x, x, m.y);
+    const Map4 m = mp[(size_t)k * s.n_lm];
+    x = fma(m.a_in, x, m.b_in);
   }
   double y = 0.0;                       // d_{n1 - 1} comes from the chunks above
   for (int k = s.nc - 1; k > c; --k) {
-    const double4 m = mp[(size_t)k * s.n_lm];
-    y = fma(m.z, y, m.w);
+    const Map4 m = mp[(size_t)k * s.n_lm];
+    y = fma(m.a_out, y, m.b_out);
   }
   const double *Ap = A + (size_t)p * s.n_r * s.n_lm + idx;
   double *Cp = cin + (size_t)p * s.n_r * s.n_lm + idx;
@@ -138,30 +156,175 @@ k_scan_apply(ScanGeom s, const double *__restrict__ A, const double *__restrict_
 //   Atot[p][n][j] = A[p][n][j] + sum_i D^l_ij A[1-p][n][i],  i, j of degree l.
 // The scans and the synthesis are linear and act on each degree alone, so this
 // gives the same potential as summing four separate ones.  One block per
-// radius; T is the type of the products (float64, or float32 with a float64
-// sum onto the own-patch moment).
+// radius and one thread per mode j, both patches at once (each D entry is
+// loaded once for the two sums).  T is the type of the products: float64, or
+// float32 (the moments rounded once, the sum added to the float64 own moment).
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024)
 k_rotate_moments(int n_r, int n_lm, const T *__restrict__ rot, const double *__restrict__ A,
                  double *__restrict__ Atot) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T *a = reinterpret_cast<T *>(smraw);   // [2][n_lm]
   const int n = blockIdx.x;
-  for (int e = threadIdx.x; e < 2 * n_lm; e += blockDim.x) {
-    const int p = e / n_lm, j = e % n_lm;
-    a[e] = (T)A[((size_t)p * n_r + n) * n_lm + j];
+  const double *A0 = A + (size_t)n * n_lm, *A1 = A + ((size_t)n_r + n) * n_lm;
+  for (int j = threadIdx.x; j < n_lm; j += blockDim.x) {
+    if constexpr (sizeof(T) == 4) {
+      a[j] = to_f32(A0[j]);
+      a[n_lm + j] = to_f32(A1[j]);
+    } else {
+      a[j] = A0[j];
+      a[n_lm + j] = A1[j];
+    }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < 2 * n_lm; e += blockDim.x) {
-    const int p = e / n_lm, j = e % n_lm;
+  for (int j = threadIdx.x; j < n_lm; j += blockDim.x) {
     const int l = mode_degree(j);
     const int w = 2 * l + 1, jj = j - l * l;
     const T *D = rot + (size_t)l * (4 * l * l - 1) / 3 + jj;
-    const T *x = a + (1 - p) * n_lm + l * l;
-    T acc = 0;
-    for (int i = 0; i < w; ++i) acc = fma(D[(size_t)i * w], x[i], acc);
-    const size_t o = ((size_t)p * n_r + n) * n_lm + j;
-    Atot[o] = A[o] + (double)acc;
+    const T *x0 = a + l * l, *x1 = a + n_lm + l * l;
+    T s0 = 0, s1 = 0;   // into patch 0 (from patch 1) and into patch 1 (from patch 0)
+#pragma unroll 4
+    for (int i = 0; i < w; ++i) {
+      const T d = D[(size_t)i * w];
+      s0 = fma(d, x1[i], s0);
+      s1 = fma(d, x0[i], s1);
+    }
+    double r0, r1;
+    if constexpr (sizeof(T) == 4) {
+      r0 = to_f64(s0);
+      r1 = to_f64(s1);
+    } else {
+      r0 = s0;
+      r1 = s1;
+    }
+    Atot[(size_t)n * n_lm + j] = A0[j] + r0;
+    Atot[((size_t)n_r + n) * n_lm + j] = A1[j] + r1;
+  }
+}
+
+// Radial scans with one warp per (patch, mode): lane L owns the radii
+// [L ch, L ch + ch), ch = ceil(n_r / 32) <= CH, and keeps its moments and inner
+// sums in registers.  Each recurrence is folded into one affine map per lane,
+// the maps are composed across the warp by shuffles (prefix for the inner
+// sums, suffix for the outer ones), and each lane then replays its radii from
+// the composed start value.  Steps past n_r use the identity map, and every
+// load is unconditional (clamped index) so that no load waits behind the
+// float64 chain.  F64OUT: output factors applied in float64; otherwise (the
+// reduced-precision paths, whose packing rounds Q to fp32 anyway) in fp32
+// from fp32 roundings of c_n and d_n, widened back exactly.
+template <int CH, bool F64OUT>
+__global__ void __launch_bounds__(128)
+k_scan_warp(int n_r, int lmax, int n_lm, const double *__restrict__ A, const double *__restrict__ coef,
+            double *__restrict__ Q, float *__restrict__ Q32) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= 2 * n_lm) return;
+  const int p = w / n_lm, j = w % n_lm;
+  const int l = mode_degree(j);
+  const int L1 = lmax + 1;
+  const int ch = (n_r + 31) / 32;
+  const int n0 = lane * ch;
+  const double *Ap = A + (size_t)p * n_r * n_lm + j;
+  const double *cl = coef + (size_t)l * 8;          // + n L1 8
+  const size_t cstride = (size_t)L1 * 8;
+  double av[CH], cv[CH];
+#pragma unroll
+  for (int i = 0; i < CH; ++i) {
+    const int n = min(n0 + i, n_r - 1);
+    const double v = Ap[(size_t)n * n_lm];
+    av[i] = (i < ch && n0 + i < n_r) ? v : 0.0;
+  }
+  // A_{n0 + ch}: first moment of the next lane's radii
+  double a_next = __shfl_down_sync(0xffffffffu, av[0], 1);
+  if (lane == 31) a_next = 0.0;
+
+  // inner sums c_n = a_n c_{n-1} + b_n A_n
+  double al = 1.0, be = 0.0;
+#pragma unroll
+  for (int i = 0; i < CH; ++i) {
+    const bool ok = i < ch && n0 + i < n_r;
+    const double2 k01 = *(const double2 *)(cl + (size_t)min(n0 + i, n_r - 1) * cstride);
+    const double a = ok ? k01.x : 1.0, b = ok ? k01.y : 0.0;
+    be = fma(a, be, b * av[i]);
+    al *= a;
+  }
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const double ao = __shfl_up_sync(0xffffffffu, al, off);
+    const double bo = __shfl_up_sync(0xffffffffu, be, off);
+    if (lane >= off) {
+      be = fma(al, bo, be);
+      al *= ao;
+    }
+  }
+  double x = __shfl_up_sync(0xffffffffu, be, 1);
+  if (lane == 0) x = 0.0;
+#pragma unroll
+  for (int i = 0; i < CH; ++i) {
+    const bool ok = i < ch && n0 + i < n_r;
+    const double2 k01 = *(const double2 *)(cl + (size_t)min(n0 + i, n_r - 1) * cstride);
+    const double a = ok ? k01.x : 1.0, b = ok ? k01.y : 0.0;
+    x = fma(a, x, b * av[i]);
+    cv[i] = x;
+  }
+
+  // outer sums d_n = e_n d_{n+1} + f_n A_{n+1}, d_{n_r - 1} = 0
+  al = 1.0;
+  be = 0.0;
+#pragma unroll
+  for (int i = CH - 1; i >= 0; --i) {
+    const bool ok = i < ch && n0 + i < n_r;
+    const double an = (i + 1 < ch) ? av[i + 1 < CH ? i + 1 : i] : a_next;   // 0 past n_r
+    const double2 k23 = *(const double2 *)(cl + (size_t)min(n0 + i, n_r - 1) * cstride + 2);
+    const double e = ok ? k23.x : 1.0, f = ok ? k23.y : 0.0;
+    be = fma(e, be, f * an);
+    al *= e;
+  }
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const double ao = __shfl_down_sync(0xffffffffu, al, off);
+    const double bo = __shfl_down_sync(0xffffffffu, be, off);
+    if (lane + off < 32) {
+      be = fma(al, bo, be);
+      al *= ao;
+    }
+  }
+  double y = __shfl_down_sync(0xffffffffu, be, 1);
+  if (lane == 31) y = 0.0;
+  const size_t qsz = (size_t)2 * n_r * n_lm;
+#pragma unroll
+  for (int i = CH - 1; i >= 0; --i) {
+    const bool ok = i < ch && n0 + i < n_r;
+    const double an = (i + 1 < ch) ? av[i + 1 < CH ? i + 1 : i] : a_next;
+    const double *k = cl + (size_t)min(n0 + i, n_r - 1) * cstride;
+    const double2 k23 = *(const double2 *)(k + 2);
+    const double e = ok ? k23.x : 1.0, f = ok ? k23.y : 0.0;
+    y = fma(e, y, f * an);
+    if (!ok) continue;
+    const size_t o = ((size_t)p * n_r + n0 + i) * n_lm + j;
+    const double cn = cv[i];
+    if constexpr (F64OUT) {
+      const double2 k45 = *(const double2 *)(k + 4);
+      const double2 k67 = *(const double2 *)(k + 6);
+      const double sum = cn + y;
+      const double q = k45.x * sum, qr = fma(k45.y, cn, k67.x * y), qt = k67.y * sum;
+      Q[o] = q;
+      Q[qsz + o] = qr;
+      Q[2 * qsz + o] = qt;
+      if (Q32 != nullptr) {
+        Q32[o] = to_f32(q);
+        Q32[qsz + o] = to_f32(qr);
+        Q32[2 * qsz + o] = to_f32(qt);
+      }
+    } else {
+      const double2 k45 = *(const double2 *)(k + 4);
+      const double2 k67 = *(const double2 *)(k + 6);
+      const float cf = to_f32(cn), yf = to_f32(y);
+      const float sum = cf + yf;
+      Q[o] = to_f64(to_f32(k45.x) * sum);
+      Q[qsz + o] = to_f64(fmaf(to_f32(k45.y), cf, to_f32(k67.x) * yf));
+      Q[2 * qsz + o] = to_f64(to_f32(k67.y) * sum);
+    }
   }
 }
 
@@ -176,10 +339,11 @@ cudaError_t rotate_moments(yy_grid *g, bool fp64, cudaStream_t st) {
                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
+  const int threads = std::min(1024, (g->n_lm + 31) / 32 * 32);
   if (fp64)
-    k_rotate_moments<double><<<g->n_r, 256, smem, st>>>(g->n_r, g->n_lm, g->rot, g->A, g->Atot);
+    k_rotate_moments<double><<<g->n_r, threads, smem, st>>>(g->n_r, g->n_lm, g->rot, g->A, g->Atot);
   else
-    k_rotate_moments<float><<<g->n_r, 256, smem, st>>>(g->n_r, g->n_lm, g->rot32, g->A, g->Atot);
+    k_rotate_moments<float><<<g->n_r, threads, smem, st>>>(g->n_r, g->n_lm, g->rot32, g->A, g->Atot);
   g->launches++;
   return cudaGetLastError();
 }
@@ -192,7 +356,26 @@ void scan_geometry(const yy_grid *g, int *nc, int *ch) {
   *nc = (g->n_r + *ch - 1) / *ch;
 }
 
-cudaError_t radial_scan(yy_grid *g, bool want_f32, cudaStream_t st) {
+cudaError_t radial_scan(yy_grid *g, bool want_f32, bool f64_out, cudaStream_t st) {
+  float *q32 = want_f32 ? g->Q32 : nullptr;
+  const unsigned wblocks = (unsigned)((2 * g->n_lm * 32 + 127) / 128);
+  if (g->n_r <= 32 * 24) {
+#define YY_SCAN_WARP(CH)                                                                               \
+  (f64_out ? (k_scan_warp<CH, true><<<wblocks, 128, 0, st>>>(g->n_r, g->lmax, g->n_lm, g->Atot, g->scan, g->Q, q32), 0) \
+           : (k_scan_warp<CH, false><<<wblocks, 128, 0, st>>>(g->n_r, g->lmax, g->n_lm, g->Atot, g->scan, g->Q, q32), 0))
+    if (g->n_r <= 32 * 8)
+      YY_SCAN_WARP(8);
+    else if (g->n_r <= 32 * 12)
+      YY_SCAN_WARP(12);
+    else if (g->n_r <= 32 * 18)
+      YY_SCAN_WARP(18);
+    else
+      YY_SCAN_WARP(24);
+#undef YY_SCAN_WARP
+    g->launches++;
+    return cudaGetLastError();
+  }
+  // long radial grids: chunks spread over warps, two passes
   ScanGeom s;
   s.n_r = g->n_r;
   s.lmax = g->lmax;
@@ -201,9 +384,9 @@ cudaError_t radial_scan(yy_grid *g, bool want_f32, cudaStream_t st) {
   scan_geometry(g, &s.nc, &s.ch);
   const int warps = 2 * s.wpp * s.nc;
   const int blocks = (warps * 32 + 127) / 128;
-  k_scan_maps<<<blocks, 128, 0, st>>>(s, g->Atot, g->scan, (double4 *)g->scan_maps);
+  k_scan_maps<<<blocks, 128, 0, st>>>(s, g->Atot, g->scan, (Map4 *)g->scan_maps);
   g->launches++;
-  k_scan_apply<<<blocks, 128, 0, st>>>(s, g->Atot, g->scan, (const double4 *)g->scan_maps, g->cin, g->Q,
+  k_scan_apply<<<blocks, 128, 0, st>>>(s, g->Atot, g->scan, (const Map4 *)g->scan_maps, g->cin, g->Q,
                                        want_f32 ? g->Q32 : nullptr);
   g->launches++;
   return cudaGetLastError();

@@ -55,7 +55,7 @@ k_radial_scan_static(int n_r, int lmax, int n_lm, double G, const double *__rest
   const int lane = threadIdx.x & 31;
   if (warp >= 2 * n_lm) return;
   const int p = warp / n_lm, idx = warp % n_lm;
-  int l = (int)sqrt((double)idx);
+  int l = (int)sqrtf((float)idx);   // corrected below; exact for idx < 2^24
   while (l * l > idx) --l;
   while ((l + 1) * (l + 1) <= idx) ++l;
   const int CH = (n_r + 31) / 32;

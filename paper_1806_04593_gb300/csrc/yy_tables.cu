@@ -207,7 +207,7 @@ __global__ void k_tbar(int n_theta, int lmax, int n_lm, double th0, double dth,
 }
 
 __device__ __forceinline__ void mode_lm(int idx, int &l, int &m, bool &is_sin) {
-  l = (int)sqrt((double)idx);
+  l = (int)sqrtf((float)idx);   // corrected below; exact for idx < 2^24
   while (l * l > idx) --l;
   while ((l + 1) * (l + 1) <= idx) ++l;
   const int r = idx - l * l;

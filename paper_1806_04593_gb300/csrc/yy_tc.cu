@@ -1,9 +1,10 @@
 // Tensor-core (tcgen05) forms of the two contractions of the solver:
 //   analysis   A[2 n_r][n_lm]    = rho . B_an^T   (§3 Eqs. ac/as with the §4 weights)
-//   synthesis  Phi[2 n_r][n_ang] = Q . Y^T        (§4 sum of the four potentials)
+//   synthesis  Phi[2 n_r][n_ang] = Q . Y^T        (§4 sum of the four potentials,
+//                                                  with combined coefficients)
 //
 // Operands are float64 on entry.  Each is split into pieces of a narrower
-// type with a power-of-two scale per row (A) or per column (B):
+// type with a power-of-two scale per row:
 //   FP16X2  x = s (h + l), h, l fp16;        products h.h + h.l + l.h
 //   BF16X3  x = s (h + m + l), bf16;         products hh hm mh hl lh mm
 //   TF32    x = s t, t tf32 (round to nearest);  one product
@@ -21,10 +22,12 @@
 // so the packing, reduction and epilogue code uses fp32 arithmetic and
 // exact integer conversions between fp32 and float64.
 //
-// Kernel layout (persistent, 10 warps per CTA, one CTA per SM):
-//   warp 0  lane 0: TMA producer over a ring of STAGES shared-memory stages
-//   warp 1  allocates TMEM; lane 0 issues the MMAs and the commits
-//   warps 2-9: epilogue, TMEM lanes 32 (w % 4) .. + 31, alternate column chunks
+// Both contractions run on one persistent kernel over pairs of CTAs
+// (clusters of two, one CTA per SM, M = 256 per MMA, cta_group::2):
+//   warp 0  lane 0: TMA producer over a ring of shared-memory stages
+//   warp 1  allocates TMEM (both CTAs); in the even CTA lane 0 issues the
+//           MMAs and the commits
+//   warps 2-17: epilogue, TMEM lanes 32 (w % 4) .. + 31, 16-column chunks
 // Every mbarrier wait gives up after ~2 s, sets the device error word and
 // lets the CTA finish (TMEM is always released).
 #include <cuda.h>
@@ -51,7 +54,7 @@ enum { KIND_F16 = 0, KIND_BF16 = 1, KIND_TF32 = 2 };
 
 struct FormFP16x2 {
   typedef __half elem;
-  static constexpr int kKind = KIND_F16, kElem = 2, kPA = 2, kPB = 2, kPairs = 3, kBN = 256, kStages = 4;
+  static constexpr int kKind = KIND_F16, kElem = 2, kPA = 2, kPB = 2, kPairs = 3;
   static constexpr int kPairStages = 6;
   __host__ __device__ static constexpr int pa(int i) { return i == 2 ? 1 : 0; }
   __host__ __device__ static constexpr int pb(int i) { return i == 1 ? 1 : 0; }
@@ -59,7 +62,7 @@ struct FormFP16x2 {
 
 struct FormBF16x3 {
   typedef __nv_bfloat16 elem;
-  static constexpr int kKind = KIND_BF16, kElem = 2, kPA = 3, kPB = 3, kPairs = 6, kBN = 128, kStages = 4;
+  static constexpr int kKind = KIND_BF16, kElem = 2, kPA = 3, kPB = 3, kPairs = 6;
   static constexpr int kPairStages = 4;
   // (0,0) (0,1) (1,0) (0,2) (2,0) (1,1)
   __host__ __device__ static constexpr int pa(int i) { return i == 2 ? 1 : (i == 4 ? 2 : (i == 5 ? 1 : 0)); }
@@ -68,31 +71,19 @@ struct FormBF16x3 {
 
 struct FormTF32 {
   typedef float elem;
-  static constexpr int kKind = KIND_TF32, kElem = 4, kPA = 1, kPB = 1, kPairs = 1, kBN = 256, kStages = 8;
+  static constexpr int kKind = KIND_TF32, kElem = 4, kPA = 1, kPB = 1, kPairs = 1;
   static constexpr int kPairStages = 12;
   __host__ __device__ static constexpr int pa(int) { return 0; }
   __host__ __device__ static constexpr int pb(int) { return 0; }
 };
 
-constexpr int kBM = 128;
 constexpr int kRowBytes = 64;        // K bytes per tile row and stage: one 64-byte swizzle atom
 constexpr int kPadK = 64;            // K padding (elements) of every packed operand
-constexpr int kBChunk = 32;          // rows of one B box when clusters share B tiles
 constexpr double kY00 = 0.28209479177387814347403972578039;   // K_00 P_0^0 = 1/sqrt(4 pi)
 
-template <class F>
-constexpr int stage_bytes() {
-  return F::kPA * kBM * kRowBytes + F::kPB * F::kBN * kRowBytes;
-}
 constexpr int kEpiWarps = 16;        // four epilogue warps per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kEpiCols = 16;         // columns per TMEM load / staged fragment
-constexpr int kStgBytes = kEpiWarps * 32 * kEpiCols * 4;   // one 32 x 16 fp32 fragment per epilogue warp
-
-template <class F>
-constexpr int smem_bytes() {
-  return F::kStages * stage_bytes<F>() + kStgBytes + 1024 /*align*/ + 256 /*barriers*/;
-}
+constexpr int kEpiCols = 16;         // columns per TMEM load
 
 // CTA-pair synthesis kernel: per CTA 128 rows of A and up to 128 rows of B
 // (half of the pair's N) in every stage.
@@ -128,10 +119,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
 __device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -165,25 +152,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
   }
 }
 
-__device__ __forceinline__ void tma_load_2d(const CUtensorMap *map, uint32_t dst, uint64_t *bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-          dst),
-      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-// Multicast variant: the same shared-memory offset and barrier in every CTA
-// of the cluster named by the mask receive the box.
-__device__ __forceinline__ void tma_load_2d_mc(const CUtensorMap *map, uint32_t dst, uint64_t *bar, int x, int y,
-                                               uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%4, %5}], [%2], %3;" ::"r"(dst),
-      "l"((uint64_t)map), "r"(smem_u32(bar)), "h"(mask), "r"(x), "r"(y)
-      : "memory");
-}
-
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -198,16 +166,6 @@ __device__ __forceinline__ void cluster_sync() {
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t base, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols) : "memory");
-}
-
 // Shared-memory matrix descriptor: K-major, 64-byte swizzle (layout type 4),
 // 8-row groups 512 bytes apart (stride byte offset), descriptor version 1.
 // The tile base must be 512-byte aligned; advancing K by 32 bytes inside the
@@ -215,56 +173,6 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t base, uint32_t ncols) {
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
-}
-
-// Instruction descriptor: fp32 accumulator, A/B format, both K-major, N, M = 128.
-template <class F>
-__host__ __device__ constexpr uint32_t instr_desc() {
-  return (1u << 4) | ((uint32_t)F::kKind << 7) | ((uint32_t)F::kKind << 10) | ((uint32_t)(F::kBN >> 3) << 17) |
-         ((uint32_t)(kBM >> 4) << 24);
-}
-
-template <class F>
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  if constexpr (F::kKind == KIND_TF32) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-  }
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // 16 columns of this warp's 32 TMEM lanes, without waiting (tmem_wait_ld).
@@ -278,16 +186,6 @@ __device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&v)[16
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
 // ---- CTA-pair (cta_group::2) forms -------------------------------------
 //
@@ -420,244 +318,15 @@ __device__ __forceinline__ float f64_to_f32(double x) {
 }
 
 // ---------------------------------------------------------------------------
-// the contraction kernel
-// ---------------------------------------------------------------------------
-
-struct TcArgs {
-  int M, N;              // valid output rows / columns
-  int kb_total;          // K blocks (kRowBytes per row) in the packed operands
-  int kb_per_tile;       // K blocks per tile (the K split)
-  int m_tiles, n_tiles, k_splits;   // tile space, M fastest, then N, then K split
-  int a_rows, b_rows;    // rows of one piece in the stacked A / B operands
-  int mode;              // 0: fp32 partials [z][M][N]; 1: float64 output
-  float *part;
-  double *out0, *out1;   // rows < out_split -> out0, others -> out1
-  int out_split;
-  long long ldo;
-  const float *row_scale, *col_scale, *row_add;   // powers of two / fp32 monopole term
-  int *err;
-};
-
-// Persistent.  CTAs form clusters of C (C = 1 or 3) along M: the C CTAs of a
-// cluster compute C vertically adjacent 128 x BN tiles that share one B tile,
-// and each loads 1/C of that B tile (32-row chunks r, r + C, ...) with TMA
-// multicast into the shared memory of all C CTAs.  A consumer frees a stage
-// in all C CTAs at once (multicast tcgen05.commit), so each CTA's "empty"
-// barrier counts C arrivals.  Cluster c handles cluster tiles c,
-// c + #clusters, ...; the producer and the MMA issuer run ahead across tiles
-// through the shared-memory ring, and the accumulator is double-buffered in
-// TMEM (2 x BN columns) so the epilogue of one tile overlaps the MMAs of the
-// next.
-template <class F, int C>
-__global__ void __launch_bounds__(kThreads, 1)
-k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
-  constexpr int BN = F::kBN, S = F::kStages;
-  constexpr int A_TILE = kBM * kRowBytes, B_TILE = BN * kRowBytes;
-  constexpr int STAGE = stage_bytes<F>();
-  constexpr int KSTEP_BYTES = 32;                   // one MMA consumes 32 bytes of K per row
-  constexpr int KSTEPS = kRowBytes / KSTEP_BYTES;   // MMAs per K block and product
-  constexpr int BK = kRowBytes / F::kElem;          // elements of K per block
-  constexpr int BROWS = (C > 1) ? kBChunk : BN;     // rows per B load (one box without clusters)
-  constexpr int NCHUNK = BN / BROWS;
-  constexpr uint16_t MASK = (uint16_t)((1u << C) - 1u);
-
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float *staging = (float *)(smem + S * STAGE);   // [kEpiWarps][32][kEpiCols], XOR-swizzled columns
-  uint64_t *full = (uint64_t *)(smem + S * STAGE + kStgBytes);
-  uint64_t *empty = full + S;
-  uint64_t *tfull = empty + S;      // [2]
-  uint64_t *tempty = tfull + 2;     // [2]
-  uint32_t *tmem_slot = (uint32_t *)(tempty + 2);
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rank = (C > 1) ? (int)cluster_rank() : 0;
-  const int cluster = (int)blockIdx.x / C, n_clusters = (int)gridDim.x / C;
-  const int m_groups = a.m_tiles / C;
-  const int total = m_groups * a.n_tiles * a.k_splits;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], C);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], kEpiWarps);
-    }
-    fence_barrier_init();
-  }
-  if (warp == 1) {
-    tmem_alloc(tmem_slot, 2 * BN);
-    tc_fence_before();
-  }
-  __syncthreads();
-  if constexpr (C > 1) cluster_sync();   // peers' barriers exist before any multicast
-  tc_fence_after();
-  const uint32_t tmem_base = *tmem_slot;
-
-  if (warp == 0) {
-    if (lane == 0) {
-      int gk = 0;
-      bool ok = true;
-      for (int t = cluster; t < total && ok; t += n_clusters) {
-        const int mt = (t % m_groups) * C + rank;
-        const int nt = (t / m_groups) % a.n_tiles, z = t / (m_groups * a.n_tiles);
-        const int kb0 = z * a.kb_per_tile;
-        const int nkb = min(a.kb_total, kb0 + a.kb_per_tile) - kb0;
-        for (int i = 0; i < nkb; ++i, ++gk) {
-          const int s = gk % S;
-          if (gk >= S && !mbar_wait(&empty[s], ((gk / S) & 1) ^ 1, a.err)) {
-            ok = false;
-            break;
-          }
-          mbar_expect_tx(&full[s], STAGE);
-          const uint32_t base = smem_u32(smem + s * STAGE);
-          const int kx = (kb0 + i) * BK;
-#pragma unroll
-          for (int p = 0; p < F::kPA; ++p)
-            tma_load_2d(&tmA, base + p * A_TILE, &full[s], kx, p * a.a_rows + mt * kBM);
-#pragma unroll
-          for (int p = 0; p < F::kPB; ++p) {
-            const uint32_t bdst = base + F::kPA * A_TILE + p * B_TILE;
-            const int brow = p * a.b_rows + nt * BN;
-            for (int c = rank; c < NCHUNK; c += C) {
-              if constexpr (C > 1)
-                tma_load_2d_mc(&tmB, bdst + c * BROWS * kRowBytes, &full[s], kx, brow + c * BROWS, MASK);
-              else
-                tma_load_2d(&tmB, bdst + c * BROWS * kRowBytes, &full[s], kx, brow + c * BROWS);
-            }
-          }
-        }
-      }
-      // every stage's last use must be released by all C consumers before
-      // this CTA may leave (peers' commits still land on our barriers)
-      if (ok)
-        for (int i = max(0, gk - S); i < gk; ++i)
-          if (!mbar_wait(&empty[i % S], (i / S) & 1, a.err)) break;
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      constexpr uint32_t idesc = instr_desc<F>();
-      int gk = 0, it = 0;
-      bool ok = true;
-      for (int t = cluster; t < total && ok; t += n_clusters, ++it) {
-        const int b = it & 1;
-        if (it >= 2) {
-          if (!mbar_wait(&tempty[b], ((it >> 1) & 1) ^ 1, a.err)) break;
-          tc_fence_after();
-        }
-        const int z = t / (m_groups * a.n_tiles);
-        const int kb0 = z * a.kb_per_tile;
-        const int nkb = min(a.kb_total, kb0 + a.kb_per_tile) - kb0;
-        const uint32_t dacc = tmem_base + (uint32_t)(b * BN);
-        for (int i = 0; i < nkb; ++i, ++gk) {
-          const int s = gk % S;
-          if (!mbar_wait(&full[s], (gk / S) & 1, a.err)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t sa = smem_u32(smem + s * STAGE);
-          const uint32_t sb = sa + F::kPA * A_TILE;
-#pragma unroll
-          for (int q = 0; q < F::kPairs; ++q) {
-#pragma unroll
-            for (int kk = 0; kk < KSTEPS; ++kk) {
-              const uint64_t da = smem_desc(sa + F::pa(q) * A_TILE + kk * KSTEP_BYTES);
-              const uint64_t db = smem_desc(sb + F::pb(q) * B_TILE + kk * KSTEP_BYTES);
-              mma<F>(dacc, da, db, idesc, (i | q | kk) != 0 ? 1u : 0u);
-            }
-          }
-          if constexpr (C > 1)
-            mma_commit_mc(&empty[s], MASK);
-          else
-            mma_commit(&empty[s]);
-        }
-        if (ok) mma_commit(&tfull[b]);
-      }
-    }
-  } else {
-    // epilogue: TMEM lane quarter of this warp; the four warps of a quarter
-    // take alternate 16-column chunks.  Each 32 x 16 fragment is scaled in
-    // fp32 (lane = row), staged in shared memory, and written out as row
-    // segments by the whole warp (half-warp = row, lane = column), so the
-    // global stores are coalesced.
-    const int quarter = warp & 3;
-    const int sub = (warp - 2) >> 2;                    // 0..3 within the quarter
-    float *stg = staging + (warp - 2) * 32 * kEpiCols;
-    int it = 0;
-    for (int t = cluster; t < total; t += n_clusters, ++it) {
-      const int b = it & 1;
-      if (!mbar_wait(&tfull[b], (it >> 1) & 1, a.err)) break;
-      tc_fence_after();
-      const int mt = (t % m_groups) * C + rank;
-      const int nt = (t / m_groups) % a.n_tiles, z = t / (m_groups * a.n_tiles);
-      const int row0 = mt * kBM + quarter * 32;          // first row of this warp's fragment
-      const int myrow = row0 + lane;
-      float rs = 1.0f, ra = 0.0f;
-      unsigned long long optr = 0ull;                    // this lane's output row (mode 1)
-      if (a.mode == 1 && myrow < a.M) {
-        rs = a.row_scale[myrow];
-        ra = a.row_add[myrow];
-        optr = (unsigned long long)((myrow < a.out_split) ? a.out0 + (size_t)myrow * a.ldo
-                                                          : a.out1 + (size_t)(myrow - a.out_split) * a.ldo);
-      }
-#pragma unroll 1
-      for (int c0 = kEpiCols * sub; c0 < BN; c0 += kEpiCols * (kEpiWarps / 4)) {
-        uint32_t v[16];
-        tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0), v);
-        const int colbase = nt * BN + c0;
-        // column scales of this chunk, one per lane of the lower half-warp
-        float csl = 0.0f;
-        if (a.mode == 1 && lane < kEpiCols && colbase + lane < a.N) csl = a.col_scale[colbase + lane];
-#pragma unroll
-        for (int j = 0; j < kEpiCols; ++j) {
-          const float cs = __shfl_sync(0xffffffffu, csl, j);
-          const float x = __uint_as_float(v[j]);
-          const float y = (a.mode == 1) ? fmaf(x * rs, cs, ra) : x;
-          stg[lane * kEpiCols + (j ^ (lane & 15))] = y;
-        }
-        __syncwarp();
-        const int hl = lane >> 4, cl = lane & 15;
-        const int col = colbase + cl;
-        const bool col_ok = col < a.N;
-#pragma unroll 4
-        for (int r = 0; r < 32; r += 2) {
-          const int rr = r + hl;                          // row of this half-warp
-          const int row = row0 + rr;
-          const float y = stg[rr * kEpiCols + (cl ^ (rr & 15))];
-          if (a.mode == 0) {
-            if (row < a.M && col_ok) a.part[((size_t)z * a.M + row) * a.N + col] = y;
-          } else {
-            const unsigned long long rp = __shfl_sync(0xffffffffu, optr, rr);
-            if (row < a.M && col_ok) ((double *)rp)[col] = f32_to_f64(y);
-          }
-        }
-        __syncwarp();
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[b]);
-    }
-  }
-  __syncthreads();
-  if constexpr (C > 1) cluster_sync();   // no CTA leaves while peers may still reach its barriers
-  if (warp == 1) {
-    tc_fence_after();
-    tmem_dealloc(tmem_base, 2 * BN);
-  }
-}
-
-
-// ---------------------------------------------------------------------------
 // the synthesis kernel: CTA pairs, M = 256 cells x N = bn coefficient rows
 // ---------------------------------------------------------------------------
 //
 // out[row][cell] = (sum_k Y[cell][k] Q[row][k]) cell_scale[cell] row_scale[row] + row_add[row]
 // with Y a packed table (operand A, one row per cell) and Q packed
 // coefficients (operand B), for up to four jobs (Phi, g_r, g_theta, g_phi)
-// in one launch.  Clusters of two CTAs; pair p handles tiles p, p + #pairs,
+// in one launch.  The analysis uses the same kernel with the analysis table
+// as A (one row per mode), the densities as B, K split over tiles, and raw
+// fp32 partial sums as output (out_mode 0).  Clusters of two CTAs; pair p handles tiles p, p + #pairs,
 // ... of the job-major tile list (coefficient-row tiles fastest, so the
 // pairs working at the same time share table tiles in L2).  Per stage each CTA loads its 128
 // table rows and its bn / 2 coefficient rows; both CTAs' loads complete on
@@ -674,10 +343,14 @@ struct PairJob {
 };
 
 struct PairArgs {
-  int cells, cell_tiles;        // valid cells; tiles of 256 cells
-  int rows, row_tiles, bn;      // valid coefficient rows; tiles of bn rows (multiple of 16, <= 256)
+  int cells, cell_tiles;        // valid A rows ("cells"); tiles of 256
+  int rows, row_tiles, bn;      // valid B rows; tiles of bn rows (multiple of 16, <= 256)
   int kb_total;                 // K blocks (kRowBytes per row)
-  int a_rows, b_rows;           // rows of one piece in the stacked A (table) / B (coefficient) operands
+  int k_splits, kb_per_split;   // K split of every tile
+  int a_rows, b_rows;           // rows of one piece in the stacked A / B operands
+  int out_mode;                 // 1: scaled float64 job outputs; 0: raw fp32 partial sums
+  float *part;                  // mode 0: part[(z rows + row) part_ld + cell]
+  int part_ld;
   int out_split;
   long long ldo;
   int n_jobs;
@@ -689,7 +362,7 @@ struct PairMaps {
   CUtensorMap a[3], b[3];       // tables (operand A), coefficient sets (operand B)
 };
 
-template <class F>
+template <class F, int OUT_MODE>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArgs a) {
   constexpr int S = F::kPairStages;
@@ -710,7 +383,7 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rank = (int)cluster_rank();
   const int pair = (int)blockIdx.x >> 1, n_pairs = (int)gridDim.x >> 1;
-  const int per_job = a.cell_tiles * a.row_tiles;
+  const int per_job = a.cell_tiles * a.row_tiles * a.k_splits;
   const int total = per_job * a.n_jobs;
   const int bh = a.bn >> 1;
 
@@ -741,12 +414,14 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
       bool ok = true;
       for (int t = pair; t < total && ok; t += n_pairs) {
         const int jb = t / per_job, tl = t % per_job;
-        const int rt = tl % a.row_tiles, ct = tl / a.row_tiles;
+        const int rt = tl % a.row_tiles, ct = (tl / a.row_tiles) % a.cell_tiles;
+        const int kb0 = (tl / (a.row_tiles * a.cell_tiles)) * a.kb_per_split;
+        const int nkb = min(a.kb_total, kb0 + a.kb_per_split) - kb0;
         const int arow = (2 * ct + rank) * kPairRows;
         const int brow = rt * a.bn + rank * bh;
         const CUtensorMap *tmA = &maps.a[a.job[jb].ta];
         const CUtensorMap *tmB = &maps.b[a.job[jb].tb];
-        for (int i = 0; i < a.kb_total; ++i, ++gk) {
+        for (int i = 0; i < nkb; ++i, ++gk) {
           const int s = gk % S;
           if (gk >= S && !mbar_wait(&empty[s], ((gk / S) & 1) ^ 1, a.err)) {
             ok = false;
@@ -755,7 +430,7 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
           if (rank == 0) mbar_expect_tx(&full[s], tx_bytes);
           const uint32_t fbar = mapa_rank(smem_u32(&full[s]), 0);
           const uint32_t base = smem_u32(smem + s * STAGE);
-          const int kx = i * BK;
+          const int kx = (kb0 + i) * BK;
 #pragma unroll
           for (int p = 0; p < F::kPA; ++p) tma_load_2d_pair(tmA, base + p * SLOT, fbar, kx, p * a.a_rows + arow);
 #pragma unroll
@@ -780,7 +455,10 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
           tc_fence_after();
         }
         const uint32_t dacc = tmem_base + (uint32_t)(b * 256);
-        for (int i = 0; i < a.kb_total; ++i, ++gk) {
+        const int tl = t % per_job;
+        const int kb0 = (tl / (a.row_tiles * a.cell_tiles)) * a.kb_per_split;
+        const int nkb = min(a.kb_total, kb0 + a.kb_per_split) - kb0;
+        for (int i = 0; i < nkb; ++i, ++gk) {
           const int s = gk % S;
           if (!mbar_wait_cluster(&full[s], (gk / S) & 1, a.err)) {
             ok = false;
@@ -817,16 +495,18 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
       const int b = it & 1;
       const PairJob &J = a.job[t / per_job];
       const int tl = t % per_job;
-      const int rt = tl % a.row_tiles, ct = tl / a.row_tiles;
+      const int rt = tl % a.row_tiles, ct = (tl / a.row_tiles) % a.cell_tiles;
+      const int z = tl / (a.row_tiles * a.cell_tiles);
+      constexpr bool scaled = OUT_MODE == 1;
       const int cell = (2 * ct + rank) * kPairRows + quarter * 32 + lane;
       const bool cell_ok = cell < a.cells;
-      const float cs = cell_ok ? J.cell_scale[cell] : 0.0f;
+      const float cs = (cell_ok && scaled) ? J.cell_scale[cell] : 0.0f;
       // lanes 0..15: scales of row (chunk i, lane) for chunk i = sub + 4 (i')
       float rsv[4], rav[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int row = rt * a.bn + (sub + 4 * i) * kEpiCols + (lane & 15);
-        const bool ok = (sub + 4 * i) < n_chunks && row < a.rows;
+        const bool ok = scaled && (sub + 4 * i) < n_chunks && row < a.rows;
         rsv[i] = ok ? J.row_scale[row] : 0.0f;
         rav[i] = ok ? J.row_add[row] : 0.0f;
       }
@@ -856,9 +536,13 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
             const int row = row0 + j;
             const float x = __uint_as_float(c == 0 ? v0[j] : v1[j]);
             if (row < a.rows && cell_ok) {
-              double *orow = (row < a.out_split) ? J.out0 + (size_t)row * a.ldo
-                                                 : J.out1 + (size_t)(row - a.out_split) * a.ldo;
-              orow[cell] = f32_to_f64(fmaf(x * cs, rs, ra));
+              if constexpr (scaled) {
+                double *orow = (row < a.out_split) ? J.out0 + (size_t)row * a.ldo
+                                                   : J.out1 + (size_t)(row - a.out_split) * a.ldo;
+                orow[cell] = f32_to_f64(fmaf(x * cs, rs, ra));
+              } else {
+                a.part[((size_t)z * a.rows + row) * a.part_ld + cell] = x;
+              }
             }
           }
         }
@@ -1287,31 +971,27 @@ static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 struct yy_tc_tables {
   yy_precision prec;
-  int sms;
-  int cluster;           // CTAs per cluster along M (1 or 3)
-  int max_clusters;      // co-resident clusters of the contraction kernel
-  // analysis
-  int an_rows_a, an_kpad, an_rows_b;      // M_pad, K_pad, N_pad
-  void *an_A, *an_B;
-  double *an_rs, *an_cs, *an_mono, *an_mean, *an_colsum;
+  int pair_slots;                         // co-resident CTA pairs of the contraction kernel
+  int bn, row_tiles, rows_pad;            // the 2 n_r rows (operand B) in tiles of bn
+  // analysis: table rows (modes) as operand A, densities as operand B
+  int an_kpad, an_modes_pad;
+  void *an_tab, *an_rho;
+  double *an_tabs, *an_rhos, *an_mono, *an_mean, *an_colsum;
   float *an_b0;                           // fp32 copy of the monopole row of the analysis table
-  float *part;
+  float *part;                            // split-K partial sums [split][2 n_r][n_lm]
   int an_splits, an_kb_per;
-  CUtensorMap an_mapA, an_mapB;
-  // synthesis (3 coefficient sets, 3 tables), CTA-pair kernel
-  int sy_kpad;
-  int sy_cells_pad, sy_cell_tiles;        // table rows (multiple of 256), tiles of 256 cells
-  int sy_bn, sy_row_tiles, sy_rows_pad;   // coefficient rows per tile, tiles, padded rows
-  int pair_slots;                         // co-resident CTA pairs
-  void *sy_q[3], *sy_tab[3];              // packed coefficients / tables
-  double *sy_qs[3], *sy_tabs[3];          // their scales (float64 copies)
+  yy::PairMaps an_maps;                   // a[0]: table, b[0]: densities
+  // synthesis: tables (cells) as operand A, coefficient sets as operand B
+  int sy_kpad, sy_cells_pad;
+  void *sy_q[3], *sy_tab[3];
+  double *sy_qs[3], *sy_tabs[3];          // scales (float64 copies)
   float *sy_qsf[3], *sy_tabsf[3], *sy_add[3];
-  yy::PairMaps sy_maps;                     // a: tables, b: coefficient sets
+  yy::PairMaps sy_maps;                   // a: tables, b: coefficient sets
 };
 
 namespace yy {
 
-// Rows up to this many values are cached in shared memory during packing.
+// Rows up to this many values are cached in shared memory by the two-pass packing.
 constexpr int kPackCacheMax = 16 * 1024 / 4;
 
 static size_t pack_smem(const PackBatch &b, int n) {
@@ -1348,104 +1028,89 @@ static cudaError_t launch_pack(PackBatch &b, int n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+static cudaLaunchConfig_t pair_config(int pairs, int smem, cudaStream_t s, cudaLaunchAttribute *attr) {
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * pairs);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+template <class F>
+static cudaError_t launch_pair(yy_grid *g, yy_tc_tables *t, const PairMaps &maps, const PairArgs &a, cudaStream_t s) {
+  const int tiles = a.cell_tiles * a.row_tiles * a.k_splits * a.n_jobs;
+  const int pairs = tiles < t->pair_slots ? tiles : t->pair_slots;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = pair_config(pairs, pair_smem_bytes<F>(), s, attr);
+  const cudaError_t e = a.out_mode == 1 ? cudaLaunchKernelEx(&cfg, k_tc_pair<F, 1>, maps, a)
+                                         : cudaLaunchKernelEx(&cfg, k_tc_pair<F, 0>, maps, a);
+  g->launches++;
+  return e;
+}
+
 template <class F>
 static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
   const int M = 2 * g->n_r;
-  cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, g->device);
-  for (int c : {1, 3}) {
-    auto kern = (c == 1) ? k_tc_gemm<F, 1> : k_tc_gemm<F, 3>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<F>()) != cudaSuccess)
-      return YY_ERR_NOT_SUPPORTED;
-  }
-  if (cudaFuncSetAttribute(k_tc_pair<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, pair_smem_bytes<F>()) !=
-      cudaSuccess)
+  if (cudaFuncSetAttribute(k_tc_pair<F, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, pair_smem_bytes<F>()) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_tc_pair<F, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pair_smem_bytes<F>()) !=
+          cudaSuccess)
     return YY_ERR_NOT_SUPPORTED;
   {
-    cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(2 * 64);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = pair_smem_bytes<F>();
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cudaLaunchConfig_t cfg = pair_config(64, pair_smem_bytes<F>(), 0, attr);
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, (void *)k_tc_pair<F>, &cfg) != cudaSuccess || n < 1) {
+    if (cudaOccupancyMaxActiveClusters(&n, (void *)k_tc_pair<F, 1>, &cfg) != cudaSuccess || n < 1) {
       cudaGetLastError();
       return YY_ERR_NOT_SUPPORTED;
     }
     t->pair_slots = n;
   }
-  // Clusters of 3 CTAs along M share B tiles by multicast.  Measured on the
-  // 1-degree grid they cut L2 reads but not the time per tile, and fewer
-  // clusters than SMs can be resident, so single CTAs are the default;
-  // YY_TC_CLUSTER=3 selects clusters (when M needs little extra padding).
-  const char *cenv = getenv("YY_TC_CLUSTER");
-  t->cluster = (cenv && atoi(cenv) == 3 && round_up(M, 3 * kBM) * 100 <= round_up(M, kBM) * 115) ? 3 : 1;
-  t->max_clusters = t->sms;
-  if (t->cluster == 3) {
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 3;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(3 * 64);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = smem_bytes<F>();
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, (void *)k_tc_gemm<F, 3>, &cfg) != cudaSuccess || n < 1) {
-      cudaGetLastError();
-      t->cluster = 1;
-    } else {
-      t->max_clusters = n;
-    }
-  }
-  t->an_rows_a = round_up(M, kBM * t->cluster);
+  // the 2 n_r rows: tiles of at most 256, each a multiple of 16
+  t->row_tiles = (M + 255) / 256;
+  t->bn = round_up((M + t->row_tiles - 1) / t->row_tiles, 16);
+  t->rows_pad = t->row_tiles * t->bn;
   t->an_kpad = round_up(g->n_ang, kPadK);
-  t->an_rows_b = round_up(g->n_lm, F::kBN);
+  t->an_modes_pad = round_up(g->n_lm, 2 * kPairRows);
   t->sy_kpad = round_up(g->n_lm, kPadK);
   t->sy_cells_pad = round_up(g->n_ang, 2 * kPairRows);
-  t->sy_cell_tiles = t->sy_cells_pad / (2 * kPairRows);
-  t->sy_row_tiles = (M + 255) / 256;
-  t->sy_bn = round_up((M + t->sy_row_tiles - 1) / t->sy_row_tiles, 16);
-  t->sy_rows_pad = t->sy_row_tiles * t->sy_bn;
+  // split K of the analysis: about two tiles per CTA pair
+  const int an_tiles = (t->an_modes_pad / (2 * kPairRows)) * t->row_tiles;
+  const int kb_total = t->an_kpad * F::kElem / kRowBytes;
+  int splits = (2 * t->pair_slots + an_tiles / 2) / an_tiles;
+  splits = splits < 1 ? 1 : (splits > kb_total ? kb_total : splits);
+  t->an_kb_per = (kb_total + splits - 1) / splits;
+  t->an_splits = (kb_total + t->an_kb_per - 1) / t->an_kb_per;
+
   cudaError_t e = cudaSuccess;
   auto A = [&](void **ptr, size_t bytes) {
     if (e == cudaSuccess) e = dmalloc(ptr, bytes);
   };
-  A(&t->an_A, (size_t)F::kPA * t->an_rows_a * t->an_kpad * F::kElem);
-  A(&t->an_B, (size_t)F::kPB * t->an_rows_b * t->an_kpad * F::kElem);
-  A((void **)&t->an_rs, t->an_rows_a * sizeof(double));
-  A((void **)&t->an_cs, t->an_rows_b * sizeof(double));
-  A((void **)&t->an_mono, t->an_rows_a * sizeof(double));
-  A((void **)&t->an_mean, t->an_rows_a * sizeof(double));
+  A(&t->an_tab, (size_t)F::kPA * t->an_modes_pad * t->an_kpad * F::kElem);
+  A(&t->an_rho, (size_t)F::kPB * t->rows_pad * t->an_kpad * F::kElem);
+  A((void **)&t->an_tabs, t->an_modes_pad * sizeof(double));
+  A((void **)&t->an_rhos, t->rows_pad * sizeof(double));
+  A((void **)&t->an_mono, t->rows_pad * sizeof(double));
+  A((void **)&t->an_mean, t->rows_pad * sizeof(double));
   A((void **)&t->an_colsum, g->n_lm * sizeof(double));
   A((void **)&t->an_b0, g->n_ang * sizeof(float));
-  for (int c = 0; c < 3; ++c) {
-    A(&t->sy_q[c], (size_t)F::kPB * t->sy_rows_pad * t->sy_kpad * F::kElem);
-    A(&t->sy_tab[c], (size_t)F::kPA * t->sy_cells_pad * t->sy_kpad * F::kElem);
-    A((void **)&t->sy_qs[c], t->sy_rows_pad * sizeof(double));
-    A((void **)&t->sy_tabs[c], t->sy_cells_pad * sizeof(double));
-    A((void **)&t->sy_qsf[c], t->sy_rows_pad * sizeof(float));
-    A((void **)&t->sy_tabsf[c], t->sy_cells_pad * sizeof(float));
-    A((void **)&t->sy_add[c], t->sy_rows_pad * sizeof(float));
-  }
-  // split K of the analysis: about three rounds of the persistent CTAs; the
-  // split also bounds the fp32 accumulation length of each partial sum
-  const int tiles = (t->an_rows_b / F::kBN) * (t->an_rows_a / kBM) / t->cluster;   // cluster tiles
-  const int kb_total = t->an_kpad * F::kElem / kRowBytes;
-  const int slots = t->cluster == 3 ? t->max_clusters : t->sms;
-  int splits = (3 * slots + tiles - 1) / tiles;
-  splits = splits < 1 ? 1 : (splits > kb_total ? kb_total : splits);
-  t->an_kb_per = (kb_total + splits - 1) / splits;
-  t->an_splits = (kb_total + t->an_kb_per - 1) / t->an_kb_per;
   A((void **)&t->part, (size_t)t->an_splits * M * g->n_lm * sizeof(float));
+  for (int c = 0; c < 3; ++c) {
+    A(&t->sy_q[c], (size_t)F::kPB * t->rows_pad * t->sy_kpad * F::kElem);
+    A(&t->sy_tab[c], (size_t)F::kPA * t->sy_cells_pad * t->sy_kpad * F::kElem);
+    A((void **)&t->sy_qs[c], t->rows_pad * sizeof(double));
+    A((void **)&t->sy_tabs[c], t->sy_cells_pad * sizeof(double));
+    A((void **)&t->sy_qsf[c], t->rows_pad * sizeof(float));
+    A((void **)&t->sy_tabsf[c], t->sy_cells_pad * sizeof(float));
+    A((void **)&t->sy_add[c], t->rows_pad * sizeof(float));
+  }
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? YY_ERR_OOM : YY_ERR_CUDA;
 
   if (cudaFuncSetAttribute(k_pack_rows<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1458,7 +1123,7 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
   PackBatch b = {};
   PackArgs &p = b.job[0];
   p.rows = g->n_lm;
-  p.rows_pad = t->an_rows_b;
+  p.rows_pad = t->an_modes_pad;
   p.K = g->n_ang;
   p.k_pad = t->an_kpad;
   p.src0 = p.src1 = g->ban;
@@ -1466,8 +1131,8 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
   p.ld = g->n_ang;
   p.zero_k0 = p.zero_k1 = -1;
   p.zero_row = 0;
-  p.scale_out = t->an_cs;
-  p.out = t->an_B;
+  p.scale_out = t->an_tabs;
+  p.out = t->an_tab;
   if ((e = launch_pack<F>(b, 1, 0)) != cudaSuccess) return YY_ERR_CUDA;
   const double *tabs[3] = {g->ysyn, g->ysyn_t, g->ysyn_p};
   PackBatch bs = {};
@@ -1489,19 +1154,20 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
   if ((e = launch_pack<F>(bs, 3, 0)) != cudaSuccess) return YY_ERR_CUDA;
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return YY_ERR_CUDA;
 
-  const int brows = t->cluster > 1 ? kBChunk : F::kBN;   // B box rows, as the kernel loads them
-  bool ok = make_map<F>(&t->an_mapA, t->an_A, t->an_kpad, F::kPA * t->an_rows_a, kBM) &&
-            make_map<F>(&t->an_mapB, t->an_B, t->an_kpad, F::kPB * t->an_rows_b, brows);
+  const int bh = t->bn / 2;
+  bool ok = make_map<F>(&t->an_maps.a[0], t->an_tab, t->an_kpad, F::kPA * t->an_modes_pad, kPairRows) &&
+            make_map<F>(&t->an_maps.b[0], t->an_rho, t->an_kpad, F::kPB * t->rows_pad, bh);
   for (int c = 0; c < 3 && ok; ++c)
     ok = make_map<F>(&t->sy_maps.a[c], t->sy_tab[c], t->sy_kpad, F::kPA * t->sy_cells_pad, kPairRows) &&
-         make_map<F>(&t->sy_maps.b[c], t->sy_q[c], t->sy_kpad, F::kPB * t->sy_rows_pad, t->sy_bn / 2);
+         make_map<F>(&t->sy_maps.b[c], t->sy_q[c], t->sy_kpad, F::kPB * t->rows_pad, bh);
   if (!ok) return YY_ERR_NOT_SUPPORTED;
   return YY_OK;
 }
 
 static void free_tables(yy_tc_tables *t) {
   if (!t) return;
-  void *ptrs[] = {t->an_A, t->an_B, t->an_rs, t->an_cs, t->an_mono, t->an_mean, t->an_colsum, t->an_b0, t->part};
+  void *ptrs[] = {t->an_tab, t->an_rho,    t->an_tabs, t->an_rhos, t->an_mono,
+                  t->an_mean, t->an_colsum, t->an_b0,   t->part};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (int c = 0; c < 3; ++c) {
@@ -1546,41 +1212,12 @@ void tc_free(yy_grid *g) {
 }
 
 template <class F>
-static cudaError_t launch_gemm(yy_grid *g, yy_tc_tables *t, const CUtensorMap &ma, const CUtensorMap &mb,
-                               const TcArgs &args, int n_tiles, int m_tiles, int splits, cudaStream_t s) {
-  TcArgs a = args;
-  a.n_tiles = n_tiles;
-  a.m_tiles = m_tiles;
-  a.k_splits = splits;
-  const int C = t->cluster;
-  const int ctiles = n_tiles * (m_tiles / C) * splits;
-  const int slots = C == 3 ? t->max_clusters : t->sms;
-  const int clusters = ctiles < slots ? ctiles : slots;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(clusters * C);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = smem_bytes<F>();
-  cfg.stream = s;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaError_t e = (C == 3) ? cudaLaunchKernelEx(&cfg, k_tc_gemm<F, 3>, ma, mb, a)
-                           : cudaLaunchKernelEx(&cfg, k_tc_gemm<F, 1>, ma, mb, a);
-  g->launches++;
-  return e;
-}
-
-template <class F>
 static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, const double *rg, cudaStream_t s) {
   const int M = 2 * g->n_r;
   PackBatch b = {};
   PackArgs &p = b.job[0];
   p.rows = M;
-  p.rows_pad = t->an_rows_a;
+  p.rows_pad = t->rows_pad;
   p.K = g->n_ang;
   p.k_pad = t->an_kpad;
   p.src0 = ry;
@@ -1592,26 +1229,31 @@ static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, 
   p.dot_vec = t->an_b0;         // monopole row of the analysis table
   p.dot_out = t->an_mono;
   p.mean_out = t->an_mean;      // the tensor cores see rho - (row mean)
-  p.scale_out = t->an_rs;
-  p.out = t->an_A;
+  p.scale_out = t->an_rhos;
+  p.out = t->an_rho;
   cudaError_t e = launch_pack<F>(b, 1, s);
   g->launches++;
   if (e != cudaSuccess) return e;
-  TcArgs a = {};
-  a.M = M;
-  a.N = g->n_lm;
+  PairArgs a = {};
+  a.cells = g->n_lm;
+  a.cell_tiles = t->an_modes_pad / (2 * kPairRows);
+  a.rows = M;
+  a.row_tiles = t->row_tiles;
+  a.bn = t->bn;
   a.kb_total = t->an_kpad * F::kElem / kRowBytes;
-  a.kb_per_tile = t->an_kb_per;
-  a.a_rows = t->an_rows_a;
-  a.b_rows = t->an_rows_b;
-  a.mode = 0;
+  a.k_splits = t->an_splits;
+  a.kb_per_split = t->an_kb_per;
+  a.a_rows = t->an_modes_pad;
+  a.b_rows = t->rows_pad;
+  a.out_mode = 0;
   a.part = t->part;
+  a.part_ld = g->n_lm;
+  a.n_jobs = 1;
   a.err = g->err;
-  e = launch_gemm<F>(g, t, t->an_mapA, t->an_mapB, a, t->an_rows_b / F::kBN, t->an_rows_a / kBM, t->an_splits, s);
-  if (e != cudaSuccess) return e;
+  if ((e = launch_pair<F>(g, t, t->an_maps, a, s)) != cudaSuccess) return e;
   const size_t cnt = (size_t)M * g->n_lm;
-  k_reduce_partials<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(M, g->n_lm, t->an_splits, t->part, t->an_rs,
-                                                                  t->an_cs, t->an_mono, t->an_mean, t->an_colsum,
+  k_reduce_partials<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(M, g->n_lm, t->an_splits, t->part, t->an_rhos,
+                                                                  t->an_tabs, t->an_mono, t->an_mean, t->an_colsum,
                                                                   g->A);
   g->launches++;
   return cudaGetLastError();
@@ -1627,7 +1269,7 @@ static cudaError_t pack_coefficients_form(yy_grid *g, yy_tc_tables *t, cudaStrea
   for (int c = 0; c < 3; ++c) {
     PackArgs &p = b.job[c];
     p.rows = M;
-    p.rows_pad = t->sy_rows_pad;
+    p.rows_pad = t->rows_pad;
     p.K = g->n_lm;
     p.k_pad = t->sy_kpad;
     p.src0 = p.src1 = g->Q + c * qsz;
@@ -1661,13 +1303,16 @@ static cudaError_t synthesis_form(yy_grid *g, yy_tc_tables *t, double *py, doubl
                {2, 2, gy ? gy + 2 * comp : nullptr, gg ? gg + 2 * comp : nullptr}};
   PairArgs a = {};
   a.cells = g->n_ang;
-  a.cell_tiles = t->sy_cell_tiles;
+  a.cell_tiles = t->sy_cells_pad / (2 * kPairRows);
   a.rows = 2 * g->n_r;
-  a.row_tiles = t->sy_row_tiles;
-  a.bn = t->sy_bn;
+  a.row_tiles = t->row_tiles;
+  a.bn = t->bn;
   a.kb_total = t->sy_kpad * F::kElem / kRowBytes;
+  a.k_splits = 1;
+  a.kb_per_split = a.kb_total;
   a.a_rows = t->sy_cells_pad;
-  a.b_rows = t->sy_rows_pad;
+  a.b_rows = t->rows_pad;
+  a.out_mode = 1;
   a.out_split = g->n_r;
   a.ldo = g->n_ang;
   a.n_jobs = gy ? 4 : 1;
@@ -1682,23 +1327,7 @@ static cudaError_t synthesis_form(yy_grid *g, yy_tc_tables *t, double *py, doubl
     J.ta = jobs[j].tab;
     J.tb = jobs[j].q;
   }
-  const int tiles = a.cell_tiles * a.row_tiles * a.n_jobs;
-  const int pairs = tiles < t->pair_slots ? tiles : t->pair_slots;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 2;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(2 * pairs);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = pair_smem_bytes<F>();
-  cfg.stream = s;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_pair<F>, t->sy_maps, a);
-  g->launches++;
-  return e;
+  return launch_pair<F>(g, t, t->sy_maps, a, s);
 }
 
 cudaError_t tc_analysis(yy_grid *g, yy_precision prec, const double *ry, const double *rg, cudaStream_t s) {
