@@ -36,6 +36,27 @@ L2_BYTES = 126 * 1024 * 1024
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 
 
+# DRAM bytes (read + write) of one synthesis launch, from an ncu capture of
+# this workload (profiles/k_tc_pair_fp16x2_production.md); valid only for the
+# kernel source it was taken with, null otherwise.
+_TRAFFIC = {("fp16x2", True): (285.875456e6 + 798.645504e6,
+                               "c60db0e7568fc56fbd539236276931b0cadca2fe7978f389f3a011d296ce34f0")}
+
+
+def _recorded_traffic(prec, gradient):
+    import hashlib
+    rec = _TRAFFIC.get((prec, gradient))
+    if rec is None:
+        return None
+    path = os.path.join(ROOT, "paper_1806_04593_gb300", "csrc", "yy_tc.cu")
+    try:
+        with open(path, "rb") as fh:
+            digest = hashlib.sha256(fh.read()).hexdigest()
+    except OSError:
+        return None
+    return rec[0] if digest == rec[1] else None
+
+
 def _measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -49,7 +70,7 @@ def _measured_peaks():
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="auto")
@@ -123,9 +144,17 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-i", str(self.gpu), "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                 "-i", str(self.gpu), "-lms", "20"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # wait (at most 5 s) for the first sample, so that sampling covers the timed region
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self.proc.poll() is None:
+            self.fh.flush()
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -292,12 +321,20 @@ def run_ours(args, dist):
     h2d = 2 * field_bytes
     d2h = 2 * field_bytes + (6 * field_bytes if gradient else 0)
 
-    # ---- roofline of the dominant kernel (the synthesis contraction)
+    # ---- roofline of the dominant kernel: the synthesis stage (one launch of
+    # k_tc_pair for all contractions on the tensor-core forms; one k_gemm_tn
+    # launch per contraction on the CUDA-core forms), timed by the library's
+    # CUDA events on the solve's stream
     n_synth = 4 if gradient else 1
-    synth_ms = stage_tot["synthesis"] / args.steps / n_synth
-    synth_flop = 2.0 * (2 * spec.n_r) * grid.n_lm * spec.n_ang
+    synth_ms = stage_tot["synthesis"] / args.steps
+    synth_flop = n_synth * 2.0 * (2 * spec.n_r) * grid.n_lm * spec.n_ang   # 2 M N K, K = n_lm
     total_flop = grid.flops(gradient)
     products = {"fp16x2": 3, "bf16x3": 6, "tf32": 1, "fp64": 1, "fp32": 1}[prec]
+    pieces_bytes = {"fp16x2": 4, "bf16x3": 6, "tf32": 4, "fp64": 8, "fp32": 4}[prec]
+    cells_pad = -(-spec.n_ang // 256) * 256
+    k_pad = -(-grid.n_lm // 64) * 64
+    synth_bytes = (n_synth * 2 * spec.n_r * spec.n_ang * 8                  # float64 outputs
+                   + n_synth * cells_pad * k_pad * pieces_bytes)             # one table pass per contraction
     peaks = _measured_peaks()
     if prec == "fp64":
         roof = {"bound": "alu", "kernel": "k_gemm_tn<double> (synthesis, FP64 DFMA)",
@@ -313,10 +350,16 @@ def run_ours(args, dist):
         ratio = 0.5 if prec == "tf32" else 1.0
         roof = {"bound": "tensor", "kernel": f"k_tc_pair<{prec}> (synthesis, tcgen05 cta_group::2)",
                 "achieved": products * synth_flop / (synth_ms / 1e3) / 1e12,
-                "peak": peaks["bf16_tflops"] * ratio, "unit": "TFLOP/s", "traffic": None,
-                "flops_counted": f"hardware: {products} tensor-core products x 2MNK per launch",
+                "peak": peaks["bf16_tflops"] * ratio, "unit": "TFLOP/s",
+                "traffic": _recorded_traffic(prec, gradient),
+                "flops_counted": (f"hardware: {products} tensor-core products x 2MNK, K = n_lm, "
+                                  f"{n_synth} contraction(s) in one launch"),
                 "peak_source": ("measured bf16 burst (MEASURED_PEAKS.json)"
                                 + (" x 0.5 (tf32 nominal ratio)" if prec == "tf32" else ""))}
+    roof["hbm"] = {"algorithmic_bytes": synth_bytes,
+                   "achieved_gbs": synth_bytes / (synth_ms / 1e3) / 1e9,
+                   "peak_gbs": peaks["hbm_gbs"],
+                   "frac": synth_bytes / (synth_ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
     roof["frac"] = roof["achieved"] / roof["peak"]
 
     # ---- the plain float64 GPU path on the same grid, for comparison
@@ -394,7 +437,10 @@ def run_reference(args, dist):
     ry, rg = inputs.density_for(spec)
     og = OracleGrid(spec.r_edges, spec.n_theta, spec.n_phi, spec.delta_theta, spec.delta_phi,
                     spec.lmax, spec.G)
-    cells = np.arange(0, spec.n_ang, args.cpu_sample)
+    # bounded sample: the whole run stays near a minute of CPU time (about 1.1 s
+    # per step at 1/4 of the cells), so long runs evaluate fewer cells per step
+    div = max(args.cpu_sample, -(-4 * (args.steps + args.warmup) // 60))
+    cells = np.arange(0, spec.n_ang, div)
     scale = spec.n_ang / cells.size
     for _ in range(args.warmup):
         oracle_sample_solve(og, ry, rg, cells, gradient)
@@ -405,7 +451,7 @@ def run_reference(args, dist):
         per.append(fixed + (t - fixed) * scale)
     value = args.steps / sum(per)
     sample = (f"float64 oracle; per step: analysis + radial sums of both patches in full, "
-              f"Phi{' and -grad Phi' if gradient else ''} at 1/{args.cpu_sample} of the cells, "
+              f"Phi{' and -grad Phi' if gradient else ''} at 1/{div} of the cells, "
               f"evaluation time scaled x{scale:.1f}")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,

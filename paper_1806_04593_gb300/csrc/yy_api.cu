@@ -153,10 +153,12 @@ yy_status yy_grid_create(const double *r_edges, int n_r, int n_theta, int n_phi,
   if (e == cudaSuccess) e = cudaMemcpy(g->r_edges, r_edges, (n_r + 1) * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(g->err, 0, sizeof(int));
   if (e == cudaSuccess) {
-    const int n_gl = l_max + 32;
-    std::vector<double> gl(2 * YY_GL_WEIGHT_NODES + 2 * n_gl);
+    const int n_gl = l_max + 32, n_mu = l_max + 1;
+    std::vector<double> gl(2 * YY_GL_WEIGHT_NODES + 2 * n_gl + 2 * n_mu);
     gauss_legendre01(YY_GL_WEIGHT_NODES, gl.data(), gl.data() + YY_GL_WEIGHT_NODES);
-    gauss_legendre01(n_gl, gl.data() + 2 * YY_GL_WEIGHT_NODES, gl.data() + 2 * YY_GL_WEIGHT_NODES + n_gl);
+    double *tg = gl.data() + 2 * YY_GL_WEIGHT_NODES;
+    gauss_legendre01(n_gl, tg, tg + n_gl);
+    gauss_legendre01(n_mu, tg + 2 * n_gl, tg + 2 * n_gl + n_mu);
     e = build_tables(g, gl.data(), n_gl);
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();

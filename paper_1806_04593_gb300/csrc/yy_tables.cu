@@ -8,13 +8,15 @@
 //  k_analysis_table w_jk K_lm T_j^(lm) {C_k^(m), S_k^(m)} (§2 closed forms for C, S)
 //  k_synth_tables   K_lm P_l^m {cos, sin}(m phi) at the cell centre and its
 //                   angular derivatives in the patch's own spherical basis
-//  k_rotation_table per degree l, the matrix D^l that expresses a harmonic
-//                   taken in the other patch's angles (Eqs. trafotheta /
+//  k_rot_points,    per degree l, the matrix D^l that expresses a harmonic
+//  k_rot_accum      taken in the other patch's angles (Eqs. trafotheta /
 //                   trafophi) through the own-frame harmonics of the same l
 //  k_scan_coeffs    per-zone factors of the scaled radial recurrences
 //                   (Eqs. rin / rout, phiin / phiout)
 #include <math.h>
 #include <stdio.h>
+
+#include <algorithm>
 
 #include "yy_internal.h"
 
@@ -321,7 +323,7 @@ __global__ void k_synth_tables(SynthGeom G, double *__restrict__ ysyn, double *_
 }
 
 // ---------------------------------------------------------------------------
-// rotation of the other patch's harmonics, one block per degree l
+// rotation of the other patch's harmonics
 // ---------------------------------------------------------------------------
 //
 // A point with own-frame Cartesian direction v has direction M v in the other
@@ -330,51 +332,69 @@ __global__ void k_synth_tables(SynthGeom G, double *__restrict__ ysyn, double *_
 // matrices serve both patches.  The real harmonics Y_i = K_lm P_l^m {cos, sin}
 // are orthonormal on the sphere and a rotation keeps the degree, hence
 //   Y_i(M v) = sum_j D^l_ij Y_j(v),   D^l_ij = int Y_i(M v) Y_j(v) dOmega,
-// i, j over the 2l+1 modes of degree l in the order m = 0, (1, c), (1, s), ...
-// The integrand is a polynomial of degree 2l on the sphere: Gauss-Legendre in
-// cos(theta) with at least lmax + 1 nodes times 2 lmax + 2 equispaced azimuths
-// integrates it to rounding.  Storage: D^l row-major at offset l (4l^2 - 1) / 3.
-__global__ void k_rotation_table(int lmax, const double *__restrict__ gx, const double *__restrict__ gw,
-                                 int n_mu, double *__restrict__ rot) {
-  const int l = blockIdx.x;
-  const int n = 2 * l + 1;
-  const int n_az = 2 * lmax + 2;
-  __shared__ double y_own[2 * YY_LMAX_CAP + 1], y_oth[2 * YY_LMAX_CAP + 1];
-  constexpr int kPer = (2 * YY_LMAX_CAP + 1) * (2 * YY_LMAX_CAP + 1) / 128 + 1;   // blockDim.x = 128
-  double acc[kPer];
-  for (int q = 0; q < kPer; ++q) acc[q] = 0.0;
-  for (int pt = 0; pt < n_mu * n_az; ++pt) {
-    const int a = pt / n_az, b = pt % n_az;
-    const double mu = 2.0 * gx[a] - 1.0;                  // nodes on [0, 1] mapped to [-1, 1]
-    const double wq = 2.0 * gw[a] * (2.0 * kPi / n_az);
-    const double ph = 2.0 * kPi * (b + 0.5) / n_az;
-    const double s = sqrt(fmax(0.0, 1.0 - mu * mu));
-    const double vx = s * cos(ph), vy = s * sin(ph), vz = mu;
-    const double ox = -vx, oy = vz, oz = vy;
-    const double so = sqrt(ox * ox + oy * oy);
-    const double pho = atan2(oy, ox);
-    __syncthreads();
-    for (int m = threadIdx.x; m <= l; m += blockDim.x) {
-      double po = 0.0, px = 0.0;
-      pbar_column(m, l, mu, s, [&](int ll, double v) { if (ll == l) po = v; });
-      pbar_column(m, l, oz, so, [&](int ll, double v) { if (ll == l) px = v; });
+// i, j over the 2l+1 modes of degree l in index order.  The integrand is a
+// polynomial of degree 2l on the sphere: Gauss-Legendre in cos(theta) with
+// lmax + 1 nodes times 2 lmax + 2 equispaced azimuths integrates it to
+// rounding.  The harmonics of a batch of quadrature points are tabulated
+// first (k_rot_points), then every D^l row accumulates over the batch
+// (k_rot_accum).  Storage: D^l row-major at offset l (4l^2 - 1) / 3.
+
+// One block per point of the batch: own-frame harmonics, and the other
+// frame's harmonics times the quadrature weight.
+__global__ void k_rot_points(int lmax, int n_lm, int n_az, int pt0, const double *__restrict__ gx,
+                             const double *__restrict__ gw, double *__restrict__ y_own,
+                             double *__restrict__ y_oth) {
+  extern __shared__ double smp[];
+  const int ntri = (lmax + 1) * (lmax + 2) / 2;
+  double *Po = smp, *Px = smp + ntri;
+  const int pt = pt0 + blockIdx.x;
+  const int a = pt / n_az, c = pt % n_az;
+  const double mu = 2.0 * gx[a] - 1.0;                   // nodes on [0, 1] mapped to [-1, 1]
+  const double wq = 2.0 * gw[a] * (2.0 * kPi / n_az);
+  const double ph = 2.0 * kPi * (c + 0.5) / n_az;
+  const double s = sqrt(fmax(0.0, 1.0 - mu * mu));
+  const double vx = s * cos(ph), vy = s * sin(ph), vz = mu;
+  const double ox = -vx, oy = vz, oz = vy;
+  const double so = sqrt(ox * ox + oy * oy);
+  const double pho = atan2(oy, ox);
+  for (int m = threadIdx.x; m <= lmax; m += blockDim.x) {
+    pbar_column(m, lmax, mu, s, [&](int l, double p) { Po[tri(l, m)] = p; });
+    pbar_column(m, lmax, oz, so, [&](int l, double p) { Px[tri(l, m)] = p; });
+  }
+  __syncthreads();
+  double *yo = y_own + (size_t)blockIdx.x * n_lm, *yx = y_oth + (size_t)blockIdx.x * n_lm;
+  for (int m = threadIdx.x; m <= lmax; m += blockDim.x) {
+    const double cm = cos(m * ph), sm_ = sin(m * ph), cmo = cos(m * pho), smo = sin(m * pho);
+    for (int l = m; l <= lmax; ++l) {
+      const double po = Po[tri(l, m)], px = wq * Px[tri(l, m)];
       if (m == 0) {
-        y_own[0] = po;
-        y_oth[0] = px;
+        yo[l * l] = po;
+        yx[l * l] = px;
       } else {
-        y_own[2 * m - 1] = po * cos(m * ph);
-        y_own[2 * m] = po * sin(m * ph);
-        y_oth[2 * m - 1] = px * cos(m * pho);
-        y_oth[2 * m] = px * sin(m * pho);
+        yo[l * l + 2 * m - 1] = po * cm;
+        yo[l * l + 2 * m] = po * sm_;
+        yx[l * l + 2 * m - 1] = px * cmo;
+        yx[l * l + 2 * m] = px * smo;
       }
     }
-    __syncthreads();
-    int q = 0;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x, ++q) acc[q] += wq * y_oth[e / n] * y_own[e % n];
   }
-  double *D = rot + (size_t)l * (4 * l * l - 1) / 3;
-  int q = 0;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x, ++q) D[e] = acc[q];
+}
+
+// One block per mode row (l, i): D^l_ij (+)= sum over the batch of
+// y_oth[pt][l^2 + i] y_own[pt][l^2 + j], points in ascending order.
+__global__ void k_rot_accum(int n_lm, int n_pts, int first, const double *__restrict__ y_own,
+                            const double *__restrict__ y_oth, double *__restrict__ rot) {
+  const int row = blockIdx.x;
+  int l, m;
+  bool is_sin;
+  mode_lm(row, l, m, is_sin);
+  const int w = 2 * l + 1, i = row - l * l;
+  double *D = rot + (size_t)l * (4 * l * l - 1) / 3 + (size_t)i * w;
+  for (int j = threadIdx.x; j < w; j += blockDim.x) {
+    double acc = first ? 0.0 : D[j];
+    for (int p = 0; p < n_pts; ++p) acc = fma(y_oth[(size_t)p * n_lm + row], y_own[(size_t)p * n_lm + l * l + j], acc);
+    D[j] = acc;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -432,9 +452,10 @@ __global__ void k_round_f32(int n, const double *__restrict__ src, float *__rest
 
 cudaError_t build_tables(yy_grid *g, const double *gl_host, int n_gl) {
   cudaError_t err;
-  // GL tables: [0, 32) nodes / [32, 64) weights for the weights kernel on
-  // [0, 1]; then n_gl nodes and weights on [0, 1] for T.
-  const int n_tab = 2 * YY_GL_WEIGHT_NODES + 2 * n_gl;
+  // GL tables on [0, 1]: [0, 32) nodes / [32, 64) weights for the weights
+  // kernel; then n_gl nodes and weights for T; then lmax + 1 nodes and
+  // weights for the rotation table.
+  const int n_tab = 2 * YY_GL_WEIGHT_NODES + 2 * n_gl + 2 * (g->lmax + 1);
   if ((err = dmalloc((void **)&g->gl_nodes, n_tab * sizeof(double))) != cudaSuccess) return err;
   if ((err = cudaMemcpy(g->gl_nodes, gl_host, n_tab * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
     return err;
@@ -478,8 +499,32 @@ cudaError_t build_tables(yy_grid *g, const double *gl_host, int n_gl) {
   k_synth_tables<<<g->n_ang, 96, smem>>>(sg, g->ysyn, g->ysyn_t, g->ysyn_p);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
 
-  k_rotation_table<<<g->lmax + 1, 128>>>(g->lmax, gx, gw, n_gl, g->rot);
-  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  {
+    // rotation table: n_mu = lmax + 1 Gauss-Legendre nodes (after the T nodes) x 2 lmax + 2 azimuths
+    const int n_mu = g->lmax + 1, n_az = 2 * g->lmax + 2, n_pts = n_mu * n_az;
+    const double *mx = gx + 2 * n_gl, *mw = mx + n_mu;
+    const size_t per_pt = (size_t)g->n_lm * sizeof(double);
+    int batch = (int)std::min<size_t>((size_t)n_pts, (64u << 20) / (2 * per_pt));
+    batch = std::max(batch, 1);
+    double *yo = nullptr, *yx = nullptr;
+    if ((err = dmalloc((void **)&yo, batch * per_pt)) != cudaSuccess) return err;
+    if ((err = dmalloc((void **)&yx, batch * per_pt)) != cudaSuccess) {
+      cudaFree(yo);
+      return err;
+    }
+    const size_t psm = 2 * (size_t)(g->lmax + 1) * (g->lmax + 2) / 2 * sizeof(double);
+    err = cudaFuncSetAttribute(k_rot_points, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+    for (int p0 = 0; p0 < n_pts && err == cudaSuccess; p0 += batch) {
+      const int nb = std::min(batch, n_pts - p0);
+      k_rot_points<<<nb, 32, psm>>>(g->lmax, g->n_lm, n_az, p0, mx, mw, yo, yx);
+      k_rot_accum<<<g->n_lm, 64>>>(g->n_lm, nb, p0 == 0 ? 1 : 0, yo, yx, g->rot);
+      err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) err = cudaDeviceSynchronize();
+    cudaFree(yo);
+    cudaFree(yx);
+    if (err != cudaSuccess) return err;
+  }
   const int n_rot = rotation_table_size(g->lmax);
   k_round_f32<<<(n_rot + 255) / 256, 256>>>(n_rot, g->rot, g->rot32);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
