@@ -483,13 +483,15 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
     }
   } else {
     // Lane quarter of this warp's TMEM lanes; the four warps of a quarter take
-    // 16-column chunks sub, sub + 4, sub + 8, sub + 12.  The scales of a tile
-    // are loaded before its accumulator is ready; the chunks are read from
-    // TMEM two at a time.
+    // 16-column chunks sub, sub + 4, sub + 8, sub + 12.  The 16 rows of a chunk are one aligned run (row0 is a multiple
+    // of 16 and the scale arrays are padded to whole tiles), so their scales
+    // arrive as warp-uniform vector loads and their output rows follow from
+    // one base pointer (unless the run crosses from Yin into Yang).
     const int quarter = warp & 3;
     const int sub = (warp - 2) >> 2;    // 0..3 within the lane quarter
     const uint32_t tempty_even = mapa_rank(smem_u32(&tempty[0]), 0);
     const int n_chunks = a.bn / kEpiCols;
+    constexpr bool scaled = OUT_MODE == 1;
     int it = 0;
     for (int t = pair; t < total; t += n_pairs, ++it) {
       const int b = it & 1;
@@ -497,53 +499,46 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
       const int tl = t % per_job;
       const int rt = tl % a.row_tiles, ct = (tl / a.row_tiles) % a.cell_tiles;
       const int z = tl / (a.row_tiles * a.cell_tiles);
-      constexpr bool scaled = OUT_MODE == 1;
       const int cell = (2 * ct + rank) * kPairRows + quarter * 32 + lane;
       const bool cell_ok = cell < a.cells;
       const float cs = (cell_ok && scaled) ? J.cell_scale[cell] : 0.0f;
-      // lanes 0..15: scales of row (chunk i, lane) for chunk i = sub + 4 (i')
-      float rsv[4], rav[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int row = rt * a.bn + (sub + 4 * i) * kEpiCols + (lane & 15);
-        const bool ok = scaled && (sub + 4 * i) < n_chunks && row < a.rows;
-        rsv[i] = ok ? J.row_scale[row] : 0.0f;
-        rav[i] = ok ? J.row_add[row] : 0.0f;
-      }
       if (!mbar_wait_cluster(&tfull[b], (it >> 1) & 1, a.err)) break;
       tc_fence_after();
       const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
+#pragma unroll 1
+      for (int k = sub; k < n_chunks; k += 4) {
+        const int row0 = rt * a.bn + k * kEpiCols;
+        uint32_t v[16];
+        tmem_ld16_async(tbase + (uint32_t)(k * kEpiCols), v);
+        if constexpr (scaled) {
+          float4 rs4[4], ra4[4];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int i0 = 2 * h, i1 = 2 * h + 1;
-        const int k0 = sub + 4 * i0, k1 = sub + 4 * i1;
-        if (k0 >= n_chunks) break;
-        uint32_t v0[16], v1[16];
-        tmem_ld16_async(tbase + (uint32_t)(k0 * kEpiCols), v0);
-        if (k1 < n_chunks) tmem_ld16_async(tbase + (uint32_t)(k1 * kEpiCols), v1);
-        tmem_wait_ld();
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const int k = c == 0 ? k0 : k1;
-          if (k >= n_chunks) break;
-          const float rsl = c == 0 ? rsv[i0] : rsv[i1];
-          const float ral = c == 0 ? rav[i0] : rav[i1];
-          const int row0 = rt * a.bn + k * kEpiCols;
+          for (int q = 0; q < 4; ++q) {
+            rs4[q] = reinterpret_cast<const float4 *>(J.row_scale + row0)[q];
+            ra4[q] = reinterpret_cast<const float4 *>(J.row_add + row0)[q];
+          }
+          const bool cross = row0 < a.out_split && row0 + kEpiCols > a.out_split;
+          double *base = (row0 < a.out_split) ? J.out0 + (size_t)row0 * a.ldo
+                                              : J.out1 + (size_t)(row0 - a.out_split) * a.ldo;
+          tmem_wait_ld();
 #pragma unroll
           for (int j = 0; j < kEpiCols; ++j) {
-            const float rs = __shfl_sync(0xffffffffu, rsl, j);
-            const float ra = __shfl_sync(0xffffffffu, ral, j);
+            const float4 r4 = rs4[j >> 2], a4 = ra4[j >> 2];
+            const float rs = (j & 3) == 0 ? r4.x : (j & 3) == 1 ? r4.y : (j & 3) == 2 ? r4.z : r4.w;
+            const float ra = (j & 3) == 0 ? a4.x : (j & 3) == 1 ? a4.y : (j & 3) == 2 ? a4.z : a4.w;
             const int row = row0 + j;
-            const float x = __uint_as_float(c == 0 ? v0[j] : v1[j]);
-            if (row < a.rows && cell_ok) {
-              if constexpr (scaled) {
-                double *orow = (row < a.out_split) ? J.out0 + (size_t)row * a.ldo
-                                                   : J.out1 + (size_t)(row - a.out_split) * a.ldo;
-                orow[cell] = f32_to_f64(fmaf(x * cs, rs, ra));
-              } else {
-                a.part[((size_t)z * a.rows + row) * a.part_ld + cell] = x;
-              }
-            }
+            double *orow = base + (size_t)j * a.ldo;
+            if (cross)
+              orow = (row < a.out_split) ? J.out0 + (size_t)row * a.ldo
+                                         : J.out1 + (size_t)(row - a.out_split) * a.ldo;
+            if (row < a.rows && cell_ok) orow[cell] = f32_to_f64(fmaf(__uint_as_float(v[j]) * cs, rs, ra));
+          }
+        } else {
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < kEpiCols; ++j) {
+            const int row = row0 + j;
+            if (row < a.rows && cell_ok) a.part[((size_t)z * a.rows + row) * a.part_ld + cell] = __uint_as_float(v[j]);
           }
         }
       }
