@@ -55,7 +55,6 @@ enum { KIND_F16 = 0, KIND_BF16 = 1, KIND_TF32 = 2 };
 struct FormFP16x2 {
   typedef __half elem;
   static constexpr int kKind = KIND_F16, kElem = 2, kPA = 2, kPB = 2, kPairs = 3;
-  static constexpr int kPairStages = 6;
   __host__ __device__ static constexpr int pa(int i) { return i == 2 ? 1 : 0; }
   __host__ __device__ static constexpr int pb(int i) { return i == 1 ? 1 : 0; }
 };
@@ -63,7 +62,6 @@ struct FormFP16x2 {
 struct FormBF16x3 {
   typedef __nv_bfloat16 elem;
   static constexpr int kKind = KIND_BF16, kElem = 2, kPA = 3, kPB = 3, kPairs = 6;
-  static constexpr int kPairStages = 4;
   // (0,0) (0,1) (1,0) (0,2) (2,0) (1,1)
   __host__ __device__ static constexpr int pa(int i) { return i == 2 ? 1 : (i == 4 ? 2 : (i == 5 ? 1 : 0)); }
   __host__ __device__ static constexpr int pb(int i) { return i == 1 ? 1 : (i == 3 ? 2 : (i == 5 ? 1 : 0)); }
@@ -72,7 +70,6 @@ struct FormBF16x3 {
 struct FormTF32 {
   typedef float elem;
   static constexpr int kKind = KIND_TF32, kElem = 4, kPA = 1, kPB = 1, kPairs = 1;
-  static constexpr int kPairStages = 12;
   __host__ __device__ static constexpr int pa(int) { return 0; }
   __host__ __device__ static constexpr int pb(int) { return 0; }
 };
@@ -82,20 +79,27 @@ constexpr int kPadK = 64;            // K padding (elements) of every packed ope
 constexpr double kY00 = 0.28209479177387814347403972578039;   // K_00 P_0^0 = 1/sqrt(4 pi)
 
 constexpr int kEpiWarps = 16;        // four epilogue warps per TMEM lane quarter
+constexpr int kEpiPerQuarter = kEpiWarps / 4;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kEpiCols = 16;         // columns per TMEM load
 
-// CTA-pair synthesis kernel: per CTA 128 rows of A and up to 128 rows of B
-// (half of the pair's N) in every stage.
+// CTA-pair kernel: per CTA and stage, the form's pieces of 128 rows of A and of
+// bn / 2 rows of B, each piece one 64-byte-wide swizzled slot.  As many stages
+// as the shared memory holds (at most kMaxStages).
 constexpr int kPairRows = 128;
 constexpr int kPairTmemCols = 512;   // two accumulators of up to 256 columns
+constexpr int kMaxStages = 16;
+constexpr int kSmemLimit = 232448;   // dynamic shared memory of one CTA
+constexpr int kSmemFixed = 1024 /*alignment*/ + 512 /*barriers, TMEM address*/;
+
 template <class F>
-constexpr int pair_stage_bytes() {
-  return (F::kPA + F::kPB) * kPairRows * kRowBytes;
+constexpr int pair_stage_bytes(int bn) {
+  return (F::kPA * kPairRows + F::kPB * (bn / 2)) * kRowBytes;
 }
 template <class F>
-constexpr int pair_smem_bytes() {
-  return F::kPairStages * pair_stage_bytes<F>() + 1024 /*align*/ + 256 /*barriers*/;
+int pair_stages(int bn) {
+  const int s = (kSmemLimit - kSmemFixed) / pair_stage_bytes<F>(bn);
+  return s < kMaxStages ? s : kMaxStages;
 }
 
 // ---------------------------------------------------------------------------
@@ -343,6 +347,7 @@ struct PairJob {
 };
 
 struct PairArgs {
+  int stages;                   // shared-memory stages (pair_stages)
   int cells, cell_tiles;        // valid A rows ("cells"); tiles of 256
   int rows, row_tiles, bn;      // valid B rows; tiles of bn rows (multiple of 16, <= 256)
   int kb_total;                 // K blocks (kRowBytes per row)
@@ -365,15 +370,17 @@ struct PairMaps {
 template <class F, int OUT_MODE>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArgs a) {
-  constexpr int S = F::kPairStages;
-  constexpr int SLOT = kPairRows * kRowBytes;
-  constexpr int STAGE = pair_stage_bytes<F>();
+  constexpr int A_SLOT = kPairRows * kRowBytes;
   constexpr int KSTEP_BYTES = 32;
   constexpr int KSTEPS = kRowBytes / KSTEP_BYTES;
   constexpr int BK = kRowBytes / F::kElem;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int S = a.stages;
+  const int bh = a.bn >> 1;
+  const int B_SLOT = bh * kRowBytes;                 // a multiple of 512 bytes (bh % 8 == 0)
+  const int STAGE = F::kPA * A_SLOT + F::kPB * B_SLOT;
   uint64_t *full = (uint64_t *)(smem + S * STAGE);
   uint64_t *empty = full + S;
   uint64_t *tfull = empty + S;      // [2]
@@ -385,7 +392,6 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
   const int pair = (int)blockIdx.x >> 1, n_pairs = (int)gridDim.x >> 1;
   const int per_job = a.cell_tiles * a.row_tiles * a.k_splits;
   const int total = per_job * a.n_jobs;
-  const int bh = a.bn >> 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -410,7 +416,8 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
   if (warp == 0) {
     if (lane == 0) {
       const uint32_t tx_bytes = 2u * (uint32_t)(F::kPA * kPairRows + F::kPB * bh) * kRowBytes;
-      int gk = 0;
+      int gk = 0, s = 0;
+      uint32_t ph = 0;   // phase of stage s in the ring (gk / S) & 1
       bool ok = true;
       for (int t = pair; t < total && ok; t += n_pairs) {
         const int jb = t / per_job, tl = t % per_job;
@@ -422,8 +429,7 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
         const CUtensorMap *tmA = &maps.a[a.job[jb].ta];
         const CUtensorMap *tmB = &maps.b[a.job[jb].tb];
         for (int i = 0; i < nkb; ++i, ++gk) {
-          const int s = gk % S;
-          if (gk >= S && !mbar_wait(&empty[s], ((gk / S) & 1) ^ 1, a.err)) {
+          if (gk >= S && !mbar_wait(&empty[s], ph ^ 1, a.err)) {
             ok = false;
             break;
           }
@@ -432,10 +438,14 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
           const uint32_t base = smem_u32(smem + s * STAGE);
           const int kx = (kb0 + i) * BK;
 #pragma unroll
-          for (int p = 0; p < F::kPA; ++p) tma_load_2d_pair(tmA, base + p * SLOT, fbar, kx, p * a.a_rows + arow);
+          for (int p = 0; p < F::kPA; ++p) tma_load_2d_pair(tmA, base + p * A_SLOT, fbar, kx, p * a.a_rows + arow);
 #pragma unroll
           for (int p = 0; p < F::kPB; ++p)
-            tma_load_2d_pair(tmB, base + (F::kPA + p) * SLOT, fbar, kx, p * a.b_rows + brow);
+            tma_load_2d_pair(tmB, base + F::kPA * A_SLOT + p * B_SLOT, fbar, kx, p * a.b_rows + brow);
+          if (++s == S) {
+            s = 0;
+            ph ^= 1;
+          }
         }
       }
       // the last uses of every stage must be complete before this CTA leaves
@@ -446,7 +456,8 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
   } else if (warp == 1) {
     if (rank == 0 && lane == 0) {
       const uint32_t idesc = instr_desc_pair<F>(a.bn);
-      int gk = 0, it = 0;
+      int gk = 0, it = 0, s = 0;
+      uint32_t ph = 0;
       bool ok = true;
       for (int t = pair; t < total && ok; t += n_pairs, ++it) {
         const int b = it & 1;
@@ -459,36 +470,39 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
         const int kb0 = (tl / (a.row_tiles * a.cell_tiles)) * a.kb_per_split;
         const int nkb = min(a.kb_total, kb0 + a.kb_per_split) - kb0;
         for (int i = 0; i < nkb; ++i, ++gk) {
-          const int s = gk % S;
-          if (!mbar_wait_cluster(&full[s], (gk / S) & 1, a.err)) {
+          if (!mbar_wait_cluster(&full[s], ph, a.err)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + s * STAGE);
-          const uint32_t sb = sa + F::kPA * SLOT;
+          const uint32_t sb = sa + F::kPA * A_SLOT;
 #pragma unroll
           for (int q = 0; q < F::kPairs; ++q) {
 #pragma unroll
             for (int kk = 0; kk < KSTEPS; ++kk) {
-              const uint64_t da = smem_desc(sa + F::pa(q) * SLOT + kk * KSTEP_BYTES);
-              const uint64_t db = smem_desc(sb + F::pb(q) * SLOT + kk * KSTEP_BYTES);
+              const uint64_t da = smem_desc(sa + F::pa(q) * A_SLOT + kk * KSTEP_BYTES);
+              const uint64_t db = smem_desc(sb + F::pb(q) * B_SLOT + kk * KSTEP_BYTES);
               mma_pair<F>(dacc, da, db, idesc, (i | q | kk) != 0 ? 1u : 0u);
             }
           }
           mma_commit_pair(&empty[s]);
+          if (++s == S) {
+            s = 0;
+            ph ^= 1;
+          }
         }
         if (ok) mma_commit_pair(&tfull[b]);
       }
     }
   } else {
-    // Lane quarter of this warp's TMEM lanes; the four warps of a quarter take
-    // 16-column chunks sub, sub + 4, sub + 8, sub + 12.  The 16 rows of a chunk are one aligned run (row0 is a multiple
+    // Lane quarter of this warp's TMEM lanes; the warps of a quarter take
+    // 16-column chunks sub, sub + kEpiPerQuarter, ...  The 16 rows of a chunk are one aligned run (row0 is a multiple
     // of 16 and the scale arrays are padded to whole tiles), so their scales
     // arrive as warp-uniform vector loads and their output rows follow from
     // one base pointer (unless the run crosses from Yin into Yang).
     const int quarter = warp & 3;
-    const int sub = (warp - 2) >> 2;    // 0..3 within the lane quarter
+    const int sub = (warp - 2) >> 2;    // 0 .. kEpiPerQuarter - 1 within the lane quarter
     const uint32_t tempty_even = mapa_rank(smem_u32(&tempty[0]), 0);
     const int n_chunks = a.bn / kEpiCols;
     constexpr bool scaled = OUT_MODE == 1;
@@ -506,7 +520,7 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
       tc_fence_after();
       const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
 #pragma unroll 1
-      for (int k = sub; k < n_chunks; k += 4) {
+      for (int k = sub; k < n_chunks; k += kEpiPerQuarter) {
         const int row0 = rt * a.bn + k * kEpiCols;
         uint32_t v[16];
         tmem_ld16_async(tbase + (uint32_t)(k * kEpiCols), v);
@@ -968,6 +982,7 @@ struct yy_tc_tables {
   yy_precision prec;
   int pair_slots;                         // co-resident CTA pairs of the contraction kernel
   int bn, row_tiles, rows_pad;            // the 2 n_r rows (operand B) in tiles of bn
+  int stages;                             // shared-memory stages of the contraction kernel
   // analysis: table rows (modes) as operand A, densities as operand B
   int an_kpad, an_modes_pad;
   void *an_tab, *an_rho;
@@ -1043,7 +1058,7 @@ static cudaError_t launch_pair(yy_grid *g, yy_tc_tables *t, const PairMaps &maps
   const int tiles = a.cell_tiles * a.row_tiles * a.k_splits * a.n_jobs;
   const int pairs = tiles < t->pair_slots ? tiles : t->pair_slots;
   cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = pair_config(pairs, pair_smem_bytes<F>(), s, attr);
+  cudaLaunchConfig_t cfg = pair_config(pairs, a.stages * pair_stage_bytes<F>(a.bn) + kSmemFixed, s, attr);
   const cudaError_t e = a.out_mode == 1 ? cudaLaunchKernelEx(&cfg, k_tc_pair<F, 1>, maps, a)
                                          : cudaLaunchKernelEx(&cfg, k_tc_pair<F, 0>, maps, a);
   g->launches++;
@@ -1053,14 +1068,17 @@ static cudaError_t launch_pair(yy_grid *g, yy_tc_tables *t, const PairMaps &maps
 template <class F>
 static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
   const int M = 2 * g->n_r;
-  if (cudaFuncSetAttribute(k_tc_pair<F, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, pair_smem_bytes<F>()) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_tc_pair<F, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pair_smem_bytes<F>()) !=
-          cudaSuccess)
+  if (cudaFuncSetAttribute(k_tc_pair<F, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) != cudaSuccess ||
+      cudaFuncSetAttribute(k_tc_pair<F, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) != cudaSuccess)
     return YY_ERR_NOT_SUPPORTED;
+  // the 2 n_r rows: tiles of at most 256, each a multiple of 16
+  t->row_tiles = (M + 255) / 256;
+  t->bn = round_up((M + t->row_tiles - 1) / t->row_tiles, 16);
+  t->rows_pad = t->row_tiles * t->bn;
+  t->stages = pair_stages<F>(t->bn);
   {
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = pair_config(64, pair_smem_bytes<F>(), 0, attr);
+    cudaLaunchConfig_t cfg = pair_config(64, t->stages * pair_stage_bytes<F>(t->bn) + kSmemFixed, 0, attr);
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, (void *)k_tc_pair<F, 1>, &cfg) != cudaSuccess || n < 1) {
       cudaGetLastError();
@@ -1068,10 +1086,6 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
     }
     t->pair_slots = n;
   }
-  // the 2 n_r rows: tiles of at most 256, each a multiple of 16
-  t->row_tiles = (M + 255) / 256;
-  t->bn = round_up((M + t->row_tiles - 1) / t->row_tiles, 16);
-  t->rows_pad = t->row_tiles * t->bn;
   t->an_kpad = round_up(g->n_ang, kPadK);
   t->an_modes_pad = round_up(g->n_lm, 2 * kPairRows);
   t->sy_kpad = round_up(g->n_lm, kPadK);
@@ -1230,6 +1244,7 @@ static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, 
   g->launches++;
   if (e != cudaSuccess) return e;
   PairArgs a = {};
+  a.stages = t->stages;
   a.cells = g->n_lm;
   a.cell_tiles = t->an_modes_pad / (2 * kPairRows);
   a.rows = M;
@@ -1297,6 +1312,7 @@ static cudaError_t synthesis_form(yy_grid *g, yy_tc_tables *t, double *py, doubl
                {2, 1, gy ? gy + comp : nullptr, gg ? gg + comp : nullptr},
                {2, 2, gy ? gy + 2 * comp : nullptr, gg ? gg + 2 * comp : nullptr}};
   PairArgs a = {};
+  a.stages = t->stages;
   a.cells = g->n_ang;
   a.cell_tiles = t->sy_cells_pad / (2 * kPairRows);
   a.rows = 2 * g->n_r;
