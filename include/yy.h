@@ -114,6 +114,25 @@ typedef enum {
   YY_TABLE_MOMENTS_TOTAL = 9
 } yy_table;
 
+/* How the analysis is evaluated (yy_grid_set_analysis).
+ *   YY_ANALYSIS_AUTO (default)  separable for YY_FP64 and YY_FP32, dense for
+ *       the tensor-core forms (there the tensor cores outrun the separable
+ *       stages on CUDA cores despite 12.6 times the flops).
+ *   YY_ANALYSIS_SEPARABLE  the weight folded into the density, then
+ *       an azimuthal stage (cell integrals C_k^(m), S_k^(m)) and a polar stage
+ *       (K_lm T_j^(lm)): 2 n_ang (2 l_max + 1) + 2 n_theta n_lm flops per shell.
+ *       Float64 for YY_FP64; for the other forms fp32 on CUDA cores with the
+ *       m = 0 sums (the monopole) carried in float64.
+ *   YY_ANALYSIS_DENSE  one contraction of the densities with the full
+ *       analysis table, 2 n_ang n_lm flops per shell, in the form's arithmetic
+ *       (tensor cores for YY_TF32 / YY_BF16X3 / YY_FP16X2).
+ * Both give the §3 moments A_p (Eqs. ac/as with the §4 weights).           */
+typedef enum {
+  YY_ANALYSIS_AUTO = 0,
+  YY_ANALYSIS_SEPARABLE = 1,
+  YY_ANALYSIS_DENSE = 2
+} yy_analysis;
+
 /* Create a grid handle on the current CUDA device and build every
  * density-independent term once (§3: the constant terms are computed only
  * while the grid is fixed): overlap weights, polar / azimuthal integrals,
@@ -132,6 +151,10 @@ typedef enum {
 yy_status yy_grid_create(const double *r_edges, int n_r, int n_theta, int n_phi,
                          double delta_theta, double delta_phi, int l_max, double G,
                          yy_grid **out);
+
+/* Select the analysis evaluation for later solves (see yy_analysis).
+ * Errors: YY_ERR_INVALID_ARG. */
+yy_status yy_grid_set_analysis(yy_grid *g, yy_analysis method);
 
 /* Build the operand tables of a reduced-precision form (allocates device
  * memory; synchronises).  YY_FP64 is always ready.  Returns
@@ -219,10 +242,11 @@ yy_status yy_radial_scan_static(const double *r_edges, int n_r, int l_max, doubl
 /* Number of CUDA kernels the last yy_potential call launched (-1 for NULL). */
 int yy_last_launch_count(const yy_grid *g);
 
-/* Dense flop count of one solve: 2 M N K of the analysis, the moment
- * combination, and one or four synthesis contractions (with_gradient = 0 / 1;
- * K = n_lm each), in floating-point operations (the algorithmic count,
- * before any operand splitting). */
+/* Flop count of one solve with the analysis evaluation of the last solve
+ * (2 M N K dense, or its two separable stages; dense before the first solve),
+ * the moment combination, and one or four synthesis
+ * contractions (with_gradient = 0 / 1; K = n_lm each), in floating-point
+ * operations (the algorithmic count, before any operand splitting). */
 double yy_solve_flops(const yy_grid *g, int with_gradient);
 
 #ifdef __cplusplus

@@ -60,7 +60,15 @@ static void free_all(yy_grid *g) {
                      g->stage_grad};
   for (double *p : dbufs)
     if (p) cudaFree(p);
-  float *fbufs[] = {g->rot32, g->ban32, g->ysyn32, g->ysyn_t32, g->ysyn_p32, g->rho32, g->Q32};
+  float *fbufs[] = {g->rot32, g->ban32, g->ysyn32, g->ysyn_t32, g->ysyn_p32, g->rho32, g->Q32,
+                    g->sep_az32, g->sep_w32, g->sep_tb32};
+  double *sbufs[] = {g->sep_az, g->sep_F, g->sep_F0, g->sep_P, g->sep_dP, g->sep_Qs, g->sep_tr};
+  float *sfbufs[] = {g->sep_P32, g->sep_dP32, g->sep_Qs32, g->sep_tr32};
+  for (float *p : sfbufs)
+    if (p) cudaFree(p);
+  for (double *p : sbufs)
+    if (p) cudaFree(p);
+  if (g->sep_tb0) cudaFree(g->sep_tb0);
   for (float *p : fbufs)
     if (p) cudaFree(p);
   if (g->err) cudaFree(g->err);
@@ -137,6 +145,10 @@ yy_status yy_grid_create(const double *r_edges, int n_r, int n_theta, int n_phi,
   A((void **)&g->ysyn_t, n_ang * n_lm * sizeof(double));
   A((void **)&g->ysyn_p, n_ang * n_lm * sizeof(double));
   A((void **)&g->rot, rotation_table_size(l_max) * sizeof(double));
+  A((void **)&g->sep_P, (size_t)n_theta * n_lm * sizeof(double));
+  A((void **)&g->sep_dP, (size_t)n_theta * n_lm * sizeof(double));
+  A((void **)&g->sep_Qs, (size_t)n_theta * n_lm * sizeof(double));
+  A((void **)&g->sep_tr, (size_t)(2 * l_max + 1) * n_phi * sizeof(double));
   A((void **)&g->rot32, rotation_table_size(l_max) * sizeof(float));
   A((void **)&g->scan, (size_t)n_r * (l_max + 1) * 8 * sizeof(double));
   {
@@ -161,6 +173,7 @@ yy_status yy_grid_create(const double *r_edges, int n_r, int n_theta, int n_phi,
     gauss_legendre01(n_mu, tg + 2 * n_gl, tg + 2 * n_gl + n_mu);
     e = build_tables(g, gl.data(), n_gl);
   }
+  if (e == cudaSuccess) e = separable_prepare(g);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     const yy_status st = from_cuda(e);
@@ -170,6 +183,13 @@ yy_status yy_grid_create(const double *r_edges, int n_r, int n_theta, int n_phi,
     return st;
   }
   *out = g;
+  return YY_OK;
+}
+
+yy_status yy_grid_set_analysis(yy_grid *g, yy_analysis method) {
+  if (!g || (method != YY_ANALYSIS_AUTO && method != YY_ANALYSIS_SEPARABLE && method != YY_ANALYSIS_DENSE))
+    return YY_ERR_INVALID_ARG;
+  g->analysis_method = (int)method;
   return YY_OK;
 }
 
@@ -222,16 +242,27 @@ yy_status yy_potential(yy_grid *g, const double *rho_yin, const double *rho_yang
   const bool f32 = (prec == YY_FP32);
   g->launches = 0;
   mark(0);
-  if (e == cudaSuccess)
-    e = simt ? analysis_simt(g, rho_yin, rho_yang, f32, s) : tc_analysis(g, prec, rho_yin, rho_yang, s);
+  if (e == cudaSuccess) {
+    const bool separable = g->analysis_method == YY_ANALYSIS_SEPARABLE ||
+                           (g->analysis_method == YY_ANALYSIS_AUTO && simt);
+    g->last_separable = separable && g->sep_ok;
+    if (g->last_separable)
+      e = analysis_separable(g, rho_yin, rho_yang, prec == YY_FP64, s);
+    else
+      e = simt ? analysis_simt(g, rho_yin, rho_yang, f32, s) : tc_analysis(g, prec, rho_yin, rho_yang, s);
+  }
   mark(1);
   if (e == cudaSuccess) e = rotate_moments(g, prec == YY_FP64, s);
   if (e == cudaSuccess) e = radial_scan(g, f32, true, s);
   if (e == cudaSuccess && !simt) e = tc_pack_coefficients(g, prec, s);
   mark(2);
-  if (e == cudaSuccess)
-    e = simt ? synthesis_simt(g, phi_yin, phi_yang, grad_yin, grad_yang, f32, s)
-             : tc_synthesis(g, prec, phi_yin, phi_yang, grad_yin, grad_yang, s);
+  if (e == cudaSuccess) {
+    if (simt && g->analysis_method != YY_ANALYSIS_DENSE && g->sep_syn_ok)
+      e = synthesis_separable(g, phi_yin, phi_yang, grad_yin, grad_yang, !f32, s);
+    else
+      e = simt ? synthesis_simt(g, phi_yin, phi_yang, grad_yin, grad_yang, f32, s)
+               : tc_synthesis(g, prec, phi_yin, phi_yang, grad_yin, grad_yang, s);
+  }
   mark(3);
   return from_cuda(e);
 }
@@ -344,7 +375,10 @@ int yy_last_launch_count(const yy_grid *g) { return g ? g->launches : -1; }
 double yy_solve_flops(const yy_grid *g, int with_gradient) {
   if (!g) return 0.0;
   const double M = 2.0 * g->n_r, K_an = g->n_ang, N_an = g->n_lm;
-  const double analysis = 2.0 * M * N_an * K_an;
+  const int nt = 2 * g->lmax + 1;
+  const double analysis = g->last_separable
+                              ? 2.0 * M * K_an * nt + 2.0 * M * g->n_theta * N_an
+                              : 2.0 * M * N_an * K_an;
   const double synth = 2.0 * M * g->n_lm * g->n_ang;
   double rotation = 0.0;
   for (int l = 0; l <= g->lmax; ++l) rotation += 2.0 * M * (2.0 * l + 1.0) * (2.0 * l + 1.0);

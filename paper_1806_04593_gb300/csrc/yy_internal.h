@@ -46,6 +46,24 @@ struct yy_grid {
   double *Q;           // [3][2 n_r][n_lm]    Phi, g_r and g_angle coefficients
   int *err;            // device error word
 
+  // separable analysis (yy_separable.cu)
+  int analysis_method;  // yy_analysis
+  int last_separable;   // the last solve used the separable analysis
+  int sep_nt_pad;       // 2 l_max + 1 azimuthal functions, padded to a multiple of 4
+  int sep_ok;           // the grid fits the separable kernels' shared memory
+  int sep_phi_blocks[2];  // persistent blocks of the azimuthal stage (fp32, float64)
+  double *sep_az;       // [n_phi][sep_nt_pad] cell integrals of the azimuthal functions
+  float *sep_az32, *sep_w32, *sep_tb32;   // fp32 copies of sep_az, w, tbar
+  double *sep_F;        // [2 n_r][n_theta][sep_nt_pad] azimuthal stage (float64 or fp32)
+  double *sep_F0;       // [2 n_r][n_theta] m = 0 row sums as fp32 pairs (fp32 form)
+  float2 *sep_tb0;      // [n_theta][l_max + 1] K_l0 T_j^(l0) d_phi as fp32 pairs
+  double *sep_P, *sep_dP, *sep_Qs;   // [n_theta][n_lm] Legendre factors at the cell colatitudes
+  double *sep_tr;                    // [2 l_max + 1][n_phi] 1, cos, sin at the cell longitudes
+  float *sep_P32, *sep_dP32, *sep_Qs32, *sep_tr32;   // fp32 copies
+  int sep_syn_ok;                    // the grid fits the separable synthesis's shared memory
+  size_t sep_syn_smem[2];            // its shared memory (fp32, float64)
+  int sep_syn_blocks[2];             // its persistent blocks (fp32, float64)
+
   // float32 form
   float *ban32, *ysyn32, *ysyn_t32, *ysyn_p32;   // same layouts as float64
   float *rho32;        // [2 n_r][n_ang]
@@ -82,6 +100,13 @@ cudaError_t analysis_simt(yy_grid *g, const double *rho_yin, const double *rho_y
 cudaError_t synthesis_simt(yy_grid *g, double *phi_yin, double *phi_yang,
                            double *grad_yin, double *grad_yang, bool fp32, cudaStream_t s);
 cudaError_t convert_tables_f32(yy_grid *g);
+
+// separable analysis (yy_separable.cu): tables once per grid, then per solve
+cudaError_t separable_prepare(yy_grid *g);
+cudaError_t analysis_separable(yy_grid *g, const double *rho_yin, const double *rho_yang, bool fp64,
+                               cudaStream_t s);
+cudaError_t synthesis_separable(yy_grid *g, double *phi_yin, double *phi_yang, double *grad_yin,
+                                double *grad_yang, bool fp64, cudaStream_t s);
 
 // Atot = A + D^T A(other patch), float32 products unless fp64 (yy_scan.cu)
 cudaError_t rotate_moments(yy_grid *g, bool fp64, cudaStream_t s);

@@ -333,10 +333,11 @@ k_scan_warp(int n_r, int lmax, int n_lm, const double *__restrict__ A, const dou
 cudaError_t rotate_moments(yy_grid *g, bool fp64, cudaStream_t st) {
   const size_t smem = 2 * (size_t)g->n_lm * (fp64 ? sizeof(double) : sizeof(float));
   if (smem > 48 * 1024) {
+    // the attribute belongs to the kernel, shared by all grids: the maximum
     const cudaError_t e = fp64 ? cudaFuncSetAttribute(k_rotate_moments<double>,
-                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)
                                : cudaFuncSetAttribute(k_rotate_moments<float>,
-                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
   }
   const int threads = std::min(1024, (g->n_lm + 31) / 32 * 32);

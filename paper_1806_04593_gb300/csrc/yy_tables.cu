@@ -322,6 +322,46 @@ __global__ void k_synth_tables(SynthGeom G, double *__restrict__ ysyn, double *_
   }
 }
 
+// Separable synthesis tables at the cell-centre colatitudes: one block per j,
+// one thread per m.  P[j][idx] = K_lm P_l^m(cos theta_j), dP the theta
+// derivative, Q the m P / sin theta factor of the phi derivative (the same
+// value in the cos and sin slot of a mode); tr[t][k] = 1, cos(m phi_k),
+// sin(m phi_k) for t = 0, 2m - 1, 2m at the cell-centre longitudes.
+__global__ void k_sep_ptables(int n_theta, int lmax, int n_lm, double th0, double dth, double *__restrict__ P,
+                              double *__restrict__ dP, double *__restrict__ Qs) {
+  extern __shared__ double smt[];
+  const int j = blockIdx.x;
+  const double th = th0 + dth * (j + 0.5);
+  const double st = sin(th), ct = cos(th);
+  for (int m = threadIdx.x; m <= lmax; m += blockDim.x)
+    pbar_column(m, lmax, ct, st, [&](int l, double p) { smt[tri(l, m)] = p; });
+  __syncthreads();
+  const size_t row = (size_t)j * n_lm;
+  for (int m = threadIdx.x; m <= lmax; m += blockDim.x) {
+    for (int l = m; l <= lmax; ++l) {
+      const double p = smt[tri(l, m)], dp = dpbar(smt, l, m, lmax), qs = mpbar_over_sin(smt, l, m, lmax);
+      const int i0 = (m == 0) ? l * l : l * l + 2 * m - 1;
+      P[row + i0] = p;
+      dP[row + i0] = dp;
+      Qs[row + i0] = qs;
+      if (m > 0) {
+        P[row + i0 + 1] = p;
+        dP[row + i0 + 1] = dp;
+        Qs[row + i0 + 1] = qs;
+      }
+    }
+  }
+}
+
+__global__ void k_sep_trig(int n_phi, int lmax, double ph0, double dph, double *__restrict__ tr) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (2 * lmax + 1) * n_phi) return;
+  const int t = e / n_phi, k = e % n_phi;
+  const double ph = ph0 + dph * (k + 0.5);
+  const int m = (t + 1) / 2;
+  tr[e] = (t == 0) ? 1.0 : ((t & 1) ? cos(m * ph) : sin(m * ph));
+}
+
 // ---------------------------------------------------------------------------
 // rotation of the other patch's harmonics
 // ---------------------------------------------------------------------------
@@ -524,6 +564,14 @@ cudaError_t build_tables(yy_grid *g, const double *gl_host, int n_gl) {
     cudaFree(yo);
     cudaFree(yx);
     if (err != cudaSuccess) return err;
+  }
+  {
+    const size_t psm = (size_t)(g->lmax + 1) * (g->lmax + 2) / 2 * sizeof(double);
+    k_sep_ptables<<<g->n_theta, 32, psm>>>(g->n_theta, g->lmax, g->n_lm, g->th0, g->dth, g->sep_P, g->sep_dP,
+                                           g->sep_Qs);
+    const int n_tr = (2 * g->lmax + 1) * g->n_phi;
+    k_sep_trig<<<(n_tr + 255) / 256, 256>>>(g->n_phi, g->lmax, g->ph0, g->dph, g->sep_tr);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   const int n_rot = rotation_table_size(g->lmax);
   k_round_f32<<<(n_rot + 255) / 256, 256>>>(n_rot, g->rot, g->rot32);

@@ -40,6 +40,10 @@ YY_TABLE_SYNTH_T = 4
 YY_TABLE_SYNTH_P = 5
 YY_TABLE_MOMENTS = 6
 YY_TABLE_COEFF = 7
+YY_ANALYSIS_AUTO = 0
+YY_ANALYSIS_SEPARABLE = 1
+YY_ANALYSIS_DENSE = 2
+ANALYSES = {"auto": YY_ANALYSIS_AUTO, "separable": YY_ANALYSIS_SEPARABLE, "dense": YY_ANALYSIS_DENSE}
 YY_TABLE_ROTATION = 8
 YY_TABLE_MOMENTS_TOTAL = 9
 
@@ -67,6 +71,8 @@ def load():
     lib.yy_grid_create.restype = I
     lib.yy_grid_prepare.argtypes = [P, I]
     lib.yy_grid_prepare.restype = I
+    lib.yy_grid_set_analysis.argtypes = [P, I]
+    lib.yy_grid_set_analysis.restype = I
     lib.yy_potential.argtypes = [P, P, P, P, P, P, P, I, P]
     lib.yy_potential.restype = I
     lib.yy_potential_host.argtypes = [P, P, P, P, P, P, P, I, P]
@@ -131,6 +137,10 @@ def yy_grid_create(r_edges, n_theta, n_phi, delta_theta, delta_phi, l_max, G=1.0
 
 def yy_grid_prepare(handle, prec):
     return load().yy_grid_prepare(handle, int(prec))
+
+
+def yy_grid_set_analysis(handle, method):
+    return load().yy_grid_set_analysis(handle, int(method))
 
 
 def yy_potential(handle, rho_yin, rho_yang, phi_yin, phi_yang, grad_yin=None, grad_yang=None,
@@ -219,6 +229,11 @@ class Grid:
     @property
     def field_shape(self):
         return (self.n_r, self.n_theta, self.n_phi)
+
+    def set_analysis(self, method):
+        st = yy_grid_set_analysis(self.handle, ANALYSES.get(method, method))
+        if st != YY_OK:
+            raise YYError(st, "yy_grid_set_analysis")
 
     def prepare(self, prec):
         st = yy_grid_prepare(self.handle, PRECISIONS.get(prec, prec))

@@ -138,12 +138,19 @@ def test_rotation_table_maps_other_frame_harmonics(yy, oracle_grid, name):
 # solves
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("analysis", ["separable", "dense"])
 @pytest.mark.parametrize("name", ["tiny", "mid"])
-def test_fp64_potential_and_gradient_match_oracle(yy, oracle_grid, name):
+def test_fp64_potential_and_gradient_match_oracle(yy, oracle_grid, name, analysis):
+    """Float64, with both analysis evaluations (separable stages and the
+    dense contraction): the same moments to rounding."""
     spec = inputs.GRIDS[name]()
     g = _grid(yy, spec)
     ry, rg = inputs.density_for(spec)
-    out = gpu_solve(g, ry, rg, gradient=True)
+    g.set_analysis(analysis)
+    try:
+        out = gpu_solve(g, ry, rg, gradient=True)
+    finally:
+        g.set_analysis("auto")
     ref = oracle_grid(spec).solve(ry, rg, gradient=True)
     for q in ("yin", "yang"):
         assert rel_max(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64, q

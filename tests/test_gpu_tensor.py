@@ -37,14 +37,21 @@ def _grid(yy, spec):
     return _GRIDS[spec.name]
 
 
+@pytest.mark.parametrize("analysis", ["separable", "dense"])
 @pytest.mark.parametrize("prec", ["fp16x2", "bf16x3", "tf32"])
 @pytest.mark.parametrize("name", ["tiny", "mid"])
-def test_tensor_form_matches_oracle(yy, oracle_grid, prec, name):
+def test_tensor_form_matches_oracle(yy, oracle_grid, prec, name, analysis):
+    """Both analysis evaluations: the separable one (fp32 azimuthal stage,
+    float64 m = 0 sums) and the dense tensor-core contraction."""
     spec = inputs.GRIDS[name]()
     g = _grid(yy, spec)
     g.prepare(prec)
     ry, rg = inputs.density_for(spec)
-    out = gpu_solve(g, ry, rg, gradient=True, prec=prec)
+    g.set_analysis(analysis)
+    try:
+        out = gpu_solve(g, ry, rg, gradient=True, prec=prec)
+    finally:
+        g.set_analysis("auto")
     assert yy.yy_last_device_status(g.handle) == yy.YY_OK
     ref = oracle_grid(spec).solve(ry, rg, gradient=True)
     tol_phi, tol_g = TOL[prec]
@@ -53,13 +60,18 @@ def test_tensor_form_matches_oracle(yy, oracle_grid, prec, name):
         assert rel_max(out["grad_" + q], ref["grad_" + q]) <= tol_g, (q, prec)
 
 
+@pytest.mark.parametrize("analysis", ["separable", "dense"])
 @pytest.mark.parametrize("prec", ["fp16x2", "bf16x3"])
-def test_tensor_form_production_sampled(yy, oracle_grid, prec):
+def test_tensor_form_production_sampled(yy, oracle_grid, prec, analysis):
     spec = inputs.production_grid()
     g = _grid(yy, spec)
     g.prepare(prec)
     ry, rg = inputs.density_for(spec)
-    out = gpu_solve(g, ry, rg, gradient=True, prec=prec)
+    g.set_analysis(analysis)
+    try:
+        out = gpu_solve(g, ry, rg, gradient=True, prec=prec)
+    finally:
+        g.set_analysis("auto")
     assert yy.yy_last_device_status(g.handle) == yy.YY_OK
     rng = np.random.default_rng(41)
     cells = np.sort(rng.choice(spec.n_ang, 64, replace=False))
