@@ -249,6 +249,60 @@ int yy_last_launch_count(const yy_grid *g);
  * operations (the algorithmic count, before any operand splitting). */
 double yy_solve_flops(const yy_grid *g, int with_gradient);
 
+/* ---- batched solves ------------------------------------------------------
+ * Many independent density fields, each on its own grid (uneven n_r, angular
+ * resolution and l_max), solved by one CUDA graph.  A field is described by
+ * the arguments of yy_grid_create; the batch owns one grid per field. */
+typedef struct yy_batch yy_batch;
+typedef struct {
+  const double *r_edges;       /* host, n_r + 1 values (copied) */
+  int n_r, n_theta, n_phi;
+  double delta_theta, delta_phi;
+  int l_max;
+  double G;
+} yy_field_desc;
+
+/* Create the fields' grids (rules and errors of yy_grid_create, per field;
+ * 1 <= n_fields <= 65536).  Synchronises.  *out is NULL on failure. */
+yy_status yy_batch_create(const yy_field_desc *fields, int n_fields, yy_batch **out);
+
+/* yy_grid_prepare for every field. */
+yy_status yy_batch_prepare(yy_batch *b, yy_precision prec);
+
+/* Autotuner: for every field, time each analysis evaluation (YY_ANALYSIS_DENSE,
+ * YY_ANALYSIS_SEPARABLE; reps solves each on zero densities in scratch
+ * buffers it allocates and frees) in the given form, with or without the
+ * gradient, and keep the faster.  chosen (NULL or n_fields entries) receives
+ * the yy_analysis picked per field.  Prepares the form; synchronises. */
+yy_status yy_batch_tune(yy_batch *b, yy_precision prec, int with_gradient, int reps, int *chosen);
+
+/* Set one field's analysis evaluation by hand (see yy_analysis). */
+yy_status yy_batch_set_analysis(yy_batch *b, int field, yy_analysis method);
+
+/* Solve every field.  Each argument is a host array of n_fields device
+ * pointers laid out as for yy_potential; grad_yin and grad_yang are both NULL
+ * (no gradient) or both arrays.  The first call with a given set of pointers,
+ * form and gradient flag records all solves into one CUDA graph (fields on
+ * parallel branches) and instantiates it; later calls with the same set replay
+ * it on cuda_stream (one graph launch, bitwise-identical results).  A few
+ * graphs are kept.  Asynchronous.  Errors as for yy_potential. */
+yy_status yy_batch_potential(yy_batch *b, const double *const *rho_yin, const double *const *rho_yang,
+                             double *const *phi_yin, double *const *phi_yang,
+                             double *const *grad_yin, double *const *grad_yang,
+                             yy_precision prec, void *cuda_stream);
+
+/* The grid of one field (owned by the batch; NULL if out of range). */
+yy_grid *yy_batch_grid(yy_batch *b, int field);
+
+/* Kernels in the last recorded graph (-1 for NULL). */
+int yy_batch_last_launch_count(const yy_batch *b);
+
+/* The first non-OK device status over the fields (reads and clears each). */
+yy_status yy_batch_last_device_status(yy_batch *b);
+
+/* Release the batch and its grids (NULL-safe; synchronises). */
+void yy_batch_destroy(yy_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -245,7 +245,7 @@ yy_status yy_potential(yy_grid *g, const double *rho_yin, const double *rho_yang
   if (e == cudaSuccess) {
     const bool separable = g->analysis_method == YY_ANALYSIS_SEPARABLE ||
                            (g->analysis_method == YY_ANALYSIS_AUTO && simt);
-    g->last_separable = separable && g->sep_ok;
+    g->last_separable = separable && (g->sep_ok & (prec == YY_FP64 ? 2 : 1));
     if (g->last_separable)
       e = analysis_separable(g, rho_yin, rho_yang, prec == YY_FP64, s);
     else

@@ -50,7 +50,7 @@ struct yy_grid {
   int analysis_method;  // yy_analysis
   int last_separable;   // the last solve used the separable analysis
   int sep_nt_pad;       // 2 l_max + 1 azimuthal functions, padded to a multiple of 4
-  int sep_ok;           // the grid fits the separable kernels' shared memory
+  int sep_ok;           // the grid fits the separable kernels' shared memory: bit 0 fp32, bit 1 float64
   int sep_phi_blocks[2];  // persistent blocks of the azimuthal stage (fp32, float64)
   double *sep_az;       // [n_phi][sep_nt_pad] cell integrals of the azimuthal functions
   float *sep_az32, *sep_w32, *sep_tb32;   // fp32 copies of sep_az, w, tbar

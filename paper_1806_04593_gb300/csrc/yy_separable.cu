@@ -456,8 +456,11 @@ cudaError_t separable_prepare(yy_grid *g) {
   // grids too large for it leave the separable analysis unavailable
   const size_t smem64 = (size_t)g->n_phi * (nt_pad + kXP) * sizeof(double);
   const size_t smem32 = (size_t)g->n_phi * (nt_pad + kXP) * sizeof(float);
-  const size_t smem_t = (size_t)g->n_theta * nt_pad * sizeof(double) + (size_t)(g->n_theta + 1) * sizeof(float2);
-  g->sep_ok = smem64 <= 227 * 1024 && smem_t <= 227 * 1024;
+  const size_t tail_t = (size_t)(g->n_theta + 1) * sizeof(float2);
+  const size_t smem_t32 = (size_t)g->n_theta * nt_pad * sizeof(float) + tail_t;
+  const size_t smem_t64 = (size_t)g->n_theta * nt_pad * sizeof(double) + tail_t;
+  g->sep_ok = (smem32 <= 227 * 1024 && smem_t32 <= 227 * 1024 ? 1 : 0) |
+              (smem64 <= 227 * 1024 && smem_t64 <= 227 * 1024 ? 2 : 0);
   if (!g->sep_ok) return cudaSuccess;
   const void *kp[2] = {(const void *)k_sep_phi<float>, (const void *)k_sep_phi<double>};
   const size_t sm[2] = {smem32, smem64};
@@ -465,6 +468,7 @@ cudaError_t separable_prepare(yy_grid *g) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
   // the attribute belongs to the kernel, not to this grid: always the maximum
   for (int q = 0; q < 2; ++q) {
+    if (!(g->sep_ok & (1 << q))) continue;
     if ((e = cudaFuncSetAttribute(kp[q], cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)) != cudaSuccess)
       return e;
     int nb = 0;

@@ -82,6 +82,10 @@ constexpr int kEpiWarps = 16;        // four epilogue warps per TMEM lane quarte
 constexpr int kEpiPerQuarter = kEpiWarps / 4;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kEpiCols = 16;         // columns per TMEM load
+// K elements per accumulator fill of the analysis: the fp32 accumulation error
+// of a chain grows with its length times the size of its partial sums, and a
+// fill of 256 keeps it near 1e-7 of the moments at K = 24300 (1 degree cells)
+constexpr int kAnalysisFill = 256;
 
 // CTA-pair kernel: per CTA and stage, the form's pieces of 128 rows of A and of
 // bn / 2 rows of B, each piece one 64-byte-wide swizzled slot.  As many stages
@@ -352,6 +356,7 @@ struct PairArgs {
   int rows, row_tiles, bn;      // valid B rows; tiles of bn rows (multiple of 16, <= 256)
   int kb_total;                 // K blocks (kRowBytes per row)
   int k_splits, kb_per_split;   // K split of every tile
+  int kb_chunk;                 // K blocks per accumulator fill; mode 0 adds the fills in registers
   int a_rows, b_rows;           // rows of one piece in the stacked A / B operands
   int out_mode;                 // 1: scaled float64 job outputs; 0: raw fp32 partial sums
   float *part;                  // mode 0: part[(z rows + row) part_ld + cell]
@@ -392,6 +397,7 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
   const int pair = (int)blockIdx.x >> 1, n_pairs = (int)gridDim.x >> 1;
   const int per_job = a.cell_tiles * a.row_tiles * a.k_splits;
   const int total = per_job * a.n_jobs;
+  const int chunk = (OUT_MODE == 0 && a.kb_chunk > 0) ? a.kb_chunk : a.kb_total;   // K blocks per accumulator fill
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -459,40 +465,47 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
       int gk = 0, it = 0, s = 0;
       uint32_t ph = 0;
       bool ok = true;
-      for (int t = pair; t < total && ok; t += n_pairs, ++it) {
-        const int b = it & 1;
-        if (it >= 2) {
-          if (!mbar_wait_cluster(&tempty[b], ((it >> 1) & 1) ^ 1, a.err)) break;
-          tc_fence_after();
-        }
-        const uint32_t dacc = tmem_base + (uint32_t)(b * 256);
+      for (int t = pair; t < total && ok; t += n_pairs) {
         const int tl = t % per_job;
         const int kb0 = (tl / (a.row_tiles * a.cell_tiles)) * a.kb_per_split;
         const int nkb = min(a.kb_total, kb0 + a.kb_per_split) - kb0;
-        for (int i = 0; i < nkb; ++i, ++gk) {
-          if (!mbar_wait_cluster(&full[s], ph, a.err)) {
-            ok = false;
-            break;
+        // the tile's K blocks in fills of kb_chunk, alternating between the two accumulators
+        for (int c0 = 0; c0 < nkb && ok; c0 += chunk, ++it) {
+          const int b = it & 1;
+          if (it >= 2) {
+            if (!mbar_wait_cluster(&tempty[b], ((it >> 1) & 1) ^ 1, a.err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
           }
-          tc_fence_after();
-          const uint32_t sa = smem_u32(smem + s * STAGE);
-          const uint32_t sb = sa + F::kPA * A_SLOT;
+          const uint32_t dacc = tmem_base + (uint32_t)(b * 256);
+          const int c1 = min(nkb, c0 + chunk);
+          for (int i = c0; i < c1; ++i, ++gk) {
+            if (!mbar_wait_cluster(&full[s], ph, a.err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + s * STAGE);
+            const uint32_t sb = sa + F::kPA * A_SLOT;
 #pragma unroll
-          for (int q = 0; q < F::kPairs; ++q) {
+            for (int q = 0; q < F::kPairs; ++q) {
 #pragma unroll
-            for (int kk = 0; kk < KSTEPS; ++kk) {
-              const uint64_t da = smem_desc(sa + F::pa(q) * A_SLOT + kk * KSTEP_BYTES);
-              const uint64_t db = smem_desc(sb + F::pb(q) * B_SLOT + kk * KSTEP_BYTES);
-              mma_pair<F>(dacc, da, db, idesc, (i | q | kk) != 0 ? 1u : 0u);
+              for (int kk = 0; kk < KSTEPS; ++kk) {
+                const uint64_t da = smem_desc(sa + F::pa(q) * A_SLOT + kk * KSTEP_BYTES);
+                const uint64_t db = smem_desc(sb + F::pb(q) * B_SLOT + kk * KSTEP_BYTES);
+                mma_pair<F>(dacc, da, db, idesc, ((i - c0) | q | kk) != 0 ? 1u : 0u);
+              }
+            }
+            mma_commit_pair(&empty[s]);
+            if (++s == S) {
+              s = 0;
+              ph ^= 1;
             }
           }
-          mma_commit_pair(&empty[s]);
-          if (++s == S) {
-            s = 0;
-            ph ^= 1;
-          }
+          if (ok) mma_commit_pair(&tfull[b]);
         }
-        if (ok) mma_commit_pair(&tfull[b]);
       }
     }
   } else {
@@ -507,6 +520,64 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
     const int n_chunks = a.bn / kEpiCols;
     constexpr bool scaled = OUT_MODE == 1;
     int it = 0;
+    if constexpr (OUT_MODE == 0) {
+      // K-split partial sums: the tile's accumulator fills (kb_chunk K blocks
+      // each) are added here in fp32 registers, so no fp32 accumulation chain
+      // in the tensor core runs longer than one fill.  This warp owns 16-column
+      // chunks sub, sub + kEpiPerQuarter, ... (at most kMaxOwn of them).
+      constexpr int kMaxOwn = 256 / kEpiCols / kEpiPerQuarter;
+      for (int t = pair; t < total; t += n_pairs) {
+        const int tl = t % per_job;
+        const int rt = tl % a.row_tiles, ct = (tl / a.row_tiles) % a.cell_tiles;
+        const int z = tl / (a.row_tiles * a.cell_tiles);
+        const int kb0 = z * a.kb_per_split;
+        const int nkb = min(a.kb_total, kb0 + a.kb_per_split) - kb0;
+        const int cell = (2 * ct + rank) * kPairRows + quarter * 32 + lane;
+        float acc[kMaxOwn][kEpiCols];
+#pragma unroll
+        for (int o = 0; o < kMaxOwn; ++o)
+#pragma unroll
+          for (int j = 0; j < kEpiCols; ++j) acc[o][j] = 0.0f;
+        bool ok = true;
+        for (int c0 = 0; c0 < nkb; c0 += chunk, ++it) {
+          const int b = it & 1;
+          if (!mbar_wait_cluster(&tfull[b], (it >> 1) & 1, a.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
+#pragma unroll
+          for (int o = 0; o < kMaxOwn; ++o) {
+            const int k = sub + o * kEpiPerQuarter;
+            if (k < n_chunks) {
+              uint32_t v[16];
+              tmem_ld16_async(tbase + (uint32_t)(k * kEpiCols), v);
+              tmem_wait_ld();
+#pragma unroll
+              for (int j = 0; j < kEpiCols; ++j) acc[o][j] += __uint_as_float(v[j]);
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive_cluster(tempty_even + (uint32_t)(b * sizeof(uint64_t)));
+        }
+        if (!ok) break;
+        if (cell < a.cells) {
+#pragma unroll
+          for (int o = 0; o < kMaxOwn; ++o) {
+            const int k = sub + o * kEpiPerQuarter;
+            if (k < n_chunks) {
+#pragma unroll
+              for (int j = 0; j < kEpiCols; ++j) {
+                const int row = rt * a.bn + k * kEpiCols + j;
+                if (row < a.rows) a.part[((size_t)z * a.rows + row) * a.part_ld + cell] = acc[o][j];
+              }
+            }
+          }
+        }
+      }
+    } else
     for (int t = pair; t < total; t += n_pairs, ++it) {
       const int b = it & 1;
       const PairJob &J = a.job[t / per_job];
@@ -546,13 +617,6 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
               orow = (row < a.out_split) ? J.out0 + (size_t)row * a.ldo
                                          : J.out1 + (size_t)(row - a.out_split) * a.ldo;
             if (row < a.rows && cell_ok) orow[cell] = f32_to_f64(fmaf(__uint_as_float(v[j]) * cs, rs, ra));
-          }
-        } else {
-          tmem_wait_ld();
-#pragma unroll
-          for (int j = 0; j < kEpiCols; ++j) {
-            const int row = row0 + j;
-            if (row < a.rows && cell_ok) a.part[((size_t)z * a.rows + row) * a.part_ld + cell] = __uint_as_float(v[j]);
           }
         }
       }
@@ -1253,6 +1317,7 @@ static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, 
   a.kb_total = t->an_kpad * F::kElem / kRowBytes;
   a.k_splits = t->an_splits;
   a.kb_per_split = t->an_kb_per;
+  a.kb_chunk = kAnalysisFill * F::kElem / kRowBytes;
   a.a_rows = t->an_modes_pad;
   a.b_rows = t->rows_pad;
   a.out_mode = 0;

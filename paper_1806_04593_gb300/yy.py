@@ -97,6 +97,24 @@ def load():
     lib.yy_grid_stage_ms.restype = I
     lib.yy_debug_fail_alloc_after.argtypes = [I]
     lib.yy_debug_fail_alloc_after.restype = None
+    lib.yy_batch_create.argtypes = [P, I, ctypes.POINTER(P)]
+    lib.yy_batch_create.restype = I
+    lib.yy_batch_prepare.argtypes = [P, I]
+    lib.yy_batch_prepare.restype = I
+    lib.yy_batch_tune.argtypes = [P, I, I, I, P]
+    lib.yy_batch_tune.restype = I
+    lib.yy_batch_set_analysis.argtypes = [P, I, I]
+    lib.yy_batch_set_analysis.restype = I
+    lib.yy_batch_potential.argtypes = [P, P, P, P, P, P, P, I, P]
+    lib.yy_batch_potential.restype = I
+    lib.yy_batch_grid.argtypes = [P, I]
+    lib.yy_batch_grid.restype = P
+    lib.yy_batch_last_launch_count.argtypes = [P]
+    lib.yy_batch_last_launch_count.restype = I
+    lib.yy_batch_last_device_status.argtypes = [P]
+    lib.yy_batch_last_device_status.restype = I
+    lib.yy_batch_destroy.argtypes = [P]
+    lib.yy_batch_destroy.restype = None
     _lib = lib
     return lib
 
@@ -207,6 +225,85 @@ def yy_grid_stage_ms(handle):
 
 def yy_debug_fail_alloc_after(n):
     load().yy_debug_fail_alloc_after(int(n))
+
+
+class FieldDesc(ctypes.Structure):
+    """yy_field_desc (include/yy.h)."""
+    _fields_ = [("r_edges", ctypes.c_void_p), ("n_r", ctypes.c_int), ("n_theta", ctypes.c_int),
+                ("n_phi", ctypes.c_int), ("delta_theta", ctypes.c_double), ("delta_phi", ctypes.c_double),
+                ("l_max", ctypes.c_int), ("G", ctypes.c_double)]
+
+
+def _ptr_array(items):
+    arr = (ctypes.c_void_p * len(items))()
+    for i, x in enumerate(items):
+        arr[i] = _ptr(x)
+    return arr
+
+
+class Batch:
+    """Owning wrapper of a yy_batch handle (many fields, one CUDA graph)."""
+
+    def __init__(self, specs):
+        self.specs = list(specs)
+        self._r = [np.ascontiguousarray(sp.r_edges, dtype=np.float64) for sp in self.specs]
+        descs = (FieldDesc * len(self.specs))()
+        for d, sp, r in zip(descs, self.specs, self._r):
+            d.r_edges = r.ctypes.data
+            d.n_r, d.n_theta, d.n_phi = int(r.size - 1), int(sp.n_theta), int(sp.n_phi)
+            d.delta_theta, d.delta_phi = float(sp.delta_theta), float(sp.delta_phi)
+            d.l_max, d.G = int(sp.lmax), float(sp.G)
+        h = ctypes.c_void_p()
+        st = load().yy_batch_create(ctypes.cast(descs, ctypes.c_void_p), len(self.specs), ctypes.byref(h))
+        if st != YY_OK:
+            raise YYError(st, "yy_batch_create")
+        self.handle = h.value
+
+    def prepare(self, prec):
+        st = load().yy_batch_prepare(self.handle, PRECISIONS.get(prec, prec))
+        if st != YY_OK:
+            raise YYError(st, "yy_batch_prepare")
+
+    def tune(self, prec, gradient=True, reps=2):
+        chosen = (ctypes.c_int * len(self.specs))()
+        st = load().yy_batch_tune(self.handle, PRECISIONS.get(prec, prec), int(bool(gradient)), int(reps),
+                                  ctypes.cast(chosen, ctypes.c_void_p))
+        if st != YY_OK:
+            raise YYError(st, "yy_batch_tune")
+        return list(chosen)
+
+    def set_analysis(self, field, method):
+        st = load().yy_batch_set_analysis(self.handle, int(field), ANALYSES.get(method, method))
+        if st != YY_OK:
+            raise YYError(st, "yy_batch_set_analysis")
+
+    def potential(self, rho_yin, rho_yang, phi_yin, phi_yang, grad_yin=None, grad_yang=None,
+                  prec=YY_FP64, stream=None):
+        gy = _ptr_array(grad_yin) if grad_yin is not None else None
+        gg = _ptr_array(grad_yang) if grad_yang is not None else None
+        vp = lambda a: ctypes.cast(a, ctypes.c_void_p) if a is not None else None
+        st = load().yy_batch_potential(self.handle, vp(_ptr_array(rho_yin)), vp(_ptr_array(rho_yang)),
+                                       vp(_ptr_array(phi_yin)), vp(_ptr_array(phi_yang)), vp(gy), vp(gg),
+                                       PRECISIONS.get(prec, prec), _stream(stream))
+        if st != YY_OK:
+            raise YYError(st, "yy_batch_potential")
+
+    def launch_count(self):
+        return load().yy_batch_last_launch_count(self.handle)
+
+    def device_status(self):
+        return load().yy_batch_last_device_status(self.handle)
+
+    def close(self):
+        if self.handle:
+            load().yy_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Grid:

@@ -1,0 +1,143 @@
+"""Batched solves (yy_batch_*): many fields of uneven shape in one CUDA graph.
+
+Checks, per the batched workload's test plan:
+  - every field of a batch equals the same field solved alone (float64,
+    bitwise: the graph runs the same kernels on the same data);
+  - graph replay is bitwise deterministic, and new buffers are recorded anew;
+  - the 64-field workload (n_r ~ U{100..600}, 2 / 1.5 / 1 degree cells,
+    l_max ~ U{10..40}) in the tuned FP16X2 form agrees with the float64 GPU
+    path field by field within the form's tolerance (Phi 1e-6, -grad Phi
+    1e-5, relative max-norm) and with the float64 oracle on sampled cells.
+"""
+
+import numpy as np
+import pytest
+
+from paper_1806_04593_gb300 import inputs
+
+from .gpu_common import lib, rel_max, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def yy():
+    require_gpu()
+    return lib()
+
+
+def _small_specs():
+    return [
+        inputs.tiny_grid(),
+        inputs.GridSpec("b1", np.logspace(-3, 0, 61), 45, 135, 0.0, 0.0, 10),
+        inputs.GridSpec("b2", np.logspace(-4, 0, 41), 60, 180, 0.0, 0.0, 12),
+        inputs.GridSpec("b3", np.concatenate([[0.0], np.logspace(-2, 0, 37)]), 20, 57, 0.03, 0.05, 7),
+    ]
+
+
+def _fields(specs, dev, gradient=True, seed0=5):
+    import torch
+    rho, out = [], []
+    for f, sp in enumerate(specs):
+        ry, rg = inputs.pns_density(sp, seed0 + f, 0.05)
+        rho.append((torch.from_numpy(ry).to(dev), torch.from_numpy(rg).to(dev)))
+        shape = (sp.n_r, sp.n_theta, sp.n_phi)
+        o = [torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(2)]
+        if gradient:
+            o += [torch.empty((3,) + shape, dtype=torch.float64, device=dev) for _ in range(2)]
+        out.append(o)
+    return rho, out
+
+
+def _run(b, rho, out, prec, stream=None):
+    grad = len(out[0]) == 4
+    b.potential([r[0] for r in rho], [r[1] for r in rho], [o[0] for o in out], [o[1] for o in out],
+                [o[2] for o in out] if grad else None, [o[3] for o in out] if grad else None,
+                prec=prec, stream=stream)
+
+
+def test_batch_fp64_equals_fields_solved_alone(yy):
+    import torch
+    dev = torch.device("cuda", 0)
+    specs = _small_specs()
+    b = yy.Batch(specs)
+    rho, out = _fields(specs, dev)
+    _run(b, rho, out, "fp64")
+    torch.cuda.synchronize()
+    assert b.device_status() == yy.YY_OK
+    assert b.launch_count() > 0
+    for sp, r, o in zip(specs, rho, out):
+        g = yy.Grid.from_spec(sp)
+        ref = g.solve(r[0], r[1], gradient=True, prec="fp64")
+        torch.cuda.synchronize()
+        assert torch.equal(o[0], ref["phi_yin"]) and torch.equal(o[1], ref["phi_yang"]), sp.name
+        assert torch.equal(o[2], ref["grad_yin"]) and torch.equal(o[3], ref["grad_yang"]), sp.name
+        g.close()
+    b.close()
+
+
+def test_batch_graph_replay_is_deterministic_and_rebinds(yy):
+    import torch
+    dev = torch.device("cuda", 0)
+    specs = _small_specs()
+    b = yy.Batch(specs)
+    b.prepare("fp16x2")
+    rho, out = _fields(specs, dev)
+    _run(b, rho, out, "fp16x2")
+    first = [[t.clone() for t in o] for o in out]
+    for o in out:
+        for t in o:
+            t.fill_(float("nan"))
+    _run(b, rho, out, "fp16x2")                       # replay of the cached graph
+    torch.cuda.synchronize()
+    for a, o in zip(first, out):
+        for x, y in zip(a, o):
+            assert torch.equal(x, y)
+    _, out2 = _fields(specs, dev)                     # other output buffers: recorded anew
+    _run(b, rho, out2, "fp16x2")
+    torch.cuda.synchronize()
+    for a, o in zip(first, out2):
+        for x, y in zip(a, o):
+            assert torch.equal(x, y)
+    assert b.device_status() == yy.YY_OK
+    b.close()
+
+
+def test_batched_workload_tuned_fp16x2(yy, oracle_grid):
+    """The 64-field workload: tuned FP16X2 batch against the float64 GPU path
+    (every field, whole fields) and against the oracle (four fields, sampled
+    cells)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    items = inputs.batched_specs()
+    specs = [sp for sp, _, _ in items]
+    b = yy.Batch(specs)
+    chosen = b.tune("fp16x2", gradient=True, reps=1)
+    assert len(chosen) == len(specs) and set(chosen) <= {yy.YY_ANALYSIS_DENSE, yy.YY_ANALYSIS_SEPARABLE}
+    rho, out = [], []
+    for sp, seed, eps in items:
+        ry, rg = inputs.pns_density(sp, seed, eps)
+        rho.append((torch.from_numpy(ry).to(dev), torch.from_numpy(rg).to(dev)))
+        shape = (sp.n_r, sp.n_theta, sp.n_phi)
+        out.append([torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(2)]
+                   + [torch.empty((3,) + shape, dtype=torch.float64, device=dev) for _ in range(2)])
+    _run(b, rho, out, "fp16x2")
+    torch.cuda.synchronize()
+    assert b.device_status() == yy.YY_OK
+    rng = np.random.default_rng(7)
+    for f, (sp, r, o) in enumerate(zip(specs, rho, out)):
+        g = yy.Grid.from_spec(sp)
+        ref = g.solve(r[0], r[1], gradient=True, prec="fp64")
+        torch.cuda.synchronize()
+        for q, (phi, grad) in enumerate((("phi_yin", "grad_yin"), ("phi_yang", "grad_yang"))):
+            assert rel_max(o[q].cpu().numpy(), ref[phi].cpu().numpy()) <= 1e-6, (f, phi)
+            assert rel_max(o[2 + q].cpu().numpy(), ref[grad].cpu().numpy()) <= 1e-5, (f, grad)
+        g.close()
+        if f % 16 == 0:
+            cells = np.sort(rng.choice(sp.n_ang, 12, replace=False))
+            ref_o = oracle_grid(sp).solve(r[0].cpu().numpy(), r[1].cpu().numpy(), gradient=True, cells=cells)
+            j, k = np.divmod(cells, sp.n_phi)
+            assert rel_max(o[0].cpu().numpy()[:, j, k], ref_o["phi_yin"]) <= 1e-6, f
+            assert rel_max(o[3].cpu().numpy()[:, :, j, k], ref_o["grad_yang"]) <= 1e-5, f
+        del ref
+    b.close()
