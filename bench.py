@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-field batched workload")
+    ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--cpu-sample", type=int, default=4, help="oracle evaluates 1/S of the cells")
     return ap.parse_args()
 
@@ -407,6 +409,10 @@ def run_ours(args, dist):
         "clocks": clk,
     }
 
+    # ---- the batched workload (uneven fields in one graph), rank-local
+    if not args.no_batch:
+        out["batched"] = run_batched(args, prec, gradient, dev, stream, flush)
+
     # ---- CPU baseline (oracle) and error vs the float64 oracle, rank 0 at N=1
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         info, ref, cells = cpu_baseline(spec, ry_np, rg_np, gradient, args.cpu_sample)
@@ -423,6 +429,80 @@ def run_ours(args, dist):
         out["error_vs_fp64_oracle"] = err
     grid.close()
     return out
+
+
+def run_batched(args, prec, gradient, dev, stream, flush):
+    """The batched workload: 64 fields of uneven size (n_r ~ U{100..600}, 2 /
+    1.5 / 1 degree cells, l_max ~ U{10..40}), the analysis of each field picked
+    by yy_batch_tune, all solves replayed as one CUDA graph per step.  Reports
+    field solves/s in the given form and in float64 on the same batch, and the
+    error of Phi against the float64 batch field by field."""
+    import torch
+
+    from paper_1806_04593_gb300 import inputs, yy
+
+    items = inputs.batched_specs()
+    specs = [sp for sp, _, _ in items]
+    b = yy.Batch(specs)
+    t0 = time.perf_counter()
+    chosen = b.tune(prec, gradient=gradient, reps=1)
+    tune_s = time.perf_counter() - t0
+    rho, outs = [], []
+    for sp, seed, eps in items:
+        ry, rg = inputs.pns_density(sp, seed, eps)
+        rho.append((torch.from_numpy(ry).to(dev), torch.from_numpy(rg).to(dev)))
+        shape = (sp.n_r, sp.n_theta, sp.n_phi)
+        o = [torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(2)]
+        if gradient:
+            o += [torch.empty((3,) + shape, dtype=torch.float64, device=dev) for _ in range(2)]
+        outs.append(o)
+
+    def step(form):
+        b.potential([r[0] for r in rho], [r[1] for r in rho], [o[0] for o in outs], [o[1] for o in outs],
+                    [o[2] for o in outs] if gradient else None, [o[3] for o in outs] if gradient else None,
+                    prec=form, stream=stream)
+
+    def timed(form, steps, warmup):
+        for _ in range(warmup):
+            step(form)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            step(form)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        st = b.device_status()
+        assert st == yy.YY_OK, yy.yy_status_string(st)
+        return sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+
+    ms = timed(prec, args.batch_steps, max(3, args.warmup))
+    launches = b.launch_count()
+    phi = [(o[0].clone(), o[1].clone()) for o in outs]
+    b.prepare("fp64")
+    ms64 = timed("fp64", 2, 1)
+    err = 0.0
+    for (py, pg), o in zip(phi, outs):
+        for got, ref in ((py, o[0]), (pg, o[1])):
+            err = max(err, float((got - ref).abs().max() / ref.abs().max()))
+    cells = sum(2 * sp.n_r * sp.n_ang for sp in specs)   # both patches
+    res = {
+        "workload": "64 fields, n_r ~ U{100..600}, 2 / 1.5 / 1 degree cells, l_max ~ U{10..40}, "
+                    "seeded proto-neutron-star densities with eps scale ~ U(0.01, 0.1)",
+        "value": len(specs) * 1e3 / ms, "unit": "field solves/s", "ms_per_step": ms,
+        "zone_cells_per_s": cells * 1e3 / ms,
+        "precision": prec, "gradient": gradient,
+        "analysis_chosen": {"dense": chosen.count(yy.YY_ANALYSIS_DENSE),
+                            "separable": chosen.count(yy.YY_ANALYSIS_SEPARABLE)},
+        "tune_s": tune_s, "graph_launches_per_step": 1, "kernels_per_step": launches,
+        "fp64_gpu_path": {"value": len(specs) * 1e3 / ms64, "unit": "field solves/s", "ms_per_step": ms64},
+        "speedup_vs_fp64": ms64 / ms,
+        "phi_rel_max_vs_fp64_worst_field": err,
+        "l2": "L2 flushed (256 MB write) before every timed step",
+    }
+    b.close()
+    return res
 
 
 def run_reference(args, dist):

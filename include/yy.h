@@ -272,11 +272,14 @@ yy_status yy_batch_prepare(yy_batch *b, yy_precision prec);
 /* Autotuner: for every field, time each analysis evaluation (YY_ANALYSIS_DENSE,
  * YY_ANALYSIS_SEPARABLE; reps solves each on zero densities in scratch
  * buffers it allocates and frees) in the given form, with or without the
- * gradient, and keep the faster.  chosen (NULL or n_fields entries) receives
- * the yy_analysis picked per field.  Prepares the form; synchronises. */
+ * gradient, and record the faster for that form: later graphs of that form
+ * use it (other forms keep theirs; untuned forms use YY_ANALYSIS_AUTO).
+ * chosen (NULL or n_fields entries) receives the yy_analysis picked per
+ * field.  Prepares the form; synchronises. */
 yy_status yy_batch_tune(yy_batch *b, yy_precision prec, int with_gradient, int reps, int *chosen);
 
-/* Set one field's analysis evaluation by hand (see yy_analysis). */
+/* Set one field's analysis evaluation by hand, for every form (see
+ * yy_analysis). */
 yy_status yy_batch_set_analysis(yy_batch *b, int field, yy_analysis method);
 
 /* Solve every field.  Each argument is a host array of n_fields device

@@ -257,7 +257,7 @@ yy_status yy_potential(yy_grid *g, const double *rho_yin, const double *rho_yang
   if (e == cudaSuccess && !simt) e = tc_pack_coefficients(g, prec, s);
   mark(2);
   if (e == cudaSuccess) {
-    if (simt && g->analysis_method != YY_ANALYSIS_DENSE && g->sep_syn_ok)
+    if (simt && g->analysis_method != YY_ANALYSIS_DENSE && (g->sep_syn_ok & (f32 ? 1 : 2)))
       e = synthesis_separable(g, phi_yin, phi_yang, grad_yin, grad_yang, !f32, s);
     else
       e = simt ? synthesis_simt(g, phi_yin, phi_yang, grad_yin, grad_yang, f32, s)

@@ -9,7 +9,7 @@
 // per (precision, gradient, buffer pointers): a replay costs one launch.
 // yy_batch_tune is the autotuner: for every field it times each analysis
 // evaluation (dense contraction, separable stages) on scratch buffers and
-// keeps the faster one.
+// records the faster one for that precision; the capture applies it.
 #include <string.h>
 
 #include <new>
@@ -21,6 +21,7 @@ namespace {
 
 constexpr int kBranches = 4;
 constexpr int kCacheSize = 4;
+constexpr int kPrecisions = YY_FP16X2 + 1;
 
 struct GraphEntry {
   int prec, grad;
@@ -34,6 +35,7 @@ struct yy_batch {
   int n;
   int device;
   std::vector<yy_grid *> grids;
+  std::vector<int> method;          // [field][precision]: analysis evaluation recorded for it
   cudaStream_t cap;                 // capture origin
   cudaStream_t branch[kBranches];
   cudaEvent_t fork, join[kBranches];
@@ -76,6 +78,7 @@ yy_status yy_batch_create(const yy_field_desc *fields, int n_fields, yy_batch **
   yy_batch *b = new (std::nothrow) yy_batch();
   if (!b) return YY_ERR_OOM;
   b->n = n_fields;
+  b->method.assign((size_t)n_fields * kPrecisions, (int)YY_ANALYSIS_AUTO);
   cudaGetDevice(&b->device);
   yy_status st = YY_OK;
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
@@ -111,9 +114,11 @@ yy_status yy_batch_prepare(yy_batch *b, yy_precision prec) {
 
 yy_status yy_batch_set_analysis(yy_batch *b, int field, yy_analysis method) {
   if (!b || field < 0 || field >= b->n) return YY_ERR_INVALID_ARG;
-  const yy_status st = yy_grid_set_analysis(b->grids[field], method);
-  if (st == YY_OK) drop_cache(b);
-  return st;
+  const yy_status st = yy_grid_set_analysis(b->grids[field], method);   // validates method
+  if (st != YY_OK) return st;
+  for (int p = 0; p < kPrecisions; ++p) b->method[(size_t)field * kPrecisions + p] = (int)method;
+  drop_cache(b);
+  return YY_OK;
 }
 
 yy_grid *yy_batch_grid(yy_batch *b, int field) {
@@ -122,7 +127,7 @@ yy_grid *yy_batch_grid(yy_batch *b, int field) {
 }
 
 yy_status yy_batch_tune(yy_batch *b, yy_precision prec, int with_gradient, int reps, int *chosen) {
-  if (!b || reps < 1) return YY_ERR_INVALID_ARG;
+  if (!b || reps < 1 || (int)prec < 0 || (int)prec >= kPrecisions) return YY_ERR_INVALID_ARG;
   yy_status st = yy_batch_prepare(b, prec);
   if (st != YY_OK) return st;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -161,7 +166,8 @@ yy_status yy_batch_tune(yy_batch *b, yy_precision prec, int with_gradient, int r
       }
     }
     cudaFree(buf);
-    yy_grid_set_analysis(g, cands[pick]);
+    yy_grid_set_analysis(g, YY_ANALYSIS_AUTO);
+    b->method[(size_t)i * kPrecisions + prec] = (int)cands[pick];
     if (chosen) chosen[i] = (int)cands[pick];
   }
   cudaEventDestroy(e0);
@@ -175,6 +181,7 @@ yy_status yy_batch_potential(yy_batch *b, const double *const *rho_yin, const do
                              double *const *grad_yang, yy_precision prec, void *cuda_stream) {
   if (!b || !rho_yin || !rho_yang || !phi_yin || !phi_yang) return YY_ERR_INVALID_ARG;
   if ((grad_yin == nullptr) != (grad_yang == nullptr)) return YY_ERR_INVALID_ARG;
+  if ((int)prec < 0 || (int)prec >= kPrecisions) return YY_ERR_INVALID_ARG;
   int dev = -1;
   cudaGetDevice(&dev);
   if (dev != b->device) return YY_ERR_INVALID_ARG;
@@ -207,6 +214,7 @@ yy_status yy_batch_potential(yy_batch *b, const double *const *rho_yin, const do
   int launches = 0;
   for (int i = 0; i < b->n && st == YY_OK; ++i) {
     yy_grid *g = b->grids[i];
+    yy_grid_set_analysis(g, (yy_analysis)b->method[(size_t)i * kPrecisions + prec]);
     st = yy_potential(g, rho_yin[i], rho_yang[i], phi_yin[i], phi_yang[i], grad ? grad_yin[i] : nullptr,
                       grad ? grad_yang[i] : nullptr, prec, b->branch[i % kBranches]);
     launches += g->launches;

@@ -51,6 +51,7 @@ struct yy_grid {
   int last_separable;   // the last solve used the separable analysis
   int sep_nt_pad;       // 2 l_max + 1 azimuthal functions, padded to a multiple of 4
   int sep_ok;           // the grid fits the separable kernels' shared memory: bit 0 fp32, bit 1 float64
+  int sep_jc[2];        // rows per item of the azimuthal stage (fp32, float64)
   int sep_phi_blocks[2];  // persistent blocks of the azimuthal stage (fp32, float64)
   double *sep_az;       // [n_phi][sep_nt_pad] cell integrals of the azimuthal functions
   float *sep_az32, *sep_w32, *sep_tb32;   // fp32 copies of sep_az, w, tbar
@@ -60,7 +61,8 @@ struct yy_grid {
   double *sep_P, *sep_dP, *sep_Qs;   // [n_theta][n_lm] Legendre factors at the cell colatitudes
   double *sep_tr;                    // [2 l_max + 1][n_phi] 1, cos, sin at the cell longitudes
   float *sep_P32, *sep_dP32, *sep_Qs32, *sep_tr32;   // fp32 copies
-  int sep_syn_ok;                    // the grid fits the separable synthesis's shared memory
+  int sep_syn_ok;                    // the grid fits the separable synthesis's shared memory: bit 0 fp32, bit 1 float64
+  int sep_syn_rows[2];               // rows of G per chunk (fp32, float64)
   size_t sep_syn_smem[2];            // its shared memory (fp32, float64)
   int sep_syn_blocks[2];             // its persistent blocks (fp32, float64)
 

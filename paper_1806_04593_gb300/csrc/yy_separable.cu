@@ -106,10 +106,11 @@ __global__ void k_round(size_t n, const double *__restrict__ src, float *__restr
   if (e < n) dst[e] = (float)src[e];
 }
 
-constexpr int kJC = 48;    // rows j per work item
+constexpr int kJC = 48;    // rows j per work item (kJCSmall where the table leaves too little room)
+constexpr int kJCSmall = 16;
 constexpr int kTJ = 4;     // rows per thread
 constexpr int kTT = 4;     // azimuthal functions per thread
-constexpr int kXP = kJC + 4;   // padded row stride of the staged densities
+__host__ __device__ constexpr int xpad(int jc) { return jc + 4; }   // padded row stride of the staged densities
 
 // four consecutive values, 16-byte aligned
 __device__ __forceinline__ void ld4(const float *p, float (&o)[4]) {
@@ -143,25 +144,26 @@ __device__ __forceinline__ void pair_fma(float &h, float &l, float ah, float al,
 }
 
 // Azimuthal stage, persistent: each block keeps the table az in shared
-// memory and takes work items (shell, chunk of kJC rows j) in turn.
-//  1. all threads stage the chunk (kJC n_phi consecutive densities) with 16
+// memory and takes work items (shell, chunk of JC rows j) in turn.
+//  1. all threads stage the chunk (JC n_phi consecutive densities) with 16
 //     independent loads in flight each, fold in w and store it transposed;
 //  2. (fp32) one warp per row forms the row's compensated sum (the m = 0
 //     azimuthal sum without the factor d_phi) as an unevaluated fp32 pair;
 //  3. each thread accumulates a tile of kTJ rows x kTT functions over all k
 //     with two vector shared-memory loads per 16 products.
-template <typename T>
+template <typename T, int JC>
 __global__ void k_sep_phi(int n_r, int n_theta, int n_phi, int nt_pad, const double *__restrict__ rho0,
                           const double *__restrict__ rho1, const T *__restrict__ w, const T *__restrict__ az,
                           T *__restrict__ F, float2 *__restrict__ F0) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T *as = reinterpret_cast<T *>(smraw);                  // [n_phi][nt_pad]
-  T *xs = as + (size_t)n_phi * nt_pad;                   // [n_phi][kXP]
+  constexpr int XP = xpad(JC);
+  T *xs = as + (size_t)n_phi * nt_pad;                   // [n_phi][XP]
   const int tg = nt_pad / kTT;
   const int tt = threadIdx.x % tg, tj = threadIdx.x / tg;   // function group, row group
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
   const size_t n_ang = (size_t)n_theta * n_phi;
-  const int chunks = (n_theta + kJC - 1) / kJC;
+  const int chunks = (n_theta + JC - 1) / JC;
   const int items = 2 * n_r * chunks;
   constexpr int kU = 16;
   const float inv_phi = 1.0f / (float)n_phi;
@@ -169,14 +171,14 @@ __global__ void k_sep_phi(int n_r, int n_theta, int n_phi, int nt_pad, const dou
   for (int e = threadIdx.x; e < n_phi * nt_pad; e += blockDim.x) as[e] = az[e];
 
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    const int shell = item / chunks, j0 = (item % chunks) * kJC;
+    const int shell = item / chunks, j0 = (item % chunks) * JC;
     const int p = shell / n_r, i = shell % n_r;
-    const int rows = min(kJC, n_theta - j0);
+    const int rows = min(JC, n_theta - j0);
     const int count = rows * n_phi;                      // consecutive values of the chunk
     const double *src = (p == 0 ? rho0 : rho1) + (size_t)i * n_ang + (size_t)j0 * n_phi;
     const T *wsrc = w + (size_t)j0 * n_phi;
     __syncthreads();   // the previous item's tiles are done with xs (and as is written)
-    for (int e0 = threadIdx.x; e0 < kJC * n_phi; e0 += kU * blockDim.x) {
+    for (int e0 = threadIdx.x; e0 < JC * n_phi; e0 += kU * blockDim.x) {
       double rv[kU];
       T wv[kU];
 #pragma unroll
@@ -188,7 +190,7 @@ __global__ void k_sep_phi(int n_r, int n_theta, int n_phi, int nt_pad, const dou
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
         const int e = e0 + u * blockDim.x;
-        if (e < kJC * n_phi) {
+        if (e < JC * n_phi) {
           // e = jj n_phi + k: quotient from the float reciprocal, then corrected
           int jj = (int)((float)e * inv_phi);
           int k = e - jj * n_phi;
@@ -199,7 +201,7 @@ __global__ void k_sep_phi(int n_r, int n_theta, int n_phi, int nt_pad, const dou
             ++jj;
             k -= n_phi;
           }
-          xs[(size_t)k * kXP + jj] = to_t<T>(rv[u]) * wv[u];
+          xs[(size_t)k * XP + jj] = to_t<T>(rv[u]) * wv[u];
         }
       }
     }
@@ -207,7 +209,7 @@ __global__ void k_sep_phi(int n_r, int n_theta, int n_phi, int nt_pad, const dou
     if constexpr (sizeof(T) == 4) {
       for (int jj = warp; jj < rows; jj += n_warps) {
         float h = 0.0f, l = 0.0f;
-        for (int k = lane; k < n_phi; k += 32) pair_add(h, l, xs[(size_t)k * kXP + jj]);
+        for (int k = lane; k < n_phi; k += 32) pair_add(h, l, xs[(size_t)k * XP + jj]);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
           const float oh = __shfl_xor_sync(0xffffffffu, h, off);
@@ -218,7 +220,7 @@ __global__ void k_sep_phi(int n_r, int n_theta, int n_phi, int nt_pad, const dou
         if (lane == 0) F0[(size_t)shell * n_theta + j0 + jj] = make_float2(h, l);
       }
     }
-    if (tj < kJC / kTJ) {
+    if (tj < JC / kTJ) {
       T acc[kTJ][kTT];
 #pragma unroll
       for (int a = 0; a < kTJ; ++a)
@@ -227,7 +229,7 @@ __global__ void k_sep_phi(int n_r, int n_theta, int n_phi, int nt_pad, const dou
 #pragma unroll 2
       for (int k = 0; k < n_phi; ++k) {
         T x4[4], a4[4];
-        ld4(xs + (size_t)k * kXP + tj * kTJ, x4);
+        ld4(xs + (size_t)k * XP + tj * kTJ, x4);
         ld4(as + (size_t)k * nt_pad + tt * kTT, a4);
 #pragma unroll
         for (int a = 0; a < kTJ; ++a)
@@ -296,15 +298,26 @@ __global__ void __launch_bounds__(256) k_sep_theta(int n_theta, int n_lm, int lm
   }
 }
 
+// launch shape of the azimuthal stage with JC rows per item
+int phi_threads(int nt_pad, int jc) { return ((nt_pad / kTT) * (jc / kTJ) + 31) / 32 * 32; }   // whole warps
+size_t phi_smem(const yy_grid *g, int nt_pad, int jc, size_t el) {
+  return (size_t)g->n_phi * (nt_pad + xpad(jc)) * el;
+}
+
 template <typename T>
 cudaError_t run_separable(yy_grid *g, const double *rho_yin, const double *rho_yang, const T *w, const T *az,
                           const T *tb, T *F, int blocks, cudaStream_t s) {
   const int nt_pad = g->sep_nt_pad;
-  const int threads = ((nt_pad / kTT) * (kJC / kTJ) + 31) / 32 * 32;   // whole warps: the staging uses shuffles
-  const size_t smem_phi = (size_t)g->n_phi * (nt_pad + kXP) * sizeof(T);
-  const int items = 2 * g->n_r * ((g->n_theta + kJC - 1) / kJC);
-  k_sep_phi<T><<<std::min(items, blocks), threads, smem_phi, s>>>(g->n_r, g->n_theta, g->n_phi, nt_pad, rho_yin,
-                                                                   rho_yang, w, az, F, (float2 *)g->sep_F0);
+  const int jc = g->sep_jc[sizeof(T) == 8];
+  const int threads = phi_threads(nt_pad, jc);
+  const size_t smem_phi = phi_smem(g, nt_pad, jc, sizeof(T));
+  const int grid = std::min(2 * g->n_r * ((g->n_theta + jc - 1) / jc), blocks);
+  if (jc == kJC)
+    k_sep_phi<T, kJC><<<grid, threads, smem_phi, s>>>(g->n_r, g->n_theta, g->n_phi, nt_pad, rho_yin, rho_yang, w, az,
+                                                      F, (float2 *)g->sep_F0);
+  else
+    k_sep_phi<T, kJCSmall><<<grid, threads, smem_phi, s>>>(g->n_r, g->n_theta, g->n_phi, nt_pad, rho_yin, rho_yang, w,
+                                                           az, F, (float2 *)g->sep_F0);
   g->launches++;
   const size_t smem_theta = (size_t)g->n_theta * nt_pad * sizeof(T) + (size_t)(g->n_theta + 1) * sizeof(float2);
   k_sep_theta<T><<<2 * g->n_r, 256, smem_theta, s>>>(g->n_theta, g->n_lm, g->lmax + 1, nt_pad, tb, g->sep_tb0, F,
@@ -326,7 +339,7 @@ struct SepOut {
 };
 
 template <typename T>
-__global__ void k_sep_synth(int n_r, int n_theta, int n_phi, int lmax, int n_lm, int n_fields,
+__global__ void k_sep_synth(int n_r, int n_theta, int n_phi, int lmax, int n_lm, int n_fields, int jr,
                             const double *__restrict__ Q, const T *__restrict__ P, const T *__restrict__ dP,
                             const T *__restrict__ Qs, const T *__restrict__ tr, const SepOut out) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -334,8 +347,8 @@ __global__ void k_sep_synth(int n_r, int n_theta, int n_phi, int lmax, int n_lm,
   const int ntr = (n_phi + 3) & ~3;                     // padded row of the trig table
   const int ntp = nt | 1;                               // odd row stride of G
   T *trs = reinterpret_cast<T *>(smraw);                // [nt][ntr]
-  T *Gs = trs + (size_t)nt * ntr;                       // [n_theta][ntp]
-  T *qs = Gs + (size_t)n_theta * ntp;                   // [n_lm]
+  T *Gs = trs + (size_t)nt * ntr;                       // [jr][ntp]: G of one chunk of jr rows
+  T *qs = Gs + (size_t)jr * ntp;                        // [n_lm]
   for (int e = threadIdx.x; e < nt * ntr; e += blockDim.x) {
     const int t = e / ntr, k = e % ntr;
     trs[e] = (k < n_phi) ? tr[(size_t)t * n_phi + k] : T(0);
@@ -351,43 +364,48 @@ __global__ void k_sep_synth(int n_r, int n_theta, int n_phi, int lmax, int n_lm,
       __syncthreads();   // trs written / the previous field's G and q consumed
       for (int idx = threadIdx.x; idx < n_lm; idx += blockDim.x) qs[idx] = to_t<T>(Q[qb * qsz + (size_t)shell * n_lm + idx]);
       __syncthreads();
-      for (int e = threadIdx.x; e < n_theta * nt; e += blockDim.x) {
-        const int j = e / nt, t = e % nt;
-        const int m = (t + 1) / 2;
-        const T *tj = tab + (size_t)j * n_lm;
-        T g = T(0);
-        if (f < 3) {
-          for (int l = m; l <= lmax; ++l) g = fma(qs[l * l + t], tj[l * l + t], g);
-        } else if (t > 0) {
-          const int src = (t & 1) ? t + 1 : t - 1;      // cos slot <- sin coefficient, sin slot <- cos
-          for (int l = m; l <= lmax; ++l) g = fma(qs[l * l + src], tj[l * l + t], g);
-          if (!(t & 1)) g = -g;
-        }
-        Gs[j * ntp + t] = g;
-      }
-      __syncthreads();
       double *dst = out.o[f][p] + (size_t)i * n_ang;
-      for (int e = threadIdx.x; e < n_theta * kg; e += blockDim.x) {
-        const int j = e / kg, k0 = (e % kg) * 4;
-        T acc[4] = {T(0), T(0), T(0), T(0)};
-        const T *gj = Gs + j * ntp;
-        for (int t = 0; t < nt; ++t) {
-          T a4[4];
-          ld4(trs + (size_t)t * ntr + k0, a4);
-          const T gv = gj[t];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) acc[u] = fma(gv, a4[u], acc[u]);
+      for (int j0 = 0; j0 < n_theta; j0 += jr) {
+        const int rows = min(jr, n_theta - j0);
+        for (int e = threadIdx.x; e < rows * nt; e += blockDim.x) {
+          const int jj = e / nt, t = e % nt;
+          const int m = (t + 1) / 2;
+          const T *tj = tab + (size_t)(j0 + jj) * n_lm;
+          T g = T(0);
+          if (f < 3) {
+            for (int l = m; l <= lmax; ++l) g = fma(qs[l * l + t], tj[l * l + t], g);
+          } else if (t > 0) {
+            const int src = (t & 1) ? t + 1 : t - 1;      // cos slot <- sin coefficient, sin slot <- cos
+            for (int l = m; l <= lmax; ++l) g = fma(qs[l * l + src], tj[l * l + t], g);
+            if (!(t & 1)) g = -g;
+          }
+          Gs[jj * ntp + t] = g;
         }
-        double *o = dst + (size_t)j * n_phi + k0;
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * kg; e += blockDim.x) {
+          const int jj = e / kg, k0 = (e % kg) * 4;
+          const int j = j0 + jj;
+          T acc[4] = {T(0), T(0), T(0), T(0)};
+          const T *gj = Gs + jj * ntp;
+          for (int t = 0; t < nt; ++t) {
+            T a4[4];
+            ld4(trs + (size_t)t * ntr + k0, a4);
+            const T gv = gj[t];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (k0 + u < n_phi) {
-            if constexpr (sizeof(T) == 4)
-              o[u] = widen(acc[u]);
-            else
-              o[u] = acc[u];
+            for (int u = 0; u < 4; ++u) acc[u] = fma(gv, a4[u], acc[u]);
+          }
+          double *o = dst + (size_t)j * n_phi + k0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (k0 + u < n_phi) {
+              if constexpr (sizeof(T) == 4)
+                o[u] = widen(acc[u]);
+              else
+                o[u] = acc[u];
+            }
           }
         }
+        __syncthreads();   // G of this chunk consumed
       }
     }
   }
@@ -432,51 +450,55 @@ cudaError_t separable_prepare(yy_grid *g) {
     k_round<<<(unsigned)((n_p + 255) / 256), 256>>>(n_p, g->sep_Qs, g->sep_Qs32);
     k_round<<<(unsigned)((n_tr + 255) / 256), 256>>>(n_tr, g->sep_tr, g->sep_tr32);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // shared memory: the trig table, G of jr rows (all n_theta where they
+    // fit, else as many as fit) and one shell's coefficients
     const int nt = 2 * g->lmax + 1, ntr = (g->n_phi + 3) & ~3;
+    const void *ks[2] = {(const void *)k_sep_synth<float>, (const void *)k_sep_synth<double>};
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+    g->sep_syn_ok = 0;
     for (int q = 0; q < 2; ++q) {
       const size_t el = q == 0 ? sizeof(float) : sizeof(double);
-      g->sep_syn_smem[q] = ((size_t)nt * ntr + (size_t)g->n_theta * (nt | 1) + g->n_lm) * el;
-    }
-    g->sep_syn_ok = g->sep_syn_smem[1] <= 227 * 1024;
-    if (g->sep_syn_ok) {
-      const void *ks[2] = {(const void *)k_sep_synth<float>, (const void *)k_sep_synth<double>};
-      int sms = 0;
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-      for (int q = 0; q < 2; ++q) {
-        if ((e = cudaFuncSetAttribute(ks[q], cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)) != cudaSuccess)
-          return e;
-        int nb = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ks[q], 256, g->sep_syn_smem[q])) != cudaSuccess)
-          return e;
-        g->sep_syn_blocks[q] = std::max(nb, 1) * sms;
-      }
+      const size_t fixed = ((size_t)nt * ntr + g->n_lm) * el, per_row = (size_t)(nt | 1) * el;
+      if (fixed + per_row > 227 * 1024) continue;
+      const int jr = (int)std::min<size_t>(g->n_theta, (227 * 1024 - fixed) / per_row);
+      g->sep_syn_rows[q] = jr;
+      g->sep_syn_smem[q] = fixed + jr * per_row;
+      if ((e = cudaFuncSetAttribute(ks[q], cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)) != cudaSuccess)
+        return e;
+      int nb = 0;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ks[q], 256, g->sep_syn_smem[q])) != cudaSuccess)
+        return e;
+      g->sep_syn_blocks[q] = std::max(nb, 1) * sms;
+      g->sep_syn_ok |= 1 << q;
     }
   }
   // shared memory of the azimuthal stage (the table and one chunk of rows);
   // grids too large for it leave the separable analysis unavailable
-  const size_t smem64 = (size_t)g->n_phi * (nt_pad + kXP) * sizeof(double);
-  const size_t smem32 = (size_t)g->n_phi * (nt_pad + kXP) * sizeof(float);
+  // (the float64 table at l_max 40 on 1-degree cells needs the short chunk)
   const size_t tail_t = (size_t)(g->n_theta + 1) * sizeof(float2);
-  const size_t smem_t32 = (size_t)g->n_theta * nt_pad * sizeof(float) + tail_t;
-  const size_t smem_t64 = (size_t)g->n_theta * nt_pad * sizeof(double) + tail_t;
-  g->sep_ok = (smem32 <= 227 * 1024 && smem_t32 <= 227 * 1024 ? 1 : 0) |
-              (smem64 <= 227 * 1024 && smem_t64 <= 227 * 1024 ? 2 : 0);
-  if (!g->sep_ok) return cudaSuccess;
-  const void *kp[2] = {(const void *)k_sep_phi<float>, (const void *)k_sep_phi<double>};
-  const size_t sm[2] = {smem32, smem64};
+  g->sep_ok = 0;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-  // the attribute belongs to the kernel, not to this grid: always the maximum
   for (int q = 0; q < 2; ++q) {
-    if (!(g->sep_ok & (1 << q))) continue;
-    if ((e = cudaFuncSetAttribute(kp[q], cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)) != cudaSuccess)
+    const size_t el = q ? sizeof(double) : sizeof(float);
+    if ((size_t)g->n_theta * nt_pad * el + tail_t > 227 * 1024) continue;
+    const int jc = phi_smem(g, nt_pad, kJC, el) <= 227 * 1024 ? kJC : kJCSmall;
+    const size_t sm = phi_smem(g, nt_pad, jc, el);
+    if (sm > 227 * 1024) continue;
+    const void *kp = q ? (jc == kJC ? (const void *)k_sep_phi<double, kJC> : (const void *)k_sep_phi<double, kJCSmall>)
+                       : (jc == kJC ? (const void *)k_sep_phi<float, kJC> : (const void *)k_sep_phi<float, kJCSmall>);
+    // the attribute belongs to the kernel, not to this grid: always the maximum
+    if ((e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)) != cudaSuccess)
       return e;
     int nb = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kp[q], ((nt_pad / kTT) * (kJC / kTJ) + 31) / 32 * 32,
-                                                           sm[q])) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kp, phi_threads(nt_pad, jc), sm)) != cudaSuccess)
       return e;
+    g->sep_jc[q] = jc;
     g->sep_phi_blocks[q] = std::max(nb, 1) * sms;
+    g->sep_ok |= 1 << q;
   }
+  if (!g->sep_ok) return cudaSuccess;
   for (auto f : {(const void *)k_sep_theta<float>, (const void *)k_sep_theta<double>})
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)) != cudaSuccess)
       return e;
@@ -498,11 +520,11 @@ cudaError_t synthesis_separable(yy_grid *g, double *phi_yin, double *phi_yang, d
   const int blocks = std::min(2 * g->n_r, g->sep_syn_blocks[q]);
   if (fp64)
     k_sep_synth<double><<<blocks, 256, g->sep_syn_smem[1], s>>>(g->n_r, g->n_theta, g->n_phi, g->lmax, g->n_lm,
-                                                                n_fields, g->Q, g->sep_P, g->sep_dP, g->sep_Qs,
+                                                                n_fields, g->sep_syn_rows[1], g->Q, g->sep_P, g->sep_dP, g->sep_Qs,
                                                                 g->sep_tr, o);
   else
     k_sep_synth<float><<<blocks, 256, g->sep_syn_smem[0], s>>>(g->n_r, g->n_theta, g->n_phi, g->lmax, g->n_lm,
-                                                               n_fields, g->Q, g->sep_P32, g->sep_dP32, g->sep_Qs32,
+                                                               n_fields, g->sep_syn_rows[0], g->Q, g->sep_P32, g->sep_dP32, g->sep_Qs32,
                                                                g->sep_tr32, o);
   g->launches++;
   return cudaGetLastError();

@@ -176,6 +176,34 @@ def test_fp64_production_sampled_cells(yy, oracle_grid):
         assert rel_max(gg, ref["grad_" + q]) <= TOL_FP64, q
 
 
+def test_fp64_separable_at_the_largest_batched_shape(yy, oracle_grid):
+    """1-degree cells at l_max = 40 (the largest field of the batched
+    workload): the float64 azimuthal stage runs with its short row chunk and
+    the separable synthesis in row chunks, since neither's tables fit shared
+    memory whole.  Sampled cells against the oracle, whole fields against the
+    dense contraction."""
+    spec = inputs.GridSpec("fine40", np.logspace(-3, 0, 13), 90, 270, 0.0, 0.0, 40)
+    g = _grid(yy, spec)
+    ry, rg = inputs.pns_density(spec, 17, 0.08)
+    sep = gpu_solve(g, ry, rg, gradient=True)
+    flops_sep = g.flops(True)
+    g.set_analysis("dense")
+    try:
+        dense = gpu_solve(g, ry, rg, gradient=True)
+        assert flops_sep < g.flops(True)        # the separable analysis did run
+    finally:
+        g.set_analysis("auto")
+    for key in sep:
+        assert rel_max(sep[key], dense[key]) <= TOL_FP64, key
+    rng = np.random.default_rng(40)
+    cells = np.sort(rng.choice(spec.n_ang, 24, replace=False))
+    ref = oracle_grid(spec).solve(ry, rg, gradient=True, cells=cells)
+    j, k = np.divmod(cells, spec.n_phi)
+    for q in ("yin", "yang"):
+        assert rel_max(sep["phi_" + q][:, j, k], ref["phi_" + q]) <= TOL_FP64, q
+        assert rel_max(sep["grad_" + q][:, :, j, k], ref["grad_" + q]) <= TOL_FP64, q
+
+
 def test_ragged_small_grid(yy):
     """Odd sizes that leave ragged tiles everywhere (n_r, n_ang, n_lm not
     multiples of any tile), r_edges[0] = 0, unequal buffers."""
