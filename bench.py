@@ -39,8 +39,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # 152 SMs x 2 DFMA/clk x 2 f
 # DRAM bytes (read + write) of one synthesis launch, from an ncu capture of
 # this workload (profiles/k_tc_pair_fp16x2_production.md); valid only for the
 # kernel source it was taken with, null otherwise.
-_TRAFFIC = {("fp16x2", True): (285.875456e6 + 798.645504e6,
-                               "c60db0e7568fc56fbd539236276931b0cadca2fe7978f389f3a011d296ce34f0")}
+_TRAFFIC = {("fp16x2", True): (287.467008e6 + 798.509312e6,
+                               "68b51d16915b46b142e744dc928059e2e6d097aba55c071e53ded34bd84b0274")}
 
 
 def _recorded_traffic(prec, gradient):
