@@ -12,6 +12,7 @@ paper is silent or garbled.
 
 from .yinyang import (  # noqa: F401
     OracleGrid,
+    OraclePolarGrid,
     angular_edges,
     assoc_legendre,
     azimuthal_integrals,

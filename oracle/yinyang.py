@@ -49,6 +49,10 @@ R8  T_j^(lm) (Eq. tlm) has a plain definition, an integral; the oracle
     agree with it to rounding, except that the T^(ll) diagonal amplifies
     rounding by ~(1/sin^2 theta)^(l/2) (6e-12 relative at l = 25 on 1-degree
     cells, 1e-6 at l = 40 on 7.5-degree cells).
+R10 Full spherical polar grid (§2): the paper does not state the cell
+    layout; we take uniform cells, theta_j^+- = (j, j+1) pi / n_theta and
+    phi_k^+- = (k, k+1) 2 pi / n_phi, one patch with w = 1, evaluated at its
+    own cell centres (R3).
 """
 
 from __future__ import annotations
@@ -394,10 +398,16 @@ class OracleGrid:
         self.lmax = int(lmax)
         self.G = float(G)
         self.theta_edges, self.phi_edges = angular_edges(n_theta, n_phi, delta_theta, delta_phi)
+        self._constant_terms(overlap_weights(self.theta_edges, self.phi_edges, delta_theta, delta_phi))
+
+    def _constant_terms(self, w):
+        """The density-independent factors of Eqs. ac/as, rin/rout and
+        potential for the cell edges set on self, with surface weights w."""
+        n_theta, n_phi = self.n_theta, self.n_phi
         self.theta_c = 0.5 * (self.theta_edges[:-1] + self.theta_edges[1:])
         self.phi_c = 0.5 * (self.phi_edges[:-1] + self.phi_edges[1:])
         L = self.lmax
-        self.w = overlap_weights(self.theta_edges, self.phi_edges, delta_theta, delta_phi)
+        self.w = w
         self.T = polar_integrals(L, self.theta_edges)
         self.C, self.S = azimuthal_integrals(L, self.phi_edges)
         self.R_in, self.R_out = radial_integrals(L, self.r_edges)
@@ -531,3 +541,44 @@ class OracleGrid:
             for key in list(res):
                 res[key] = res[key].reshape(((3,) if key.startswith("grad") else ()) + shp)
         return res
+
+
+class OraclePolarGrid(OracleGrid):
+    """The full spherical polar grid of §2: one patch, theta_j^+- = (j, j+1)
+    pi / n_theta and phi_k^+- = (k, k+1) 2 pi / n_phi, every cell counted once
+    (w = 1), no second patch.  Eqs. potential, phiin_tot and phiout_tot with
+    the sums over all cells of the sphere; the radial sums and the evaluation
+    are those of :class:`OracleGrid`.
+    """
+
+    def __init__(self, r_edges, n_theta, n_phi, lmax, G=1.0):
+        self.r_edges = np.asarray(r_edges, dtype=np.float64)
+        self.n_r = self.r_edges.size - 1
+        self.n_theta, self.n_phi = int(n_theta), int(n_phi)
+        self.delta_theta = self.delta_phi = 0.0
+        self.lmax = int(lmax)
+        self.G = float(G)
+        self.theta_edges = math.pi / self.n_theta * np.arange(self.n_theta + 1)
+        self.phi_edges = 2.0 * math.pi / self.n_phi * np.arange(self.n_phi + 1)
+        self._constant_terms(np.ones((self.n_theta, self.n_phi)))
+
+    def solve(self, rho, gradient=False, cells=None):
+        """Phi (and optionally -grad Phi in the local spherical basis, R7) at
+        the interfaces r_n^+ and the cell centres (R3).  Returns 'phi' of
+        shape (n_R, n_theta, n_phi) (or (n_R, n_cells) for a cell sample) and
+        'grad' of shape (3, ...)."""
+        coef = self.radial_sums(*self.analysis(rho))
+        th = self.target_theta if cells is None else self.target_theta[cells]
+        ph = self.target_phi if cells is None else self.target_phi[cells]
+        res = {"phi": self.evaluate(coef, th, ph)}
+        if gradient:
+            v = self.evaluate_gradient(coef, th, ph)
+            e_r, e_t, e_p = spherical_basis(th, ph)
+            res["grad"] = np.stack([np.einsum("cnp,cp->np", v, e) for e in (e_r, e_t, e_p)])
+        if cells is None:
+            shp = (self.n_r, self.n_theta, self.n_phi)
+            res["phi"] = res["phi"].reshape(shp)
+            if gradient:
+                res["grad"] = res["grad"].reshape((3,) + shp)
+        return res
+

@@ -8,6 +8,10 @@ Densities are defined in a global Cartesian frame equal to the Yin frame.
 A Yang cell's local Cartesian position (x, y, z) sits at (-x, z, y) in the
 global frame (the Yin-Yang map, its own inverse).  Arrays are float64
 [n_r][n_theta][n_phi] per patch, C-contiguous.
+
+A full spherical polar grid (``GridSpec.polar``) has one patch covering
+theta in [0, pi] and phi in [0, 2 pi) in the global frame; the density
+functions then return (rho, None).
 """
 
 from __future__ import annotations
@@ -29,6 +33,7 @@ class GridSpec:
     delta_phi: float
     lmax: int
     G: float = 1.0
+    polar: bool = False      # one patch over the whole sphere (buffers unused)
 
     @property
     def n_r(self) -> int:
@@ -43,6 +48,20 @@ def _patch_step(n_theta, n_phi, delta_theta, delta_phi):
     dth = (math.pi / 2 + 2 * delta_theta) / n_theta
     dph = (3 * math.pi / 2 + 2 * delta_phi) / n_phi
     return dth, dph
+
+
+def angular_cell_edges(spec: GridSpec):
+    """Cell edges in theta and phi of one patch (both patches share them)."""
+    if spec.polar:
+        return (math.pi / spec.n_theta * np.arange(spec.n_theta + 1),
+                2 * math.pi / spec.n_phi * np.arange(spec.n_phi + 1))
+    dth, dph = _patch_step(spec.n_theta, spec.n_phi, spec.delta_theta, spec.delta_phi)
+    return (math.pi / 4 - spec.delta_theta + dth * np.arange(spec.n_theta + 1),
+            -3 * math.pi / 4 - spec.delta_phi + dph * np.arange(spec.n_phi + 1))
+
+
+def patches(spec: GridSpec):
+    return ("yin",) if spec.polar else ("yin", "yang")
 
 
 def tiny_grid() -> GridSpec:
@@ -65,7 +84,24 @@ def production_grid() -> GridSpec:
     return GridSpec("production", np.logspace(-4, 0, 551), 90, 270, 0.0, 0.0, 25)
 
 
-GRIDS = {"tiny": tiny_grid, "mid": mid_grid, "production": production_grid}
+def polar_grid(r_edges, n_theta, n_phi, lmax, name="polar", G=1.0) -> GridSpec:
+    """Full spherical polar grid: theta_j^+- = (j, j+1) pi / n_theta,
+    phi_k^+- = (k, k+1) 2 pi / n_phi."""
+    return GridSpec(name, np.asarray(r_edges, dtype=np.float64), n_theta, n_phi, 0.0, 0.0, lmax, G, True)
+
+
+def tiny_polar_grid() -> GridSpec:
+    """32 log-spaced zones in [1e-3, 1], 16 x 32 cells (11.25 degrees), l_max = 8."""
+    return polar_grid(np.logspace(-3, 0, 33), 16, 32, 8, "tiny_polar")
+
+
+def mid_polar_grid() -> GridSpec:
+    """200 log-spaced zones in [1e-3, 1], 2-degree cells (90 x 180), l_max = 15."""
+    return polar_grid(np.logspace(-3, 0, 201), 90, 180, 15, "mid_polar")
+
+
+GRIDS = {"tiny": tiny_grid, "mid": mid_grid, "production": production_grid,
+         "tiny_polar": tiny_polar_grid, "mid_polar": mid_polar_grid}
 
 
 def cell_centres(spec: GridSpec):
@@ -74,13 +110,15 @@ def cell_centres(spec: GridSpec):
     Returns r_c [n_r], and for each patch the unit vectors [3, n_theta, n_phi]
     of the cell-centre directions in the global (Yin) frame.
     """
-    dth, dph = _patch_step(spec.n_theta, spec.n_phi, spec.delta_theta, spec.delta_phi)
-    th = math.pi / 4 - spec.delta_theta + dth * (np.arange(spec.n_theta) + 0.5)
-    ph = -3 * math.pi / 4 - spec.delta_phi + dph * (np.arange(spec.n_phi) + 0.5)
+    te, pe = angular_cell_edges(spec)
+    th = 0.5 * (te[:-1] + te[1:])
+    ph = 0.5 * (pe[:-1] + pe[1:])
     T, P = np.meshgrid(th, ph, indexing="ij")
     local = np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)])
-    yang_global = np.stack([-local[0], local[2], local[1]])
     r_c = 0.5 * (spec.r_edges[:-1] + spec.r_edges[1:])
+    if spec.polar:
+        return r_c, {"yin": local}
+    yang_global = np.stack([-local[0], local[2], local[1]])
     return r_c, {"yin": local, "yang": yang_global}
 
 
@@ -94,7 +132,7 @@ def centred_sphere_density(spec: GridSpec, radius: float, rho0: float):
     rm, rp = spec.r_edges[:-1], spec.r_edges[1:]
     inside = np.clip(np.minimum(rp, radius) ** 3 - rm ** 3, 0.0, None) / (rp ** 3 - rm ** 3)
     rho = rho0 * inside[:, None, None] * np.ones((1, spec.n_theta, spec.n_phi))
-    return rho.copy(), rho.copy()
+    return rho.copy(), (None if spec.polar else rho.copy())
 
 
 def offcentre_sphere_density(spec: GridSpec, centre, radius: float, rho0: float, q: int = 4):
@@ -105,17 +143,16 @@ def offcentre_sphere_density(spec: GridSpec, centre, radius: float, rho0: float,
     g, gw = np.polynomial.legendre.leggauss(q)
     u = 0.5 * (g + 1.0)              # nodes on [0, 1]
     uw = 0.5 * gw                    # weights summing to 1
-    dth, dph = _patch_step(spec.n_theta, spec.n_phi, spec.delta_theta, spec.delta_phi)
-    th_e = math.pi / 4 - spec.delta_theta + dth * np.arange(spec.n_theta + 1)
-    ph_e = -3 * math.pi / 4 - spec.delta_phi + dph * np.arange(spec.n_phi + 1)
+    th_e, ph_e = angular_cell_edges(spec)
+    dph = ph_e[1] - ph_e[0]
     r3m, r3p = spec.r_edges[:-1] ** 3, spec.r_edges[1:] ** 3
     r_s = np.cbrt(r3m[:, None] + (r3p - r3m)[:, None] * u[None, :])              # [n_r, q]
     cm, cp = np.cos(th_e[:-1]), np.cos(th_e[1:])
     ct_s = cm[:, None] + (cp - cm)[:, None] * u[None, :]                           # [n_t, q]
     st_s = np.sqrt(np.clip(1.0 - ct_s ** 2, 0.0, None))
     ph_s = ph_e[:-1, None] + dph * u[None, :]                                      # [n_p, q]
-    out = {}
-    for patch in ("yin", "yang"):
+    out = {"yang": None}
+    for patch in patches(spec):
         # local unit vectors at sub-points: [3, n_t, q, n_p, q]
         x = st_s[:, :, None, None] * np.cos(ph_s)[None, None, :, :]
         y = st_s[:, :, None, None] * np.sin(ph_s)[None, None, :, :]
@@ -138,7 +175,7 @@ def tiny_density(spec: GridSpec | None = None):
     spec = spec or tiny_grid()
     a_yin, a_yang = centred_sphere_density(spec, 0.3, 1.0)
     b_yin, b_yang = offcentre_sphere_density(spec, (0.2, 0.1, -0.15), 0.1, 5.0)
-    return a_yin + b_yin, a_yang + b_yang
+    return a_yin + b_yin, (None if spec.polar else a_yang + b_yang)
 
 
 def oblate_density(spec: GridSpec | None = None, seed: int = 1):
@@ -147,8 +184,8 @@ def oblate_density(spec: GridSpec | None = None, seed: int = 1):
     spec = spec or mid_grid()
     rng = np.random.default_rng(seed)
     r_c, units = cell_centres(spec)
-    out = {}
-    for patch in ("yin", "yang"):
+    out = {"yang": None}
+    for patch in patches(spec):
         u = units[patch]
         X = r_c[:, None, None] * u[0][None]
         Y = r_c[:, None, None] * u[1][None]
@@ -174,13 +211,67 @@ def pns_density(spec: GridSpec | None = None, seed: int = 2, eps_scale: float = 
     eps = rng.normal(0.0, eps_scale, size=len(_MONOMIALS))
     r_c, units = cell_centres(spec)
     radial = np.exp(-r_c / 0.02) + 1e-4 * r_c ** -2.5
-    out = {}
-    for patch in ("yin", "yang"):
+    out = {"yang": None}
+    for patch in patches(spec):
         u = units[patch]
         ang = np.ones(u.shape[1:])
         for e, (a, b, c) in zip(eps, _MONOMIALS):
             ang = ang + e * u[0] ** a * u[1] ** b * u[2] ** c
         out[patch] = radial[:, None, None] * ang[None]
+    return out["yin"], out["yang"]
+
+
+def ellipsoid_density(spec: GridSpec, axes, rho0: float = 1.0, dphi: float = math.pi / 8, q: int = 4):
+    """Cell averages of the homogeneous ellipsoid (x/a)^2 + (y/b)^2 + (z/c)^2 <= 1
+    (density rho0 inside), whose frame is the global one turned by dphi about z:
+    a point at global angles (theta, phi) has ellipsoid coordinates
+    r (sin theta cos(phi + dphi), sin theta sin(phi + dphi), cos theta).
+
+    A cell whose centre value g = sqrt((x/a)^2 + (y/b)^2 + (z/c)^2) differs
+    from 1 by more than (cell extent) / min(a, b, c) lies wholly inside or
+    outside (g changes by at most |dx| / min(a, b, c)); it takes the centre's
+    value.  The other cells average the indicator over a q x q x q product
+    rule uniform in volume (r^3, cos theta, phi)."""
+    a, b, c = (float(v) for v in axes)
+    amin = min(a, b, c)
+    cd, sd = math.cos(dphi), math.sin(dphi)
+    th_e, ph_e = angular_cell_edges(spec)
+    dth, dph = th_e[1] - th_e[0], ph_e[1] - ph_e[0]
+    rm, rp = spec.r_edges[:-1], spec.r_edges[1:]
+    extent = (rp - rm) + rp * (dth + dph)                      # bounds twice the half-diagonal
+    r_c, units = cell_centres(spec)
+
+    def g_of(x, y, z):
+        xe, ye = cd * x - sd * y, sd * x + cd * y
+        return np.sqrt((xe / a) ** 2 + (ye / b) ** 2 + (z / c) ** 2)
+
+    gq, gw = np.polynomial.legendre.leggauss(q)
+    u, uw = 0.5 * (gq + 1.0), 0.5 * gw
+    out = {"yang": None}
+    for patch in patches(spec):
+        v = units[patch]
+        gc = g_of(*(r_c[:, None, None] * v[k][None] for k in range(3)))
+        rho = np.where(gc <= 1.0, rho0, 0.0)
+        cut = np.abs(gc - 1.0) <= extent[:, None, None] / amin
+        i_idx, j_idx, k_idx = np.nonzero(cut)
+        if i_idx.size:
+            r3m, r3p = rm[i_idx] ** 3, rp[i_idx] ** 3
+            cm, cp = np.cos(th_e[j_idx]), np.cos(th_e[j_idx + 1])
+            acc = np.zeros(i_idx.size)
+            for ia in range(q):
+                rr = np.cbrt(r3m + (r3p - r3m) * u[ia])
+                for ib in range(q):
+                    ct = cm + (cp - cm) * u[ib]
+                    st = np.sqrt(np.clip(1.0 - ct * ct, 0.0, None))
+                    for ic in range(q):
+                        ph = ph_e[k_idx] + dph * u[ic]
+                        x, y, z = st * np.cos(ph), st * np.sin(ph), ct
+                        if patch == "yang":
+                            x, y, z = -x, z, y
+                        ind = g_of(rr * x, rr * y, rr * z) <= 1.0
+                        acc += uw[ia] * uw[ib] * uw[ic] * ind
+            rho[i_idx, j_idx, k_idx] = rho0 * acc
+        out[patch] = rho
     return out["yin"], out["yang"]
 
 

@@ -24,7 +24,14 @@ import numpy as np
 from numpy.polynomial import legendre as npleg
 
 
+def _patches(spec):
+    return ("yin",) if getattr(spec, "polar", False) else ("yin", "yang")
+
+
 def _edges(spec):
+    if getattr(spec, "polar", False):       # one patch over the sphere, global frame
+        return (math.pi / spec.n_theta * np.arange(spec.n_theta + 1),
+                2 * math.pi / spec.n_phi * np.arange(spec.n_phi + 1))
     dth = (math.pi / 2 + 2 * spec.delta_theta) / spec.n_theta
     dph = (3 * math.pi / 2 + 2 * spec.delta_phi) / spec.n_phi
     te = math.pi / 4 - spec.delta_theta + dth * np.arange(spec.n_theta + 1)
@@ -42,7 +49,7 @@ def source_points(spec, q=16):
     te, pe = _edges(spec)
     g, gw = npleg.leggauss(q)
     out = {}
-    for patch in ("yin", "yang"):
+    for patch in _patches(spec):
         th = 0.5 * (te[:-1, None] + te[1:, None]) + 0.5 * (te[1:, None] - te[:-1, None]) * g[None]
         ph = 0.5 * (pe[:-1, None] + pe[1:, None]) + 0.5 * (pe[1:, None] - pe[:-1, None]) * g[None]
         wt = 0.5 * (te[1:, None] - te[:-1, None]) * gw[None] * np.sin(th)       # [n_t, q]
@@ -108,7 +115,7 @@ def potential_and_gradient(spec, w, rho, targets, q=16):
         F, dF = _radial_factors(spec.r_edges, r, L)
         phi = 0.0
         grad = np.zeros(3)
-        for patch_s in ("yin", "yang"):
+        for patch_s in _patches(spec):
             v, W = src[patch_s]
             cg = np.einsum("c,cnq->nq", e_r, v)
             I = np.empty((L + 1, cg.shape[0]))
@@ -148,7 +155,7 @@ def green_potential(spec, w, rho, targets, q=8, qr=8):
         e_r = target_frame(spec, patch_t, j, k)[0]
         x = r * e_r
         phi = 0.0
-        for patch_s in ("yin", "yang"):
+        for patch_s in _patches(spec):
             v, W = src[patch_s]
             wcell = W * w.reshape(-1)[:, None]                          # [cell, q2]
             for i in range(spec.n_r):

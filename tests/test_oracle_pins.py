@@ -478,3 +478,65 @@ def test_gradient_matches_finite_differences_in_angle(oracle_grid):
     g_p = np.einsum("cnp,cp->np", v, e_p)
     assert np.abs(g_t + dth / r).max() <= 1e-6 * np.abs(g_t).max()
     assert np.abs(g_p + dph / (r * np.sin(th))).max() <= 1e-6 * np.abs(g_p).max()
+
+
+# ---------------------------------------------------------------------------
+# §2: the full spherical polar grid (one patch, w = 1; reading R10)
+# ---------------------------------------------------------------------------
+
+def test_polar_grid_spherical_density_exact_at_any_lmax():
+    """Over the whole sphere the cell integrals of every l > 0 harmonic sum to
+    zero (T over [0, pi] times C/S over [0, 2 pi)), so a spherical density
+    gives the shell closed form at any l_max, with no leakage."""
+    spec = inputs.tiny_polar_grid()
+    rng = np.random.default_rng(21)
+    rho_shell = rng.uniform(0.1, 2.0, spec.n_r)
+    g = oracle.OraclePolarGrid(spec.r_edges, spec.n_theta, spec.n_phi, 8, G=1.7)
+    rho = np.broadcast_to(rho_shell[:, None, None], (spec.n_r, spec.n_theta, spec.n_phi))
+    res = g.solve(rho, gradient=True)
+    phi_ref, g_ref = _shell_closed_form(spec.r_edges, rho_shell, 1.7)
+    assert np.abs(res["phi"] - phi_ref[:, None, None]).max() <= 1e-12 * np.abs(phi_ref).max()
+    assert np.abs(res["grad"][0] - g_ref[:, None, None]).max() <= 1e-12 * np.abs(g_ref).max()
+    assert np.abs(res["grad"][1:]).max() <= 1e-12 * np.abs(g_ref).max()
+
+
+def test_polar_grid_cells_tile_the_sphere():
+    g = oracle.OraclePolarGrid(np.linspace(0.0, 1.0, 3), 7, 13, 2)
+    assert g.theta_edges[0] == 0.0 and abs(g.theta_edges[-1] - math.pi) <= 1e-15
+    assert g.phi_edges[0] == 0.0 and abs(g.phi_edges[-1] - 2 * math.pi) <= 1e-15
+    dO = np.outer(np.cos(g.theta_edges[:-1]) - np.cos(g.theta_edges[1:]), np.diff(g.phi_edges))
+    assert abs(dO.sum() - 4 * math.pi) <= 1e-13
+    assert np.all(g.w == 1.0)
+
+
+def test_polar_grid_bruteforce_addition_theorem():
+    """Whole discrete formula on the polar grid against the brute-force sum
+    through the addition theorem, on a random density."""
+    spec = inputs.polar_grid(np.linspace(0.0, 1.0, 7), 10, 22, 6, G=0.8)
+    g = oracle.OraclePolarGrid(spec.r_edges, spec.n_theta, spec.n_phi, spec.lmax, spec.G)
+    rng = np.random.default_rng(22)
+    rho = rng.uniform(0, 1, (6, 10, 22))
+    res = g.solve(rho, gradient=True)
+    targets = [("yin", int(rng.integers(6)), int(rng.integers(10)), int(rng.integers(22))) for _ in range(16)]
+    phi_bf, g_bf = bf.potential_and_gradient(spec, g.w, {"yin": rho}, targets)
+    phi_o = np.array([res["phi"][n, j, k] for _, n, j, k in targets])
+    g_o = np.array([res["grad"][:, n, j, k] for _, n, j, k in targets])
+    assert np.abs(phi_bf - phi_o).max() <= 1e-12 * np.abs(phi_o).max()
+    assert np.abs(g_bf - g_o).max() <= 1e-12 * np.abs(g_o).max()
+
+
+def test_polar_grid_green_function_convergence_with_lmax():
+    """The truncated expansion on the polar grid approaches the exact
+    1/|x - x'| sum as l_max grows."""
+    spec = inputs.polar_grid(np.linspace(0.05, 1.0, 9), 12, 24, 1)
+    rng = np.random.default_rng(23)
+    rho = rng.uniform(0.5, 1.5, (8, 12, 24))
+    targets = [("yin", 7, 3, 10), ("yin", 7, 8, 20), ("yin", 2, 6, 3)]
+    errs = []
+    for L in (1, 4, 10):
+        res = oracle.OraclePolarGrid(spec.r_edges, 12, 24, L).solve(rho)
+        errs.append(np.array([res["phi"][n, j, k] for _, n, j, k in targets]))
+    exact = bf.green_potential(spec, np.ones((12, 24)), {"yin": rho}, targets)
+    e = [np.abs(x - exact).max() / np.abs(exact).max() for x in errs]
+    assert e[2] < e[1] < e[0]
+    assert e[2] < 1e-2
