@@ -152,6 +152,17 @@ yy_status yy_grid_create(const double *r_edges, int n_r, int n_theta, int n_phi,
                          double delta_theta, double delta_phi, int l_max, double G,
                          yy_grid **out);
 
+/* Create a handle for the full spherical polar grid of §2 (the comparison
+ * grid of §5): one patch, theta_j^+- = (j, j+1) pi / n_theta and
+ * phi_k^+- = (k, k+1) 2 pi / n_phi in the global frame, every cell counted
+ * once (w = 1), no second patch and no rotation table.  Arguments, rules and
+ * errors as for yy_grid_create without the buffer widths.  For this handle
+ * yy_potential and yy_potential_host take the Yin arguments only and require
+ * rho_yang, phi_yang and grad_yang to be NULL; the per-patch tables hold n_r
+ * rows instead of 2 n_r, and YY_TABLE_ROTATION gives YY_ERR_NOT_SUPPORTED. */
+yy_status yy_polar_grid_create(const double *r_edges, int n_r, int n_theta, int n_phi, int l_max,
+                               double G, yy_grid **out);
+
 /* Select the analysis evaluation for later solves (see yy_analysis).
  * Errors: YY_ERR_INVALID_ARG. */
 yy_status yy_grid_set_analysis(yy_grid *g, yy_analysis method);
@@ -165,6 +176,7 @@ yy_status yy_grid_prepare(yy_grid *g, yy_precision prec);
  *   rho_yin, rho_yang   device, [n_r][n_theta][n_phi] float64 (read)
  *   phi_yin, phi_yang   device, same shape (written)
  *   grad_yin, grad_yang device, [3][n_r][n_theta][n_phi] or both NULL
+ * On a polar grid (yy_polar_grid_create) the Yang pointers must be NULL.
  * Asynchronous; no host synchronisation.  Errors: YY_ERR_INVALID_ARG (NULL
  * or misaligned pointer, one gradient pointer NULL), YY_ERR_NOT_SUPPORTED
  * (precision not prepared), YY_ERR_CUDA (launch failure). */

@@ -98,25 +98,28 @@ const char *yy_status_string(yy_status s) {
   return "unknown status";
 }
 
-yy_status yy_grid_create(const double *r_edges, int n_r, int n_theta, int n_phi, double delta_theta,
-                         double delta_phi, int l_max, double G, yy_grid **out) {
-  if (out == nullptr) return YY_ERR_INVALID_ARG;
-  *out = nullptr;
-  const double quarter_pi = 0.78539816339744830962;
+static constexpr double kQuarterPi = 0.78539816339744830962;
+
+// checks shared by both grid kinds
+static bool valid_shape(const double *r_edges, int n_r, int n_theta, int n_phi, int l_max, double G) {
   if (r_edges == nullptr || n_r < 1 || n_r > (1 << 20) || n_theta < 1 || n_phi < 1 ||
       (long long)n_theta * n_phi > (1 << 24) || l_max < 0 || l_max > YY_LMAX_CAP)
-    return YY_ERR_INVALID_ARG;
-  if (!(delta_theta >= 0.0 && delta_theta < quarter_pi) || !(delta_phi >= 0.0 && delta_phi < quarter_pi))
-    return YY_ERR_INVALID_ARG;
-  if (!isfinite(G)) return YY_ERR_INVALID_ARG;
-  if (!(r_edges[0] >= 0.0) || !isfinite(r_edges[0])) return YY_ERR_INVALID_ARG;
+    return false;
+  if (!isfinite(G)) return false;
+  if (!(r_edges[0] >= 0.0) || !isfinite(r_edges[0])) return false;
   for (int i = 0; i < n_r; ++i)
-    if (!(r_edges[i + 1] > r_edges[i]) || !isfinite(r_edges[i + 1])) return YY_ERR_INVALID_ARG;
+    if (!(r_edges[i + 1] > r_edges[i]) || !isfinite(r_edges[i + 1])) return false;
+  return true;
+}
 
+static yy_status create_grid(const double *r_edges, int n_r, int n_theta, int n_phi, double delta_theta,
+                             double delta_phi, int l_max, double G, bool polar, yy_grid **out) {
+  const double quarter_pi = kQuarterPi;
   yy_grid *g = new (std::nothrow) yy_grid();
   if (!g) return YY_ERR_OOM;
   memset((void *)g, 0, sizeof(yy_grid));
   cudaGetDevice(&g->device);
+  g->n_patch = polar ? 1 : 2;
   g->n_r = n_r;
   g->n_theta = n_theta;
   g->n_phi = n_phi;
@@ -126,12 +129,19 @@ yy_status yy_grid_create(const double *r_edges, int n_r, int n_theta, int n_phi,
   g->delta_theta = delta_theta;
   g->delta_phi = delta_phi;
   g->G = G;
-  g->th0 = quarter_pi - delta_theta;
-  g->ph0 = -3.0 * quarter_pi - delta_phi;
-  g->dth = (2.0 * quarter_pi + 2.0 * delta_theta) / n_theta;
-  g->dph = (6.0 * quarter_pi + 2.0 * delta_phi) / n_phi;
+  if (polar) {   // theta in [0, pi], phi in [0, 2 pi)
+    g->th0 = 0.0;
+    g->ph0 = 0.0;
+    g->dth = 4.0 * quarter_pi / n_theta;
+    g->dph = 8.0 * quarter_pi / n_phi;
+  } else {
+    g->th0 = quarter_pi - delta_theta;
+    g->ph0 = -3.0 * quarter_pi - delta_phi;
+    g->dth = (2.0 * quarter_pi + 2.0 * delta_theta) / n_theta;
+    g->dph = (6.0 * quarter_pi + 2.0 * delta_phi) / n_phi;
+  }
 
-  const size_t n_ang = g->n_ang, n_lm = g->n_lm, M = 2 * (size_t)n_r;
+  const size_t n_ang = g->n_ang, n_lm = g->n_lm, M = (size_t)grid_rows(g);
   g->split_k = choose_split_k((int)M, (int)n_lm, (int)n_ang);
   cudaError_t e = cudaSuccess;
   auto A = [&](void **p, size_t bytes) {
@@ -144,17 +154,17 @@ yy_status yy_grid_create(const double *r_edges, int n_r, int n_theta, int n_phi,
   A((void **)&g->ysyn, n_ang * n_lm * sizeof(double));
   A((void **)&g->ysyn_t, n_ang * n_lm * sizeof(double));
   A((void **)&g->ysyn_p, n_ang * n_lm * sizeof(double));
-  A((void **)&g->rot, rotation_table_size(l_max) * sizeof(double));
+  if (!polar) A((void **)&g->rot, rotation_table_size(l_max) * sizeof(double));
   A((void **)&g->sep_P, (size_t)n_theta * n_lm * sizeof(double));
   A((void **)&g->sep_dP, (size_t)n_theta * n_lm * sizeof(double));
   A((void **)&g->sep_Qs, (size_t)n_theta * n_lm * sizeof(double));
   A((void **)&g->sep_tr, (size_t)(2 * l_max + 1) * n_phi * sizeof(double));
-  A((void **)&g->rot32, rotation_table_size(l_max) * sizeof(float));
+  if (!polar) A((void **)&g->rot32, rotation_table_size(l_max) * sizeof(float));
   A((void **)&g->scan, (size_t)n_r * (l_max + 1) * 8 * sizeof(double));
   {
     int nc = 1, ch = 1;
     scan_geometry(g, &nc, &ch);
-    A((void **)&g->scan_maps, (size_t)2 * nc * n_lm * 4 * sizeof(double));
+    A((void **)&g->scan_maps, (size_t)g->n_patch * nc * n_lm * 4 * sizeof(double));
   }
   A((void **)&g->A, M * n_lm * sizeof(double));
   A((void **)&g->Atot, M * n_lm * sizeof(double));
@@ -186,6 +196,24 @@ yy_status yy_grid_create(const double *r_edges, int n_r, int n_theta, int n_phi,
   return YY_OK;
 }
 
+yy_status yy_grid_create(const double *r_edges, int n_r, int n_theta, int n_phi, double delta_theta,
+                         double delta_phi, int l_max, double G, yy_grid **out) {
+  if (out == nullptr) return YY_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!valid_shape(r_edges, n_r, n_theta, n_phi, l_max, G)) return YY_ERR_INVALID_ARG;
+  if (!(delta_theta >= 0.0 && delta_theta < kQuarterPi) || !(delta_phi >= 0.0 && delta_phi < kQuarterPi))
+    return YY_ERR_INVALID_ARG;
+  return create_grid(r_edges, n_r, n_theta, n_phi, delta_theta, delta_phi, l_max, G, false, out);
+}
+
+yy_status yy_polar_grid_create(const double *r_edges, int n_r, int n_theta, int n_phi, int l_max, double G,
+                               yy_grid **out) {
+  if (out == nullptr) return YY_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!valid_shape(r_edges, n_r, n_theta, n_phi, l_max, G)) return YY_ERR_INVALID_ARG;
+  return create_grid(r_edges, n_r, n_theta, n_phi, 0.0, 0.0, l_max, G, true, out);
+}
+
 yy_status yy_grid_set_analysis(yy_grid *g, yy_analysis method) {
   if (!g || (method != YY_ANALYSIS_AUTO && method != YY_ANALYSIS_SEPARABLE && method != YY_ANALYSIS_DENSE))
     return YY_ERR_INVALID_ARG;
@@ -213,8 +241,13 @@ yy_status yy_grid_prepare(yy_grid *g, yy_precision prec) {
 static yy_status check_solve_args(yy_grid *g, const double *rho_yin, const double *rho_yang,
                                   double *phi_yin, double *phi_yang, double *grad_yin,
                                   double *grad_yang, yy_precision prec) {
-  if (!g || !rho_yin || !rho_yang || !phi_yin || !phi_yang) return YY_ERR_INVALID_ARG;
-  if ((grad_yin == nullptr) != (grad_yang == nullptr)) return YY_ERR_INVALID_ARG;
+  if (!g || !rho_yin || !phi_yin) return YY_ERR_INVALID_ARG;
+  if (g->n_patch == 1) {   // polar grid: one patch, the Yang arguments stay NULL
+    if (rho_yang || phi_yang || grad_yang) return YY_ERR_INVALID_ARG;
+  } else {
+    if (!rho_yang || !phi_yang) return YY_ERR_INVALID_ARG;
+    if ((grad_yin == nullptr) != (grad_yang == nullptr)) return YY_ERR_INVALID_ARG;
+  }
   const void *ptrs[] = {rho_yin, rho_yang, phi_yin, phi_yang, grad_yin, grad_yang};
   for (const void *p : ptrs)
     if (p && !aligned16(p)) return YY_ERR_INVALID_ARG;
@@ -270,35 +303,39 @@ yy_status yy_potential(yy_grid *g, const double *rho_yin, const double *rho_yang
 yy_status yy_potential_host(yy_grid *g, const double *rho_yin, const double *rho_yang, double *phi_yin,
                             double *phi_yang, double *grad_yin, double *grad_yang, yy_precision prec,
                             void *cuda_stream) {
-  if (!g || !rho_yin || !rho_yang || !phi_yin || !phi_yang) return YY_ERR_INVALID_ARG;
-  if ((grad_yin == nullptr) != (grad_yang == nullptr)) return YY_ERR_INVALID_ARG;
-  const size_t field = (size_t)g->n_r * g->n_ang;
+  if (!g || !rho_yin || !phi_yin) return YY_ERR_INVALID_ARG;
+  const bool two = g->n_patch == 2;
+  if (two ? (!rho_yang || !phi_yang || (grad_yin == nullptr) != (grad_yang == nullptr))
+          : (rho_yang || phi_yang || grad_yang))
+    return YY_ERR_INVALID_ARG;
+  const size_t field = (size_t)g->n_r * g->n_ang, np = (size_t)g->n_patch;
   cudaError_t e = cudaSuccess;
-  if (!g->stage_rho) e = dmalloc((void **)&g->stage_rho, 2 * field * sizeof(double));
-  if (e == cudaSuccess && !g->stage_phi) e = dmalloc((void **)&g->stage_phi, 2 * field * sizeof(double));
-  if (e == cudaSuccess && grad_yin && !g->stage_grad) e = dmalloc((void **)&g->stage_grad, 6 * field * sizeof(double));
+  if (!g->stage_rho) e = dmalloc((void **)&g->stage_rho, np * field * sizeof(double));
+  if (e == cudaSuccess && !g->stage_phi) e = dmalloc((void **)&g->stage_phi, np * field * sizeof(double));
+  if (e == cudaSuccess && grad_yin && !g->stage_grad)
+    e = dmalloc((void **)&g->stage_grad, 3 * np * field * sizeof(double));
   if (e != cudaSuccess) return from_cuda(e);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const size_t bytes = field * sizeof(double);
   e = cudaMemcpyAsync(g->stage_rho, rho_yin, bytes, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(g->stage_rho + field, rho_yang, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && two) e = cudaMemcpyAsync(g->stage_rho + field, rho_yang, bytes, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return from_cuda(e);
   double *gy = grad_yin ? g->stage_grad : nullptr;
-  double *gg = grad_yin ? g->stage_grad + 3 * field : nullptr;
-  yy_status st = yy_potential(g, g->stage_rho, g->stage_rho + field, g->stage_phi, g->stage_phi + field, gy, gg,
-                              prec, cuda_stream);
+  double *gg = (grad_yin && two) ? g->stage_grad + 3 * field : nullptr;
+  yy_status st = yy_potential(g, g->stage_rho, two ? g->stage_rho + field : nullptr, g->stage_phi,
+                              two ? g->stage_phi + field : nullptr, gy, gg, prec, cuda_stream);
   if (st != YY_OK) return st;
   e = cudaMemcpyAsync(phi_yin, g->stage_phi, bytes, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(phi_yang, g->stage_phi + field, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && two) e = cudaMemcpyAsync(phi_yang, g->stage_phi + field, bytes, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && grad_yin) e = cudaMemcpyAsync(grad_yin, gy, 3 * bytes, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && grad_yin) e = cudaMemcpyAsync(grad_yang, gg, 3 * bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && gg) e = cudaMemcpyAsync(grad_yang, gg, 3 * bytes, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return from_cuda(e);
 }
 
 yy_status yy_grid_copy_table(yy_grid *g, yy_table which, double *host_dst, size_t *count) {
   if (!g || !count) return YY_ERR_INVALID_ARG;
-  const size_t n_ang = g->n_ang, n_lm = g->n_lm, M = 2 * (size_t)g->n_r;
+  const size_t n_ang = g->n_ang, n_lm = g->n_lm, M = (size_t)grid_rows(g);
   const double *src = nullptr;
   size_t n = 0;
   switch (which) {
@@ -310,8 +347,12 @@ yy_status yy_grid_copy_table(yy_grid *g, yy_table which, double *host_dst, size_
     case YY_TABLE_SYNTH_P: src = g->ysyn_p; n = n_ang * n_lm; break;
     case YY_TABLE_MOMENTS: src = g->A; n = M * n_lm; break;
     case YY_TABLE_COEFF: src = g->Q; n = 3 * M * n_lm; break;
-    case YY_TABLE_ROTATION: src = g->rot; n = (size_t)rotation_table_size(g->lmax); break;
-    case YY_TABLE_MOMENTS_TOTAL: src = g->Atot; n = M * n_lm; break;
+    case YY_TABLE_ROTATION:
+      if (g->n_patch != 2) return YY_ERR_NOT_SUPPORTED;   // a polar grid has no second patch
+      src = g->rot;
+      n = (size_t)rotation_table_size(g->lmax);
+      break;
+    case YY_TABLE_MOMENTS_TOTAL: src = moments_total(g); n = M * n_lm; break;
     default: return YY_ERR_INVALID_ARG;
   }
   if (host_dst == nullptr) {
@@ -374,14 +415,14 @@ int yy_last_launch_count(const yy_grid *g) { return g ? g->launches : -1; }
 
 double yy_solve_flops(const yy_grid *g, int with_gradient) {
   if (!g) return 0.0;
-  const double M = 2.0 * g->n_r, K_an = g->n_ang, N_an = g->n_lm;
+  const double M = (double)grid_rows(g), K_an = g->n_ang, N_an = g->n_lm;
   const int nt = 2 * g->lmax + 1;
   const double analysis = g->last_separable
                               ? 2.0 * M * K_an * nt + 2.0 * M * g->n_theta * N_an
                               : 2.0 * M * N_an * K_an;
   const double synth = 2.0 * M * g->n_lm * g->n_ang;
   double rotation = 0.0;
-  for (int l = 0; l <= g->lmax; ++l) rotation += 2.0 * M * (2.0 * l + 1.0) * (2.0 * l + 1.0);
+  for (int l = 0; l <= g->lmax && g->n_patch == 2; ++l) rotation += 2.0 * M * (2.0 * l + 1.0) * (2.0 * l + 1.0);
   return analysis + rotation + (with_gradient ? 4.0 : 1.0) * synth;
 }
 

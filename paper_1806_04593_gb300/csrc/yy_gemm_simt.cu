@@ -123,7 +123,7 @@ __global__ void k_rho_to_f32(size_t per_patch, const double *__restrict__ a, con
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < per_patch) {
     dst[e] = (float)a[e];
-    dst[per_patch + e] = (float)b[e];
+    if (b) dst[per_patch + e] = (float)b[e];   // no second patch on a polar grid
   }
 }
 
@@ -153,7 +153,7 @@ int choose_split_k(int M, int N, int K) {
 
 cudaError_t analysis_simt(yy_grid *g, const double *rho_yin, const double *rho_yang, bool fp32,
                           cudaStream_t s) {
-  const int M = 2 * g->n_r, N = g->n_lm, K = g->n_ang;
+  const int M = grid_rows(g), N = g->n_lm, K = g->n_ang;
   const int splits = g->split_k;
   double *out = (splits > 1) ? g->part : g->A;
   cudaError_t err;
@@ -180,7 +180,7 @@ cudaError_t analysis_simt(yy_grid *g, const double *rho_yin, const double *rho_y
 
 cudaError_t synthesis_simt(yy_grid *g, double *phi_yin, double *phi_yang, double *grad_yin,
                            double *grad_yang, bool fp32, cudaStream_t s) {
-  const int M = 2 * g->n_r, N = g->n_ang, K = g->n_lm;
+  const int M = grid_rows(g), N = g->n_ang, K = g->n_lm;
   const size_t qsz = (size_t)M * K;
   const size_t comp = (size_t)g->n_r * g->n_ang;
   cudaError_t err;
@@ -221,9 +221,9 @@ cudaError_t convert_tables_f32(yy_grid *g) {
   if ((err = dmalloc((void **)&g->ysyn32, n_syn * sizeof(float))) != cudaSuccess) return err;
   if ((err = dmalloc((void **)&g->ysyn_t32, n_syn * sizeof(float))) != cudaSuccess) return err;
   if ((err = dmalloc((void **)&g->ysyn_p32, n_syn * sizeof(float))) != cudaSuccess) return err;
-  if ((err = dmalloc((void **)&g->rho32, 2 * (size_t)g->n_r * g->n_ang * sizeof(float))) != cudaSuccess)
+  if ((err = dmalloc((void **)&g->rho32, (size_t)grid_rows(g) * g->n_ang * sizeof(float))) != cudaSuccess)
     return err;
-  if ((err = dmalloc((void **)&g->Q32, 3 * (size_t)2 * g->n_r * g->n_lm * sizeof(float))) != cudaSuccess)
+  if ((err = dmalloc((void **)&g->Q32, 3 * (size_t)grid_rows(g) * g->n_lm * sizeof(float))) != cudaSuccess)
     return err;
   k_to_f32<<<(unsigned)((n_ban + 255) / 256), 256>>>(n_ban, g->ban, g->ban32);
   k_to_f32<<<(unsigned)((n_syn + 255) / 256), 256>>>(n_syn, g->ysyn, g->ysyn32);

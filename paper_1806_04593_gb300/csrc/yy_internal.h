@@ -19,6 +19,7 @@ struct yy_tc_tables;
 
 struct yy_grid {
   int device;
+  int n_patch;          // 2: Yin-Yang; 1: full spherical polar grid (rows of every stage: n_patch n_r)
   int n_r, n_theta, n_phi, n_ang, lmax, n_lm;
   double delta_theta, delta_phi, G;
   double th0, ph0, dth, dph;
@@ -38,6 +39,7 @@ struct yy_grid {
   double *gl_nodes;    // GL nodes / weights on [0, 1] for the weight integrals
 
   // workspace (device)
+  // (row counts below are for the Yin-Yang grid; a polar grid has n_r rows)
   double *A;           // [2 n_r][n_lm]           moments of each patch's own cells
   double *Atot;        // [2 n_r][n_lm]           both patches' moments in each patch's frame
   double *part;        // split-K partials [split][2 n_r][n_lm]
@@ -94,6 +96,10 @@ cudaError_t dmalloc(void **p, size_t bytes);
 cudaError_t build_tables(yy_grid *g, const double *gl_host, int n_gl);
 // entries of the rotation table: sum_{l <= lmax} (2l+1)^2
 inline int rotation_table_size(int lmax) { return (lmax + 1) * (4 * (lmax + 1) * (lmax + 1) - 1) / 3; }
+// rows of the stacked per-patch arrays (moments, coefficients, outputs)
+inline int grid_rows(const yy_grid *g) { return g->n_patch * g->n_r; }
+// the moments the radial scans read: both patches combined (Yin-Yang) or A itself (polar)
+inline const double *moments_total(const yy_grid *g) { return g->n_patch == 2 ? g->Atot : g->A; }
 
 // float64 / float32 CUDA-core contractions (yy_gemm_simt.cu)
 cudaError_t analysis_simt(yy_grid *g, const double *rho_yin, const double *rho_yang,

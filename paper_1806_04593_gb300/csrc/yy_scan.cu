@@ -64,12 +64,13 @@ struct __align__(32) Map4 {
 
 struct ScanGeom {
   int n_r, lmax, n_lm, nc, ch, wpp;   // chunks, chunk length, warps per patch and chunk
+  int n_patch;
 };
 
 __device__ __forceinline__ bool scan_lane(const ScanGeom &s, int &p, int &idx, int &c, int &n0, int &n1) {
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= 2 * s.wpp * s.nc) return false;
+  if (w >= s.n_patch * s.wpp * s.nc) return false;
   c = w % s.nc;
   const int rest = w / s.nc;
   p = rest / s.wpp;
@@ -127,7 +128,7 @@ k_scan_apply(ScanGeom s, const double *__restrict__ A, const double *__restrict_
     x = fma(k[0], x, k[1] * Ap[(size_t)n * s.n_lm]);
     Cp[(size_t)n * s.n_lm] = x;
   }
-  const size_t qsz = (size_t)2 * s.n_r * s.n_lm;
+  const size_t qsz = (size_t)s.n_patch * s.n_r * s.n_lm;
   for (int n = n1 - 1; n >= n0; --n) {
     const double *k = coef + ((size_t)n * L1 + l) * 8;
     const double an = (n + 1 < s.n_r) ? Ap[(size_t)(n + 1) * s.n_lm] : 0.0;
@@ -214,11 +215,11 @@ k_rotate_moments(int n_r, int n_lm, const T *__restrict__ rot, const double *__r
 // from fp32 roundings of c_n and d_n, widened back exactly.
 template <int CH, bool F64OUT>
 __global__ void __launch_bounds__(128)
-k_scan_warp(int n_r, int lmax, int n_lm, const double *__restrict__ A, const double *__restrict__ coef,
+k_scan_warp(int n_patch, int n_r, int lmax, int n_lm, const double *__restrict__ A, const double *__restrict__ coef,
             double *__restrict__ Q, float *__restrict__ Q32) {
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= 2 * n_lm) return;
+  if (w >= n_patch * n_lm) return;
   const int p = w / n_lm, j = w % n_lm;
   const int l = mode_degree(j);
   const int L1 = lmax + 1;
@@ -291,7 +292,7 @@ k_scan_warp(int n_r, int lmax, int n_lm, const double *__restrict__ A, const dou
   }
   double y = __shfl_down_sync(0xffffffffu, be, 1);
   if (lane == 31) y = 0.0;
-  const size_t qsz = (size_t)2 * n_r * n_lm;
+  const size_t qsz = (size_t)n_patch * n_r * n_lm;
 #pragma unroll
   for (int i = CH - 1; i >= 0; --i) {
     const bool ok = i < ch && n0 + i < n_r;
@@ -331,6 +332,7 @@ k_scan_warp(int n_r, int lmax, int n_lm, const double *__restrict__ A, const dou
 }  // namespace
 
 cudaError_t rotate_moments(yy_grid *g, bool fp64, cudaStream_t st) {
+  if (g->n_patch == 1) return cudaSuccess;   // polar grid: the scans read A itself
   const size_t smem = 2 * (size_t)g->n_lm * (fp64 ? sizeof(double) : sizeof(float));
   if (smem > 48 * 1024) {
     // the attribute belongs to the kernel, shared by all grids: the maximum
@@ -359,11 +361,12 @@ void scan_geometry(const yy_grid *g, int *nc, int *ch) {
 
 cudaError_t radial_scan(yy_grid *g, bool want_f32, bool f64_out, cudaStream_t st) {
   float *q32 = want_f32 ? g->Q32 : nullptr;
-  const unsigned wblocks = (unsigned)((2 * g->n_lm * 32 + 127) / 128);
+  const unsigned wblocks = (unsigned)((g->n_patch * g->n_lm * 32 + 127) / 128);
+  const double *At = moments_total(g);
   if (g->n_r <= 32 * 24) {
 #define YY_SCAN_WARP(CH)                                                                               \
-  (f64_out ? (k_scan_warp<CH, true><<<wblocks, 128, 0, st>>>(g->n_r, g->lmax, g->n_lm, g->Atot, g->scan, g->Q, q32), 0) \
-           : (k_scan_warp<CH, false><<<wblocks, 128, 0, st>>>(g->n_r, g->lmax, g->n_lm, g->Atot, g->scan, g->Q, q32), 0))
+  (f64_out ? (k_scan_warp<CH, true><<<wblocks, 128, 0, st>>>(g->n_patch, g->n_r, g->lmax, g->n_lm, At, g->scan, g->Q, q32), 0) \
+           : (k_scan_warp<CH, false><<<wblocks, 128, 0, st>>>(g->n_patch, g->n_r, g->lmax, g->n_lm, At, g->scan, g->Q, q32), 0))
     if (g->n_r <= 32 * 8)
       YY_SCAN_WARP(8);
     else if (g->n_r <= 32 * 12)
@@ -382,12 +385,13 @@ cudaError_t radial_scan(yy_grid *g, bool want_f32, bool f64_out, cudaStream_t st
   s.lmax = g->lmax;
   s.n_lm = g->n_lm;
   s.wpp = (g->n_lm + 31) / 32;
+  s.n_patch = g->n_patch;
   scan_geometry(g, &s.nc, &s.ch);
-  const int warps = 2 * s.wpp * s.nc;
+  const int warps = s.n_patch * s.wpp * s.nc;
   const int blocks = (warps * 32 + 127) / 128;
-  k_scan_maps<<<blocks, 128, 0, st>>>(s, g->Atot, g->scan, (Map4 *)g->scan_maps);
+  k_scan_maps<<<blocks, 128, 0, st>>>(s, At, g->scan, (Map4 *)g->scan_maps);
   g->launches++;
-  k_scan_apply<<<blocks, 128, 0, st>>>(s, g->Atot, g->scan, (const Map4 *)g->scan_maps, g->cin, g->Q,
+  k_scan_apply<<<blocks, 128, 0, st>>>(s, At, g->scan, (const Map4 *)g->scan_maps, g->cin, g->Q,
                                        want_f32 ? g->Q32 : nullptr);
   g->launches++;
   return cudaGetLastError();

@@ -152,7 +152,7 @@ __device__ __forceinline__ void pair_fma(float &h, float &l, float ah, float al,
 //  3. each thread accumulates a tile of kTJ rows x kTT functions over all k
 //     with two vector shared-memory loads per 16 products.
 template <typename T, int JC>
-__global__ void k_sep_phi(int n_r, int n_theta, int n_phi, int nt_pad, const double *__restrict__ rho0,
+__global__ void k_sep_phi(int n_shells, int n_r, int n_theta, int n_phi, int nt_pad, const double *__restrict__ rho0,
                           const double *__restrict__ rho1, const T *__restrict__ w, const T *__restrict__ az,
                           T *__restrict__ F, float2 *__restrict__ F0) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -164,7 +164,7 @@ __global__ void k_sep_phi(int n_r, int n_theta, int n_phi, int nt_pad, const dou
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
   const size_t n_ang = (size_t)n_theta * n_phi;
   const int chunks = (n_theta + JC - 1) / JC;
-  const int items = 2 * n_r * chunks;
+  const int items = n_shells * chunks;
   constexpr int kU = 16;
   const float inv_phi = 1.0f / (float)n_phi;
 
@@ -311,16 +311,17 @@ cudaError_t run_separable(yy_grid *g, const double *rho_yin, const double *rho_y
   const int jc = g->sep_jc[sizeof(T) == 8];
   const int threads = phi_threads(nt_pad, jc);
   const size_t smem_phi = phi_smem(g, nt_pad, jc, sizeof(T));
-  const int grid = std::min(2 * g->n_r * ((g->n_theta + jc - 1) / jc), blocks);
+  const int shells = grid_rows(g);
+  const int grid = std::min(shells * ((g->n_theta + jc - 1) / jc), blocks);
   if (jc == kJC)
-    k_sep_phi<T, kJC><<<grid, threads, smem_phi, s>>>(g->n_r, g->n_theta, g->n_phi, nt_pad, rho_yin, rho_yang, w, az,
-                                                      F, (float2 *)g->sep_F0);
+    k_sep_phi<T, kJC><<<grid, threads, smem_phi, s>>>(shells, g->n_r, g->n_theta, g->n_phi, nt_pad, rho_yin, rho_yang,
+                                                      w, az, F, (float2 *)g->sep_F0);
   else
-    k_sep_phi<T, kJCSmall><<<grid, threads, smem_phi, s>>>(g->n_r, g->n_theta, g->n_phi, nt_pad, rho_yin, rho_yang, w,
-                                                           az, F, (float2 *)g->sep_F0);
+    k_sep_phi<T, kJCSmall><<<grid, threads, smem_phi, s>>>(shells, g->n_r, g->n_theta, g->n_phi, nt_pad, rho_yin,
+                                                           rho_yang, w, az, F, (float2 *)g->sep_F0);
   g->launches++;
   const size_t smem_theta = (size_t)g->n_theta * nt_pad * sizeof(T) + (size_t)(g->n_theta + 1) * sizeof(float2);
-  k_sep_theta<T><<<2 * g->n_r, 256, smem_theta, s>>>(g->n_theta, g->n_lm, g->lmax + 1, nt_pad, tb, g->sep_tb0, F,
+  k_sep_theta<T><<<shells, 256, smem_theta, s>>>(g->n_theta, g->n_lm, g->lmax + 1, nt_pad, tb, g->sep_tb0, F,
                                                     (const float2 *)g->sep_F0, g->A);
   g->launches++;
   return cudaGetLastError();
@@ -339,7 +340,7 @@ struct SepOut {
 };
 
 template <typename T>
-__global__ void k_sep_synth(int n_r, int n_theta, int n_phi, int lmax, int n_lm, int n_fields, int jr,
+__global__ void k_sep_synth(int n_shells, int n_r, int n_theta, int n_phi, int lmax, int n_lm, int n_fields, int jr,
                             const double *__restrict__ Q, const T *__restrict__ P, const T *__restrict__ dP,
                             const T *__restrict__ Qs, const T *__restrict__ tr, const SepOut out) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -354,9 +355,9 @@ __global__ void k_sep_synth(int n_r, int n_theta, int n_phi, int lmax, int n_lm,
     trs[e] = (k < n_phi) ? tr[(size_t)t * n_phi + k] : T(0);
   }
   const size_t n_ang = (size_t)n_theta * n_phi;
-  const size_t qsz = (size_t)2 * n_r * n_lm;
+  const size_t qsz = (size_t)n_shells * n_lm;
   const int kg = ntr / 4;                                // groups of four longitudes
-  for (int shell = blockIdx.x; shell < 2 * n_r; shell += gridDim.x) {
+  for (int shell = blockIdx.x; shell < n_shells; shell += gridDim.x) {
     const int p = shell / n_r, i = shell % n_r;
     for (int f = 0; f < n_fields; ++f) {
       const int qb = f < 2 ? f : 2;
@@ -418,7 +419,7 @@ cudaError_t separable_prepare(yy_grid *g) {
   g->sep_nt_pad = nt_pad;
   const size_t n_az = (size_t)g->n_phi * nt_pad;
   const size_t n_tb = (size_t)g->n_theta * g->n_lm;
-  const size_t n_f = (size_t)2 * g->n_r * g->n_theta * nt_pad;
+  const size_t n_f = (size_t)grid_rows(g) * g->n_theta * nt_pad;
   cudaError_t e = cudaSuccess;
   auto A = [&](void **p, size_t bytes) {
     if (e == cudaSuccess) e = dmalloc(p, bytes);
@@ -428,7 +429,7 @@ cudaError_t separable_prepare(yy_grid *g) {
   A((void **)&g->sep_w32, (size_t)g->n_ang * sizeof(float));
   A((void **)&g->sep_tb32, n_tb * sizeof(float));
   A((void **)&g->sep_F, n_f * sizeof(double));   // float64 or fp32 partial transforms
-  A((void **)&g->sep_F0, (size_t)2 * g->n_r * g->n_theta * sizeof(float2));
+  A((void **)&g->sep_F0, (size_t)grid_rows(g) * g->n_theta * sizeof(float2));
   A((void **)&g->sep_tb0, (size_t)g->n_theta * (g->lmax + 1) * sizeof(float2));
   if (e != cudaSuccess) return e;
   k_tb0<<<(g->n_theta * (g->lmax + 1) + 255) / 256, 256>>>(g->n_theta, g->lmax, g->n_lm, g->dph, g->tbar,
@@ -513,17 +514,17 @@ cudaError_t synthesis_separable(yy_grid *g, double *phi_yin, double *phi_yang, d
   o.o[0][1] = phi_yang;
   for (int c = 0; c < 3 && grad_yin; ++c) {
     o.o[1 + c][0] = grad_yin + c * comp;
-    o.o[1 + c][1] = grad_yang + c * comp;
+    o.o[1 + c][1] = grad_yang ? grad_yang + c * comp : nullptr;
   }
   const int n_fields = grad_yin ? 4 : 1;
   const int q = fp64 ? 1 : 0;
-  const int blocks = std::min(2 * g->n_r, g->sep_syn_blocks[q]);
+  const int blocks = std::min(grid_rows(g), g->sep_syn_blocks[q]);
   if (fp64)
-    k_sep_synth<double><<<blocks, 256, g->sep_syn_smem[1], s>>>(g->n_r, g->n_theta, g->n_phi, g->lmax, g->n_lm,
+    k_sep_synth<double><<<blocks, 256, g->sep_syn_smem[1], s>>>(grid_rows(g), g->n_r, g->n_theta, g->n_phi, g->lmax, g->n_lm,
                                                                 n_fields, g->sep_syn_rows[1], g->Q, g->sep_P, g->sep_dP, g->sep_Qs,
                                                                 g->sep_tr, o);
   else
-    k_sep_synth<float><<<blocks, 256, g->sep_syn_smem[0], s>>>(g->n_r, g->n_theta, g->n_phi, g->lmax, g->n_lm,
+    k_sep_synth<float><<<blocks, 256, g->sep_syn_smem[0], s>>>(grid_rows(g), g->n_r, g->n_theta, g->n_phi, g->lmax, g->n_lm,
                                                                n_fields, g->sep_syn_rows[0], g->Q, g->sep_P32, g->sep_dP32, g->sep_Qs32,
                                                                g->sep_tr32, o);
   g->launches++;

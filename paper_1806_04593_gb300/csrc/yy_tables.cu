@@ -483,6 +483,12 @@ __global__ void k_scan_coeffs(int n_r, int lmax, double G, const double *__restr
   o[7] = -fq * inv_r;               // g_angle:   G 4pi/(2l+1) (c + d) / r
 }
 
+// w = 1: on the full spherical polar grid every cell is counted once
+__global__ void k_unit_weights(int n, double *__restrict__ w) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) w[e] = 1.0;
+}
+
 __global__ void k_round_f32(int n, const double *__restrict__ src, float *__restrict__ dst) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) dst[e] = (float)src[e];
@@ -509,7 +515,10 @@ cudaError_t build_tables(yy_grid *g, const double *gl_host, int n_gl) {
   wg.t2 = tan(kPi / 4 - g->delta_phi);
   wg.n_theta = g->n_theta;
   wg.n_phi = g->n_phi;
-  k_weights<<<(g->n_ang + 127) / 128, 128>>>(wg, g->gl_nodes, g->w);
+  if (g->n_patch == 2)
+    k_weights<<<(g->n_ang + 127) / 128, 128>>>(wg, g->gl_nodes, g->w);
+  else
+    k_unit_weights<<<(g->n_ang + 255) / 256, 256>>>(g->n_ang, g->w);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
 
   const double *gx = g->gl_nodes + 2 * YY_GL_WEIGHT_NODES;
@@ -539,7 +548,7 @@ cudaError_t build_tables(yy_grid *g, const double *gl_host, int n_gl) {
   k_synth_tables<<<g->n_ang, 96, smem>>>(sg, g->ysyn, g->ysyn_t, g->ysyn_p);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
 
-  {
+  if (g->n_patch == 2) {
     // rotation table: n_mu = lmax + 1 Gauss-Legendre nodes (after the T nodes) x 2 lmax + 2 azimuths
     const int n_mu = g->lmax + 1, n_az = 2 * g->lmax + 2, n_pts = n_mu * n_az;
     const double *mx = gx + 2 * n_gl, *mw = mx + n_mu;
@@ -573,9 +582,11 @@ cudaError_t build_tables(yy_grid *g, const double *gl_host, int n_gl) {
     k_sep_trig<<<(n_tr + 255) / 256, 256>>>(g->n_phi, g->lmax, g->ph0, g->dph, g->sep_tr);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
-  const int n_rot = rotation_table_size(g->lmax);
-  k_round_f32<<<(n_rot + 255) / 256, 256>>>(n_rot, g->rot, g->rot32);
-  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if (g->n_patch == 2) {
+    const int n_rot = rotation_table_size(g->lmax);
+    k_round_f32<<<(n_rot + 255) / 256, 256>>>(n_rot, g->rot, g->rot32);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
 
   const int n_sc = g->n_r * (g->lmax + 1);
   k_scan_coeffs<<<(n_sc + 127) / 128, 128>>>(g->n_r, g->lmax, g->G, g->r_edges, g->scan);

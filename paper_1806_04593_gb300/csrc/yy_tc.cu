@@ -1131,11 +1131,11 @@ static cudaError_t launch_pair(yy_grid *g, yy_tc_tables *t, const PairMaps &maps
 
 template <class F>
 static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
-  const int M = 2 * g->n_r;
+  const int M = grid_rows(g);
   if (cudaFuncSetAttribute(k_tc_pair<F, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) != cudaSuccess ||
       cudaFuncSetAttribute(k_tc_pair<F, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) != cudaSuccess)
     return YY_ERR_NOT_SUPPORTED;
-  // the 2 n_r rows: tiles of at most 256, each a multiple of 16
+  // the n_patch n_r rows: tiles of at most 256, each a multiple of 16
   t->row_tiles = (M + 255) / 256;
   t->bn = round_up((M + t->row_tiles - 1) / t->row_tiles, 16);
   t->rows_pad = t->row_tiles * t->bn;
@@ -1286,7 +1286,7 @@ void tc_free(yy_grid *g) {
 
 template <class F>
 static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, const double *rg, cudaStream_t s) {
-  const int M = 2 * g->n_r;
+  const int M = grid_rows(g);
   PackBatch b = {};
   PackArgs &p = b.job[0];
   p.rows = M;
@@ -1336,7 +1336,7 @@ static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, 
 
 template <class F>
 static cudaError_t pack_coefficients_form(yy_grid *g, yy_tc_tables *t, cudaStream_t s) {
-  const int M = 2 * g->n_r;
+  const int M = grid_rows(g);
   const size_t qsz = (size_t)M * g->n_lm;
   // Phi and g_r: the monopole (column 0) is added in the epilogue
   const double add[3] = {kY00, kY00, 0.0};
@@ -1380,7 +1380,7 @@ static cudaError_t synthesis_form(yy_grid *g, yy_tc_tables *t, double *py, doubl
   a.stages = t->stages;
   a.cells = g->n_ang;
   a.cell_tiles = t->sy_cells_pad / (2 * kPairRows);
-  a.rows = 2 * g->n_r;
+  a.rows = grid_rows(g);
   a.row_tiles = t->row_tiles;
   a.bn = t->bn;
   a.kb_total = t->sy_kpad * F::kElem / kRowBytes;

@@ -69,6 +69,8 @@ def load():
     I = ctypes.c_int
     lib.yy_grid_create.argtypes = [P, I, I, I, D, D, I, D, ctypes.POINTER(P)]
     lib.yy_grid_create.restype = I
+    lib.yy_polar_grid_create.argtypes = [P, I, I, I, I, D, ctypes.POINTER(P)]
+    lib.yy_polar_grid_create.restype = I
     lib.yy_grid_prepare.argtypes = [P, I]
     lib.yy_grid_prepare.restype = I
     lib.yy_grid_set_analysis.argtypes = [P, I]
@@ -150,6 +152,15 @@ def yy_grid_create(r_edges, n_theta, n_phi, delta_theta, delta_phi, l_max, G=1.0
     st = load().yy_grid_create(r.ctypes.data, int(r.size - 1), int(n_theta), int(n_phi),
                                float(delta_theta), float(delta_phi), int(l_max), float(G),
                                ctypes.byref(h))
+    return st, h.value
+
+
+def yy_polar_grid_create(r_edges, n_theta, n_phi, l_max, G=1.0):
+    """Returns (status, handle) of a full spherical polar grid."""
+    r = np.ascontiguousarray(r_edges, dtype=np.float64)
+    h = ctypes.c_void_p()
+    st = load().yy_polar_grid_create(r.ctypes.data, int(r.size - 1), int(n_theta), int(n_phi), int(l_max),
+                                     float(G), ctypes.byref(h))
     return st, h.value
 
 
@@ -320,6 +331,8 @@ class Grid:
 
     @classmethod
     def from_spec(cls, spec):
+        if getattr(spec, "polar", False):
+            return PolarGrid(spec.r_edges, spec.n_theta, spec.n_phi, spec.lmax, spec.G)
         return cls(spec.r_edges, spec.n_theta, spec.n_phi, spec.delta_theta, spec.delta_phi,
                    spec.lmax, spec.G)
 
@@ -378,3 +391,30 @@ class Grid:
             self.close()
         except Exception:
             pass
+
+
+class PolarGrid(Grid):
+    """Owning wrapper of a full spherical polar grid handle (one patch)."""
+
+    def __init__(self, r_edges, n_theta, n_phi, l_max, G=1.0):
+        st, h = yy_polar_grid_create(r_edges, n_theta, n_phi, l_max, G)
+        if st != YY_OK:
+            raise YYError(st, "yy_polar_grid_create")
+        self.handle = h
+        self.n_r = int(np.asarray(r_edges).size - 1)
+        self.n_theta, self.n_phi, self.l_max = int(n_theta), int(n_phi), int(l_max)
+        self.n_lm = (self.l_max + 1) ** 2
+
+    def solve(self, rho, rho_yang=None, gradient=False, prec=YY_FP64, stream=None):
+        """Allocate outputs and solve; returns {'phi': ..., 'grad': ...}."""
+        import torch
+        if rho_yang is not None:
+            raise ValueError("a polar grid has one patch")
+        phi = torch.empty_like(rho)
+        grad = torch.empty((3,) + tuple(rho.shape), dtype=torch.float64, device=rho.device) if gradient else None
+        self.potential(rho, None, phi, None, grad, None, prec, stream)
+        out = {"phi": phi}
+        if gradient:
+            out["grad"] = grad
+        return out
+

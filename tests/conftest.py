@@ -18,14 +18,18 @@ _GRID_CACHE = {}
 @pytest.fixture(scope="session")
 def oracle_grid():
     """Session-cached oracle grids by spec name."""
-    from oracle import OracleGrid
+    from oracle import OracleGrid, OraclePolarGrid
 
     def get(spec):
-        key = (spec.name, spec.n_r, spec.n_theta, spec.n_phi, spec.lmax,
+        polar = bool(getattr(spec, "polar", False))
+        key = (spec.name, polar, spec.n_r, spec.n_theta, spec.n_phi, spec.lmax,
                spec.delta_theta, spec.delta_phi, float(spec.r_edges[0]), float(spec.r_edges[-1]))
         if key not in _GRID_CACHE:
-            _GRID_CACHE[key] = OracleGrid(spec.r_edges, spec.n_theta, spec.n_phi,
-                                          spec.delta_theta, spec.delta_phi, spec.lmax, spec.G)
+            if polar:
+                _GRID_CACHE[key] = OraclePolarGrid(spec.r_edges, spec.n_theta, spec.n_phi, spec.lmax, spec.G)
+            else:
+                _GRID_CACHE[key] = OracleGrid(spec.r_edges, spec.n_theta, spec.n_phi,
+                                              spec.delta_theta, spec.delta_phi, spec.lmax, spec.G)
         return _GRID_CACHE[key]
 
     return get

@@ -31,7 +31,7 @@ def lib_path():
 
 def test_headers_declare_the_boundary():
     names = _declared_functions()
-    for required in ("yy_grid_create", "yy_potential", "yy_destroy", "yy_potential_host",
+    for required in ("yy_grid_create", "yy_polar_grid_create", "yy_potential", "yy_destroy", "yy_potential_host",
                      "yy_grid_prepare", "yy_last_device_status", "yy_status_string"):
         assert required in names
 
@@ -64,6 +64,9 @@ def test_invalid_arguments_rejected_on_host(lib_path):
     ]
     for args in bad:
         st, h = yy.yy_grid_create(*args)
+        assert st == yy.YY_ERR_INVALID_ARG and not h, args
+    for args in [(r[::-1], 4, 12, 4), (r, 4, 0, 4), (r, 4, 12, 81), (np.array([-1.0, 0.5, 1.0]), 4, 12, 2)]:
+        st, h = yy.yy_polar_grid_create(*args)
         assert st == yy.YY_ERR_INVALID_ARG and not h, args
     assert yy.yy_potential(None, 16, 16, 16, 16) == yy.YY_ERR_INVALID_ARG
     assert yy.yy_grid_prepare(None, yy.YY_FP64) == yy.YY_ERR_INVALID_ARG
