@@ -114,19 +114,29 @@ typedef enum {
   YY_TABLE_MOMENTS_TOTAL = 9
 } yy_table;
 
-/* How the analysis is evaluated (yy_grid_set_analysis).
- *   YY_ANALYSIS_AUTO (default)  separable for YY_FP64 and YY_FP32, dense for
- *       the tensor-core forms (there the tensor cores outrun the separable
- *       stages on CUDA cores despite 12.6 times the flops).
+/* How the analysis and the synthesis are evaluated (yy_grid_set_analysis).
+ *   YY_ANALYSIS_AUTO (default)  separable analysis and synthesis for YY_FP64
+ *       and YY_FP32; dense contractions for the tensor-core forms (there the
+ *       tensor cores outrun the separable stages despite 12.6 times the
+ *       flops).  Grids whose tables overflow the separable kernels' shared
+ *       memory use the dense evaluation.
  *   YY_ANALYSIS_SEPARABLE  the weight folded into the density, then
  *       an azimuthal stage (cell integrals C_k^(m), S_k^(m)) and a polar stage
  *       (K_lm T_j^(lm)): 2 n_ang (2 l_max + 1) + 2 n_theta n_lm flops per shell.
  *       Float64 for YY_FP64; for the other forms fp32 on CUDA cores with the
  *       m = 0 sums (the monopole) carried in float64.
+ *       The synthesis is separable too: a polar stage
+ *       G[t] = sum_l q[l^2 + t] K_lm P_l^m (theta_j) and an azimuthal stage
+ *       sum_t G[t] {cos, sin}(m phi_k); for the tensor-core forms the polar
+ *       stage runs on CUDA cores and the azimuthal one on the tensor cores
+ *       with G and the trig table as three bf16 pieces (the t = 0 term, which
+ *       holds the monopole, added per cell).
  *   YY_ANALYSIS_DENSE  one contraction of the densities with the full
  *       analysis table, 2 n_ang n_lm flops per shell, in the form's arithmetic
- *       (tensor cores for YY_TF32 / YY_BF16X3 / YY_FP16X2).
- * Both give the §3 moments A_p (Eqs. ac/as with the §4 weights).           */
+ *       (tensor cores for YY_TF32 / YY_BF16X3 / YY_FP16X2), and the synthesis
+ *       as dense contractions with the full harmonic tables.
+ * All give the §3 moments A_p (Eqs. ac/as with the §4 weights) and the §2
+ * sums of Eq. potential.                                                   */
 typedef enum {
   YY_ANALYSIS_AUTO = 0,
   YY_ANALYSIS_SEPARABLE = 1,
@@ -281,7 +291,7 @@ yy_status yy_batch_create(const yy_field_desc *fields, int n_fields, yy_batch **
 /* yy_grid_prepare for every field. */
 yy_status yy_batch_prepare(yy_batch *b, yy_precision prec);
 
-/* Autotuner: for every field, time each analysis evaluation (YY_ANALYSIS_DENSE,
+/* Autotuner: for every field, time each evaluation (YY_ANALYSIS_DENSE,
  * YY_ANALYSIS_SEPARABLE; reps solves each on zero densities in scratch
  * buffers it allocates and frees) in the given form, with or without the
  * gradient, and record the faster for that form: later graphs of that form

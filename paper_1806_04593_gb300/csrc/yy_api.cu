@@ -285,16 +285,25 @@ yy_status yy_potential(yy_grid *g, const double *rho_yin, const double *rho_yang
       e = simt ? analysis_simt(g, rho_yin, rho_yang, f32, s) : tc_analysis(g, prec, rho_yin, rho_yang, s);
   }
   mark(1);
+  // synthesis evaluation: on the CUDA-core forms separable unless
+  // YY_ANALYSIS_DENSE is set; on the tensor-core forms dense unless
+  // YY_ANALYSIS_SEPARABLE is set (there the dense contraction is faster);
+  // dense wherever the grid does not fit the separable kernels
+  const bool sep_synth = simt ? (g->analysis_method != YY_ANALYSIS_DENSE && (g->sep_syn_ok & (f32 ? 1 : 2)) != 0)
+                              : (g->analysis_method == YY_ANALYSIS_SEPARABLE && tc_separable_synthesis_ready(g, prec));
+  g->last_sep_synthesis = sep_synth ? 1 : 0;
   if (e == cudaSuccess) e = rotate_moments(g, prec == YY_FP64, s);
   if (e == cudaSuccess) e = radial_scan(g, f32, true, s);
-  if (e == cudaSuccess && !simt) e = tc_pack_coefficients(g, prec, s);
+  if (e == cudaSuccess && !simt)
+    e = sep_synth ? tc_theta(g, prec, grad_yin != nullptr, s) : tc_pack_coefficients(g, prec, s);
   mark(2);
   if (e == cudaSuccess) {
-    if (simt && g->analysis_method != YY_ANALYSIS_DENSE && (g->sep_syn_ok & (f32 ? 1 : 2)))
-      e = synthesis_separable(g, phi_yin, phi_yang, grad_yin, grad_yang, !f32, s);
+    if (simt)
+      e = sep_synth ? synthesis_separable(g, phi_yin, phi_yang, grad_yin, grad_yang, !f32, s)
+                    : synthesis_simt(g, phi_yin, phi_yang, grad_yin, grad_yang, f32, s);
     else
-      e = simt ? synthesis_simt(g, phi_yin, phi_yang, grad_yin, grad_yang, f32, s)
-               : tc_synthesis(g, prec, phi_yin, phi_yang, grad_yin, grad_yang, s);
+      e = sep_synth ? tc_separable_synthesis(g, prec, phi_yin, phi_yang, grad_yin, grad_yang, s)
+                    : tc_synthesis(g, prec, phi_yin, phi_yang, grad_yin, grad_yang, s);
   }
   mark(3);
   return from_cuda(e);
@@ -420,7 +429,8 @@ double yy_solve_flops(const yy_grid *g, int with_gradient) {
   const double analysis = g->last_separable
                               ? 2.0 * M * K_an * nt + 2.0 * M * g->n_theta * N_an
                               : 2.0 * M * N_an * K_an;
-  const double synth = 2.0 * M * g->n_lm * g->n_ang;
+  const double synth = g->last_sep_synthesis ? 2.0 * M * g->n_theta * N_an + 2.0 * M * K_an * nt
+                                             : 2.0 * M * g->n_lm * g->n_ang;
   double rotation = 0.0;
   for (int l = 0; l <= g->lmax && g->n_patch == 2; ++l) rotation += 2.0 * M * (2.0 * l + 1.0) * (2.0 * l + 1.0);
   return analysis + rotation + (with_gradient ? 4.0 : 1.0) * synth;

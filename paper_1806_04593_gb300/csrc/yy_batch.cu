@@ -7,9 +7,9 @@
 // the short kernels of one field overlap the long ones of another, and then
 // replays the instantiated graph on the caller's stream.  Graphs are cached
 // per (precision, gradient, buffer pointers): a replay costs one launch.
-// yy_batch_tune is the autotuner: for every field it times each analysis
-// evaluation (dense contraction, separable stages) on scratch buffers and
-// records the faster one for that precision; the capture applies it.
+// yy_batch_tune is the autotuner: for every field it times both evaluations
+// (dense contractions, separable stages) on scratch buffers and records the
+// faster for that precision; the capture applies it.
 #include <string.h>
 
 #include <new>

@@ -50,6 +50,7 @@ struct yy_grid {
 
   // separable analysis (yy_separable.cu)
   int analysis_method;  // yy_analysis
+  int last_sep_synthesis;   // the last solve's synthesis ran in separable form
   int last_separable;   // the last solve used the separable analysis
   int sep_nt_pad;       // 2 l_max + 1 azimuthal functions, padded to a multiple of 4
   int sep_ok;           // the grid fits the separable kernels' shared memory: bit 0 fp32, bit 1 float64
@@ -129,6 +130,12 @@ void tc_free(yy_grid *g);
 cudaError_t tc_analysis(yy_grid *g, yy_precision prec, const double *rho_yin,
                         const double *rho_yang, cudaStream_t s);
 cudaError_t tc_pack_coefficients(yy_grid *g, yy_precision prec, cudaStream_t s);
+// separable synthesis on the tensor cores: polar stage (G operands), then the
+// azimuthal contraction; available once the form is prepared, when it fits
+bool tc_separable_synthesis_ready(const yy_grid *g, yy_precision prec);
+cudaError_t tc_theta(yy_grid *g, yy_precision prec, bool grad, cudaStream_t s);
+cudaError_t tc_separable_synthesis(yy_grid *g, yy_precision prec, double *phi_yin, double *phi_yang,
+                                   double *grad_yin, double *grad_yang, cudaStream_t s);
 cudaError_t tc_synthesis(yy_grid *g, yy_precision prec, double *phi_yin,
                          double *phi_yang, double *grad_yin, double *grad_yang, cudaStream_t s);
 

@@ -92,6 +92,12 @@ constexpr int kAnalysisFill = 256;
 // as the shared memory holds (at most kMaxStages).
 constexpr int kPairRows = 128;
 constexpr int kPairTmemCols = 512;   // two accumulators of up to 256 columns
+// out_mode 2 stages each epilogue warp's 32 x 16 results in shared memory
+// (rows padded to 18 doubles: 16-byte accesses without bank conflicts) plus
+// its 32 output-row pointers, so that the float64 stores run along the rows
+constexpr int kEpiPad = kEpiCols + 2;
+constexpr int kEpiWarpBytes = 32 * kEpiPad * 8 + 32 * 8;
+constexpr int kEpiStageBytes = kEpiWarps * kEpiWarpBytes;
 constexpr int kMaxStages = 16;
 constexpr int kSmemLimit = 232448;   // dynamic shared memory of one CTA
 constexpr int kSmemFixed = 1024 /*alignment*/ + 512 /*barriers, TMEM address*/;
@@ -101,8 +107,8 @@ constexpr int pair_stage_bytes(int bn) {
   return (F::kPA * kPairRows + F::kPB * (bn / 2)) * kRowBytes;
 }
 template <class F>
-int pair_stages(int bn) {
-  const int s = (kSmemLimit - kSmemFixed) / pair_stage_bytes<F>(bn);
+int pair_stages(int bn, int reserve = 0) {
+  const int s = (kSmemLimit - kSmemFixed - reserve) / pair_stage_bytes<F>(bn);
   return s < kMaxStages ? s : kMaxStages;
 }
 
@@ -236,8 +242,13 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity
 }
 
 // Arrive on a barrier given by its shared::cluster address (own or peer CTA).
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+// Release of a TMEM accumulator by an epilogue warp.  Its tcgen05.ld have
+// completed (tcgen05.wait::ld) and are fenced (tcgen05.fence::before_thread_sync)
+// before this arrive, so the MMAs that follow the barrier cannot disturb
+// them; nothing else needs ordering, in particular not the warp's global
+// stores, which a release arrive would wait for.
+__device__ __forceinline__ void mbar_arrive_cluster_relaxed(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 
 // TMA load into this CTA's shared memory that completes on a barrier of
@@ -346,7 +357,9 @@ __device__ __forceinline__ float f64_to_f32(double x) {
 // of both CTAs release a buffer on the even CTA's "tempty" barrier.
 struct PairJob {
   double *out0, *out1;          // row r < out_split -> out0 + r ldo, else out1 + (r - out_split) ldo
+                                // (out_mode 2: cell c < out_split -> out0 + c ldo, ...)
   const float *cell_scale, *row_scale, *row_add;
+  const float *cell_add;        // out_mode 2: added to every value of the cell
   int ta, tb;                   // operand maps of this job
 };
 
@@ -358,7 +371,8 @@ struct PairArgs {
   int k_splits, kb_per_split;   // K split of every tile
   int kb_chunk;                 // K blocks per accumulator fill; mode 0 adds the fills in registers
   int a_rows, b_rows;           // rows of one piece in the stacked A / B operands
-  int out_mode;                 // 1: scaled float64 job outputs; 0: raw fp32 partial sums
+  int out_mode;                 // 1: scaled float64 job outputs; 0: raw fp32 partial sums;
+                                // 2: scaled float64 outputs stored along the rows of each cell
   float *part;                  // mode 0: part[(z rows + row) part_ld + cell]
   int part_ld;
   int out_split;
@@ -369,7 +383,7 @@ struct PairArgs {
 };
 
 struct PairMaps {
-  CUtensorMap a[3], b[3];       // tables (operand A), coefficient sets (operand B)
+  CUtensorMap a[4], b[3];       // tables (operand A), coefficient sets (operand B)
 };
 
 template <class F, int OUT_MODE>
@@ -560,7 +574,7 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
           }
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive_cluster(tempty_even + (uint32_t)(b * sizeof(uint64_t)));
+          if (lane == 0) mbar_arrive_cluster_relaxed(tempty_even + (uint32_t)(b * sizeof(uint64_t)));
         }
         if (!ok) break;
         if (cell < a.cells) {
@@ -576,6 +590,80 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
             }
           }
         }
+      }
+    } else if constexpr (OUT_MODE == 2) {
+      // Cells are rows of the output arrays (stride ldo) and the accumulator
+      // columns run along them: each lane holds 16 consecutive values of its
+      // cell's row.  They go through this warp's shared-memory block, and the
+      // warp then writes two cells' 16-value runs per store instruction.
+      uint8_t *wbuf = smem + S * STAGE + 512 + (size_t)(warp - 2) * kEpiWarpBytes;
+      double *ebuf = reinterpret_cast<double *>(wbuf);                          // [32][kEpiPad]
+      double **rowp = reinterpret_cast<double **>(wbuf + 32 * kEpiPad * 8);     // [32] output rows
+      const bool vec = (a.ldo & 1) == 0;   // rows start on 16-byte boundaries (with 16-byte aligned bases)
+      for (int t = pair; t < total; t += n_pairs, ++it) {
+        const int b = it & 1;
+        const PairJob &J = a.job[t / per_job];
+        const int tl = t % per_job;
+        const int rt = tl % a.row_tiles, ct = (tl / a.row_tiles) % a.cell_tiles;
+        const int cell0 = (2 * ct + rank) * kPairRows + quarter * 32;
+        const int cell = cell0 + lane;
+        const bool cell_ok = cell < a.cells;
+        const float cs = cell_ok ? J.cell_scale[cell] : 0.0f;
+        const float ca = cell_ok ? J.cell_add[cell] : 0.0f;
+        __syncwarp();   // the previous tile's row pointers are no longer read
+        rowp[lane] = !cell_ok ? nullptr
+                     : (cell < a.out_split) ? J.out0 + (size_t)cell * a.ldo
+                                            : J.out1 + (size_t)(cell - a.out_split) * a.ldo;
+        if (!mbar_wait_cluster(&tfull[b], (it >> 1) & 1, a.err)) break;
+        tc_fence_after();
+        const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
+#pragma unroll 1
+        for (int k = sub; k < n_chunks; k += kEpiPerQuarter) {
+          const int row0 = rt * a.bn + k * kEpiCols;
+          uint32_t v[16];
+          tmem_ld16_async(tbase + (uint32_t)(k * kEpiCols), v);
+          float4 rs4[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) rs4[q] = reinterpret_cast<const float4 *>(J.row_scale + row0)[q];
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < kEpiCols; j += 2) {
+            const float4 r4 = rs4[j >> 2];
+            const float ra = (j & 2) ? r4.z : r4.x, rb = (j & 2) ? r4.w : r4.y;
+            *reinterpret_cast<double2 *>(ebuf + lane * kEpiPad + j) =
+                make_double2(f32_to_f64(fmaf(__uint_as_float(v[j]) * cs, ra, ca)),
+                             f32_to_f64(fmaf(__uint_as_float(v[j + 1]) * cs, rb, ca)));
+          }
+          __syncwarp();
+          if (vec) {
+            // lanes 8 c' + e: cell 4 q + c', values 2 e and 2 e + 1 of the run
+            const int e = lane & 7, row = row0 + 2 * e;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int c = 4 * q + (lane >> 3);
+              double *orow = rowp[c];
+              const double2 val = *reinterpret_cast<const double2 *>(ebuf + c * kEpiPad + 2 * e);
+              if (orow != nullptr) {
+                if (row + 1 < a.rows)
+                  *reinterpret_cast<double2 *>(orow + row) = val;
+                else if (row < a.rows)
+                  orow[row] = val.x;
+              }
+            }
+          } else {
+            const int e = lane & 15, row = row0 + e;
+#pragma unroll 4
+            for (int q = 0; q < 16; ++q) {
+              const int c = 2 * q + (lane >> 4);
+              double *orow = rowp[c];
+              if (orow != nullptr && row < a.rows) orow[row] = ebuf[c * kEpiPad + e];
+            }
+          }
+          __syncwarp();
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster_relaxed(tempty_even + (uint32_t)(b * sizeof(uint64_t)));
       }
     } else
     for (int t = pair; t < total; t += n_pairs, ++it) {
@@ -622,7 +710,7 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive_cluster(tempty_even + (uint32_t)(b * sizeof(uint64_t)));
+      if (lane == 0) mbar_arrive_cluster_relaxed(tempty_even + (uint32_t)(b * sizeof(uint64_t)));
     }
   }
   __syncthreads();
@@ -968,6 +1056,194 @@ k_pack_reg(PackBatch batch) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// separable synthesis on the tensor cores: the polar stage
+// ---------------------------------------------------------------------------
+//
+// For every output row (shell, j) and field f, the azimuthal coefficients
+//   G_f[t] = sum_{l >= m(t)} q_f[l^2 + t] T_f[j][l^2 + t]
+// (T = K_lm P_l^m, its theta derivative, or m K_lm P_l^m / sin theta; g_phi
+// takes the sin coefficient into the cos slot and minus the cos one into the
+// sin slot), so that the field is sum_t G_f[t] trig_t(phi_k): the azimuthal
+// stage is a contraction with K = 2 l_max + 1 done by k_tc_pair (out_mode 2).
+// t = 0 (cos 0 = 1 at every phi_k) carries the monopole; it is summed as an
+// unevaluated fp32 pair and added per cell, and its slot of the operand is
+// zero.  The other slots are scaled per row by a power of two (row maximum in
+// [2^14, 2^15)) and split into the form's pieces.  One block per shell, one
+// warp per (j, field); each lane owns slots 2 lane + {0, 1} + 64 i.
+
+struct ThetaArgs {
+  int n_shells, n_theta, lmax, n_lm, nt, k_pad, n_jobs, rows_pad;
+  const double *Q;              // [3][n_shells][n_lm]: Phi, g_r and angular coefficients
+  const float *tab[3];          // [n_theta][n_lm]: P, dP/dtheta, m P / sin theta
+  const double *tab64[2];       // [n_theta][n_lm]: P and dP in float64 (their l = 0 column is used)
+  void *G[4];                   // per field: bf16 pieces [3][rows_pad][k_pad]
+  float *add[4];                // per field: [rows_pad] slot-0 term
+};
+
+constexpr int kThetaSmemMax = 200 * 1024;
+
+// exact split of an fp32 value into three bf16 pieces (hi + mid + lo)
+__device__ __forceinline__ void split_bf16x3(float y, __nv_bfloat16 *base, size_t stride) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(y);
+  const float r = y - __bfloat162float(h);
+  const __nv_bfloat16 m = __float2bfloat16_rn(r);
+  base[0] = h;
+  base[stride] = m;
+  base[2 * stride] = __float2bfloat16_rn(r - __bfloat162float(m));
+}
+
+// Blocks take S consecutive shells (coefficients in shared memory, shell
+// fastest so that one vector load serves all S); a warp task is two polar
+// rows j of one field.  Slots come in blocks of 64; lane i takes slots
+// c0 + i and c0 + 63 - i, whose l-ranges (l >= m(t), m = ceil(t / 2)) add up
+// to about the same length in every lane, walked as one loop.  G goes out
+// unscaled as three bf16 pieces (bf16 has the fp32 exponent range); slot 0 is
+// zero and its value (the m = 0 cos term, which holds the monopole) goes to
+// add[] with the l = 0 product in float64.
+template <int S, bool STAGE>
+__global__ void __launch_bounds__(256) k_theta_g(ThetaArgs a) {
+  extern __shared__ __align__(16) float qs[];                 // [3][n_lm][S], then (STAGE) [8 warps][2][n_lm]
+  const int shell0 = blockIdx.x * S;
+  const int ns = min(S, a.n_shells - shell0);
+  const size_t qsz = (size_t)a.n_shells * a.n_lm;
+  for (int e = threadIdx.x; e < 3 * a.n_lm * S; e += blockDim.x) {
+    const int sh = e % S, ci = e / S;                         // ci = c n_lm + idx
+    const int c = ci / a.n_lm, idx = ci - c * a.n_lm;
+    qs[e] = sh < ns ? f64_to_f32(a.Q[c * qsz + (size_t)(shell0 + sh) * a.n_lm + idx]) : 0.0f;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t ps = (size_t)a.rows_pad * a.k_pad;
+  const int L = a.lmax;
+  const int pairs_j = (a.n_theta + 1) >> 1;
+  for (int task = warp; task < pairs_j * a.n_jobs; task += blockDim.x >> 5) {
+    const int job = task % a.n_jobs, j0 = 2 * (task / a.n_jobs);
+    const bool two = j0 + 1 < a.n_theta;
+    const int c = job < 2 ? job : 2;
+    const float *T0 = a.tab[job < 2 ? 0 : job - 1] + (size_t)j0 * a.n_lm;
+    const float *T1 = two ? T0 + a.n_lm : T0;
+    if constexpr (STAGE) {
+      // the task's two table rows, read once with coalesced loads
+      float *tw = qs + (size_t)3 * a.n_lm * S + (size_t)warp * 2 * a.n_lm;
+      __syncwarp();
+      for (int e = lane; e < a.n_lm; e += 32) {
+        tw[e] = T0[e];
+        tw[a.n_lm + e] = T1[e];
+      }
+      __syncwarp();
+      T0 = tw;
+      T1 = tw + a.n_lm;
+    }
+    const float *qc = qs + (size_t)c * a.n_lm * S;
+    for (int c0 = 0; c0 < a.k_pad; c0 += 64) {
+      const int ta = c0 + lane, tb = c0 + 63 - lane;
+      const int ma = (ta + 1) >> 1, mb = (tb + 1) >> 1;
+      const int na = (ta >= 1 && ta < a.nt) ? L + 1 - ma : 0;
+      const int nb = (tb >= 1 && tb < a.nt) ? L + 1 - mb : 0;
+      // d/dphi (g_phi): the sin slot takes minus the cos coefficient, the cos slot the sin one
+      const int sa = job == 3 ? ((ta & 1) ? ta + 1 : ta - 1) : ta;
+      const int sb = job == 3 ? ((tb & 1) ? tb + 1 : tb - 1) : tb;
+      float acc[2][S], va[2][S];
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int q = 0; q < S; ++q) acc[r][q] = va[r][q] = 0.0f;
+      int t = ta, src = sa, l = ma;
+      for (int k = 0; k < na + nb; ++k) {
+        if (k == na) {
+#pragma unroll
+          for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int q = 0; q < S; ++q) {
+              va[r][q] = acc[r][q];
+              acc[r][q] = 0.0f;
+            }
+          t = tb;
+          src = sb;
+          l = mb;
+        }
+        const int b = l * l;
+        const float x0 = T0[b + t], x1 = T1[b + t];
+        const float *qv = qc + (size_t)(b + src) * S;
+        float qq[S];
+        if constexpr (S % 4 == 0) {
+#pragma unroll
+          for (int q = 0; q < S; q += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(qv + q);
+            qq[q] = v.x;
+            qq[q + 1] = v.y;
+            qq[q + 2] = v.z;
+            qq[q + 3] = v.w;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < S; ++q) qq[q] = qv[q];
+        }
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+          acc[0][q] = fmaf(qq[q], x0, acc[0][q]);
+          acc[1][q] = fmaf(qq[q], x1, acc[1][q]);
+        }
+        ++l;
+      }
+      if (nb == 0) {   // the loop never reached the switch: acc holds slot ta
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+          for (int q = 0; q < S; ++q) {
+            va[r][q] = acc[r][q];
+            acc[r][q] = 0.0f;
+          }
+      }
+      const float sga = (job == 3 && !(ta & 1)) ? -1.0f : 1.0f, sgb = (job == 3 && !(tb & 1)) ? -1.0f : 1.0f;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if (r == 1 && !two) break;
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+          if (q >= ns) break;
+          __nv_bfloat16 *row = (__nv_bfloat16 *)a.G[job] + ((size_t)(shell0 + q) * a.n_theta + j0 + r) * a.k_pad;
+          split_bf16x3(sga * va[r][q], row + ta, ps);
+          split_bf16x3(sgb * acc[r][q], row + tb, ps);
+        }
+      }
+    }
+    // slot 0: lane 2 q + r sums shell q, row j0 + r
+    if (lane < 2 * ns && (lane & 1) <= (two ? 1 : 0)) {
+      const int q = lane >> 1, r = lane & 1;
+      float add = 0.0f;
+      if (job < 3) {
+        const float *T = r ? T1 : T0;
+        float sum = 0.0f;
+        for (int l = L; l >= 1; --l) sum = fmaf(qc[(size_t)(l * l) * S + q], T[l * l], sum);
+        const double q00 = a.Q[c * qsz + (size_t)(shell0 + q) * a.n_lm];
+        const double t00 = a.tab64[job < 2 ? 0 : 1][(size_t)(j0 + r) * a.n_lm];
+        add = f64_to_f32(fma(q00, t00, f32_to_f64(sum)));
+      }
+      a.add[job][(size_t)(shell0 + q) * a.n_theta + j0 + r] = add;
+    }
+  }
+}
+
+template <int S, bool STAGE>
+size_t theta_smem(const yy_grid *g) {
+  return ((size_t)3 * S + (STAGE ? 16 : 0)) * g->n_lm * sizeof(float);
+}
+
+__global__ void k_fill_ones(int n, float *__restrict__ dst) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) dst[e] = 1.0f;
+}
+
+// rows k of the trig table: dst[k][t] = src[t][k]
+__global__ void k_transpose_trig(int nt, int n_phi, const double *__restrict__ src, double *__restrict__ dst) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nt * n_phi) return;
+  const int k = e / nt, t = e - k * nt;
+  dst[e] = src[(size_t)t * n_phi + k];
+}
+
 // A[row][col] = (sum_z part[z][row][col]) row_scale col_scale + mean[row] colsum[col]
 // (the tensor cores saw rho - mean); column 0 is the float64 monopole.
 __global__ void k_reduce_partials(int M, int N, int S, const float *__restrict__ part,
@@ -1061,6 +1337,14 @@ struct yy_tc_tables {
   double *sy_qs[3], *sy_tabs[3];          // scales (float64 copies)
   float *sy_qsf[3], *sy_tabsf[3], *sy_add[3];
   yy::PairMaps sy_maps;                   // a: tables, b: coefficient sets
+  // separable synthesis: G rows (shell, j) per field as operand A, the
+  // cell-centre trig table (rows phi_k, slots t) as operand B, both as
+  // three bf16 pieces whatever the requested form
+  int sp_ok, sp_kpad, sp_rows, sp_rows_pad, sp_bn, sp_row_tiles, sp_b_rows_pad, sp_stages;
+  void *sp_G[4], *sp_trig;
+  float *sp_ones, *sp_ga[4], *sp_trigs_f;   // unit cell scales, slot-0 terms, trig row scales
+  double *sp_trigs;
+  yy::PairMaps sp_maps;                   // a[field]: G, b[0]: trig table
 };
 
 namespace yy {
@@ -1122,11 +1406,86 @@ static cudaError_t launch_pair(yy_grid *g, yy_tc_tables *t, const PairMaps &maps
   const int tiles = a.cell_tiles * a.row_tiles * a.k_splits * a.n_jobs;
   const int pairs = tiles < t->pair_slots ? tiles : t->pair_slots;
   cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = pair_config(pairs, a.stages * pair_stage_bytes<F>(a.bn) + kSmemFixed, s, attr);
-  const cudaError_t e = a.out_mode == 1 ? cudaLaunchKernelEx(&cfg, k_tc_pair<F, 1>, maps, a)
-                                         : cudaLaunchKernelEx(&cfg, k_tc_pair<F, 0>, maps, a);
+  const int smem = a.stages * pair_stage_bytes<F>(a.bn) + kSmemFixed + (a.out_mode == 2 ? kEpiStageBytes : 0);
+  cudaLaunchConfig_t cfg = pair_config(pairs, smem, s, attr);
+  const cudaError_t e = a.out_mode == 2   ? cudaLaunchKernelEx(&cfg, k_tc_pair<F, 2>, maps, a)
+                        : a.out_mode == 1 ? cudaLaunchKernelEx(&cfg, k_tc_pair<F, 1>, maps, a)
+                                          : cudaLaunchKernelEx(&cfg, k_tc_pair<F, 0>, maps, a);
   g->launches++;
   return e;
+}
+
+// Tables of the separable synthesis (out_mode 2): the trig table packed as
+// operand B in three bf16 pieces (slot 0 left out: it is 1 at every phi_k and
+// goes in per cell), unit cell scales, and the G operands of the four fields
+// (rows past the last (shell, j) stay zero).  The azimuthal contraction is
+// K = 2 l_max + 1 long, so its six products cost next to nothing whatever
+// the requested form.
+static yy_status prepare_separable_synthesis(yy_grid *g, yy_tc_tables *t) {
+  typedef FormBF16x3 F;
+  const int nt = 2 * g->lmax + 1;
+  t->sp_kpad = round_up(nt, kPadK);
+  t->sp_rows = grid_rows(g) * g->n_theta;
+  t->sp_rows_pad = round_up(t->sp_rows, 2 * kPairRows);
+  t->sp_row_tiles = (g->n_phi + 255) / 256;
+  t->sp_bn = round_up((g->n_phi + t->sp_row_tiles - 1) / t->sp_row_tiles, 16);
+  t->sp_b_rows_pad = t->sp_row_tiles * t->sp_bn;
+  t->sp_stages = pair_stages<F>(t->sp_bn, kEpiStageBytes);
+  if (t->sp_stages < 2) return YY_OK;   // not available: the dense synthesis stays
+  // the polar stage keeps S shells' coefficients in shared memory
+  if (cudaFuncSetAttribute(k_tc_pair<F, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) != cudaSuccess ||
+      cudaFuncSetAttribute(k_theta_g<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kThetaSmemMax) != cudaSuccess ||
+      cudaFuncSetAttribute(k_theta_g<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kThetaSmemMax) != cudaSuccess ||
+      cudaFuncSetAttribute(k_theta_g<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kThetaSmemMax) != cudaSuccess)
+    return YY_ERR_NOT_SUPPORTED;
+  if (theta_smem<2, false>(g) > (size_t)kThetaSmemMax) return YY_OK;
+  const size_t g_bytes = (size_t)F::kPA * t->sp_rows_pad * t->sp_kpad * F::kElem;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void **ptr, size_t bytes) {
+    if (e == cudaSuccess) e = dmalloc(ptr, bytes);
+  };
+  for (int f = 0; f < 4; ++f) {
+    A(&t->sp_G[f], g_bytes);
+    A((void **)&t->sp_ga[f], t->sp_rows_pad * sizeof(float));
+  }
+  A((void **)&t->sp_ones, t->sp_rows_pad * sizeof(float));
+  A(&t->sp_trig, (size_t)F::kPB * t->sp_b_rows_pad * t->sp_kpad * F::kElem);
+  A((void **)&t->sp_trigs, t->sp_b_rows_pad * sizeof(double));
+  A((void **)&t->sp_trigs_f, t->sp_b_rows_pad * sizeof(float));
+  double *trig_rows = nullptr;
+  A((void **)&trig_rows, (size_t)g->n_phi * nt * sizeof(double));
+  if (e != cudaSuccess) {
+    if (trig_rows) cudaFree(trig_rows);
+    return e == cudaErrorMemoryAllocation ? YY_ERR_OOM : YY_ERR_CUDA;
+  }
+  for (int f = 0; f < 4 && e == cudaSuccess; ++f) e = cudaMemset(t->sp_G[f], 0, g_bytes);
+  k_fill_ones<<<(t->sp_rows_pad + 255) / 256, 256>>>(t->sp_rows_pad, t->sp_ones);
+  k_transpose_trig<<<(nt * g->n_phi + 255) / 256, 256>>>(nt, g->n_phi, g->sep_tr, trig_rows);
+  PackBatch b = {};
+  PackArgs &p = b.job[0];
+  p.rows = g->n_phi;
+  p.rows_pad = t->sp_b_rows_pad;
+  p.K = nt;
+  p.k_pad = t->sp_kpad;
+  p.src0 = p.src1 = trig_rows;
+  p.split_row = g->n_phi;
+  p.ld = nt;
+  p.zero_k0 = 0;
+  p.zero_k1 = -1;
+  p.zero_row = -1;
+  p.scale_out = t->sp_trigs;
+  p.scale_out_f = t->sp_trigs_f;
+  p.out = t->sp_trig;
+  if (e == cudaSuccess) e = launch_pack<F>(b, 1, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(trig_rows);
+  if (e != cudaSuccess) return YY_ERR_CUDA;
+  bool ok = make_map<F>(&t->sp_maps.b[0], t->sp_trig, t->sp_kpad, F::kPB * t->sp_b_rows_pad, t->sp_bn / 2);
+  for (int f = 0; f < 4 && ok; ++f)
+    ok = make_map<F>(&t->sp_maps.a[f], t->sp_G[f], t->sp_kpad, F::kPA * t->sp_rows_pad, kPairRows);
+  if (!ok) return YY_ERR_NOT_SUPPORTED;
+  t->sp_ok = 1;
+  return YY_OK;
 }
 
 template <class F>
@@ -1234,7 +1593,7 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
     ok = make_map<F>(&t->sy_maps.a[c], t->sy_tab[c], t->sy_kpad, F::kPA * t->sy_cells_pad, kPairRows) &&
          make_map<F>(&t->sy_maps.b[c], t->sy_q[c], t->sy_kpad, F::kPB * t->rows_pad, bh);
   if (!ok) return YY_ERR_NOT_SUPPORTED;
-  return YY_OK;
+  return prepare_separable_synthesis(g, t);
 }
 
 static void free_tables(yy_tc_tables *t) {
@@ -1248,6 +1607,14 @@ static void free_tables(yy_tc_tables *t) {
     for (void *p : q)
       if (p) cudaFree(p);
   }
+  for (int f = 0; f < 4; ++f) {
+    void *q[] = {t->sp_G[f], t->sp_ga[f]};
+    for (void *p : q)
+      if (p) cudaFree(p);
+  }
+  void *sp[] = {t->sp_trig, t->sp_trigs_f, t->sp_trigs, t->sp_ones};
+  for (void *p : sp)
+    if (p) cudaFree(p);
   delete t;
 }
 
@@ -1414,6 +1781,87 @@ cudaError_t tc_analysis(yy_grid *g, yy_precision prec, const double *ry, const d
     case YY_TF32: return analysis_form<FormTF32>(g, t, ry, rg, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+static cudaError_t theta_form(yy_grid *g, yy_tc_tables *t, bool grad, cudaStream_t s) {
+  ThetaArgs a = {};
+  a.n_shells = grid_rows(g);
+  a.n_theta = g->n_theta;
+  a.lmax = g->lmax;
+  a.n_lm = g->n_lm;
+  a.nt = 2 * g->lmax + 1;
+  a.k_pad = t->sp_kpad;
+  a.n_jobs = grad ? 4 : 1;
+  a.rows_pad = t->sp_rows_pad;
+  a.Q = g->Q;
+  a.tab[0] = g->sep_P32;
+  a.tab[1] = g->sep_dP32;
+  a.tab[2] = g->sep_Qs32;
+  a.tab64[0] = g->sep_P;
+  a.tab64[1] = g->sep_dP;
+  for (int f = 0; f < 4; ++f) {
+    a.G[f] = t->sp_G[f];
+    a.add[f] = t->sp_ga[f];
+  }
+  // four shells per block and the table rows staged while they fit in shared memory
+  if (theta_smem<4, true>(g) <= (size_t)kThetaSmemMax)
+    k_theta_g<4, true><<<(a.n_shells + 3) / 4, 256, theta_smem<4, true>(g), s>>>(a);
+  else if (theta_smem<2, true>(g) <= (size_t)kThetaSmemMax)
+    k_theta_g<2, true><<<(a.n_shells + 1) / 2, 256, theta_smem<2, true>(g), s>>>(a);
+  else
+    k_theta_g<2, false><<<(a.n_shells + 1) / 2, 256, theta_smem<2, false>(g), s>>>(a);
+  g->launches++;
+  return cudaGetLastError();
+}
+
+static cudaError_t sep_synthesis_form(yy_grid *g, yy_tc_tables *t, double *py, double *pg, double *gy, double *gg,
+                                      cudaStream_t s) {
+  typedef FormBF16x3 F;
+  const size_t comp = (size_t)g->n_r * g->n_ang;
+  double *o0[4] = {py, gy, gy ? gy + comp : nullptr, gy ? gy + 2 * comp : nullptr};
+  double *o1[4] = {pg, gg, gg ? gg + comp : nullptr, gg ? gg + 2 * comp : nullptr};
+  PairArgs a = {};
+  a.stages = t->sp_stages;
+  a.cells = t->sp_rows;
+  a.cell_tiles = t->sp_rows_pad / (2 * kPairRows);
+  a.rows = g->n_phi;
+  a.row_tiles = t->sp_row_tiles;
+  a.bn = t->sp_bn;
+  a.kb_total = t->sp_kpad * F::kElem / kRowBytes;
+  a.k_splits = 1;
+  a.kb_per_split = a.kb_total;
+  a.a_rows = t->sp_rows_pad;
+  a.b_rows = t->sp_b_rows_pad;
+  a.out_mode = 2;
+  a.out_split = g->n_r * g->n_theta;
+  a.ldo = g->n_phi;
+  a.n_jobs = gy ? 4 : 1;
+  a.err = g->err;
+  for (int f = 0; f < a.n_jobs; ++f) {
+    PairJob &J = a.job[f];
+    J.out0 = o0[f];
+    J.out1 = o1[f];
+    J.cell_scale = t->sp_ones;
+    J.cell_add = t->sp_ga[f];
+    J.row_scale = t->sp_trigs_f;
+    J.ta = f;
+    J.tb = 0;
+  }
+  return launch_pair<F>(g, t, t->sp_maps, a, s);
+}
+
+bool tc_separable_synthesis_ready(const yy_grid *g, yy_precision prec) {
+  const yy_tc_tables *t = ((int)prec >= 0 && (int)prec < 5) ? g->tc[prec] : nullptr;
+  return t && t->sp_ok;
+}
+
+cudaError_t tc_theta(yy_grid *g, yy_precision prec, bool grad, cudaStream_t s) {
+  return theta_form(g, g->tc[prec], grad, s);
+}
+
+cudaError_t tc_separable_synthesis(yy_grid *g, yy_precision prec, double *py, double *pg, double *gy, double *gg,
+                                   cudaStream_t s) {
+  return sep_synthesis_form(g, g->tc[prec], py, pg, gy, gg, s);
 }
 
 cudaError_t tc_pack_coefficients(yy_grid *g, yy_precision prec, cudaStream_t s) {

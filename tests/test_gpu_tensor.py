@@ -37,7 +37,7 @@ def _grid(yy, spec):
     return _GRIDS[spec.name]
 
 
-@pytest.mark.parametrize("analysis", ["separable", "dense"])
+@pytest.mark.parametrize("analysis", ["auto", "separable", "dense"])
 @pytest.mark.parametrize("prec", ["fp16x2", "bf16x3", "tf32"])
 @pytest.mark.parametrize("name", ["tiny", "mid"])
 def test_tensor_form_matches_oracle(yy, oracle_grid, prec, name, analysis):
@@ -60,7 +60,7 @@ def test_tensor_form_matches_oracle(yy, oracle_grid, prec, name, analysis):
         assert rel_max(out["grad_" + q], ref["grad_" + q]) <= tol_g, (q, prec)
 
 
-@pytest.mark.parametrize("analysis", ["separable", "dense"])
+@pytest.mark.parametrize("analysis", ["auto", "separable", "dense"])
 @pytest.mark.parametrize("prec", ["fp16x2", "bf16x3"])
 def test_tensor_form_production_sampled(yy, oracle_grid, prec, analysis):
     spec = inputs.production_grid()
