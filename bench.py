@@ -39,8 +39,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # 152 SMs x 2 DFMA/clk x 2 f
 # DRAM bytes (read + write) of one synthesis launch, from an ncu capture of
 # this workload (profiles/k_tc_pair_fp16x2_production.md); valid only for the
 # kernel source it was taken with, null otherwise.
-_TRAFFIC = {("fp16x2", True): (287.467008e6 + 798.509312e6,
-                               "68b51d16915b46b142e744dc928059e2e6d097aba55c071e53ded34bd84b0274")}
+_TRAFFIC = {("fp16x2", True): (287.090944e6 + 798.199296e6,
+                               "30018162ea21bfec951e977625c19a2cbb66784fbeee2881ed4a45d54b5fe468")}
 
 
 def _recorded_traffic(prec, gradient):
