@@ -204,6 +204,24 @@ yy_status yy_potential_host(yy_grid *g, const double *rho_yin, const double *rho
                             double *grad_yin, double *grad_yang,
                             yy_precision prec, void *cuda_stream);
 
+/* Pipelined form of yy_potential_host for a stream of solves: enqueues the
+ * copy in, the solve (on cuda_stream) and the copy out, and returns without
+ * waiting.  Two staging sets alternate between calls, and the copies run on
+ * the handle's own streams, so the copy out of one call overlaps the copy in
+ * and the solve of the next (host-device copies run at about 200 GB/s in each
+ * direction on this machine; a solve with the gradient moves 1.07 GB).  The
+ * host buffers of a call must stay valid and untouched until the results are
+ * in: after yy_potential_host_wait, or two calls later for its input.  Use one
+ * cuda_stream for all calls on a handle.  Errors as for yy_potential_host. */
+yy_status yy_potential_host_async(yy_grid *g, const double *rho_yin, const double *rho_yang,
+                                  double *phi_yin, double *phi_yang,
+                                  double *grad_yin, double *grad_yang,
+                                  yy_precision prec, void *cuda_stream);
+
+/* Wait until every yy_potential_host_async call on the handle has delivered
+ * its results to host memory. */
+yy_status yy_potential_host_wait(yy_grid *g);
+
 /* Copy a table or intermediate (see yy_table) into host memory; `count` is
  * the number of float64 values the caller's buffer holds and must equal the
  * table's size (query it with host_dst = NULL: *count receives the size).

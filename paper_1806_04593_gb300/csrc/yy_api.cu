@@ -72,6 +72,16 @@ static void free_all(yy_grid *g) {
   for (float *p : fbufs)
     if (p) cudaFree(p);
   if (g->err) cudaFree(g->err);
+  for (int k = 0; k < 2; ++k) {
+    double *pb[] = {g->pipe_rho[k], g->pipe_phi[k], g->pipe_grad[k]};
+    for (double *p : pb)
+      if (p) cudaFree(p);
+    if (g->pipe_ev_in[k]) cudaEventDestroy(g->pipe_ev_in[k]);
+    if (g->pipe_ev_done[k]) cudaEventDestroy(g->pipe_ev_done[k]);
+    if (g->pipe_ev_out[k]) cudaEventDestroy(g->pipe_ev_out[k]);
+  }
+  if (g->pipe_in) cudaStreamDestroy(g->pipe_in);
+  if (g->pipe_out) cudaStreamDestroy(g->pipe_out);
   tc_free(g);
 }
 
@@ -339,6 +349,72 @@ yy_status yy_potential_host(yy_grid *g, const double *rho_yin, const double *rho
   if (e == cudaSuccess && grad_yin) e = cudaMemcpyAsync(grad_yin, gy, 3 * bytes, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && gg) e = cudaMemcpyAsync(grad_yang, gg, 3 * bytes, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return from_cuda(e);
+}
+
+// Pipelined host-buffer solve.  Staging set k alternates between calls; the
+// copy in (stream pipe_in) waits until the last solve that read set k is
+// done, the solve (cuda_stream) waits for its copy in and for the last copy
+// out of set k, and the copy out (stream pipe_out) waits for the solve.  So
+// the copy out of one call runs beside the copy in and the solve of the next.
+yy_status yy_potential_host_async(yy_grid *g, const double *rho_yin, const double *rho_yang, double *phi_yin,
+                                  double *phi_yang, double *grad_yin, double *grad_yang, yy_precision prec,
+                                  void *cuda_stream) {
+  if (!g || !rho_yin || !phi_yin) return YY_ERR_INVALID_ARG;
+  const bool two = g->n_patch == 2;
+  if (two ? (!rho_yang || !phi_yang || (grad_yin == nullptr) != (grad_yang == nullptr))
+          : (rho_yang || phi_yang || grad_yang))
+    return YY_ERR_INVALID_ARG;
+  const size_t field = (size_t)g->n_r * g->n_ang, np = (size_t)g->n_patch;
+  cudaError_t e = cudaSuccess;
+  if (!g->pipe_in) e = cudaStreamCreateWithFlags(&g->pipe_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !g->pipe_out) e = cudaStreamCreateWithFlags(&g->pipe_out, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    if (!g->pipe_ev_in[k]) e = cudaEventCreateWithFlags(&g->pipe_ev_in[k], cudaEventDisableTiming);
+    if (e == cudaSuccess && !g->pipe_ev_done[k]) e = cudaEventCreateWithFlags(&g->pipe_ev_done[k], cudaEventDisableTiming);
+    if (e == cudaSuccess && !g->pipe_ev_out[k]) e = cudaEventCreateWithFlags(&g->pipe_ev_out[k], cudaEventDisableTiming);
+  }
+  const int k = g->pipe_next;
+  if (e == cudaSuccess && !g->pipe_rho[k]) e = dmalloc((void **)&g->pipe_rho[k], np * field * sizeof(double));
+  if (e == cudaSuccess && !g->pipe_phi[k]) e = dmalloc((void **)&g->pipe_phi[k], np * field * sizeof(double));
+  if (e == cudaSuccess && grad_yin && !g->pipe_grad[k])
+    e = dmalloc((void **)&g->pipe_grad[k], 3 * np * field * sizeof(double));
+  if (e != cudaSuccess) return from_cuda(e);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const size_t bytes = field * sizeof(double);
+  double *rho = g->pipe_rho[k], *phi = g->pipe_phi[k], *grad = grad_yin ? g->pipe_grad[k] : nullptr;
+  // copy in, once the last solve on this set has read it
+  if (g->pipe_used[k]) e = cudaStreamWaitEvent(g->pipe_in, g->pipe_ev_done[k], 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rho, rho_yin, bytes, cudaMemcpyHostToDevice, g->pipe_in);
+  if (e == cudaSuccess && two) e = cudaMemcpyAsync(rho + field, rho_yang, bytes, cudaMemcpyHostToDevice, g->pipe_in);
+  if (e == cudaSuccess) e = cudaEventRecord(g->pipe_ev_in[k], g->pipe_in);
+  // solve, once the data is in and the last copy out of this set has finished
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, g->pipe_ev_in[k], 0);
+  if (e == cudaSuccess && g->pipe_used[k]) e = cudaStreamWaitEvent(s, g->pipe_ev_out[k], 0);
+  if (e != cudaSuccess) return from_cuda(e);
+  yy_status st = yy_potential(g, rho, two ? rho + field : nullptr, phi, two ? phi + field : nullptr, grad,
+                              (grad && two) ? grad + 3 * field : nullptr, prec, cuda_stream);
+  if (st != YY_OK) return st;
+  e = cudaEventRecord(g->pipe_ev_done[k], s);
+  // copy out
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(g->pipe_out, g->pipe_ev_done[k], 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(phi_yin, phi, bytes, cudaMemcpyDeviceToHost, g->pipe_out);
+  if (e == cudaSuccess && two) e = cudaMemcpyAsync(phi_yang, phi + field, bytes, cudaMemcpyDeviceToHost, g->pipe_out);
+  if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad_yin, grad, 3 * bytes, cudaMemcpyDeviceToHost, g->pipe_out);
+  if (e == cudaSuccess && grad && two)
+    e = cudaMemcpyAsync(grad_yang, grad + 3 * field, 3 * bytes, cudaMemcpyDeviceToHost, g->pipe_out);
+  if (e == cudaSuccess) e = cudaEventRecord(g->pipe_ev_out[k], g->pipe_out);
+  if (e != cudaSuccess) return from_cuda(e);
+  g->pipe_used[k] = 1;
+  g->pipe_next = k ^ 1;
+  return YY_OK;
+}
+
+yy_status yy_potential_host_wait(yy_grid *g) {
+  if (!g) return YY_ERR_INVALID_ARG;
+  cudaError_t e = cudaSuccess;
+  if (g->pipe_out) e = cudaStreamSynchronize(g->pipe_out);
+  if (e == cudaSuccess && g->pipe_in) e = cudaStreamSynchronize(g->pipe_in);
   return from_cuda(e);
 }
 

@@ -86,6 +86,12 @@ struct yy_grid {
 
   // host-buffer staging (yy_potential_host)
   double *stage_rho, *stage_phi, *stage_grad;
+  // pipelined host-buffer solves (yy_potential_host_async): two staging sets,
+  // copies in and out on their own streams, ordered by events
+  double *pipe_rho[2], *pipe_phi[2], *pipe_grad[2];
+  cudaStream_t pipe_in, pipe_out;
+  cudaEvent_t pipe_ev_in[2], pipe_ev_done[2], pipe_ev_out[2];
+  int pipe_used[2], pipe_next;
 };
 
 namespace yy {

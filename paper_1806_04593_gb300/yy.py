@@ -79,6 +79,10 @@ def load():
     lib.yy_potential.restype = I
     lib.yy_potential_host.argtypes = [P, P, P, P, P, P, P, I, P]
     lib.yy_potential_host.restype = I
+    lib.yy_potential_host_async.argtypes = [P, P, P, P, P, P, P, I, P]
+    lib.yy_potential_host_async.restype = I
+    lib.yy_potential_host_wait.argtypes = [P]
+    lib.yy_potential_host_wait.restype = I
     lib.yy_grid_copy_table.argtypes = [P, I, P, ctypes.POINTER(ctypes.c_size_t)]
     lib.yy_grid_copy_table.restype = I
     lib.yy_last_device_status.argtypes = [P]
@@ -183,6 +187,17 @@ def yy_potential_host(handle, rho_yin, rho_yang, phi_yin, phi_yang, grad_yin=Non
     return load().yy_potential_host(handle, _ptr(rho_yin), _ptr(rho_yang), _ptr(phi_yin),
                                     _ptr(phi_yang), _ptr(grad_yin), _ptr(grad_yang), int(prec),
                                     _stream(stream))
+
+
+def yy_potential_host_async(handle, rho_yin, rho_yang, phi_yin, phi_yang, grad_yin=None, grad_yang=None,
+                            prec=YY_FP64, stream=None):
+    return load().yy_potential_host_async(handle, _ptr(rho_yin), _ptr(rho_yang), _ptr(phi_yin),
+                                          _ptr(phi_yang), _ptr(grad_yin), _ptr(grad_yang), int(prec),
+                                          _stream(stream))
+
+
+def yy_potential_host_wait(handle):
+    return load().yy_potential_host_wait(handle)
 
 
 def yy_grid_copy_table(handle, which):

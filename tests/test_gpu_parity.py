@@ -291,6 +291,36 @@ def test_host_entry_point_matches_device_path(yy):
     assert np.array_equal(h["gg"].numpy(), dev["grad_yang"])
 
 
+def test_pipelined_host_calls_match_device_path(yy):
+    """yy_potential_host_async: five calls in a row with different densities
+    and their own host buffers (the staging sets alternate and the copies
+    overlap); after yy_potential_host_wait each result equals the device
+    path bitwise, in float64 and in FP16X2."""
+    import torch
+    spec = inputs.mid_grid()
+    g = _grid(yy, spec)
+    g.prepare("fp16x2")
+    ry, rg = inputs.density_for(spec)
+    shape = (spec.n_r, spec.n_theta, spec.n_phi)
+    stream = torch.cuda.current_stream()
+    for prec in ("fp64", "fp16x2"):
+        calls = []
+        for i in range(5):
+            f = 1.0 + 0.25 * i
+            rin = [torch.from_numpy(np.ascontiguousarray(a * f)).pin_memory() for a in (ry, rg)]
+            out = [torch.empty(shape, dtype=torch.float64).pin_memory() for _ in range(2)] + \
+                  [torch.empty((3,) + shape, dtype=torch.float64).pin_memory() for _ in range(2)]
+            st = yy.yy_potential_host_async(g.handle, rin[0], rin[1], out[0], out[1], out[2], out[3],
+                                            yy.PRECISIONS[prec], stream)
+            assert st == yy.YY_OK
+            calls.append((f, rin, out))
+        assert yy.yy_potential_host_wait(g.handle) == yy.YY_OK
+        for f, rin, out in calls:
+            ref = gpu_solve(g, ry * f, rg * f, gradient=True, prec=prec)
+            for key, o in zip(("phi_yin", "phi_yang", "grad_yin", "grad_yang"), out):
+                assert np.array_equal(o.numpy(), ref[key]), (prec, f, key)
+
+
 def test_error_paths(yy):
     import torch
     spec = inputs.tiny_grid()
