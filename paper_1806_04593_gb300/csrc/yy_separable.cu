@@ -334,7 +334,11 @@ cudaError_t run_separable(yy_grid *g, const double *rho_yin, const double *rho_y
 //                (g_phi: the cos slot takes the sin coefficients and the sin
 //                slot minus the cos ones, from d/dphi of cos / sin (m phi))
 //   phi stage    out[j][k] = sum_t G[j][t] tr[t][k]
-// with q the combined coefficients of the field (Q, Q_r, Q_t, Q_t).
+// with q the combined coefficients of the field (Q, Q_r, Q_t, Q_t).  Both
+// sums run from the top down (l from l_max, t from 2 l_max): the monopole
+// (l = 0, t = 0) dominates Phi and g_r, and adding it last leaves one
+// rounding of the large value instead of one per small term (fp32: Phi
+// error about 1e-6 -> a few 1e-7).
 struct SepOut {
   double *o[4][2];     // field, patch
 };
@@ -374,10 +378,10 @@ __global__ void k_sep_synth(int n_shells, int n_r, int n_theta, int n_phi, int l
           const T *tj = tab + (size_t)(j0 + jj) * n_lm;
           T g = T(0);
           if (f < 3) {
-            for (int l = m; l <= lmax; ++l) g = fma(qs[l * l + t], tj[l * l + t], g);
+            for (int l = lmax; l >= m; --l) g = fma(qs[l * l + t], tj[l * l + t], g);
           } else if (t > 0) {
             const int src = (t & 1) ? t + 1 : t - 1;      // cos slot <- sin coefficient, sin slot <- cos
-            for (int l = m; l <= lmax; ++l) g = fma(qs[l * l + src], tj[l * l + t], g);
+            for (int l = lmax; l >= m; --l) g = fma(qs[l * l + src], tj[l * l + t], g);
             if (!(t & 1)) g = -g;
           }
           Gs[jj * ntp + t] = g;
@@ -388,7 +392,7 @@ __global__ void k_sep_synth(int n_shells, int n_r, int n_theta, int n_phi, int l
           const int j = j0 + jj;
           T acc[4] = {T(0), T(0), T(0), T(0)};
           const T *gj = Gs + jj * ntp;
-          for (int t = 0; t < nt; ++t) {
+          for (int t = nt - 1; t >= 0; --t) {
             T a4[4];
             ld4(trs + (size_t)t * ntr + k0, a4);
             const T gv = gj[t];
