@@ -503,6 +503,20 @@ def run_batched(args, prec, gradient, dev, stream, flush):
 
     ms = timed(prec, args.batch_steps, max(3, args.warmup))
     launches = b.launch_count()
+    splits = [b.analysis_splits(i, prec) for i in range(len(specs))]
+    # each field solved alone on its own grid (tuned settings), back to back
+    solo_ms = 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i, (sp, (ry, rg), o) in enumerate(zip(specs, rho, outs)):
+        h = b.grid_handle(i)
+        args_i = (h, ry, rg, o[0], o[1], o[2] if gradient else None, o[3] if gradient else None,
+                  yy.PRECISIONS[prec], stream)
+        yy.yy_potential(*args_i)
+        e0.record(stream)
+        yy.yy_potential(*args_i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        solo_ms += e0.elapsed_time(e1)
     phi = [(o[0].clone(), o[1].clone()) for o in outs]
     b.prepare("fp64")
     ms64 = timed("fp64", 2, 1)
@@ -520,6 +534,9 @@ def run_batched(args, prec, gradient, dev, stream, flush):
         "analysis_chosen": {"dense": chosen.count(yy.YY_ANALYSIS_DENSE),
                             "separable": chosen.count(yy.YY_ANALYSIS_SEPARABLE)},
         "tune_s": tune_s, "graph_launches_per_step": 1, "kernels_per_step": launches,
+        "graph_branches": b.branches(),
+        "analysis_splits_chosen": {str(v): splits.count(v) for v in sorted(set(splits))},
+        "sum_of_solo_solves_ms": solo_ms,
         "fp64_gpu_path": {"value": len(specs) * 1e3 / ms64, "unit": "field solves/s", "ms_per_step": ms64},
         "speedup_vs_fp64": ms64 / ms,
         "phi_rel_max_vs_fp64_worst_field": err,

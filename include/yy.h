@@ -312,10 +312,14 @@ yy_status yy_batch_prepare(yy_batch *b, yy_precision prec);
 /* Autotuner: for every field, time each evaluation (YY_ANALYSIS_DENSE,
  * YY_ANALYSIS_SEPARABLE; reps solves each on zero densities in scratch
  * buffers it allocates and frees) in the given form, with or without the
- * gradient, and record the faster for that form: later graphs of that form
- * use it (other forms keep theirs; untuned forms use YY_ANALYSIS_AUTO).
- * chosen (NULL or n_fields entries) receives the yy_analysis picked per
- * field.  Prepares the form; synchronises. */
+ * gradient, together with the K split of the dense tensor-core analysis
+ * (the rule's count times 1/2, 1, 2 and 4, within the partial buffer), and
+ * record the fastest for that form: later graphs of that form use it (other
+ * forms keep theirs; untuned forms use YY_ANALYSIS_AUTO and the rule).  The
+ * first yy_batch_potential after tuning also times its graph with 1, 2, 4, 8
+ * and 16 parallel branches on the caller's buffers, keeps the fastest, and
+ * synchronises.  chosen (NULL or n_fields entries) receives the yy_analysis
+ * picked per field.  Prepares the form; synchronises. */
 yy_status yy_batch_tune(yy_batch *b, yy_precision prec, int with_gradient, int reps, int *chosen);
 
 /* Set one field's analysis evaluation by hand, for every form (see
@@ -339,6 +343,14 @@ yy_grid *yy_batch_grid(yy_batch *b, int field);
 
 /* Kernels in the last recorded graph (-1 for NULL). */
 int yy_batch_last_launch_count(const yy_batch *b);
+
+/* Parallel branches of the batch's graphs: 4, or the count the first capture
+ * after yy_batch_tune picked by timing 1, 2, 4, 8 and 16 (-1 for NULL). */
+int yy_batch_branches(const yy_batch *b);
+
+/* K split of the dense tensor-core analysis recorded for a field and form by
+ * yy_batch_tune (0: the rule's count; -1 for bad arguments). */
+int yy_batch_analysis_splits(const yy_batch *b, int field, yy_precision prec);
 
 /* The first non-OK device status over the fields (reads and clears each). */
 yy_status yy_batch_last_device_status(yy_batch *b);

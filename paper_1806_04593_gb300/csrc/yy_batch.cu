@@ -3,13 +3,17 @@
 //
 // Each field keeps its own grid handle (tables built once).  yy_batch_potential
 // records every field's solve into one graph by stream capture, the fields
-// spread over kBranches parallel branches (fork / join through events) so that
-// the short kernels of one field overlap the long ones of another, and then
+// spread over parallel branches (fork / join through events) so that the
+// short kernels of one field overlap the long ones of another, and then
 // replays the instantiated graph on the caller's stream.  Graphs are cached
 // per (precision, gradient, buffer pointers): a replay costs one launch.
-// yy_batch_tune is the autotuner: for every field it times both evaluations
-// (dense contractions, separable stages) on scratch buffers and records the
-// faster for that precision; the capture applies it.
+//
+// yy_batch_tune is the autotuner.  Per field it times both evaluations
+// (dense contractions, separable stages) and, for a dense tensor-core
+// analysis, the K split of the contraction (the rule's count times 1/2, 1, 2
+// and 4), on scratch buffers, and records the fastest for that precision.
+// The first capture after tuning also times the whole graph with 1, 2, 4, 8
+// and 16 branches on the caller's buffers and keeps the fastest.
 #include <string.h>
 
 #include <new>
@@ -19,7 +23,8 @@
 
 namespace {
 
-constexpr int kBranches = 4;
+constexpr int kBranchesMax = 16;
+constexpr int kBranchesDefault = 4;
 constexpr int kCacheSize = 4;
 constexpr int kPrecisions = YY_FP16X2 + 1;
 
@@ -36,9 +41,12 @@ struct yy_batch {
   int device;
   std::vector<yy_grid *> grids;
   std::vector<int> method;          // [field][precision]: analysis evaluation recorded for it
+  std::vector<int> splits;          // [field][precision]: K split of the dense analysis (0: the rule's)
+  int branches;                     // parallel branches of the graph
+  int tune_branches;                // time the branch counts at the next capture
   cudaStream_t cap;                 // capture origin
-  cudaStream_t branch[kBranches];
-  cudaEvent_t fork, join[kBranches];
+  cudaStream_t branch[kBranchesMax];
+  cudaEvent_t fork, join[kBranchesMax];
   std::vector<GraphEntry> cache;
   int launches;                     // kernels in the last captured graph
 };
@@ -51,6 +59,8 @@ yy_status to_status(cudaError_t e) {
   return YY_ERR_CUDA;
 }
 
+bool tensor_form(yy_precision p) { return p == YY_TF32 || p == YY_BF16X3 || p == YY_FP16X2; }
+
 void drop_cache(yy_batch *b) {
   for (GraphEntry &g : b->cache) cudaGraphExecDestroy(g.exec);
   b->cache.clear();
@@ -60,11 +70,82 @@ void free_batch(yy_batch *b) {
   drop_cache(b);
   for (yy_grid *g : b->grids) yy_destroy(g);
   if (b->cap) cudaStreamDestroy(b->cap);
-  for (int k = 0; k < kBranches; ++k) {
+  for (int k = 0; k < kBranchesMax; ++k) {
     if (b->branch[k]) cudaStreamDestroy(b->branch[k]);
     if (b->join[k]) cudaEventDestroy(b->join[k]);
   }
   if (b->fork) cudaEventDestroy(b->fork);
+}
+
+// the field's recorded evaluation and K split for this precision
+yy_status apply_field_setting(yy_batch *b, int i, yy_precision prec) {
+  yy_grid *g = b->grids[i];
+  yy_grid_set_analysis(g, (yy_analysis)b->method[(size_t)i * kPrecisions + prec]);
+  if (!tensor_form(prec)) return YY_OK;
+  int rule = 0;
+  if (yy::tc_analysis_splits(g, prec, &rule, nullptr) == 0) return YY_OK;   // not prepared: yy_potential reports it
+  const int s = b->splits[(size_t)i * kPrecisions + prec];
+  return yy::tc_set_analysis_splits(g, prec, s > 0 ? s : rule);
+}
+
+struct Buffers {
+  const double *const *rho_yin, *const *rho_yang;
+  double *const *phi_yin, *const *phi_yang, *const *grad_yin, *const *grad_yang;
+};
+
+// record every field's solve on `branches` parallel branches into a graph
+yy_status capture(yy_batch *b, const Buffers &io, yy_precision prec, int branches, cudaGraphExec_t *out,
+                  int *launches) {
+  const bool grad = io.grad_yin != nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return to_status(e);
+  yy_status st = YY_OK;
+  if ((e = cudaEventRecord(b->fork, b->cap)) != cudaSuccess) st = to_status(e);
+  for (int k = 0; k < branches && st == YY_OK; ++k)
+    if ((e = cudaStreamWaitEvent(b->branch[k], b->fork, 0)) != cudaSuccess) st = to_status(e);
+  int n_launch = 0;
+  for (int i = 0; i < b->n && st == YY_OK; ++i) {
+    yy_grid *g = b->grids[i];
+    st = apply_field_setting(b, i, prec);
+    if (st == YY_OK)
+      st = yy_potential(g, io.rho_yin[i], io.rho_yang[i], io.phi_yin[i], io.phi_yang[i],
+                        grad ? io.grad_yin[i] : nullptr, grad ? io.grad_yang[i] : nullptr, prec,
+                        b->branch[i % branches]);
+    n_launch += g->launches;
+  }
+  for (int k = 0; k < branches && st == YY_OK; ++k) {
+    if ((e = cudaEventRecord(b->join[k], b->branch[k])) == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join[k], 0);
+    if (e != cudaSuccess) st = to_status(e);
+  }
+  e = cudaStreamEndCapture(b->cap, &graph);
+  if (st == YY_OK && e != cudaSuccess) st = to_status(e);
+  if (st != YY_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return st;
+  }
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return to_status(e);
+  *launches = n_launch;
+  return YY_OK;
+}
+
+// time one graph replay on stream s (after one untimed replay)
+yy_status time_graph(cudaGraphExec_t exec, cudaStream_t s, float *ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return to_status(e);
 }
 
 }  // namespace
@@ -79,10 +160,12 @@ yy_status yy_batch_create(const yy_field_desc *fields, int n_fields, yy_batch **
   if (!b) return YY_ERR_OOM;
   b->n = n_fields;
   b->method.assign((size_t)n_fields * kPrecisions, (int)YY_ANALYSIS_AUTO);
+  b->splits.assign((size_t)n_fields * kPrecisions, 0);
+  b->branches = kBranchesDefault;
   cudaGetDevice(&b->device);
   yy_status st = YY_OK;
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-  for (int k = 0; k < kBranches && e == cudaSuccess; ++k) {
+  for (int k = 0; k < kBranchesMax && e == cudaSuccess; ++k) {
     e = cudaStreamCreateWithFlags(&b->branch[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
   }
@@ -134,7 +217,6 @@ yy_status yy_batch_tune(yy_batch *b, yy_precision prec, int with_gradient, int r
   cudaError_t ce = cudaEventCreate(&e0);
   if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
   if (ce != cudaSuccess) return to_status(ce);
-  const yy_analysis cands[2] = {YY_ANALYSIS_DENSE, YY_ANALYSIS_SEPARABLE};
   for (int i = 0; i < b->n && st == YY_OK; ++i) {
     yy_grid *g = b->grids[i];
     const size_t field = ((size_t)g->n_r * g->n_ang + 1) & ~(size_t)1;   // even: every part 16-byte aligned
@@ -146,11 +228,32 @@ yy_status yy_batch_tune(yy_batch *b, yy_precision prec, int with_gradient, int r
       break;
     }
     double *gy = with_gradient ? buf + 4 * field : nullptr, *gg = with_gradient ? buf + 7 * field : nullptr;
+    // candidates: (evaluation, K split of the dense tensor-core analysis; 0 = not applicable)
+    int rule = 0, cap = 0;
+    const bool tc = tensor_form(prec) && yy::tc_analysis_splits(g, prec, &rule, &cap) > 0;
+    struct Cand {
+      yy_analysis method;
+      int splits;
+    } cands[6];
+    int n_cand = 0;
+    cands[n_cand++] = {YY_ANALYSIS_SEPARABLE, 0};
+    if (tc) {
+      const int opts[4] = {rule / 2, rule, 2 * rule, 4 * rule};
+      for (int o : opts) {
+        bool dup = o < 1 || o > cap;
+        for (int q = 0; q < n_cand && !dup; ++q) dup = cands[q].splits == o;
+        if (!dup) cands[n_cand++] = {YY_ANALYSIS_DENSE, o};
+      }
+    } else {
+      cands[n_cand++] = {YY_ANALYSIS_DENSE, 0};
+    }
     float best = 1e30f;
     int pick = 0;
-    for (int c = 0; c < 2 && st == YY_OK; ++c) {
-      yy_grid_set_analysis(g, cands[c]);
-      st = yy_potential(g, buf, buf + field, buf + 2 * field, buf + 3 * field, gy, gg, prec, b->cap);   // warm-up
+    for (int c = 0; c < n_cand && st == YY_OK; ++c) {
+      yy_grid_set_analysis(g, cands[c].method);
+      if (tc) st = yy::tc_set_analysis_splits(g, prec, cands[c].splits > 0 ? cands[c].splits : rule);
+      if (st == YY_OK)   // warm-up
+        st = yy_potential(g, buf, buf + field, buf + 2 * field, buf + 3 * field, gy, gg, prec, b->cap);
       if (st != YY_OK) break;
       cudaEventRecord(e0, b->cap);
       for (int r = 0; r < reps && st == YY_OK; ++r)
@@ -167,12 +270,15 @@ yy_status yy_batch_tune(yy_batch *b, yy_precision prec, int with_gradient, int r
     }
     cudaFree(buf);
     yy_grid_set_analysis(g, YY_ANALYSIS_AUTO);
-    b->method[(size_t)i * kPrecisions + prec] = (int)cands[pick];
-    if (chosen) chosen[i] = (int)cands[pick];
+    if (tc) yy::tc_set_analysis_splits(g, prec, rule);
+    b->method[(size_t)i * kPrecisions + prec] = (int)cands[pick].method;
+    b->splits[(size_t)i * kPrecisions + prec] = cands[pick].splits;
+    if (chosen) chosen[i] = (int)cands[pick].method;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   drop_cache(b);
+  if (st == YY_OK) b->tune_branches = 1;
   return st;
 }
 
@@ -204,36 +310,39 @@ yy_status yy_batch_potential(yy_batch *b, const double *const *rho_yin, const do
   for (yy_grid *g : b->grids) {
     if (g->profiling) yy_grid_set_profiling(g, 0);
   }
-  cudaGraph_t graph = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return to_status(e);
-  yy_status st = YY_OK;
-  if ((e = cudaEventRecord(b->fork, b->cap)) != cudaSuccess) st = to_status(e);
-  for (int k = 0; k < kBranches && st == YY_OK; ++k)
-    if ((e = cudaStreamWaitEvent(b->branch[k], b->fork, 0)) != cudaSuccess) st = to_status(e);
-  int launches = 0;
-  for (int i = 0; i < b->n && st == YY_OK; ++i) {
-    yy_grid *g = b->grids[i];
-    yy_grid_set_analysis(g, (yy_analysis)b->method[(size_t)i * kPrecisions + prec]);
-    st = yy_potential(g, rho_yin[i], rho_yang[i], phi_yin[i], phi_yang[i], grad ? grad_yin[i] : nullptr,
-                      grad ? grad_yang[i] : nullptr, prec, b->branch[i % kBranches]);
-    launches += g->launches;
-  }
-  for (int k = 0; k < kBranches && st == YY_OK; ++k) {
-    if ((e = cudaEventRecord(b->join[k], b->branch[k])) == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join[k], 0);
-    if (e != cudaSuccess) st = to_status(e);
-  }
-  e = cudaStreamEndCapture(b->cap, &graph);
-  if (st == YY_OK && e != cudaSuccess) st = to_status(e);
-  if (st != YY_OK) {
-    if (graph) cudaGraphDestroy(graph);
-    cudaGetLastError();
-    return st;
-  }
+  const Buffers io = {rho_yin, rho_yang, phi_yin, phi_yang, grad_yin, grad_yang};
   cudaGraphExec_t exec = nullptr;
-  e = cudaGraphInstantiate(&exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return to_status(e);
+  int launches = 0;
+  yy_status st = YY_OK;
+  if (b->tune_branches) {
+    // time the graph with each branch count on these buffers (every trial
+    // leaves the same results in them) and keep the fastest
+    float best = 1e30f;
+    for (int nb = 1; nb <= kBranchesMax && st == YY_OK; nb *= 2) {
+      cudaGraphExec_t trial = nullptr;
+      int n_launch = 0;
+      float ms = 0.0f;
+      st = capture(b, io, prec, nb, &trial, &n_launch);
+      if (st == YY_OK) st = time_graph(trial, s, &ms);
+      if (st == YY_OK && ms < best) {
+        best = ms;
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = trial;
+        launches = n_launch;
+        b->branches = nb;
+      } else if (trial) {
+        cudaGraphExecDestroy(trial);
+      }
+    }
+    if (st != YY_OK) {
+      if (exec) cudaGraphExecDestroy(exec);
+      return st;
+    }
+    b->tune_branches = 0;
+  } else {
+    st = capture(b, io, prec, b->branches, &exec, &launches);
+    if (st != YY_OK) return st;
+  }
   if ((int)b->cache.size() >= kCacheSize) {
     cudaGraphExecDestroy(b->cache.front().exec);
     b->cache.erase(b->cache.begin());
@@ -244,6 +353,13 @@ yy_status yy_batch_potential(yy_batch *b, const double *const *rho_yin, const do
 }
 
 int yy_batch_last_launch_count(const yy_batch *b) { return b ? b->launches : -1; }
+
+int yy_batch_branches(const yy_batch *b) { return b ? b->branches : -1; }
+
+int yy_batch_analysis_splits(const yy_batch *b, int field, yy_precision prec) {
+  if (!b || field < 0 || field >= b->n || (int)prec < 0 || (int)prec >= kPrecisions) return -1;
+  return b->splits[(size_t)field * kPrecisions + prec];
+}
 
 yy_status yy_batch_last_device_status(yy_batch *b) {
   if (!b) return YY_ERR_INVALID_ARG;

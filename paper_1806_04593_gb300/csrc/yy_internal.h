@@ -139,6 +139,10 @@ cudaError_t tc_pack_coefficients(yy_grid *g, yy_precision prec, cudaStream_t s);
 // separable synthesis on the tensor cores: polar stage (G operands), then the
 // azimuthal contraction; available once the form is prepared, when it fits
 bool tc_separable_synthesis_ready(const yy_grid *g, yy_precision prec);
+// K split of the dense tensor-core analysis: current count (0 when the form is
+// not prepared), the rule's count and the largest the partial buffer holds
+int tc_analysis_splits(const yy_grid *g, yy_precision prec, int *rule, int *cap);
+yy_status tc_set_analysis_splits(yy_grid *g, yy_precision prec, int splits);
 cudaError_t tc_theta(yy_grid *g, yy_precision prec, bool grad, cudaStream_t s);
 cudaError_t tc_separable_synthesis(yy_grid *g, yy_precision prec, double *phi_yin, double *phi_yang,
                                    double *grad_yin, double *grad_yang, cudaStream_t s);

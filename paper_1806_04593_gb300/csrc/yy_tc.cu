@@ -1330,6 +1330,7 @@ struct yy_tc_tables {
   float *an_b0;                           // fp32 copy of the monopole row of the analysis table
   float *part;                            // split-K partial sums [split][2 n_r][n_lm]
   int an_splits, an_kb_per;
+  int an_kb_total, an_splits_rule, an_splits_cap;   // K blocks; the rule's split count; partial-buffer capacity
   yy::PairMaps an_maps;                   // a[0]: table, b[0]: densities
   // synthesis: tables (cells) as operand A, coefficient sets as operand B
   int sy_kpad, sy_cells_pad;
@@ -1518,8 +1519,12 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
   const int kb_total = t->an_kpad * F::kElem / kRowBytes;
   int splits = (2 * t->pair_slots + an_tiles / 2) / an_tiles;
   splits = splits < 1 ? 1 : (splits > kb_total ? kb_total : splits);
+  t->an_kb_total = kb_total;
   t->an_kb_per = (kb_total + splits - 1) / splits;
   t->an_splits = (kb_total + t->an_kb_per - 1) / t->an_kb_per;
+  t->an_splits_rule = t->an_splits;
+  // the partial buffer holds up to four times the rule's splits (tuning range)
+  t->an_splits_cap = std::min(kb_total, 4 * t->an_splits);
 
   cudaError_t e = cudaSuccess;
   auto A = [&](void **ptr, size_t bytes) {
@@ -1533,7 +1538,7 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
   A((void **)&t->an_mean, t->rows_pad * sizeof(double));
   A((void **)&t->an_colsum, g->n_lm * sizeof(double));
   A((void **)&t->an_b0, g->n_ang * sizeof(float));
-  A((void **)&t->part, (size_t)t->an_splits * M * g->n_lm * sizeof(float));
+  A((void **)&t->part, (size_t)t->an_splits_cap * M * g->n_lm * sizeof(float));
   for (int c = 0; c < 3; ++c) {
     A(&t->sy_q[c], (size_t)F::kPB * t->rows_pad * t->sy_kpad * F::kElem);
     A(&t->sy_tab[c], (size_t)F::kPA * t->sy_cells_pad * t->sy_kpad * F::kElem);
@@ -1848,6 +1853,23 @@ static cudaError_t sep_synthesis_form(yy_grid *g, yy_tc_tables *t, double *py, d
     J.tb = 0;
   }
   return launch_pair<F>(g, t, t->sp_maps, a, s);
+}
+
+int tc_analysis_splits(const yy_grid *g, yy_precision prec, int *rule, int *cap) {
+  const yy_tc_tables *t = ((int)prec >= 0 && (int)prec < 5) ? g->tc[prec] : nullptr;
+  if (!t) return 0;
+  if (rule) *rule = t->an_splits_rule;
+  if (cap) *cap = t->an_splits_cap;
+  return t->an_splits;
+}
+
+yy_status tc_set_analysis_splits(yy_grid *g, yy_precision prec, int splits) {
+  yy_tc_tables *t = ((int)prec >= 0 && (int)prec < 5) ? g->tc[prec] : nullptr;
+  if (!t) return YY_ERR_NOT_SUPPORTED;
+  if (splits < 1 || splits > t->an_splits_cap) return YY_ERR_INVALID_ARG;
+  t->an_kb_per = (t->an_kb_total + splits - 1) / splits;
+  t->an_splits = (t->an_kb_total + t->an_kb_per - 1) / t->an_kb_per;
+  return YY_OK;
 }
 
 bool tc_separable_synthesis_ready(const yy_grid *g, yy_precision prec) {

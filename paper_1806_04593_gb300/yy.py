@@ -117,6 +117,10 @@ def load():
     lib.yy_batch_grid.restype = P
     lib.yy_batch_last_launch_count.argtypes = [P]
     lib.yy_batch_last_launch_count.restype = I
+    lib.yy_batch_branches.argtypes = [P]
+    lib.yy_batch_branches.restype = I
+    lib.yy_batch_analysis_splits.argtypes = [P, I, I]
+    lib.yy_batch_analysis_splits.restype = I
     lib.yy_batch_last_device_status.argtypes = [P]
     lib.yy_batch_last_device_status.restype = I
     lib.yy_batch_destroy.argtypes = [P]
@@ -316,6 +320,15 @@ class Batch:
 
     def launch_count(self):
         return load().yy_batch_last_launch_count(self.handle)
+
+    def branches(self):
+        return load().yy_batch_branches(self.handle)
+
+    def grid_handle(self, field):
+        return load().yy_batch_grid(self.handle, int(field))
+
+    def analysis_splits(self, field, prec):
+        return load().yy_batch_analysis_splits(self.handle, int(field), PRECISIONS.get(prec, prec))
 
     def device_status(self):
         return load().yy_batch_last_device_status(self.handle)
