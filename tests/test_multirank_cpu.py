@@ -1,0 +1,69 @@
+"""The replica path of bench.py with world_size 2 on CPU (gloo).
+
+The solver does not shard (replicas only: each rank solves its own field), so
+the multi-GPU logic is the bench's: barrier, the maximum of the per-rank times
+over ranks, and the reference arm printing one line from rank 0 while the
+other ranks exit without work.
+"""
+
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, queue):
+    os.environ.update({"WORLD_SIZE": str(world), "RANK": str(rank), "LOCAL_RANK": str(rank),
+                       "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    sys.path.insert(0, ROOT)
+    import bench
+    bench.Dist._cuda = staticmethod(lambda: False)   # gloo ranks on CPU even where a GPU is visible
+    d = bench.Dist(init=True)
+    try:
+        d.barrier()
+        # per-rank "device time": the job's time is the slowest rank's
+        queue.put((rank, d.max(0.5 + rank)))
+    finally:
+        d.close()
+
+
+def test_dist_barrier_and_max_over_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    queue = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, queue)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = sorted(queue.get(timeout=10) for _ in range(2))
+    assert got == [(0, 1.5), (1, 1.5)]
+
+
+def test_reference_arm_under_torchrun_two_ranks():
+    """Rank 0 alone runs the oracle and prints one JSON line; rank 1 exits 0."""
+    port = _free_port()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0", "--cpu-sample", "64"]
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    res = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stderr[-2000:]
+    lines = [ln for ln in res.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    out = json.loads(lines[0])
+    assert out["impl"] == "reference" and out["n_gpus"] == 2 and out["value"] > 0
+    assert out["cpu_baseline"]["kind"] == "oracle"
