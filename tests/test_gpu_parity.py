@@ -204,6 +204,40 @@ def test_fp64_separable_at_the_largest_batched_shape(yy, oracle_grid):
         assert rel_max(sep["grad_" + q][:, :, j, k], ref["grad_" + q]) <= TOL_FP64, q
 
 
+def test_long_radial_grid_uses_the_chunked_scan(yy, oracle_grid):
+    """n_r = 1000 (> 768): the radial sums run as the two-kernel chunked scan
+    (per-chunk affine maps, then the composed starts).  Float64 at 1e-12 and
+    FP16X2 at its tolerance against the oracle."""
+    spec = inputs.GridSpec("long_r", np.logspace(-4, 0, 1001), 16, 48, 0.2, 0.1, 10)
+    g = _grid(yy, spec)
+    g.prepare("fp16x2")
+    ry, rg = inputs.pns_density(spec, 31, 0.05)
+    ref = oracle_grid(spec).solve(ry, rg, gradient=True)
+    out = gpu_solve(g, ry, rg, gradient=True)
+    half = gpu_solve(g, ry, rg, gradient=True, prec="fp16x2")
+    for q in ("yin", "yang"):
+        assert rel_max(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64, q
+        assert rel_max(out["grad_" + q], ref["grad_" + q]) <= TOL_FP64, q
+        assert rel_max(half["phi_" + q], ref["phi_" + q]) <= 1e-6, q
+        assert rel_max(half["grad_" + q], ref["grad_" + q]) <= 1e-5, q
+
+
+def test_high_degree_lmax60(yy, oracle_grid):
+    """l_max = 60 on a small grid: the normalised polar tables, the rotation
+    between the patches and the scans at high degree, float64 at 1e-12."""
+    spec = inputs.GridSpec("lmax60", np.logspace(-2, 0, 9), 40, 120, 0.0, 0.0, 60)
+    g = _grid(yy, spec)
+    ry, rg = inputs.pns_density(spec, 32, 0.08)
+    out = gpu_solve(g, ry, rg, gradient=True)
+    rng = np.random.default_rng(60)
+    cells = np.sort(rng.choice(spec.n_ang, 40, replace=False))
+    ref = oracle_grid(spec).solve(ry, rg, gradient=True, cells=cells)
+    j, k = np.divmod(cells, spec.n_phi)
+    for q in ("yin", "yang"):
+        assert rel_max(out["phi_" + q][:, j, k], ref["phi_" + q]) <= TOL_FP64, q
+        assert rel_max(out["grad_" + q][:, :, j, k], ref["grad_" + q]) <= TOL_FP64, q
+
+
 def test_ragged_small_grid(yy):
     """Odd sizes that leave ragged tiles everywhere (n_r, n_ang, n_lm not
     multiples of any tile), r_edges[0] = 0, unequal buffers."""
