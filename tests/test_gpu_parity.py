@@ -222,14 +222,16 @@ def test_long_radial_grid_uses_the_chunked_scan(yy, oracle_grid):
         assert rel_max(half["grad_" + q], ref["grad_" + q]) <= 1e-5, q
 
 
-def test_high_degree_lmax60(yy, oracle_grid):
-    """l_max = 60 on a small grid: the normalised polar tables, the rotation
-    between the patches and the scans at high degree, float64 at 1e-12."""
-    spec = inputs.GridSpec("lmax60", np.logspace(-2, 0, 9), 40, 120, 0.0, 0.0, 60)
+@pytest.mark.parametrize("lmax", [60, 80])
+def test_high_degree(yy, oracle_grid, lmax):
+    """l_max = 60 and 80 (the cap) on a small grid: the normalised polar
+    tables, the rotation between the patches and the scans at high degree,
+    float64 at 1e-12."""
+    spec = inputs.GridSpec(f"lmax{lmax}", np.logspace(-2, 0, 9), 40, 120, 0.0, 0.0, lmax)
     g = _grid(yy, spec)
     ry, rg = inputs.pns_density(spec, 32, 0.08)
     out = gpu_solve(g, ry, rg, gradient=True)
-    rng = np.random.default_rng(60)
+    rng = np.random.default_rng(lmax)
     cells = np.sort(rng.choice(spec.n_ang, 40, replace=False))
     ref = oracle_grid(spec).solve(ry, rg, gradient=True, cells=cells)
     j, k = np.divmod(cells, spec.n_phi)
