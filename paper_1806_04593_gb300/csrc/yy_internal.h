@@ -136,9 +136,32 @@ void tc_free(yy_grid *g);
 cudaError_t tc_analysis(yy_grid *g, yy_precision prec, const double *rho_yin,
                         const double *rho_yang, cudaStream_t s);
 cudaError_t tc_pack_coefficients(yy_grid *g, yy_precision prec, cudaStream_t s);
+// polar stage of the separable analysis from the raw sums of the tensor-core
+// azimuthal stage (yy_separable.cu; the launcher fills the tables, A and the
+// sizes from the grid)
+struct SepThetaPartials {
+  int n_theta, n_lm, lmax1, nt_pad, nt;
+  const float *part;            // [t][part_ld]: raw fp32 sums per row (shell, j)
+  size_t part_ld;
+  const float *row_scale;       // per row: undoes the row's power-of-two scaling
+  const double *mean;           // per row: the centring value
+  const float *t_scale;         // per slot t: undoes the table row's scaling
+  const float *colsum;          // per slot t: sum over k of the table row
+  const double *F0;             // per row: sum over k of rho w (slot 0, times d_phi in tb0)
+  const float *tb;
+  const float2 *tb0;
+  double *A;
+};
+cudaError_t separable_theta_partials(yy_grid *g, SepThetaPartials a, cudaStream_t s);
+size_t separable_theta_partials_smem(const yy_grid *g, int nt_pad);
+
 // separable synthesis on the tensor cores: polar stage (G operands), then the
 // azimuthal contraction; available once the form is prepared, when it fits
 bool tc_separable_synthesis_ready(const yy_grid *g, yy_precision prec);
+// separable analysis with its azimuthal stage on the tensor cores
+bool tc_separable_analysis_ready(const yy_grid *g, yy_precision prec);
+cudaError_t tc_separable_analysis(yy_grid *g, yy_precision prec, const double *rho_yin, const double *rho_yang,
+                                  cudaStream_t s);
 // K split of the dense tensor-core analysis: current count (0 when the form is
 // not prepared), the rule's count and the largest the partial buffer holds
 int tc_analysis_splits(const yy_grid *g, yy_precision prec, int *rule, int *cap);

@@ -246,6 +246,33 @@ __global__ void k_sep_phi(int n_shells, int n_r, int n_theta, int n_phi, int nt_
   }
 }
 
+// The fp32 polar stage on one shell: F (shared memory, [n_theta][nt_pad]) and
+// the pair row sums f0s; the m = 0 modes as an unevaluated-pair dot product,
+// the others as fp32 dot products over j.
+__device__ void theta_modes_f32(int n_theta, int n_lm, int lmax1, int nt_pad, const float *__restrict__ tb,
+                                const float2 *__restrict__ tb0, const float *fs, const float2 *f0s,
+                                double *__restrict__ Arow) {
+  if (threadIdx.x < 32) {
+    for (int l = threadIdx.x; l < lmax1; l += 32) {
+      float h = 0.0f, lo = 0.0f;
+      for (int j = 0; j < n_theta; ++j) {
+        const float2 a = tb0[(size_t)j * lmax1 + l], b = f0s[j];
+        pair_fma(h, lo, a.x, a.y, b.x, b.y);
+      }
+      Arow[l * l] = widen(h) + widen(lo);
+    }
+  }
+  for (int idx = threadIdx.x; idx < n_lm; idx += blockDim.x) {
+    const int l = degree_of(idx);
+    const int t = idx - l * l;
+    if (t == 0) continue;
+    float s = 0.0f;
+#pragma unroll 8
+    for (int j = 0; j < n_theta; ++j) s = fmaf(tb[(size_t)j * n_lm + idx], fs[j * nt_pad + t], s);
+    Arow[idx] = widen(s);
+  }
+}
+
 // Polar stage: one block per shell, the shell's F staged in shared memory, one
 // thread per mode.  The m = 0 modes (fp32 form): an unevaluated-pair dot
 // product of the pair-split table (with d_phi folded in) and the pair row
@@ -265,27 +292,7 @@ __global__ void __launch_bounds__(256) k_sep_theta(int n_theta, int n_lm, int lm
     for (int j = threadIdx.x; j < n_theta; j += blockDim.x) f0s[j] = F0[(size_t)shell * n_theta + j];
   __syncthreads();
   if constexpr (sizeof(T) == 4) {
-    // m = 0 modes: one warp, lane = degree l, compensated
-    if (threadIdx.x < 32) {
-      for (int l = threadIdx.x; l < lmax1; l += 32) {
-        float h = 0.0f, lo = 0.0f;
-        for (int j = 0; j < n_theta; ++j) {
-          const float2 a = tb0[(size_t)j * lmax1 + l], b = f0s[j];
-          pair_fma(h, lo, a.x, a.y, b.x, b.y);
-        }
-        A[(size_t)shell * n_lm + l * l] = widen(h) + widen(lo);
-      }
-    }
-    // the other modes: fp32 dot products over j
-    for (int idx = threadIdx.x; idx < n_lm; idx += blockDim.x) {
-      const int l = degree_of(idx);
-      const int t = idx - l * l;
-      if (t == 0) continue;
-      float s = 0.0f;
-#pragma unroll 8
-      for (int j = 0; j < n_theta; ++j) s = fmaf(tb[(size_t)j * n_lm + idx], fs[j * nt_pad + t], s);
-      A[(size_t)shell * n_lm + idx] = widen(s);
-    }
+    theta_modes_f32(n_theta, n_lm, lmax1, nt_pad, tb, tb0, fs, f0s, A + (size_t)shell * n_lm);
   } else {
     for (int idx = threadIdx.x; idx < n_lm; idx += blockDim.x) {
       const int l = degree_of(idx);
@@ -295,6 +302,83 @@ __global__ void __launch_bounds__(256) k_sep_theta(int n_theta, int n_lm, int lm
       for (int j = 0; j < n_theta; ++j) s = fma(tb[(size_t)j * n_lm + idx], fs[j * nt_pad + t], s);
       A[(size_t)shell * n_lm + idx] = s;
     }
+  }
+}
+
+// Polar stage after the tensor-core azimuthal stage: F of the rows (shell, j)
+// comes from the raw fp32 sums part[t][row] of the centred and scaled rows,
+// F = part * row_scale * t_scale + mean * colsum[t] (the centring undone with
+// the column sums of the table), and the m = 0 row sums from their float64
+// values.  A block takes kThetaShells shells (each table value read serves
+// all of them); one measured fastest: with four, 275 blocks of 98 KB left
+// most SMs with a single block.
+constexpr int kThetaShells = 1;
+
+__global__ void __launch_bounds__(256) k_sep_theta_partials(SepThetaPartials a, int n_shells) {
+  constexpr int S = kThetaShells;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2 *f0s = reinterpret_cast<float2 *>(smraw);                          // [S][n_theta]
+  float *rsm = reinterpret_cast<float *>(f0s + S * a.n_theta);               // [S][n_theta][2]: scale, mean
+  float *fs = rsm + 2 * S * a.n_theta;                                      // [S][n_theta][nt_pad + 1]
+  const int fst = a.nt_pad + 1;                                             // odd stride: conflict-free fill
+  const int shell0 = blockIdx.x * S;
+  const int ns = min(S, n_shells - shell0);
+  for (int e = threadIdx.x; e < S * a.n_theta; e += blockDim.x) {
+    const int q = e / a.n_theta, j = e - q * a.n_theta;
+    float2 f0 = make_float2(0.0f, 0.0f);
+    float sc = 0.0f, mn = 0.0f;
+    if (q < ns) {
+      const size_t row = (size_t)(shell0 + q) * a.n_theta + j;
+      const double d = a.F0[row];
+      const float hi = narrow(d);
+      f0 = make_float2(hi, narrow(d - widen(hi)));
+      sc = a.row_scale[row];
+      mn = narrow(a.mean[row]);
+    }
+    f0s[e] = f0;
+    rsm[2 * e] = sc;
+    rsm[2 * e + 1] = mn;
+  }
+  __syncthreads();
+  const int rows = S * a.n_theta;   // the block's rows are consecutive: (shell0 + q) n_theta + j
+  const size_t row0 = (size_t)shell0 * a.n_theta;
+  for (int e = threadIdx.x; e < a.nt_pad * rows; e += blockDim.x) {
+    const int t = e / rows, qj = e - t * rows;
+    float v = 0.0f;
+    if (t >= 1 && t < a.nt && qj < ns * a.n_theta)
+      v = fmaf(a.part[(size_t)t * a.part_ld + row0 + qj] * rsm[2 * qj], a.t_scale[t], rsm[2 * qj + 1] * a.colsum[t]);
+    fs[(size_t)qj * fst + t] = v;
+  }
+  __syncthreads();
+  // m = 0 modes: warp q < S takes shell q, lanes the degrees, compensated
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < ns) {
+    for (int l = lane; l < a.lmax1; l += 32) {
+      float h = 0.0f, lo = 0.0f;
+      for (int j = 0; j < a.n_theta; ++j) {
+        const float2 x = a.tb0[(size_t)j * a.lmax1 + l], y = f0s[warp * a.n_theta + j];
+        pair_fma(h, lo, x.x, x.y, y.x, y.y);
+      }
+      a.A[(size_t)(shell0 + warp) * a.n_lm + l * l] = widen(h) + widen(lo);
+    }
+  }
+  // the other modes: fp32 dot products over j, one table read for all S shells
+  for (int idx = threadIdx.x; idx < a.n_lm; idx += blockDim.x) {
+    const int l = degree_of(idx);
+    const int t = idx - l * l;
+    if (t == 0) continue;
+    float acc[S];
+#pragma unroll
+    for (int q = 0; q < S; ++q) acc[q] = 0.0f;
+#pragma unroll 4
+    for (int j = 0; j < a.n_theta; ++j) {
+      const float tv = a.tb[(size_t)j * a.n_lm + idx];
+#pragma unroll
+      for (int q = 0; q < S; ++q) acc[q] = fmaf(tv, fs[((size_t)q * a.n_theta + j) * fst + t], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < S; ++q)
+      if (q < ns) a.A[(size_t)(shell0 + q) * a.n_lm + idx] = widen(acc[q]);
   }
 }
 
@@ -503,8 +587,8 @@ cudaError_t separable_prepare(yy_grid *g) {
     g->sep_phi_blocks[q] = std::max(nb, 1) * sms;
     g->sep_ok |= 1 << q;
   }
-  if (!g->sep_ok) return cudaSuccess;
-  for (auto f : {(const void *)k_sep_theta<float>, (const void *)k_sep_theta<double>})
+  // the attribute belongs to the kernel, not to this grid: always the maximum
+  for (auto f : {(const void *)k_sep_theta<float>, (const void *)k_sep_theta<double>, (const void *)k_sep_theta_partials})
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)) != cudaSuccess)
       return e;
   return cudaSuccess;
@@ -531,6 +615,25 @@ cudaError_t synthesis_separable(yy_grid *g, double *phi_yin, double *phi_yang, d
     k_sep_synth<float><<<blocks, 256, g->sep_syn_smem[0], s>>>(grid_rows(g), g->n_r, g->n_theta, g->n_phi, g->lmax, g->n_lm,
                                                                n_fields, g->sep_syn_rows[0], g->Q, g->sep_P32, g->sep_dP32, g->sep_Qs32,
                                                                g->sep_tr32, o);
+  g->launches++;
+  return cudaGetLastError();
+}
+
+size_t separable_theta_partials_smem(const yy_grid *g, int nt_pad) {
+  return (size_t)kThetaShells * g->n_theta * (sizeof(float2) + 2 * sizeof(float) + (nt_pad + 1) * sizeof(float));
+}
+
+cudaError_t separable_theta_partials(yy_grid *g, SepThetaPartials a, cudaStream_t s) {
+  a.n_theta = g->n_theta;
+  a.n_lm = g->n_lm;
+  a.lmax1 = g->lmax + 1;
+  a.tb = g->sep_tb32;
+  a.tb0 = (const float2 *)g->sep_tb0;
+  a.A = g->A;
+  const int S = kThetaShells;
+  const size_t smem = separable_theta_partials_smem(g, a.nt_pad);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  k_sep_theta_partials<<<(grid_rows(g) + S - 1) / S, 256, smem, s>>>(a, grid_rows(g));
   g->launches++;
   return cudaGetLastError();
 }

@@ -750,6 +750,8 @@ struct PackArgs {
   float *scale_out_f;    // the same in fp32 (optional)
   void *out;             // pieces
   int cache;             // 1: row cached in shared memory (K floats)
+  const float *wrow;     // optional (register-resident form only): x[k] *= wrow[(row % w_rows) K + k]
+  int w_rows;
 };
 
 struct PackBatch {
@@ -975,7 +977,7 @@ __device__ __forceinline__ void row_stats(RowStats &r, RowStats *red) {
 }
 
 template <class F, int TPR, int P>
-__global__ void __launch_bounds__(TPR > 256 ? TPR : 256, 1)
+__global__ void __launch_bounds__(TPR > 256 ? TPR : 256, (TPR <= 32 && P <= 6) ? 4 : 1)
 k_pack_reg(PackBatch batch) {
   constexpr int TPB = TPR > 256 ? TPR : 256;
   __shared__ RowStats red[32];
@@ -1016,7 +1018,8 @@ k_pack_reg(PackBatch batch) {
       const int c = 2 * c0 + i;
       const int k = 2 * ((c0 + i / 2) * TPR + tid) + (i & 1);
       const bool used = valid && k < K && k != z0 && k != z1;
-      const float v = used ? f64_to_f32(xv[i]) : 0.0f;
+      float v = used ? f64_to_f32(xv[i]) : 0.0f;
+      if (p.wrow && used) v *= p.wrow[(size_t)(row % p.w_rows) * K + k];
       x[c] = v;
       st.s += v;
       if (used) {
@@ -1231,6 +1234,29 @@ size_t theta_smem(const yy_grid *g) {
   return ((size_t)3 * S + (STAGE ? 16 : 0)) * g->n_lm * sizeof(float);
 }
 
+// rows t of the azimuthal analysis table: dst[t][k] = az[k][t] (zero past nt)
+__global__ void k_az_rows(int n_phi, int nt, int nt_src, int rows, const double *__restrict__ az,
+                          double *__restrict__ dst) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * n_phi) return;
+  const int t = e / n_phi, k = e - t * n_phi;
+  dst[e] = t < nt ? az[(size_t)k * nt_src + t] : 0.0;
+}
+
+// colsum[t] = sum_k rows[t][k] (float64, fixed order), one block per row
+__global__ void __launch_bounds__(256) k_row_total(int K, const double *__restrict__ rows, float *__restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) s += rows[(size_t)blockIdx.x * K + k];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = (float)red[0];
+}
+
 __global__ void k_fill_ones(int n, float *__restrict__ dst) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) dst[e] = 1.0f;
@@ -1346,6 +1372,13 @@ struct yy_tc_tables {
   float *sp_ones, *sp_ga[4], *sp_trigs_f;   // unit cell scales, slot-0 terms, trig row scales
   double *sp_trigs;
   yy::PairMaps sp_maps;                   // a[field]: G, b[0]: trig table
+  // separable analysis: rows (shell, j) of rho w as operand A, the azimuthal
+  // table (rows t, columns phi_k) as operand B
+  int san_ok, san_kpad, san_rows, san_rows_pad, san_bn, san_stages;
+  void *san_x, *san_az;
+  double *san_rs, *san_mean, *san_F0, *san_azs;
+  float *san_rsf, *san_azsf, *san_colsum, *san_ones, *san_part;
+  yy::PairMaps san_maps;                  // a[0]: rho w rows, b[0]: table
 };
 
 namespace yy {
@@ -1372,6 +1405,8 @@ static cudaError_t launch_pack(PackBatch &b, int n, cudaStream_t s) {
   const unsigned wblocks = (unsigned)((rows + 7) / 8);
   if (kp <= 32 * 8)
     k_pack_reg<F, 32, 4><<<dim3(wblocks, n), 256, 0, s>>>(b);
+  else if (kp <= 32 * 12)
+    k_pack_reg<F, 32, 6><<<dim3(wblocks, n), 256, 0, s>>>(b);
   else if (kp <= 32 * 24)
     k_pack_reg<F, 32, 12><<<dim3(wblocks, n), 256, 0, s>>>(b);
   else if (kp <= 32 * 64)
@@ -1489,6 +1524,73 @@ static yy_status prepare_separable_synthesis(yy_grid *g, yy_tc_tables *t) {
   return YY_OK;
 }
 
+// Tables of the separable analysis on the tensor cores: the azimuthal table
+// packed as operand B (rows t; row 0, the constant d_phi, left out: its sums
+// come from the packing's compensated row sums), its column sums for the
+// centring, and the buffers of the weighted density rows.  Rows longer than
+// the register-resident packing takes (2048) leave it unavailable.
+template <class F>
+static yy_status prepare_separable_analysis(yy_grid *g, yy_tc_tables *t) {
+  const int nt = 2 * g->lmax + 1;
+  t->san_kpad = round_up(g->n_phi, kPadK);
+  t->san_rows = grid_rows(g) * g->n_theta;
+  t->san_rows_pad = round_up(t->san_rows, 2 * kPairRows);
+  t->san_bn = round_up(nt, 16);
+  if (t->san_kpad > 32 * 64 || t->san_bn > 256 || !g->sep_az || !g->sep_w32 || !g->sep_tb32 ||
+      separable_theta_partials_smem(g, t->san_bn) > 227 * 1024)
+    return YY_OK;
+  t->san_stages = pair_stages<F>(t->san_bn);
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void **ptr, size_t bytes) {
+    if (e == cudaSuccess) e = dmalloc(ptr, bytes);
+  };
+  const size_t rp = t->san_rows_pad;
+  A(&t->san_x, (size_t)F::kPA * rp * t->san_kpad * F::kElem);
+  A((void **)&t->san_rs, rp * sizeof(double));
+  A((void **)&t->san_rsf, rp * sizeof(float));
+  A((void **)&t->san_mean, rp * sizeof(double));
+  A((void **)&t->san_F0, rp * sizeof(double));
+  A(&t->san_az, (size_t)F::kPB * t->san_bn * t->san_kpad * F::kElem);
+  A((void **)&t->san_azs, t->san_bn * sizeof(double));
+  A((void **)&t->san_azsf, t->san_bn * sizeof(float));
+  A((void **)&t->san_colsum, t->san_bn * sizeof(float));
+  A((void **)&t->san_ones, g->n_phi * sizeof(float));
+  A((void **)&t->san_part, (size_t)t->san_bn * rp * sizeof(float));
+  double *az_rows = nullptr;
+  A((void **)&az_rows, (size_t)t->san_bn * g->n_phi * sizeof(double));
+  if (e != cudaSuccess) {
+    if (az_rows) cudaFree(az_rows);
+    return e == cudaErrorMemoryAllocation ? YY_ERR_OOM : YY_ERR_CUDA;
+  }
+  const int n_az = t->san_bn * g->n_phi;
+  k_az_rows<<<(n_az + 255) / 256, 256>>>(g->n_phi, nt, g->sep_nt_pad, t->san_bn, g->sep_az, az_rows);
+  k_row_total<<<t->san_bn, 256>>>(g->n_phi, az_rows, t->san_colsum);
+  k_fill_ones<<<(g->n_phi + 255) / 256, 256>>>(g->n_phi, t->san_ones);
+  PackBatch b = {};
+  PackArgs &p = b.job[0];
+  p.rows = t->san_bn;
+  p.rows_pad = t->san_bn;
+  p.K = g->n_phi;
+  p.k_pad = t->san_kpad;
+  p.src0 = p.src1 = az_rows;
+  p.split_row = t->san_bn;
+  p.ld = g->n_phi;
+  p.zero_k0 = p.zero_k1 = -1;
+  p.zero_row = 0;
+  p.scale_out = t->san_azs;
+  p.scale_out_f = t->san_azsf;
+  p.out = t->san_az;
+  if ((e = cudaGetLastError()) == cudaSuccess) e = launch_pack<F>(b, 1, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(az_rows);
+  if (e != cudaSuccess) return YY_ERR_CUDA;
+  const bool ok = make_map<F>(&t->san_maps.a[0], t->san_x, t->san_kpad, F::kPA * t->san_rows_pad, kPairRows) &&
+                  make_map<F>(&t->san_maps.b[0], t->san_az, t->san_kpad, F::kPB * t->san_bn, t->san_bn / 2);
+  if (!ok) return YY_ERR_NOT_SUPPORTED;
+  t->san_ok = 1;
+  return YY_OK;
+}
+
 template <class F>
 static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
   const int M = grid_rows(g);
@@ -1598,6 +1700,8 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
     ok = make_map<F>(&t->sy_maps.a[c], t->sy_tab[c], t->sy_kpad, F::kPA * t->sy_cells_pad, kPairRows) &&
          make_map<F>(&t->sy_maps.b[c], t->sy_q[c], t->sy_kpad, F::kPB * t->rows_pad, bh);
   if (!ok) return YY_ERR_NOT_SUPPORTED;
+  const yy_status st = prepare_separable_analysis<F>(g, t);
+  if (st != YY_OK) return st;
   return prepare_separable_synthesis(g, t);
 }
 
@@ -1619,6 +1723,10 @@ static void free_tables(yy_tc_tables *t) {
   }
   void *sp[] = {t->sp_trig, t->sp_trigs_f, t->sp_trigs, t->sp_ones};
   for (void *p : sp)
+    if (p) cudaFree(p);
+  void *sa[] = {t->san_x, t->san_az, t->san_rs, t->san_mean, t->san_F0, t->san_azs,
+                t->san_rsf, t->san_azsf, t->san_colsum, t->san_ones, t->san_part};
+  for (void *p : sa)
     if (p) cudaFree(p);
   delete t;
 }
@@ -1870,6 +1978,83 @@ yy_status tc_set_analysis_splits(yy_grid *g, yy_precision prec, int splits) {
   t->an_kb_per = (t->an_kb_total + splits - 1) / splits;
   t->an_splits = (t->an_kb_total + t->an_kb_per - 1) / t->an_kb_per;
   return YY_OK;
+}
+
+// Separable analysis on the tensor cores: the weighted density rows (shell,
+// j) are centred, scaled and split by the packing (which also forms their
+// compensated sums, slot 0), contracted with the azimuthal table (K = n_phi,
+// raw fp32 sums), and the polar stage turns the sums into the moments.
+template <class F>
+static cudaError_t separable_analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, const double *rg,
+                                           cudaStream_t s) {
+  PackBatch b = {};
+  PackArgs &p = b.job[0];
+  p.rows = t->san_rows;
+  p.rows_pad = t->san_rows_pad;
+  p.K = g->n_phi;
+  p.k_pad = t->san_kpad;
+  p.src0 = ry;
+  p.src1 = rg;
+  p.split_row = g->n_r * g->n_theta;
+  p.ld = g->n_phi;
+  p.zero_k0 = p.zero_k1 = -1;
+  p.zero_row = -1;
+  p.dot_vec = t->san_ones;        // row sums (slot 0)
+  p.dot_out = t->san_F0;
+  p.mean_out = t->san_mean;
+  p.scale_out = t->san_rs;
+  p.scale_out_f = t->san_rsf;
+  p.out = t->san_x;
+  p.wrow = g->sep_w32;            // rho w
+  p.w_rows = g->n_theta;
+  cudaError_t e = launch_pack<F>(b, 1, s);
+  g->launches++;
+  if (e != cudaSuccess) return e;
+  PairArgs a = {};
+  a.stages = t->san_stages;
+  a.cells = t->san_rows;
+  a.cell_tiles = t->san_rows_pad / (2 * kPairRows);
+  a.rows = 2 * g->lmax + 1;
+  a.row_tiles = 1;
+  a.bn = t->san_bn;
+  a.kb_total = t->san_kpad * F::kElem / kRowBytes;
+  a.k_splits = 1;
+  a.kb_per_split = a.kb_total;
+  a.kb_chunk = kAnalysisFill * F::kElem / kRowBytes;
+  a.a_rows = t->san_rows_pad;
+  a.b_rows = t->san_bn;
+  a.out_mode = 0;
+  a.part = t->san_part;
+  a.part_ld = t->san_rows_pad;
+  a.n_jobs = 1;
+  a.err = g->err;
+  if ((e = launch_pair<F>(g, t, t->san_maps, a, s)) != cudaSuccess) return e;
+  SepThetaPartials th = {};
+  th.nt_pad = t->san_bn;
+  th.nt = 2 * g->lmax + 1;
+  th.part = t->san_part;
+  th.part_ld = t->san_rows_pad;
+  th.row_scale = t->san_rsf;
+  th.mean = t->san_mean;
+  th.t_scale = t->san_azsf;
+  th.colsum = t->san_colsum;
+  th.F0 = t->san_F0;
+  return separable_theta_partials(g, th, s);
+}
+
+bool tc_separable_analysis_ready(const yy_grid *g, yy_precision prec) {
+  const yy_tc_tables *t = ((int)prec >= 0 && (int)prec < 5) ? g->tc[prec] : nullptr;
+  return t && t->san_ok;
+}
+
+cudaError_t tc_separable_analysis(yy_grid *g, yy_precision prec, const double *ry, const double *rg, cudaStream_t s) {
+  yy_tc_tables *t = g->tc[prec];
+  switch (prec) {
+    case YY_FP16X2: return separable_analysis_form<FormFP16x2>(g, t, ry, rg, s);
+    case YY_BF16X3: return separable_analysis_form<FormBF16x3>(g, t, ry, rg, s);
+    case YY_TF32: return separable_analysis_form<FormTF32>(g, t, ry, rg, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 bool tc_separable_synthesis_ready(const yy_grid *g, yy_precision prec) {
