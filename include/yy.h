@@ -174,7 +174,14 @@ yy_status yy_polar_grid_create(const double *r_edges, int n_r, int n_theta, int 
                                double G, yy_grid **out);
 
 /* Select the analysis evaluation for later solves (see yy_analysis).
- * Errors: YY_ERR_INVALID_ARG. */
+ * YY_ANALYSIS_SEPARABLE builds the separable tensor-core tables of every
+ * tensor-core form already prepared (allocates device memory, synchronises;
+ * a form prepared later while it is selected builds them in yy_grid_prepare).
+ * They stay until the handle is destroyed or the batch tuner drops them for a
+ * field that does not use them.  Must not be called while a stream is being
+ * captured unless the tables already exist.
+ * Errors: YY_ERR_INVALID_ARG; YY_ERR_OOM / YY_ERR_CUDA from building the
+ * tables (the method stays selected; those forms then use the dense path). */
 yy_status yy_grid_set_analysis(yy_grid *g, yy_analysis method);
 
 /* Build the operand tables of a reduced-precision form (allocates device
@@ -319,7 +326,10 @@ yy_status yy_batch_prepare(yy_batch *b, yy_precision prec);
  * first yy_batch_potential after tuning also times its graph with 1, 2, 4, 8
  * and 16 parallel branches on the caller's buffers, keeps the fastest, and
  * synchronises.  chosen (NULL or n_fields entries) receives the yy_analysis
- * picked per field.  Prepares the form; synchronises. */
+ * picked per field.  Prepares the form; synchronises.  The separable
+ * tensor-core tables of this form are freed for fields that pick the dense
+ * evaluation, and rebuilt (before any capture) if a field is later set to
+ * YY_ANALYSIS_SEPARABLE. */
 yy_status yy_batch_tune(yy_batch *b, yy_precision prec, int with_gradient, int reps, int *chosen);
 
 /* Set one field's analysis evaluation by hand, for every form (see

@@ -228,6 +228,11 @@ yy_status yy_grid_set_analysis(yy_grid *g, yy_analysis method) {
   if (!g || (method != YY_ANALYSIS_AUTO && method != YY_ANALYSIS_SEPARABLE && method != YY_ANALYSIS_DENSE))
     return YY_ERR_INVALID_ARG;
   g->analysis_method = (int)method;
+  if (method == YY_ANALYSIS_SEPARABLE)   // the separable tensor-core tables of the prepared forms
+    for (yy_precision p : {YY_TF32, YY_BF16X3, YY_FP16X2}) {
+      const yy_status st = tc_build_separable(g, p);
+      if (st != YY_OK) return st;
+    }
   return YY_OK;
 }
 

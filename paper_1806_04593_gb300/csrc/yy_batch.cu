@@ -250,7 +250,11 @@ yy_status yy_batch_tune(yy_batch *b, yy_precision prec, int with_gradient, int r
     float best = 1e30f;
     int pick = 0;
     for (int c = 0; c < n_cand && st == YY_OK; ++c) {
-      yy_grid_set_analysis(g, cands[c].method);
+      if (yy_grid_set_analysis(g, cands[c].method) != YY_OK) {   // its tables could not be built
+        cudaGetLastError();
+        if (c == pick) pick = c + 1;
+        continue;
+      }
       if (tc) st = yy::tc_set_analysis_splits(g, prec, cands[c].splits > 0 ? cands[c].splits : rule);
       if (st == YY_OK)   // warm-up
         st = yy_potential(g, buf, buf + field, buf + 2 * field, buf + 3 * field, gy, gg, prec, b->cap);
@@ -271,6 +275,7 @@ yy_status yy_batch_tune(yy_batch *b, yy_precision prec, int with_gradient, int r
     cudaFree(buf);
     yy_grid_set_analysis(g, YY_ANALYSIS_AUTO);
     if (tc) yy::tc_set_analysis_splits(g, prec, rule);
+    if (cands[pick].method != YY_ANALYSIS_SEPARABLE) yy::tc_release_separable(g, prec);
     b->method[(size_t)i * kPrecisions + prec] = (int)cands[pick].method;
     b->splits[(size_t)i * kPrecisions + prec] = cands[pick].splits;
     if (chosen) chosen[i] = (int)cands[pick].method;
@@ -306,9 +311,13 @@ yy_status yy_batch_potential(yy_batch *b, const double *const *rho_yin, const do
   for (GraphEntry &ge : b->cache)
     if (ge.prec == (int)prec && ge.grad == grad && ge.ptrs == key) return to_status(cudaGraphLaunch(ge.exec, s));
 
-  // first use of this set of buffers: capture every field's solve
-  for (yy_grid *g : b->grids) {
+  // first use of this set of buffers: capture every field's solve.  Tables a
+  // field's evaluation needs are built here, before the capture begins.
+  for (int i = 0; i < b->n; ++i) {
+    yy_grid *g = b->grids[i];
     if (g->profiling) yy_grid_set_profiling(g, 0);
+    const yy_status st = yy_grid_set_analysis(g, (yy_analysis)b->method[(size_t)i * kPrecisions + prec]);
+    if (st != YY_OK) return st;
   }
   const Buffers io = {rho_yin, rho_yang, phi_yin, phi_yang, grad_yin, grad_yang};
   cudaGraphExec_t exec = nullptr;

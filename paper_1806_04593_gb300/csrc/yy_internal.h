@@ -158,6 +158,11 @@ size_t separable_theta_partials_smem(const yy_grid *g, int nt_pad);
 // separable synthesis on the tensor cores: polar stage (G operands), then the
 // azimuthal contraction; available once the form is prepared, when it fits
 bool tc_separable_synthesis_ready(const yy_grid *g, yy_precision prec);
+// tables of both separable tensor-core paths: built for a prepared form while
+// YY_ANALYSIS_SEPARABLE is selected (never during stream capture), released
+// by the batch tuner for fields that do not use them
+yy_status tc_build_separable(yy_grid *g, yy_precision prec);
+void tc_release_separable(yy_grid *g, yy_precision prec);
 // separable analysis with its azimuthal stage on the tensor cores
 bool tc_separable_analysis_ready(const yy_grid *g, yy_precision prec);
 cudaError_t tc_separable_analysis(yy_grid *g, yy_precision prec, const double *rho_yin, const double *rho_yang,

@@ -134,3 +134,63 @@ def test_unprepared_precision_is_not_supported(yy):
     x = torch.zeros((spec.n_r, spec.n_theta, spec.n_phi), dtype=torch.float64, device="cuda")
     assert yy.yy_potential(g.handle, x, x, x.clone(), x.clone(), prec=yy.YY_BF16X3) == yy.YY_ERR_NOT_SUPPORTED
     g.close()
+
+
+def test_separable_tables_built_on_selection(yy):
+    """The separable tensor-core tables cost device memory only while the
+    separable evaluation is selected, and selecting it before or after the
+    form is prepared gives bitwise the same solve."""
+    import torch
+    spec = inputs.GRIDS["mid"]()
+    ry, rg = inputs.density_for(spec)
+    a = yy.Grid.from_spec(spec)
+    b = yy.Grid.from_spec(spec)
+    try:
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        a.prepare("fp16x2")                        # AUTO: dense, no separable tables
+        free1 = torch.cuda.mem_get_info()[0]
+        a.set_analysis("separable")                # builds them now
+        free2 = torch.cuda.mem_get_info()[0]
+        assert free2 < free1 <= free0
+        b.set_analysis("separable")
+        b.prepare("fp16x2")                        # builds them while preparing
+        out_a = gpu_solve(a, ry, rg, gradient=True, prec="fp16x2")
+        out_b = gpu_solve(b, ry, rg, gradient=True, prec="fp16x2")
+        for key in out_a:
+            assert np.array_equal(out_a[key], out_b[key]), key
+        assert yy.yy_last_device_status(a.handle) == yy.YY_OK
+    finally:
+        a.close()
+        b.close()
+
+
+def test_long_rows_streaming_packing(yy):
+    """Density rows of 2 760 cells (even, longer than a warp's share) go
+    through the streaming packing: 194 rows over at most one block per SM,
+    so blocks walk several rows.  Against the oracle for every form; a
+    density pointer off the 16-byte grid is refused."""
+    import torch
+
+    from oracle import OracleGrid
+    spec = inputs.GridSpec("long_rows_tc", np.logspace(-2, 0, 98), 30, 92, 0.02, 0.04, 12, 1.0)
+    rng = np.random.default_rng(43)
+    ry = rng.uniform(0.5, 1.5, (spec.n_r, 30, 92))
+    rg = rng.uniform(0.5, 1.5, (spec.n_r, 30, 92))
+    ref = OracleGrid(spec.r_edges, 30, 92, 0.02, 0.04, 12).solve(ry, rg, gradient=True)
+    g = yy.Grid.from_spec(spec)
+    try:
+        for prec in ("fp16x2", "bf16x3", "tf32"):
+            g.prepare(prec)
+            out = gpu_solve(g, ry, rg, gradient=True, prec=prec)
+            tol_phi, tol_g = TOL[prec]
+            for q in ("yin", "yang"):
+                assert rel_max(out["phi_" + q], ref["phi_" + q]) <= tol_phi, prec
+                assert rel_max(out["grad_" + q], ref["grad_" + q]) <= tol_g, prec
+        assert yy.yy_last_device_status(g.handle) == yy.YY_OK
+        buf = torch.zeros(ry.size + 1, dtype=torch.float64, device="cuda")
+        off = buf[1:].view(ry.shape)
+        phi = torch.empty_like(off)
+        assert yy.yy_potential(g.handle, off, off, phi, phi.clone(), prec=yy.YY_FP16X2) == yy.YY_ERR_INVALID_ARG
+    finally:
+        g.close()
