@@ -408,6 +408,32 @@ def run_ours(args, dist):
         ms64 = e0.elapsed_time(e1) / 2
         fp64_path = {"value": 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64,
                      "headline_speedup": value / dist.world / (1e3 / ms64)}
+        # the same float64 accuracy with the synthesis's azimuthal stage on the
+        # tensor cores (Ozaki scheme), and its largest difference from the
+        # CUDA-core float64 result
+        try:
+            grid.prepare("fp64_ozaki")
+        except yy.YYError as exc:
+            fp64_path["ozaki"] = {"unavailable": str(exc)}
+        else:
+            ref64 = {"phi_yin": phi_y.clone(), "phi_yang": phi_g.clone()}
+            if gradient:
+                ref64["grad_yin"], ref64["grad_yang"] = g_y.clone(), g_g.clone()
+            grid.potential(ry, rg, phi_y, phi_g, g_y, g_g, prec="fp64_ozaki", stream=stream)
+            torch.cuda.synchronize()
+            got = {"phi_yin": phi_y, "phi_yang": phi_g, "grad_yin": g_y, "grad_yang": g_g}
+            diff = max(float((got[k] - v).abs().max() / v.abs().max()) for k, v in ref64.items())
+            e0.record(stream)
+            for _ in range(3):
+                grid.potential(ry, rg, phi_y, phi_g, g_y, g_g, prec="fp64_ozaki", stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            msoz = e0.elapsed_time(e1) / 3
+            fp64_path["ozaki"] = {"value": 1e3 / msoz, "unit": UNIT, "ms_per_step": msoz,
+                                  "speedup_vs_fp64_path": ms64 / msoz,
+                                  "rel_max_diff_vs_fp64_path": diff,
+                                  "precision": "fp64_ozaki (float64 results; azimuthal synthesis "
+                                               "stage on tcgen05 by 8-bit slices, exact per level)"}
         solve()                                   # leave the headline form's result in place
         torch.cuda.synchronize()
 

@@ -73,13 +73,24 @@ typedef enum {
  *   YY_BF16X3 operands split into 3 bf16 terms, 6 cross products, fp32
  *             accumulation per K chunk, chunks summed in float64.
  *   YY_FP16X2 operands split into 2 scaled fp16 terms, 3 cross products,
- *             fp32 accumulation per K chunk, chunks summed in float64.       */
+ *             fp32 accumulation per K chunk, chunks summed in float64.
+ *   YY_FP64_OZAKI  float64 results (the YY_FP64 tolerance) with the
+ *             synthesis's azimuthal stage on tcgen05 tensor cores by the
+ *             Ozaki scheme: the polar-stage rows G and the trig table cut
+ *             into six 8-bit fixed-point slices (integers exact in bf16)
+ *             under a power-of-two scale per row, the 21 slice products of
+ *             levels <= 5 accumulated exactly in fp32 per level, levels
+ *             combined in integers and rounded once to float64.  The
+ *             analysis, the scans and the polar stage are float64 on CUDA
+ *             cores as for YY_FP64.  Needs yy_grid_prepare and
+ *             2 l_max + 1 <= 64 (l_max <= 31).                             */
 typedef enum {
   YY_FP64 = 0,
   YY_FP32 = 1,
   YY_TF32 = 2,
   YY_BF16X3 = 3,
-  YY_FP16X2 = 4
+  YY_FP16X2 = 4,
+  YY_FP64_OZAKI = 5
 } yy_precision;
 
 /* Tables and intermediates readable through yy_grid_copy_table (tests and
@@ -184,9 +195,10 @@ yy_status yy_polar_grid_create(const double *r_edges, int n_r, int n_theta, int 
  * tables (the method stays selected; those forms then use the dense path). */
 yy_status yy_grid_set_analysis(yy_grid *g, yy_analysis method);
 
-/* Build the operand tables of a reduced-precision form (allocates device
- * memory; synchronises).  YY_FP64 is always ready.  Returns
- * YY_ERR_NOT_SUPPORTED if the device cannot run the form. */
+/* Build the operand tables of a reduced-precision form or of YY_FP64_OZAKI
+ * (allocates device memory; synchronises).  YY_FP64 is always ready.
+ * Returns YY_ERR_NOT_SUPPORTED if the device cannot run the form, or for
+ * YY_FP64_OZAKI when l_max > 31. */
 yy_status yy_grid_prepare(yy_grid *g, yy_precision prec);
 
 /* One solve on `cuda_stream` (a cudaStream_t, NULL = legacy default stream).

@@ -83,6 +83,7 @@ static void free_all(yy_grid *g) {
   if (g->pipe_in) cudaStreamDestroy(g->pipe_in);
   if (g->pipe_out) cudaStreamDestroy(g->pipe_out);
   tc_free(g);
+  ozaki_free(g);
 }
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
@@ -249,6 +250,10 @@ yy_status yy_grid_prepare(yy_grid *g, yy_precision prec) {
     case YY_TF32:
     case YY_BF16X3:
     case YY_FP16X2: return tc_prepare(g, prec);
+    case YY_FP64_OZAKI: {
+      const yy_status st = ozaki_prepare(g);
+      return st == YY_OK ? from_cuda(cudaDeviceSynchronize()) : st;
+    }
   }
   return YY_ERR_INVALID_ARG;
 }
@@ -266,8 +271,9 @@ static yy_status check_solve_args(yy_grid *g, const double *rho_yin, const doubl
   const void *ptrs[] = {rho_yin, rho_yang, phi_yin, phi_yang, grad_yin, grad_yang};
   for (const void *p : ptrs)
     if (p && !aligned16(p)) return YY_ERR_INVALID_ARG;
-  if ((int)prec < 0 || (int)prec > (int)YY_FP16X2) return YY_ERR_INVALID_ARG;
+  if ((int)prec < 0 || (int)prec > (int)YY_FP64_OZAKI) return YY_ERR_INVALID_ARG;
   if (prec == YY_FP32 && !g->ban32) return YY_ERR_NOT_SUPPORTED;
+  if (prec == YY_FP64_OZAKI && !ozaki_ready(g)) return YY_ERR_NOT_SUPPORTED;
   if ((prec == YY_TF32 || prec == YY_BF16X3 || prec == YY_FP16X2) && !g->tc[prec]) return YY_ERR_NOT_SUPPORTED;
   return YY_OK;
 }
@@ -286,6 +292,9 @@ yy_status yy_potential(yy_grid *g, const double *rho_yin, const double *rho_yang
   auto mark = [&](int i) {
     if (prof && e == cudaSuccess) e = cudaEventRecord(g->ev[i], s);
   };
+  // YY_FP64_OZAKI: the analysis and the scans of YY_FP64, the synthesis by the Ozaki scheme
+  const bool ozaki = prec == YY_FP64_OZAKI;
+  if (ozaki) prec = YY_FP64;
   const bool simt = (prec == YY_FP64 || prec == YY_FP32);
   const bool f32 = (prec == YY_FP32);
   g->launches = 0;
@@ -307,8 +316,8 @@ yy_status yy_potential(yy_grid *g, const double *rho_yin, const double *rho_yang
   // YY_ANALYSIS_DENSE is set; on the tensor-core forms dense unless
   // YY_ANALYSIS_SEPARABLE is set (there the dense contraction is faster);
   // dense wherever the grid does not fit the separable kernels
-  const bool sep_synth = simt ? (g->analysis_method != YY_ANALYSIS_DENSE && (g->sep_syn_ok & (f32 ? 1 : 2)) != 0)
-                              : (g->analysis_method == YY_ANALYSIS_SEPARABLE && tc_separable_synthesis_ready(g, prec));
+  const bool sep_synth = ozaki || (simt ? (g->analysis_method != YY_ANALYSIS_DENSE && (g->sep_syn_ok & (f32 ? 1 : 2)) != 0)
+                                        : (g->analysis_method == YY_ANALYSIS_SEPARABLE && tc_separable_synthesis_ready(g, prec)));
   g->last_sep_synthesis = sep_synth ? 1 : 0;
   if (e == cudaSuccess) e = rotate_moments(g, prec == YY_FP64, s);
   if (e == cudaSuccess) e = radial_scan(g, f32, true, s);
@@ -316,7 +325,9 @@ yy_status yy_potential(yy_grid *g, const double *rho_yin, const double *rho_yang
     e = sep_synth ? tc_theta(g, prec, grad_yin != nullptr, s) : tc_pack_coefficients(g, prec, s);
   mark(2);
   if (e == cudaSuccess) {
-    if (simt)
+    if (ozaki)
+      e = ozaki_synthesis(g, phi_yin, phi_yang, grad_yin, grad_yang, s);
+    else if (simt)
       e = sep_synth ? synthesis_separable(g, phi_yin, phi_yang, grad_yin, grad_yang, !f32, s)
                     : synthesis_simt(g, phi_yin, phi_yang, grad_yin, grad_yang, f32, s);
     else

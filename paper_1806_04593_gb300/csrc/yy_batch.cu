@@ -26,7 +26,7 @@ namespace {
 constexpr int kBranchesMax = 16;
 constexpr int kBranchesDefault = 4;
 constexpr int kCacheSize = 4;
-constexpr int kPrecisions = YY_FP16X2 + 1;
+constexpr int kPrecisions = YY_FP64_OZAKI + 1;
 
 struct GraphEntry {
   int prec, grad;

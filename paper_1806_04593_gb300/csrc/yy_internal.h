@@ -16,6 +16,7 @@
 
 // Operand tables of one reduced-precision form (tensor-core path).
 struct yy_tc_tables;
+struct yy_oz_tables;
 
 struct yy_grid {
   int device;
@@ -76,6 +77,8 @@ struct yy_grid {
 
   // tensor-core forms
   yy_tc_tables *tc[5];
+  // float64 by the Ozaki scheme (YY_FP64_OZAKI): slices of G and of the trig table
+  yy_oz_tables *oz;
 
   // kernels launched by the last yy_potential call
   int launches;
@@ -176,5 +179,13 @@ cudaError_t tc_separable_synthesis(yy_grid *g, yy_precision prec, double *phi_yi
                                    double *grad_yin, double *grad_yang, cudaStream_t s);
 cudaError_t tc_synthesis(yy_grid *g, yy_precision prec, double *phi_yin,
                          double *phi_yang, double *grad_yin, double *grad_yang, cudaStream_t s);
+
+// float64 synthesis with its azimuthal stage on the tensor cores by the Ozaki
+// scheme (yy_tc.cu): tables once (2 l_max + 1 <= 64), then per solve
+yy_status ozaki_prepare(yy_grid *g);
+void ozaki_free(yy_grid *g);
+bool ozaki_ready(const yy_grid *g);
+cudaError_t ozaki_synthesis(yy_grid *g, double *phi_yin, double *phi_yang, double *grad_yin, double *grad_yang,
+                            cudaStream_t s);
 
 }  // namespace yy

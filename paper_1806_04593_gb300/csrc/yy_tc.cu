@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <new>
+#include <vector>
 
 #include "yy_internal.h"
 #include "yy_tc_pair.cuh"
@@ -911,7 +912,7 @@ static cudaError_t launch_pair(yy_grid *g, yy_tc_tables *t, const PairMaps &maps
   const int tiles = a.cell_tiles * a.row_tiles * a.k_splits * a.n_jobs;
   const int pairs = tiles < t->pair_slots ? tiles : t->pair_slots;
   cudaLaunchAttribute attr[1];
-  const int smem = a.stages * pair_stage_bytes<F>(a.bn) + kSmemFixed + (a.out_mode == 2 ? kEpiStageBytes : 0);
+  const int smem = a.stages * pair_stage_bytes<F>(a.bn) + kSmemFixed + (a.out_mode >= 2 ? kEpiStageBytes : 0);
   cudaLaunchConfig_t cfg = pair_config(pairs, smem, s, attr);
   const cudaError_t e = a.out_mode == 2   ? cudaLaunchKernelEx(&cfg, k_tc_pair<F, 2>, maps, a)
                         : a.out_mode == 1 ? cudaLaunchKernelEx(&cfg, k_tc_pair<F, 1>, maps, a)
@@ -1596,6 +1597,282 @@ cudaError_t tc_synthesis(yy_grid *g, yy_precision prec, double *py, double *pg, 
     case YY_TF32: return synthesis_form<FormTF32>(g, t, py, pg, gy, gg, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// ---------------------------------------------------------------------------
+// float64 synthesis by the Ozaki scheme (YY_FP64_OZAKI)
+// ---------------------------------------------------------------------------
+//
+// The separable synthesis with its azimuthal stage on the tensor cores at
+// float64 accuracy: a float64 polar stage forms G[t] per output row (shell,
+// j) and field and cuts each row into FormOzaki's six fixed-point slices
+// under the row's power-of-two scale; k_tc_pair (out_mode 3) contracts them
+// with the slices of the trig table (scaled by 1/2: cos 0 = 1 must lie inside
+// (-1, 1)) over K = 2 l_max + 1 <= 64, exact per level, and rounds each value
+// once.  The monopole slot t = 0 is part of the contraction: it is exact too.
+
+struct OzThetaArgs {
+  int n_shells, n_theta, lmax, n_lm, nt, n_jobs, rows_pad;
+  const double *Q;              // [3][n_shells][n_lm]: Phi, g_r and angular coefficients
+  const double *tab[3];         // [n_theta][n_lm]: P, dP/dtheta, m P / sin theta (float64)
+  __nv_bfloat16 *G[4];          // per field: slices [6][rows_pad][kMaxK]
+  int *gexp[4];                 // per field: [rows_pad] power of two of a unit level-5 sum
+};
+
+// Balanced base-256 digits of X < 2^48 (most significant first): each
+// digit taken in [-127, 128] with a carry into the next; the top one is at
+// most 128 for X <= 2^47.
+__host__ __device__ __forceinline__ void oz_digits(unsigned long long X, int (&d)[6]) {
+#pragma unroll
+  for (int s = 5; s > 0; --s) {
+    int v = (int)(X & 255u);
+    X >>= 8;
+    if (v > 128) {
+      v -= 256;
+      X += 1;
+    }
+    d[s] = v;
+  }
+  d[0] = (int)X;
+}
+
+// One warp per (field, row (shell, j)); lane L forms G at t = 2 L and 2 L + 1
+// with the float64 polar sums of the CUDA-core separable synthesis (l from
+// l_max down, g_phi with the cos / sin slots swapped), then the row's scale
+// 2^e (e from the largest |G|: every |G| 2^-e < 1/2) and the digits of
+// X = round(|G| 2^(48 - e)) <= 2^47, taken from the float64 bits, each with
+// the sign of G.  A row of zeros (or of values below the normal range) gets
+// zero digits.
+__global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  const int rows = a.n_shells * a.n_theta;
+  if (warp >= rows * a.n_jobs) return;
+  const int f = warp / rows, row = warp % rows;
+  const int shell = row / a.n_theta, j = row % a.n_theta;
+  const int qb = f < 2 ? f : 2;
+  const double *q = a.Q + ((size_t)qb * a.n_shells + shell) * a.n_lm;
+  const double *tj = a.tab[f <= 1 ? 0 : f - 1] + (size_t)j * a.n_lm;
+  double gv[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int t = 2 * lane + h;
+    double g = 0.0;
+    if (t < a.nt) {
+      const int m = (t + 1) / 2;
+      if (f < 3) {
+        for (int l = a.lmax; l >= m; --l) g = fma(q[l * l + t], tj[l * l + t], g);
+      } else if (t > 0) {
+        const int src = (t & 1) ? t + 1 : t - 1;   // cos slot <- sin coefficient, sin slot <- cos
+        for (int l = a.lmax; l >= m; --l) g = fma(q[l * l + src], tj[l * l + t], g);
+        if (!(t & 1)) g = -g;
+      }
+    }
+    gv[h] = g;
+  }
+  const unsigned long long b0 = (unsigned long long)__double_as_longlong(gv[0]);
+  const unsigned long long b1 = (unsigned long long)__double_as_longlong(gv[1]);
+  unsigned long long mb = max(b0 & 0x7FFFFFFFFFFFFFFFull, b1 & 0x7FFFFFFFFFFFFFFFull);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
+  const int exm = (int)(mb >> 52);                 // biased exponent of the largest |G|
+  const int e = exm - 1021;                        // |G| < 2^(exm - 1022) = 2^(e - 1)
+  int d[2][6];
+  const unsigned long long bits[2] = {b0, b1};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int ex = (int)((bits[h] >> 52) & 0x7FFu);
+    const int sh = 1027 - ex + e;                  // |G| 2^(48 - e) = significand >> sh, sh >= 6
+    unsigned long long X = 0ull;
+    if (exm != 0 && ex != 0 && sh < 64)
+      X = ((((bits[h] & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> (sh - 1)) + 1ull) >> 1;   // round half up
+    oz_digits(X, d[h]);
+  }
+  const size_t stride = (size_t)a.rows_pad * FormOzaki::kMaxK;
+  __nv_bfloat16 *dst = a.G[f] + (size_t)row * FormOzaki::kMaxK + 2 * lane;
+#pragma unroll
+  for (int sl = 0; sl < 6; ++sl) {
+    const float v0 = (b0 >> 63) ? -(float)d[0][sl] : (float)d[0][sl];
+    const float v1 = (b1 >> 63) ? -(float)d[1][sl] : (float)d[1][sl];
+    *reinterpret_cast<__nv_bfloat162 *>(dst + sl * stride) = __floats2bfloat162_rn(v0, v1);
+  }
+  // value = 2^(e + 1 - 64) (digit sums): trig scale 2^1, digit weights 2^-64
+  if (lane == 0) a.gexp[f][row] = exm == 0 ? 0 : e + 1 - 64;
+}
+
+}  // namespace yy
+
+struct yy_oz_tables {
+  int rows, rows_pad, bn, row_tiles, b_rows_pad, stages, pair_slots;
+  void *G[4];                   // per field: slices [6][rows_pad][64]
+  int *gexp[4];                 // per field: [rows_pad]
+  void *trig;                   // slices of trig / 2: [6][b_rows_pad][64]
+  yy::PairMaps maps;
+};
+
+namespace yy {
+
+static void free_oz(yy_oz_tables *o) {
+  if (!o) return;
+  for (int f = 0; f < 4; ++f) {
+    if (o->G[f]) cudaFree(o->G[f]);
+    if (o->gexp[f]) cudaFree(o->gexp[f]);
+  }
+  if (o->trig) cudaFree(o->trig);
+  delete o;
+}
+
+void ozaki_free(yy_grid *g) {
+  free_oz(g->oz);
+  g->oz = nullptr;
+}
+
+bool ozaki_ready(const yy_grid *g) { return g->oz != nullptr; }
+
+// bf16 bits of a small integer (|v| <= 255: exact, the low 16 bits of the
+// fp32 pattern are zero)
+static uint16_t bf16_int(int v) {
+  const float f = (float)v;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  return (uint16_t)(u >> 16);
+}
+
+yy_status ozaki_prepare(yy_grid *g) {
+  typedef FormOzaki F;
+  if (g->oz) return YY_OK;
+  const int nt = 2 * g->lmax + 1;
+  if (nt > F::kMaxK || !g->sep_tr || !g->sep_P || !g->sep_dP || !g->sep_Qs) return YY_ERR_NOT_SUPPORTED;
+  yy_oz_tables *o = new (std::nothrow) yy_oz_tables();
+  if (!o) return YY_ERR_OOM;
+  o->rows = grid_rows(g) * g->n_theta;
+  o->rows_pad = round_up(o->rows, 2 * kPairRows);
+  o->bn = 32;   // eight accumulators of bn columns fill one 256-column TMEM buffer
+  o->row_tiles = (g->n_phi + o->bn - 1) / o->bn;
+  o->b_rows_pad = o->row_tiles * o->bn;
+  o->stages = pair_stages<F>(o->bn, kEpiStageBytes);
+  yy_status st = YY_OK;
+  if (o->stages < 2 ||
+      cudaFuncSetAttribute(k_tc_pair<F, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) != cudaSuccess)
+    st = YY_ERR_NOT_SUPPORTED;
+  if (st == YY_OK) {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg =
+        pair_config(64, o->stages * pair_stage_bytes<F>(o->bn) + kSmemFixed + kEpiStageBytes, 0, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (void *)k_tc_pair<F, 3>, &cfg) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      st = YY_ERR_NOT_SUPPORTED;
+    }
+    o->pair_slots = n;
+  }
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void **ptr, size_t bytes) {
+    if (e == cudaSuccess) e = dmalloc(ptr, bytes);
+  };
+  const size_t g_bytes = (size_t)F::kPA * o->rows_pad * F::kMaxK * F::kElem;
+  const size_t t_elems = (size_t)F::kPB * o->b_rows_pad * F::kMaxK;
+  if (st == YY_OK) {
+    for (int f = 0; f < 4; ++f) {
+      A(&o->G[f], g_bytes);
+      A((void **)&o->gexp[f], o->rows_pad * sizeof(int));
+    }
+    A(&o->trig, t_elems * F::kElem);
+    for (int f = 0; f < 4 && e == cudaSuccess; ++f) e = cudaMemset(o->G[f], 0, g_bytes);
+    if (e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? YY_ERR_OOM : YY_ERR_CUDA;
+  }
+  if (st == YY_OK) {
+    // trig digits on the host: y = trig / 2, |y| <= 1/2, X = round(|y| 2^48)
+    // (exact: |y| 2^48 < 2^52), balanced digits with the sign of y
+    std::vector<double> tr((size_t)nt * g->n_phi);
+    std::vector<uint16_t> sl(t_elems, 0);
+    if (cudaMemcpy(tr.data(), g->sep_tr, tr.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      st = YY_ERR_CUDA;
+    for (int k = 0; k < g->n_phi && st == YY_OK; ++k)
+      for (int t = 0; t < nt; ++t) {
+        const double y = tr[(size_t)t * g->n_phi + k] * 0.5;
+        int d[6];
+        oz_digits((unsigned long long)floor(ldexp(fabs(y), 48) + 0.5), d);
+        for (int s2 = 0; s2 < F::kPB; ++s2)
+          sl[((size_t)s2 * o->b_rows_pad + k) * F::kMaxK + t] = bf16_int(y < 0 ? -d[s2] : d[s2]);
+      }
+    if (st == YY_OK && cudaMemcpy(o->trig, sl.data(), t_elems * F::kElem, cudaMemcpyHostToDevice) != cudaSuccess)
+      st = YY_ERR_CUDA;
+  }
+  if (st == YY_OK) {
+    bool ok = make_map<F>(&o->maps.b[0], o->trig, F::kMaxK, F::kPB * o->b_rows_pad, o->bn / 2);
+    for (int f = 0; f < 4 && ok; ++f)
+      ok = make_map<F>(&o->maps.a[f], o->G[f], F::kMaxK, F::kPA * o->rows_pad, kPairRows);
+    if (!ok) st = YY_ERR_NOT_SUPPORTED;
+  }
+  if (st != YY_OK) {
+    cudaGetLastError();
+    free_oz(o);
+    return st;
+  }
+  g->oz = o;
+  return YY_OK;
+}
+
+cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, double *gg, cudaStream_t s) {
+  typedef FormOzaki F;
+  yy_oz_tables *o = g->oz;
+  const int n_jobs = gy ? 4 : 1;
+  OzThetaArgs ta = {};
+  ta.n_shells = grid_rows(g);
+  ta.n_theta = g->n_theta;
+  ta.lmax = g->lmax;
+  ta.n_lm = g->n_lm;
+  ta.nt = 2 * g->lmax + 1;
+  ta.n_jobs = n_jobs;
+  ta.rows_pad = o->rows_pad;
+  ta.Q = g->Q;
+  ta.tab[0] = g->sep_P;
+  ta.tab[1] = g->sep_dP;
+  ta.tab[2] = g->sep_Qs;
+  for (int f = 0; f < 4; ++f) {
+    ta.G[f] = (__nv_bfloat16 *)o->G[f];
+    ta.gexp[f] = o->gexp[f];
+  }
+  const size_t warps = (size_t)o->rows * n_jobs;
+  k_theta_ozaki<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(ta);
+  g->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t comp = (size_t)g->n_r * g->n_ang;
+  double *o0[4] = {py, gy, gy ? gy + comp : nullptr, gy ? gy + 2 * comp : nullptr};
+  double *o1[4] = {pg, gg, gg ? gg + comp : nullptr, gg ? gg + 2 * comp : nullptr};
+  PairArgs a = {};
+  a.stages = o->stages;
+  a.cells = o->rows;
+  a.cell_tiles = o->rows_pad / (2 * kPairRows);
+  a.rows = g->n_phi;
+  a.row_tiles = o->row_tiles;
+  a.bn = o->bn;
+  a.kb_total = F::kMaxK * F::kElem / kRowBytes;
+  a.k_splits = 1;
+  a.kb_per_split = a.kb_total;
+  a.a_rows = o->rows_pad;
+  a.b_rows = o->b_rows_pad;
+  a.out_mode = 3;
+  a.out_split = g->n_r * g->n_theta;
+  a.ldo = g->n_phi;
+  a.n_jobs = n_jobs;
+  a.err = g->err;
+  for (int f = 0; f < n_jobs; ++f) {
+    PairJob &J = a.job[f];
+    J.out0 = o0[f];
+    J.out1 = o1[f];
+    J.cell_exp = o->gexp[f];
+    J.ta = f;
+    J.tb = 0;
+  }
+  const int tiles = a.cell_tiles * a.row_tiles * n_jobs;
+  const int pairs = tiles < o->pair_slots ? tiles : o->pair_slots;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = pair_config(pairs, o->stages * pair_stage_bytes<F>(o->bn) + kSmemFixed + kEpiStageBytes, s, attr);
+  e = cudaLaunchKernelEx(&cfg, k_tc_pair<F, 3>, o->maps, a);
+  g->launches++;
+  return e;
 }
 
 }  // namespace yy

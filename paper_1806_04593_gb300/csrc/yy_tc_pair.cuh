@@ -55,27 +55,71 @@ namespace yy {
 
 enum { KIND_F16 = 0, KIND_BF16 = 1, KIND_TF32 = 2 };
 
+// A form lists its piece products q = 0 .. kPairs - 1 (pieces pa(q) of A and
+// pb(q) of B) and the TMEM accumulator acc(q) each goes to; first(q) marks
+// the first product of its accumulator in a fill.  The split forms sum every
+// product in one accumulator.
 struct FormFP16x2 {
   typedef __half elem;
-  static constexpr int kKind = KIND_F16, kElem = 2, kPA = 2, kPB = 2, kPairs = 3;
+  static constexpr int kKind = KIND_F16, kElem = 2, kPA = 2, kPB = 2, kPairs = 3, kAccs = 1;
   __host__ __device__ static constexpr int pa(int i) { return i == 2 ? 1 : 0; }
   __host__ __device__ static constexpr int pb(int i) { return i == 1 ? 1 : 0; }
+  __host__ __device__ static constexpr int acc(int) { return 0; }
+  __host__ __device__ static constexpr bool first(int i) { return i == 0; }
 };
 
 struct FormBF16x3 {
   typedef __nv_bfloat16 elem;
-  static constexpr int kKind = KIND_BF16, kElem = 2, kPA = 3, kPB = 3, kPairs = 6;
+  static constexpr int kKind = KIND_BF16, kElem = 2, kPA = 3, kPB = 3, kPairs = 6, kAccs = 1;
   // (0,0) (0,1) (1,0) (0,2) (2,0) (1,1)
   __host__ __device__ static constexpr int pa(int i) { return i == 2 ? 1 : (i == 4 ? 2 : (i == 5 ? 1 : 0)); }
   __host__ __device__ static constexpr int pb(int i) { return i == 1 ? 1 : (i == 3 ? 2 : (i == 5 ? 1 : 0)); }
+  __host__ __device__ static constexpr int acc(int) { return 0; }
+  __host__ __device__ static constexpr bool first(int i) { return i == 0; }
 };
 
 struct FormTF32 {
   typedef float elem;
-  static constexpr int kKind = KIND_TF32, kElem = 4, kPA = 1, kPB = 1, kPairs = 1;
+  static constexpr int kKind = KIND_TF32, kElem = 4, kPA = 1, kPB = 1, kPairs = 1, kAccs = 1;
   __host__ __device__ static constexpr int pa(int) { return 0; }
   __host__ __device__ static constexpr int pb(int) { return 0; }
+  __host__ __device__ static constexpr int acc(int) { return 0; }
+  __host__ __device__ static constexpr bool first(int i) { return i == 0; }
 };
+
+// Float64 results by the Ozaki scheme: each operand row is scaled by a power
+// of two to |x| <= 1/2 and written with six balanced base-256 digits,
+// x = sum_s a_s 2^(-8 (s + 1)) + r, integers |a_s| <= 128 (exact in bf16),
+// |r| <= 2^-49: the digits of round(|x| 2^48), each taken in [-127, 128]
+// with a carry into the next.  The products of digit levels L = s + t <= 6
+// (26 of the 36) are kept; the dropped ones add up to below 2^-56.  A
+// product sum over K <= 64 is at most 64 * 128^2 = 2^20, and a level has at
+// most 6 products, so every level accumulates in one TMEM accumulator below
+// 2^23: exact in fp32.  The epilogue combines the seven levels in integers
+// and rounds once to float64.  The rounding of the digits makes the
+// representation error unbiased, so it does not add up along K.
+// Products in level order; level L has s = max(0, L - 5) .. min(L, 5).
+struct FormOzaki {
+  typedef __nv_bfloat16 elem;
+  static constexpr int kKind = KIND_BF16, kElem = 2, kPA = 6, kPB = 6, kPairs = 26, kAccs = 7;
+  static constexpr int kMaxK = 64;
+  __host__ __device__ static constexpr int s_lo(int L) { return L > 5 ? L - 5 : 0; }
+  // first product of level L (levels hold 1, 2, 3, 4, 5, 6, 5 products)
+  __host__ __device__ static constexpr int start(int L) {
+    return L <= 0 ? 0 : L == 1 ? 1 : L == 2 ? 3 : L == 3 ? 6 : L == 4 ? 10 : L == 5 ? 15 : L == 6 ? 21 : 26;
+  }
+  __host__ __device__ static constexpr int level(int i) {
+    return i < 1 ? 0 : i < 3 ? 1 : i < 6 ? 2 : i < 10 ? 3 : i < 15 ? 4 : i < 21 ? 5 : 6;
+  }
+  __host__ __device__ static constexpr int pa(int i) { return s_lo(level(i)) + i - start(level(i)); }
+  __host__ __device__ static constexpr int pb(int i) { return level(i) - pa(i); }
+  __host__ __device__ static constexpr int acc(int i) { return level(i); }
+  __host__ __device__ static constexpr bool first(int i) { return i == start(level(i)); }
+};
+static_assert(FormOzaki::start(7) == 26 && FormOzaki::level(25) == 6 && FormOzaki::pa(25) == 5 &&
+                  FormOzaki::pb(25) == 1 && FormOzaki::pa(21) == 1 && FormOzaki::first(21) &&
+                  FormOzaki::pa(20) == 5 && FormOzaki::pb(20) == 0 && !FormOzaki::first(20),
+              "Ozaki product table");
 
 constexpr int kRowBytes = 64;        // K bytes per tile row and stage: one 64-byte swizzle atom
 constexpr int kPadK = 64;            // K padding (elements) of every packed operand
@@ -200,6 +244,12 @@ __device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&v)[16
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
         "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld8_async(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -339,6 +389,59 @@ __device__ __forceinline__ float f64_to_f32(double x) {
   return __uint_as_float((hi & 0x80000000u) | (((uint32_t)e32 << 23) + m23 + up));
 }
 
+// v 2^e exactly, for |v| < 2^53 and a result in the normal range (built from
+// the bits: the top bit's position gives the exponent, the bits below it the
+// fraction); anything else takes ldexp.
+__device__ __forceinline__ double i64_ldexp(long long v, int e) {
+  if (v == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ull;
+  const unsigned long long u = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const int lz = __clzll((long long)u);
+  const int be = 1086 - lz + e;   // (63 - lz) + 1023 + e
+  if (lz < 11 || be <= 0 || be >= 2047) return ldexp((double)v, e);
+  const unsigned long long frac = ((u << lz) << 1) >> 12;
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | frac));
+}
+
+// An accumulator value of FormOzaki: an integer below 2^23 held in fp32.
+__device__ __forceinline__ int oz_int(uint32_t v) { return __float2int_rn(__uint_as_float(v)); }
+
+// The 16 float64 values of one epilogue chunk (TMEM column tcol of the first
+// accumulator, accumulators bn columns apart) from the level sums S_0 .. S_6:
+//   value = 2^ce (hi 2^32 + lo),  hi = S_0 2^16 + S_1 2^8 + S_2,
+//                                  lo = S_3 2^24 + S_4 2^16 + S_5 2^8 + S_6,
+// hi (below 2^40) and lo (below 2^48) exact in int64 and in float64; one
+// rounding, in the final addition.
+__device__ __forceinline__ void ozaki_chunk(uint32_t tcol, int bn, int ce, double *dst) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const uint32_t c = tcol + (uint32_t)(h * 8);
+    uint32_t v0[8], v1[8], v2[8];
+    long long hi[8], lo[8];
+    tmem_ld8_async(c, v0);
+    tmem_ld8_async(c + (uint32_t)bn, v1);
+    tmem_ld8_async(c + (uint32_t)(2 * bn), v2);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      hi[j] = ((long long)oz_int(v0[j]) << 16) + ((long long)oz_int(v1[j]) << 8) + (long long)oz_int(v2[j]);
+    tmem_ld8_async(c + (uint32_t)(3 * bn), v0);
+    tmem_ld8_async(c + (uint32_t)(4 * bn), v1);
+    tmem_ld8_async(c + (uint32_t)(5 * bn), v2);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      lo[j] = ((long long)oz_int(v0[j]) << 24) + ((long long)oz_int(v1[j]) << 16) + ((long long)oz_int(v2[j]) << 8);
+    tmem_ld8_async(c + (uint32_t)(6 * bn), v0);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      lo[j] += (long long)oz_int(v0[j]);
+      dst[h * 8 + j] = i64_ldexp(hi[j], ce + 32) + i64_ldexp(lo[j], ce);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // the synthesis kernel: CTA pairs, M = 256 cells x N = bn coefficient rows
 // ---------------------------------------------------------------------------
@@ -363,6 +466,7 @@ struct PairJob {
                                 // (out_mode 2: cell c < out_split -> out0 + c ldo, ...)
   const float *cell_scale, *row_scale, *row_add;
   const float *cell_add;        // out_mode 2: added to every value of the cell
+  const int *cell_exp;          // out_mode 3: power of two of a unit level-6 sum in the cell's row
   int ta, tb;                   // operand maps of this job
 };
 
@@ -375,7 +479,8 @@ struct PairArgs {
   int kb_chunk;                 // K blocks per accumulator fill; mode 0 adds the fills in registers
   int a_rows, b_rows;           // rows of one piece in the stacked A / B operands
   int out_mode;                 // 1: scaled float64 job outputs; 0: raw fp32 partial sums;
-                                // 2: scaled float64 outputs stored along the rows of each cell
+                                // 2: scaled float64 outputs stored along the rows of each cell;
+                                // 3: as 2, from the exact level sums of FormOzaki
   float *part;                  // mode 0: part[(z rows + row) part_ld + cell]
   int part_ld;
   int out_split;
@@ -496,7 +601,7 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
             }
             tc_fence_after();
           }
-          const uint32_t dacc = tmem_base + (uint32_t)(b * 256);
+          const uint32_t dacc = tmem_base + (uint32_t)(b * 256);   // accumulator a at + a bn
           const int c1 = min(nkb, c0 + chunk);
           for (int i = c0; i < c1; ++i, ++gk) {
             if (!mbar_wait_cluster(&full[s], ph, a.err)) {
@@ -508,11 +613,12 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
             const uint32_t sb = sa + F::kPA * A_SLOT;
 #pragma unroll
             for (int q = 0; q < F::kPairs; ++q) {
+              const uint32_t dq = dacc + (uint32_t)(F::acc(q) * a.bn);
 #pragma unroll
               for (int kk = 0; kk < KSTEPS; ++kk) {
                 const uint64_t da = smem_desc(sa + F::pa(q) * A_SLOT + kk * KSTEP_BYTES);
                 const uint64_t db = smem_desc(sb + F::pb(q) * B_SLOT + kk * KSTEP_BYTES);
-                mma_pair<F>(dacc, da, db, idesc, ((i - c0) | q | kk) != 0 ? 1u : 0u);
+                mma_pair<F>(dq, da, db, idesc, (((i - c0) | kk) != 0 || !F::first(q)) ? 1u : 0u);
               }
             }
             mma_commit_pair(&empty[s]);
@@ -594,11 +700,12 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
           }
         }
       }
-    } else if constexpr (OUT_MODE == 2) {
+    } else if constexpr (OUT_MODE == 2 || OUT_MODE == 3) {
       // Cells are rows of the output arrays (stride ldo) and the accumulator
       // columns run along them: each lane holds 16 consecutive values of its
       // cell's row.  They go through this warp's shared-memory block, and the
       // warp then writes two cells' 16-value runs per store instruction.
+      // Mode 3 forms the values from FormOzaki's level accumulators.
       uint8_t *wbuf = smem + S * STAGE + 512 + (size_t)(warp - 2) * kEpiWarpBytes;
       double *ebuf = reinterpret_cast<double *>(wbuf);                          // [32][kEpiPad]
       double **rowp = reinterpret_cast<double **>(wbuf + 32 * kEpiPad * 8);     // [32] output rows
@@ -611,8 +718,9 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
         const int cell0 = (2 * ct + rank) * kPairRows + quarter * 32;
         const int cell = cell0 + lane;
         const bool cell_ok = cell < a.cells;
-        const float cs = cell_ok ? J.cell_scale[cell] : 0.0f;
-        const float ca = cell_ok ? J.cell_add[cell] : 0.0f;
+        const float cs = (OUT_MODE == 2 && cell_ok) ? J.cell_scale[cell] : 0.0f;
+        const float ca = (OUT_MODE == 2 && cell_ok) ? J.cell_add[cell] : 0.0f;
+        const int ce = (OUT_MODE == 3 && cell_ok) ? J.cell_exp[cell] : 0;
         __syncwarp();   // the previous tile's row pointers are no longer read
         rowp[lane] = !cell_ok ? nullptr
                      : (cell < a.out_split) ? J.out0 + (size_t)cell * a.ldo
@@ -623,19 +731,23 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
 #pragma unroll 1
         for (int k = sub; k < n_chunks; k += kEpiPerQuarter) {
           const int row0 = rt * a.bn + k * kEpiCols;
-          uint32_t v[16];
-          tmem_ld16_async(tbase + (uint32_t)(k * kEpiCols), v);
-          float4 rs4[4];
+          if constexpr (OUT_MODE == 3) {
+            ozaki_chunk(tbase + (uint32_t)(k * kEpiCols), a.bn, ce, ebuf + lane * kEpiPad);
+          } else {
+            uint32_t v[16];
+            tmem_ld16_async(tbase + (uint32_t)(k * kEpiCols), v);
+            float4 rs4[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) rs4[q] = reinterpret_cast<const float4 *>(J.row_scale + row0)[q];
-          tmem_wait_ld();
+            for (int q = 0; q < 4; ++q) rs4[q] = reinterpret_cast<const float4 *>(J.row_scale + row0)[q];
+            tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < kEpiCols; j += 2) {
-            const float4 r4 = rs4[j >> 2];
-            const float ra = (j & 2) ? r4.z : r4.x, rb = (j & 2) ? r4.w : r4.y;
-            *reinterpret_cast<double2 *>(ebuf + lane * kEpiPad + j) =
-                make_double2(f32_to_f64(fmaf(__uint_as_float(v[j]) * cs, ra, ca)),
-                             f32_to_f64(fmaf(__uint_as_float(v[j + 1]) * cs, rb, ca)));
+            for (int j = 0; j < kEpiCols; j += 2) {
+              const float4 r4 = rs4[j >> 2];
+              const float ra = (j & 2) ? r4.z : r4.x, rb = (j & 2) ? r4.w : r4.y;
+              *reinterpret_cast<double2 *>(ebuf + lane * kEpiPad + j) =
+                  make_double2(f32_to_f64(fmaf(__uint_as_float(v[j]) * cs, ra, ca)),
+                               f32_to_f64(fmaf(__uint_as_float(v[j + 1]) * cs, rb, ca)));
+            }
           }
           __syncwarp();
           if (vec) {

@@ -30,7 +30,9 @@ YY_FP32 = 1
 YY_TF32 = 2
 YY_BF16X3 = 3
 YY_FP16X2 = 4
-PRECISIONS = {"fp64": YY_FP64, "fp32": YY_FP32, "tf32": YY_TF32, "bf16x3": YY_BF16X3, "fp16x2": YY_FP16X2}
+YY_FP64_OZAKI = 5
+PRECISIONS = {"fp64": YY_FP64, "fp32": YY_FP32, "tf32": YY_TF32, "bf16x3": YY_BF16X3, "fp16x2": YY_FP16X2,
+              "fp64_ozaki": YY_FP64_OZAKI}
 
 YY_TABLE_WEIGHTS = 0
 YY_TABLE_TBAR = 1

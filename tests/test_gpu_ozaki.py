@@ -1,0 +1,151 @@
+"""YY_FP64_OZAKI: float64 results with the synthesis's azimuthal stage on the
+tensor cores by the Ozaki scheme, against the float64 oracle at the float64
+tolerance (1e-12 relative, max-norm over the field, Phi and -grad Phi) and
+against the CUDA-core float64 path.
+
+Each operand is six balanced base-256 digits of round(|x| 2^48) under a
+per-row scale that puts |x| at most 1/2, so a product term is off by at most
+2^-49 of the scales (2^-46 of the largest |G|), with a rounding error of
+either sign; over K <= 63 terms that is about sqrt(K / 3) 2^-46 of the row's
+largest value, 7e-14 at K = 51.  2e-13 relative is the bar against the
+CUDA-core float64 path.
+"""
+
+import numpy as np
+import pytest
+
+from paper_1806_04593_gb300 import inputs
+
+from .gpu_common import gpu_solve, lib, rel_max, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-12
+TOL_VS_FP64_PATH = 2e-13
+
+
+@pytest.fixture(scope="module")
+def yy():
+    require_gpu()
+    return lib()
+
+
+_GRIDS = {}
+
+
+def _grid(yy, spec):
+    if spec.name not in _GRIDS:
+        g = yy.Grid.from_spec(spec)
+        g.prepare("fp64_ozaki")
+        _GRIDS[spec.name] = g
+    return _GRIDS[spec.name]
+
+
+@pytest.mark.parametrize("analysis", ["auto", "dense"])
+@pytest.mark.parametrize("name", ["tiny", "mid"])
+def test_ozaki_matches_oracle_and_fp64_path(yy, oracle_grid, name, analysis):
+    spec = inputs.GRIDS[name]()
+    g = _grid(yy, spec)
+    ry, rg = inputs.density_for(spec)
+    g.set_analysis(analysis)
+    try:
+        oz = gpu_solve(g, ry, rg, gradient=True, prec="fp64_ozaki")
+        f64 = gpu_solve(g, ry, rg, gradient=True, prec="fp64")
+    finally:
+        g.set_analysis("auto")
+    assert yy.yy_last_device_status(g.handle) == yy.YY_OK
+    ref = oracle_grid(spec).solve(ry, rg, gradient=True)
+    for q in ("yin", "yang"):
+        assert rel_max(oz["phi_" + q], ref["phi_" + q]) <= TOL_FP64, q
+        assert rel_max(oz["grad_" + q], ref["grad_" + q]) <= TOL_FP64, q
+    for key in oz:
+        assert rel_max(oz[key], f64[key]) <= TOL_VS_FP64_PATH, key
+
+
+def test_ozaki_production_sampled(yy, oracle_grid):
+    spec = inputs.production_grid()
+    g = _grid(yy, spec)
+    ry, rg = inputs.density_for(spec)
+    out = gpu_solve(g, ry, rg, gradient=True, prec="fp64_ozaki")
+    assert yy.yy_last_device_status(g.handle) == yy.YY_OK
+    rng = np.random.default_rng(44)
+    cells = np.sort(rng.choice(spec.n_ang, 64, replace=False))
+    ref = oracle_grid(spec).solve(ry, rg, gradient=True, cells=cells)
+    j, k = np.divmod(cells, spec.n_phi)
+    for q in ("yin", "yang"):
+        assert rel_max(out["phi_" + q][:, j, k], ref["phi_" + q]) <= TOL_FP64
+        assert rel_max(out["grad_" + q][:, :, j, k], ref["grad_" + q]) <= TOL_FP64
+
+
+def test_ozaki_ragged_and_highest_degree(yy):
+    """Sizes that are multiples of no tile (17 x 41 cells, 131 zones), and
+    l_max = 31, the largest with 2 l_max + 1 <= 64."""
+    from oracle import OracleGrid
+    for n_r, nt, npp, lmax, seed in ((131, 17, 41, 13, 45), (40, 20, 60, 31, 46)):
+        spec = inputs.GridSpec(f"ragged_oz_{lmax}", np.logspace(-2, 0, n_r + 1), nt, npp, 0.03, 0.05, lmax, 1.0)
+        rng = np.random.default_rng(seed)
+        ry = rng.uniform(0.5, 1.5, (n_r, nt, npp))
+        rg = rng.uniform(0.5, 1.5, (n_r, nt, npp))
+        g = yy.Grid.from_spec(spec)
+        try:
+            g.prepare("fp64_ozaki")
+            out = gpu_solve(g, ry, rg, gradient=True, prec="fp64_ozaki")
+            assert yy.yy_last_device_status(g.handle) == yy.YY_OK
+        finally:
+            g.close()
+        ref = OracleGrid(spec.r_edges, nt, npp, 0.03, 0.05, lmax).solve(ry, rg, gradient=True)
+        for q in ("yin", "yang"):
+            assert rel_max(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64, (lmax, q)
+            assert rel_max(out["grad_" + q], ref["grad_" + q]) <= TOL_FP64, (lmax, q)
+
+
+def test_ozaki_polar_grid(yy, oracle_grid):
+    import torch
+    spec = inputs.mid_polar_grid()
+    g = yy.Grid.from_spec(spec)
+    try:
+        g.prepare("fp64_ozaki")
+        rho, _ = inputs.pns_density(spec, 3, 0.05)
+        r = torch.as_tensor(np.ascontiguousarray(rho), device="cuda")
+        out = g.solve(r, gradient=True, prec="fp64_ozaki")
+        torch.cuda.synchronize()
+        assert yy.yy_last_device_status(g.handle) == yy.YY_OK
+        ref = oracle_grid(spec).solve(rho, gradient=True)
+        assert rel_max(out["phi"].cpu().numpy(), ref["phi"]) <= TOL_FP64
+        assert rel_max(out["grad"].cpu().numpy(), ref["grad"]) <= TOL_FP64
+    finally:
+        g.close()
+
+
+def test_ozaki_deterministic_swap_and_zero(yy):
+    spec = inputs.tiny_grid()
+    g = _grid(yy, spec)
+    ry, rg = inputs.density_for(spec)
+    a = gpu_solve(g, ry, rg, gradient=True, prec="fp64_ozaki")
+    b = gpu_solve(g, ry, rg, gradient=True, prec="fp64_ozaki")
+    c = gpu_solve(g, rg, ry, gradient=True, prec="fp64_ozaki")
+    for key in a:
+        assert np.array_equal(a[key], b[key]), key
+    assert np.array_equal(a["phi_yin"], c["phi_yang"])
+    assert np.array_equal(a["grad_yang"], c["grad_yin"])
+    z = np.zeros_like(ry)
+    for v in gpu_solve(g, z, z, gradient=True, prec="fp64_ozaki").values():
+        assert np.all(v == 0.0)
+
+
+def test_ozaki_needs_prepare_and_low_degree(yy):
+    import torch
+    spec = inputs.tiny_grid()
+    g = yy.Grid.from_spec(spec)
+    try:
+        x = torch.zeros((spec.n_r, spec.n_theta, spec.n_phi), dtype=torch.float64, device="cuda")
+        st = yy.yy_potential(g.handle, x, x, x.clone(), x.clone(), prec=yy.YY_FP64_OZAKI)
+        assert st == yy.YY_ERR_NOT_SUPPORTED
+    finally:
+        g.close()
+    big = inputs.GridSpec("oz_lmax40", np.logspace(-2, 0, 9), 12, 36, 0.05, 0.05, 40, 1.0)
+    g = yy.Grid.from_spec(big)
+    try:
+        assert yy.yy_grid_prepare(g.handle, yy.YY_FP64_OZAKI) == yy.YY_ERR_NOT_SUPPORTED
+    finally:
+        g.close()
