@@ -43,8 +43,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # 152 SMs x 2 DFMA/clk x 2 f
 # DRAM bytes (read + write) of one synthesis launch, from an ncu capture of
 # this workload (profiles/k_tc_pair_fp16x2_production.md); valid only for the
 # kernel source it was taken with, null otherwise.
-_TRAFFIC = {("fp16x2", True): (288.747520e6 + 798.676992e6,
-                               "fc6dfb7a90d3bd283a9fe27d3fe7e1920d2c330c2c9fb2a5f7d4db944c3260af")}
+_TRAFFIC = {("fp16x2", True): (288.610816e6 + 798.690816e6,
+                               "6aa090546c2e40bb454ac0d4d82167b00d3a33e8f3dced61c1d5546ae346b3a3")}
 
 
 def _recorded_traffic(prec, gradient):
@@ -360,14 +360,29 @@ def run_ours(args, dist):
     synth_ms = stage_tot["synthesis"] / prof_steps
     synth_flop = n_synth * 2.0 * (2 * spec.n_r) * grid.n_lm * spec.n_ang   # 2 M N K, K = n_lm
     total_flop = grid.flops(gradient)
-    products = {"fp16x2": 3, "bf16x3": 6, "tf32": 1, "fp64": 1, "fp32": 1}[prec]
-    pieces_bytes = {"fp16x2": 4, "bf16x3": 6, "tf32": 4, "fp64": 8, "fp32": 4}[prec]
+    products = {"fp16x2": 3, "bf16x3": 6, "tf32": 1, "fp64": 1, "fp32": 1, "fp64_ozaki": 26}[prec]
+    pieces_bytes = {"fp16x2": 4, "bf16x3": 6, "tf32": 4, "fp64": 8, "fp32": 4, "fp64_ozaki": 12}[prec]
     cells_pad = -(-spec.n_ang // 256) * 256
     k_pad = -(-grid.n_lm // 64) * 64
     synth_bytes = (n_synth * 2 * spec.n_r * spec.n_ang * 8                  # float64 outputs
                    + n_synth * cells_pad * k_pad * pieces_bytes)             # one table pass per contraction
     peaks = _measured_peaks()
-    if prec == "fp64":
+    if prec == "fp64_ozaki":
+        # separable synthesis: float64 polar stage, then the azimuthal stage as
+        # 26 digit products over rows (shell, j) x longitudes, K = 64
+        g_rows = 2 * spec.n_r * spec.n_theta
+        digit_flop = products * n_synth * 2.0 * g_rows * spec.n_phi * 64
+        synth_bytes = (n_synth * 2 * spec.n_r * spec.n_ang * 8            # float64 outputs
+                       + 2 * n_synth * g_rows * 64 * pieces_bytes)          # digit rows written, then read
+        roof = {"bound": "tensor",
+                "kernel": ("k_tc_pair<FormOzaki, 3> (azimuthal synthesis stage, digit products on tcgen05), "
+                           "timed together with the float64 polar stage k_theta_ozaki"),
+                "achieved": digit_flop / (synth_ms / 1e3) / 1e12, "peak": peaks["bf16_tflops"],
+                "unit": "TFLOP/s", "traffic": None,
+                "flops_counted": (f"hardware: {products} bf16 digit products x 2 M N K, M = 2 n_r n_theta, "
+                                  f"N = n_phi, K = 64, {n_synth} field(s)"),
+                "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)"}
+    elif prec == "fp64":
         roof = {"bound": "alu", "kernel": "k_gemm_tn<double> (synthesis, FP64 DFMA)",
                 "achieved": synth_flop / (synth_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "traffic": None,
@@ -416,24 +431,28 @@ def run_ours(args, dist):
         except yy.YYError as exc:
             fp64_path["ozaki"] = {"unavailable": str(exc)}
         else:
-            ref64 = {"phi_yin": phi_y.clone(), "phi_yang": phi_g.clone()}
-            if gradient:
-                ref64["grad_yin"], ref64["grad_yang"] = g_y.clone(), g_g.clone()
-            grid.potential(ry, rg, phi_y, phi_g, g_y, g_g, prec="fp64_ozaki", stream=stream)
-            torch.cuda.synchronize()
-            got = {"phi_yin": phi_y, "phi_yang": phi_g, "grad_yin": g_y, "grad_yang": g_g}
-            diff = max(float((got[k] - v).abs().max() / v.abs().max()) for k, v in ref64.items())
-            e0.record(stream)
-            for _ in range(3):
+            if prec == "fp64_ozaki":
+                fp64_path["ozaki"] = {"same_as": "the headline value of this line"}
+            else:
+                ref64 = {"phi_yin": phi_y.clone(), "phi_yang": phi_g.clone()}
+                if gradient:
+                    ref64["grad_yin"], ref64["grad_yang"] = g_y.clone(), g_g.clone()
                 grid.potential(ry, rg, phi_y, phi_g, g_y, g_g, prec="fp64_ozaki", stream=stream)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            msoz = e0.elapsed_time(e1) / 3
-            fp64_path["ozaki"] = {"value": 1e3 / msoz, "unit": UNIT, "ms_per_step": msoz,
-                                  "speedup_vs_fp64_path": ms64 / msoz,
-                                  "rel_max_diff_vs_fp64_path": diff,
-                                  "precision": "fp64_ozaki (float64 results; azimuthal synthesis "
-                                               "stage on tcgen05 by 8-bit slices, exact per level)"}
+                torch.cuda.synchronize()
+                got = {"phi_yin": phi_y, "phi_yang": phi_g, "grad_yin": g_y, "grad_yang": g_g}
+                diff = max(float((got[k] - v).abs().max() / v.abs().max()) for k, v in ref64.items())
+                e0.record(stream)
+                for _ in range(3):
+                    grid.potential(ry, rg, phi_y, phi_g, g_y, g_g, prec="fp64_ozaki", stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                msoz = e0.elapsed_time(e1) / 3
+                fp64_path["ozaki"] = {"value": 1e3 / msoz, "unit": UNIT, "ms_per_step": msoz,
+                                      "speedup_vs_fp64_path": ms64 / msoz,
+                                      "rel_max_diff_vs_fp64_path": diff,
+                                      "precision": "fp64_ozaki (float64 results; the azimuthal stages of "
+                                                   "analysis and synthesis as balanced 8-bit digit "
+                                                   "products on tcgen05, exact per level)"}
         solve()                                   # leave the headline form's result in place
         torch.cuda.synchronize()
 
@@ -444,7 +463,8 @@ def run_ours(args, dist):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp32": "f32", "fp16x2": "fp16x2 (fp32 accumulate, f64 scans)",
                   "bf16x3": "bf16x3 (fp32 accumulate, f64 scans)",
-                  "tf32": "tf32 (fp32 accumulate, f64 scans)"}[prec],
+                  "tf32": "tf32 (fp32 accumulate, f64 scans)",
+                  "fp64_ozaki": "f64 (Ozaki: azimuthal stages as 8-bit digit products on tcgen05, exact per level)"}[prec],
         "data": "synthetic (seeded proto-neutron-star density, l<=4 angular perturbation)",
         "config": {"workload": "1-degree Yin-Yang grid, 2 x 90 x 270 cells, n_r=550 log r in [1e-4,1], "
                                "l_max=25, Phi and -grad Phi per solve" if gradient else

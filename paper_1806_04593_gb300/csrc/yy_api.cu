@@ -303,8 +303,11 @@ yy_status yy_potential(yy_grid *g, const double *rho_yin, const double *rho_yang
     const bool separable = g->analysis_method == YY_ANALYSIS_SEPARABLE ||
                            (g->analysis_method == YY_ANALYSIS_AUTO && simt);
     const bool tc_sep = separable && !simt && tc_separable_analysis_ready(g, prec);
-    g->last_separable = tc_sep || (separable && (g->sep_ok & (prec == YY_FP64 ? 2 : 1)));
-    if (tc_sep)
+    const bool oz_an = ozaki && separable && ozaki_analysis_ready(g);
+    g->last_separable = tc_sep || oz_an || (separable && (g->sep_ok & (prec == YY_FP64 ? 2 : 1)));
+    if (oz_an)
+      e = ozaki_analysis(g, rho_yin, rho_yang, s);
+    else if (tc_sep)
       e = tc_separable_analysis(g, prec, rho_yin, rho_yang, s);
     else if (g->last_separable)
       e = analysis_separable(g, rho_yin, rho_yang, prec == YY_FP64, s);

@@ -125,6 +125,8 @@ cudaError_t analysis_separable(yy_grid *g, const double *rho_yin, const double *
                                cudaStream_t s);
 cudaError_t synthesis_separable(yy_grid *g, double *phi_yin, double *phi_yang, double *grad_yin,
                                 double *grad_yang, bool fp64, cudaStream_t s);
+// the float64 polar stage alone: A from the azimuthal sums in sep_F
+cudaError_t separable_theta_f64(yy_grid *g, cudaStream_t s);
 
 // Atot = A + D^T A(other patch), float32 products unless fp64 (yy_scan.cu)
 cudaError_t rotate_moments(yy_grid *g, bool fp64, cudaStream_t s);
@@ -185,6 +187,9 @@ cudaError_t tc_synthesis(yy_grid *g, yy_precision prec, double *phi_yin,
 yy_status ozaki_prepare(yy_grid *g);
 void ozaki_free(yy_grid *g);
 bool ozaki_ready(const yy_grid *g);
+// the separable analysis with its azimuthal stage by the same scheme (n_phi <= 320)
+bool ozaki_analysis_ready(const yy_grid *g);
+cudaError_t ozaki_analysis(yy_grid *g, const double *rho_yin, const double *rho_yang, cudaStream_t s);
 cudaError_t ozaki_synthesis(yy_grid *g, double *phi_yin, double *phi_yang, double *grad_yin, double *grad_yang,
                             cudaStream_t s);
 

@@ -638,6 +638,15 @@ cudaError_t separable_theta_partials(yy_grid *g, SepThetaPartials a, cudaStream_
   return cudaGetLastError();
 }
 
+cudaError_t separable_theta_f64(yy_grid *g, cudaStream_t s) {
+  const int nt_pad = g->sep_nt_pad;
+  const size_t smem_theta = (size_t)g->n_theta * nt_pad * sizeof(double) + (size_t)(g->n_theta + 1) * sizeof(float2);
+  k_sep_theta<double><<<grid_rows(g), 256, smem_theta, s>>>(g->n_theta, g->n_lm, g->lmax + 1, nt_pad, g->tbar,
+                                                            g->sep_tb0, g->sep_F, (const float2 *)g->sep_F0, g->A);
+  g->launches++;
+  return cudaGetLastError();
+}
+
 cudaError_t analysis_separable(yy_grid *g, const double *rho_yin, const double *rho_yang, bool fp64, cudaStream_t s) {
   if (fp64)
     return run_separable<double>(g, rho_yin, rho_yang, g->w, g->sep_az, g->tbar, g->sep_F, g->sep_phi_blocks[1], s);

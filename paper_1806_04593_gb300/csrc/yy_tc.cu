@@ -1636,9 +1636,11 @@ __host__ __device__ __forceinline__ void oz_digits(unsigned long long X, int (&d
   d[0] = (int)X;
 }
 
-// One warp per (field, row (shell, j)); lane L forms G at t = 2 L and 2 L + 1
-// with the float64 polar sums of the CUDA-core separable synthesis (l from
-// l_max down, g_phi with the cos / sin slots swapped), then the row's scale
+// One warp per (field, row (shell, j)); lane L forms G at t = L and 63 - L
+// (slot t sums l_max + 1 - (t + 1) / 2 terms, so every lane does about the
+// same work) with the float64 polar sums of the CUDA-core separable
+// synthesis (l from l_max down, g_phi with the cos / sin slots swapped),
+// then the row's scale
 // 2^e (e from the largest |G|: every |G| 2^-e < 1/2) and the digits of
 // X = round(|G| 2^(48 - e)) <= 2^47, taken from the float64 bits, each with
 // the sign of G.  A row of zeros (or of values below the normal range) gets
@@ -1652,22 +1654,30 @@ __global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
   const int qb = f < 2 ? f : 2;
   const double *q = a.Q + ((size_t)qb * a.n_shells + shell) * a.n_lm;
   const double *tj = a.tab[f <= 1 ? 0 : f - 1] + (size_t)j * a.n_lm;
-  double gv[2];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int t = 2 * lane + h;
-    double g = 0.0;
-    if (t < a.nt) {
-      const int m = (t + 1) / 2;
-      if (f < 3) {
-        for (int l = a.lmax; l >= m; --l) g = fma(q[l * l + t], tj[l * l + t], g);
-      } else if (t > 0) {
-        const int src = (t & 1) ? t + 1 : t - 1;   // cos slot <- sin coefficient, sin slot <- cos
-        for (int l = a.lmax; l >= m; --l) g = fma(q[l * l + src], tj[l * l + t], g);
-        if (!(t & 1)) g = -g;
-      }
-    }
-    gv[h] = g;
+  // both slots' terms in one loop (about l_max + 1 - 16 steps for every lane)
+  const int t0 = lane, t1 = 63 - lane;
+  const int m0 = (t0 + 1) / 2, m1 = (t1 + 1) / 2;
+  int s0 = t0, s1 = t1;                               // coefficient slots
+  if (f == 3) {                                       // cos slot <- sin coefficient, sin slot <- cos
+    s0 = (t0 & 1) ? t0 + 1 : t0 - 1;
+    s1 = (t1 & 1) ? t1 + 1 : t1 - 1;
+  }
+  const int n0 = (t0 < a.nt && (f < 3 || t0 > 0)) ? a.lmax + 1 - m0 : 0;
+  const int n1 = (t1 < a.nt && (f < 3 || t1 > 0)) ? a.lmax + 1 - m1 : 0;
+  double gv[2] = {0.0, 0.0};
+  for (int it = 0; it < n0 + n1; ++it) {
+    const bool first = it < n0;
+    const int l = a.lmax - (first ? it : it - n0);
+    const int t = first ? t0 : t1, sq = first ? s0 : s1;
+    const double v = fma(q[l * l + sq], tj[l * l + t], first ? gv[0] : gv[1]);
+    if (first)
+      gv[0] = v;
+    else
+      gv[1] = v;
+  }
+  if (f == 3) {
+    if (!(t0 & 1)) gv[0] = -gv[0];
+    if (!(t1 & 1)) gv[1] = -gv[1];
   }
   const unsigned long long b0 = (unsigned long long)__double_as_longlong(gv[0]);
   const unsigned long long b1 = (unsigned long long)__double_as_longlong(gv[1]);
@@ -1688,15 +1698,76 @@ __global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
     oz_digits(X, d[h]);
   }
   const size_t stride = (size_t)a.rows_pad * FormOzaki::kMaxK;
-  __nv_bfloat16 *dst = a.G[f] + (size_t)row * FormOzaki::kMaxK + 2 * lane;
+  __nv_bfloat16 *dst = a.G[f] + (size_t)row * FormOzaki::kMaxK;
 #pragma unroll
   for (int sl = 0; sl < 6; ++sl) {
-    const float v0 = (b0 >> 63) ? -(float)d[0][sl] : (float)d[0][sl];
-    const float v1 = (b1 >> 63) ? -(float)d[1][sl] : (float)d[1][sl];
-    *reinterpret_cast<__nv_bfloat162 *>(dst + sl * stride) = __floats2bfloat162_rn(v0, v1);
+    dst[sl * stride + lane] = __float2bfloat16_rn((b0 >> 63) ? -(float)d[0][sl] : (float)d[0][sl]);
+    dst[sl * stride + 63 - lane] = __float2bfloat16_rn((b1 >> 63) ? -(float)d[1][sl] : (float)d[1][sl]);
   }
   // value = 2^(e + 1 - 64) (digit sums): trig scale 2^1, digit weights 2^-64
   if (lane == 0) a.gexp[f][row] = exm == 0 ? 0 : e + 1 - 64;
+}
+
+// The weighted densities of the separable analysis, rho w, as digit rows for
+// FormOzakiWide: one warp per row (shell, j); lane L takes the pairs
+// k = 2 L + 64 c.  rho w is the float64 product of the CUDA-core path; the
+// row's scale and digits as in k_theta_ozaki, and the row exponent of a unit
+// level-6 sum includes the table's scale 2^eb.
+struct OzRhoArgs {
+  int n_r, n_theta, n_phi, rows, k_pad, rows_pad, eb;
+  const double *rho0, *rho1;    // [n_r][n_theta][n_phi] per patch (rho1 NULL on a polar grid)
+  const double *w;              // [n_theta][n_phi]
+  __nv_bfloat16 *X;             // [6][rows_pad][k_pad]
+  int *rexp;                    // [rows_pad]
+};
+
+__global__ void __launch_bounds__(256) k_rhow_ozaki(OzRhoArgs a) {
+  constexpr int C = FormOzakiWide::kMaxK / 64;
+  const int row = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (row >= a.rows) return;
+  const int shell = row / a.n_theta, j = row % a.n_theta;
+  const int p = shell / a.n_r, i = shell % a.n_r;
+  const double *rho = (p == 0 ? a.rho0 : a.rho1) + ((size_t)i * a.n_theta + j) * a.n_phi;
+  const double *wj = a.w + (size_t)j * a.n_phi;
+  unsigned long long bits[C][2];
+  unsigned long long mb = 0ull;
+#pragma unroll
+  for (int c = 0; c < C; ++c)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = 2 * lane + 64 * c + h;
+      const double v = k < a.n_phi ? rho[k] * wj[k] : 0.0;
+      bits[c][h] = (unsigned long long)__double_as_longlong(v);
+      mb = max(mb, bits[c][h] & 0x7FFFFFFFFFFFFFFFull);
+    }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
+  const int exm = (int)(mb >> 52);
+  const int e = exm - 1021;
+  const size_t stride = (size_t)a.rows_pad * a.k_pad;
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int k0 = 2 * lane + 64 * c;
+    if (k0 >= a.k_pad) break;
+    int d[2][6];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int ex = (int)((bits[c][h] >> 52) & 0x7FFu);
+      const int sh = 1027 - ex + e;
+      unsigned long long X = 0ull;
+      if (exm != 0 && ex != 0 && sh < 64)
+        X = ((((bits[c][h] & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> (sh - 1)) + 1ull) >> 1;
+      oz_digits(X, d[h]);
+    }
+    __nv_bfloat16 *dst = a.X + (size_t)row * a.k_pad + k0;
+#pragma unroll
+    for (int sl = 0; sl < 6; ++sl) {
+      const float v0 = (bits[c][0] >> 63) ? -(float)d[0][sl] : (float)d[0][sl];
+      const float v1 = (bits[c][1] >> 63) ? -(float)d[1][sl] : (float)d[1][sl];
+      *reinterpret_cast<__nv_bfloat162 *>(dst + sl * stride) = __floats2bfloat162_rn(v0, v1);
+    }
+  }
+  if (lane == 0) a.rexp[row] = exm == 0 ? 0 : e + a.eb - 64;
 }
 
 }  // namespace yy
@@ -1707,6 +1778,12 @@ struct yy_oz_tables {
   int *gexp[4];                 // per field: [rows_pad]
   void *trig;                   // slices of trig / 2: [6][b_rows_pad][64]
   yy::PairMaps maps;
+  // analysis (FormOzakiWide): rho w digit rows as operand A, the azimuthal table as operand B
+  int an_ok, an_kpad, an_bn, an_row_tiles, an_b_rows_pad, an_stages, an_slots, an_eb;
+  void *an_x;                   // [6][rows_pad][an_kpad]
+  int *an_exp;                  // [rows_pad]
+  void *an_az;                  // [6][an_b_rows_pad][an_kpad]
+  yy::PairMaps an_maps;
 };
 
 namespace yy {
@@ -1718,6 +1795,9 @@ static void free_oz(yy_oz_tables *o) {
     if (o->gexp[f]) cudaFree(o->gexp[f]);
   }
   if (o->trig) cudaFree(o->trig);
+  if (o->an_x) cudaFree(o->an_x);
+  if (o->an_exp) cudaFree(o->an_exp);
+  if (o->an_az) cudaFree(o->an_az);
   delete o;
 }
 
@@ -1728,6 +1808,8 @@ void ozaki_free(yy_grid *g) {
 
 bool ozaki_ready(const yy_grid *g) { return g->oz != nullptr; }
 
+bool ozaki_analysis_ready(const yy_grid *g) { return g->oz != nullptr && g->oz->an_ok; }
+
 // bf16 bits of a small integer (|v| <= 255: exact, the low 16 bits of the
 // fp32 pattern are zero)
 static uint16_t bf16_int(int v) {
@@ -1735,6 +1817,124 @@ static uint16_t bf16_int(int v) {
   uint32_t u;
   memcpy(&u, &f, 4);
   return (uint16_t)(u >> 16);
+}
+
+// Tables of the analysis by the Ozaki scheme; leaves an_ok = 0 (the float64
+// analysis serves) where the rows are longer than FormOzakiWide takes.
+static yy_status ozaki_prepare_analysis(yy_grid *g, yy_oz_tables *o) {
+  typedef FormOzakiWide F;
+  const int nt = 2 * g->lmax + 1;
+  if (g->n_phi > F::kMaxK || !g->sep_az || !g->sep_F) return YY_OK;
+  o->an_kpad = round_up(g->n_phi, kPadK);
+  o->an_bn = 16;   // eleven accumulators of bn columns within one 256-column TMEM buffer
+  o->an_row_tiles = (nt + o->an_bn - 1) / o->an_bn;
+  o->an_b_rows_pad = o->an_row_tiles * o->an_bn;
+  o->an_stages = pair_stages<F>(o->an_bn, kEpiStageBytes);
+  if (o->an_stages < 2 ||
+      cudaFuncSetAttribute(k_tc_pair<F, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) != cudaSuccess)
+    return YY_OK;
+  {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg =
+        pair_config(64, o->an_stages * pair_stage_bytes<F>(o->an_bn) + kSmemFixed + kEpiStageBytes, 0, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (void *)k_tc_pair<F, 3>, &cfg) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      return YY_OK;
+    }
+    o->an_slots = n;
+  }
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void **ptr, size_t bytes) {
+    if (e == cudaSuccess) e = dmalloc(ptr, bytes);
+  };
+  const size_t x_bytes = (size_t)F::kPA * o->rows_pad * o->an_kpad * F::kElem;
+  const size_t b_elems = (size_t)F::kPB * o->an_b_rows_pad * o->an_kpad;
+  A(&o->an_x, x_bytes);
+  A((void **)&o->an_exp, o->rows_pad * sizeof(int));
+  A(&o->an_az, b_elems * F::kElem);
+  if (e == cudaSuccess) e = cudaMemset(o->an_x, 0, x_bytes);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? YY_ERR_OOM : YY_ERR_CUDA;
+  // the azimuthal table az[k][t] (rows of sep_nt_pad) as operand B, rows t:
+  // one scale 2^eb for all of it (every row's largest value is about d_phi)
+  const int ntp = g->sep_nt_pad;
+  std::vector<double> az((size_t)g->n_phi * ntp);
+  std::vector<uint16_t> sl(b_elems, 0);
+  if (cudaMemcpy(az.data(), g->sep_az, az.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return YY_ERR_CUDA;
+  double mx = 0.0;
+  for (int k = 0; k < g->n_phi; ++k)
+    for (int t = 0; t < nt; ++t) mx = fmax(mx, fabs(az[(size_t)k * ntp + t]));
+  int E2 = 0;
+  frexp(mx, &E2);   // mx < 2^E2
+  o->an_eb = E2 + 1;
+  for (int k = 0; k < g->n_phi && mx > 0.0; ++k)
+    for (int t = 0; t < nt; ++t) {
+      const double y = ldexp(az[(size_t)k * ntp + t], -o->an_eb);   // |y| < 1/2
+      int d[6];
+      oz_digits((unsigned long long)floor(ldexp(fabs(y), 48) + 0.5), d);
+      for (int s2 = 0; s2 < F::kPB; ++s2)
+        sl[((size_t)s2 * o->an_b_rows_pad + t) * o->an_kpad + k] = bf16_int(y < 0 ? -d[s2] : d[s2]);
+    }
+  if (cudaMemcpy(o->an_az, sl.data(), b_elems * F::kElem, cudaMemcpyHostToDevice) != cudaSuccess) return YY_ERR_CUDA;
+  if (!make_map<F>(&o->an_maps.a[0], o->an_x, o->an_kpad, F::kPA * o->rows_pad, kPairRows) ||
+      !make_map<F>(&o->an_maps.b[0], o->an_az, o->an_kpad, F::kPB * o->an_b_rows_pad, o->an_bn / 2))
+    return YY_ERR_NOT_SUPPORTED;
+  o->an_ok = 1;
+  return YY_OK;
+}
+
+cudaError_t ozaki_analysis(yy_grid *g, const double *ry, const double *rg, cudaStream_t s) {
+  typedef FormOzakiWide F;
+  yy_oz_tables *o = g->oz;
+  OzRhoArgs ra = {};
+  ra.n_r = g->n_r;
+  ra.n_theta = g->n_theta;
+  ra.n_phi = g->n_phi;
+  ra.rows = o->rows;
+  ra.k_pad = o->an_kpad;
+  ra.rows_pad = o->rows_pad;
+  ra.eb = o->an_eb;
+  ra.rho0 = ry;
+  ra.rho1 = rg;
+  ra.w = g->w;
+  ra.X = (__nv_bfloat16 *)o->an_x;
+  ra.rexp = o->an_exp;
+  k_rhow_ozaki<<<(unsigned)(((size_t)o->rows * 32 + 255) / 256), 256, 0, s>>>(ra);
+  g->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  PairArgs a = {};
+  a.stages = o->an_stages;
+  a.cells = o->rows;
+  a.cell_tiles = o->rows_pad / (2 * kPairRows);
+  a.rows = 2 * g->lmax + 1;
+  a.row_tiles = o->an_row_tiles;
+  a.bn = o->an_bn;
+  a.kb_total = o->an_kpad * F::kElem / kRowBytes;
+  a.k_splits = 1;
+  a.kb_per_split = a.kb_total;
+  a.a_rows = o->rows_pad;
+  a.b_rows = o->an_b_rows_pad;
+  a.out_mode = 3;
+  a.out_split = o->rows;
+  a.ldo = g->sep_nt_pad;
+  a.n_jobs = 1;
+  a.err = g->err;
+  a.job[0].out0 = g->sep_F;
+  a.job[0].out1 = g->sep_F;
+  a.job[0].cell_exp = o->an_exp;
+  a.job[0].ta = 0;
+  a.job[0].tb = 0;
+  const int tiles = a.cell_tiles * a.row_tiles;
+  const int pairs = tiles < o->an_slots ? tiles : o->an_slots;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg =
+      pair_config(pairs, o->an_stages * pair_stage_bytes<F>(o->an_bn) + kSmemFixed + kEpiStageBytes, s, attr);
+  e = cudaLaunchKernelEx(&cfg, k_tc_pair<F, 3>, o->an_maps, a);
+  g->launches++;
+  if (e != cudaSuccess) return e;
+  return separable_theta_f64(g, s);
 }
 
 yy_status ozaki_prepare(yy_grid *g) {
@@ -1804,6 +2004,7 @@ yy_status ozaki_prepare(yy_grid *g) {
       ok = make_map<F>(&o->maps.a[f], o->G[f], F::kMaxK, F::kPA * o->rows_pad, kPairRows);
     if (!ok) st = YY_ERR_NOT_SUPPORTED;
   }
+  if (st == YY_OK) st = ozaki_prepare_analysis(g, o);
   if (st != YY_OK) {
     cudaGetLastError();
     free_oz(o);

@@ -115,7 +115,24 @@ struct FormOzaki {
   __host__ __device__ static constexpr int pb(int i) { return level(i) - pa(i); }
   __host__ __device__ static constexpr int acc(int i) { return level(i); }
   __host__ __device__ static constexpr bool first(int i) { return i == start(level(i)); }
+  // accumulators of level L: acc_base(L) .. + n_acc(L) - 1
+  __host__ __device__ static constexpr int acc_base(int L) { return L; }
+  __host__ __device__ static constexpr int n_acc(int) { return 1; }
 };
+
+// The same digits and products for longer K (up to 320): a product's sum is
+// at most K 2^14, so an accumulator takes at most 3 products (3 * 341 * 2^14
+// < 2^24) and levels 3-6 use two accumulators each: eleven in all.
+struct FormOzakiWide : FormOzaki {
+  static constexpr int kAccs = 11, kMaxK = 320;
+  __host__ __device__ static constexpr int acc_base(int L) { return L <= 3 ? L : 3 + 2 * (L - 3); }
+  __host__ __device__ static constexpr int n_acc(int L) { return L <= 2 ? 1 : 2; }
+  __host__ __device__ static constexpr int acc(int i) { return acc_base(level(i)) + (pa(i) - s_lo(level(i))) / 3; }
+  __host__ __device__ static constexpr bool first(int i) { return (pa(i) - s_lo(level(i))) % 3 == 0; }
+};
+static_assert(FormOzakiWide::acc(9) == 4 && FormOzakiWide::acc(25) == 10 && FormOzakiWide::acc(21) == 9 &&
+                  FormOzakiWide::first(24) && !FormOzakiWide::first(25) && FormOzakiWide::acc(14) == 6,
+              "wide Ozaki product table");
 static_assert(FormOzaki::start(7) == 26 && FormOzaki::level(25) == 6 && FormOzaki::pa(25) == 5 &&
                   FormOzaki::pb(25) == 1 && FormOzaki::pa(21) == 1 && FormOzaki::first(21) &&
                   FormOzaki::pa(20) == 5 && FormOzaki::pb(20) == 0 && !FormOzaki::first(20),
@@ -403,42 +420,59 @@ __device__ __forceinline__ double i64_ldexp(long long v, int e) {
   return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | frac));
 }
 
-// An accumulator value of FormOzaki: an integer below 2^23 held in fp32.
+// An accumulator value of the Ozaki forms: an integer below 2^24 held in fp32.
 __device__ __forceinline__ int oz_int(uint32_t v) { return __float2int_rn(__uint_as_float(v)); }
 
-// The 16 float64 values of one epilogue chunk (TMEM column tcol of the first
-// accumulator, accumulators bn columns apart) from the level sums S_0 .. S_6:
+// Level sum S_L of 8 columns: the level's accumulators (one or two, bn
+// columns apart from tcol onwards) added as integers (below 2^25).
+template <class F>
+__device__ __forceinline__ void oz_level(uint32_t tcol, int bn, int L, int (&S)[8]) {
+  uint32_t v[8];
+  tmem_ld8_async(tcol + (uint32_t)(F::acc_base(L) * bn), v);
+  tmem_wait_ld();
+#pragma unroll
+  for (int j = 0; j < 8; ++j) S[j] = oz_int(v[j]);
+  if (F::n_acc(L) == 2) {
+    tmem_ld8_async(tcol + (uint32_t)((F::acc_base(L) + 1) * bn), v);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 8; ++j) S[j] += oz_int(v[j]);
+  }
+}
+
+// The 8 float64 values of one epilogue chunk (TMEM column tcol) from the
+// level sums S_0 .. S_6:
 //   value = 2^ce (hi 2^32 + lo),  hi = S_0 2^16 + S_1 2^8 + S_2,
 //                                  lo = S_3 2^24 + S_4 2^16 + S_5 2^8 + S_6,
-// hi (below 2^40) and lo (below 2^48) exact in int64 and in float64; one
+// hi (below 2^42) and lo (below 2^50) exact in int64 and in float64; one
 // rounding, in the final addition.
+template <class F>
 __device__ __forceinline__ void ozaki_chunk(uint32_t tcol, int bn, int ce, double *dst) {
+  int S[8];
+  long long hi[8], lo[8];
+  oz_level<F>(tcol, bn, 0, S);
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const uint32_t c = tcol + (uint32_t)(h * 8);
-    uint32_t v0[8], v1[8], v2[8];
-    long long hi[8], lo[8];
-    tmem_ld8_async(c, v0);
-    tmem_ld8_async(c + (uint32_t)bn, v1);
-    tmem_ld8_async(c + (uint32_t)(2 * bn), v2);
-    tmem_wait_ld();
+  for (int j = 0; j < 8; ++j) hi[j] = (long long)S[j] << 16;
+  oz_level<F>(tcol, bn, 1, S);
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-      hi[j] = ((long long)oz_int(v0[j]) << 16) + ((long long)oz_int(v1[j]) << 8) + (long long)oz_int(v2[j]);
-    tmem_ld8_async(c + (uint32_t)(3 * bn), v0);
-    tmem_ld8_async(c + (uint32_t)(4 * bn), v1);
-    tmem_ld8_async(c + (uint32_t)(5 * bn), v2);
-    tmem_wait_ld();
+  for (int j = 0; j < 8; ++j) hi[j] += (long long)S[j] << 8;
+  oz_level<F>(tcol, bn, 2, S);
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-      lo[j] = ((long long)oz_int(v0[j]) << 24) + ((long long)oz_int(v1[j]) << 16) + ((long long)oz_int(v2[j]) << 8);
-    tmem_ld8_async(c + (uint32_t)(6 * bn), v0);
-    tmem_wait_ld();
+  for (int j = 0; j < 8; ++j) hi[j] += (long long)S[j];
+  oz_level<F>(tcol, bn, 3, S);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      lo[j] += (long long)oz_int(v0[j]);
-      dst[h * 8 + j] = i64_ldexp(hi[j], ce + 32) + i64_ldexp(lo[j], ce);
-    }
+  for (int j = 0; j < 8; ++j) lo[j] = (long long)S[j] << 24;
+  oz_level<F>(tcol, bn, 4, S);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) lo[j] += (long long)S[j] << 16;
+  oz_level<F>(tcol, bn, 5, S);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) lo[j] += (long long)S[j] << 8;
+  oz_level<F>(tcol, bn, 6, S);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    lo[j] += (long long)S[j];
+    dst[j] = i64_ldexp(hi[j], ce + 32) + i64_ldexp(lo[j], ce);
   }
 }
 
@@ -728,12 +762,43 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
         if (!mbar_wait_cluster(&tfull[b], (it >> 1) & 1, a.err)) break;
         tc_fence_after();
         const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
+        if constexpr (OUT_MODE == 3) {
+          // 8-column chunks, so that every epilogue warp takes part at bn = 32
+          for (int k = sub; k < a.bn / 8; k += kEpiPerQuarter) {
+            const int row0 = rt * a.bn + k * 8;
+            ozaki_chunk<F>(tbase + (uint32_t)(k * 8), a.bn, ce, ebuf + lane * kEpiPad);
+            __syncwarp();
+            if (vec) {
+              // lanes 4 c' + e: cell 8 q + c', values 2 e and 2 e + 1 of the run
+              const int e = lane & 3, row = row0 + 2 * e;
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const int c = 8 * q + (lane >> 2);
+                double *orow = rowp[c];
+                const double2 val = *reinterpret_cast<const double2 *>(ebuf + c * kEpiPad + 2 * e);
+                if (orow != nullptr) {
+                  if (row + 1 < a.rows)
+                    *reinterpret_cast<double2 *>(orow + row) = val;
+                  else if (row < a.rows)
+                    orow[row] = val.x;
+                }
+              }
+            } else {
+              const int e = lane & 7, row = row0 + e;
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const int c = 4 * q + (lane >> 3);
+                double *orow = rowp[c];
+                if (orow != nullptr && row < a.rows) orow[row] = ebuf[c * kEpiPad + e];
+              }
+            }
+            __syncwarp();
+          }
+        } else {
 #pragma unroll 1
         for (int k = sub; k < n_chunks; k += kEpiPerQuarter) {
           const int row0 = rt * a.bn + k * kEpiCols;
-          if constexpr (OUT_MODE == 3) {
-            ozaki_chunk(tbase + (uint32_t)(k * kEpiCols), a.bn, ce, ebuf + lane * kEpiPad);
-          } else {
+          {
             uint32_t v[16];
             tmem_ld16_async(tbase + (uint32_t)(k * kEpiCols), v);
             float4 rs4[4];
@@ -775,6 +840,7 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
             }
           }
           __syncwarp();
+        }
         }
         tc_fence_before();
         __syncwarp();

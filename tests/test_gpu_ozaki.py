@@ -50,10 +50,16 @@ def test_ozaki_matches_oracle_and_fp64_path(yy, oracle_grid, name, analysis):
     g.set_analysis(analysis)
     try:
         oz = gpu_solve(g, ry, rg, gradient=True, prec="fp64_ozaki")
+        n_oz = yy.yy_last_launch_count(g.handle)
         f64 = gpu_solve(g, ry, rg, gradient=True, prec="fp64")
+        n_64 = yy.yy_last_launch_count(g.handle)
     finally:
         g.set_analysis("auto")
     assert yy.yy_last_device_status(g.handle) == yy.YY_OK
+    if analysis == "auto":
+        # separable both ways; the emulated analysis and synthesis each launch
+        # one kernel more (the digit rows) than their float64 counterparts
+        assert n_oz == n_64 + 2, (n_oz, n_64)
     ref = oracle_grid(spec).solve(ry, rg, gradient=True)
     for q in ("yin", "yang"):
         assert rel_max(oz["phi_" + q], ref["phi_" + q]) <= TOL_FP64, q

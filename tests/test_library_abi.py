@@ -73,3 +73,18 @@ def test_invalid_arguments_rejected_on_host(lib_path):
     assert yy.yy_grid_set_analysis(None, yy.YY_ANALYSIS_DENSE) == yy.YY_ERR_INVALID_ARG
     assert yy.yy_last_device_status(None) == yy.YY_ERR_INVALID_ARG
     yy.yy_destroy(None)
+
+
+def test_binding_constants_match_header():
+    """Every enumerator of include/yy.h that the Python binding names has the
+    header's value (precisions, statuses, tables, evaluations)."""
+    from paper_1806_04593_gb300 import yy
+    text = open(os.path.join(ROOT, "include", "yy.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    values = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(YY_[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    assert values["YY_FP64_OZAKI"] == 5
+    shared = [n for n in values if hasattr(yy, n)]
+    assert len(shared) >= 15
+    for name in shared:
+        assert getattr(yy, name) == values[name], name
+    assert yy.PRECISIONS["fp64_ozaki"] == values["YY_FP64_OZAKI"]
