@@ -141,3 +141,34 @@ def test_batched_workload_tuned_fp16x2(yy, oracle_grid):
             assert rel_max(o[3].cpu().numpy()[:, :, j, k], ref_o["grad_yang"]) <= 1e-5, f
         del ref
     b.close()
+
+
+def test_batch_fp64_ozaki_tuned_matches_fp64(yy):
+    """The float64 results by the Ozaki scheme through the batch: tuned,
+    captured in one graph, every field within 2e-13 of the float64 batch and
+    bitwise equal to the same field solved alone with the evaluation the
+    tuner picked for it."""
+    import torch
+    dev = torch.device("cuda", 0)
+    specs = _small_specs()
+    b = yy.Batch(specs)
+    chosen = b.tune("fp64_ozaki", gradient=True, reps=1)
+    rho, out = _fields(specs, dev)
+    _, ref = _fields(specs, dev)
+    _run(b, rho, out, "fp64_ozaki")
+    _run(b, rho, ref, "fp64")
+    torch.cuda.synchronize()
+    assert b.device_status() == yy.YY_OK
+    for sp, o, r in zip(specs, out, ref):
+        for x, y in zip(o, r):
+            assert rel_max(x.cpu().numpy(), y.cpu().numpy()) <= 2e-13, sp.name
+    names = {yy.ANALYSES[k]: k for k in yy.ANALYSES}
+    for f in (0, 3):
+        g = yy.Grid.from_spec(specs[f])
+        g.prepare("fp64_ozaki")
+        g.set_analysis(names[chosen[f]])
+        alone = g.solve(rho[f][0], rho[f][1], gradient=True, prec="fp64_ozaki")
+        torch.cuda.synchronize()
+        assert torch.equal(alone["phi_yin"], out[f][0]) and torch.equal(alone["grad_yang"], out[f][3]), f
+        g.close()
+    b.close()
