@@ -75,15 +75,17 @@ typedef enum {
  *   YY_FP16X2 operands split into 2 scaled fp16 terms, 3 cross products,
  *             fp32 accumulation per K chunk, chunks summed in float64.
  *   YY_FP64_OZAKI  float64 results (the YY_FP64 tolerance) with the
- *             synthesis's azimuthal stage on tcgen05 tensor cores by the
- *             Ozaki scheme: the polar-stage rows G and the trig table cut
- *             into six 8-bit fixed-point slices (integers exact in bf16)
- *             under a power-of-two scale per row, the 21 slice products of
- *             levels <= 5 accumulated exactly in fp32 per level, levels
- *             combined in integers and rounded once to float64.  The
- *             analysis, the scans and the polar stage are float64 on CUDA
- *             cores as for YY_FP64.  Needs yy_grid_prepare and
- *             2 l_max + 1 <= 64 (l_max <= 31).                             */
+ *             azimuthal stages of the separable analysis and synthesis on
+ *             tcgen05 tensor cores by the Ozaki scheme: the rows (rho w, the
+ *             polar-stage sums G) and the azimuthal / trig tables written as
+ *             six balanced 8-bit digits (integers exact in bf16) under a
+ *             power-of-two scale per row, the 26 digit products of levels
+ *             <= 6 accumulated exactly in fp32 per level, levels combined in
+ *             integers and rounded once to float64.  The polar stages, the
+ *             combination of the patches and the scans are float64 on CUDA
+ *             cores as for YY_FP64 (and so is the analysis with
+ *             YY_ANALYSIS_DENSE, or with more than 320 cells per row).
+ *             Needs yy_grid_prepare and 2 l_max + 1 <= 64 (l_max <= 31).    */
 typedef enum {
   YY_FP64 = 0,
   YY_FP32 = 1,
