@@ -43,8 +43,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # 152 SMs x 2 DFMA/clk x 2 f
 # DRAM bytes (read + write) of one synthesis launch, from an ncu capture of
 # this workload (profiles/k_tc_pair_fp16x2_production.md); valid only for the
 # kernel source it was taken with, null otherwise.
-_TRAFFIC = {("fp16x2", True): (288.610816e6 + 798.690816e6,
-                               "6aa090546c2e40bb454ac0d4d82167b00d3a33e8f3dced61c1d5546ae346b3a3")}
+_TRAFFIC = {("fp16x2", True): (288.019712e6 + 798.214144e6,
+                               "ce479479ba295f6eab961a966c99cc15a9732d09c989e51a2e66836c17c1a6fb")}
 
 
 def _recorded_traffic(prec, gradient):
