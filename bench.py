@@ -382,16 +382,20 @@ def run_ours(args, dist):
                 "flops_counted": (f"hardware: {products} bf16 digit products x 2 M N K, M = 2 n_r n_theta, "
                                   f"N = n_phi, K = 64, {n_synth} field(s)"),
                 "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)"}
-    elif prec == "fp64":
-        roof = {"bound": "alu", "kernel": "k_gemm_tn<double> (synthesis, FP64 DFMA)",
-                "achieved": synth_flop / (synth_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "traffic": None,
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz"}
-    elif prec == "fp32":
-        roof = {"bound": "alu", "kernel": "k_gemm_tn<float> (synthesis, FP32 FFMA)",
-                "achieved": synth_flop / (synth_ms / 1e3) / 1e12,
-                "peak": 152 * 128 * 2 * 2.070e9 / 1e12, "unit": "TFLOP/s", "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz"}
+    elif prec in ("fp64", "fp32"):
+        # the CUDA-core forms synthesise in separable form by default: a polar
+        # stage (K = n_lm per theta row) and an azimuthal one (K = 2 l_max + 1)
+        g_rows = 2 * spec.n_r * spec.n_theta
+        sep_flop = n_synth * (2.0 * g_rows * grid.n_lm + 2.0 * g_rows * spec.n_phi * (2 * spec.lmax + 1))
+        t = "double" if prec == "fp64" else "float"
+        roof = {"bound": "alu", "kernel": f"k_sep_synth<{t}> (separable synthesis, CUDA cores)",
+                "achieved": sep_flop / (synth_ms / 1e3) / 1e12, "unit": "TFLOP/s", "traffic": None,
+                "flops_counted": "2 x (theta-stage + phi-stage multiply-adds) of the separable synthesis"}
+        if prec == "fp64":
+            roof.update(peak=FP64_PEAK_TFLOPS, peak_source="derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz")
+        else:
+            roof.update(peak=152 * 128 * 2 * 2.070e9 / 1e12,
+                        peak_source="derived: 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz")
     else:
         ratio = 0.5 if prec == "tf32" else 1.0
         roof = {"bound": "tensor", "kernel": f"k_tc_pair<{prec}> (synthesis, tcgen05 cta_group::2)",
