@@ -155,3 +155,33 @@ def test_ozaki_needs_prepare_and_low_degree(yy):
         assert yy.yy_grid_prepare(g.handle, yy.YY_FP64_OZAKI) == yy.YY_ERR_NOT_SUPPORTED
     finally:
         g.close()
+
+
+def test_ozaki_long_rows_keep_the_float64_analysis(yy, oracle_grid):
+    """A grid with more than 320 longitudes: the digit rows of the analysis
+    would not stay exact, so that stage stays float64 (one launch fewer than
+    the emulated analysis) while the synthesis runs on the digits; against
+    the oracle on sampled cells."""
+    import torch
+    spec = inputs.polar_grid(np.logspace(-3, 0, 41), 90, 360, 20, "polar_360_oz")
+    g = yy.Grid.from_spec(spec)
+    try:
+        g.prepare("fp64_ozaki")
+        rho, _ = inputs.pns_density(spec, 7, 0.05)
+        r = torch.as_tensor(np.ascontiguousarray(rho), device="cuda")
+        out = g.solve(r, gradient=True, prec="fp64_ozaki")
+        torch.cuda.synchronize()
+        n_oz = yy.yy_last_launch_count(g.handle)
+        g.solve(r, gradient=True, prec="fp64")
+        torch.cuda.synchronize()
+        n_64 = yy.yy_last_launch_count(g.handle)
+        assert yy.yy_last_device_status(g.handle) == yy.YY_OK
+        assert n_oz == n_64 + 1, (n_oz, n_64)     # only the synthesis adds its digit rows
+        rng = np.random.default_rng(47)
+        cells = np.sort(rng.choice(spec.n_ang, 64, replace=False))
+        ref = oracle_grid(spec).solve(rho, gradient=True, cells=cells)
+        j, k = np.divmod(cells, spec.n_phi)
+        assert rel_max(out["phi"].cpu().numpy()[:, j, k], ref["phi"]) <= TOL_FP64
+        assert rel_max(out["grad"].cpu().numpy()[:, :, j, k], ref["grad"]) <= TOL_FP64
+    finally:
+        g.close()
