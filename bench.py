@@ -43,8 +43,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # 152 SMs x 2 DFMA/clk x 2 f
 # DRAM bytes (read + write) of one synthesis launch, from an ncu capture of
 # this workload (profiles/k_tc_pair_fp16x2_production.md); valid only for the
 # kernel source it was taken with, null otherwise.
-_TRAFFIC = {("fp16x2", True): (288.019712e6 + 798.214144e6,
-                               "ce479479ba295f6eab961a966c99cc15a9732d09c989e51a2e66836c17c1a6fb")}
+_TRAFFIC = {("fp16x2", True): (288.576512e6 + 798.440192e6,
+                               "933feec6e70168707e470471a68dd3cfee2a75552822e0b5b580f626169b9a4c")}
 
 
 def _recorded_traffic(prec, gradient):

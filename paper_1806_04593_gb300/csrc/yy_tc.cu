@@ -1709,7 +1709,7 @@ __global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
 }
 
 // The weighted densities of the separable analysis, rho w, as digit rows for
-// FormOzakiWide: one warp per row (shell, j); lane L takes the pairs
+// the analysis: one warp per row (shell, j); lane L takes the pairs
 // k = 2 L + 64 c.  rho w is the float64 product of the CUDA-core path; the
 // row's scale and digits as in k_theta_ozaki, and the row exponent of a unit
 // level-6 sum includes the table's scale 2^eb.
@@ -1722,7 +1722,7 @@ struct OzRhoArgs {
 };
 
 __global__ void __launch_bounds__(256) k_rhow_ozaki(OzRhoArgs a) {
-  constexpr int C = FormOzakiWide::kMaxK / 64;
+  constexpr int C = FormOzaki::kFillK * FormOzaki::kMaxFills / 64;
   const int row = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (row >= a.rows) return;
   const int shell = row / a.n_theta, j = row % a.n_theta;
@@ -1736,7 +1736,8 @@ __global__ void __launch_bounds__(256) k_rhow_ozaki(OzRhoArgs a) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int k = 2 * lane + 64 * c + h;
-      const double v = k < a.n_phi ? rho[k] * wj[k] : 0.0;
+      double v = 0.0;
+      if (64 * c < a.k_pad && k < a.n_phi) v = rho[k] * wj[k];   // whole 64-wide pieces past k_pad skipped
       bits[c][h] = (unsigned long long)__double_as_longlong(v);
       mb = max(mb, bits[c][h] & 0x7FFFFFFFFFFFFFFFull);
     }
@@ -1778,7 +1779,7 @@ struct yy_oz_tables {
   int *gexp[4];                 // per field: [rows_pad]
   void *trig;                   // slices of trig / 2: [6][b_rows_pad][64]
   yy::PairMaps maps;
-  // analysis (FormOzakiWide): rho w digit rows as operand A, the azimuthal table as operand B
+  // analysis (FormOzaki in fills of kFillK): rho w digit rows as operand A, the azimuthal table as operand B
   int an_ok, an_kpad, an_bn, an_row_tiles, an_b_rows_pad, an_stages, an_slots, an_eb;
   void *an_x;                   // [6][rows_pad][an_kpad]
   int *an_exp;                  // [rows_pad]
@@ -1820,13 +1821,13 @@ static uint16_t bf16_int(int v) {
 }
 
 // Tables of the analysis by the Ozaki scheme; leaves an_ok = 0 (the float64
-// analysis serves) where the rows are longer than FormOzakiWide takes.
+// analysis serves) where the rows are longer than four fills.
 static yy_status ozaki_prepare_analysis(yy_grid *g, yy_oz_tables *o) {
-  typedef FormOzakiWide F;
+  typedef FormOzaki F;
   const int nt = 2 * g->lmax + 1;
-  if (g->n_phi > F::kMaxK || !g->sep_az || !g->sep_F) return YY_OK;
+  if (g->n_phi > F::kFillK * F::kMaxFills || !g->sep_az || !g->sep_F) return YY_OK;
   o->an_kpad = round_up(g->n_phi, kPadK);
-  o->an_bn = 16;   // eleven accumulators of bn columns within one 256-column TMEM buffer
+  o->an_bn = 32;   // seven level accumulators of bn columns within one 256-column TMEM buffer
   o->an_row_tiles = (nt + o->an_bn - 1) / o->an_bn;
   o->an_b_rows_pad = o->an_row_tiles * o->an_bn;
   o->an_stages = pair_stages<F>(o->an_bn, kEpiStageBytes);
@@ -1885,7 +1886,7 @@ static yy_status ozaki_prepare_analysis(yy_grid *g, yy_oz_tables *o) {
 }
 
 cudaError_t ozaki_analysis(yy_grid *g, const double *ry, const double *rg, cudaStream_t s) {
-  typedef FormOzakiWide F;
+  typedef FormOzaki F;
   yy_oz_tables *o = g->oz;
   OzRhoArgs ra = {};
   ra.n_r = g->n_r;
@@ -1912,6 +1913,7 @@ cudaError_t ozaki_analysis(yy_grid *g, const double *ry, const double *rg, cudaS
   a.row_tiles = o->an_row_tiles;
   a.bn = o->an_bn;
   a.kb_total = o->an_kpad * F::kElem / kRowBytes;
+  a.kb_chunk = F::kFillK * F::kElem / kRowBytes;   // exact level sums per fill; the epilogue adds the fills
   a.k_splits = 1;
   a.kb_per_split = a.kb_total;
   a.a_rows = o->rows_pad;

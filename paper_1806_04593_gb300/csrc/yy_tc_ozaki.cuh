@@ -11,16 +11,20 @@ namespace yy {
 // |r| <= 2^-49: the digits of round(|x| 2^48), each taken in [-127, 128]
 // with a carry into the next.  The products of digit levels L = s + t <= 6
 // (26 of the 36) are kept; the dropped ones add up to below 2^-56.  A
-// product sum over K <= 64 is at most 64 * 128^2 = 2^20, and a level has at
-// most 6 products, so every level accumulates in one TMEM accumulator below
-// 2^23: exact in fp32.  The epilogue combines the seven levels in integers
+// product sum over K <= 160 is at most 160 * 128^2 < 2^21.4, and a level has
+// at most 6 products, so every level accumulates in one TMEM accumulator
+// below 2^24 over a fill of up to 160: exact in fp32.  Longer K runs in
+// several fills, which the epilogue adds.  The epilogue combines the seven levels in integers
 // and rounds once to float64.  The rounding of the digits makes the
 // representation error unbiased, so it does not add up along K.
 // Products in level order; level L has s = max(0, L - 5) .. min(L, 5).
 struct FormOzaki {
   typedef __nv_bfloat16 elem;
   static constexpr int kKind = KIND_BF16, kElem = 2, kPA = 6, kPB = 6, kPairs = 26, kAccs = 7;
-  static constexpr int kMaxK = 64;
+  // K per accumulator fill (a level sum stays below 6 * 160 * 2^14 < 2^24), and
+  // the longest K taken: the epilogue adds up to four fills in int64 / fp32
+  static constexpr int kFillK = 160, kMaxFills = 4;
+  static constexpr int kMaxK = 64;   // K of the synthesis (2 l_max + 1, one fill)
   __host__ __device__ static constexpr int s_lo(int L) { return L > 5 ? L - 5 : 0; }
   // first product of level L (levels hold 1, 2, 3, 4, 5, 6, 5 products)
   __host__ __device__ static constexpr int start(int L) {
@@ -33,24 +37,8 @@ struct FormOzaki {
   __host__ __device__ static constexpr int pb(int i) { return level(i) - pa(i); }
   __host__ __device__ static constexpr int acc(int i) { return level(i); }
   __host__ __device__ static constexpr bool first(int i) { return i == start(level(i)); }
-  // accumulators of level L: acc_base(L) .. + n_acc(L) - 1
-  __host__ __device__ static constexpr int acc_base(int L) { return L; }
-  __host__ __device__ static constexpr int n_acc(int) { return 1; }
 };
 
-// The same digits and products for longer K (up to 320): a product's sum is
-// at most K 2^14, so an accumulator takes at most 3 products (3 * 341 * 2^14
-// < 2^24) and levels 3-6 use two accumulators each: eleven in all.
-struct FormOzakiWide : FormOzaki {
-  static constexpr int kAccs = 11, kMaxK = 320;
-  __host__ __device__ static constexpr int acc_base(int L) { return L <= 3 ? L : 3 + 2 * (L - 3); }
-  __host__ __device__ static constexpr int n_acc(int L) { return L <= 2 ? 1 : 2; }
-  __host__ __device__ static constexpr int acc(int i) { return acc_base(level(i)) + (pa(i) - s_lo(level(i))) / 3; }
-  __host__ __device__ static constexpr bool first(int i) { return (pa(i) - s_lo(level(i))) % 3 == 0; }
-};
-static_assert(FormOzakiWide::acc(9) == 4 && FormOzakiWide::acc(25) == 10 && FormOzakiWide::acc(21) == 9 &&
-                  FormOzakiWide::first(24) && !FormOzakiWide::first(25) && FormOzakiWide::acc(14) == 6,
-              "wide Ozaki product table");
 static_assert(FormOzaki::start(7) == 26 && FormOzaki::level(25) == 6 && FormOzaki::pa(25) == 5 &&
                   FormOzaki::pb(25) == 1 && FormOzaki::pa(21) == 1 && FormOzaki::first(21) &&
                   FormOzaki::pa(20) == 5 && FormOzaki::pb(20) == 0 && !FormOzaki::first(20),
@@ -73,38 +61,22 @@ __device__ __forceinline__ double i64_ldexp(long long v, int e) {
 // An accumulator value of the Ozaki forms: an integer below 2^24 held in fp32.
 __device__ __forceinline__ int oz_int(uint32_t v) { return __float2int_rn(__uint_as_float(v)); }
 
-// Level sum S_L of 8 columns: the level's accumulators (one or two, bn
-// columns apart from tcol onwards) added as integers (below 2^25).
-template <class F>
+// Level sum S_L of 8 columns (accumulator L, bn columns apart from tcol
+// onwards), as an integer and as the fp32 value itself.
 __device__ __forceinline__ void oz_level(uint32_t tcol, int bn, int L, int (&S)[8]) {
   uint32_t v[8];
-  tmem_ld8_async(tcol + (uint32_t)(F::acc_base(L) * bn), v);
+  tmem_ld8_async(tcol + (uint32_t)(L * bn), v);
   tmem_wait_ld();
 #pragma unroll
   for (int j = 0; j < 8; ++j) S[j] = oz_int(v[j]);
-  if (F::n_acc(L) == 2) {
-    tmem_ld8_async(tcol + (uint32_t)((F::acc_base(L) + 1) * bn), v);
-    tmem_wait_ld();
-#pragma unroll
-    for (int j = 0; j < 8; ++j) S[j] += oz_int(v[j]);
-  }
 }
 
-// Level sum S_L of 8 columns as fp32 (exact for one accumulator; the two of
-// a FormOzakiWide level added with one rounding).
-template <class F>
 __device__ __forceinline__ void oz_level_f(uint32_t tcol, int bn, int L, float (&S)[8]) {
   uint32_t v[8];
-  tmem_ld8_async(tcol + (uint32_t)(F::acc_base(L) * bn), v);
+  tmem_ld8_async(tcol + (uint32_t)(L * bn), v);
   tmem_wait_ld();
 #pragma unroll
   for (int j = 0; j < 8; ++j) S[j] = __uint_as_float(v[j]);
-  if (F::n_acc(L) == 2) {
-    tmem_ld8_async(tcol + (uint32_t)((F::acc_base(L) + 1) * bn), v);
-    tmem_wait_ld();
-#pragma unroll
-    for (int j = 0; j < 8; ++j) S[j] += __uint_as_float(v[j]);
-  }
 }
 
 // exact float64 of an fp32 value times 2^e (a normal result; zero stays zero)
@@ -119,43 +91,43 @@ __device__ __forceinline__ double f32_ldexp(float f, int e) {
   return __longlong_as_double((long long)bits);
 }
 
-// The 8 float64 values of one epilogue chunk (TMEM column tcol) from the
-// level sums S_0 .. S_6:
-//   value = 2^ce (hi 2^24 + lo),  hi = S_0 2^24 + S_1 2^16 + S_2 2^8 + S_3  (int64, below 2^49),
-//                                  lo = S_4 2^16 + S_5 2^8 + S_6          (fp32).
-// hi is exact in int64 and in float64.  lo is formed in fp32 from the
-// accumulator values (a unit is 2^-64 of the two rows' scales): |lo| is
-// below 2^39 units for FormOzaki and 2^41 for FormOzakiWide, so its rounding
-// is at most 2^15 or 2^17 units, under the digits' own error, which is up to
-// 2^15 units per product term (2^-49 of the scales) and adds up over the K
-// (<= 64 or <= 320) terms.  One more rounding, in the final addition.
-template <class F>
-__device__ __forceinline__ void ozaki_chunk(uint32_t tcol, int bn, int ce, double *dst) {
+// One fill's level sums S_0 .. S_6 of 8 columns (TMEM column tcol) added to
+// the chunk's running value 2^ce (hi 2^24 + lo):
+//   hi += S_0 2^24 + S_1 2^16 + S_2 2^8 + S_3   (int64: below 2^48 per fill)
+//   lo += S_4 2^16 + S_5 2^8 + S_6             (fp32)
+// hi stays exact (below 2^50 over four fills, exact in float64 too).  lo is
+// formed in fp32 from the accumulator values (a unit is 2^-64 of the two
+// rows' scales): below 2^40 units per fill, so its rounding stays under 2^18
+// units over four fills, below the digits' own error, which is up to 2^15
+// units per product term (2^-49 of the scales) and adds up over the K terms.
+__device__ __forceinline__ void ozaki_accumulate(uint32_t tcol, int bn, long long (&hi)[8], float (&lo)[8]) {
   int S[8];
-  long long hi[8];
-  oz_level<F>(tcol, bn, 0, S);
+  oz_level(tcol, bn, 0, S);
 #pragma unroll
-  for (int j = 0; j < 8; ++j) hi[j] = (long long)S[j] << 24;
-  oz_level<F>(tcol, bn, 1, S);
+  for (int j = 0; j < 8; ++j) hi[j] += (long long)S[j] << 24;
+  oz_level(tcol, bn, 1, S);
 #pragma unroll
   for (int j = 0; j < 8; ++j) hi[j] += (long long)S[j] << 16;
-  oz_level<F>(tcol, bn, 2, S);
+  oz_level(tcol, bn, 2, S);
 #pragma unroll
   for (int j = 0; j < 8; ++j) hi[j] += (long long)S[j] << 8;
-  oz_level<F>(tcol, bn, 3, S);
+  oz_level(tcol, bn, 3, S);
 #pragma unroll
   for (int j = 0; j < 8; ++j) hi[j] += (long long)S[j];
-  float lo[8];
-  oz_level_f<F>(tcol, bn, 4, lo);
+  float u[8], w[8];
+  oz_level_f(tcol, bn, 4, u);
+  oz_level_f(tcol, bn, 5, w);
 #pragma unroll
-  for (int j = 0; j < 8; ++j) lo[j] *= 65536.0f;
-  float t[8];
-  oz_level_f<F>(tcol, bn, 5, t);
+  for (int j = 0; j < 8; ++j) u[j] = fmaf(w[j], 256.0f, u[j] * 65536.0f);
+  oz_level_f(tcol, bn, 6, w);
 #pragma unroll
-  for (int j = 0; j < 8; ++j) lo[j] = fmaf(t[j], 256.0f, lo[j]);
-  oz_level_f<F>(tcol, bn, 6, t);
+  for (int j = 0; j < 8; ++j) lo[j] += u[j] + w[j];
+}
+
+// The chunk's float64 values: one rounding, in the final addition.
+__device__ __forceinline__ void ozaki_finish(const long long (&hi)[8], const float (&lo)[8], int ce, double *dst) {
 #pragma unroll
-  for (int j = 0; j < 8; ++j) dst[j] = i64_ldexp(hi[j], ce + 24) + f32_ldexp(lo[j] + t[j], ce);
+  for (int j = 0; j < 8; ++j) dst[j] = i64_ldexp(hi[j], ce + 24) + f32_ldexp(lo[j], ce);
 }
 
 }  // namespace yy

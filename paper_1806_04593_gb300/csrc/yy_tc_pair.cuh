@@ -440,7 +440,8 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
   const int pair = (int)blockIdx.x >> 1, n_pairs = (int)gridDim.x >> 1;
   const int per_job = a.cell_tiles * a.row_tiles * a.k_splits;
   const int total = per_job * a.n_jobs;
-  const int chunk = (OUT_MODE == 0 && a.kb_chunk > 0) ? a.kb_chunk : a.kb_total;   // K blocks per accumulator fill
+  // K blocks per accumulator fill (modes 0 and 3 add the fills in the epilogue)
+  const int chunk = ((OUT_MODE == 0 || OUT_MODE == 3) && a.kb_chunk > 0) ? a.kb_chunk : a.kb_total;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -631,29 +632,50 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
       double *ebuf = reinterpret_cast<double *>(wbuf);                          // [32][kEpiPad]
       double **rowp = reinterpret_cast<double **>(wbuf + 32 * kEpiPad * 8);     // [32] output rows
       const bool vec = (a.ldo & 1) == 0;   // rows start on 16-byte boundaries (with 16-byte aligned bases)
-      for (int t = pair; t < total; t += n_pairs, ++it) {
-        const int b = it & 1;
-        const PairJob &J = a.job[t / per_job];
-        const int tl = t % per_job;
-        const int rt = tl % a.row_tiles, ct = (tl / a.row_tiles) % a.cell_tiles;
-        const int cell0 = (2 * ct + rank) * kPairRows + quarter * 32;
-        const int cell = cell0 + lane;
-        const bool cell_ok = cell < a.cells;
-        const float cs = (OUT_MODE == 2 && cell_ok) ? J.cell_scale[cell] : 0.0f;
-        const float ca = (OUT_MODE == 2 && cell_ok) ? J.cell_add[cell] : 0.0f;
-        const int ce = (OUT_MODE == 3 && cell_ok) ? J.cell_exp[cell] : 0;
-        __syncwarp();   // the previous tile's row pointers are no longer read
-        rowp[lane] = !cell_ok ? nullptr
-                     : (cell < a.out_split) ? J.out0 + (size_t)cell * a.ldo
-                                            : J.out1 + (size_t)(cell - a.out_split) * a.ldo;
-        if (!mbar_wait_cluster(&tfull[b], (it >> 1) & 1, a.err)) break;
-        tc_fence_after();
-        const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
-        if constexpr (OUT_MODE == 3) {
-          // 8-column chunks, so that every epilogue warp takes part at bn = 32
-          for (int k = sub; k < a.bn / 8; k += kEpiPerQuarter) {
+      if constexpr (OUT_MODE == 3) {
+        // FormOzaki: the tile's fills (kb_chunk K blocks each) are added in
+        // registers, level by level; this warp owns the 8-column chunk sub
+        // (bn <= 8 kEpiPerQuarter), and the values are formed after the last fill.
+        const int k = sub;
+        const bool mine = k < a.bn / 8;
+        for (int t = pair; t < total; t += n_pairs) {
+          const PairJob &J = a.job[t / per_job];
+          const int tl = t % per_job;
+          const int rt = tl % a.row_tiles, ct = (tl / a.row_tiles) % a.cell_tiles;
+          const int kb0 = (tl / (a.row_tiles * a.cell_tiles)) * a.kb_per_split;
+          const int nkb = min(a.kb_total, kb0 + a.kb_per_split) - kb0;
+          const int cell = (2 * ct + rank) * kPairRows + quarter * 32 + lane;
+          const bool cell_ok = cell < a.cells;
+          const int ce = cell_ok ? J.cell_exp[cell] : 0;
+          __syncwarp();   // the previous tile's row pointers are no longer read
+          rowp[lane] = !cell_ok ? nullptr
+                       : (cell < a.out_split) ? J.out0 + (size_t)cell * a.ldo
+                                              : J.out1 + (size_t)(cell - a.out_split) * a.ldo;
+          long long hi[8];
+          float lo[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            hi[j] = 0;
+            lo[j] = 0.0f;
+          }
+          bool ok = true;
+          for (int c0 = 0; c0 < nkb; c0 += chunk, ++it) {
+            const int b = it & 1;
+            if (!mbar_wait_cluster(&tfull[b], (it >> 1) & 1, a.err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
+            if (mine) ozaki_accumulate(tbase + (uint32_t)(k * 8), a.bn, hi, lo);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster_relaxed(tempty_even + (uint32_t)(b * sizeof(uint64_t)));
+          }
+          if (!ok) break;
+          if (mine) {
             const int row0 = rt * a.bn + k * 8;
-            ozaki_chunk<F>(tbase + (uint32_t)(k * 8), a.bn, ce, ebuf + lane * kEpiPad);
+            ozaki_finish(hi, lo, ce, ebuf + lane * kEpiPad);
             __syncwarp();
             if (vec) {
               // lanes 4 c' + e: cell 8 q + c', values 2 e and 2 e + 1 of the run
@@ -681,7 +703,26 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
             }
             __syncwarp();
           }
-        } else {
+        }
+      } else
+      for (int t = pair; t < total; t += n_pairs, ++it) {
+        const int b = it & 1;
+        const PairJob &J = a.job[t / per_job];
+        const int tl = t % per_job;
+        const int rt = tl % a.row_tiles, ct = (tl / a.row_tiles) % a.cell_tiles;
+        const int cell0 = (2 * ct + rank) * kPairRows + quarter * 32;
+        const int cell = cell0 + lane;
+        const bool cell_ok = cell < a.cells;
+        const float cs = cell_ok ? J.cell_scale[cell] : 0.0f;
+        const float ca = cell_ok ? J.cell_add[cell] : 0.0f;
+        __syncwarp();   // the previous tile's row pointers are no longer read
+        rowp[lane] = !cell_ok ? nullptr
+                     : (cell < a.out_split) ? J.out0 + (size_t)cell * a.ldo
+                                            : J.out1 + (size_t)(cell - a.out_split) * a.ldo;
+        if (!mbar_wait_cluster(&tfull[b], (it >> 1) & 1, a.err)) break;
+        tc_fence_after();
+        const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
+        {
 #pragma unroll 1
         for (int k = sub; k < n_chunks; k += kEpiPerQuarter) {
           const int row0 = rt * a.bn + k * kEpiCols;
