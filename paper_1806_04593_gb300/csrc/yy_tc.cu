@@ -1721,8 +1721,9 @@ struct OzRhoArgs {
   int *rexp;                    // [rows_pad]
 };
 
+// C: 64-wide pieces of a row held per lane (k_pad <= 64 C)
+template <int C>
 __global__ void __launch_bounds__(256) k_rhow_ozaki(OzRhoArgs a) {
-  constexpr int C = FormOzaki::kFillK * FormOzaki::kMaxFills / 64;
   const int row = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (row >= a.rows) return;
   const int shell = row / a.n_theta, j = row % a.n_theta;
@@ -1736,8 +1737,7 @@ __global__ void __launch_bounds__(256) k_rhow_ozaki(OzRhoArgs a) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int k = 2 * lane + 64 * c + h;
-      double v = 0.0;
-      if (64 * c < a.k_pad && k < a.n_phi) v = rho[k] * wj[k];   // whole 64-wide pieces past k_pad skipped
+      const double v = k < a.n_phi ? rho[k] * wj[k] : 0.0;
       bits[c][h] = (unsigned long long)__double_as_longlong(v);
       mb = max(mb, bits[c][h] & 0x7FFFFFFFFFFFFFFFull);
     }
@@ -1901,7 +1901,12 @@ cudaError_t ozaki_analysis(yy_grid *g, const double *ry, const double *rg, cudaS
   ra.w = g->w;
   ra.X = (__nv_bfloat16 *)o->an_x;
   ra.rexp = o->an_exp;
-  k_rhow_ozaki<<<(unsigned)(((size_t)o->rows * 32 + 255) / 256), 256, 0, s>>>(ra);
+  const unsigned blocks = (unsigned)(((size_t)o->rows * 32 + 255) / 256);
+  constexpr int kCmax = FormOzaki::kFillK * FormOzaki::kMaxFills / 64;
+  if (o->an_kpad <= 64 * 5)
+    k_rhow_ozaki<5><<<blocks, 256, 0, s>>>(ra);
+  else
+    k_rhow_ozaki<kCmax><<<blocks, 256, 0, s>>>(ra);
   g->launches++;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
