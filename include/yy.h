@@ -84,7 +84,7 @@ typedef enum {
  *             integers and rounded once to float64.  The polar stages, the
  *             combination of the patches and the scans are float64 on CUDA
  *             cores as for YY_FP64 (and so is the analysis with
- *             YY_ANALYSIS_DENSE, or with more than 320 cells per row).
+ *             YY_ANALYSIS_DENSE, or with more than 640 cells per row).
  *             Needs yy_grid_prepare and 2 l_max + 1 <= 64 (l_max <= 31).    */
 typedef enum {
   YY_FP64 = 0,

@@ -187,7 +187,7 @@ cudaError_t tc_synthesis(yy_grid *g, yy_precision prec, double *phi_yin,
 yy_status ozaki_prepare(yy_grid *g);
 void ozaki_free(yy_grid *g);
 bool ozaki_ready(const yy_grid *g);
-// the separable analysis with its azimuthal stage by the same scheme (n_phi <= 320)
+// the separable analysis with its azimuthal stage by the same scheme (n_phi <= 640)
 bool ozaki_analysis_ready(const yy_grid *g);
 cudaError_t ozaki_analysis(yy_grid *g, const double *rho_yin, const double *rho_yang, cudaStream_t s);
 cudaError_t ozaki_synthesis(yy_grid *g, double *phi_yin, double *phi_yang, double *grad_yin, double *grad_yang,
