@@ -14,9 +14,10 @@ namespace yy {
 // product sum over K <= 160 is at most 160 * 128^2 < 2^21.4, and a level has
 // at most 6 products, so every level accumulates in one TMEM accumulator
 // below 2^24 over a fill of up to 160: exact in fp32.  Longer K runs in
-// several fills, which the epilogue adds.  The epilogue combines the seven levels in integers
-// and rounds once to float64.  The rounding of the digits makes the
-// representation error unbiased, so it does not add up along K.
+// several fills, which the epilogue adds.  The epilogue combines levels 0-3
+// in int64 and the three lowest in fp32, and rounds once to float64.  The
+// digits are rounded to nearest, so their representation errors take either
+// sign and grow like sqrt(K) along K rather than like K.
 // Products in level order; level L has s = max(0, L - 5) .. min(L, 5).
 struct FormOzaki {
   typedef __nv_bfloat16 elem;
