@@ -5,7 +5,8 @@ frame is the global one turned by pi/8 about z.  Grids as in §5: equidistant
 radial zones on [0, c], "LR" with 400 zones and 2-degree cells, "HR" with
 800 zones and 1-degree cells, each as a Yin-Yang grid and as a full
 spherical polar grid.  For every l_max the float64 solve (and, at chosen
-l_max, the FP16X2 form) is compared with the semi-analytic potential at the
+l_max, the FP16X2 form and the float64 results by the Ozaki scheme) is
+compared with the semi-analytic potential at the
 solver's output points (r_n^+, cell centres); reported are the maximum and
 the L2 relative error over all cells of all patches.
 
@@ -81,12 +82,14 @@ def main():
     ap.add_argument("--res", default="LR,HR")
     ap.add_argument("--lmax", default="0,5,10,20,40,60,80")
     ap.add_argument("--fp16x2-at", default="20,40")
+    ap.add_argument("--ozaki-at", default="20")
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
     from paper_1806_04593_gb300 import build
     build.build()
     lmaxes = [int(v) for v in args.lmax.split(",")]
     half = {int(v) for v in args.fp16x2_at.split(",") if v}
+    oz = {int(v) for v in args.ozaki_at.split(",") if v}
     rows = []
     for res in args.res.split(","):
         for kind, spec in grid_specs(res).items():
@@ -94,7 +97,7 @@ def main():
             rho, ref = reference(spec)
             t_ref = time.time() - t0
             for L in lmaxes:
-                for prec in ["fp64"] + (["fp16x2"] if L in half else []):
+                for prec in ["fp64"] + (["fp16x2"] if L in half else []) + (["fp64_ozaki"] if L in oz else []):
                     t1 = time.time()
                     got = solve(spec, L, rho, prec)
                     e_max, e_l2 = errors(got, ref)
