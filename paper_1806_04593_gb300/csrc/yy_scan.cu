@@ -156,12 +156,14 @@ k_scan_apply(ScanGeom s, const double *__restrict__ A, const double *__restrict_
 // moments into own-frame ones of the same degree:
 //   Atot[p][n][j] = A[p][n][j] + sum_i D^l_ij A[1-p][n][i],  i, j of degree l.
 // The scans and the synthesis are linear and act on each degree alone, so this
-// gives the same potential as summing four separate ones.  One block per
-// radius and one thread per mode j, both patches at once (each D entry is
-// loaded once for the two sums).  T is the type of the products: float64, or
-// float32 (the moments rounded once, the sum added to the float64 own moment).
+// gives the same potential as summing four separate ones.  Blocks of 256
+// threads: blockIdx.x is the radius, blockIdx.y a group of 256 modes, one
+// thread per mode j, both patches at once (each D entry is loaded once for
+// the two sums); every block stages both rows.  Small blocks keep several
+// resident per SM.  T is the type of the products: float64, or float32 (the
+// moments rounded once, the sum added to the float64 own moment).
 template <typename T>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(256)
 k_rotate_moments(int n_r, int n_lm, const T *__restrict__ rot, const double *__restrict__ A,
                  double *__restrict__ Atot) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -178,7 +180,8 @@ k_rotate_moments(int n_r, int n_lm, const T *__restrict__ rot, const double *__r
     }
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < n_lm; j += blockDim.x) {
+  const int j = (int)(blockIdx.y * blockDim.x + threadIdx.x);
+  if (j < n_lm) {
     const int l = mode_degree(j);
     const int w = 2 * l + 1, jj = j - l * l;
     const T *D = rot + (size_t)l * (4 * l * l - 1) / 3 + jj;
@@ -342,11 +345,11 @@ cudaError_t rotate_moments(yy_grid *g, bool fp64, cudaStream_t st) {
                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
   }
-  const int threads = std::min(1024, (g->n_lm + 31) / 32 * 32);
+  const dim3 grid((unsigned)g->n_r, (unsigned)((g->n_lm + 255) / 256));
   if (fp64)
-    k_rotate_moments<double><<<g->n_r, threads, smem, st>>>(g->n_r, g->n_lm, g->rot, g->A, g->Atot);
+    k_rotate_moments<double><<<grid, 256, smem, st>>>(g->n_r, g->n_lm, g->rot, g->A, g->Atot);
   else
-    k_rotate_moments<float><<<g->n_r, threads, smem, st>>>(g->n_r, g->n_lm, g->rot32, g->A, g->Atot);
+    k_rotate_moments<float><<<grid, 256, smem, st>>>(g->n_r, g->n_lm, g->rot32, g->A, g->Atot);
   g->launches++;
   return cudaGetLastError();
 }

@@ -353,7 +353,7 @@ __device__ __forceinline__ void pack_store(const PackArgs &p, int row, const dou
 }
 
 template <class F, int TPR, int P>
-__global__ void __launch_bounds__(TPR > 256 ? TPR : 256, (TPR <= 32 && P <= 6) ? 4 : 1)
+__global__ void __launch_bounds__(TPR > 256 ? TPR : 256, (TPR <= 32 && P <= 6) ? 4 : ((TPR <= 32 && P <= 12) ? 3 : 1))
 k_pack_reg(PackBatch batch) {
   constexpr int TPB = TPR > 256 ? TPR : 256;
   __shared__ RowStats red[32];
