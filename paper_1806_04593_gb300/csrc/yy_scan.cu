@@ -217,7 +217,7 @@ k_rotate_moments(int n_r, int n_lm, const T *__restrict__ rot, const double *__r
 // reduced-precision paths, whose packing rounds Q to fp32 anyway) in fp32
 // from fp32 roundings of c_n and d_n, widened back exactly.
 template <int CH, bool F64OUT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 3)
 k_scan_warp(int n_patch, int n_r, int lmax, int n_lm, const double *__restrict__ A, const double *__restrict__ coef,
             double *__restrict__ Q, float *__restrict__ Q32) {
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
