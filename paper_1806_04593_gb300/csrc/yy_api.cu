@@ -298,6 +298,7 @@ yy_status yy_potential(yy_grid *g, const double *rho_yin, const double *rho_yang
   const bool simt = (prec == YY_FP64 || prec == YY_FP32);
   const bool f32 = (prec == YY_FP32);
   g->launches = 0;
+  g->atot_done = 0;
   mark(0);
   if (e == cudaSuccess) {
     const bool separable = g->analysis_method == YY_ANALYSIS_SEPARABLE ||
@@ -322,7 +323,7 @@ yy_status yy_potential(yy_grid *g, const double *rho_yin, const double *rho_yang
   const bool sep_synth = ozaki || (simt ? (g->analysis_method != YY_ANALYSIS_DENSE && (g->sep_syn_ok & (f32 ? 1 : 2)) != 0)
                                         : (g->analysis_method == YY_ANALYSIS_SEPARABLE && tc_separable_synthesis_ready(g, prec)));
   g->last_sep_synthesis = sep_synth ? 1 : 0;
-  if (e == cudaSuccess) e = rotate_moments(g, prec == YY_FP64, s);
+  if (e == cudaSuccess && !g->atot_done) e = rotate_moments(g, prec == YY_FP64, s);
   if (e == cudaSuccess) e = radial_scan(g, f32, true, s);
   if (e == cudaSuccess && !simt)
     e = sep_synth ? tc_theta(g, prec, grad_yin != nullptr, s) : tc_pack_coefficients(g, prec, s);

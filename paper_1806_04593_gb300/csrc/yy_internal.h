@@ -82,6 +82,9 @@ struct yy_grid {
 
   // kernels launched by the last yy_potential call
   int launches;
+  // the last analysis also formed Atot (the combined moments): the separate
+  // combination is skipped
+  int atot_done;
 
   // stage timing
   int profiling;

@@ -740,6 +740,71 @@ __global__ void k_reduce_partials(int M, int N, int S, const float *__restrict__
   A[e] = fma(sum * rs[row], cs[col], mean[row] * colsum[col]);
 }
 
+// degree l of mode index idx (l^2 <= idx < (l + 1)^2): fp32 square root and
+// an integer correction
+__device__ __forceinline__ int degree_of_mode(int idx) {
+  int l = (int)sqrtf((float)idx);
+  while (l * l > idx) --l;
+  while ((l + 1) * (l + 1) <= idx) ++l;
+  return l;
+}
+
+// The split-K sum of the analysis fused with the combination of the two
+// patches' moments (Atot = A + D^T A(other patch), fp32 products as in the
+// separate combination kernel).  Block (radius n, group of 256 modes): the
+// moments of the degrees the group touches, both patches, are formed from the
+// partials exactly as k_reduce_partials forms them (written to A for the
+// group's own modes) and kept in shared memory; each thread then combines
+// one mode.  Same values as the two kernels in sequence.
+__global__ void __launch_bounds__(256)
+k_reduce_rotate(int n_r, int n_lm, int S, const float *__restrict__ part, const double *__restrict__ rs,
+                const double *__restrict__ cs, const double *__restrict__ mono, const double *__restrict__ mean,
+                const double *__restrict__ colsum, const float *__restrict__ rot, double *__restrict__ A,
+                double *__restrict__ Atot) {
+  __shared__ double ad[2 * 640];   // two rows of at most 640 modes (group of 256 plus its degrees' ends)
+  __shared__ float af[2 * 640];
+  const int n = blockIdx.x;
+  const int M = 2 * n_r;
+  const int j0 = blockIdx.y * blockDim.x;
+  const int j1 = min(n_lm, j0 + (int)blockDim.x);   // this group's modes [j0, j1)
+  const int la = degree_of_mode(j0), lb = degree_of_mode(j1 - 1);
+  const int m0 = la * la, m1 = (lb + 1) * (lb + 1), span = m1 - m0;
+  const size_t zs = (size_t)M * n_lm;
+  for (int e = threadIdx.x; e < 2 * span; e += blockDim.x) {
+    const int p = e / span, c = m0 + e % span;
+    const int row = p * n_r + n;
+    const size_t idx = (size_t)row * n_lm + c;
+    double v;
+    if (c == 0) {
+      v = mono[row];
+    } else {
+      float sum = 0.f, comp = 0.f;
+      for (int z = 0; z < S; ++z) kahan_add(sum, comp, part[(size_t)z * zs + idx]);
+      const double tot = f32_to_f64(sum) + f32_to_f64(comp);
+      v = fma(tot * rs[row], cs[c], mean[row] * colsum[c]);
+    }
+    ad[p * span + (c - m0)] = v;
+    af[p * span + (c - m0)] = f64_to_f32(v);
+    if (c >= j0 && c < j1) A[idx] = v;
+  }
+  __syncthreads();
+  const int j = j0 + (int)threadIdx.x;
+  if (j >= j1) return;
+  const int l = degree_of_mode(j);
+  const int w = 2 * l + 1, jj = j - l * l;
+  const float *D = rot + (size_t)l * (4 * l * l - 1) / 3 + jj;
+  const float *x0 = af + (l * l - m0), *x1 = af + span + (l * l - m0);
+  float s0 = 0.f, s1 = 0.f;   // into patch 0 (from patch 1) and into patch 1 (from patch 0)
+#pragma unroll 4
+  for (int i = 0; i < w; ++i) {
+    const float d = D[(size_t)i * w];
+    s0 = fmaf(d, x1[i], s0);
+    s1 = fmaf(d, x0[i], s1);
+  }
+  Atot[(size_t)n * n_lm + j] = ad[j - m0] + f32_to_f64(s0);
+  Atot[((size_t)n_r + n) * n_lm + j] = ad[span + (j - m0)] + f32_to_f64(s1);
+}
+
 // colsum[row] = sum_k table[row][k] (float64, fixed order); b0[k] = fp32(table[0][k])
 __global__ void __launch_bounds__(256) k_row_sums(int K, const double *__restrict__ table, double *__restrict__ out,
                                                   float *__restrict__ b0) {
@@ -837,6 +902,9 @@ namespace yy {
 
 // Rows up to this many values are cached in shared memory by the two-pass packing.
 constexpr int kPackCacheMax = 16 * 1024 / 4;
+// k_reduce_rotate keeps two rows of at most 640 modes: a group of 256 modes
+// plus the ends of its first and last degrees (2 (2 l + 1) <= 384 at l <= 95)
+constexpr int kReduceRotateLmax = 80;
 
 static size_t pack_smem(const PackBatch &b, int n) {
   size_t m = 0;
@@ -1313,6 +1381,15 @@ static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, 
   a.n_jobs = 1;
   a.err = g->err;
   if ((e = launch_pair<F>(g, t, t->an_maps, a, s)) != cudaSuccess) return e;
+  if (g->n_patch == 2 && g->lmax <= kReduceRotateLmax) {
+    // the split-K sum and the combination of the patches in one launch
+    const dim3 grid((unsigned)g->n_r, (unsigned)((g->n_lm + 255) / 256));
+    k_reduce_rotate<<<grid, 256, 0, s>>>(g->n_r, g->n_lm, t->an_splits, t->part, t->an_rhos, t->an_tabs, t->an_mono,
+                                         t->an_mean, t->an_colsum, g->rot32, g->A, g->Atot);
+    g->launches++;
+    g->atot_done = 1;
+    return cudaGetLastError();
+  }
   const size_t cnt = (size_t)M * g->n_lm;
   k_reduce_partials<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(M, g->n_lm, t->an_splits, t->part, t->an_rhos,
                                                                   t->an_tabs, t->an_mono, t->an_mean, t->an_colsum,
