@@ -70,6 +70,7 @@ def test_invalid_arguments_rejected_on_host(lib_path):
         assert st == yy.YY_ERR_INVALID_ARG and not h, args
     assert yy.yy_potential(None, 16, 16, 16, 16) == yy.YY_ERR_INVALID_ARG
     assert yy.yy_grid_prepare(None, yy.YY_FP64) == yy.YY_ERR_INVALID_ARG
+    assert yy.yy_grid_prepare(None, yy.YY_FP64_OZAKI) == yy.YY_ERR_INVALID_ARG
     assert yy.yy_grid_set_analysis(None, yy.YY_ANALYSIS_DENSE) == yy.YY_ERR_INVALID_ARG
     assert yy.yy_last_device_status(None) == yy.YY_ERR_INVALID_ARG
     yy.yy_destroy(None)
