@@ -1730,7 +1730,10 @@ __global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
   const int shell = row / a.n_theta, j = row % a.n_theta;
   const int qb = f < 2 ? f : 2;
   const double *q = a.Q + ((size_t)qb * a.n_shells + shell) * a.n_lm;
-  const double *tj = a.tab[f <= 1 ? 0 : f - 1] + (size_t)j * a.n_lm;
+  // parameter arrays read at constant indexes (a dynamic index copies the
+  // whole argument block to local memory)
+  const double *tab = f <= 1 ? a.tab[0] : (f == 2 ? a.tab[1] : a.tab[2]);
+  const double *tj = tab + (size_t)j * a.n_lm;
   // both slots' terms in one loop (about l_max + 1 - 16 steps for every lane)
   const int t0 = lane, t1 = 63 - lane;
   const int m0 = (t0 + 1) / 2, m1 = (t1 + 1) / 2;
@@ -1741,17 +1744,28 @@ __global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
   }
   const int n0 = (t0 < a.nt && (f < 3 || t0 > 0)) ? a.lmax + 1 - m0 : 0;
   const int n1 = (t1 < a.nt && (f < 3 || t1 > 0)) ? a.lmax + 1 - m1 : 0;
-  double gv[2] = {0.0, 0.0};
+  // one accumulator: slot t0's sum, then (from step n0) slot t1's; the
+  // switch moves registers, so the float64 pipe runs the multiply-adds alone
+  double gv[2] = {0.0, 0.0}, acc = 0.0;
+  const double *pq = q + a.lmax * a.lmax + s0, *pt = tj + a.lmax * a.lmax + t0;
+  int l = a.lmax;
   for (int it = 0; it < n0 + n1; ++it) {
-    const bool first = it < n0;
-    const int l = a.lmax - (first ? it : it - n0);
-    const int t = first ? t0 : t1, sq = first ? s0 : s1;
-    const double v = fma(q[l * l + sq], tj[l * l + t], first ? gv[0] : gv[1]);
-    if (first)
-      gv[0] = v;
-    else
-      gv[1] = v;
+    if (it == n0) {
+      gv[0] = acc;
+      acc = 0.0;
+      l = a.lmax;
+      pq = q + a.lmax * a.lmax + s1;
+      pt = tj + a.lmax * a.lmax + t1;
+    }
+    acc = fma(*pq, *pt, acc);
+    pq -= 2 * l - 1;   // l^2 - (l - 1)^2
+    pt -= 2 * l - 1;
+    --l;
   }
+  if (n1 > 0)
+    gv[1] = acc;
+  else
+    gv[0] = acc;
   if (f == 3) {
     if (!(t0 & 1)) gv[0] = -gv[0];
     if (!(t1 & 1)) gv[1] = -gv[1];
@@ -1775,14 +1789,16 @@ __global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
     oz_digits(X, d[h]);
   }
   const size_t stride = (size_t)a.rows_pad * FormOzaki::kMaxK;
-  __nv_bfloat16 *dst = a.G[f] + (size_t)row * FormOzaki::kMaxK;
+  __nv_bfloat16 *const Gf = f == 0 ? a.G[0] : f == 1 ? a.G[1] : f == 2 ? a.G[2] : a.G[3];
+  __nv_bfloat16 *dst = Gf + (size_t)row * FormOzaki::kMaxK;
 #pragma unroll
   for (int sl = 0; sl < 6; ++sl) {
     dst[sl * stride + lane] = __float2bfloat16_rn((b0 >> 63) ? -(float)d[0][sl] : (float)d[0][sl]);
     dst[sl * stride + 63 - lane] = __float2bfloat16_rn((b1 >> 63) ? -(float)d[1][sl] : (float)d[1][sl]);
   }
   // value = 2^(e + 1 - 64) (digit sums): trig scale 2^1, digit weights 2^-64
-  if (lane == 0) a.gexp[f][row] = exm == 0 ? 0 : e + 1 - 64;
+  int *const gexp = f == 0 ? a.gexp[0] : f == 1 ? a.gexp[1] : f == 2 ? a.gexp[2] : a.gexp[3];
+  if (lane == 0) gexp[row] = exm == 0 ? 0 : e + 1 - 64;
 }
 
 // The weighted densities of the separable analysis, rho w, as digit rows for
