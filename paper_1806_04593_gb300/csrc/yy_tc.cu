@@ -1713,65 +1713,15 @@ __host__ __device__ __forceinline__ void oz_digits(unsigned long long X, int (&d
   d[0] = (int)X;
 }
 
-// One warp per (field, row (shell, j)); lane L forms G at t = L and 63 - L
-// (slot t sums l_max + 1 - (t + 1) / 2 terms, so every lane does about the
-// same work) with the float64 polar sums of the CUDA-core separable
-// synthesis (l from l_max down, g_phi with the cos / sin slots swapped),
-// then the row's scale
-// 2^e (e from the largest |G|: every |G| 2^-e < 1/2) and the digits of
-// X = round(|G| 2^(48 - e)) <= 2^47, taken from the float64 bits, each with
-// the sign of G.  A row of zeros (or of values below the normal range) gets
-// zero digits.
-__global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
-  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  const int rows = a.n_shells * a.n_theta;
-  if (warp >= rows * a.n_jobs) return;
-  const int f = warp / rows, row = warp % rows;
-  const int shell = row / a.n_theta, j = row % a.n_theta;
-  const int qb = f < 2 ? f : 2;
-  const double *q = a.Q + ((size_t)qb * a.n_shells + shell) * a.n_lm;
-  // parameter arrays read at constant indexes (a dynamic index copies the
-  // whole argument block to local memory)
-  const double *tab = f <= 1 ? a.tab[0] : (f == 2 ? a.tab[1] : a.tab[2]);
-  const double *tj = tab + (size_t)j * a.n_lm;
-  // both slots' terms in one loop (about l_max + 1 - 16 steps for every lane)
-  const int t0 = lane, t1 = 63 - lane;
-  const int m0 = (t0 + 1) / 2, m1 = (t1 + 1) / 2;
-  int s0 = t0, s1 = t1;                               // coefficient slots
-  if (f == 3) {                                       // cos slot <- sin coefficient, sin slot <- cos
-    s0 = (t0 & 1) ? t0 + 1 : t0 - 1;
-    s1 = (t1 & 1) ? t1 + 1 : t1 - 1;
-  }
-  const int n0 = (t0 < a.nt && (f < 3 || t0 > 0)) ? a.lmax + 1 - m0 : 0;
-  const int n1 = (t1 < a.nt && (f < 3 || t1 > 0)) ? a.lmax + 1 - m1 : 0;
-  // one accumulator: slot t0's sum, then (from step n0) slot t1's; the
-  // switch moves registers, so the float64 pipe runs the multiply-adds alone
-  double gv[2] = {0.0, 0.0}, acc = 0.0;
-  const double *pq = q + a.lmax * a.lmax + s0, *pt = tj + a.lmax * a.lmax + t0;
-  int l = a.lmax;
-  for (int it = 0; it < n0 + n1; ++it) {
-    if (it == n0) {
-      gv[0] = acc;
-      acc = 0.0;
-      l = a.lmax;
-      pq = q + a.lmax * a.lmax + s1;
-      pt = tj + a.lmax * a.lmax + t1;
-    }
-    acc = fma(*pq, *pt, acc);
-    pq -= 2 * l - 1;   // l^2 - (l - 1)^2
-    pt -= 2 * l - 1;
-    --l;
-  }
-  if (n1 > 0)
-    gv[1] = acc;
-  else
-    gv[0] = acc;
-  if (f == 3) {
-    if (!(t0 & 1)) gv[0] = -gv[0];
-    if (!(t1 & 1)) gv[1] = -gv[1];
-  }
-  const unsigned long long b0 = (unsigned long long)__double_as_longlong(gv[0]);
-  const unsigned long long b1 = (unsigned long long)__double_as_longlong(gv[1]);
+// One row's digits (row slots t0 = lane and t1 = 63 - lane hold G0 and G1):
+// the row's scale 2^e (e from the largest |G|: every |G| 2^-e < 1/2) and the
+// digits of X = round(|G| 2^(48 - e)) <= 2^47, taken from the float64 bits,
+// each with the sign of G.  A row of zeros (or of values below the normal
+// range) gets zero digits.
+__device__ __forceinline__ void oz_theta_row(double G0, double G1, int lane, __nv_bfloat16 *dst, size_t stride,
+                                             int *gexp) {
+  const unsigned long long b0 = (unsigned long long)__double_as_longlong(G0);
+  const unsigned long long b1 = (unsigned long long)__double_as_longlong(G1);
   unsigned long long mb = max(b0 & 0x7FFFFFFFFFFFFFFFull, b1 & 0x7FFFFFFFFFFFFFFFull);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
@@ -1788,17 +1738,98 @@ __global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
       X = ((((bits[h] & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> (sh - 1)) + 1ull) >> 1;   // round half up
     oz_digits(X, d[h]);
   }
-  const size_t stride = (size_t)a.rows_pad * FormOzaki::kMaxK;
-  __nv_bfloat16 *const Gf = f == 0 ? a.G[0] : f == 1 ? a.G[1] : f == 2 ? a.G[2] : a.G[3];
-  __nv_bfloat16 *dst = Gf + (size_t)row * FormOzaki::kMaxK;
 #pragma unroll
   for (int sl = 0; sl < 6; ++sl) {
     dst[sl * stride + lane] = __float2bfloat16_rn((b0 >> 63) ? -(float)d[0][sl] : (float)d[0][sl]);
     dst[sl * stride + 63 - lane] = __float2bfloat16_rn((b1 >> 63) ? -(float)d[1][sl] : (float)d[1][sl]);
   }
   // value = 2^(e + 1 - 64) (digit sums): trig scale 2^1, digit weights 2^-64
+  if (lane == 0) *gexp = exm == 0 ? 0 : e + 1 - 64;
+}
+
+// One warp per (field, shell, mirrored row pair j, j' = n_theta - 1 - j).
+// The polar cells are symmetric about the equator (theta_j + theta_j' = pi on
+// the Yin-Yang patch and on the polar grid), and P_l^m(cos(pi - theta)) =
+// (-1)^(l + m) P_l^m(cos theta): with E and O the sums over the terms of even
+// and of odd l + m at row j, G = E + O at j and E - O at j' (for P and
+// m P / sin theta; dP/dtheta has the opposite parity, -(E - O) at j').  So one
+// pass over the coefficients gives both rows.  Lane L takes the slots t = L
+// and 63 - L (slot t sums l_max + 1 - (t + 1) / 2 terms, so every lane does
+// about the same work), l from l_max down in steps of two (terms l and l - 1:
+// one of each parity), g_phi with the cos / sin slots swapped, one pair of
+// accumulators that moves from slot t0 to t1 by register moves.
+__global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  const int half = (a.n_theta + 1) >> 1;
+  const int pairs = a.n_shells * half;
+  if (warp >= pairs * a.n_jobs) return;
+  const int f = warp / pairs, pr = warp % pairs;
+  const int shell = pr / half, j = pr % half, jm = a.n_theta - 1 - j;
+  const int qb = f < 2 ? f : 2;
+  const double *q = a.Q + ((size_t)qb * a.n_shells + shell) * a.n_lm;
+  // parameter arrays read at constant indexes (a dynamic index copies the
+  // whole argument block to local memory)
+  const double *tab = f <= 1 ? a.tab[0] : (f == 2 ? a.tab[1] : a.tab[2]);
+  const double *tj = tab + (size_t)j * a.n_lm;
+  const int L = a.lmax;
+  const int t0 = lane, t1 = 63 - lane;
+  const int m0 = (t0 + 1) / 2, m1 = (t1 + 1) / 2;
+  int s0 = t0, s1 = t1;                               // coefficient slots
+  if (f == 3) {                                       // cos slot <- sin coefficient, sin slot <- cos
+    s0 = (t0 & 1) ? t0 + 1 : t0 - 1;
+    s1 = (t1 & 1) ? t1 + 1 : t1 - 1;
+  }
+  const int n0 = (t0 < a.nt && (f < 3 || t0 > 0)) ? L + 1 - m0 : 0;
+  const int n1 = (t1 < a.nt && (f < 3 || t1 > 0)) ? L + 1 - m1 : 0;
+  const int k0 = (n0 + 1) >> 1, k1 = (n1 + 1) >> 1;  // steps of two terms per slot
+  // a1: terms with l = l_max, l_max - 2, ...; a2: l = l_max - 1, l_max - 3, ...
+  double a1 = 0.0, a2 = 0.0, h1 = 0.0, h2 = 0.0;
+  const double *pq = q + L * L + s0, *pt = tj + L * L + t0;
+  int l = L, m = m0;
+  for (int it = 0; it < k0 + k1; ++it) {
+    if (it == k0) {
+      h1 = a1;
+      h2 = a2;
+      a1 = 0.0;
+      a2 = 0.0;
+      l = L;
+      m = m1;
+      pq = q + L * L + s1;
+      pt = tj + L * L + t1;
+    }
+    a1 = fma(pq[0], pt[0], a1);
+    const int d1 = 2 * l - 1;                        // l^2 - (l - 1)^2
+    if (l > m) a2 = fma(pq[-d1], pt[-d1], a2);
+    pq -= 4 * l - 4;                                 // l^2 - (l - 2)^2
+    pt -= 4 * l - 4;
+    l -= 2;
+  }
+  double x0[2], x1[2];                               // (a1, a2) of slots t0 and t1
+  if (k1 > 0) {
+    x0[0] = h1; x0[1] = h2; x1[0] = a1; x1[1] = a2;
+  } else {
+    x0[0] = a1; x0[1] = a2; x1[0] = 0.0; x1[1] = 0.0;
+  }
+  // E and O: a1 holds the terms of l + m = l_max + m (mod 2)
+  const bool ev0 = ((L + m0) & 1) == 0, ev1 = ((L + m1) & 1) == 0;
+  const double E0 = ev0 ? x0[0] : x0[1], O0 = ev0 ? x0[1] : x0[0];
+  const double E1 = ev1 ? x1[0] : x1[1], O1 = ev1 ? x1[1] : x1[0];
+  double g0 = E0 + O0, g1 = E1 + O1;                 // row j
+  double r0 = E0 - O0, r1 = E1 - O1;                 // row j'
+  if (f == 2) {
+    r0 = -r0;
+    r1 = -r1;
+  }
+  if (f == 3) {
+    if (!(t0 & 1)) { g0 = -g0; r0 = -r0; }
+    if (!(t1 & 1)) { g1 = -g1; r1 = -r1; }
+  }
+  const size_t stride = (size_t)a.rows_pad * FormOzaki::kMaxK;
+  __nv_bfloat16 *const Gf = f == 0 ? a.G[0] : f == 1 ? a.G[1] : f == 2 ? a.G[2] : a.G[3];
   int *const gexp = f == 0 ? a.gexp[0] : f == 1 ? a.gexp[1] : f == 2 ? a.gexp[2] : a.gexp[3];
-  if (lane == 0) gexp[row] = exm == 0 ? 0 : e + 1 - 64;
+  const size_t row = (size_t)shell * a.n_theta + j, rowm = (size_t)shell * a.n_theta + jm;
+  oz_theta_row(g0, g1, lane, Gf + row * FormOzaki::kMaxK, stride, gexp + row);
+  if (jm != j) oz_theta_row(r0, r1, lane, Gf + rowm * FormOzaki::kMaxK, stride, gexp + rowm);
 }
 
 // The weighted densities of the separable analysis, rho w, as digit rows for
@@ -2134,7 +2165,7 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
     ta.G[f] = (__nv_bfloat16 *)o->G[f];
     ta.gexp[f] = o->gexp[f];
   }
-  const size_t warps = (size_t)o->rows * n_jobs;
+  const size_t warps = (size_t)ta.n_shells * ((g->n_theta + 1) / 2) * n_jobs;   // mirrored row pairs
   k_theta_ozaki<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(ta);
   g->launches++;
   cudaError_t e = cudaGetLastError();

@@ -115,8 +115,9 @@ def test_ozaki_analysis_in_several_fills(yy, oracle_grid):
 
 
 def test_ozaki_ragged_and_highest_degree(yy):
-    """Sizes that are multiples of no tile (17 x 41 cells, 131 zones), and
-    l_max = 31, the largest with 2 l_max + 1 <= 64."""
+    """Sizes that are multiples of no tile (17 x 41 cells, 131 zones; an odd
+    n_theta, whose middle polar row is its own mirror in the polar synthesis
+    stage), and l_max = 31, the largest with 2 l_max + 1 <= 64."""
     from oracle import OracleGrid
     for n_r, nt, npp, lmax, seed in ((131, 17, 41, 13, 45), (40, 20, 60, 31, 46)):
         spec = inputs.GridSpec(f"ragged_oz_{lmax}", np.logspace(-2, 0, n_r + 1), nt, npp, 0.03, 0.05, lmax, 1.0)
