@@ -283,26 +283,49 @@ __global__ void __launch_bounds__(256) k_sep_theta(int n_theta, int n_lm, int lm
                                                    const T *__restrict__ F, const float2 *__restrict__ F0,
                                                    double *__restrict__ A) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2 *f0s = reinterpret_cast<float2 *>(smraw);       // [n_theta]
-  T *fs = reinterpret_cast<T *>(f0s + n_theta + (n_theta & 1));   // [n_theta][nt_pad]
   const int shell = blockIdx.x;
   const T *Fs = F + (size_t)shell * n_theta * nt_pad;
-  for (int e = threadIdx.x; e < n_theta * nt_pad; e += blockDim.x) fs[e] = Fs[e];
-  if constexpr (sizeof(T) == 4)
-    for (int j = threadIdx.x; j < n_theta; j += blockDim.x) f0s[j] = F0[(size_t)shell * n_theta + j];
-  __syncthreads();
   if constexpr (sizeof(T) == 4) {
+    float2 *f0s = reinterpret_cast<float2 *>(smraw);       // [n_theta]
+    T *fs = reinterpret_cast<T *>(f0s + n_theta + (n_theta & 1));   // [n_theta][nt_pad]
+    for (int e = threadIdx.x; e < n_theta * nt_pad; e += blockDim.x) fs[e] = Fs[e];
+    for (int j = threadIdx.x; j < n_theta; j += blockDim.x) f0s[j] = F0[(size_t)shell * n_theta + j];
+    __syncthreads();
     theta_modes_f32(n_theta, n_lm, lmax1, nt_pad, tb, tb0, fs, f0s, A + (size_t)shell * n_lm);
   } else {
+    // The polar cells are symmetric about the equator (cell n_theta - 1 - j is
+    // cell j reflected), so the cell integrals of P_l^m(cos theta) sin theta
+    // have its parity: T_j' = (-1)^(l + m) T_j.  With S_j = F_j + F_j' and
+    // D_j = F_j - F_j', a mode is the sum over j < ceil(n_theta / 2) of T_j S_j
+    // (even l + m) or T_j D_j (odd): half the products.  A middle row (odd
+    // n_theta) is its own mirror and enters once, as both S and D.
+    const int half = (n_theta + 1) >> 1;
+    T *cs = reinterpret_cast<T *>(smraw);                  // [2][half][nt_pad]: S, then D
+    for (int e = threadIdx.x; e < half * nt_pad; e += blockDim.x) {
+      const int j = e / nt_pad, jm = n_theta - 1 - j;
+      const T a = Fs[e], b = Fs[(size_t)(jm - j) * nt_pad + e];
+      cs[e] = jm == j ? a : a + b;
+      cs[(size_t)half * nt_pad + e] = jm == j ? a : a - b;
+    }
+    __syncthreads();
     for (int idx = threadIdx.x; idx < n_lm; idx += blockDim.x) {
       const int l = degree_of(idx);
       const int t = idx - l * l;
+      const T *c = cs + ((((l + ((t + 1) >> 1)) & 1) != 0) ? (size_t)half * nt_pad : 0) + t;
       T s = T(0);
 #pragma unroll 8
-      for (int j = 0; j < n_theta; ++j) s = fma(tb[(size_t)j * n_lm + idx], fs[j * nt_pad + t], s);
+      for (int j = 0; j < half; ++j) s = fma(tb[(size_t)j * n_lm + idx], c[j * nt_pad], s);
       A[(size_t)shell * n_lm + idx] = s;
     }
   }
+}
+
+// Dynamic shared memory of k_sep_theta: the fp32 form stages F and the m = 0
+// pair sums, the float64 form the mirrored sums S and D of ceil(n_theta / 2)
+// rows each.
+static size_t theta_smem(int n_theta, int nt_pad, size_t el) {
+  if (el == sizeof(double)) return (size_t)(n_theta + 1) * nt_pad * sizeof(double);
+  return (size_t)n_theta * nt_pad * el + (size_t)(n_theta + 1) * sizeof(float2);
 }
 
 // Polar stage after the tensor-core azimuthal stage: F of the rows (shell, j)
@@ -404,7 +427,7 @@ cudaError_t run_separable(yy_grid *g, const double *rho_yin, const double *rho_y
     k_sep_phi<T, kJCSmall><<<grid, threads, smem_phi, s>>>(shells, g->n_r, g->n_theta, g->n_phi, nt_pad, rho_yin,
                                                            rho_yang, w, az, F, (float2 *)g->sep_F0);
   g->launches++;
-  const size_t smem_theta = (size_t)g->n_theta * nt_pad * sizeof(T) + (size_t)(g->n_theta + 1) * sizeof(float2);
+  const size_t smem_theta = theta_smem(g->n_theta, nt_pad, sizeof(T));
   k_sep_theta<T><<<shells, 256, smem_theta, s>>>(g->n_theta, g->n_lm, g->lmax + 1, nt_pad, tb, g->sep_tb0, F,
                                                     (const float2 *)g->sep_F0, g->A);
   g->launches++;
@@ -571,7 +594,8 @@ cudaError_t separable_prepare(yy_grid *g) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
   for (int q = 0; q < 2; ++q) {
     const size_t el = q ? sizeof(double) : sizeof(float);
-    if ((size_t)g->n_theta * nt_pad * el + tail_t > 227 * 1024) continue;
+    if ((size_t)g->n_theta * nt_pad * el + tail_t > 227 * 1024 || theta_smem(g->n_theta, nt_pad, el) > 227 * 1024)
+      continue;
     const int jc = phi_smem(g, nt_pad, kJC, el) <= 227 * 1024 ? kJC : kJCSmall;
     const size_t sm = phi_smem(g, nt_pad, jc, el);
     if (sm > 227 * 1024) continue;
@@ -640,7 +664,7 @@ cudaError_t separable_theta_partials(yy_grid *g, SepThetaPartials a, cudaStream_
 
 cudaError_t separable_theta_f64(yy_grid *g, cudaStream_t s) {
   const int nt_pad = g->sep_nt_pad;
-  const size_t smem_theta = (size_t)g->n_theta * nt_pad * sizeof(double) + (size_t)(g->n_theta + 1) * sizeof(float2);
+  const size_t smem_theta = theta_smem(g->n_theta, nt_pad, sizeof(double));
   k_sep_theta<double><<<grid_rows(g), 256, smem_theta, s>>>(g->n_theta, g->n_lm, g->lmax + 1, nt_pad, g->tbar,
                                                             g->sep_tb0, g->sep_F, (const float2 *)g->sep_F0, g->A);
   g->launches++;
