@@ -152,6 +152,32 @@ def test_polar_integrals_full_range_closed_forms():
         assert abs(T[l, 0]) <= 1e-13                      # int P_l = 0, l > 0
 
 
+@pytest.mark.parametrize("th_lo, th_hi, n", [(math.pi / 4 - 0.03, 3 * math.pi / 4 + 0.03, 90),
+                                             (math.pi / 4 - 0.03, 3 * math.pi / 4 + 0.03, 17),
+                                             (0.0, math.pi, 45)])
+def test_equatorial_parity_of_legendre_tables(th_lo, th_hi, n):
+    """Grids symmetric about the equator (the Yin-Yang patch, the full polar
+    grid; odd n has a middle cell that is its own mirror): under
+    theta -> pi - theta, P_l^m(cos theta), m P_l^m / sin theta and the cell
+    integrals T_j change sign by (-1)^(l+m), dP/dtheta by the opposite sign.
+    The float64 polar stages of the GPU path sum half the rows on this."""
+    lmax = 25
+    edges = np.linspace(th_lo, th_hi, n + 1)
+    th = 0.5 * (edges[1:] + edges[:-1])
+    P = yinyang.assoc_legendre(lmax, np.cos(th), np.sin(th))
+    tables = {"P": (P, 0), "dP": (yinyang.dlegendre_dtheta(P), 1), "mP/sin": (yinyang.legendre_m_over_sin(P), 0),
+              "T": (oracle.polar_integrals(lmax, edges), 0)}
+    for name, (tab, flip) in tables.items():
+        for l in range(lmax + 1):
+            for m in range(l + 1):
+                row = tab[l, m]
+                scale = np.abs(row).max()
+                if scale == 0.0:
+                    continue
+                sign = (-1) ** (l + m + flip)
+                assert np.abs(row[::-1] - sign * row).max() <= 1e-12 * scale, (name, l, m)
+
+
 def test_T22_reading_R1():
     # printed seed (literal) vs bracketed seed vs the T^(ll) recurrence at l = 2
     tm, tp = 0.0, math.pi
