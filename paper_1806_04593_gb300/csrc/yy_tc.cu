@@ -1713,15 +1713,14 @@ __host__ __device__ __forceinline__ void oz_digits(unsigned long long X, int (&d
   d[0] = (int)X;
 }
 
-// One row's digits (row slots t0 = lane and t1 = 63 - lane hold G0 and G1):
+// One row's digits (row slots t0 = lane and t1 = 63 - lane hold G0 and G1,
+// passed as their float64 bit patterns b0 and b1):
 // the row's scale 2^e (e from the largest |G|: every |G| 2^-e < 1/2) and the
 // digits of X = round(|G| 2^(48 - e)) <= 2^47, taken from the float64 bits,
 // each with the sign of G.  A row of zeros (or of values below the normal
 // range) gets zero digits.
-__device__ __forceinline__ void oz_theta_row(double G0, double G1, int lane, __nv_bfloat16 *dst, size_t stride,
-                                             int *gexp) {
-  const unsigned long long b0 = (unsigned long long)__double_as_longlong(G0);
-  const unsigned long long b1 = (unsigned long long)__double_as_longlong(G1);
+__device__ __forceinline__ void oz_theta_row(unsigned long long b0, unsigned long long b1, int lane,
+                                             __nv_bfloat16 *dst, size_t stride, int *gexp) {
   unsigned long long mb = max(b0 & 0x7FFFFFFFFFFFFFFFull, b1 & 0x7FFFFFFFFFFFFFFFull);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
@@ -1810,20 +1809,25 @@ __global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
   } else {
     x0[0] = a1; x0[1] = a2; x1[0] = 0.0; x1[1] = 0.0;
   }
-  // E and O: a1 holds the terms of l + m = l_max + m (mod 2)
-  const bool ev0 = ((L + m0) & 1) == 0, ev1 = ((L + m1) & 1) == 0;
-  const double E0 = ev0 ? x0[0] : x0[1], O0 = ev0 ? x0[1] : x0[0];
-  const double E1 = ev1 ? x1[0] : x1[1], O1 = ev1 ? x1[1] : x1[0];
-  double g0 = E0 + O0, g1 = E1 + O1;                 // row j
-  double r0 = E0 - O0, r1 = E1 - O1;                 // row j'
+  // Row j: E + O = a1 + a2.  Row j': E - O, which is a1 - a2 when a1 holds
+  // the terms of even l + m (l_max + m even), else a2 - a1.  Every sign change
+  // (that one, dP/dtheta's parity, g_phi's swapped slots) flips the sign bit
+  // of the bit pattern on the integer units: four float64 additions per lane.
+  const unsigned long long SB = 0x8000000000000000ull;
+  unsigned long long fg0 = 0ull, fg1 = 0ull;
+  unsigned long long fr0 = ((L + m0) & 1) ? SB : 0ull, fr1 = ((L + m1) & 1) ? SB : 0ull;
   if (f == 2) {
-    r0 = -r0;
-    r1 = -r1;
+    fr0 ^= SB;
+    fr1 ^= SB;
   }
   if (f == 3) {
-    if (!(t0 & 1)) { g0 = -g0; r0 = -r0; }
-    if (!(t1 & 1)) { g1 = -g1; r1 = -r1; }
+    if (!(t0 & 1)) { fg0 = SB; fr0 ^= SB; }
+    if (!(t1 & 1)) { fg1 = SB; fr1 ^= SB; }
   }
+  const unsigned long long g0 = (unsigned long long)__double_as_longlong(x0[0] + x0[1]) ^ fg0;
+  const unsigned long long g1 = (unsigned long long)__double_as_longlong(x1[0] + x1[1]) ^ fg1;
+  const unsigned long long r0 = (unsigned long long)__double_as_longlong(x0[0] - x0[1]) ^ fr0;
+  const unsigned long long r1 = (unsigned long long)__double_as_longlong(x1[0] - x1[1]) ^ fr1;
   const size_t stride = (size_t)a.rows_pad * FormOzaki::kMaxK;
   __nv_bfloat16 *const Gf = f == 0 ? a.G[0] : f == 1 ? a.G[1] : f == 2 ? a.G[2] : a.G[3];
   int *const gexp = f == 0 ? a.gexp[0] : f == 1 ? a.gexp[1] : f == 2 ? a.gexp[2] : a.gexp[3];
