@@ -1860,15 +1860,31 @@ __global__ void __launch_bounds__(256) k_rhow_ozaki(OzRhoArgs a) {
   const double *wj = a.w + (size_t)j * a.n_phi;
   unsigned long long bits[C][2];
   unsigned long long mb = 0ull;
+  // an even n_phi keeps every row on a 16-byte boundary (the densities are
+  // 16-byte aligned): a lane's two cells k, k + 1 in one load of each array
+  const bool pairs = (a.n_phi & 1) == 0;
 #pragma unroll
-  for (int c = 0; c < C; ++c)
+  for (int c = 0; c < C; ++c) {
+    const int k = 2 * lane + 64 * c;
+    double v[2] = {0.0, 0.0};
+    if (pairs) {
+      if (k < a.n_phi) {
+        const double2 r2 = *reinterpret_cast<const double2 *>(rho + k);
+        const double2 w2 = *reinterpret_cast<const double2 *>(wj + k);
+        v[0] = r2.x * w2.x;
+        v[1] = r2.y * w2.y;
+      }
+    } else {
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (k + h < a.n_phi) v[h] = rho[k + h] * wj[k + h];
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int k = 2 * lane + 64 * c + h;
-      const double v = k < a.n_phi ? rho[k] * wj[k] : 0.0;
-      bits[c][h] = (unsigned long long)__double_as_longlong(v);
+      bits[c][h] = (unsigned long long)__double_as_longlong(v[h]);
       mb = max(mb, bits[c][h] & 0x7FFFFFFFFFFFFFFFull);
     }
+  }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
   const int exm = (int)(mb >> 52);
