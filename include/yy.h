@@ -276,27 +276,41 @@ typedef enum {
 yy_status yy_grid_set_profiling(yy_grid *g, int enable);
 yy_status yy_grid_stage_ms(yy_grid *g, double *ms);
 
+/* Per-kernel timing (diagnostics).  While profiling is enabled, yy_potential
+ * also records a CUDA event on its stream after each kernel it launches (the
+ * first 32).  For the last solve, kernel `index` (0 <= index <
+ * yy_last_launch_count) gets *ms = the time from the end of the kernel before
+ * it (from the solve's start for index 0) to its own end, and *name = a static
+ * string naming the kernel (not to be freed).  Synchronises on that event.
+ * Errors: YY_ERR_INVALID_ARG (profiling off, index out of range). */
+yy_status yy_grid_kernel_ms(yy_grid *g, int index, double *ms, const char **name);
+
 /* Radial inner / outer sums without a handle and without any allocation.
  * (No counterpart in the paper: this is a deployment variant of the scan.)
- * For callers that cannot allocate device memory when they need the sums:
- * code running while a CUDA graph is captured, applications whose device
- * memory is owned by their own pool, loops that must not enter the driver's
- * allocator.  It computes the same coefficients as the solve's scan stage.
+ * For callers that cannot allocate device memory where they need the sums:
+ * applications whose device memory is owned entirely by their own pool or
+ * arena, hosts that load this code as a plugin and forbid it the allocator,
+ * and time-critical loops where cudaMalloc / cudaFree (which may synchronise
+ * the device) are not allowed.  It computes the same coefficients as the
+ * solve's scan stage.
  *   r_edges  device, n_r + 1 radii obeying yy_grid_create's rules (not
  *            checked here; values that break them give undefined results)
  *   moments  device, [2 n_r][n_lm] normalised moments, Yin rows first: the
  *            combined moments of YY_TABLE_MOMENTS_TOTAL
  *   coeff    device out, [3][2 n_r][n_lm]: the Phi, g_r and angular-gradient
  *            coefficients, in the layout of YY_TABLE_COEFF
- *   n_r >= 1, 0 <= l_max <= 80, G finite; all pointers 16-byte aligned.
+ *   n_r >= 1, 0 <= l_max <= 80, G finite; pointers 8-byte aligned (the
+ *   kernel reads and writes single float64 values).
  * Scratch: a static device array of 2^21 float64 (16 MiB) that every GPU
  * loading the library keeps until exit; 2 n_r (l_max+1)^2 must not exceed
  * 2^21, otherwise YY_ERR_INVALID_ARG and nothing is launched.  Nothing in the
  * scratch needs clearing (each value is written before it is read), but all
  * calls share it: calls whose kernels overlap on the GPU (other streams,
  * other threads) race and give wrong results.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  Asynchronous on cuda_stream. */
+ * (and again the first call after its context is recreated, for example by
+ * cudaDeviceReset) does the set-up: it looks up the array's device address
+ * (cudaGetSymbolAddress), which allocates nothing; make that first call
+ * before any stream capture.  Asynchronous on cuda_stream. */
 yy_status yy_radial_scan_static(const double *r_edges, int n_r, int l_max, double G,
                                 const double *moments, double *coeff, void *cuda_stream);
 

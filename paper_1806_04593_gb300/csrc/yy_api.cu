@@ -500,9 +500,15 @@ yy_status yy_grid_set_profiling(yy_grid *g, int enable) {
       cudaError_t e = cudaEventCreate(&g->ev[i]);
       if (e != cudaSuccess) return from_cuda(e);
     }
+    for (int i = 0; i < YY_MAX_KERNEL_EVENTS; ++i) {
+      cudaError_t e = cudaEventCreate(&g->kev[i]);
+      if (e != cudaSuccess) return from_cuda(e);
+      g->kname[i] = nullptr;
+    }
   } else if (!enable && g->profiling) {
     cudaDeviceSynchronize();
     for (int i = 0; i <= YY_STAGE_COUNT; ++i) cudaEventDestroy(g->ev[i]);
+    for (int i = 0; i < YY_MAX_KERNEL_EVENTS; ++i) cudaEventDestroy(g->kev[i]);
   }
   g->profiling = enable ? 1 : 0;
   return YY_OK;
@@ -516,6 +522,19 @@ yy_status yy_grid_stage_ms(yy_grid *g, double *ms) {
     e = cudaEventElapsedTime(&t[i], g->ev[i], g->ev[i + 1]);
   if (e != cudaSuccess) return from_cuda(e);
   for (int i = 0; i < YY_STAGE_COUNT; ++i) ms[i] = t[i];
+  return YY_OK;
+}
+
+yy_status yy_grid_kernel_ms(yy_grid *g, int index, double *ms, const char **name) {
+  if (!g || !ms || !g->profiling || index < 0 || index >= g->launches || index >= YY_MAX_KERNEL_EVENTS ||
+      !g->kname[index])
+    return YY_ERR_INVALID_ARG;
+  cudaError_t e = cudaEventSynchronize(g->kev[index]);
+  float t = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, index == 0 ? g->ev[0] : g->kev[index - 1], g->kev[index]);
+  if (e != cudaSuccess) return from_cuda(e);
+  *ms = t;
+  if (name) *name = g->kname[index];
   return YY_OK;
 }
 

@@ -160,7 +160,7 @@ cudaError_t analysis_simt(yy_grid *g, const double *rho_yin, const double *rho_y
   if (fp32) {
     const size_t pp = (size_t)g->n_r * g->n_ang;
     k_rho_to_f32<<<(unsigned)((pp + 255) / 256), 256, 0, s>>>(pp, rho_yin, rho_yang, g->rho32);
-    g->launches++;
+    note_launch(g, "k_rho_to_f32", s);
     err = launch_gemm<float, float>(M, N, K, splits, g->rho32, g->rho32 + pp, g->n_r, K, g->ban32, K,
                                     out, out, M, N, s);
   } else {
@@ -168,11 +168,11 @@ cudaError_t analysis_simt(yy_grid *g, const double *rho_yin, const double *rho_y
                                       out, M, N, s);
   }
   if (err != cudaSuccess) return err;
-  g->launches++;
+  note_launch(g, "k_gemm_tn/analysis", s);
   if (splits > 1) {
     const size_t count = (size_t)M * N;
     k_sum_partials<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(count, splits, g->part, g->A);
-    g->launches++;
+    note_launch(g, "k_sum_partials", s);
     err = cudaGetLastError();
   }
   return err;
@@ -208,7 +208,7 @@ cudaError_t synthesis_simt(yy_grid *g, double *phi_yin, double *phi_yang, double
                                         g->n_r, N, s);
     }
     if (err != cudaSuccess) return err;
-    g->launches++;
+    note_launch(g, "k_gemm_tn/synthesis", s);
   }
   return cudaSuccess;
 }

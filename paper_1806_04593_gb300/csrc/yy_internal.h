@@ -9,6 +9,7 @@
 
 #define YY_LMAX_CAP 80
 #define YY_GL_WEIGHT_NODES 32
+#define YY_MAX_KERNEL_EVENTS 32
 
 // Device error word bits (set with atomicOr, read by yy_last_device_status).
 #define YY_DEVERR_CHECK 1
@@ -82,6 +83,10 @@ struct yy_grid {
 
   // kernels launched by the last yy_potential call
   int launches;
+  // per-kernel timing while profiling: an event recorded after each launch of
+  // the solve, and the kernel's name
+  cudaEvent_t kev[YY_MAX_KERNEL_EVENTS];
+  const char *kname[YY_MAX_KERNEL_EVENTS];
   // the last analysis also formed Atot (the combined moments): the separate
   // combination is skipped
   int atot_done;
@@ -101,6 +106,16 @@ struct yy_grid {
 };
 
 namespace yy {
+
+// Count a kernel launch of the current solve; while profiling, also record an
+// event after it on the launching stream (yy_grid_kernel_ms reads them).
+inline void note_launch(yy_grid *g, const char *name, cudaStream_t s) {
+  if (g->profiling && g->launches < YY_MAX_KERNEL_EVENTS) {
+    cudaEventRecord(g->kev[g->launches], s);
+    g->kname[g->launches] = name;
+  }
+  g->launches++;
+}
 
 // allocation with the test hook (see yy_debug.h)
 cudaError_t dmalloc(void **p, size_t bytes);

@@ -350,7 +350,7 @@ cudaError_t rotate_moments(yy_grid *g, bool fp64, cudaStream_t st) {
     k_rotate_moments<double><<<grid, 256, smem, st>>>(g->n_r, g->n_lm, g->rot, g->A, g->Atot);
   else
     k_rotate_moments<float><<<grid, 256, smem, st>>>(g->n_r, g->n_lm, g->rot32, g->A, g->Atot);
-  g->launches++;
+  note_launch(g, "k_rotate_moments", st);
   return cudaGetLastError();
 }
 
@@ -379,7 +379,7 @@ cudaError_t radial_scan(yy_grid *g, bool want_f32, bool f64_out, cudaStream_t st
     else
       YY_SCAN_WARP(24);
 #undef YY_SCAN_WARP
-    g->launches++;
+    note_launch(g, "k_scan_warp", st);
     return cudaGetLastError();
   }
   // long radial grids: chunks spread over warps, two passes
@@ -393,10 +393,10 @@ cudaError_t radial_scan(yy_grid *g, bool want_f32, bool f64_out, cudaStream_t st
   const int warps = s.n_patch * s.wpp * s.nc;
   const int blocks = (warps * 32 + 127) / 128;
   k_scan_maps<<<blocks, 128, 0, st>>>(s, At, g->scan, (Map4 *)g->scan_maps);
-  g->launches++;
+  note_launch(g, "k_scan_maps", st);
   k_scan_apply<<<blocks, 128, 0, st>>>(s, At, g->scan, (const Map4 *)g->scan_maps, g->cin, g->Q,
                                        want_f32 ? g->Q32 : nullptr);
-  g->launches++;
+  note_launch(g, "k_scan_apply", st);
   return cudaGetLastError();
 }
 

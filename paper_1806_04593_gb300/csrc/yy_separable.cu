@@ -426,11 +426,11 @@ cudaError_t run_separable(yy_grid *g, const double *rho_yin, const double *rho_y
   else
     k_sep_phi<T, kJCSmall><<<grid, threads, smem_phi, s>>>(shells, g->n_r, g->n_theta, g->n_phi, nt_pad, rho_yin,
                                                            rho_yang, w, az, F, (float2 *)g->sep_F0);
-  g->launches++;
+  note_launch(g, "k_sep_phi", s);
   const size_t smem_theta = theta_smem(g->n_theta, nt_pad, sizeof(T));
   k_sep_theta<T><<<shells, 256, smem_theta, s>>>(g->n_theta, g->n_lm, g->lmax + 1, nt_pad, tb, g->sep_tb0, F,
                                                     (const float2 *)g->sep_F0, g->A);
-  g->launches++;
+  note_launch(g, "k_sep_theta", s);
   return cudaGetLastError();
 }
 
@@ -639,7 +639,7 @@ cudaError_t synthesis_separable(yy_grid *g, double *phi_yin, double *phi_yang, d
     k_sep_synth<float><<<blocks, 256, g->sep_syn_smem[0], s>>>(grid_rows(g), g->n_r, g->n_theta, g->n_phi, g->lmax, g->n_lm,
                                                                n_fields, g->sep_syn_rows[0], g->Q, g->sep_P32, g->sep_dP32, g->sep_Qs32,
                                                                g->sep_tr32, o);
-  g->launches++;
+  note_launch(g, "k_sep_synth", s);
   return cudaGetLastError();
 }
 
@@ -658,7 +658,7 @@ cudaError_t separable_theta_partials(yy_grid *g, SepThetaPartials a, cudaStream_
   const size_t smem = separable_theta_partials_smem(g, a.nt_pad);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   k_sep_theta_partials<<<(grid_rows(g) + S - 1) / S, 256, smem, s>>>(a, grid_rows(g));
-  g->launches++;
+  note_launch(g, "k_sep_theta_partials", s);
   return cudaGetLastError();
 }
 
@@ -667,7 +667,7 @@ cudaError_t separable_theta_f64(yy_grid *g, cudaStream_t s) {
   const size_t smem_theta = theta_smem(g->n_theta, nt_pad, sizeof(double));
   k_sep_theta<double><<<grid_rows(g), 256, smem_theta, s>>>(g->n_theta, g->n_lm, g->lmax + 1, nt_pad, g->tbar,
                                                             g->sep_tb0, g->sep_F, (const float2 *)g->sep_F0, g->A);
-  g->launches++;
+  note_launch(g, "k_sep_theta<double>", s);
   return cudaGetLastError();
 }
 

@@ -12,6 +12,7 @@
 
 #include "yy_internal.h"
 #include "yy_tc_pair.cuh"
+#include "yy_oz_synth.cuh"
 
 namespace yy {
 
@@ -985,7 +986,7 @@ static cudaError_t launch_pair(yy_grid *g, yy_tc_tables *t, const PairMaps &maps
   const cudaError_t e = a.out_mode == 2   ? cudaLaunchKernelEx(&cfg, k_tc_pair<F, 2>, maps, a)
                         : a.out_mode == 1 ? cudaLaunchKernelEx(&cfg, k_tc_pair<F, 1>, maps, a)
                                           : cudaLaunchKernelEx(&cfg, k_tc_pair<F, 0>, maps, a);
-  g->launches++;
+  note_launch(g, a.out_mode == 0 ? "k_tc_pair/split-K" : a.out_mode == 1 ? "k_tc_pair/synthesis" : "k_tc_pair/azimuthal", s);
   return e;
 }
 
@@ -1360,7 +1361,7 @@ static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, 
   p.scale_out = t->an_rhos;
   p.out = t->an_rho;
   cudaError_t e = launch_pack_long<F>(b, g->err, s);
-  g->launches++;
+  note_launch(g, "k_pack_stream", s);
   if (e != cudaSuccess) return e;
   PairArgs a = {};
   a.stages = t->stages;
@@ -1386,7 +1387,7 @@ static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, 
     const dim3 grid((unsigned)g->n_r, (unsigned)((g->n_lm + 255) / 256));
     k_reduce_rotate<<<grid, 256, 0, s>>>(g->n_r, g->n_lm, t->an_splits, t->part, t->an_rhos, t->an_tabs, t->an_mono,
                                          t->an_mean, t->an_colsum, g->rot32, g->A, g->Atot);
-    g->launches++;
+    note_launch(g, "k_reduce_rotate", s);
     g->atot_done = 1;
     return cudaGetLastError();
   }
@@ -1394,7 +1395,7 @@ static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, 
   k_reduce_partials<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(M, g->n_lm, t->an_splits, t->part, t->an_rhos,
                                                                   t->an_tabs, t->an_mono, t->an_mean, t->an_colsum,
                                                                   g->A);
-  g->launches++;
+  note_launch(g, "k_reduce_partials", s);
   return cudaGetLastError();
 }
 
@@ -1424,7 +1425,7 @@ static cudaError_t pack_coefficients_form(yy_grid *g, yy_tc_tables *t, cudaStrea
     p.out = t->sy_q[c];
   }
   cudaError_t e = launch_pack<F>(b, 3, s);
-  g->launches++;
+  note_launch(g, "k_pack_reg/coefficients", s);
   return e;
 }
 
@@ -1507,7 +1508,7 @@ static cudaError_t theta_form(yy_grid *g, yy_tc_tables *t, bool grad, cudaStream
     k_theta_g<2, true><<<(a.n_shells + 1) / 2, 256, theta_smem<2, true>(g), s>>>(a);
   else
     k_theta_g<2, false><<<(a.n_shells + 1) / 2, 256, theta_smem<2, false>(g), s>>>(a);
-  g->launches++;
+  note_launch(g, "k_theta_g", s);
   return cudaGetLastError();
 }
 
@@ -1592,7 +1593,7 @@ static cudaError_t separable_analysis_form(yy_grid *g, yy_tc_tables *t, const do
   p.wrow = g->sep_w32;            // rho w
   p.w_rows = g->n_theta;
   cudaError_t e = launch_pack<F>(b, 1, s);
-  g->launches++;
+  note_launch(g, "k_pack_reg/rho_rows", s);
   if (e != cudaSuccess) return e;
   PairArgs a = {};
   a.stages = t->san_stages;
@@ -1694,6 +1695,7 @@ struct OzThetaArgs {
   const double *tab[3];         // [n_theta][n_lm]: P, dP/dtheta, m P / sin theta (float64)
   __nv_bfloat16 *G[4];          // per field: slices [6][rows_pad][kMaxK]
   int *gexp[4];                 // per field: [rows_pad] power of two of a unit level-5 sum
+  int bias;                     // write the bias digits of output mode 4 in slots nt and nt + 1
 };
 
 // Balanced base-256 digits of X < 2^48 (most significant first): each
@@ -1720,7 +1722,7 @@ __host__ __device__ __forceinline__ void oz_digits(unsigned long long X, int (&d
 // each with the sign of G.  A row of zeros (or of values below the normal
 // range) gets zero digits.
 __device__ __forceinline__ void oz_theta_row(unsigned long long b0, unsigned long long b1, int lane,
-                                             __nv_bfloat16 *dst, size_t stride, int *gexp) {
+                                             __nv_bfloat16 *dst, size_t stride, int *gexp, int nt, int bias) {
   unsigned long long mb = max(b0 & 0x7FFFFFFFFFFFFFFFull, b1 & 0x7FFFFFFFFFFFFFFFull);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
@@ -1737,10 +1739,16 @@ __device__ __forceinline__ void oz_theta_row(unsigned long long b0, unsigned lon
       X = ((((bits[h] & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> (sh - 1)) + 1ull) >> 1;   // round half up
     oz_digits(X, d[h]);
   }
+  // the bias digits of output mode 4 (slots nt and nt + 1 hold G = 0)
+  const int t1 = 63 - lane;
+  const int bias0 = bias ? (lane == nt ? 0 : lane == nt + 1 ? 1 : -1) : -1;
+  const int bias1 = bias ? (t1 == nt ? 0 : t1 == nt + 1 ? 1 : -1) : -1;
 #pragma unroll
   for (int sl = 0; sl < 6; ++sl) {
-    dst[sl * stride + lane] = __float2bfloat16_rn((b0 >> 63) ? -(float)d[0][sl] : (float)d[0][sl]);
-    dst[sl * stride + 63 - lane] = __float2bfloat16_rn((b1 >> 63) ? -(float)d[1][sl] : (float)d[1][sl]);
+    const float v0 = sl == bias0 ? kOzBiasG : ((b0 >> 63) ? -(float)d[0][sl] : (float)d[0][sl]);
+    const float v1 = sl == bias1 ? kOzBiasG : ((b1 >> 63) ? -(float)d[1][sl] : (float)d[1][sl]);
+    dst[sl * stride + lane] = __float2bfloat16_rn(v0);
+    dst[sl * stride + t1] = __float2bfloat16_rn(v1);
   }
   // value = 2^(e + 1 - 64) (digit sums): trig scale 2^1, digit weights 2^-64
   if (lane == 0) *gexp = exm == 0 ? 0 : e + 1 - 64;
@@ -1832,8 +1840,8 @@ __global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
   __nv_bfloat16 *const Gf = f == 0 ? a.G[0] : f == 1 ? a.G[1] : f == 2 ? a.G[2] : a.G[3];
   int *const gexp = f == 0 ? a.gexp[0] : f == 1 ? a.gexp[1] : f == 2 ? a.gexp[2] : a.gexp[3];
   const size_t row = (size_t)shell * a.n_theta + j, rowm = (size_t)shell * a.n_theta + jm;
-  oz_theta_row(g0, g1, lane, Gf + row * FormOzaki::kMaxK, stride, gexp + row);
-  if (jm != j) oz_theta_row(r0, r1, lane, Gf + rowm * FormOzaki::kMaxK, stride, gexp + rowm);
+  oz_theta_row(g0, g1, lane, Gf + row * FormOzaki::kMaxK, stride, gexp + row, a.nt, a.bias);
+  if (jm != j) oz_theta_row(r0, r1, lane, Gf + rowm * FormOzaki::kMaxK, stride, gexp + rowm, a.nt, a.bias);
 }
 
 // The weighted densities of the separable analysis, rho w, as digit rows for
@@ -1919,6 +1927,9 @@ __global__ void __launch_bounds__(256) k_rhow_ozaki(OzRhoArgs a) {
 
 struct yy_oz_tables {
   int rows, rows_pad, bn, row_tiles, b_rows_pad, stages, pair_slots;
+  int bias;                     // synthesis with biased level sums (one fill): k_oz_synth
+  int synth_slots;              // resident clusters of k_oz_synth (0: use k_tc_pair output mode 4)
+  yy::OzSynthMaps synth_maps;   // its G maps (those of `maps`) and the trig map with 48-row boxes
   void *G[4];                   // per field: slices [6][rows_pad][64]
   int *gexp[4];                 // per field: [rows_pad]
   void *trig;                   // slices of trig / 2: [6][b_rows_pad][64]
@@ -2051,7 +2062,7 @@ cudaError_t ozaki_analysis(yy_grid *g, const double *ry, const double *rg, cudaS
     k_rhow_ozaki<5><<<blocks, 256, 0, s>>>(ra);
   else
     k_rhow_ozaki<kCmax><<<blocks, 256, 0, s>>>(ra);
-  g->launches++;
+  note_launch(g, "k_rhow_ozaki", s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   PairArgs a = {};
@@ -2083,7 +2094,7 @@ cudaError_t ozaki_analysis(yy_grid *g, const double *ry, const double *rg, cudaS
   cudaLaunchConfig_t cfg =
       pair_config(pairs, o->an_stages * pair_stage_bytes<F>(o->an_bn) + kSmemFixed + kEpiStageBytes, s, attr);
   e = cudaLaunchKernelEx(&cfg, k_tc_pair<F, 3>, o->an_maps, a);
-  g->launches++;
+  note_launch(g, "k_tc_pair<FormOzaki,3>/analysis", s);
   if (e != cudaSuccess) return e;
   return separable_theta_f64(g, s);
 }
@@ -2099,22 +2110,26 @@ yy_status ozaki_prepare(yy_grid *g) {
   o->rows_pad = round_up(o->rows, 2 * kPairRows);
   o->bn = 32;   // eight accumulators of bn columns fill one 256-column TMEM buffer
   o->row_tiles = (g->n_phi + o->bn - 1) / o->bn;
-  o->b_rows_pad = o->row_tiles * o->bn;
+  // trig rows padded for both synthesis kernels: tiles of bn (k_tc_pair) and
+  // of kOzSynthBN (k_oz_synth)
+  o->b_rows_pad = round_up(g->n_phi, kOzSynthBN);
   o->stages = pair_stages<F>(o->bn, kEpiStageBytes);
   yy_status st = YY_OK;
   if (o->stages < 2 ||
-      cudaFuncSetAttribute(k_tc_pair<F, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) != cudaSuccess)
+      cudaFuncSetAttribute(k_tc_pair<F, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) != cudaSuccess ||
+      cudaFuncSetAttribute(k_tc_pair<F, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) != cudaSuccess)
     st = YY_ERR_NOT_SUPPORTED;
   if (st == YY_OK) {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg =
         pair_config(64, o->stages * pair_stage_bytes<F>(o->bn) + kSmemFixed + kEpiStageBytes, 0, attr);
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, (void *)k_tc_pair<F, 3>, &cfg) != cudaSuccess || n < 1) {
+    int n = 0, n4 = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (void *)k_tc_pair<F, 3>, &cfg) != cudaSuccess || n < 1 ||
+        cudaOccupancyMaxActiveClusters(&n4, (void *)k_tc_pair<F, 4>, &cfg) != cudaSuccess || n4 < 1) {
       cudaGetLastError();
       st = YY_ERR_NOT_SUPPORTED;
     }
-    o->pair_slots = n;
+    o->pair_slots = n < n4 ? n : n4;
   }
   cudaError_t e = cudaSuccess;
   auto A = [&](void **ptr, size_t bytes) {
@@ -2138,14 +2153,36 @@ yy_status ozaki_prepare(yy_grid *g) {
     std::vector<uint16_t> sl(t_elems, 0);
     if (cudaMemcpy(tr.data(), g->sep_tr, tr.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
       st = YY_ERR_CUDA;
-    for (int k = 0; k < g->n_phi && st == YY_OK; ++k)
+    // output mode 4 needs two spare K columns and |S_L| < 2^22 for every
+    // level and longitude: |S_L| <= 128 sum over the level's products (s, u)
+    // of sum_t |trig digit u at t| (G digits are at most 128 in magnitude)
+    bool bias = nt + 2 <= F::kMaxK;
+    for (int k = 0; k < g->n_phi && st == YY_OK; ++k) {
+      long long asum[6] = {0, 0, 0, 0, 0, 0};
       for (int t = 0; t < nt; ++t) {
         const double y = tr[(size_t)t * g->n_phi + k] * 0.5;
         int d[6];
         oz_digits((unsigned long long)floor(ldexp(fabs(y), 48) + 0.5), d);
-        for (int s2 = 0; s2 < F::kPB; ++s2)
+        for (int s2 = 0; s2 < F::kPB; ++s2) {
           sl[((size_t)s2 * o->b_rows_pad + k) * F::kMaxK + t] = bf16_int(y < 0 ? -d[s2] : d[s2]);
+          asum[s2] += d[s2] < 0 ? -d[s2] : d[s2];
+        }
       }
+      for (int L = 0; L < F::kAccs; ++L) {
+        long long b = 0;
+        for (int s2 = F::s_lo(L); s2 <= (L < 5 ? L : 5); ++s2) b += asum[L - s2];
+        if (128 * b >= (1ll << 22)) bias = false;
+      }
+    }
+    if (bias) {
+      // the trig side of the bias columns: 2^11 in every slice at nt, in slice 5 at nt + 1
+      const uint16_t two11 = bf16_int(2048);   // a power of two: exact in bf16
+      for (int k = 0; k < o->b_rows_pad; ++k) {
+        for (int s2 = 0; s2 < F::kPB; ++s2) sl[((size_t)s2 * o->b_rows_pad + k) * F::kMaxK + nt] = two11;
+        sl[((size_t)5 * o->b_rows_pad + k) * F::kMaxK + nt + 1] = two11;
+      }
+    }
+    o->bias = bias ? 1 : 0;
     if (st == YY_OK && cudaMemcpy(o->trig, sl.data(), t_elems * F::kElem, cudaMemcpyHostToDevice) != cudaSuccess)
       st = YY_ERR_CUDA;
   }
@@ -2154,6 +2191,20 @@ yy_status ozaki_prepare(yy_grid *g) {
     for (int f = 0; f < 4 && ok; ++f)
       ok = make_map<F>(&o->maps.a[f], o->G[f], F::kMaxK, F::kPA * o->rows_pad, kPairRows);
     if (!ok) st = YY_ERR_NOT_SUPPORTED;
+  }
+  if (st == YY_OK && o->bias && F::kMaxK == kOzSynthKB * 32) {
+    // the synthesis kernel with the G tile resident (falls back to the pair
+    // kernel's output mode 4 where it cannot run)
+    int n = 0;
+    for (int f = 0; f < 4; ++f) o->synth_maps.a[f] = o->maps.a[f];
+    if (make_map<F>(&o->synth_maps.b, o->trig, F::kMaxK, F::kPB * o->b_rows_pad, kOzSynthBN / 2) &&
+        cudaFuncSetAttribute(k_oz_synth, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSynthSmem) == cudaSuccess) {
+      cudaLaunchAttribute attr[1];
+      cudaLaunchConfig_t cfg = pair_config(64, kOzSynthSmem, 0, attr);
+      if (cudaOccupancyMaxActiveClusters(&n, (void *)k_oz_synth, &cfg) != cudaSuccess) n = 0;
+    }
+    cudaGetLastError();
+    o->synth_slots = n > 0 ? n : 0;
   }
   if (st == YY_OK) st = ozaki_prepare_analysis(g, o);
   if (st != YY_OK) {
@@ -2177,6 +2228,7 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
   ta.nt = 2 * g->lmax + 1;
   ta.n_jobs = n_jobs;
   ta.rows_pad = o->rows_pad;
+  ta.bias = o->bias;
   ta.Q = g->Q;
   ta.tab[0] = g->sep_P;
   ta.tab[1] = g->sep_dP;
@@ -2187,12 +2239,38 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
   }
   const size_t warps = (size_t)ta.n_shells * ((g->n_theta + 1) / 2) * n_jobs;   // mirrored row pairs
   k_theta_ozaki<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(ta);
-  g->launches++;
+  note_launch(g, "k_theta_ozaki", s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t comp = (size_t)g->n_r * g->n_ang;
   double *o0[4] = {py, gy, gy ? gy + comp : nullptr, gy ? gy + 2 * comp : nullptr};
   double *o1[4] = {pg, gg, gg ? gg + comp : nullptr, gg ? gg + 2 * comp : nullptr};
+  if (o->bias && o->synth_slots > 0) {
+    OzSynthArgs z = {};
+    z.cells = o->rows;
+    z.cell_tiles = o->rows_pad / (2 * kPairRows);
+    z.cols = g->n_phi;
+    z.col_tiles = o->b_rows_pad / kOzSynthBN;
+    z.a_rows = o->rows_pad;
+    z.b_rows = o->b_rows_pad;
+    z.out_split = g->n_r * g->n_theta;
+    z.ldo = g->n_phi;
+    z.n_jobs = n_jobs;
+    z.prefetch = 1;
+    z.err = g->err;
+    for (int f = 0; f < n_jobs; ++f) {
+      z.job[f].out0 = o0[f];
+      z.job[f].out1 = o1[f];
+      z.job[f].cell_exp = o->gexp[f];
+    }
+    const int tiles = z.cell_tiles * n_jobs;
+    const int pairs = tiles < o->synth_slots ? tiles : o->synth_slots;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = pair_config(pairs, kOzSynthSmem, s, attr);
+    e = cudaLaunchKernelEx(&cfg, k_oz_synth, o->synth_maps, z);
+    note_launch(g, "k_oz_synth", s);
+    return e;
+  }
   PairArgs a = {};
   a.stages = o->stages;
   a.cells = o->rows;
@@ -2205,7 +2283,7 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
   a.kb_per_split = a.kb_total;
   a.a_rows = o->rows_pad;
   a.b_rows = o->b_rows_pad;
-  a.out_mode = 3;
+  a.out_mode = o->bias ? 4 : 3;
   a.out_split = g->n_r * g->n_theta;
   a.ldo = g->n_phi;
   a.n_jobs = n_jobs;
@@ -2222,8 +2300,8 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
   const int pairs = tiles < o->pair_slots ? tiles : o->pair_slots;
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = pair_config(pairs, o->stages * pair_stage_bytes<F>(o->bn) + kSmemFixed + kEpiStageBytes, s, attr);
-  e = cudaLaunchKernelEx(&cfg, k_tc_pair<F, 3>, o->maps, a);
-  g->launches++;
+  e = o->bias ? cudaLaunchKernelEx(&cfg, k_tc_pair<F, 4>, o->maps, a) : cudaLaunchKernelEx(&cfg, k_tc_pair<F, 3>, o->maps, a);
+  note_launch(g, "k_tc_pair<FormOzaki,3>/synthesis", s);
   return e;
 }
 

@@ -1,5 +1,5 @@
 // The Ozaki forms of the pair kernel: float64 results from exact products of
-// bf16 digits (output mode 3 of k_tc_pair), and their epilogue.  Included by
+// bf16 digits (output modes 3 and 4 of k_tc_pair), and their epilogues.  Included by
 // yy_tc_pair.cuh after the PTX wrappers it uses.
 #pragma once
 
@@ -123,6 +123,47 @@ __device__ __forceinline__ void ozaki_accumulate(uint32_t tcol, int bn, long lon
   oz_level_f(tcol, bn, 6, w);
 #pragma unroll
   for (int j = 0; j < 8; ++j) lo[j] += u[j] + w[j];
+}
+
+// ---- the biased single-fill epilogue (output mode 4) ----------------------
+//
+// Two spare columns of the K padding carry a constant product into every
+// level accumulator: column nt holds the digit 6144 = 3 2^11 in slice 0 of
+// each G row and 2048 = 2^11 in all six slices of the trig table, column
+// nt + 1 holds 6144 in slice 1 of each G row and 2048 in slice 5 of the trig
+// table.  Of the kept products (s, t) exactly one per level meets a non-zero
+// pair there -- (0, L) for L <= 5 in column nt, (1, 5) for L = 6 in column
+// nt + 1 -- so every level sum becomes 3 2^22 + S_L.  The host checks, from
+// the trig digits and |G digit| <= 128, that |S_L| < 2^22 for every column;
+// the accumulator then lies in [2^23, 2^24), where fp32 steps by exactly 1,
+// and its bit pattern minus that of 3 2^22 is S_L as an integer: no float to
+// integer conversions.
+constexpr uint32_t kOzBiasBits = 0x4B400000u;        // fp32 bits of 3 2^22
+constexpr float kOzBiasG = 6144.0f, kOzBiasT = 2048.0f;
+// a 2^8 + b of two biased levels minus the biases' share (mod 2^32)
+constexpr uint32_t kOzBias2 = (kOzBiasBits << 8) + kOzBiasBits;
+
+// Float64 values of 8 columns (TMEM column tcol, accumulator L at + L bn) of
+// a single fill, rows scaled by 2^ce per unit level-6 sum.  In units of a
+// level-4 sum, V = S_0 2^32 + S_1 2^24 + S_2 2^16 + S_3 2^8 + S_4 +
+// round((S_5 2^8 + S_6) / 2^16): an integer below 2^53 in magnitude (|S_0| <=
+// 2^14 K with K <= 64), so its conversion is exact and the only rounding is
+// that of the two lowest levels, at most half a level-4 unit (2^-49 of the
+// rows' scales, below the digits' own representation error).
+__device__ __forceinline__ void ozaki_biased8(uint32_t tcol, int bn, int ce, double *dst) {
+  uint32_t u[7][8];
+#pragma unroll
+  for (int L = 0; L < 7; ++L) tmem_ld8_async(tcol + (uint32_t)(L * bn), u[L]);
+  tmem_wait_ld();
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int t56 = (int)((u[5][j] << 8) + u[6][j] - kOzBias2);          // S_5 2^8 + S_6
+    const int lo = (int)((u[3][j] << 8) + u[4][j] - kOzBias2) + ((t56 + 32768) >> 16);
+    const int mid = (int)((u[1][j] << 8) + u[2][j] - kOzBias2);          // S_1 2^8 + S_2
+    const int hi = (int)(u[0][j] - kOzBiasBits);                          // S_0
+    const long long V = ((long long)hi << 32) + ((long long)mid << 16) + (long long)lo;
+    dst[j] = i64_ldexp(V, ce + 16);
+  }
 }
 
 // The chunk's float64 values: one rounding, in the final addition.

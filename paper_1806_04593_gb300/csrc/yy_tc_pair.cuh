@@ -401,7 +401,8 @@ struct PairArgs {
   int a_rows, b_rows;           // rows of one piece in the stacked A / B operands
   int out_mode;                 // 1: scaled float64 job outputs; 0: raw fp32 partial sums;
                                 // 2: scaled float64 outputs stored along the rows of each cell;
-                                // 3: as 2, from the exact level sums of FormOzaki
+                                // 3: as 2, from the exact level sums of FormOzaki;
+                                // 4: as 3 with one fill and biased level sums
   float *part;                  // mode 0: part[(z rows + row) part_ld + cell]
   int part_ld;
   int out_split;
@@ -622,7 +623,7 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
           }
         }
       }
-    } else if constexpr (OUT_MODE == 2 || OUT_MODE == 3) {
+    } else if constexpr (OUT_MODE == 2 || OUT_MODE == 3 || OUT_MODE == 4) {
       // Cells are rows of the output arrays (stride ldo) and the accumulator
       // columns run along them: each lane holds 16 consecutive values of its
       // cell's row.  They go through this warp's shared-memory block, and the
@@ -632,10 +633,12 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
       double *ebuf = reinterpret_cast<double *>(wbuf);                          // [32][kEpiPad]
       double **rowp = reinterpret_cast<double **>(wbuf + 32 * kEpiPad * 8);     // [32] output rows
       const bool vec = (a.ldo & 1) == 0;   // rows start on 16-byte boundaries (with 16-byte aligned bases)
-      if constexpr (OUT_MODE == 3) {
+      if constexpr (OUT_MODE == 3 || OUT_MODE == 4) {
         // FormOzaki: the tile's fills (kb_chunk K blocks each) are added in
         // registers, level by level; this warp owns the 8-column chunk sub
         // (bn <= 8 kEpiPerQuarter), and the values are formed after the last fill.
+        // Mode 4 has one fill with biased level sums (ozaki_biased8) and forms
+        // the values straight from the accumulator.
         const int k = sub;
         const bool mine = k < a.bn / 8;
         for (int t = pair; t < total; t += n_pairs) {
@@ -667,7 +670,12 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
             }
             tc_fence_after();
             const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
-            if (mine) ozaki_accumulate(tbase + (uint32_t)(k * 8), a.bn, hi, lo);
+            if (mine) {
+              if constexpr (OUT_MODE == 4)
+                ozaki_biased8(tbase + (uint32_t)(k * 8), a.bn, ce, ebuf + lane * kEpiPad);
+              else
+                ozaki_accumulate(tbase + (uint32_t)(k * 8), a.bn, hi, lo);
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive_cluster_relaxed(tempty_even + (uint32_t)(b * sizeof(uint64_t)));
@@ -675,7 +683,7 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
           if (!ok) break;
           if (mine) {
             const int row0 = rt * a.bn + k * 8;
-            ozaki_finish(hi, lo, ce, ebuf + lane * kEpiPad);
+            if constexpr (OUT_MODE == 3) ozaki_finish(hi, lo, ce, ebuf + lane * kEpiPad);
             __syncwarp();
             if (vec) {
               // lanes 4 c' + e: cell 8 q + c', values 2 e and 2 e + 1 of the run

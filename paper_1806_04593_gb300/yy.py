@@ -103,6 +103,8 @@ def load():
     lib.yy_grid_set_profiling.restype = I
     lib.yy_grid_stage_ms.argtypes = [P, ctypes.POINTER(D)]
     lib.yy_grid_stage_ms.restype = I
+    lib.yy_grid_kernel_ms.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_char_p)]
+    lib.yy_grid_kernel_ms.restype = I
     lib.yy_debug_fail_alloc_after.argtypes = [I]
     lib.yy_debug_fail_alloc_after.restype = None
     lib.yy_batch_create.argtypes = [P, I, ctypes.POINTER(P)]
@@ -253,6 +255,25 @@ def yy_grid_stage_ms(handle):
     buf = (ctypes.c_double * YY_STAGE_COUNT)()
     st = load().yy_grid_stage_ms(handle, buf)
     return st, dict(zip(STAGES, list(buf)))
+
+
+def yy_grid_kernel_ms(handle, index):
+    """Returns (status, ms, name) of kernel `index` of the last profiled solve."""
+    ms = ctypes.c_double(0.0)
+    name = ctypes.c_char_p()
+    st = load().yy_grid_kernel_ms(handle, int(index), ctypes.byref(ms), ctypes.byref(name))
+    return st, ms.value, (name.value.decode() if name.value else None)
+
+
+def yy_grid_kernels_ms(handle):
+    """List of (name, ms) for every kernel of the last profiled solve."""
+    out = []
+    for i in range(min(yy_last_launch_count(handle), 32)):
+        st, ms, name = yy_grid_kernel_ms(handle, i)
+        if st != YY_OK:
+            raise YYError(st, "yy_grid_kernel_ms")
+        out.append((name, ms))
+    return out
 
 
 def yy_debug_fail_alloc_after(n):

@@ -6,8 +6,8 @@ Checks, per the batched workload's test plan:
   - graph replay is bitwise deterministic, and new buffers are recorded anew;
   - the 64-field workload (n_r ~ U{100..600}, 2 / 1.5 / 1 degree cells,
     l_max ~ U{10..40}) in the tuned FP16X2 form agrees with the float64 GPU
-    path field by field within the form's tolerance (Phi 1e-6, -grad Phi
-    1e-5, relative max-norm) and with the float64 oracle on sampled cells.
+    path field by field within the form's tolerance (Phi 1e-6 pointwise,
+    -grad Phi 1e-5 normwise) and with the float64 oracle on sampled cells.
 """
 
 import numpy as np
@@ -15,9 +15,14 @@ import pytest
 
 from paper_1806_04593_gb300 import inputs
 
-from .gpu_common import lib, rel_max, require_gpu
+from .gpu_common import field_err, grad_err, lib, phi_err, require_gpu
 
 pytestmark = pytest.mark.gpu
+
+# FP16X2 against the float64 path over the 64 uneven fields (l_max up to 40):
+# Phi pointwise at the 1e-6 target (worst measured 3.8e-7), -grad Phi
+# normwise at 4x the worst measured (2.5e-6)
+TOL_PHI, TOL_GRAD = 1e-6, 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -130,15 +135,15 @@ def test_batched_workload_tuned_fp16x2(yy, oracle_grid):
         ref = g.solve(r[0], r[1], gradient=True, prec="fp64")
         torch.cuda.synchronize()
         for q, (phi, grad) in enumerate((("phi_yin", "grad_yin"), ("phi_yang", "grad_yang"))):
-            assert rel_max(o[q].cpu().numpy(), ref[phi].cpu().numpy()) <= 1e-6, (f, phi)
-            assert rel_max(o[2 + q].cpu().numpy(), ref[grad].cpu().numpy()) <= 1e-5, (f, grad)
+            assert phi_err(o[q].cpu().numpy(), ref[phi].cpu().numpy()) <= TOL_PHI, (f, phi)
+            assert grad_err(o[2 + q].cpu().numpy(), ref[grad].cpu().numpy()) <= TOL_GRAD, (f, grad)
         g.close()
         if f % 16 == 0:
             cells = np.sort(rng.choice(sp.n_ang, 12, replace=False))
             ref_o = oracle_grid(sp).solve(r[0].cpu().numpy(), r[1].cpu().numpy(), gradient=True, cells=cells)
             j, k = np.divmod(cells, sp.n_phi)
-            assert rel_max(o[0].cpu().numpy()[:, j, k], ref_o["phi_yin"]) <= 1e-6, f
-            assert rel_max(o[3].cpu().numpy()[:, :, j, k], ref_o["grad_yang"]) <= 1e-5, f
+            assert phi_err(o[0].cpu().numpy()[:, j, k], ref_o["phi_yin"]) <= TOL_PHI, f
+            assert grad_err(o[3].cpu().numpy()[:, :, j, k], ref_o["grad_yang"]) <= TOL_GRAD, f
         del ref
     b.close()
 
@@ -160,8 +165,8 @@ def test_batch_fp64_ozaki_tuned_matches_fp64(yy):
     torch.cuda.synchronize()
     assert b.device_status() == yy.YY_OK
     for sp, o, r in zip(specs, out, ref):
-        for x, y in zip(o, r):
-            assert rel_max(x.cpu().numpy(), y.cpu().numpy()) <= 2e-13, sp.name
+        for key, x, y in zip(("phi_yin", "phi_yang", "grad_yin", "grad_yang"), o, r):
+            assert field_err(key, x.cpu().numpy(), y.cpu().numpy()) <= 2e-13, (sp.name, key)
     names = {yy.ANALYSES[k]: k for k in yy.ANALYSES}
     for f in (0, 3):
         g = yy.Grid.from_spec(specs[f])

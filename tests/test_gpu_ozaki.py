@@ -1,7 +1,9 @@
 """YY_FP64_OZAKI: float64 results with the synthesis's azimuthal stage on the
-tensor cores by the Ozaki scheme, against the float64 oracle at the float64
-tolerance (1e-12 relative, max-norm over the field, Phi and -grad Phi) and
-against the CUDA-core float64 path.
+tensor cores by the Ozaki scheme, against the float64 oracle and against
+the CUDA-core float64 path.  The float64 bar is 1e-12 relative (Phi
+pointwise, -grad Phi normwise); the tests assert 4e-13 against the oracle,
+about 4.6x the worst error measured (8.6e-14), so that a regression shows
+before the bar is reached.
 
 Each operand is six balanced base-256 digits of round(|x| 2^48) under a
 per-row scale that puts |x| at most 1/2, so a product term is off by at most
@@ -16,11 +18,11 @@ import pytest
 
 from paper_1806_04593_gb300 import inputs
 
-from .gpu_common import gpu_solve, lib, rel_max, require_gpu
+from .gpu_common import field_err, gpu_solve, grad_err, lib, phi_err, require_gpu
 
 pytestmark = pytest.mark.gpu
 
-TOL_FP64 = 1e-12
+TOL_FP64 = 4e-13
 TOL_VS_FP64_PATH = 2e-13
 
 
@@ -62,10 +64,10 @@ def test_ozaki_matches_oracle_and_fp64_path(yy, oracle_grid, name, analysis):
         assert n_oz == n_64 + 2, (n_oz, n_64)
     ref = oracle_grid(spec).solve(ry, rg, gradient=True)
     for q in ("yin", "yang"):
-        assert rel_max(oz["phi_" + q], ref["phi_" + q]) <= TOL_FP64, q
-        assert rel_max(oz["grad_" + q], ref["grad_" + q]) <= TOL_FP64, q
+        assert phi_err(oz["phi_" + q], ref["phi_" + q]) <= TOL_FP64, q
+        assert grad_err(oz["grad_" + q], ref["grad_" + q]) <= TOL_FP64, q
     for key in oz:
-        assert rel_max(oz[key], f64[key]) <= TOL_VS_FP64_PATH, key
+        assert field_err(key, oz[key], f64[key]) <= TOL_VS_FP64_PATH, key
 
 
 def test_ozaki_production_sampled(yy, oracle_grid):
@@ -79,8 +81,8 @@ def test_ozaki_production_sampled(yy, oracle_grid):
     ref = oracle_grid(spec).solve(ry, rg, gradient=True, cells=cells)
     j, k = np.divmod(cells, spec.n_phi)
     for q in ("yin", "yang"):
-        assert rel_max(out["phi_" + q][:, j, k], ref["phi_" + q]) <= TOL_FP64
-        assert rel_max(out["grad_" + q][:, :, j, k], ref["grad_" + q]) <= TOL_FP64
+        assert phi_err(out["phi_" + q][:, j, k], ref["phi_" + q]) <= TOL_FP64
+        assert grad_err(out["grad_" + q][:, :, j, k], ref["grad_" + q]) <= TOL_FP64
 
 
 def test_ozaki_analysis_in_several_fills(yy, oracle_grid):
@@ -103,13 +105,13 @@ def test_ozaki_analysis_in_several_fills(yy, oracle_grid):
         # stage), scans, synthesis (polar stage, digit products)
         assert n_oz == 6, n_oz
         for key in ("phi", "grad"):
-            assert rel_max(out[key].cpu().numpy(), f64[key].cpu().numpy()) <= TOL_VS_FP64_PATH, key
+            assert field_err(key, out[key].cpu().numpy(), f64[key].cpu().numpy()) <= TOL_VS_FP64_PATH, key
         rng = np.random.default_rng(48)
         cells = np.sort(rng.choice(spec.n_ang, 48, replace=False))
         ref = oracle_grid(spec).solve(rho, gradient=True, cells=cells)
         j, k = np.divmod(cells, spec.n_phi)
-        assert rel_max(out["phi"].cpu().numpy()[:, j, k], ref["phi"]) <= TOL_FP64
-        assert rel_max(out["grad"].cpu().numpy()[:, :, j, k], ref["grad"]) <= TOL_FP64
+        assert phi_err(out["phi"].cpu().numpy()[:, j, k], ref["phi"]) <= TOL_FP64
+        assert grad_err(out["grad"].cpu().numpy()[:, :, j, k], ref["grad"]) <= TOL_FP64
     finally:
         g.close()
 
@@ -133,8 +135,8 @@ def test_ozaki_ragged_and_highest_degree(yy):
             g.close()
         ref = OracleGrid(spec.r_edges, nt, npp, 0.03, 0.05, lmax).solve(ry, rg, gradient=True)
         for q in ("yin", "yang"):
-            assert rel_max(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64, (lmax, q)
-            assert rel_max(out["grad_" + q], ref["grad_" + q]) <= TOL_FP64, (lmax, q)
+            assert phi_err(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64, (lmax, q)
+            assert grad_err(out["grad_" + q], ref["grad_" + q]) <= TOL_FP64, (lmax, q)
 
 
 def test_ozaki_polar_grid(yy, oracle_grid):
@@ -149,8 +151,8 @@ def test_ozaki_polar_grid(yy, oracle_grid):
         torch.cuda.synchronize()
         assert yy.yy_last_device_status(g.handle) == yy.YY_OK
         ref = oracle_grid(spec).solve(rho, gradient=True)
-        assert rel_max(out["phi"].cpu().numpy(), ref["phi"]) <= TOL_FP64
-        assert rel_max(out["grad"].cpu().numpy(), ref["grad"]) <= TOL_FP64
+        assert phi_err(out["phi"].cpu().numpy(), ref["phi"]) <= TOL_FP64
+        assert grad_err(out["grad"].cpu().numpy(), ref["grad"]) <= TOL_FP64
     finally:
         g.close()
 
@@ -212,7 +214,7 @@ def test_ozaki_long_rows_keep_the_float64_analysis(yy, oracle_grid):
         cells = np.sort(rng.choice(spec.n_ang, 64, replace=False))
         ref = oracle_grid(spec).solve(rho, gradient=True, cells=cells)
         j, k = np.divmod(cells, spec.n_phi)
-        assert rel_max(out["phi"].cpu().numpy()[:, j, k], ref["phi"]) <= TOL_FP64
-        assert rel_max(out["grad"].cpu().numpy()[:, :, j, k], ref["grad"]) <= TOL_FP64
+        assert phi_err(out["phi"].cpu().numpy()[:, j, k], ref["phi"]) <= TOL_FP64
+        assert grad_err(out["grad"].cpu().numpy()[:, :, j, k], ref["grad"]) <= TOL_FP64
     finally:
         g.close()

@@ -1,7 +1,9 @@
 """GPU path (through the C ABI) against the CPU oracle.
 
-Tolerance of the float64 path: 1e-12 relative (max-norm over the field) for
-Phi and -grad Phi, the bar the solver is specified to; tables 1e-13.
+Tolerance of the float64 path: the bar the solver is specified to is 1e-12
+relative (Phi pointwise, |dPhi| / |Phi| at every cell; -grad Phi normwise);
+the tests assert 1e-13, about 8x the worst error measured (1.3e-14), so
+that a regression shows before the bar is reached.  Tables 1e-13.
 """
 
 import math
@@ -11,11 +13,11 @@ import pytest
 
 from paper_1806_04593_gb300 import inputs
 
-from .gpu_common import K_lm, gpu_solve, lib, mode_index, rel_l2, rel_max, require_gpu
+from .gpu_common import K_lm, field_err, gpu_solve, grad_err, lib, mode_index, phi_err, rel_l2, require_gpu
 
 pytestmark = pytest.mark.gpu
 
-TOL_FP64 = 1e-12
+TOL_FP64 = 1e-13
 
 
 @pytest.fixture(scope="module")
@@ -153,9 +155,9 @@ def test_fp64_potential_and_gradient_match_oracle(yy, oracle_grid, name, analysi
         g.set_analysis("auto")
     ref = oracle_grid(spec).solve(ry, rg, gradient=True)
     for q in ("yin", "yang"):
-        assert rel_max(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64, q
+        assert phi_err(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64, q
         assert rel_l2(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64, q
-        assert rel_max(out["grad_" + q], ref["grad_" + q]) <= TOL_FP64, q
+        assert grad_err(out["grad_" + q], ref["grad_" + q]) <= TOL_FP64, q
 
 
 def test_fp64_production_sampled_cells(yy, oracle_grid):
@@ -171,9 +173,9 @@ def test_fp64_production_sampled_cells(yy, oracle_grid):
     j, k = np.divmod(cells, spec.n_phi)
     for q in ("yin", "yang"):
         got = out["phi_" + q][:, j, k]
-        assert rel_max(got, ref["phi_" + q]) <= TOL_FP64, q
+        assert phi_err(got, ref["phi_" + q]) <= TOL_FP64, q
         gg = out["grad_" + q][:, :, j, k]
-        assert rel_max(gg, ref["grad_" + q]) <= TOL_FP64, q
+        assert grad_err(gg, ref["grad_" + q]) <= TOL_FP64, q
 
 
 def test_fp64_separable_at_the_largest_batched_shape(yy, oracle_grid):
@@ -194,19 +196,19 @@ def test_fp64_separable_at_the_largest_batched_shape(yy, oracle_grid):
     finally:
         g.set_analysis("auto")
     for key in sep:
-        assert rel_max(sep[key], dense[key]) <= TOL_FP64, key
+        assert field_err(key, sep[key], dense[key]) <= TOL_FP64, key
     rng = np.random.default_rng(40)
     cells = np.sort(rng.choice(spec.n_ang, 24, replace=False))
     ref = oracle_grid(spec).solve(ry, rg, gradient=True, cells=cells)
     j, k = np.divmod(cells, spec.n_phi)
     for q in ("yin", "yang"):
-        assert rel_max(sep["phi_" + q][:, j, k], ref["phi_" + q]) <= TOL_FP64, q
-        assert rel_max(sep["grad_" + q][:, :, j, k], ref["grad_" + q]) <= TOL_FP64, q
+        assert phi_err(sep["phi_" + q][:, j, k], ref["phi_" + q]) <= TOL_FP64, q
+        assert grad_err(sep["grad_" + q][:, :, j, k], ref["grad_" + q]) <= TOL_FP64, q
 
 
 def test_long_radial_grid_uses_the_chunked_scan(yy, oracle_grid):
     """n_r = 1000 (> 768): the radial sums run as the two-kernel chunked scan
-    (per-chunk affine maps, then the composed starts).  Float64 at 1e-12 and
+    (per-chunk affine maps, then the composed starts).  Float64 at 1e-13 and
     FP16X2 at its tolerance against the oracle."""
     spec = inputs.GridSpec("long_r", np.logspace(-4, 0, 1001), 16, 48, 0.2, 0.1, 10)
     g = _grid(yy, spec)
@@ -216,17 +218,17 @@ def test_long_radial_grid_uses_the_chunked_scan(yy, oracle_grid):
     out = gpu_solve(g, ry, rg, gradient=True)
     half = gpu_solve(g, ry, rg, gradient=True, prec="fp16x2")
     for q in ("yin", "yang"):
-        assert rel_max(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64, q
-        assert rel_max(out["grad_" + q], ref["grad_" + q]) <= TOL_FP64, q
-        assert rel_max(half["phi_" + q], ref["phi_" + q]) <= 1e-6, q
-        assert rel_max(half["grad_" + q], ref["grad_" + q]) <= 1e-5, q
+        assert phi_err(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64, q
+        assert grad_err(out["grad_" + q], ref["grad_" + q]) <= TOL_FP64, q
+        assert phi_err(half["phi_" + q], ref["phi_" + q]) <= 1e-6, q
+        assert grad_err(half["grad_" + q], ref["grad_" + q]) <= 4e-6, q
 
 
 @pytest.mark.parametrize("lmax", [60, 80])
 def test_high_degree(yy, oracle_grid, lmax):
     """l_max = 60 and 80 (the cap) on a small grid: the normalised polar
     tables, the rotation between the patches and the scans at high degree,
-    float64 at 1e-12."""
+    float64 at 1e-13."""
     spec = inputs.GridSpec(f"lmax{lmax}", np.logspace(-2, 0, 9), 40, 120, 0.0, 0.0, lmax)
     g = _grid(yy, spec)
     ry, rg = inputs.pns_density(spec, 32, 0.08)
@@ -236,8 +238,8 @@ def test_high_degree(yy, oracle_grid, lmax):
     ref = oracle_grid(spec).solve(ry, rg, gradient=True, cells=cells)
     j, k = np.divmod(cells, spec.n_phi)
     for q in ("yin", "yang"):
-        assert rel_max(out["phi_" + q][:, j, k], ref["phi_" + q]) <= TOL_FP64, q
-        assert rel_max(out["grad_" + q][:, :, j, k], ref["grad_" + q]) <= TOL_FP64, q
+        assert phi_err(out["phi_" + q][:, j, k], ref["phi_" + q]) <= TOL_FP64, q
+        assert grad_err(out["grad_" + q][:, :, j, k], ref["grad_" + q]) <= TOL_FP64, q
 
 
 def test_ragged_small_grid(yy):
@@ -253,8 +255,8 @@ def test_ragged_small_grid(yy):
     out = gpu_solve(g, ry, rg, gradient=True)
     ref = OracleGrid(spec.r_edges, 13, 37, 0.06, 0.02, 11, 0.5).solve(ry, rg, gradient=True)
     for q in ("yin", "yang"):
-        assert rel_max(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64
-        assert rel_max(out["grad_" + q], ref["grad_" + q]) <= TOL_FP64
+        assert phi_err(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64
+        assert grad_err(out["grad_" + q], ref["grad_" + q]) <= TOL_FP64
     g.close()
 
 
@@ -268,8 +270,8 @@ def test_degenerate_lmax0_single_zone(yy):
     out = gpu_solve(g, ry, rg, gradient=True)
     ref = OracleGrid(r, 1, 1, 0.0, 0.0, 0, 1.0).solve(ry, rg, gradient=True)
     for q in ("yin", "yang"):
-        assert rel_max(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64
-        assert rel_max(out["grad_" + q][0], ref["grad_" + q][0]) <= TOL_FP64
+        assert phi_err(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64
+        assert grad_err(out["grad_" + q][0], ref["grad_" + q][0]) <= TOL_FP64
     g.close()
 
 
@@ -389,8 +391,9 @@ def test_allocation_failure_is_reported_cleanly(yy):
 def test_fp32_path_tolerance(yy, oracle_grid, analysis):
     """float32 on CUDA cores (float64 tables cast once, float64 scans).
     Default (separable stages, sums of short chains with the monopole added
-    last): Phi <= 1e-6, -grad Phi <= 1e-5.  Dense contractions: long fp32
-    chains, Phi <= 1e-5, -grad Phi <= 1e-4."""
+    last): Phi <= 1e-6 pointwise, -grad Phi <= 1e-6 normwise (worst measured
+    2.1e-7 and 1.9e-7).  Dense contractions, long fp32 chains: 1e-5 and 1e-5
+    (worst measured 2.4e-6 and 1.9e-6)."""
     spec = inputs.mid_grid()
     g = _grid(yy, spec)
     g.prepare("fp32")
@@ -401,7 +404,7 @@ def test_fp32_path_tolerance(yy, oracle_grid, analysis):
     finally:
         g.set_analysis("auto")
     ref = oracle_grid(spec).solve(ry, rg, gradient=True)
-    tol_phi, tol_g = (1e-6, 1e-5) if analysis == "auto" else (1e-5, 1e-4)
+    tol_phi, tol_g = (1e-6, 1e-6) if analysis == "auto" else (1e-5, 1e-5)
     for q in ("yin", "yang"):
-        assert rel_max(out["phi_" + q], ref["phi_" + q]) <= tol_phi
-        assert rel_max(out["grad_" + q], ref["grad_" + q]) <= tol_g
+        assert phi_err(out["phi_" + q], ref["phi_" + q]) <= tol_phi
+        assert grad_err(out["grad_" + q], ref["grad_" + q]) <= tol_g

@@ -1,8 +1,9 @@
 """The full spherical polar grid of §2 (yy_polar_grid_create) against the
-float64 oracle's polar grid: float64 at 1e-12 with both analysis
-evaluations, the tensor-core forms at their stated tolerances (Phi 1e-6 and
--grad Phi 1e-5 for FP16X2 / BF16X3, 5e-4 / 5e-3 for TF32), a 1-degree grid on
-sampled cells, and the one-patch argument rules.
+float64 oracle's polar grid: float64 at 1e-13 (the 1e-12 bar with room
+for regressions to show) with both analysis evaluations, the tensor-core
+forms at their stated tolerances (Phi pointwise 1e-6 and -grad Phi normwise
+4e-6 for FP16X2 / BF16X3, 5e-4 / 7e-4 for TF32), a 1-degree grid on sampled
+cells, and the one-patch argument rules.
 """
 
 import numpy as np
@@ -10,12 +11,12 @@ import pytest
 
 from paper_1806_04593_gb300 import inputs
 
-from .gpu_common import lib, rel_max, require_gpu
+from .gpu_common import grad_err, lib, phi_err, require_gpu
 
 pytestmark = pytest.mark.gpu
 
-TOL_FP64 = 1e-12
-TOL = {"fp16x2": (1e-6, 1e-5), "bf16x3": (1e-6, 1e-5), "tf32": (5e-4, 5e-3)}
+TOL_FP64 = 1e-13
+TOL = {"fp16x2": (1e-6, 4e-6), "bf16x3": (1e-6, 4e-6), "tf32": (5e-4, 7e-4)}
 
 
 @pytest.fixture(scope="module")
@@ -55,8 +56,8 @@ def test_polar_fp64_matches_oracle(yy, oracle_grid, name, analysis):
         g.set_analysis("auto")
     assert yy.yy_last_device_status(g.handle) == yy.YY_OK
     ref = oracle_grid(spec).solve(rho, gradient=True)
-    assert rel_max(out["phi"], ref["phi"]) <= TOL_FP64
-    assert rel_max(out["grad"], ref["grad"]) <= TOL_FP64
+    assert phi_err(out["phi"], ref["phi"]) <= TOL_FP64
+    assert grad_err(out["grad"], ref["grad"]) <= TOL_FP64
 
 
 @pytest.mark.parametrize("prec", ["fp16x2", "bf16x3", "tf32"])
@@ -69,8 +70,8 @@ def test_polar_tensor_forms_match_oracle(yy, oracle_grid, prec):
     assert yy.yy_last_device_status(g.handle) == yy.YY_OK
     ref = oracle_grid(spec).solve(rho, gradient=True)
     tol_phi, tol_g = TOL[prec]
-    assert rel_max(out["phi"], ref["phi"]) <= tol_phi
-    assert rel_max(out["grad"], ref["grad"]) <= tol_g
+    assert phi_err(out["phi"], ref["phi"]) <= tol_phi
+    assert grad_err(out["grad"], ref["grad"]) <= tol_g
 
 
 def test_polar_one_degree_sampled_cells(yy, oracle_grid):
@@ -86,10 +87,10 @@ def test_polar_one_degree_sampled_cells(yy, oracle_grid):
     cells = np.sort(rng.choice(spec.n_ang, 32, replace=False))
     ref = oracle_grid(spec).solve(rho, gradient=True, cells=cells)
     j, k = np.divmod(cells, spec.n_phi)
-    assert rel_max(out64["phi"][:, j, k], ref["phi"]) <= TOL_FP64
-    assert rel_max(out64["grad"][:, :, j, k], ref["grad"]) <= TOL_FP64
-    assert rel_max(out16["phi"][:, j, k], ref["phi"]) <= 1e-6
-    assert rel_max(out16["grad"][:, :, j, k], ref["grad"]) <= 1e-5
+    assert phi_err(out64["phi"][:, j, k], ref["phi"]) <= TOL_FP64
+    assert grad_err(out64["grad"][:, :, j, k], ref["grad"]) <= TOL_FP64
+    assert phi_err(out16["phi"][:, j, k], ref["phi"]) <= TOL["fp16x2"][0]
+    assert grad_err(out16["grad"][:, :, j, k], ref["grad"]) <= TOL["fp16x2"][1]
 
 
 def test_polar_argument_rules_and_host_entry(yy):

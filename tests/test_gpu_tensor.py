@@ -1,8 +1,11 @@
 """Tensor-core forms (tcgen05) against the float64 oracle.
 
-Stated tolerances (max-norm relative error over the whole field):
-  FP16X2, BF16X3  Phi <= 1e-6;  -grad Phi <= 1e-5
-  TF32            Phi <= 5e-4;  -grad Phi <= 5e-3
+Stated tolerances (Phi: the largest pointwise relative error |dPhi|/|Phi|;
+-grad Phi: normwise, max |dg| / max |g|), over the whole field:
+  FP16X2, BF16X3  Phi <= 1e-6 (the target; worst measured 5.3e-7, tiny grid)
+                  -grad Phi <= 4e-6 (4x the worst measured, 8.8e-7)
+  TF32            Phi <= 5e-4, -grad Phi <= 7e-4 (about 5x and 4.5x the worst
+                  measured, 1.0e-4 and 1.5e-4; TF32 misses the 1e-6 target)
 The split forms keep about 22 (fp16 x 2) or 24 (bf16 x 3) significant bits
 per operand; the bound comes from the fp32 accumulation in tensor memory
 (about 2^-24 per accumulation step, a few hundred steps per output) with the
@@ -15,11 +18,11 @@ import pytest
 
 from paper_1806_04593_gb300 import inputs
 
-from .gpu_common import gpu_solve, lib, rel_max, require_gpu
+from .gpu_common import gpu_solve, grad_err, lib, phi_err, require_gpu
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp16x2": (1e-6, 1e-5), "bf16x3": (1e-6, 1e-5), "tf32": (5e-4, 5e-3)}
+TOL = {"fp16x2": (1e-6, 4e-6), "bf16x3": (1e-6, 4e-6), "tf32": (5e-4, 7e-4)}
 
 
 @pytest.fixture(scope="module")
@@ -56,8 +59,8 @@ def test_tensor_form_matches_oracle(yy, oracle_grid, prec, name, analysis):
     ref = oracle_grid(spec).solve(ry, rg, gradient=True)
     tol_phi, tol_g = TOL[prec]
     for q in ("yin", "yang"):
-        assert rel_max(out["phi_" + q], ref["phi_" + q]) <= tol_phi, (q, prec)
-        assert rel_max(out["grad_" + q], ref["grad_" + q]) <= tol_g, (q, prec)
+        assert phi_err(out["phi_" + q], ref["phi_" + q]) <= tol_phi, (q, prec)
+        assert grad_err(out["grad_" + q], ref["grad_" + q]) <= tol_g, (q, prec)
 
 
 @pytest.mark.parametrize("analysis", ["auto", "separable", "dense"])
@@ -79,8 +82,8 @@ def test_tensor_form_production_sampled(yy, oracle_grid, prec, analysis):
     j, k = np.divmod(cells, spec.n_phi)
     tol_phi, tol_g = TOL[prec]
     for q in ("yin", "yang"):
-        assert rel_max(out["phi_" + q][:, j, k], ref["phi_" + q]) <= tol_phi
-        assert rel_max(out["grad_" + q][:, :, j, k], ref["grad_" + q]) <= tol_g
+        assert phi_err(out["phi_" + q][:, j, k], ref["phi_" + q]) <= tol_phi
+        assert grad_err(out["grad_" + q][:, :, j, k], ref["grad_" + q]) <= tol_g
 
 
 def test_tensor_form_ragged_sizes(yy):
@@ -97,8 +100,8 @@ def test_tensor_form_ragged_sizes(yy):
         out = gpu_solve(g, ry, rg, gradient=True, prec=prec)
         tol_phi, tol_g = TOL[prec]
         for q in ("yin", "yang"):
-            assert rel_max(out["phi_" + q], ref["phi_" + q]) <= tol_phi, prec
-            assert rel_max(out["grad_" + q], ref["grad_" + q]) <= tol_g, prec
+            assert phi_err(out["phi_" + q], ref["phi_" + q]) <= tol_phi, prec
+            assert grad_err(out["grad_" + q], ref["grad_" + q]) <= tol_g, prec
     assert yy.yy_last_device_status(g.handle) == yy.YY_OK
     g.close()
 
@@ -185,8 +188,8 @@ def test_long_rows_streaming_packing(yy):
             out = gpu_solve(g, ry, rg, gradient=True, prec=prec)
             tol_phi, tol_g = TOL[prec]
             for q in ("yin", "yang"):
-                assert rel_max(out["phi_" + q], ref["phi_" + q]) <= tol_phi, prec
-                assert rel_max(out["grad_" + q], ref["grad_" + q]) <= tol_g, prec
+                assert phi_err(out["phi_" + q], ref["phi_" + q]) <= tol_phi, prec
+                assert grad_err(out["grad_" + q], ref["grad_" + q]) <= tol_g, prec
         assert yy.yy_last_device_status(g.handle) == yy.YY_OK
         buf = torch.zeros(ry.size + 1, dtype=torch.float64, device="cuda")
         off = buf[1:].view(ry.shape)
