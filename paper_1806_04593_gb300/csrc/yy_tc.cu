@@ -13,6 +13,7 @@
 #include "yy_internal.h"
 #include "yy_tc_pair.cuh"
 #include "yy_oz_synth.cuh"
+#include "yy_oz_analysis.cuh"
 
 namespace yy {
 
@@ -1940,6 +1941,8 @@ struct yy_oz_tables {
   int *an_exp;                  // [rows_pad]
   void *an_az;                  // [6][an_b_rows_pad][an_kpad]
   yy::PairMaps an_maps;
+  int an_slots2;                // resident clusters of k_oz_analysis (0: the pair kernel serves)
+  yy::OzAnalysisMaps an_maps2;  // its maps: density digits (box 128 rows), table digits (box 32 rows)
 };
 
 namespace yy {
@@ -1984,7 +1987,7 @@ static yy_status ozaki_prepare_analysis(yy_grid *g, yy_oz_tables *o) {
   o->an_kpad = round_up(g->n_phi, kPadK);
   o->an_bn = 32;   // seven level accumulators of bn columns within one 256-column TMEM buffer
   o->an_row_tiles = (nt + o->an_bn - 1) / o->an_bn;
-  o->an_b_rows_pad = o->an_row_tiles * o->an_bn;
+  o->an_b_rows_pad = round_up(nt, kOzAnBN);   // tiles of an_bn (pair kernel) and kOzAnBN (k_oz_analysis)
   o->an_stages = pair_stages<F>(o->an_bn, kEpiStageBytes);
   if (o->an_stages < 2 ||
       cudaFuncSetAttribute(k_tc_pair<F, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) != cudaSuccess)
@@ -2037,6 +2040,19 @@ static yy_status ozaki_prepare_analysis(yy_grid *g, yy_oz_tables *o) {
       !make_map<F>(&o->an_maps.b[0], o->an_az, o->an_kpad, F::kPB * o->an_b_rows_pad, o->an_bn / 2))
     return YY_ERR_NOT_SUPPORTED;
   o->an_ok = 1;
+  // the analysis kernel with the table resident, where K fits its shared memory
+  o->an_slots2 = 0;
+  const int kb = o->an_kpad * F::kElem / kRowBytes;
+  if (kb <= kOzAnMaxKB && make_map<F>(&o->an_maps2.a, o->an_x, o->an_kpad, F::kPA * o->rows_pad, kPairRows) &&
+      make_map<F>(&o->an_maps2.b, o->an_az, o->an_kpad, F::kPB * o->an_b_rows_pad, kOzAnBN / 2) &&
+      cudaFuncSetAttribute(k_oz_analysis, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           oz_analysis_smem(kOzAnMaxKB)) == cudaSuccess) {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = pair_config(64, oz_analysis_smem(kb), 0, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (void *)k_oz_analysis, &cfg) == cudaSuccess && n > 0) o->an_slots2 = n;
+  }
+  cudaGetLastError();
   return YY_OK;
 }
 
@@ -2065,6 +2081,27 @@ cudaError_t ozaki_analysis(yy_grid *g, const double *ry, const double *rg, cudaS
   note_launch(g, "k_rhow_ozaki", s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (o->an_slots2 > 0) {
+    OzAnalysisArgs z = {};
+    z.cells = o->rows;
+    z.cell_tiles = o->rows_pad / (2 * kPairRows);
+    z.cols = 2 * g->lmax + 1;
+    z.kb_total = o->an_kpad * F::kElem / kRowBytes;
+    z.kb_fill = F::kFillK * F::kElem / kRowBytes;   // exact level sums per fill; the epilogue adds the fills
+    z.a_rows = o->rows_pad;
+    z.b_rows = o->an_b_rows_pad;
+    z.ldo = g->sep_nt_pad;
+    z.out = g->sep_F;
+    z.cell_exp = o->an_exp;
+    z.err = g->err;
+    const int pairs = z.cell_tiles < o->an_slots2 ? z.cell_tiles : o->an_slots2;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = pair_config(pairs, oz_analysis_smem(z.kb_total), s, attr);
+    e = cudaLaunchKernelEx(&cfg, k_oz_analysis, o->an_maps2, z);
+    note_launch(g, "k_oz_analysis", s);
+    if (e != cudaSuccess) return e;
+    return separable_theta_f64(g, s);
+  }
   PairArgs a = {};
   a.stages = o->an_stages;
   a.cells = o->rows;
