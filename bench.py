@@ -332,7 +332,7 @@ def kernel_work(name, spec, n_lm, gradient, prec):
         k_pad = -(-nt // 32) * 32
         w = {"flop": 2.0 * rows * spec.n_phi * nt * J, "flop_kind": "tensor", "products": "ozaki",
              "bytes": out_bytes + J * rows * k_pad * 6 * 2}
-    elif name.startswith("k_tc_pair<FormOzaki,3>/analysis"):
+    elif name.startswith("k_tc_pair<FormOzaki,3>/analysis") or name == "k_oz_analysis":
         k_pad = -(-spec.n_phi // 64) * 64
         w = {"flop": 2.0 * rows * spec.n_phi * nt, "flop_kind": "tensor", "products": "ozaki",
              "bytes": rows * k_pad * 6 * 2}
