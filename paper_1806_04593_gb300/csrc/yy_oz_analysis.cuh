@@ -9,19 +9,20 @@
 // level sums stay exact in fp32 (below 2^24), and the epilogue adds the fills
 // in integers (ozaki_accumulate) before the one rounding to float64.
 //
-// Schedule: the azimuthal table is small (64 slots x K digits, half of them
-// per CTA: 120 KiB at K = 320, the longest K taken; longer rows use the pair
-// kernel), so each CTA loads its half once and keeps it in shared memory;
-// only the density digits stream through a
-// two-stage ring, one 32-wide K block of 128 rows and six slices (48 KiB)
-// per stage.  All slots of a row tile go into one MMA (N = 64), so an MMA's
+// Schedule: each stage of a three-stage ring holds one 32-wide K block of
+// both operands, six digit slices each: 128 density rows (48 KiB) and this
+// CTA's 32 slot rows of the table (12 KiB).  (Keeping the table resident,
+// 120 KiB at K = 320, left room for two density stages only, and the loads
+// of one stage did not hide behind the MMAs of the other.)  The table is
+// re-read from L2 for every row tile, 245 KiB per tile pair.  All slots of a
+// row tile go into one MMA (N = 64), so an MMA's
 // fixed cost -- reading its 4 KiB A tile from shared memory -- buys twice
 // the work of the 32-column tiles of the pair kernel, and the density digits
 // are read once instead of once per 32 slots.  The seven level accumulators
 // of 64 columns (448 TMEM columns) have one buffer: each fill's MMAs wait
 // until the epilogue has read the previous fill, which takes a small part
 // of a fill's MMA time.
-//   warp 0  lane 0: TMA producer (the table once, then the density ring)
+//   warp 0  lane 0: TMA producer
 //   warp 1  TMEM allocation; in the even CTA lane 0 issues MMAs and commits
 //   warps 2-17: epilogue, 16 slots x 32 rows each, results stored straight
 //               from registers (128 contiguous bytes per row)
@@ -32,18 +33,16 @@
 namespace yy {
 
 constexpr int kOzAnBN = 64;                   // slots per MMA (N)
-constexpr int kOzAnMaxKB = 10;                // K blocks of the resident table (K <= 320)
-constexpr int kOzAnStages = 2;
+constexpr int kOzAnStages = 3;
 constexpr int kOzAnSlotA = kPairRows * kRowBytes;                    // 8 KiB
 constexpr int kOzAnSlotB = (kOzAnBN / 2) * kRowBytes;                // 2 KiB
 constexpr int kOzAnStageA = FormOzaki::kPA * kOzAnSlotA;             // 48 KiB
 constexpr int kOzAnKBlockB = FormOzaki::kPB * kOzAnSlotB;            // 12 KiB per K block
 static_assert(FormOzaki::kAccs * kOzAnBN <= kPairTmemCols, "k_oz_analysis accumulators");
 
-// shared memory of a launch with kb K blocks
-__host__ __device__ constexpr int oz_analysis_smem(int kb) {
-  return 1024 + kOzAnStages * kOzAnStageA + kb * kOzAnKBlockB + 512;
-}
+constexpr int kOzAnStage = kOzAnStageA + kOzAnKBlockB;               // 60 KiB
+constexpr int kOzAnSmem = 1024 + kOzAnStages * kOzAnStage + 512;
+static_assert(kOzAnSmem <= kSmemLimit, "k_oz_analysis shared memory");
 
 struct OzAnalysisArgs {
   int cells, cell_tiles;        // valid density rows; tiles of 256 rows (pairs of 128)
@@ -69,11 +68,9 @@ k_oz_analysis(const __grid_constant__ OzAnalysisMaps maps, const __grid_constant
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t *ringA = smem;                                     // [stage][slice][128 rows][64 B]
-  uint8_t *tabB = smem + S * kOzAnStageA;                    // [kb][slice][32 rows][64 B]
-  uint64_t *bars = (uint64_t *)(tabB + a.kb_total * kOzAnKBlockB);
-  uint64_t *b_full = bars;
-  uint64_t *full = bars + 1, *empty = full + S;
+  uint8_t *ring = smem;                                      // [stage]{[slice][128 rows][64 B], [slice][32 rows][64 B]}
+  uint64_t *bars = (uint64_t *)(ring + S * kOzAnStage);
+  uint64_t *full = bars, *empty = full + S;
   uint64_t *tfull = empty + S, *tempty = tfull + 1;          // one accumulator set; tempty counted in the even CTA
   uint32_t *tmem_slot = (uint32_t *)(tempty + 1);
 
@@ -84,7 +81,6 @@ k_oz_analysis(const __grid_constant__ OzAnalysisMaps maps, const __grid_constant
   const int fills = (a.kb_total + a.kb_fill - 1) / a.kb_fill;
 
   if (threadIdx.x == 0) {
-    mbar_init(b_full, 1);
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
@@ -104,15 +100,7 @@ k_oz_analysis(const __grid_constant__ OzAnalysisMaps maps, const __grid_constant
 
   if (warp == 0) {
     if (lane == 0) {
-      // the table, once: this CTA's 32 slot rows of every K block and slice
-      if (rank == 0) mbar_expect_tx(b_full, 2u * (uint32_t)(a.kb_total * kOzAnKBlockB));
-      const uint32_t bbar = mapa_rank(smem_u32(b_full), 0);
-      for (int kb = 0; kb < a.kb_total; ++kb)
-#pragma unroll
-        for (int p = 0; p < F::kPB; ++p)
-          tma_load_2d_pair(&maps.b, smem_u32(tabB + (kb * F::kPB + p) * kOzAnSlotB), bbar, kb * 32,
-                           p * a.b_rows + rank * BH);
-      const uint32_t a_tx = 2u * (uint32_t)kOzAnStageA;
+      const uint32_t tx = 2u * (uint32_t)kOzAnStage;
       int gk = 0, s = 0;
       uint32_t ph = 0;
       bool ok = true;
@@ -123,12 +111,16 @@ k_oz_analysis(const __grid_constant__ OzAnalysisMaps maps, const __grid_constant
             ok = false;
             break;
           }
-          if (rank == 0) mbar_expect_tx(&full[s], a_tx);
+          if (rank == 0) mbar_expect_tx(&full[s], tx);
           const uint32_t fbar = mapa_rank(smem_u32(&full[s]), 0);
+          uint8_t *st = ring + s * kOzAnStage;
 #pragma unroll
           for (int p = 0; p < F::kPA; ++p)
-            tma_load_2d_pair(&maps.a, smem_u32(ringA + s * kOzAnStageA + p * kOzAnSlotA), fbar, kb * 32,
-                             p * a.a_rows + arow);
+            tma_load_2d_pair(&maps.a, smem_u32(st + p * kOzAnSlotA), fbar, kb * 32, p * a.a_rows + arow);
+#pragma unroll
+          for (int p = 0; p < F::kPB; ++p)
+            tma_load_2d_pair(&maps.b, smem_u32(st + kOzAnStageA + p * kOzAnSlotB), fbar, kb * 32,
+                             p * a.b_rows + rank * BH);
           if (++s == S) {
             s = 0;
             ph ^= 1;
@@ -144,8 +136,7 @@ k_oz_analysis(const __grid_constant__ OzAnalysisMaps maps, const __grid_constant
       const uint32_t idesc = instr_desc_pair<F>(kOzAnBN);
       int gk = 0, it = 0, s = 0;
       uint32_t ph = 0;
-      bool ok = mbar_wait_cluster(b_full, 0, a.err);
-      if (ok) tc_fence_after();
+      bool ok = true;
       for (int t = pair; t < total && ok; t += n_pairs) {
         for (int c0 = 0; c0 < a.kb_total && ok; c0 += a.kb_fill, ++it) {
           // the epilogue has read the previous fill out of the accumulators
@@ -163,8 +154,8 @@ k_oz_analysis(const __grid_constant__ OzAnalysisMaps maps, const __grid_constant
               break;
             }
             tc_fence_after();
-            const uint32_t sa = smem_u32(ringA + s * kOzAnStageA);
-            const uint32_t sb = smem_u32(tabB + kb * kOzAnKBlockB);
+            const uint32_t sa = smem_u32(ring + s * kOzAnStage);
+            const uint32_t sb = sa + kOzAnStageA;
 #pragma unroll
             for (int q = 0; q < F::kPairs; ++q) {
               const uint32_t dq = tmem_base + (uint32_t)(F::acc(q) * kOzAnBN);

@@ -1858,9 +1858,39 @@ struct OzRhoArgs {
   int *rexp;                    // [rows_pad]
 };
 
-// C: 64-wide pieces of a row held per lane (k_pad <= 64 C)
+// Balanced base-256 digits of X < 2^48 as oz_digits computes them, in 32-bit
+// operations: the three low digits from the low 24 bits, their carry (0 or 1)
+// into the high 24 bits, then the two next digits and the rest.  A digit
+// v in [0, 255] becomes v - 256 with a carry of one when v > 128, which
+// (v + 127) >> 8 tells without a branch.
+__device__ __forceinline__ void oz_digits32(unsigned long long X, int (&d)[6]) {
+  unsigned lo = (unsigned)X & 0xFFFFFFu;
+  unsigned hi = (unsigned)(X >> 24);
+#pragma unroll
+  for (int s = 5; s >= 3; --s) {
+    const unsigned v = lo & 255u;
+    const unsigned c = (v + 127u) >> 8;
+    d[s] = (int)v - (int)(c << 8);
+    lo = (lo >> 8) + c;
+  }
+  hi += lo;
+#pragma unroll
+  for (int s = 2; s >= 1; --s) {
+    const unsigned v = hi & 255u;
+    const unsigned c = (v + 127u) >> 8;
+    d[s] = (int)v - (int)(c << 8);
+    hi = (hi >> 8) + c;
+  }
+  d[0] = (int)hi;
+}
+
+// C: 64-wide pieces of a row held per lane (k_pad <= 64 C).  The bf16 bit
+// patterns of the digits -128 .. 128 come from a table in shared memory.
 template <int C>
 __global__ void __launch_bounds__(256) k_rhow_ozaki(OzRhoArgs a) {
+  __shared__ uint16_t bf16_of[257];   // bf16 bits of the integer i - 128
+  for (int i = threadIdx.x; i < 257; i += blockDim.x) bf16_of[i] = (uint16_t)(__float_as_uint((float)(i - 128)) >> 16);
+  __syncthreads();
   const int row = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (row >= a.rows) return;
   const int shell = row / a.n_theta, j = row % a.n_theta;
@@ -1911,15 +1941,13 @@ __global__ void __launch_bounds__(256) k_rhow_ozaki(OzRhoArgs a) {
       unsigned long long X = 0ull;
       if (exm != 0 && ex != 0 && sh < 64)
         X = ((((bits[c][h] & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> (sh - 1)) + 1ull) >> 1;
-      oz_digits(X, d[h]);
+      oz_digits32(X, d[h]);
     }
-    __nv_bfloat16 *dst = a.X + (size_t)row * a.k_pad + k0;
+    const int s0 = (bits[c][0] >> 63) ? -1 : 1, s1 = (bits[c][1] >> 63) ? -1 : 1;
+    uint32_t *dst = reinterpret_cast<uint32_t *>(a.X + (size_t)row * a.k_pad + k0);
 #pragma unroll
-    for (int sl = 0; sl < 6; ++sl) {
-      const float v0 = (bits[c][0] >> 63) ? -(float)d[0][sl] : (float)d[0][sl];
-      const float v1 = (bits[c][1] >> 63) ? -(float)d[1][sl] : (float)d[1][sl];
-      *reinterpret_cast<__nv_bfloat162 *>(dst + sl * stride) = __floats2bfloat162_rn(v0, v1);
-    }
+    for (int sl = 0; sl < 6; ++sl)
+      dst[sl * (stride / 2)] = (uint32_t)bf16_of[s0 * d[0][sl] + 128] | ((uint32_t)bf16_of[s1 * d[1][sl] + 128] << 16);
   }
   if (lane == 0) a.rexp[row] = exm == 0 ? 0 : e + a.eb - 64;
 }
@@ -2040,15 +2068,13 @@ static yy_status ozaki_prepare_analysis(yy_grid *g, yy_oz_tables *o) {
       !make_map<F>(&o->an_maps.b[0], o->an_az, o->an_kpad, F::kPB * o->an_b_rows_pad, o->an_bn / 2))
     return YY_ERR_NOT_SUPPORTED;
   o->an_ok = 1;
-  // the analysis kernel with the table resident, where K fits its shared memory
+  // the analysis kernel with all slots in one MMA
   o->an_slots2 = 0;
-  const int kb = o->an_kpad * F::kElem / kRowBytes;
-  if (kb <= kOzAnMaxKB && make_map<F>(&o->an_maps2.a, o->an_x, o->an_kpad, F::kPA * o->rows_pad, kPairRows) &&
+  if (make_map<F>(&o->an_maps2.a, o->an_x, o->an_kpad, F::kPA * o->rows_pad, kPairRows) &&
       make_map<F>(&o->an_maps2.b, o->an_az, o->an_kpad, F::kPB * o->an_b_rows_pad, kOzAnBN / 2) &&
-      cudaFuncSetAttribute(k_oz_analysis, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           oz_analysis_smem(kOzAnMaxKB)) == cudaSuccess) {
+      cudaFuncSetAttribute(k_oz_analysis, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzAnSmem) == cudaSuccess) {
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = pair_config(64, oz_analysis_smem(kb), 0, attr);
+    cudaLaunchConfig_t cfg = pair_config(64, kOzAnSmem, 0, attr);
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, (void *)k_oz_analysis, &cfg) == cudaSuccess && n > 0) o->an_slots2 = n;
   }
@@ -2096,7 +2122,7 @@ cudaError_t ozaki_analysis(yy_grid *g, const double *ry, const double *rg, cudaS
     z.err = g->err;
     const int pairs = z.cell_tiles < o->an_slots2 ? z.cell_tiles : o->an_slots2;
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = pair_config(pairs, oz_analysis_smem(z.kb_total), s, attr);
+    cudaLaunchConfig_t cfg = pair_config(pairs, kOzAnSmem, s, attr);
     e = cudaLaunchKernelEx(&cfg, k_oz_analysis, o->an_maps2, z);
     note_launch(g, "k_oz_analysis", s);
     if (e != cudaSuccess) return e;
