@@ -197,6 +197,28 @@ yy_status yy_polar_grid_create(const double *r_edges, int n_r, int n_theta, int 
  * tables (the method stays selected; those forms then use the dense path). */
 yy_status yy_grid_set_analysis(yy_grid *g, yy_analysis method);
 
+/* K split of the dense analysis (YY_ANALYSIS_DENSE, or AUTO where it picks
+ * the dense evaluation) for one form: the number of tiles along the K axis
+ * (n_ang cells) that run side by side.  K is cut into segments fixed by the
+ * grid's sizes; each segment's products are summed in one fixed order into a
+ * partial of its own, a split takes whole segments, and the partials are
+ * added in segment order.  So the moments A -- and everything computed from
+ * them -- are bitwise the same for every split; the split changes only the
+ * speed.  (Sec. 3, the paragraph on the global summation of A_C and A_S:
+ * there the order of the sums changed with the number of tasks, and
+ * double-double sums made A reproducible; here the order is fixed instead.)
+ *   yy_grid_analysis_splits returns the current split (-1 for a NULL handle
+ *   or an unknown form; 0 for a tensor-core form not prepared yet) and, when
+ *   not NULL, writes the sizes' default to *rule and the largest accepted
+ *   split (the number of segments) to *max_splits.  YY_FP64, YY_FP32 and
+ *   YY_FP64_OZAKI (whose dense analysis is that of YY_FP64) share the
+ *   CUDA-core contraction's split.
+ *   yy_grid_set_analysis_splits sets it (0: the default) for later solves.
+ *   Errors: YY_ERR_INVALID_ARG (NULL, unknown form, splits < 0 or above
+ *   *max_splits); YY_ERR_NOT_SUPPORTED (tensor-core form not prepared). */
+int yy_grid_analysis_splits(const yy_grid *g, yy_precision prec, int *rule, int *max_splits);
+yy_status yy_grid_set_analysis_splits(yy_grid *g, yy_precision prec, int splits);
+
 /* Build the operand tables of a reduced-precision form or of YY_FP64_OZAKI
  * (allocates device memory; synchronises).  YY_FP64 is always ready.
  * Returns YY_ERR_NOT_SUPPORTED if the device cannot run the form, or for
@@ -348,7 +370,8 @@ yy_status yy_batch_prepare(yy_batch *b, yy_precision prec);
  * YY_ANALYSIS_SEPARABLE; reps solves each on zero densities in scratch
  * buffers it allocates and frees) in the given form, with or without the
  * gradient, together with the K split of the dense tensor-core analysis
- * (the rule's count times 1/2, 1, 2 and 4, within the partial buffer), and
+ * (half the default and the default, which is also the largest; the
+ * results do not depend on it, see yy_grid_set_analysis_splits), and
  * record the fastest for that form: later graphs of that form use it (other
  * forms keep theirs; untuned forms use YY_ANALYSIS_AUTO and the rule).  The
  * first yy_batch_potential after tuning also times its graph with 1, 2, 4, 8

@@ -20,7 +20,7 @@ cudaError_t dmalloc(void **p, size_t bytes) {
   return cudaMalloc(p, bytes == 0 ? 16 : bytes);
 }
 
-int choose_split_k(int M, int N, int K);
+void simt_segments(int M, int N, int K, int *seg, int *n_seg);
 
 // Gauss-Legendre nodes and weights on [0, 1] (weights sum to 1), by Newton
 // iteration on P_n with the three-term recurrence.
@@ -153,7 +153,8 @@ static yy_status create_grid(const double *r_edges, int n_r, int n_theta, int n_
   }
 
   const size_t n_ang = g->n_ang, n_lm = g->n_lm, M = (size_t)grid_rows(g);
-  g->split_k = choose_split_k((int)M, (int)n_lm, (int)n_ang);
+  simt_segments((int)M, (int)n_lm, (int)n_ang, &g->seg_k, &g->split_k);
+  g->simt_splits = g->split_k;
   cudaError_t e = cudaSuccess;
   auto A = [&](void **p, size_t bytes) {
     if (e == cudaSuccess) e = dmalloc(p, bytes);
@@ -235,6 +236,42 @@ yy_status yy_grid_set_analysis(yy_grid *g, yy_analysis method) {
       if (st != YY_OK) return st;
     }
   return YY_OK;
+}
+
+int yy_grid_analysis_splits(const yy_grid *g, yy_precision prec, int *rule, int *max_splits) {
+  if (!g) return -1;
+  switch (prec) {
+    case YY_FP64:
+    case YY_FP32:
+    case YY_FP64_OZAKI:
+      if (rule) *rule = g->split_k;
+      if (max_splits) *max_splits = g->split_k;
+      return g->simt_splits;
+    case YY_TF32:
+    case YY_BF16X3:
+    case YY_FP16X2: return tc_analysis_splits(g, prec, rule, max_splits);
+  }
+  return -1;
+}
+
+yy_status yy_grid_set_analysis_splits(yy_grid *g, yy_precision prec, int splits) {
+  if (!g || splits < 0) return YY_ERR_INVALID_ARG;
+  switch (prec) {
+    case YY_FP64:
+    case YY_FP32:
+    case YY_FP64_OZAKI:
+      if (splits > g->split_k) return YY_ERR_INVALID_ARG;
+      g->simt_splits = splits == 0 ? g->split_k : splits;
+      return YY_OK;
+    case YY_TF32:
+    case YY_BF16X3:
+    case YY_FP16X2: {
+      int rule = 0;
+      if (tc_analysis_splits(g, prec, &rule, nullptr) == 0) return YY_ERR_NOT_SUPPORTED;
+      return tc_set_analysis_splits(g, prec, splits == 0 ? rule : splits);
+    }
+  }
+  return YY_ERR_INVALID_ARG;
 }
 
 yy_status yy_grid_prepare(yy_grid *g, yy_precision prec) {

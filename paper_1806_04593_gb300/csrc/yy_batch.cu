@@ -238,7 +238,7 @@ yy_status yy_batch_tune(yy_batch *b, yy_precision prec, int with_gradient, int r
     int n_cand = 0;
     cands[n_cand++] = {YY_ANALYSIS_SEPARABLE, 0};
     if (tc) {
-      const int opts[4] = {rule / 2, rule, 2 * rule, 4 * rule};
+      const int opts[2] = {rule / 2, rule};   // rule: one K segment per tile, the finest split
       for (int o : opts) {
         bool dup = o < 1 || o > cap;
         for (int q = 0; q < n_cand && !dup; ++q) dup = cands[q].splits == o;

@@ -7,8 +7,10 @@
 // Both operands are K-major (row m of A and row n of B are contiguous in k),
 // rows of A may come from two arrays (Yin rows then Yang rows) and rows of C
 // may go to two arrays, so the caller's per-patch buffers are used in place.
-// The analysis splits K over blockIdx.z into float64 partials that a second
-// kernel sums in fixed order (deterministic, no atomics).
+// The analysis cuts K into fixed segments (set by the grid's sizes alone) and
+// writes one float64 partial per segment, which a second kernel sums in
+// segment order; blockIdx.z takes one or more whole segments, so the moments
+// are bitwise the same for every K split (deterministic, no atomics).
 #include <algorithm>
 
 #include "yy_internal.h"
@@ -20,7 +22,7 @@ constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4, NT = 256;
 
 template <typename T, typename Acc, bool PARTIAL>
 __global__ void __launch_bounds__(NT)
-k_gemm_tn(int M, int N, int K, int k_chunk,
+k_gemm_tn(int M, int N, int K, int k_chunk, int seg,
           const T *__restrict__ A0, const T *__restrict__ A1, int a_split, long long lda,
           const T *__restrict__ B, long long ldb,
           double *__restrict__ C0, double *__restrict__ C1, int c_split, long long ldc) {
@@ -82,19 +84,37 @@ k_gemm_tn(int M, int N, int K, int k_chunk,
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = fma((Acc)a[i], (Acc)b[j], acc[i][j]);
     }
+    if (PARTIAL) {
+      // the end of a K segment (seg is a multiple of BK): its partial goes out
+      const int k_next = kz0 + (t + 1) * BK;
+      if (k_next % seg == 0 || t + 1 == nk) {
+        const size_t zs = (size_t)((kz0 + t * BK) / seg);   // the segment this step belongs to
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+          const int m = bm + ty * TM + i;
+          if (m < M) {
+            double *crow = C0 + zs * M * ldc + (size_t)m * ldc;
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+              const int n = bn + tx * TN + j;
+              if (n < N) crow[n] = (double)acc[i][j];
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = Acc(0);
+        }
+      }
+    }
     if (t + 1 < nk) store(buf ^ 1);
     __syncthreads();
   }
+  if (PARTIAL) return;
 
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
     const int m = bm + ty * TM + i;
     if (m >= M) continue;
-    double *crow;
-    if (PARTIAL)
-      crow = C0 + (size_t)blockIdx.z * M * ldc + (size_t)m * ldc;
-    else
-      crow = (m < c_split) ? C0 + (size_t)m * ldc : C1 + (size_t)(m - c_split) * ldc;
+    double *crow = (m < c_split) ? C0 + (size_t)m * ldc : C1 + (size_t)(m - c_split) * ldc;
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int n = bn + tx * TN + j;
@@ -127,51 +147,59 @@ __global__ void k_rho_to_f32(size_t per_patch, const double *__restrict__ a, con
   }
 }
 
+// K in n_seg segments of seg elements (n_seg 1: one unsplit pass writing C0 / C1),
+// taken `splits` ways: each z block takes ceil(n_seg / splits) whole segments.
 template <typename T, typename Acc>
-cudaError_t launch_gemm(int M, int N, int K, int splits, const T *A0, const T *A1, int a_split,
-                        long long lda, const T *B, long long ldb, double *C0, double *C1, int c_split,
-                        long long ldc, cudaStream_t s) {
-  const int k_chunk = ((K + splits - 1) / splits + BK - 1) / BK * BK;
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
-  if (splits > 1)
-    k_gemm_tn<T, Acc, true><<<grid, NT, 0, s>>>(M, N, K, k_chunk, A0, A1, a_split, lda, B, ldb, C0, C1,
+cudaError_t launch_gemm(int M, int N, int K, int seg, int n_seg, int splits, const T *A0, const T *A1,
+                        int a_split, long long lda, const T *B, long long ldb, double *C0, double *C1,
+                        int c_split, long long ldc, cudaStream_t s) {
+  if (n_seg > 1) {
+    const int per = (n_seg + splits - 1) / splits;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, (n_seg + per - 1) / per);
+    k_gemm_tn<T, Acc, true><<<grid, NT, 0, s>>>(M, N, K, per * seg, seg, A0, A1, a_split, lda, B, ldb, C0, C1,
                                                 c_split, ldc);
-  else
-    k_gemm_tn<T, Acc, false><<<grid, NT, 0, s>>>(M, N, K, k_chunk, A0, A1, a_split, lda, B, ldb, C0, C1,
-                                                 c_split, ldc);
+  } else {
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, 1);
+    k_gemm_tn<T, Acc, false><<<grid, NT, 0, s>>>(M, N, K, K, K, A0, A1, a_split, lda, B, ldb, C0, C1, c_split,
+                                                 ldc);
+  }
   return cudaGetLastError();
 }
 
 }  // namespace
 
-int choose_split_k(int M, int N, int K) {
+// K segments of the float64 / float32 dense analysis, from the sizes alone:
+// about eight blocks per SM at the full split, segments of at least 512.
+void simt_segments(int M, int N, int K, int *seg, int *n_seg) {
   const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
   int s = (8 * 152 + tiles - 1) / tiles;
-  s = std::min(s, std::max(1, K / 512));
-  return std::max(1, std::min(s, 64));
+  s = std::max(1, std::min(std::min(s, std::max(1, K / 512)), 64));
+  const int len = ((K + s - 1) / s + BK - 1) / BK * BK;
+  *seg = len;
+  *n_seg = (K + len - 1) / len;
 }
 
 cudaError_t analysis_simt(yy_grid *g, const double *rho_yin, const double *rho_yang, bool fp32,
                           cudaStream_t s) {
   const int M = grid_rows(g), N = g->n_lm, K = g->n_ang;
-  const int splits = g->split_k;
-  double *out = (splits > 1) ? g->part : g->A;
+  const int n_seg = g->split_k, splits = g->simt_splits;
+  double *out = (n_seg > 1) ? g->part : g->A;
   cudaError_t err;
   if (fp32) {
     const size_t pp = (size_t)g->n_r * g->n_ang;
     k_rho_to_f32<<<(unsigned)((pp + 255) / 256), 256, 0, s>>>(pp, rho_yin, rho_yang, g->rho32);
     note_launch(g, "k_rho_to_f32", s);
-    err = launch_gemm<float, float>(M, N, K, splits, g->rho32, g->rho32 + pp, g->n_r, K, g->ban32, K,
+    err = launch_gemm<float, float>(M, N, K, g->seg_k, n_seg, splits, g->rho32, g->rho32 + pp, g->n_r, K, g->ban32, K,
                                     out, out, M, N, s);
   } else {
-    err = launch_gemm<double, double>(M, N, K, splits, rho_yin, rho_yang, g->n_r, K, g->ban, K, out,
+    err = launch_gemm<double, double>(M, N, K, g->seg_k, n_seg, splits, rho_yin, rho_yang, g->n_r, K, g->ban, K, out,
                                       out, M, N, s);
   }
   if (err != cudaSuccess) return err;
   note_launch(g, "k_gemm_tn/analysis", s);
-  if (splits > 1) {
+  if (n_seg > 1) {
     const size_t count = (size_t)M * N;
-    k_sum_partials<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(count, splits, g->part, g->A);
+    k_sum_partials<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(count, n_seg, g->part, g->A);
     note_launch(g, "k_sum_partials", s);
     err = cudaGetLastError();
   }
@@ -199,12 +227,12 @@ cudaError_t synthesis_simt(yy_grid *g, double *phi_yin, double *phi_yang, double
     if (fp32) {
       const float *tabs[3] = {g->ysyn32, g->ysyn_t32, g->ysyn_p32};
       const float *Aq = g->Q32 + jb.q * qsz;
-      err = launch_gemm<float, float>(M, N, K, 1, Aq, Aq, M, K, tabs[jb.table], K, jb.c0, jb.c1,
+      err = launch_gemm<float, float>(M, N, K, K, 1, 1, Aq, Aq, M, K, tabs[jb.table], K, jb.c0, jb.c1,
                                       g->n_r, N, s);
     } else {
       const double *tabs[3] = {g->ysyn, g->ysyn_t, g->ysyn_p};
       const double *Aq = g->Q + jb.q * qsz;
-      err = launch_gemm<double, double>(M, N, K, 1, Aq, Aq, M, K, tabs[jb.table], K, jb.c0, jb.c1,
+      err = launch_gemm<double, double>(M, N, K, K, 1, 1, Aq, Aq, M, K, tabs[jb.table], K, jb.c0, jb.c1,
                                         g->n_r, N, s);
     }
     if (err != cudaSuccess) return err;

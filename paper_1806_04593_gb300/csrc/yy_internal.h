@@ -44,8 +44,10 @@ struct yy_grid {
   // (row counts below are for the Yin-Yang grid; a polar grid has n_r rows)
   double *A;           // [2 n_r][n_lm]           moments of each patch's own cells
   double *Atot;        // [2 n_r][n_lm]           both patches' moments in each patch's frame
-  double *part;        // split-K partials [split][2 n_r][n_lm]
-  int split_k;
+  double *part;        // K-segment partials [segment][2 n_r][n_lm]
+  int split_k;         // K segments of the dense CUDA-core analysis (fixed by the sizes)
+  int seg_k;           // K per segment (a multiple of the contraction's K step)
+  int simt_splits;     // blocks along K, each taking whole segments (1 .. split_k)
   double *cin;         // [2 n_r][n_lm] inner scan values
   double *Q;           // [3][2 n_r][n_lm]    Phi, g_r and g_angle coefficients
   int *err;            // device error word

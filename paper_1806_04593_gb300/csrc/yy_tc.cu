@@ -872,9 +872,10 @@ struct yy_tc_tables {
   void *an_tab, *an_rho;
   double *an_tabs, *an_rhos, *an_mono, *an_mean, *an_colsum;
   float *an_b0;                           // fp32 copy of the monopole row of the analysis table
-  float *part;                            // split-K partial sums [split][2 n_r][n_lm]
-  int an_splits, an_kb_per;
-  int an_kb_total, an_splits_rule, an_splits_cap;   // K blocks; the rule's split count; partial-buffer capacity
+  float *part;                            // K-segment partial sums [segment][2 n_r][n_lm]
+  int an_splits, an_kb_per;               // K split: tiles along K, K blocks per tile (whole segments)
+  int an_kb_total, an_splits_rule;        // K blocks; the rule's split count
+  int an_segs, an_segs_per;               // K segments (one partial each); segments per split
   yy::PairMaps an_maps;                   // a[0]: table, b[0]: densities
   // synthesis: tables (cells) as operand A, coefficient sets as operand B
   int sy_kpad, sy_cells_pad;
@@ -899,6 +900,14 @@ struct yy_tc_tables {
   float *san_rsf, *san_azsf, *san_colsum, *san_ones, *san_part;
   yy::PairMaps san_maps;                  // a[0]: rho w rows, b[0]: table
 };
+
+// The dense analysis split into `splits` tiles along K, each of whole
+// segments (splits <= an_segs).
+static void set_an_splits(yy_tc_tables *t, int splits) {
+  t->an_segs_per = (t->an_segs + splits - 1) / splits;
+  t->an_splits = (t->an_segs + t->an_segs_per - 1) / t->an_segs_per;
+  t->an_kb_per = (t->an_kb_total + t->an_splits - 1) / t->an_splits;   // about; the segments decide
+}
 
 namespace yy {
 
@@ -1158,17 +1167,19 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
   t->an_modes_pad = round_up(g->n_lm, 2 * kPairRows);
   t->sy_kpad = round_up(g->n_lm, kPadK);
   t->sy_cells_pad = round_up(g->n_ang, 2 * kPairRows);
-  // split K of the analysis: about two tiles per CTA pair
+  // split K of the analysis: about two tiles per CTA pair.  K is cut into
+  // that many segments of (nearly) equal length, each summed in fills of
+  // kAnalysisFill into its own partial; a split takes whole segments, so the
+  // moments do not depend on it (coarser splits are the tuning range; finer
+  // segments would cost a partial's traffic each at every split).
   const int an_tiles = (t->an_modes_pad / (2 * kPairRows)) * t->row_tiles;
   const int kb_total = t->an_kpad * F::kElem / kRowBytes;
   int splits = (2 * t->pair_slots + an_tiles / 2) / an_tiles;
   splits = splits < 1 ? 1 : (splits > kb_total ? kb_total : splits);
   t->an_kb_total = kb_total;
-  t->an_kb_per = (kb_total + splits - 1) / splits;
-  t->an_splits = (kb_total + t->an_kb_per - 1) / t->an_kb_per;
+  t->an_segs = splits;
+  set_an_splits(t, splits);
   t->an_splits_rule = t->an_splits;
-  // the partial buffer holds up to four times the rule's splits (tuning range)
-  t->an_splits_cap = std::min(kb_total, 4 * t->an_splits);
 
   cudaError_t e = cudaSuccess;
   auto A = [&](void **ptr, size_t bytes) {
@@ -1182,7 +1193,7 @@ static yy_status prepare_form(yy_grid *g, yy_tc_tables *t) {
   A((void **)&t->an_mean, t->rows_pad * sizeof(double));
   A((void **)&t->an_colsum, g->n_lm * sizeof(double));
   A((void **)&t->an_b0, g->n_ang * sizeof(float));
-  A((void **)&t->part, (size_t)t->an_splits_cap * M * g->n_lm * sizeof(float));
+  A((void **)&t->part, (size_t)t->an_segs * M * g->n_lm * sizeof(float));
   for (int c = 0; c < 3; ++c) {
     A(&t->sy_q[c], (size_t)F::kPB * t->rows_pad * t->sy_kpad * F::kElem);
     A(&t->sy_tab[c], (size_t)F::kPA * t->sy_cells_pad * t->sy_kpad * F::kElem);
@@ -1375,6 +1386,8 @@ static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, 
   a.k_splits = t->an_splits;
   a.kb_per_split = t->an_kb_per;
   a.kb_chunk = kAnalysisFill * F::kElem / kRowBytes;
+  a.k_segs = t->an_segs;
+  a.segs_per_split = t->an_segs_per;
   a.a_rows = t->an_modes_pad;
   a.b_rows = t->rows_pad;
   a.out_mode = 0;
@@ -1386,14 +1399,14 @@ static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, 
   if (g->n_patch == 2 && g->lmax <= kReduceRotateLmax) {
     // the split-K sum and the combination of the patches in one launch
     const dim3 grid((unsigned)g->n_r, (unsigned)((g->n_lm + 255) / 256));
-    k_reduce_rotate<<<grid, 256, 0, s>>>(g->n_r, g->n_lm, t->an_splits, t->part, t->an_rhos, t->an_tabs, t->an_mono,
+    k_reduce_rotate<<<grid, 256, 0, s>>>(g->n_r, g->n_lm, t->an_segs, t->part, t->an_rhos, t->an_tabs, t->an_mono,
                                          t->an_mean, t->an_colsum, g->rot32, g->A, g->Atot);
     note_launch(g, "k_reduce_rotate", s);
     g->atot_done = 1;
     return cudaGetLastError();
   }
   const size_t cnt = (size_t)M * g->n_lm;
-  k_reduce_partials<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(M, g->n_lm, t->an_splits, t->part, t->an_rhos,
+  k_reduce_partials<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(M, g->n_lm, t->an_segs, t->part, t->an_rhos,
                                                                   t->an_tabs, t->an_mono, t->an_mean, t->an_colsum,
                                                                   g->A);
   note_launch(g, "k_reduce_partials", s);
@@ -1553,16 +1566,15 @@ int tc_analysis_splits(const yy_grid *g, yy_precision prec, int *rule, int *cap)
   const yy_tc_tables *t = ((int)prec >= 0 && (int)prec < 5) ? g->tc[prec] : nullptr;
   if (!t) return 0;
   if (rule) *rule = t->an_splits_rule;
-  if (cap) *cap = t->an_splits_cap;
+  if (cap) *cap = t->an_segs;
   return t->an_splits;
 }
 
 yy_status tc_set_analysis_splits(yy_grid *g, yy_precision prec, int splits) {
   yy_tc_tables *t = ((int)prec >= 0 && (int)prec < 5) ? g->tc[prec] : nullptr;
   if (!t) return YY_ERR_NOT_SUPPORTED;
-  if (splits < 1 || splits > t->an_splits_cap) return YY_ERR_INVALID_ARG;
-  t->an_kb_per = (t->an_kb_total + splits - 1) / splits;
-  t->an_splits = (t->an_kb_total + t->an_kb_per - 1) / t->an_kb_per;
+  if (splits < 1 || splits > t->an_segs) return YY_ERR_INVALID_ARG;
+  set_an_splits(t, splits);
   return YY_OK;
 }
 

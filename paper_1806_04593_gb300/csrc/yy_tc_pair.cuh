@@ -398,12 +398,16 @@ struct PairArgs {
   int kb_total;                 // K blocks (kRowBytes per row)
   int k_splits, kb_per_split;   // K split of every tile
   int kb_chunk;                 // K blocks per accumulator fill; mode 0 adds the fills in registers
+  int k_segs, segs_per_split;   // mode 0: K segments (0: none) -- segment z starts at K block
+                                // floor(z kb_total / k_segs), a split takes segs_per_split whole
+                                // segments, fills restart at every segment and each segment's
+                                // sums go out as one partial
   int a_rows, b_rows;           // rows of one piece in the stacked A / B operands
   int out_mode;                 // 1: scaled float64 job outputs; 0: raw fp32 partial sums;
                                 // 2: scaled float64 outputs stored along the rows of each cell;
                                 // 3: as 2, from the exact level sums of FormOzaki;
                                 // 4: as 3 with one fill and biased level sums
-  float *part;                  // mode 0: part[(z rows + row) part_ld + cell]
+  float *part;                  // mode 0: part[(segment rows + row) part_ld + cell]
   int part_ld;
   int out_split;
   long long ldo;
@@ -414,6 +418,43 @@ struct PairArgs {
 
 struct PairMaps {
   CUtensorMap a[4], b[3];       // tables (operand A), coefficient sets (operand B)
+};
+
+// First K block of segment z (of k_segs) of the K axis.
+__device__ __forceinline__ int seg_start(const PairArgs &a, int z) {
+  return (int)(((long long)z * a.kb_total) / a.k_segs);
+}
+
+// The K blocks of split z of a tile, [kb0, kb0 + nkb), walked in fills of
+// `chunk` blocks that restart at every segment start.  seg is the current
+// segment (the split's own index when K has no segments), seg_end its end
+// relative to kb0.
+struct TileFills {
+  int kb0, nkb, seg, seg_end;
+  __device__ __forceinline__ TileFills(const PairArgs &a, int z) {
+    if (a.k_segs > 0) {
+      seg = z * a.segs_per_split;
+      kb0 = seg_start(a, seg);
+      nkb = seg_start(a, min(a.k_segs, seg + a.segs_per_split)) - kb0;
+      seg_end = seg_start(a, seg + 1) - kb0;
+    } else {
+      seg = z;
+      kb0 = z * a.kb_per_split;
+      nkb = min(a.kb_total, kb0 + a.kb_per_split) - kb0;
+      seg_end = nkb;
+    }
+  }
+  // end (relative to kb0) of the fill that starts at c0
+  __device__ __forceinline__ int fill_end(int c0, int chunk) const { return min(c0 + chunk, seg_end); }
+  // after the fill ending at c1: whether it closed segment `seg`; if so, and
+  // more follow, move on to the next (the caller reads seg first)
+  __device__ __forceinline__ bool closes(int c1) const { return c1 == seg_end; }
+  __device__ __forceinline__ void advance(const PairArgs &a, int c1) {
+    if (c1 == seg_end && c1 < nkb) {
+      ++seg;
+      seg_end = seg_start(a, seg + 1) - kb0;
+    }
+  }
 };
 
 template <class F, int OUT_MODE>
@@ -473,8 +514,8 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
       for (int t = pair; t < total && ok; t += n_pairs) {
         const int jb = t / per_job, tl = t % per_job;
         const int rt = tl % a.row_tiles, ct = (tl / a.row_tiles) % a.cell_tiles;
-        const int kb0 = (tl / (a.row_tiles * a.cell_tiles)) * a.kb_per_split;
-        const int nkb = min(a.kb_total, kb0 + a.kb_per_split) - kb0;
+        const TileFills tf(a, tl / (a.row_tiles * a.cell_tiles));
+        const int kb0 = tf.kb0, nkb = tf.nkb;
         const int arow = (2 * ct + rank) * kPairRows;
         const int brow = rt * a.bn + rank * bh;
         const CUtensorMap *tmA = &maps.a[a.job[jb].ta];
@@ -512,10 +553,12 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
       bool ok = true;
       for (int t = pair; t < total && ok; t += n_pairs) {
         const int tl = t % per_job;
-        const int kb0 = (tl / (a.row_tiles * a.cell_tiles)) * a.kb_per_split;
-        const int nkb = min(a.kb_total, kb0 + a.kb_per_split) - kb0;
+        TileFills tf(a, tl / (a.row_tiles * a.cell_tiles));
+        const int nkb = tf.nkb;
         // the tile's K blocks in fills of kb_chunk, alternating between the two accumulators
-        for (int c0 = 0; c0 < nkb && ok; c0 += chunk, ++it) {
+        for (int c0 = 0, c1 = 0; c0 < nkb && ok; c0 = c1, ++it) {
+          c1 = tf.fill_end(c0, chunk);
+          tf.advance(a, c1);
           const int b = it & 1;
           if (it >= 2) {
             if (!mbar_wait_cluster(&tempty[b], ((it >> 1) & 1) ^ 1, a.err)) {
@@ -525,7 +568,6 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
             tc_fence_after();
           }
           const uint32_t dacc = tmem_base + (uint32_t)(b * 256);   // accumulator a at + a bn
-          const int c1 = min(nkb, c0 + chunk);
           for (int i = c0; i < c1; ++i, ++gk) {
             if (!mbar_wait_cluster(&full[s], ph, a.err)) {
               ok = false;
@@ -567,17 +609,19 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
     constexpr bool scaled = OUT_MODE == 1;
     int it = 0;
     if constexpr (OUT_MODE == 0) {
-      // K-split partial sums: the tile's accumulator fills (kb_chunk K blocks
+      // Segment partial sums: the tile's accumulator fills (kb_chunk K blocks
       // each) are added here in fp32 registers, so no fp32 accumulation chain
-      // in the tensor core runs longer than one fill.  This warp owns 16-column
-      // chunks sub, sub + kEpiPerQuarter, ... (at most kMaxOwn of them).
+      // in the tensor core runs longer than one fill, and each K segment
+      // (k_segs of them, fixed by the sizes; a split takes whole segments and
+      // fills restart at each) goes out as its own partial: the same fills
+      // are added in the same order whatever the split.  This warp owns 16-column chunks sub,
+      // sub + kEpiPerQuarter, ... (at most kMaxOwn of them).
       constexpr int kMaxOwn = 256 / kEpiCols / kEpiPerQuarter;
       for (int t = pair; t < total; t += n_pairs) {
         const int tl = t % per_job;
         const int rt = tl % a.row_tiles, ct = (tl / a.row_tiles) % a.cell_tiles;
-        const int z = tl / (a.row_tiles * a.cell_tiles);
-        const int kb0 = z * a.kb_per_split;
-        const int nkb = min(a.kb_total, kb0 + a.kb_per_split) - kb0;
+        TileFills tf(a, tl / (a.row_tiles * a.cell_tiles));
+        const int nkb = tf.nkb;
         const int cell = (2 * ct + rank) * kPairRows + quarter * 32 + lane;
         float acc[kMaxOwn][kEpiCols];
 #pragma unroll
@@ -585,7 +629,8 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
 #pragma unroll
           for (int j = 0; j < kEpiCols; ++j) acc[o][j] = 0.0f;
         bool ok = true;
-        for (int c0 = 0; c0 < nkb; c0 += chunk, ++it) {
+        for (int c0 = 0, c1 = 0; c0 < nkb; c0 = c1, ++it) {
+          c1 = tf.fill_end(c0, chunk);
           const int b = it & 1;
           if (!mbar_wait_cluster(&tfull[b], (it >> 1) & 1, a.err)) {
             ok = false;
@@ -607,21 +652,25 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive_cluster_relaxed(tempty_even + (uint32_t)(b * sizeof(uint64_t)));
-        }
-        if (!ok) break;
-        if (cell < a.cells) {
+          if (!tf.closes(c1)) continue;
+          // the end of a segment: its partial sums go out
+          const size_t zs = (size_t)tf.seg;
+          tf.advance(a, c1);
 #pragma unroll
           for (int o = 0; o < kMaxOwn; ++o) {
             const int k = sub + o * kEpiPerQuarter;
-            if (k < n_chunks) {
+            if (k < n_chunks && cell < a.cells) {
 #pragma unroll
               for (int j = 0; j < kEpiCols; ++j) {
                 const int row = rt * a.bn + k * kEpiCols + j;
-                if (row < a.rows) a.part[((size_t)z * a.rows + row) * a.part_ld + cell] = acc[o][j];
+                if (row < a.rows) a.part[(zs * a.rows + row) * a.part_ld + cell] = acc[o][j];
               }
             }
+#pragma unroll
+            for (int j = 0; j < kEpiCols; ++j) acc[o][j] = 0.0f;
           }
         }
+        if (!ok) break;
       }
     } else if constexpr (OUT_MODE == 2 || OUT_MODE == 3 || OUT_MODE == 4) {
       // Cells are rows of the output arrays (stride ldo) and the accumulator
@@ -645,8 +694,8 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
           const PairJob &J = a.job[t / per_job];
           const int tl = t % per_job;
           const int rt = tl % a.row_tiles, ct = (tl / a.row_tiles) % a.cell_tiles;
-          const int kb0 = (tl / (a.row_tiles * a.cell_tiles)) * a.kb_per_split;
-          const int nkb = min(a.kb_total, kb0 + a.kb_per_split) - kb0;
+          TileFills tf(a, tl / (a.row_tiles * a.cell_tiles));
+          const int nkb = tf.nkb;
           const int cell = (2 * ct + rank) * kPairRows + quarter * 32 + lane;
           const bool cell_ok = cell < a.cells;
           const int ce = cell_ok ? J.cell_exp[cell] : 0;
@@ -662,7 +711,9 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
             lo[j] = 0.0f;
           }
           bool ok = true;
-          for (int c0 = 0; c0 < nkb; c0 += chunk, ++it) {
+          for (int c0 = 0, c1 = 0; c0 < nkb; c0 = c1, ++it) {
+            c1 = tf.fill_end(c0, chunk);
+            tf.advance(a, c1);
             const int b = it & 1;
             if (!mbar_wait_cluster(&tfull[b], (it >> 1) & 1, a.err)) {
               ok = false;
@@ -788,7 +839,6 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
       const PairJob &J = a.job[t / per_job];
       const int tl = t % per_job;
       const int rt = tl % a.row_tiles, ct = (tl / a.row_tiles) % a.cell_tiles;
-      const int z = tl / (a.row_tiles * a.cell_tiles);
       const int cell = (2 * ct + rank) * kPairRows + quarter * 32 + lane;
       const bool cell_ok = cell < a.cells;
       const float cs = (cell_ok && scaled) ? J.cell_scale[cell] : 0.0f;

@@ -77,6 +77,10 @@ def load():
     lib.yy_grid_prepare.restype = I
     lib.yy_grid_set_analysis.argtypes = [P, I]
     lib.yy_grid_set_analysis.restype = I
+    lib.yy_grid_analysis_splits.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.yy_grid_analysis_splits.restype = I
+    lib.yy_grid_set_analysis_splits.argtypes = [P, I, I]
+    lib.yy_grid_set_analysis_splits.restype = I
     lib.yy_potential.argtypes = [P, P, P, P, P, P, P, I, P]
     lib.yy_potential.restype = I
     lib.yy_potential_host.argtypes = [P, P, P, P, P, P, P, I, P]
@@ -182,6 +186,17 @@ def yy_grid_prepare(handle, prec):
 
 def yy_grid_set_analysis(handle, method):
     return load().yy_grid_set_analysis(handle, int(method))
+
+
+def yy_grid_analysis_splits(handle, prec):
+    """(current split, the sizes' default, the largest accepted split)."""
+    rule, cap = ctypes.c_int(0), ctypes.c_int(0)
+    cur = load().yy_grid_analysis_splits(handle, int(prec), ctypes.byref(rule), ctypes.byref(cap))
+    return cur, rule.value, cap.value
+
+
+def yy_grid_set_analysis_splits(handle, prec, splits):
+    return load().yy_grid_set_analysis_splits(handle, int(prec), int(splits))
 
 
 def yy_potential(handle, rho_yin, rho_yang, phi_yin, phi_yang, grad_yin=None, grad_yang=None,
@@ -395,6 +410,15 @@ class Grid:
         st = yy_grid_set_analysis(self.handle, ANALYSES.get(method, method))
         if st != YY_OK:
             raise YYError(st, "yy_grid_set_analysis")
+
+    def analysis_splits(self, prec):
+        """(current, default, largest) K split of the dense analysis of a form."""
+        return yy_grid_analysis_splits(self.handle, PRECISIONS.get(prec, prec))
+
+    def set_analysis_splits(self, prec, splits):
+        st = yy_grid_set_analysis_splits(self.handle, PRECISIONS.get(prec, prec), splits)
+        if st != YY_OK:
+            raise YYError(st, "yy_grid_set_analysis_splits")
 
     def prepare(self, prec):
         st = yy_grid_prepare(self.handle, PRECISIONS.get(prec, prec))
