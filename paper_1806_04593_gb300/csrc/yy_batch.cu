@@ -10,8 +10,9 @@
 //
 // yy_batch_tune is the autotuner.  Per field it times both evaluations
 // (dense contractions, separable stages) and, for a dense tensor-core
-// analysis, the K split of the contraction (the rule's count times 1/2, 1, 2
-// and 4), on scratch buffers, and records the fastest for that precision.
+// analysis, the K split of the contraction (the rule's count and half of it;
+// the moments are the same at every split), on scratch buffers, and records
+// the fastest for that precision.
 // The first capture after tuning also times the whole graph with 1, 2, 4, 8
 // and 16 branches on the caller's buffers and keeps the fastest.
 #include <string.h>

@@ -1870,39 +1870,37 @@ struct OzRhoArgs {
   int *rexp;                    // [rows_pad]
 };
 
-// Balanced base-256 digits of X < 2^48 as oz_digits computes them, in 32-bit
-// operations: the three low digits from the low 24 bits, their carry (0 or 1)
-// into the high 24 bits, then the two next digits and the rest.  A digit
-// v in [0, 255] becomes v - 256 with a carry of one when v > 128, which
-// (v + 127) >> 8 tells without a branch.
-__device__ __forceinline__ void oz_digits32(unsigned long long X, int (&d)[6]) {
-  unsigned lo = (unsigned)X & 0xFFFFFFu;
-  unsigned hi = (unsigned)(X >> 24);
+// Balanced base-256 digits of a signed X, |X| <= 2^47, as fp32 integers:
+// the low 24 bits taken as a signed number in [-2^23, 2^23) (with a carry
+// into the high part), then three digits of each 24-bit half, each digit the
+// remainder rounded to the nearest multiple of 2^16 or 2^8 by one fused
+// multiply-add against 1.5 2^23 (every value below 2^24: all exact).  Each
+// digit lies in [-128, 128]; its fp32 bit pattern has sixteen zero low bits,
+// so the upper half is the digit in bf16.
+__device__ __forceinline__ void oz_digits_f(long long X, float (&d)[6]) {
+  constexpr float kRound = 12582912.0f;   // 1.5 2^23: the sum's last place is 1
+  int lo = (int)((unsigned)X & 0xFFFFFFu);
+  int hi = (int)(X >> 24);
+  const int carry = lo >= 0x800000 ? 1 : 0;
+  lo -= carry << 24;
+  hi += carry;
+  const float half[2] = {(float)hi, (float)lo};
 #pragma unroll
-  for (int s = 5; s >= 3; --s) {
-    const unsigned v = lo & 255u;
-    const unsigned c = (v + 127u) >> 8;
-    d[s] = (int)v - (int)(c << 8);
-    lo = (lo >> 8) + c;
+  for (int h = 0; h < 2; ++h) {
+    const float r0 = half[h];
+    const float d0 = __fsub_rn(__fmaf_rn(r0, 1.0f / 65536.0f, kRound), kRound);
+    const float r1 = __fmaf_rn(-d0, 65536.0f, r0);
+    const float d1 = __fsub_rn(__fmaf_rn(r1, 1.0f / 256.0f, kRound), kRound);
+    d[3 * h] = d0;
+    d[3 * h + 1] = d1;
+    d[3 * h + 2] = __fmaf_rn(-d1, 256.0f, r1);
   }
-  hi += lo;
-#pragma unroll
-  for (int s = 2; s >= 1; --s) {
-    const unsigned v = hi & 255u;
-    const unsigned c = (v + 127u) >> 8;
-    d[s] = (int)v - (int)(c << 8);
-    hi = (hi >> 8) + c;
-  }
-  d[0] = (int)hi;
 }
 
-// C: 64-wide pieces of a row held per lane (k_pad <= 64 C).  The bf16 bit
-// patterns of the digits -128 .. 128 come from a table in shared memory.
+// C: 64-wide pieces of a row held per lane (k_pad <= 64 C).  Two cells'
+// digits of one slice go out as one 32-bit store of their bf16 patterns.
 template <int C>
 __global__ void __launch_bounds__(256) k_rhow_ozaki(OzRhoArgs a) {
-  __shared__ uint16_t bf16_of[257];   // bf16 bits of the integer i - 128
-  for (int i = threadIdx.x; i < 257; i += blockDim.x) bf16_of[i] = (uint16_t)(__float_as_uint((float)(i - 128)) >> 16);
-  __syncthreads();
   const int row = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (row >= a.rows) return;
   const int shell = row / a.n_theta, j = row % a.n_theta;
@@ -1945,21 +1943,20 @@ __global__ void __launch_bounds__(256) k_rhow_ozaki(OzRhoArgs a) {
   for (int c = 0; c < C; ++c) {
     const int k0 = 2 * lane + 64 * c;
     if (k0 >= a.k_pad) break;
-    int d[2][6];
+    float d[2][6];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int ex = (int)((bits[c][h] >> 52) & 0x7FFu);
       const int sh = 1027 - ex + e;
-      unsigned long long X = 0ull;
+      long long X = 0;
       if (exm != 0 && ex != 0 && sh < 64)
-        X = ((((bits[c][h] & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> (sh - 1)) + 1ull) >> 1;
-      oz_digits32(X, d[h]);
+        X = (long long)(((((bits[c][h] & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> (sh - 1)) + 1ull) >> 1);
+      oz_digits_f((bits[c][h] >> 63) ? -X : X, d[h]);
     }
-    const int s0 = (bits[c][0] >> 63) ? -1 : 1, s1 = (bits[c][1] >> 63) ? -1 : 1;
     uint32_t *dst = reinterpret_cast<uint32_t *>(a.X + (size_t)row * a.k_pad + k0);
 #pragma unroll
     for (int sl = 0; sl < 6; ++sl)
-      dst[sl * (stride / 2)] = (uint32_t)bf16_of[s0 * d[0][sl] + 128] | ((uint32_t)bf16_of[s1 * d[1][sl] + 128] << 16);
+      dst[sl * (stride / 2)] = __byte_perm(__float_as_uint(d[0][sl]), __float_as_uint(d[1][sl]), 0x7632);
   }
   if (lane == 0) a.rexp[row] = exm == 0 ? 0 : e + a.eb - 64;
 }
