@@ -696,6 +696,15 @@ def run_batched(args, gradient, dev, stream, flush):
 
     ms = timed(prec, args.batch_steps, max(3, args.warmup))
     launches = b.launch_count()
+    groups = b.groups()
+    # the graph forms the first capture chose between, each timed the same way
+    modes = {}
+    for ng in (0, 1, 2, 4):
+        b.set_grouping(ng)
+        m = timed(prec, args.batch_steps, max(3, args.warmup))
+        modes["per_field_graph" if ng == 0 else f"grouped_{ng}"] = {
+            "ms_per_step": m, "kernels_per_step": b.launch_count(), "value": len(specs) * 1e3 / m}
+    b.set_grouping(groups)
     splits = [b.analysis_splits(i, prec) for i in range(len(specs))]
     # each field solved alone on its own grid (tuned settings), back to back
     solo_ms = 0.0
@@ -727,7 +736,12 @@ def run_batched(args, gradient, dev, stream, flush):
         "analysis_chosen": {"dense": chosen.count(yy.YY_ANALYSIS_DENSE),
                             "separable": chosen.count(yy.YY_ANALYSIS_SEPARABLE)},
         "tune_s": tune_s, "graph_launches_per_step": 1, "kernels_per_step": launches,
-        "graph_branches": b.branches(),
+        "graph_form": (f"{groups} concurrent groups of fields, one launch per stage and group (density packing, "
+                    "analysis contraction, split-K sum and patch combination, radial scans, coefficient "
+                    "packing, synthesis contraction)") if launches < len(specs) else
+                   "per-field solves on parallel branches",
+        "graph_forms": modes,
+        "graph_branches": b.branches(), "field_groups": groups,
         "analysis_splits_chosen": {str(v): splits.count(v) for v in sorted(set(splits))},
         "sum_of_solo_solves_ms": solo_ms,
         "fp64_gpu_path": {"value": len(specs) * 1e3 / ms64, "unit": "field solves/s", "ms_per_step": ms64},

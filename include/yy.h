@@ -402,12 +402,37 @@ yy_status yy_batch_potential(yy_batch *b, const double *const *rho_yin, const do
 /* The grid of one field (owned by the batch; NULL if out of range). */
 yy_grid *yy_batch_grid(yy_batch *b, int field);
 
-/* Kernels in the last recorded graph (-1 for NULL). */
+/* Kernels in the graph the last yy_batch_potential launched (-1 for NULL). */
 int yy_batch_last_launch_count(const yy_batch *b);
+
+/* Grouped solves: `groups` concurrent groups of fields, or 0 for one graph
+ * of per-field solves (default: grouped, two groups).  In a tensor-core form, when every field
+ * uses the dense evaluation (YY_ANALYSIS_AUTO or _DENSE, as yy_batch_tune
+ * records for the batched workload) and fits the grouped kernels (two
+ * patches, l_max <= 80, n_r <= 768, rows of at most 24,576 cells and 2,048
+ * modes), the graph holds one launch per stage over all fields: the density
+ * packing, the analysis contraction (one tile list spanning every field's
+ * tiles, each field's tensor maps in device memory), the split-K sum with
+ * the patches' combination, the radial scans, the coefficient packing and the
+ * synthesis contraction -- six to eight kernels (the density rows take the
+ * form the field's own solve packs them in: a warp a row up to 2,048 cells,
+ * streamed when longer and even, a block a row otherwise), with each field's
+ * arithmetic that of its own solve (bitwise the same results).  The fields
+ * are split into groups of about equal work that run side by side, each with
+ * its own launch per stage; unless this call fixed their number, the first
+ * grouped capture after yy_batch_tune times one, two and four groups and
+ * keeps the fastest.  Otherwise, or with groups = 0, every field's solve is
+ * recorded on parallel branches.  The call drops the recorded graphs.
+ * Errors: YY_ERR_INVALID_ARG for NULL or groups outside 0 .. 16. */
+yy_status yy_batch_set_grouping(yy_batch *b, int groups);
 
 /* Parallel branches of the batch's graphs: 4, or the count the first capture
  * after yy_batch_tune picked by timing 1, 2, 4, 8 and 16 (-1 for NULL). */
 int yy_batch_branches(const yy_batch *b);
+
+/* Concurrent groups of the grouped solves (see yy_batch_set_grouping; 0 when
+ * grouping is off, -1 for NULL). */
+int yy_batch_groups(const yy_batch *b);
 
 /* K split of the dense tensor-core analysis recorded for a field and form by
  * yy_batch_tune (0: the rule's count; -1 for bad arguments). */

@@ -17,6 +17,7 @@
 // and 16 branches on the caller's buffers and keeps the fastest.
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -33,6 +34,8 @@ struct GraphEntry {
   int prec, grad;
   std::vector<const void *> ptrs;
   cudaGraphExec_t exec;
+  std::vector<yy::TcGroup *> groups;   // the grouped solves' argument tables (empty: per-field graph)
+  int launches;
 };
 
 }  // namespace
@@ -50,6 +53,9 @@ struct yy_batch {
   cudaEvent_t fork, join[kBranchesMax];
   std::vector<GraphEntry> cache;
   int launches;                     // kernels in the last captured graph
+  int grouping;                     // tensor-core forms: one launch per stage over all fields when they allow
+  int n_groups;                     // concurrent groups of fields (each its own launch per stage)
+  int tune_groups;                  // time 1, 2 and 4 groups at the next grouped capture
 };
 
 namespace {
@@ -62,8 +68,18 @@ yy_status to_status(cudaError_t e) {
 
 bool tensor_form(yy_precision p) { return p == YY_TF32 || p == YY_BF16X3 || p == YY_FP16X2; }
 
+void drop_groups(std::vector<yy::TcGroup *> &groups) {
+  for (yy::TcGroup *grp : groups) yy::tc_group_destroy(grp);
+  groups.clear();
+}
+
+void drop_entry(GraphEntry &g) {
+  cudaGraphExecDestroy(g.exec);
+  drop_groups(g.groups);
+}
+
 void drop_cache(yy_batch *b) {
-  for (GraphEntry &g : b->cache) cudaGraphExecDestroy(g.exec);
+  for (GraphEntry &g : b->cache) drop_entry(g);
   b->cache.clear();
 }
 
@@ -93,6 +109,82 @@ struct Buffers {
   const double *const *rho_yin, *const *rho_yang;
   double *const *phi_yin, *const *phi_yang, *const *grad_yin, *const *grad_yang;
 };
+
+// The fields in `ng` groups of about equal work (largest first, each to the
+// group with the least so far; the synthesis, n_r n_ang (l_max + 1)^2, leads),
+// each group's argument tables built; NOT_SUPPORTED if a field does not fit.
+yy_status build_groups(yy_batch *b, const Buffers &io, yy_precision prec, int ng,
+                       std::vector<yy::TcGroup *> *out) {
+  std::vector<int> order(b->n);
+  std::vector<double> work(b->n);
+  for (int i = 0; i < b->n; ++i) {
+    const yy_grid *g = b->grids[i];
+    order[i] = i;
+    work[i] = (double)g->n_r * g->n_ang * (double)g->n_lm;
+  }
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+  std::vector<std::vector<int>> members(ng);
+  std::vector<double> load(ng, 0.0);
+  for (int i : order) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    members[k].push_back(i);
+    load[k] += work[i];
+  }
+  const bool grad = io.grad_yin != nullptr;
+  for (int k = 0; k < ng; ++k) {
+    if (members[k].empty()) continue;
+    std::sort(members[k].begin(), members[k].end());
+    std::vector<yy_grid *> gs;
+    std::vector<const double *> ry, rg;
+    std::vector<double *> py, pg, gy, gg;
+    for (int i : members[k]) {
+      gs.push_back(b->grids[i]);
+      ry.push_back(io.rho_yin[i]);
+      rg.push_back(io.rho_yang[i]);
+      py.push_back(io.phi_yin[i]);
+      pg.push_back(io.phi_yang[i]);
+      gy.push_back(grad ? io.grad_yin[i] : nullptr);
+      gg.push_back(grad ? io.grad_yang[i] : nullptr);
+    }
+    yy::TcGroup *grp = nullptr;
+    const yy_status st = yy::tc_group_create(gs.data(), (int)gs.size(), prec, ry.data(), rg.data(), py.data(),
+                                             pg.data(), grad ? gy.data() : nullptr, grad ? gg.data() : nullptr, &grp);
+    if (st != YY_OK) {
+      drop_groups(*out);
+      return st;
+    }
+    out->push_back(grp);
+  }
+  return YY_OK;
+}
+
+// record the grouped solves into a graph: each group's launches on its own
+// branch, the groups running side by side
+yy_status capture_groups(yy_batch *b, const std::vector<yy::TcGroup *> &groups, cudaGraphExec_t *out,
+                         int *launches) {
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return to_status(e);
+  cudaError_t run = cudaEventRecord(b->fork, b->cap);
+  int n = 0;
+  for (size_t k = 0; k < groups.size() && run == cudaSuccess; ++k) {
+    run = cudaStreamWaitEvent(b->branch[k], b->fork, 0);
+    if (run == cudaSuccess) run = yy::tc_group_run(groups[k], b->branch[k]);
+    if (run == cudaSuccess) run = cudaEventRecord(b->join[k], b->branch[k]);
+    if (run == cudaSuccess) run = cudaStreamWaitEvent(b->cap, b->join[k], 0);
+    n += yy::tc_group_launches(groups[k]);
+  }
+  e = cudaStreamEndCapture(b->cap, &graph);
+  if (run != cudaSuccess || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return to_status(run != cudaSuccess ? run : e);
+  }
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  *launches = n;
+  return to_status(e);
+}
 
 // record every field's solve on `branches` parallel branches into a graph
 yy_status capture(yy_batch *b, const Buffers &io, yy_precision prec, int branches, cudaGraphExec_t *out,
@@ -163,6 +255,8 @@ yy_status yy_batch_create(const yy_field_desc *fields, int n_fields, yy_batch **
   b->method.assign((size_t)n_fields * kPrecisions, (int)YY_ANALYSIS_AUTO);
   b->splits.assign((size_t)n_fields * kPrecisions, 0);
   b->branches = kBranchesDefault;
+  b->grouping = 1;
+  b->n_groups = 2;
   cudaGetDevice(&b->device);
   yy_status st = YY_OK;
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
@@ -284,7 +378,7 @@ yy_status yy_batch_tune(yy_batch *b, yy_precision prec, int with_gradient, int r
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   drop_cache(b);
-  if (st == YY_OK) b->tune_branches = 1;
+  if (st == YY_OK) b->tune_branches = b->tune_groups = 1;
   return st;
 }
 
@@ -310,7 +404,10 @@ yy_status yy_batch_potential(yy_batch *b, const double *const *rho_yin, const do
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   for (GraphEntry &ge : b->cache)
-    if (ge.prec == (int)prec && ge.grad == grad && ge.ptrs == key) return to_status(cudaGraphLaunch(ge.exec, s));
+    if (ge.prec == (int)prec && ge.grad == grad && ge.ptrs == key) {
+      b->launches = ge.launches;
+      return to_status(cudaGraphLaunch(ge.exec, s));
+    }
 
   // first use of this set of buffers: capture every field's solve.  Tables a
   // field's evaluation needs are built here, before the capture begins.
@@ -322,49 +419,132 @@ yy_status yy_batch_potential(yy_batch *b, const double *const *rho_yin, const do
   }
   const Buffers io = {rho_yin, rho_yang, phi_yin, phi_yang, grad_yin, grad_yang};
   cudaGraphExec_t exec = nullptr;
+  std::vector<yy::TcGroup *> groups;
   int launches = 0;
   yy_status st = YY_OK;
-  if (b->tune_branches) {
-    // time the graph with each branch count on these buffers (every trial
-    // leaves the same results in them) and keep the fastest
+  bool timing = false;   // after tuning: time the grouped and the per-field graphs
+  float best_grouped = 1e30f;
+  if (b->grouping && tensor_form(prec)) {
+    timing = b->tune_groups != 0;
+    // every field dense: one launch per stage over the fields of a group,
+    // the groups side by side (their number timed once after tuning)
+    bool dense = true;
+    for (int i = 0; i < b->n && dense; ++i) dense = b->method[(size_t)i * kPrecisions + prec] != YY_ANALYSIS_SEPARABLE;
+    for (int i = 0; i < b->n && dense && st == YY_OK; ++i) st = apply_field_setting(b, i, prec);
+    if (st != YY_OK) return st;
+    const int trials[3] = {1, 2, 4};
     float best = 1e30f;
-    for (int nb = 1; nb <= kBranchesMax && st == YY_OK; nb *= 2) {
+    for (int q = 0; q < 3 && dense; ++q) {
+      const int ng = b->tune_groups ? trials[q] : b->n_groups;
+      if (!b->tune_groups && q > 0) break;
+      if (ng > b->n || ng > kBranchesMax) continue;
+      std::vector<yy::TcGroup *> trial_groups;
+      st = build_groups(b, io, prec, ng, &trial_groups);
+      if (st == YY_ERR_NOT_SUPPORTED) {   // a field does not fit: per-field graphs
+        st = YY_OK;
+        break;
+      }
+      if (st != YY_OK) break;
       cudaGraphExec_t trial = nullptr;
       int n_launch = 0;
       float ms = 0.0f;
-      st = capture(b, io, prec, nb, &trial, &n_launch);
-      if (st == YY_OK) st = time_graph(trial, s, &ms);
+      st = capture_groups(b, trial_groups, &trial, &n_launch);
+      if (st == YY_OK && b->tune_groups) st = time_graph(trial, s, &ms);
       if (st == YY_OK && ms < best) {
         best = ms;
         if (exec) cudaGraphExecDestroy(exec);
+        drop_groups(groups);
         exec = trial;
+        groups = trial_groups;
         launches = n_launch;
-        b->branches = nb;
-      } else if (trial) {
-        cudaGraphExecDestroy(trial);
+        b->n_groups = ng;
+      } else {
+        if (trial) cudaGraphExecDestroy(trial);
+        drop_groups(trial_groups);
       }
+      if (st != YY_OK) break;
     }
     if (st != YY_OK) {
       if (exec) cudaGraphExecDestroy(exec);
+      drop_groups(groups);
       return st;
     }
-    b->tune_branches = 0;
-  } else {
-    st = capture(b, io, prec, b->branches, &exec, &launches);
-    if (st != YY_OK) return st;
+    best_grouped = best;
   }
+  if (!exec || timing) {
+    // the per-field graph: when nothing was grouped, or to compare with the grouped one
+    cudaGraphExec_t fexec = nullptr;
+    int flaunch = 0;
+    float fbest = 1e30f;
+    if (b->tune_branches) {
+      // time the graph with each branch count on these buffers (every trial
+      // leaves the same results in them) and keep the fastest
+      for (int nb = 1; nb <= kBranchesMax && st == YY_OK; nb *= 2) {
+        cudaGraphExec_t trial = nullptr;
+        int n_launch = 0;
+        float ms = 0.0f;
+        st = capture(b, io, prec, nb, &trial, &n_launch);
+        if (st == YY_OK) st = time_graph(trial, s, &ms);
+        if (st == YY_OK && ms < fbest) {
+          fbest = ms;
+          if (fexec) cudaGraphExecDestroy(fexec);
+          fexec = trial;
+          flaunch = n_launch;
+          b->branches = nb;
+        } else if (trial) {
+          cudaGraphExecDestroy(trial);
+        }
+      }
+      if (st == YY_OK) b->tune_branches = 0;
+    } else {
+      st = capture(b, io, prec, b->branches, &fexec, &flaunch);
+      if (st == YY_OK && exec) st = time_graph(fexec, s, &fbest);
+    }
+    if (st != YY_OK) {
+      if (fexec) cudaGraphExecDestroy(fexec);
+      if (exec) cudaGraphExecDestroy(exec);
+      drop_groups(groups);
+      return st;
+    }
+    if (!exec || fbest < best_grouped) {
+      // the per-field graph it is (the tuner keeps to it for this batch)
+      if (exec) {
+        cudaGraphExecDestroy(exec);
+        drop_groups(groups);
+        b->grouping = 0;
+      }
+      exec = fexec;
+      launches = flaunch;
+    } else {
+      cudaGraphExecDestroy(fexec);
+    }
+  }
+  if (timing) b->tune_groups = 0;
   if ((int)b->cache.size() >= kCacheSize) {
-    cudaGraphExecDestroy(b->cache.front().exec);
+    drop_entry(b->cache.front());
     b->cache.erase(b->cache.begin());
   }
-  b->cache.push_back(GraphEntry{(int)prec, grad, key, exec});
+  b->cache.push_back(GraphEntry{(int)prec, grad, key, exec, groups, launches});
   b->launches = launches;
   return to_status(cudaGraphLaunch(exec, s));
 }
 
 int yy_batch_last_launch_count(const yy_batch *b) { return b ? b->launches : -1; }
 
+yy_status yy_batch_set_grouping(yy_batch *b, int groups) {
+  if (!b || groups < 0 || groups > kBranchesMax) return YY_ERR_INVALID_ARG;
+  drop_cache(b);   // later calls record their graphs anew
+  b->grouping = groups > 0;
+  if (groups > 0) {
+    b->n_groups = groups;
+    b->tune_groups = 0;
+  }
+  return YY_OK;
+}
+
 int yy_batch_branches(const yy_batch *b) { return b ? b->branches : -1; }
+
+int yy_batch_groups(const yy_batch *b) { return b ? (b->grouping ? b->n_groups : 0) : -1; }
 
 int yy_batch_analysis_splits(const yy_batch *b, int field, yy_precision prec) {
   if (!b || field < 0 || field >= b->n || (int)prec < 0 || (int)prec >= kPrecisions) return -1;

@@ -155,6 +155,32 @@ cudaError_t rotate_moments(yy_grid *g, bool fp64, cudaStream_t s);
 void scan_geometry(const yy_grid *g, int *nc, int *ch);
 cudaError_t radial_scan(yy_grid *g, bool want_f32, bool f64_out, cudaStream_t s);
 
+// Grouped solves (yy_tc.cu): every field solved densely in a tensor-core form,
+// one launch per stage over all of them; NOT_SUPPORTED when a field does not
+// fit the grouped kernels (then each field is solved on its own).
+struct TcGroup;
+yy_status tc_group_create(yy_grid *const *grids, int n, yy_precision prec, const double *const *rho_yin,
+                          const double *const *rho_yang, double *const *phi_yin, double *const *phi_yang,
+                          double *const *grad_yin, double *const *grad_yang, TcGroup **out);
+cudaError_t tc_group_run(const TcGroup *grp, cudaStream_t s);
+int tc_group_launches(const TcGroup *grp);
+void tc_group_destroy(TcGroup *grp);
+
+// Grouped radial scans (one launch for many fields, yy_scan.cu): a field's
+// arguments when its scan takes the one-pass warp form (n_r <= 768), the
+// 128-thread blocks it takes, and the launch over a device table of fields
+// with a block map (per block: field << 24 | the field's own block).
+struct ScanGroupField {
+  int n_patch, n_r, lmax, n_lm, ch;   // ch: radii per lane, 8, 12, 18 or 24
+  const double *A, *coef;
+  double *Q;
+  float *Q32;
+};
+bool scan_group_field(yy_grid *g, bool want_f32, ScanGroupField *f);
+int scan_group_blocks(const ScanGroupField &f);
+cudaError_t scan_group_launch(const ScanGroupField *fields, const uint32_t *block_map, int blocks, bool f64_out,
+                              cudaStream_t s);
+
 // tensor-core path (yy_tc.cu)
 yy_status tc_prepare(yy_grid *g, yy_precision prec);
 void tc_free(yy_grid *g);

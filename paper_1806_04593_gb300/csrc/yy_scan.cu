@@ -217,10 +217,9 @@ k_rotate_moments(int n_r, int n_lm, const T *__restrict__ rot, const double *__r
 // reduced-precision paths, whose packing rounds Q to fp32 anyway) in fp32
 // from fp32 roundings of c_n and d_n, widened back exactly.
 template <int CH, bool F64OUT>
-__global__ void __launch_bounds__(128, 3)
-k_scan_warp(int n_patch, int n_r, int lmax, int n_lm, const double *__restrict__ A, const double *__restrict__ coef,
-            double *__restrict__ Q, float *__restrict__ Q32) {
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ __forceinline__ void scan_warp_body(int w, int n_patch, int n_r, int lmax, int n_lm,
+                                               const double *__restrict__ A, const double *__restrict__ coef,
+                                               double *__restrict__ Q, float *__restrict__ Q32) {
   const int lane = threadIdx.x & 31;
   if (w >= n_patch * n_lm) return;
   const int p = w / n_lm, j = w % n_lm;
@@ -332,7 +331,57 @@ k_scan_warp(int n_patch, int n_r, int lmax, int n_lm, const double *__restrict__
   }
 }
 
+template <int CH, bool F64OUT>
+__global__ void __launch_bounds__(128, 3)
+k_scan_warp(int n_patch, int n_r, int lmax, int n_lm, const double *__restrict__ A, const double *__restrict__ coef,
+            double *__restrict__ Q, float *__restrict__ Q32) {
+  scan_warp_body<CH, F64OUT>((int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), n_patch, n_r, lmax, n_lm, A, coef,
+                             Q, Q32);
+}
+
+// Many fields' scans in one launch: block b scans for field block_map[b] >> 24
+// (its block block_map[b] & 0xFFFFFF, four (patch, mode) warps each), in the
+// register form the field's radial grid needs (ch = 8, 12, 18 or 24 radii per lane).
+template <bool F64OUT>
+__global__ void __launch_bounds__(128, 3)
+k_scan_group(const ScanGroupField *__restrict__ fields, const uint32_t *__restrict__ block_map) {
+  const uint32_t m = block_map[blockIdx.x];
+  const ScanGroupField f = fields[m >> 24];
+  const int w = (int)(m & 0xFFFFFFu) * 4 + (int)(threadIdx.x >> 5);
+  switch (f.ch) {
+    case 8: scan_warp_body<8, F64OUT>(w, f.n_patch, f.n_r, f.lmax, f.n_lm, f.A, f.coef, f.Q, f.Q32); break;
+    case 12: scan_warp_body<12, F64OUT>(w, f.n_patch, f.n_r, f.lmax, f.n_lm, f.A, f.coef, f.Q, f.Q32); break;
+    case 18: scan_warp_body<18, F64OUT>(w, f.n_patch, f.n_r, f.lmax, f.n_lm, f.A, f.coef, f.Q, f.Q32); break;
+    default: scan_warp_body<24, F64OUT>(w, f.n_patch, f.n_r, f.lmax, f.n_lm, f.A, f.coef, f.Q, f.Q32); break;
+  }
+}
+
 }  // namespace
+
+bool scan_group_field(yy_grid *g, bool want_f32, ScanGroupField *f) {
+  if (g->n_r > 32 * 24) return false;
+  f->n_patch = g->n_patch;
+  f->n_r = g->n_r;
+  f->lmax = g->lmax;
+  f->n_lm = g->n_lm;
+  f->ch = g->n_r <= 32 * 8 ? 8 : g->n_r <= 32 * 12 ? 12 : g->n_r <= 32 * 18 ? 18 : 24;
+  f->A = moments_total(g);
+  f->coef = g->scan;
+  f->Q = g->Q;
+  f->Q32 = want_f32 ? g->Q32 : nullptr;
+  return true;
+}
+
+int scan_group_blocks(const ScanGroupField &f) { return (f.n_patch * f.n_lm + 3) / 4; }
+
+cudaError_t scan_group_launch(const ScanGroupField *fields, const uint32_t *block_map, int blocks, bool f64_out,
+                              cudaStream_t st) {
+  if (f64_out)
+    k_scan_group<true><<<blocks, 128, 0, st>>>(fields, block_map);
+  else
+    k_scan_group<false><<<blocks, 128, 0, st>>>(fields, block_map);
+  return cudaGetLastError();
+}
 
 cudaError_t rotate_moments(yy_grid *g, bool fp64, cudaStream_t st) {
   if (g->n_patch == 1) return cudaSuccess;   // polar grid: the scans read A itself

@@ -512,6 +512,123 @@ __global__ void __launch_bounds__(1024, 1) k_pack_stream(PackArgs p, int *err) {
   }
 }
 
+// The streaming form over the long, even rows of many jobs: the grid walks
+// the concatenated rows (row_map[i] = job << 24 | the job's own row, padding
+// rows included), each row with its job's arguments, the next row's copy in
+// flight as above.
+template <class F>
+__global__ void __launch_bounds__(1024, 1)
+k_pack_stream_group(const PackArgs *__restrict__ jobs, const uint32_t *__restrict__ row_map, int n_rows, int *err) {
+  extern __shared__ __align__(16) double rowbuf_f64[];
+  __shared__ RowStats red[32];
+  __shared__ __align__(8) uint64_t bar;
+  typedef typename F::elem E;
+  const int tid = threadIdx.x;
+  auto issue = [&](const PackArgs &q, int r) {   // one thread
+    const double *src = (r < q.split_row) ? q.src0 + (size_t)r * q.ld : q.src1 + (size_t)(r - q.split_row) * q.ld;
+    mbar_expect_tx(&bar, (uint32_t)q.K * 8u);
+    for (int k0 = 0; k0 < q.K; k0 += kStreamChunk) {
+      const int n = min(kStreamChunk, q.K - k0);
+      bulk_load(smem_u32(rowbuf_f64 + k0), src + k0, (uint32_t)n * 8u, &bar);
+    }
+  };
+  // the job and row of global row i, and whether it carries data
+  auto at = [&](int i, int &job, int &r) {
+    const uint32_t m = row_map[i];
+    job = (int)(m >> 24);
+    r = (int)(m & 0xFFFFFFu);
+  };
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (tid == 0 && (int)blockIdx.x < n_rows) {
+    int j0, r0;
+    at((int)blockIdx.x, j0, r0);
+    if (r0 < jobs[j0].rows) issue(jobs[j0], r0);
+  }
+  uint32_t phase = 0;
+  for (int gi = blockIdx.x; gi < n_rows; gi += gridDim.x) {
+    int jb, row;
+    at(gi, jb, row);
+    const PackArgs &p = jobs[jb];
+    const int K = p.K;
+    const size_t piece_stride = (size_t)p.rows_pad * p.k_pad;
+    const bool valid = row < p.rows;
+    if (valid) {
+      const bool ok = mbar_wait(&bar, phase, err);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {   // timed out: let the copy finish (bounded), then leave
+        if (tid == 0) mbar_wait(&bar, phase ^ 1u, err);
+        return;
+      }
+    }
+    // the row in fp32 registers and its statistics (runs of 4 pairs for the dot product)
+    float x[2 * kStreamP];
+    RowStats st = {0.f, 0.f, 0.f, INFINITY, -INFINITY};
+#pragma unroll
+    for (int c0 = 0; c0 < kStreamP; c0 += 4) {
+      float run = 0.0f;
+#pragma unroll
+      for (int c = c0; c < c0 + 4; ++c) {
+        const int k = 2 * (c * 1024 + tid);
+        float v0 = 0.0f, v1 = 0.0f, d0 = 0.0f, d1 = 0.0f;
+        if (valid && k < K) {
+          const double2 t = *(const double2 *)(rowbuf_f64 + k);
+          v0 = f64_to_f32_rn(t.x);
+          v1 = f64_to_f32_rn(t.y);
+          st.mn = fminf(st.mn, fminf(v0, v1));
+          st.mx = fmaxf(st.mx, fmaxf(v0, v1));
+          if (p.dot_vec) {
+            const float2 d = *(const float2 *)(p.dot_vec + k);
+            d0 = d.x;
+            d1 = d.y;
+          }
+        }
+        x[2 * c] = v0;
+        x[2 * c + 1] = v1;
+        st.s += v0;
+        st.s += v1;
+        run = fmaf(v0, d0, run);
+        run = fmaf(v1, d1, run);
+      }
+      if (p.dot_vec) two_sum_add(st.dh, st.dl, run, 0.0f);
+    }
+    __syncthreads();   // every thread holds the row: the buffer is free
+    const int next = gi + gridDim.x;
+    if (tid == 0 && next < n_rows) {
+      int jn, rn;
+      at(next, jn, rn);
+      if (rn < jobs[jn].rows) issue(jobs[jn], rn);
+    }
+    row_stats<1024>(st, red);
+    float mean = 0.0f;
+    if (p.mean_out && valid) mean = st.s / (float)K;
+    float amax = 0.0f;
+    if (valid) amax = fmaxf(st.mx - mean, mean - st.mn);
+    float scf = 1.0f;
+    if (amax > 0.0f && isfinite(amax)) scf = ldexpf(1.0f, 14 - ilogbf(amax));
+    if (tid == 0) {
+      p.scale_out[row] = (double)(1.0f / scf);   // a power of two: exact in fp32
+      if (p.scale_out_f) p.scale_out_f[row] = 1.0f / scf;
+      if (p.mean_out) p.mean_out[row] = (double)mean;
+      if (p.dot_vec && valid) p.dot_out[row] = (double)st.dh + (double)st.dl;
+    }
+    // (x - mean) scf as one rounding: scf is a power of two
+    const float off = -mean * scf;
+    E *orow = (E *)p.out + (size_t)row * p.k_pad;
+#pragma unroll
+    for (int c = 0; c < kStreamP; ++c) {
+      const int k = 2 * (c * 1024 + tid);
+      if (k >= p.k_pad) break;
+      const bool u = valid && k < K;
+      split2<F>(u ? fmaf(x[2 * c], scf, off) : 0.0f, u ? fmaf(x[2 * c + 1], scf, off) : 0.0f, orow + k,
+                piece_stride);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // separable synthesis on the tensor cores: the polar stage
 // ---------------------------------------------------------------------------
@@ -758,16 +875,21 @@ __device__ __forceinline__ int degree_of_mode(int idx) {
 // partials exactly as k_reduce_partials forms them (written to A for the
 // group's own modes) and kept in shared memory; each thread then combines
 // one mode.  Same values as the two kernels in sequence.
-__global__ void __launch_bounds__(256)
-k_reduce_rotate(int n_r, int n_lm, int S, const float *__restrict__ part, const double *__restrict__ rs,
-                const double *__restrict__ cs, const double *__restrict__ mono, const double *__restrict__ mean,
-                const double *__restrict__ colsum, const float *__restrict__ rot, double *__restrict__ A,
-                double *__restrict__ Atot) {
+struct ReduceRotateArgs {
+  int n_r, n_lm, S;             // radii, modes, segment partials
+  const float *part;            // [S][2 n_r][n_lm]
+  const double *rs, *cs, *mono, *mean, *colsum;
+  const float *rot;             // per-degree rotation matrices
+  double *A, *Atot;
+};
+
+// Block (n, group): radius n, modes [256 group, 256 group + 256) of both patches.
+__device__ __forceinline__ void reduce_rotate_block(const ReduceRotateArgs &r, int n, int group) {
   __shared__ double ad[2 * 640];   // two rows of at most 640 modes (group of 256 plus its degrees' ends)
   __shared__ float af[2 * 640];
-  const int n = blockIdx.x;
+  const int n_r = r.n_r, n_lm = r.n_lm;
   const int M = 2 * n_r;
-  const int j0 = blockIdx.y * blockDim.x;
+  const int j0 = group * blockDim.x;
   const int j1 = min(n_lm, j0 + (int)blockDim.x);   // this group's modes [j0, j1)
   const int la = degree_of_mode(j0), lb = degree_of_mode(j1 - 1);
   const int m0 = la * la, m1 = (lb + 1) * (lb + 1), span = m1 - m0;
@@ -778,23 +900,23 @@ k_reduce_rotate(int n_r, int n_lm, int S, const float *__restrict__ part, const 
     const size_t idx = (size_t)row * n_lm + c;
     double v;
     if (c == 0) {
-      v = mono[row];
+      v = r.mono[row];
     } else {
       float sum = 0.f, comp = 0.f;
-      for (int z = 0; z < S; ++z) kahan_add(sum, comp, part[(size_t)z * zs + idx]);
+      for (int z = 0; z < r.S; ++z) kahan_add(sum, comp, r.part[(size_t)z * zs + idx]);
       const double tot = f32_to_f64(sum) + f32_to_f64(comp);
-      v = fma(tot * rs[row], cs[c], mean[row] * colsum[c]);
+      v = fma(tot * r.rs[row], r.cs[c], r.mean[row] * r.colsum[c]);
     }
     ad[p * span + (c - m0)] = v;
     af[p * span + (c - m0)] = f64_to_f32(v);
-    if (c >= j0 && c < j1) A[idx] = v;
+    if (c >= j0 && c < j1) r.A[idx] = v;
   }
   __syncthreads();
   const int j = j0 + (int)threadIdx.x;
   if (j >= j1) return;
   const int l = degree_of_mode(j);
   const int w = 2 * l + 1, jj = j - l * l;
-  const float *D = rot + (size_t)l * (4 * l * l - 1) / 3 + jj;
+  const float *D = r.rot + (size_t)l * (4 * l * l - 1) / 3 + jj;
   const float *x0 = af + (l * l - m0), *x1 = af + span + (l * l - m0);
   float s0 = 0.f, s1 = 0.f;   // into patch 0 (from patch 1) and into patch 1 (from patch 0)
 #pragma unroll 4
@@ -803,8 +925,75 @@ k_reduce_rotate(int n_r, int n_lm, int S, const float *__restrict__ part, const 
     s0 = fmaf(d, x1[i], s0);
     s1 = fmaf(d, x0[i], s1);
   }
-  Atot[(size_t)n * n_lm + j] = ad[j - m0] + f32_to_f64(s0);
-  Atot[((size_t)n_r + n) * n_lm + j] = ad[span + (j - m0)] + f32_to_f64(s1);
+  r.Atot[(size_t)n * n_lm + j] = ad[j - m0] + f32_to_f64(s0);
+  r.Atot[((size_t)n_r + n) * n_lm + j] = ad[span + (j - m0)] + f32_to_f64(s1);
+}
+
+__global__ void __launch_bounds__(256) k_reduce_rotate(ReduceRotateArgs r) {
+  reduce_rotate_block(r, (int)blockIdx.x, (int)blockIdx.y);
+}
+
+
+// Grouped packing: the rows of many jobs in one launch, each row as
+// k_pack_reg<F, TPR, P> packs it.  Block b packs rows of job block_map[b] >> 24
+// (its block block_map[b] & 0xFFFFFF, TPB / TPR rows per block), and
+// pclass[j] picks the job's register form: P = 4, 8, 12 for TPR = 1024 (rows up to
+// 8192, 16384, 24576 values), P = 4, 6, 12, 32 for TPR = 32 (up to 256, 384,
+// 768, 2048).
+template <class F, int TPR, int P>
+__device__ __forceinline__ void pack_group_row(const PackArgs &p, int row, RowStats *red) {
+  const int tid = threadIdx.x % TPR;
+  const bool valid = row < p.rows && row != p.zero_row;
+  const double *src = nullptr;
+  if (valid) src = (row < p.split_row) ? p.src0 + (size_t)row * p.ld : p.src1 + (size_t)(row - p.split_row) * p.ld;
+  const bool vec = ((uintptr_t)src & 15u) == 0;
+  float x[2 * P];
+  RowStats st;
+  pack_load<TPR, P>(p, row, src, valid, vec, tid, x, st);
+  pack_store<F, TPR, P>(p, row, src, valid, tid, x, st, red);
+}
+
+template <class F, int TPR>
+__global__ void __launch_bounds__(TPR > 256 ? TPR : 256, 1)
+k_pack_group(const PackArgs *__restrict__ jobs, const uint32_t *__restrict__ block_map,
+             const unsigned char *__restrict__ pclass) {
+  constexpr int TPB = TPR > 256 ? TPR : 256;
+  __shared__ RowStats red[32];
+  const uint32_t m = block_map[blockIdx.x];   // job << 24 | the job's own block
+  const int j = (int)(m >> 24);
+  const PackArgs &p = jobs[j];
+  const int row = (int)(m & 0xFFFFFFu) * (TPB / TPR) + (int)threadIdx.x / TPR;
+  if (row >= p.rows_pad) return;   // whole rows (and, for TPR > 32, whole blocks) leave together
+  if constexpr (TPR > 32) {
+    switch (pclass[j]) {
+      case 0: pack_group_row<F, TPR, 4>(p, row, red); break;
+      case 1: pack_group_row<F, TPR, 8>(p, row, red); break;
+      default: pack_group_row<F, TPR, 12>(p, row, red); break;
+    }
+  } else {
+    switch (pclass[j]) {
+      case 0: pack_group_row<F, TPR, 4>(p, row, red); break;
+      case 1: pack_group_row<F, TPR, 6>(p, row, red); break;
+      case 2: pack_group_row<F, TPR, 12>(p, row, red); break;
+      default: pack_group_row<F, TPR, 32>(p, row, red); break;
+    }
+  }
+}
+
+// The register form of a job for k_pack_group (-1: the row is too long).
+static int pack_class(int tpr, int k_pad) {
+  if (tpr > 32) return k_pad <= 1024 * 8 ? 0 : k_pad <= 1024 * 16 ? 1 : k_pad <= 1024 * 24 ? 2 : -1;
+  return k_pad <= 32 * 8 ? 0 : k_pad <= 32 * 12 ? 1 : k_pad <= 32 * 24 ? 2 : k_pad <= 32 * 64 ? 3 : -1;
+}
+
+// All fields of a group: block_map[b] = field << 24 | the field's own block
+// (n_r x ceil(n_lm / 256) of them).
+__global__ void __launch_bounds__(256) k_reduce_rotate_group(const ReduceRotateArgs *__restrict__ fields,
+                                                             const uint32_t *__restrict__ block_map) {
+  const uint32_t m = block_map[blockIdx.x];
+  const ReduceRotateArgs &r = fields[m >> 24];
+  const int b = (int)(m & 0xFFFFFFu);
+  reduce_rotate_block(r, b % r.n_r, b / r.n_r);
 }
 
 // colsum[row] = sum_k table[row][k] (float64, fixed order); b0[k] = fp32(table[0][k])
@@ -1352,11 +1541,11 @@ void tc_free(yy_grid *g) {
   }
 }
 
+// The density packing and the contraction of the dense analysis.
 template <class F>
-static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, const double *rg, cudaStream_t s) {
+static void analysis_args(yy_grid *g, yy_tc_tables *t, const double *ry, const double *rg, PackArgs &p, PairArgs &a) {
   const int M = grid_rows(g);
-  PackBatch b = {};
-  PackArgs &p = b.job[0];
+  p = PackArgs{};
   p.rows = M;
   p.rows_pad = t->rows_pad;
   p.K = g->n_ang;
@@ -1372,10 +1561,7 @@ static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, 
   p.mean_out = t->an_mean;      // the tensor cores see rho - (row mean)
   p.scale_out = t->an_rhos;
   p.out = t->an_rho;
-  cudaError_t e = launch_pack_long<F>(b, g->err, s);
-  note_launch(g, "k_pack_stream", s);
-  if (e != cudaSuccess) return e;
-  PairArgs a = {};
+  a = PairArgs{};
   a.stages = t->stages;
   a.cells = g->n_lm;
   a.cell_tiles = t->an_modes_pad / (2 * kPairRows);
@@ -1395,16 +1581,46 @@ static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, 
   a.part_ld = g->n_lm;
   a.n_jobs = 1;
   a.err = g->err;
+}
+
+// The split-K sum and the combination of the patches (Yin-Yang grids up to
+// l_max kReduceRotateLmax).
+static void reduce_rotate_args(yy_grid *g, yy_tc_tables *t, ReduceRotateArgs &r) {
+  r = ReduceRotateArgs{};
+  r.n_r = g->n_r;
+  r.n_lm = g->n_lm;
+  r.S = t->an_segs;
+  r.part = t->part;
+  r.rs = t->an_rhos;
+  r.cs = t->an_tabs;
+  r.mono = t->an_mono;
+  r.mean = t->an_mean;
+  r.colsum = t->an_colsum;
+  r.rot = g->rot32;
+  r.A = g->A;
+  r.Atot = g->Atot;
+}
+
+template <class F>
+static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, const double *rg, cudaStream_t s) {
+  PackBatch b = {};
+  PairArgs a;
+  analysis_args<F>(g, t, ry, rg, b.job[0], a);
+  cudaError_t e = launch_pack_long<F>(b, g->err, s);
+  note_launch(g, "k_pack_stream", s);
+  if (e != cudaSuccess) return e;
   if ((e = launch_pair<F>(g, t, t->an_maps, a, s)) != cudaSuccess) return e;
   if (g->n_patch == 2 && g->lmax <= kReduceRotateLmax) {
     // the split-K sum and the combination of the patches in one launch
+    ReduceRotateArgs r;
+    reduce_rotate_args(g, t, r);
     const dim3 grid((unsigned)g->n_r, (unsigned)((g->n_lm + 255) / 256));
-    k_reduce_rotate<<<grid, 256, 0, s>>>(g->n_r, g->n_lm, t->an_segs, t->part, t->an_rhos, t->an_tabs, t->an_mono,
-                                         t->an_mean, t->an_colsum, g->rot32, g->A, g->Atot);
+    k_reduce_rotate<<<grid, 256, 0, s>>>(r);
     note_launch(g, "k_reduce_rotate", s);
     g->atot_done = 1;
     return cudaGetLastError();
   }
+  const int M = grid_rows(g);
   const size_t cnt = (size_t)M * g->n_lm;
   k_reduce_partials<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(M, g->n_lm, t->an_segs, t->part, t->an_rhos,
                                                                   t->an_tabs, t->an_mono, t->an_mean, t->an_colsum,
@@ -1413,15 +1629,15 @@ static cudaError_t analysis_form(yy_grid *g, yy_tc_tables *t, const double *ry, 
   return cudaGetLastError();
 }
 
-template <class F>
-static cudaError_t pack_coefficients_form(yy_grid *g, yy_tc_tables *t, cudaStream_t s) {
+// The three coefficient sets' packing (Phi and g_r: the monopole, column 0,
+// is added in the epilogue).
+static void coefficient_args(yy_grid *g, yy_tc_tables *t, PackArgs (&jobs)[3]) {
   const int M = grid_rows(g);
   const size_t qsz = (size_t)M * g->n_lm;
-  // Phi and g_r: the monopole (column 0) is added in the epilogue
   const double add[3] = {kY00, kY00, 0.0};
-  PackBatch b = {};
   for (int c = 0; c < 3; ++c) {
-    PackArgs &p = b.job[c];
+    PackArgs &p = jobs[c];
+    p = PackArgs{};
     p.rows = M;
     p.rows_pad = t->rows_pad;
     p.K = g->n_lm;
@@ -1438,14 +1654,19 @@ static cudaError_t pack_coefficients_form(yy_grid *g, yy_tc_tables *t, cudaStrea
     p.scale_out_f = t->sy_qsf[c];
     p.out = t->sy_q[c];
   }
+}
+
+template <class F>
+static cudaError_t pack_coefficients_form(yy_grid *g, yy_tc_tables *t, cudaStream_t s) {
+  PackBatch b = {};
+  coefficient_args(g, t, b.job);
   cudaError_t e = launch_pack<F>(b, 3, s);
   note_launch(g, "k_pack_reg/coefficients", s);
   return e;
 }
 
 template <class F>
-static cudaError_t synthesis_form(yy_grid *g, yy_tc_tables *t, double *py, double *pg, double *gy, double *gg,
-                                  cudaStream_t s) {
+static void synthesis_args(yy_grid *g, yy_tc_tables *t, double *py, double *pg, double *gy, double *gg, PairArgs &a) {
   const size_t comp = (size_t)g->n_r * g->n_ang;
   // (coefficient set, table, outputs): Phi = Q.Y, g_r = Q_r.Y, g_theta = Q_t.Y_t, g_phi = Q_t.Y_p
   const struct {
@@ -1455,7 +1676,7 @@ static cudaError_t synthesis_form(yy_grid *g, yy_tc_tables *t, double *py, doubl
                {1, 0, gy, gg},
                {2, 1, gy ? gy + comp : nullptr, gg ? gg + comp : nullptr},
                {2, 2, gy ? gy + 2 * comp : nullptr, gg ? gg + 2 * comp : nullptr}};
-  PairArgs a = {};
+  a = PairArgs{};
   a.stages = t->stages;
   a.cells = g->n_ang;
   a.cell_tiles = t->sy_cells_pad / (2 * kPairRows);
@@ -1482,6 +1703,13 @@ static cudaError_t synthesis_form(yy_grid *g, yy_tc_tables *t, double *py, doubl
     J.ta = jobs[j].tab;
     J.tb = jobs[j].q;
   }
+}
+
+template <class F>
+static cudaError_t synthesis_form(yy_grid *g, yy_tc_tables *t, double *py, double *pg, double *gy, double *gg,
+                                  cudaStream_t s) {
+  PairArgs a;
+  synthesis_args<F>(g, t, py, pg, gy, gg, a);
   return launch_pair<F>(g, t, t->sy_maps, a, s);
 }
 
@@ -2375,6 +2603,282 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
   e = o->bias ? cudaLaunchKernelEx(&cfg, k_tc_pair<F, 4>, o->maps, a) : cudaLaunchKernelEx(&cfg, k_tc_pair<F, 3>, o->maps, a);
   note_launch(g, "k_tc_pair<FormOzaki,3>/synthesis", s);
   return e;
+}
+
+// ---------------------------------------------------------------------------
+// grouped solves: one launch per stage over many fields (batched workload)
+// ---------------------------------------------------------------------------
+//
+// Every field solved densely in a tensor-core form: the density packing, the
+// analysis contraction, the split-K sum with the patches' combination, the
+// radial scans, the coefficient packing and the synthesis, each one launch
+// over all fields.  The per-field arguments are those of the field's own
+// solve (the same tiles, K segments, fills and arithmetic, so the results are
+// the same bit for bit); they live in one device buffer built here, with the
+// fields' tensor maps for the grouped contractions.
+
+struct TcGroup {
+  yy_precision prec;
+  int n;
+  void *dev;                          // every table below
+  // density rows: long and even (streamed), other long ones (1024 threads a row), short ones (a warp a row)
+  PackArgs *st_jobs, *rho_jobs, *rs_jobs, *cf_jobs;
+  uint32_t *st_map;                                        // per row: job << 24 | the job's own row
+  uint32_t *rho_map, *rs_map, *cf_map, *rr_map, *sc_map;   // per block: job << 24 | the job's own block
+  int st_rows, st_grid, st_smem;
+  unsigned char *rho_class, *rs_class, *cf_class;
+  PairArgs *an_args, *sy_args;
+  PairMaps *an_maps, *sy_maps;
+  ReduceRotateArgs *rr;
+  ScanGroupField *sc;
+  int rho_nblocks, rs_nblocks, cf_nblocks, rr_nblocks, sc_nblocks;
+  PairArgs an_top, sy_top;            // kernel arguments of the grouped contractions
+  int an_pairs, sy_pairs, an_smem, sy_smem;
+};
+
+// blocks of job j, appended to a block map
+static void map_blocks(std::vector<uint32_t> &map, int j, int blocks) {
+  for (int b = 0; b < blocks; ++b) map.push_back((uint32_t)j << 24 | (uint32_t)b);
+}
+
+template <class F>
+static yy_status group_build(yy_grid *const *grids, int n, yy_precision prec, const double *const *ry,
+                             const double *const *rg, double *const *py, double *const *pg, double *const *gy,
+                             double *const *gg, TcGroup *G) {
+  if (n > 85) return YY_ERR_NOT_SUPPORTED;   // three coefficient jobs a field within the maps' 8 job bits
+  std::vector<PackArgs> stj, rho, rs, cf(3 * (size_t)n);
+  std::vector<uint32_t> st_m, rho_m, rs_m, cf_m, rr_m, sc_m;
+  int st_kmax = 0;
+  std::vector<unsigned char> rho_c, rs_c, cf_c(3 * (size_t)n);
+  std::vector<PairArgs> an(n), sy(n);
+  std::vector<PairMaps> anm(n), sym(n);
+  std::vector<ReduceRotateArgs> rr(n);
+  std::vector<ScanGroupField> sc(n);
+  int bn_max = 16, an_tiles = 0, sy_tiles = 0;
+  for (int i = 0; i < n; ++i) {
+    yy_grid *g = grids[i];
+    yy_tc_tables *t = g->tc[prec];
+    if (!t || g->n_patch != 2 || g->lmax > kReduceRotateLmax) return YY_ERR_NOT_SUPPORTED;
+    if ((gy == nullptr) != (gg == nullptr)) return YY_ERR_INVALID_ARG;
+    PackArgs pr;
+    analysis_args<F>(g, t, ry[i], rg[i], pr, an[i]);
+    reduce_rotate_args(g, t, rr[i]);
+    if (!scan_group_field(g, false, &sc[i])) return YY_ERR_NOT_SUPPORTED;
+    PackArgs c3[3];
+    coefficient_args(g, t, c3);
+    synthesis_args<F>(g, t, py[i], pg[i], gy ? gy[i] : nullptr, gg ? gg[i] : nullptr, sy[i]);
+    // the density rows in the form the field's own solve packs them in:
+    // short rows a warp each, long ones a 1024-thread block each
+    const bool short_rows = pr.K <= 32 * 64;
+    const int rc = pack_class(short_rows ? 32 : 1024, pr.k_pad);
+    const int cc = pack_class(32, c3[0].k_pad);
+    if (rc < 0 || cc < 0) return YY_ERR_NOT_SUPPORTED;
+    const bool stream = !short_rows && ((uintptr_t)pr.src0 % 16) == 0 && ((uintptr_t)pr.src1 % 16) == 0 &&
+                        (pr.ld % 2) == 0 && (pr.K % 2) == 0 && pr.K <= kStreamMaxK && pr.k_pad <= kStreamMaxK &&
+                        (pr.dot_vec == nullptr || (uintptr_t)pr.dot_vec % 8 == 0);
+    if (short_rows) {
+      map_blocks(rs_m, (int)rs.size(), (pr.rows_pad + 7) / 8);        // eight rows per 256-thread block
+      rs.push_back(pr);
+      rs_c.push_back((unsigned char)rc);
+    } else if (stream) {
+      map_blocks(st_m, (int)stj.size(), pr.rows_pad);                 // the rows themselves
+      stj.push_back(pr);
+      st_kmax = std::max(st_kmax, pr.K);
+    } else {
+      map_blocks(rho_m, (int)rho.size(), pr.rows_pad);                // one 1024-thread block per row
+      rho.push_back(pr);
+      rho_c.push_back((unsigned char)rc);
+    }
+    for (int c = 0; c < 3; ++c) {
+      const int k = 3 * i + c;
+      cf[k] = c3[c];
+      cf_c[k] = (unsigned char)cc;
+      map_blocks(cf_m, k, (c3[c].rows_pad + 7) / 8);
+    }
+    map_blocks(rr_m, i, g->n_r * ((g->n_lm + 255) / 256));
+    map_blocks(sc_m, i, scan_group_blocks(sc[i]));
+    anm[i] = t->an_maps;
+    sym[i] = t->sy_maps;
+    bn_max = std::max(bn_max, t->bn);
+    an_tiles += an[i].cell_tiles * an[i].row_tiles * an[i].k_splits * an[i].n_jobs;
+    sy_tiles += sy[i].cell_tiles * sy[i].row_tiles * sy[i].k_splits * sy[i].n_jobs;
+  }
+  // one device buffer, each table on a 128-byte boundary (tensor maps want 64)
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 127) / 128 * 128;
+    return o;
+  };
+  const int n_rho = (int)rho.size(), n_rs = (int)rs.size(), n_st = (int)stj.size();
+  const size_t o_anm = take(sizeof(PairMaps) * n), o_sym = take(sizeof(PairMaps) * n);
+  const size_t o_an = take(sizeof(PairArgs) * n), o_sy = take(sizeof(PairArgs) * n);
+  const size_t o_rho = take(sizeof(PackArgs) * n_rho), o_rs = take(sizeof(PackArgs) * n_rs);
+  const size_t o_st = take(sizeof(PackArgs) * n_st), o_stm = take(4 * st_m.size());
+  const size_t o_cf = take(sizeof(PackArgs) * 3 * n);
+  const size_t o_rr = take(sizeof(ReduceRotateArgs) * n), o_sc = take(sizeof(ScanGroupField) * n);
+  const size_t o_rhom = take(4 * rho_m.size()), o_rsm = take(4 * rs_m.size()), o_cfm = take(4 * cf_m.size());
+  const size_t o_rrm = take(4 * rr_m.size()), o_scm = take(4 * sc_m.size());
+  const size_t o_rhoc = take(n_rho), o_rsc = take(n_rs), o_cfc = take(3 * (size_t)n);
+  std::vector<unsigned char> host(off, 0);
+  auto put = [&](size_t o, const void *src, size_t bytes) {
+    if (bytes > 0) memcpy(host.data() + o, src, bytes);
+  };
+  put(o_anm, anm.data(), sizeof(PairMaps) * n);
+  put(o_sym, sym.data(), sizeof(PairMaps) * n);
+  put(o_an, an.data(), sizeof(PairArgs) * n);
+  put(o_sy, sy.data(), sizeof(PairArgs) * n);
+  put(o_rho, rho.data(), sizeof(PackArgs) * n_rho);
+  put(o_rs, rs.data(), sizeof(PackArgs) * n_rs);
+  put(o_st, stj.data(), sizeof(PackArgs) * n_st);
+  put(o_stm, st_m.data(), 4 * st_m.size());
+  put(o_cf, cf.data(), sizeof(PackArgs) * 3 * n);
+  put(o_rr, rr.data(), sizeof(ReduceRotateArgs) * n);
+  put(o_sc, sc.data(), sizeof(ScanGroupField) * n);
+  put(o_rhom, rho_m.data(), 4 * rho_m.size());
+  put(o_rsm, rs_m.data(), 4 * rs_m.size());
+  put(o_cfm, cf_m.data(), 4 * cf_m.size());
+  put(o_rrm, rr_m.data(), 4 * rr_m.size());
+  put(o_scm, sc_m.data(), 4 * sc_m.size());
+  put(o_rhoc, rho_c.data(), n_rho);
+  put(o_rsc, rs_c.data(), n_rs);
+  put(o_cfc, cf_c.data(), 3 * (size_t)n);
+  uint8_t *d = nullptr;
+  cudaError_t e = dmalloc((void **)&d, off);
+  if (e == cudaSuccess) e = cudaMemcpy(d, host.data(), off, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (d) cudaFree(d);
+    return e == cudaErrorMemoryAllocation ? YY_ERR_OOM : YY_ERR_CUDA;
+  }
+  G->prec = prec;
+  G->n = n;
+  G->dev = d;
+  G->an_maps = (PairMaps *)(d + o_anm);
+  G->sy_maps = (PairMaps *)(d + o_sym);
+  G->an_args = (PairArgs *)(d + o_an);
+  G->sy_args = (PairArgs *)(d + o_sy);
+  G->rho_jobs = (PackArgs *)(d + o_rho);
+  G->rs_jobs = (PackArgs *)(d + o_rs);
+  G->st_jobs = (PackArgs *)(d + o_st);
+  G->st_map = (uint32_t *)(d + o_stm);
+  G->st_rows = (int)st_m.size();
+  G->st_smem = st_kmax * (int)sizeof(double);
+  {
+    int dev = 0, n_sm = 1;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm < 1) n_sm = 1;
+    G->st_grid = std::min(G->st_rows, n_sm);
+  }
+  if (G->st_rows > 0 && cudaFuncSetAttribute(k_pack_stream_group<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              kStreamMaxK * (int)sizeof(double)) != cudaSuccess)
+    return YY_ERR_NOT_SUPPORTED;
+  G->cf_jobs = (PackArgs *)(d + o_cf);
+  G->rr = (ReduceRotateArgs *)(d + o_rr);
+  G->sc = (ScanGroupField *)(d + o_sc);
+  G->rho_map = (uint32_t *)(d + o_rhom);
+  G->rs_map = (uint32_t *)(d + o_rsm);
+  G->cf_map = (uint32_t *)(d + o_cfm);
+  G->rr_map = (uint32_t *)(d + o_rrm);
+  G->sc_map = (uint32_t *)(d + o_scm);
+  G->rho_class = d + o_rhoc;
+  G->rs_class = d + o_rsc;
+  G->cf_class = d + o_cfc;
+  G->rho_nblocks = (int)rho_m.size();
+  G->rs_nblocks = (int)rs_m.size();
+  G->cf_nblocks = (int)cf_m.size();
+  G->rr_nblocks = (int)rr_m.size();
+  G->sc_nblocks = (int)sc_m.size();
+  // the grouped contractions: shared-memory stages for the largest field's bn
+  const int stages = pair_stages<F>(bn_max);
+  const int smem = stages * pair_stage_bytes<F>(bn_max) + kSmemFixed;
+  for (int m = 0; m < 2; ++m) {
+    PairArgs &top = m == 0 ? G->an_top : G->sy_top;
+    top = PairArgs{};
+    top.stages = stages;
+    top.bn = bn_max;
+    top.out_mode = m;
+    top.err = grids[0]->err;
+    top.group = m == 0 ? G->an_args : G->sy_args;
+    top.group_maps = m == 0 ? G->an_maps : G->sy_maps;
+    top.n_group = n;
+  }
+  G->an_smem = G->sy_smem = smem;
+  int slots = 0;
+  {
+    if (cudaFuncSetAttribute(k_tc_pair<F, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_tc_pair<F, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) !=
+            cudaSuccess)
+      return YY_ERR_NOT_SUPPORTED;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = pair_config(64, smem, 0, attr);
+    if (cudaOccupancyMaxActiveClusters(&slots, (void *)k_tc_pair<F, 1, true>, &cfg) != cudaSuccess || slots < 1) {
+      cudaGetLastError();
+      return YY_ERR_NOT_SUPPORTED;
+    }
+  }
+  G->an_pairs = std::min(an_tiles, slots);
+  G->sy_pairs = std::min(sy_tiles, slots);
+  return YY_OK;
+}
+
+template <class F>
+static cudaError_t group_run(const TcGroup *G, cudaStream_t s) {
+  const PairMaps none = {};   // the grouped contractions read each field's maps from G
+  if (G->st_rows > 0)
+    k_pack_stream_group<F><<<G->st_grid, 1024, G->st_smem, s>>>(G->st_jobs, G->st_map, G->st_rows, G->n > 0 ? G->an_top.err : nullptr);
+  if (G->rho_nblocks > 0) k_pack_group<F, 1024><<<G->rho_nblocks, 1024, 0, s>>>(G->rho_jobs, G->rho_map, G->rho_class);
+  if (G->rs_nblocks > 0) k_pack_group<F, 32><<<G->rs_nblocks, 256, 0, s>>>(G->rs_jobs, G->rs_map, G->rs_class);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = pair_config(G->an_pairs, G->an_smem, s, attr);
+  if ((e = cudaLaunchKernelEx(&cfg, k_tc_pair<F, 0, true>, none, G->an_top)) != cudaSuccess) return e;
+  k_reduce_rotate_group<<<G->rr_nblocks, 256, 0, s>>>(G->rr, G->rr_map);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = scan_group_launch(G->sc, G->sc_map, G->sc_nblocks, true, s)) != cudaSuccess) return e;
+  k_pack_group<F, 32><<<G->cf_nblocks, 256, 0, s>>>(G->cf_jobs, G->cf_map, G->cf_class);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  cfg = pair_config(G->sy_pairs, G->sy_smem, s, attr);
+  return cudaLaunchKernelEx(&cfg, k_tc_pair<F, 1, true>, none, G->sy_top);
+}
+
+yy_status tc_group_create(yy_grid *const *grids, int n, yy_precision prec, const double *const *ry,
+                          const double *const *rg, double *const *py, double *const *pg, double *const *gy,
+                          double *const *gg, TcGroup **out) {
+  if (!grids || n < 1 || !out) return YY_ERR_INVALID_ARG;
+  TcGroup *G = new (std::nothrow) TcGroup();
+  if (!G) return YY_ERR_OOM;
+  yy_status st;
+  switch (prec) {
+    case YY_FP16X2: st = group_build<FormFP16x2>(grids, n, prec, ry, rg, py, pg, gy, gg, G); break;
+    case YY_BF16X3: st = group_build<FormBF16x3>(grids, n, prec, ry, rg, py, pg, gy, gg, G); break;
+    case YY_TF32: st = group_build<FormTF32>(grids, n, prec, ry, rg, py, pg, gy, gg, G); break;
+    default: st = YY_ERR_NOT_SUPPORTED;
+  }
+  if (st != YY_OK) {
+    tc_group_destroy(G);
+    return st;
+  }
+  *out = G;
+  return YY_OK;
+}
+
+cudaError_t tc_group_run(const TcGroup *G, cudaStream_t s) {
+  switch (G->prec) {
+    case YY_FP16X2: return group_run<FormFP16x2>(G, s);
+    case YY_BF16X3: return group_run<FormBF16x3>(G, s);
+    case YY_TF32: return group_run<FormTF32>(G, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int tc_group_launches(const TcGroup *G) { return 5 + (G->st_rows > 0) + (G->rho_nblocks > 0) + (G->rs_nblocks > 0); }
+
+void tc_group_destroy(TcGroup *G) {
+  if (!G) return;
+  if (G->dev) cudaFree(G->dev);
+  delete G;
 }
 
 }  // namespace yy

@@ -414,6 +414,12 @@ struct PairArgs {
   int n_jobs;
   PairJob job[4];
   int *err;
+  // grouped launch (k_tc_pair<F, MODE, true>): the fields' own arguments and
+  // tensor maps in global memory; this struct then gives only the stage count,
+  // the largest field's bn (the shared-memory layout) and the error word
+  const struct PairArgs *group;
+  const struct PairMaps *group_maps;
+  int n_group;
 };
 
 struct PairMaps {
@@ -457,9 +463,28 @@ struct TileFills {
   }
 };
 
-template <class F, int OUT_MODE>
+// The tiles of one launch in order: field by field (one field unless the
+// launch is grouped), each field's tiles as its own launch would order them.
+// Pair p takes the tiles p, p + #pairs, ... of the whole sequence: from
+// (field f, its tile t) this moves on to the next such tile, crossing into
+// later fields; false past the last field.  base: tiles of the fields before f.
+template <bool GROUPED>
+__device__ __forceinline__ bool pair_tile_next(const PairArgs &a0, int pair, int n_pairs, int &f, int &base, int &t) {
+  const int nf = GROUPED ? a0.n_group : 1;
+  while (f < nf) {
+    const PairArgs &a = GROUPED ? a0.group[f] : a0;
+    const int total = a.cell_tiles * a.row_tiles * a.k_splits * a.n_jobs;
+    if (t < total) return true;
+    base += total;
+    ++f;
+    t = ((pair - base) % n_pairs + n_pairs) % n_pairs;
+  }
+  return false;
+}
+
+template <class F, int OUT_MODE, bool GROUPED = false>
 __global__ void __launch_bounds__(kThreads, 1)
-k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArgs a) {
+k_tc_pair(const __grid_constant__ PairMaps maps0, const __grid_constant__ PairArgs a0) {
   constexpr int A_SLOT = kPairRows * kRowBytes;
   constexpr int KSTEP_BYTES = 32;
   constexpr int KSTEPS = kRowBytes / KSTEP_BYTES;
@@ -467,9 +492,9 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int S = a.stages;
-  const int bh = a.bn >> 1;
-  const int B_SLOT = bh * kRowBytes;                 // a multiple of 512 bytes (bh % 8 == 0)
+  const int S = a0.stages;
+  // B slots sized for a0.bn (grouped: the largest field's); a field's tiles fill their first bn / 2 rows
+  const int B_SLOT = (a0.bn >> 1) * kRowBytes;       // a multiple of 512 bytes (bn / 2 % 8 == 0)
   const int STAGE = F::kPA * A_SLOT + F::kPB * B_SLOT;
   uint64_t *full = (uint64_t *)(smem + S * STAGE);
   uint64_t *empty = full + S;
@@ -480,10 +505,6 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rank = (int)cluster_rank();
   const int pair = (int)blockIdx.x >> 1, n_pairs = (int)gridDim.x >> 1;
-  const int per_job = a.cell_tiles * a.row_tiles * a.k_splits;
-  const int total = per_job * a.n_jobs;
-  // K blocks per accumulator fill (modes 0 and 3 add the fills in the epilogue)
-  const int chunk = ((OUT_MODE == 0 || OUT_MODE == 3) && a.kb_chunk > 0) ? a.kb_chunk : a.kb_total;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -507,11 +528,16 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
 
   if (warp == 0) {
     if (lane == 0) {
-      const uint32_t tx_bytes = 2u * (uint32_t)(F::kPA * kPairRows + F::kPB * bh) * kRowBytes;
       int gk = 0, s = 0;
       uint32_t ph = 0;   // phase of stage s in the ring (gk / S) & 1
       bool ok = true;
-      for (int t = pair; t < total && ok; t += n_pairs) {
+      for (int f_ = 0, base_ = 0, t = pair; ok && pair_tile_next<GROUPED>(a0, pair, n_pairs, f_, base_, t);
+           t += n_pairs) {
+        const PairArgs &a = GROUPED ? a0.group[f_] : a0;
+        const PairMaps &maps = GROUPED ? a0.group_maps[f_] : maps0;
+        const int per_job = a.cell_tiles * a.row_tiles * a.k_splits;
+        const int bh = a.bn >> 1;
+        const uint32_t tx_bytes = 2u * (uint32_t)(F::kPA * kPairRows + F::kPB * bh) * kRowBytes;
         const int jb = t / per_job, tl = t % per_job;
         const int rt = tl % a.row_tiles, ct = (tl / a.row_tiles) % a.cell_tiles;
         const TileFills tf(a, tl / (a.row_tiles * a.cell_tiles));
@@ -520,6 +546,13 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
         const int brow = rt * a.bn + rank * bh;
         const CUtensorMap *tmA = &maps.a[a.job[jb].ta];
         const CUtensorMap *tmB = &maps.b[a.job[jb].tb];
+        if constexpr (GROUPED) {
+          // the field's tensor maps live in device memory (written before the launch)
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmA) : "memory");
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmB) : "memory");
+          asm volatile("prefetch.tensormap [%0];" ::"l"(tmA) : "memory");
+          asm volatile("prefetch.tensormap [%0];" ::"l"(tmB) : "memory");
+        }
         for (int i = 0; i < nkb; ++i, ++gk) {
           if (gk >= S && !mbar_wait(&empty[s], ph ^ 1, a.err)) {
             ok = false;
@@ -543,15 +576,20 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
       // the last uses of every stage must be complete before this CTA leaves
       if (ok)
         for (int i = max(0, gk - S); i < gk; ++i)
-          if (!mbar_wait(&empty[i % S], (i / S) & 1, a.err)) break;
+          if (!mbar_wait(&empty[i % S], (i / S) & 1, a0.err)) break;
     }
   } else if (warp == 1) {
     if (rank == 0 && lane == 0) {
-      const uint32_t idesc = instr_desc_pair<F>(a.bn);
       int gk = 0, it = 0, s = 0;
       uint32_t ph = 0;
       bool ok = true;
-      for (int t = pair; t < total && ok; t += n_pairs) {
+      for (int f_ = 0, base_ = 0, t = pair; ok && pair_tile_next<GROUPED>(a0, pair, n_pairs, f_, base_, t);
+           t += n_pairs) {
+        const PairArgs &a = GROUPED ? a0.group[f_] : a0;
+        const int per_job = a.cell_tiles * a.row_tiles * a.k_splits;
+        // K blocks per accumulator fill (modes 0 and 3 add the fills in the epilogue)
+        const int chunk = ((OUT_MODE == 0 || OUT_MODE == 3) && a.kb_chunk > 0) ? a.kb_chunk : a.kb_total;
+        const uint32_t idesc = instr_desc_pair<F>(a.bn);
         const int tl = t % per_job;
         TileFills tf(a, tl / (a.row_tiles * a.cell_tiles));
         const int nkb = tf.nkb;
@@ -605,7 +643,6 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
     const int quarter = warp & 3;
     const int sub = (warp - 2) >> 2;    // 0 .. kEpiPerQuarter - 1 within the lane quarter
     const uint32_t tempty_even = mapa_rank(smem_u32(&tempty[0]), 0);
-    const int n_chunks = a.bn / kEpiCols;
     constexpr bool scaled = OUT_MODE == 1;
     int it = 0;
     if constexpr (OUT_MODE == 0) {
@@ -617,7 +654,12 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
       // are added in the same order whatever the split.  This warp owns 16-column chunks sub,
       // sub + kEpiPerQuarter, ... (at most kMaxOwn of them).
       constexpr int kMaxOwn = 256 / kEpiCols / kEpiPerQuarter;
-      for (int t = pair; t < total; t += n_pairs) {
+      for (int f_ = 0, base_ = 0, t = pair; pair_tile_next<GROUPED>(a0, pair, n_pairs, f_, base_, t); t += n_pairs) {
+        const PairArgs &a = GROUPED ? a0.group[f_] : a0;
+        const int per_job = a.cell_tiles * a.row_tiles * a.k_splits;
+        // K blocks per accumulator fill (modes 0 and 3 add the fills in the epilogue)
+        const int chunk = ((OUT_MODE == 0 || OUT_MODE == 3) && a.kb_chunk > 0) ? a.kb_chunk : a.kb_total;
+        const int n_chunks = a.bn / kEpiCols;
         const int tl = t % per_job;
         const int rt = tl % a.row_tiles, ct = (tl / a.row_tiles) % a.cell_tiles;
         TileFills tf(a, tl / (a.row_tiles * a.cell_tiles));
@@ -656,14 +698,17 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
           // the end of a segment: its partial sums go out
           const size_t zs = (size_t)tf.seg;
           tf.advance(a, c1);
+          const int rows_v = a.rows, bn = a.bn, part_ld = a.part_ld;
+          float *const part = a.part;
+          const bool cell_ok = cell < a.cells;
 #pragma unroll
           for (int o = 0; o < kMaxOwn; ++o) {
             const int k = sub + o * kEpiPerQuarter;
-            if (k < n_chunks && cell < a.cells) {
+            if (k < n_chunks && cell_ok) {
 #pragma unroll
               for (int j = 0; j < kEpiCols; ++j) {
-                const int row = rt * a.bn + k * kEpiCols + j;
-                if (row < a.rows) a.part[(zs * a.rows + row) * a.part_ld + cell] = acc[o][j];
+                const int row = rt * bn + k * kEpiCols + j;
+                if (row < rows_v) part[(zs * rows_v + row) * part_ld + cell] = acc[o][j];
               }
             }
 #pragma unroll
@@ -678,6 +723,12 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
       // cell's row.  They go through this warp's shared-memory block, and the
       // warp then writes two cells' 16-value runs per store instruction.
       // Mode 3 forms the values from FormOzaki's level accumulators.
+      static_assert(!GROUPED, "grouped launches take output modes 0 and 1");
+      const PairArgs &a = a0;
+      const int per_job = a.cell_tiles * a.row_tiles * a.k_splits;
+      const int total = per_job * a.n_jobs;
+      const int chunk = (OUT_MODE == 3 && a.kb_chunk > 0) ? a.kb_chunk : a.kb_total;
+      const int n_chunks = a.bn / kEpiCols;
       uint8_t *wbuf = smem + S * STAGE + 512 + (size_t)(warp - 2) * kEpiWarpBytes;
       double *ebuf = reinterpret_cast<double *>(wbuf);                          // [32][kEpiPad]
       double **rowp = reinterpret_cast<double **>(wbuf + 32 * kEpiPad * 8);     // [32] output rows
@@ -834,7 +885,10 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
         if (lane == 0) mbar_arrive_cluster_relaxed(tempty_even + (uint32_t)(b * sizeof(uint64_t)));
       }
     } else
-    for (int t = pair; t < total; t += n_pairs, ++it) {
+    for (int f_ = 0, base_ = 0, t = pair; pair_tile_next<GROUPED>(a0, pair, n_pairs, f_, base_, t); t += n_pairs, ++it) {
+      const PairArgs &a = GROUPED ? a0.group[f_] : a0;
+      const int per_job = a.cell_tiles * a.row_tiles * a.k_splits;
+      const int n_chunks = a.bn / kEpiCols;
       const int b = it & 1;
       const PairJob &J = a.job[t / per_job];
       const int tl = t % per_job;
@@ -842,24 +896,29 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
       const int cell = (2 * ct + rank) * kPairRows + quarter * 32 + lane;
       const bool cell_ok = cell < a.cells;
       const float cs = (cell_ok && scaled) ? J.cell_scale[cell] : 0.0f;
+      // the tile's arguments in registers (the output stores could otherwise
+      // alias them in a grouped launch, whose arguments are in device memory)
+      const int rows_v = a.rows, out_split = a.out_split, bn = a.bn;
+      const long long ldo = a.ldo;
+      double *const out0 = J.out0, *const out1 = J.out1;
+      const float *const row_scale = J.row_scale, *const row_add = J.row_add;
       if (!mbar_wait_cluster(&tfull[b], (it >> 1) & 1, a.err)) break;
       tc_fence_after();
       const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
 #pragma unroll 1
       for (int k = sub; k < n_chunks; k += kEpiPerQuarter) {
-        const int row0 = rt * a.bn + k * kEpiCols;
+        const int row0 = rt * bn + k * kEpiCols;
         uint32_t v[16];
         tmem_ld16_async(tbase + (uint32_t)(k * kEpiCols), v);
         if constexpr (scaled) {
           float4 rs4[4], ra4[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            rs4[q] = reinterpret_cast<const float4 *>(J.row_scale + row0)[q];
-            ra4[q] = reinterpret_cast<const float4 *>(J.row_add + row0)[q];
+            rs4[q] = reinterpret_cast<const float4 *>(row_scale + row0)[q];
+            ra4[q] = reinterpret_cast<const float4 *>(row_add + row0)[q];
           }
-          const bool cross = row0 < a.out_split && row0 + kEpiCols > a.out_split;
-          double *base = (row0 < a.out_split) ? J.out0 + (size_t)row0 * a.ldo
-                                              : J.out1 + (size_t)(row0 - a.out_split) * a.ldo;
+          const bool cross = row0 < out_split && row0 + kEpiCols > out_split;
+          double *base = (row0 < out_split) ? out0 + (size_t)row0 * ldo : out1 + (size_t)(row0 - out_split) * ldo;
           tmem_wait_ld();
 #pragma unroll
           for (int j = 0; j < kEpiCols; ++j) {
@@ -867,11 +926,9 @@ k_tc_pair(const __grid_constant__ PairMaps maps, const __grid_constant__ PairArg
             const float rs = (j & 3) == 0 ? r4.x : (j & 3) == 1 ? r4.y : (j & 3) == 2 ? r4.z : r4.w;
             const float ra = (j & 3) == 0 ? a4.x : (j & 3) == 1 ? a4.y : (j & 3) == 2 ? a4.z : a4.w;
             const int row = row0 + j;
-            double *orow = base + (size_t)j * a.ldo;
-            if (cross)
-              orow = (row < a.out_split) ? J.out0 + (size_t)row * a.ldo
-                                         : J.out1 + (size_t)(row - a.out_split) * a.ldo;
-            if (row < a.rows && cell_ok) orow[cell] = f32_to_f64(fmaf(__uint_as_float(v[j]) * cs, rs, ra));
+            double *orow = base + (size_t)j * ldo;
+            if (cross) orow = (row < out_split) ? out0 + (size_t)row * ldo : out1 + (size_t)(row - out_split) * ldo;
+            if (row < rows_v && cell_ok) orow[cell] = f32_to_f64(fmaf(__uint_as_float(v[j]) * cs, rs, ra));
           }
         }
       }

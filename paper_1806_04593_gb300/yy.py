@@ -129,6 +129,10 @@ def load():
     lib.yy_batch_branches.restype = I
     lib.yy_batch_analysis_splits.argtypes = [P, I, I]
     lib.yy_batch_analysis_splits.restype = I
+    lib.yy_batch_set_grouping.argtypes = [P, I]
+    lib.yy_batch_set_grouping.restype = I
+    lib.yy_batch_groups.argtypes = [P]
+    lib.yy_batch_groups.restype = I
     lib.yy_batch_last_device_status.argtypes = [P]
     lib.yy_batch_last_device_status.restype = I
     lib.yy_batch_destroy.argtypes = [P]
@@ -362,11 +366,21 @@ class Batch:
     def branches(self):
         return load().yy_batch_branches(self.handle)
 
+    def groups(self):
+        return load().yy_batch_groups(self.handle)
+
     def grid_handle(self, field):
         return load().yy_batch_grid(self.handle, int(field))
 
     def analysis_splits(self, field, prec):
         return load().yy_batch_analysis_splits(self.handle, int(field), PRECISIONS.get(prec, prec))
+
+    def set_grouping(self, groups):
+        """Grouped solves in `groups` concurrent groups of fields (one launch per
+        stage each; tensor-core forms, dense fields), or 0 for per-field graphs."""
+        st = load().yy_batch_set_grouping(self.handle, int(groups))
+        if st != YY_OK:
+            raise YYError(st, "yy_batch_set_grouping")
 
     def device_status(self):
         return load().yy_batch_last_device_status(self.handle)

@@ -2,7 +2,9 @@
 
 Checks, per the batched workload's test plan:
   - every field of a batch equals the same field solved alone (float64,
-    bitwise: the graph runs the same kernels on the same data);
+    bitwise: the graph runs the same kernels on the same data), and the
+    grouped solves (one launch per stage over all fields, tensor-core forms)
+    equal the per-field graphs and the fields solved alone bitwise;
   - graph replay is bitwise deterministic, and new buffers are recorded anew;
   - the 64-field workload (n_r ~ U{100..600}, 2 / 1.5 / 1 degree cells,
     l_max ~ U{10..40}) in the tuned FP16X2 form agrees with the float64 GPU
@@ -79,6 +81,50 @@ def test_batch_fp64_equals_fields_solved_alone(yy):
         assert torch.equal(o[2], ref["grad_yin"]) and torch.equal(o[3], ref["grad_yang"]), sp.name
         g.close()
     b.close()
+
+
+def test_batch_grouped_equals_per_field_graphs_and_fields_alone(yy):
+    """Grouped solves (one launch per stage over every field) give, in each
+    tensor-core form, the results of the per-field graph and of each field
+    solved alone bit for bit: each field keeps its own tiles, K segments and
+    arithmetic.  The small batch has all three density row forms (rows of at
+    most 2,048 cells, longer odd and longer even rows): eight kernels."""
+    import torch
+    dev = torch.device("cuda", 0)
+    specs = _small_specs()
+    for prec in ("fp16x2", "bf16x3", "tf32"):
+        b = yy.Batch(specs)
+        b.prepare(prec)
+        b.set_grouping(1)                             # one group: every stage one launch
+        rho, grouped = _fields(specs, dev)
+        _run(b, rho, grouped, prec)
+        torch.cuda.synchronize()
+        assert b.device_status() == yy.YY_OK
+        assert b.launch_count() == 8, (prec, b.launch_count())
+        b.set_grouping(2)                             # two groups side by side: the same results
+        _, two = _fields(specs, dev)
+        _run(b, rho, two, prec)
+        torch.cuda.synchronize()
+        assert 12 <= b.launch_count() <= 16, (prec, b.launch_count())
+        for x, y in zip(grouped, two):
+            for a, c in zip(x, y):
+                assert torch.equal(a, c), prec
+        b.set_grouping(0)
+        _, per_field = _fields(specs, dev)
+        _run(b, rho, per_field, prec)
+        torch.cuda.synchronize()
+        assert b.launch_count() > 8 * len(specs) // 2
+        for sp, r, x, y in zip(specs, rho, grouped, per_field):
+            for a, c in zip(x, y):
+                assert torch.equal(a, c), (prec, sp.name)
+            g = yy.Grid.from_spec(sp)
+            g.prepare(prec)
+            alone = g.solve(r[0], r[1], gradient=True, prec=prec)
+            torch.cuda.synchronize()
+            for key, a in zip(("phi_yin", "phi_yang", "grad_yin", "grad_yang"), x):
+                assert torch.equal(a, alone[key]), (prec, sp.name, key)
+            g.close()
+        b.close()
 
 
 def test_batch_graph_replay_is_deterministic_and_rebinds(yy):
