@@ -103,6 +103,9 @@ def parse():
     ap.add_argument("--form-steps", type=int, default=20)
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-field batched workload")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--batch-profile", type=int, default=None, metavar="GROUPS",
+                    help="after the batch timing, replay its graph once inside cudaProfilerStart/Stop "
+                         "(ncu --profile-from-start off) in this form: 0 per-field graph, N >= 1 grouped")
     ap.add_argument("--ref-budget-s", type=float, default=240.0,
                     help="reference arm: full oracle solves per step while (steps + warmup) fit in this time")
     ap.add_argument("--ref-cells-div", type=int, default=0,
@@ -705,6 +708,17 @@ def run_batched(args, gradient, dev, stream, flush):
         modes["per_field_graph" if ng == 0 else f"grouped_{ng}"] = {
             "ms_per_step": m, "kernels_per_step": b.launch_count(), "value": len(specs) * 1e3 / m}
     b.set_grouping(groups)
+    if args.batch_profile is not None:
+        # one replay in the given graph form inside the profiler range
+        b.set_grouping(args.batch_profile)
+        step(prec)
+        step(prec)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        step(prec)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        b.set_grouping(groups)
     splits = [b.analysis_splits(i, prec) for i in range(len(specs))]
     # each field solved alone on its own grid (tuned settings), back to back
     solo_ms = 0.0

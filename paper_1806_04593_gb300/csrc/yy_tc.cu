@@ -884,9 +884,11 @@ struct ReduceRotateArgs {
 };
 
 // Block (n, group): radius n, modes [256 group, 256 group + 256) of both patches.
-__device__ __forceinline__ void reduce_rotate_block(const ReduceRotateArgs &r, int n, int group) {
+__device__ __forceinline__ void reduce_rotate_block(const ReduceRotateArgs &ra, int n, int group) {
   __shared__ double ad[2 * 640];   // two rows of at most 640 modes (group of 256 plus its degrees' ends)
   __shared__ float af[2 * 640];
+  // the arguments in registers: the stores to A and Atot could otherwise alias them
+  const ReduceRotateArgs r = ra;
   const int n_r = r.n_r, n_lm = r.n_lm;
   const int M = 2 * n_r;
   const int j0 = group * blockDim.x;
@@ -903,7 +905,8 @@ __device__ __forceinline__ void reduce_rotate_block(const ReduceRotateArgs &r, i
       v = r.mono[row];
     } else {
       float sum = 0.f, comp = 0.f;
-      for (int z = 0; z < r.S; ++z) kahan_add(sum, comp, r.part[(size_t)z * zs + idx]);
+#pragma unroll 4
+      for (int z = 0; z < r.S; ++z) kahan_add(sum, comp, r.part[(size_t)z * zs + idx]);   // loads in flight, sums in order
       const double tot = f32_to_f64(sum) + f32_to_f64(comp);
       v = fma(tot * r.rs[row], r.cs[c], r.mean[row] * r.colsum[c]);
     }
