@@ -1935,6 +1935,9 @@ cudaError_t tc_synthesis(yy_grid *g, yy_precision prec, double *py, double *pg, 
 
 struct OzThetaArgs {
   int n_shells, n_theta, lmax, n_lm, nt, n_jobs, rows_pad;
+  int n_r;                      // shells of one patch
+  const double *inv_sin;        // [n_theta]: 1 / sin theta_j at the polar cell centres
+  const double *inv_r;          // [n_r]: the angular coefficients are -Q inv_r[n]
   const double *Q;              // [3][n_shells][n_lm]: Phi, g_r and angular coefficients
   const double *tab[3];         // [n_theta][n_lm]: P, dP/dtheta, m P / sin theta (float64)
   __nv_bfloat16 *G[4];          // per field: slices [6][rows_pad][kMaxK]
@@ -1996,6 +1999,19 @@ __device__ __forceinline__ void oz_theta_row(unsigned long long b0, unsigned lon
   }
   // value = 2^(e + 1 - 64) (digit sums): trig scale 2^1, digit weights 2^-64
   if (lane == 0) *gexp = exm == 0 ? 0 : e + 1 - 64;
+}
+
+// The float64 value of a G bit pattern from another lane: slot t0 = lane
+// takes slot t0 + 1 (t0 odd) or t0 - 1 (t0 even), slot t1 = 63 - lane slot
+// t1 - 1 (t1 even) or t1 + 1 (t1 odd), i.e. the other slot of the same m.
+__device__ __forceinline__ void oz_swap_slots(unsigned long long b0, unsigned long long b1, int lane,
+                                              unsigned long long &s0, unsigned long long &s1) {
+  const int src0 = (lane & 1) ? lane + 1 : lane - 1;   // holds slot swap(t0) as its t0 (lane 31: own t1)
+  const int src1 = (lane & 1) ? lane + 1 : lane - 1;   // holds slot swap(t1) as its t1 (lane 31: own t0)
+  const unsigned long long x0 = __shfl_sync(0xffffffffu, b0, src0 & 31);
+  const unsigned long long x1 = __shfl_sync(0xffffffffu, b1, src1 & 31);
+  s0 = lane == 31 ? b1 : x0;
+  s1 = lane == 31 ? b0 : x1;
 }
 
 // One warp per (field, shell, mirrored row pair j, j' = n_theta - 1 - j).
@@ -2086,6 +2102,27 @@ __global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
   const size_t row = (size_t)shell * a.n_theta + j, rowm = (size_t)shell * a.n_theta + jm;
   oz_theta_row(g0, g1, lane, Gf + row * FormOzaki::kMaxK, stride, gexp + row, a.nt, a.bias);
   if (jm != j) oz_theta_row(r0, r1, lane, Gf + rowm * FormOzaki::kMaxK, stride, gexp + rowm, a.nt, a.bias);
+  if (f != 0 || a.n_jobs < 4) return;
+  // g_phi from Phi's values: its coefficients are the angular set, -Q / r
+  // (r the shell's outer edge), and its table m P / sin theta is m / sin
+  // theta times Phi's P in the other slot of the same m, so
+  //   G_phi[t] = (+1 for t even, -1 for t odd) (m / (r sin theta)) G_Phi[swap t]
+  // at both rows (sin theta_j' = sin theta_j); slot 0 (m = 0) and the slots
+  // past nt are zero.  This takes the place of a fourth pass over the terms.
+  unsigned long long sg0, sg1, sr0, sr1;
+  oz_swap_slots(g0, g1, lane, sg0, sg1);
+  oz_swap_slots(r0, r1, lane, sr0, sr1);
+  const double c = a.inv_r[shell % a.n_r] * a.inv_sin[j];
+  const double c0 = (t0 >= 1 && t0 < a.nt) ? ((t0 & 1) ? -c : c) * (double)m0 : 0.0;
+  const double c1 = (t1 >= 1 && t1 < a.nt) ? ((t1 & 1) ? -c : c) * (double)m1 : 0.0;
+  const unsigned long long p0 = (unsigned long long)__double_as_longlong(c0 * __longlong_as_double((long long)sg0));
+  const unsigned long long p1 = (unsigned long long)__double_as_longlong(c1 * __longlong_as_double((long long)sg1));
+  oz_theta_row(p0, p1, lane, a.G[3] + row * FormOzaki::kMaxK, stride, a.gexp[3] + row, a.nt, a.bias);
+  if (jm != j) {
+    const unsigned long long q0 = (unsigned long long)__double_as_longlong(c0 * __longlong_as_double((long long)sr0));
+    const unsigned long long q1 = (unsigned long long)__double_as_longlong(c1 * __longlong_as_double((long long)sr1));
+    oz_theta_row(q0, q1, lane, a.G[3] + rowm * FormOzaki::kMaxK, stride, a.gexp[3] + rowm, a.nt, a.bias);
+  }
 }
 
 // The weighted densities of the separable analysis, rho w, as digit rows for
@@ -2201,6 +2238,7 @@ struct yy_oz_tables {
   yy::OzSynthMaps synth_maps;   // its G maps (those of `maps`) and the trig map with 48-row boxes
   void *G[4];                   // per field: slices [6][rows_pad][64]
   int *gexp[4];                 // per field: [rows_pad]
+  double *inv_sin, *inv_r;      // 1 / sin theta_j at the polar cell centres, 1 / r_(n+1) per shell
   void *trig;                   // slices of trig / 2: [6][b_rows_pad][64]
   yy::PairMaps maps;
   // analysis (FormOzaki in fills of kFillK): rho w digit rows as operand A, the azimuthal table as operand B
@@ -2222,6 +2260,8 @@ static void free_oz(yy_oz_tables *o) {
     if (o->gexp[f]) cudaFree(o->gexp[f]);
   }
   if (o->trig) cudaFree(o->trig);
+  if (o->inv_sin) cudaFree(o->inv_sin);
+  if (o->inv_r) cudaFree(o->inv_r);
   if (o->an_x) cudaFree(o->an_x);
   if (o->an_exp) cudaFree(o->an_exp);
   if (o->an_az) cudaFree(o->an_az);
@@ -2446,7 +2486,19 @@ yy_status ozaki_prepare(yy_grid *g) {
       A((void **)&o->gexp[f], o->rows_pad * sizeof(int));
     }
     A(&o->trig, t_elems * F::kElem);
+    A((void **)&o->inv_sin, g->n_theta * sizeof(double));
+    A((void **)&o->inv_r, g->n_r * sizeof(double));
     for (int f = 0; f < 4 && e == cudaSuccess; ++f) e = cudaMemset(o->G[f], 0, g_bytes);
+    if (e == cudaSuccess) {
+      // g_phi's polar factors (k_theta_ozaki): the same cell centres as the
+      // tables and the same 1 / r as the scan coefficients
+      std::vector<double> is(g->n_theta), ir(g->n_r), re(g->n_r + 1);
+      for (int j = 0; j < g->n_theta; ++j) is[j] = 1.0 / sin(g->th0 + g->dth * (j + 0.5));
+      e = cudaMemcpy(re.data(), g->r_edges, re.size() * sizeof(double), cudaMemcpyDeviceToHost);
+      for (int n = 0; n < g->n_r; ++n) ir[n] = 1.0 / re[n + 1];
+      if (e == cudaSuccess) e = cudaMemcpy(o->inv_sin, is.data(), is.size() * sizeof(double), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(o->inv_r, ir.data(), ir.size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? YY_ERR_OOM : YY_ERR_CUDA;
   }
   if (st == YY_OK) {
@@ -2532,6 +2584,9 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
   ta.n_jobs = n_jobs;
   ta.rows_pad = o->rows_pad;
   ta.bias = o->bias;
+  ta.n_r = g->n_r;
+  ta.inv_sin = o->inv_sin;
+  ta.inv_r = o->inv_r;
   ta.Q = g->Q;
   ta.tab[0] = g->sep_P;
   ta.tab[1] = g->sep_dP;
@@ -2540,7 +2595,8 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
     ta.G[f] = (__nv_bfloat16 *)o->G[f];
     ta.gexp[f] = o->gexp[f];
   }
-  const size_t warps = (size_t)ta.n_shells * ((g->n_theta + 1) / 2) * n_jobs;   // mirrored row pairs
+  // mirrored row pairs of Phi, g_r and g_theta (Phi's warps also write g_phi)
+  const size_t warps = (size_t)ta.n_shells * ((g->n_theta + 1) / 2) * (n_jobs == 4 ? 3 : n_jobs);
   k_theta_ozaki<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(ta);
   note_launch(g, "k_theta_ozaki", s);
   cudaError_t e = cudaGetLastError();
