@@ -131,6 +131,48 @@ inline int grid_rows(const yy_grid *g) { return g->n_patch * g->n_r; }
 // the moments the radial scans read: both patches combined (Yin-Yang) or A itself (polar)
 inline const double *moments_total(const yy_grid *g) { return g->n_patch == 2 ? g->Atot : g->A; }
 
+#ifdef __CUDACC__
+// The rotation M (x, y, z) -> (-x, z, y) commutes with the reflection
+// x -> -x, under which a real harmonic of order m is even or odd: cos(m phi)
+// with the sign (-1)^m, sin(m phi) with (-1)^(m + 1).  So D^l_ij vanishes
+// unless modes i and j have the same parity, and the sum over i runs over
+// j's class only (half the products): local index 0 (m = 0) and 4k + 2,
+// 4k + 3 are even, 1 and 4k, 4k + 1 (k >= 1) odd.  The table's entries
+// across the classes are quadrature rounding (below 1e-16 of the others).
+__device__ __forceinline__ bool rot_even(int i) { return i == 0 || (i & 3) >= 2; }
+
+template <typename T>
+__device__ __forceinline__ void rot_class_dot(const T *__restrict__ D, int w, int jj, const T *x0, const T *x1, T &s0,
+                                              T &s1) {
+  const bool even = rot_even(jj);
+  // first index of the class, then steps alternating +1 and +3
+  int i = even ? 0 : 1;
+  if (even) {
+    const T d = D[0];
+    s0 = fma(d, x1[0], s0);
+    s1 = fma(d, x0[0], s1);
+    i = 2;
+  } else {
+    const T d = D[(size_t)w];
+    s0 = fma(d, x1[1], s0);
+    s1 = fma(d, x0[1], s1);
+    i = 4;
+  }
+#pragma unroll 2
+  for (; i < w; i += 4) {
+    const T d = D[(size_t)i * w];
+    s0 = fma(d, x1[i], s0);
+    s1 = fma(d, x0[i], s1);
+    if (i + 1 < w) {
+      const T e = D[(size_t)(i + 1) * w];
+      s0 = fma(e, x1[i + 1], s0);
+      s1 = fma(e, x0[i + 1], s1);
+    }
+  }
+}
+#endif
+
+
 // float64 / float32 CUDA-core contractions (yy_gemm_simt.cu)
 cudaError_t analysis_simt(yy_grid *g, const double *rho_yin, const double *rho_yang,
                           bool fp32, cudaStream_t s);

@@ -187,12 +187,7 @@ k_rotate_moments(int n_r, int n_lm, const T *__restrict__ rot, const double *__r
     const T *D = rot + (size_t)l * (4 * l * l - 1) / 3 + jj;
     const T *x0 = a + l * l, *x1 = a + n_lm + l * l;
     T s0 = 0, s1 = 0;   // into patch 0 (from patch 1) and into patch 1 (from patch 0)
-#pragma unroll 4
-    for (int i = 0; i < w; ++i) {
-      const T d = D[(size_t)i * w];
-      s0 = fma(d, x1[i], s0);
-      s1 = fma(d, x0[i], s1);
-    }
+    rot_class_dot(D, w, jj, x0, x1, s0, s1);
     double r0, r1;
     if constexpr (sizeof(T) == 4) {
       r0 = to_f64(s0);

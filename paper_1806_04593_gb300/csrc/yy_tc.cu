@@ -923,7 +923,7 @@ __device__ __forceinline__ void reduce_rotate_block(const ReduceRotateArgs &ra, 
   const float *x0 = af + (l * l - m0), *x1 = af + span + (l * l - m0);
   float s0 = 0.f, s1 = 0.f;   // into patch 0 (from patch 1) and into patch 1 (from patch 0)
 #pragma unroll 4
-  for (int i = 0; i < w; ++i) {
+  for (int i = 0; i < w; ++i) {   // all 2l + 1 terms (fp32: the loads, not the products, bound it)
     const float d = D[(size_t)i * w];
     s0 = fmaf(d, x1[i], s0);
     s1 = fmaf(d, x0[i], s1);
