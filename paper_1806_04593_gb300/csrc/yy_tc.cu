@@ -799,6 +799,136 @@ __global__ void __launch_bounds__(256) k_theta_g(ThetaArgs a) {
   }
 }
 
+// The same polar stage in the layout of k_theta_ozaki: one warp per (field,
+// shell, mirrored row pair j, j' = n_theta - 1 - j), the terms of even and of
+// odd l + m summed apart so that one pass gives both rows (P and m P / sin
+// theta keep the parity of l + m across the equator, dP/dtheta takes the
+// opposite one).  Lane L takes the slot pairs 64 g + L and 64 g + 63 - L
+// (their term counts add up to about l_max + 1 whatever L), the coefficients
+// in fp32 from the scan.  Slot 0 sums l >= 1 here and adds the l = 0 product
+// in float64 into add[] (its operand column stays zero).  g_phi needs no sum
+// of its own: its coefficients are -Q / r and its table m / sin theta times
+// Phi's, so Phi's warps form it from their values of the other slot of the
+// same m (as in k_theta_ozaki).
+struct ThetaF32Args {
+  int n_shells, n_theta, n_r, lmax, n_lm, nt, k_pad, n_jobs, rows_pad;
+  const float *Q32;             // [3][n_shells][n_lm]: Phi, g_r and angular coefficients in fp32
+  const double *Q;              // float64 (the l = 0 coefficient of slot 0)
+  const float *tab[3];          // [n_theta][n_lm]: P, dP/dtheta, m P / sin theta
+  const double *tab64[2];       // P and dP in float64 (their l = 0 column)
+  const float *inv_sin, *inv_r; // 1 / sin theta_j, 1 / r_(n+1)
+  void *G[4];                   // per field: bf16 pieces [3][rows_pad][k_pad]
+  float *add[4];                // per field: [rows_pad] slot-0 term
+};
+
+__device__ __forceinline__ void store_bf16x3(float y, uint16_t *base, size_t stride) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(y);
+  const float r = y - __bfloat162float(h);
+  const __nv_bfloat16 m = __float2bfloat16_rn(r);
+  base[0] = __bfloat16_as_ushort(h);
+  base[stride] = __bfloat16_as_ushort(m);
+  base[2 * stride] = __bfloat16_as_ushort(__float2bfloat16_rn(r - __bfloat162float(m)));
+}
+
+template <int NG>
+__global__ void __launch_bounds__(256) k_theta_f32(ThetaF32Args a) {
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  const int half = (a.n_theta + 1) >> 1;
+  const int pairs = a.n_shells * half;
+  const int n_f = a.n_jobs == 4 ? 3 : a.n_jobs;
+  if (warp >= pairs * n_f) return;
+  const int f = warp / pairs, pr = warp % pairs;
+  const int shell = pr / half, j = pr % half, jm = a.n_theta - 1 - j;
+  const int qb = f < 2 ? f : 2;
+  const float *q = a.Q32 + ((size_t)qb * a.n_shells + shell) * a.n_lm;
+  const float *tab = f <= 1 ? a.tab[0] : a.tab[1];
+  const float *tj = tab + (size_t)j * a.n_lm;
+  const int L = a.lmax;
+  float gj[NG][2], gm[NG][2];   // this lane's slots (64 g + lane, 64 g + 63 - lane) at rows j and j'
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int t = 64 * g + (h == 0 ? lane : 63 - lane);
+      const int m = (t + 1) >> 1;
+      const int l_lo = t == 0 ? 1 : m;                      // slot 0: l >= 1 here
+      float a1 = 0.f, a2 = 0.f;                            // l = L, L - 2, ... and l = L - 1, L - 3, ...
+      if (t < a.nt) {
+        int l = L;
+        const float *pq = q + L * L + t, *pt = tj + L * L + t;
+#pragma unroll 2
+        for (; l >= l_lo + 1; l -= 2) {
+          a1 = fmaf(pq[0], pt[0], a1);
+          const int d1 = 2 * l - 1;                        // l^2 - (l - 1)^2
+          a2 = fmaf(pq[-d1], pt[-d1], a2);
+          pq -= 4 * l - 4;                                 // l^2 - (l - 2)^2
+          pt -= 4 * l - 4;
+        }
+        if (l == l_lo) a1 = fmaf(pq[0], pt[0], a1);
+      }
+      // row j: E + O; row j': E - O when a1 holds even l + m (L + m even), else O - E;
+      // dP/dtheta has the opposite parity
+      const float e_o = ((L + m) & 1) ? a2 - a1 : a1 - a2;
+      gj[g][h] = a1 + a2;
+      gm[g][h] = f == 2 ? -e_o : e_o;
+    }
+  }
+  const size_t ps = (size_t)a.rows_pad * a.k_pad;
+  const size_t row = (size_t)shell * a.n_theta + j, rowm = (size_t)shell * a.n_theta + jm;
+  uint16_t *const Gf = (uint16_t *)(f == 0 ? a.G[0] : f == 1 ? a.G[1] : a.G[2]);
+#pragma unroll
+  for (int g = 0; g < NG; ++g)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int t = 64 * g + (h == 0 ? lane : 63 - lane);
+      if (t < 1 || t >= a.nt) continue;                    // slot 0 and the padding stay zero
+      store_bf16x3(gj[g][h], Gf + row * a.k_pad + t, ps);
+      if (jm != j) store_bf16x3(gm[g][h], Gf + rowm * a.k_pad + t, ps);
+    }
+  // slot 0 (lane 0, first slot): the l = 0 product in float64
+  if (lane == 0) {
+    float *const add = f == 0 ? a.add[0] : f == 1 ? a.add[1] : a.add[2];
+    const double q00 = a.Q[((size_t)qb * a.n_shells + shell) * a.n_lm];
+    const double t00 = (f == 2 ? a.tab64[1] : a.tab64[0])[(size_t)j * a.n_lm];
+    add[row] = f64_to_f32(fma(q00, t00, f32_to_f64(gj[0][0])));
+    if (jm != j) add[rowm] = f64_to_f32(fma(q00, f == 2 ? -t00 : t00, f32_to_f64(gm[0][0])));
+  }
+  if (f != 0 || a.n_jobs < 4) return;
+  // g_phi: G_phi[t] = (+1 for t even, -1 for t odd) (m / (r sin theta)) G_Phi[swap t]
+  const float c = a.inv_r[shell % a.n_r] * a.inv_sin[j];
+  uint16_t *const Gp = (uint16_t *)a.G[3];
+  const int src = (lane & 1) ? lane + 1 : lane - 1;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    // the other slot of the same m: the neighbouring lane's slot in the
+    // same half of the group, or for lanes 0 and 31 a slot of their own
+    float sj0 = __shfl_sync(0xffffffffu, gj[g][0], src & 31), sm0 = __shfl_sync(0xffffffffu, gm[g][0], src & 31);
+    float sj1 = __shfl_sync(0xffffffffu, gj[g][1], src & 31), sm1 = __shfl_sync(0xffffffffu, gm[g][1], src & 31);
+    if (lane == 31) {
+      sj0 = gj[g][1]; sm0 = gm[g][1];
+      sj1 = gj[g][0]; sm1 = gm[g][0];
+    } else if (lane == 0) {
+      sj0 = g > 0 ? gj[g > 0 ? g - 1 : 0][1] : 0.f;       // slot 64 g - 1
+      sm0 = g > 0 ? gm[g > 0 ? g - 1 : 0][1] : 0.f;
+      sj1 = g + 1 < NG ? gj[g + 1 < NG ? g + 1 : g][0] : 0.f;   // slot 64 g + 64
+      sm1 = g + 1 < NG ? gm[g + 1 < NG ? g + 1 : g][0] : 0.f;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int t = 64 * g + (h == 0 ? lane : 63 - lane);
+      if (t < 1 || t >= a.nt) continue;
+      const int m = (t + 1) >> 1;
+      const float ct = ((t & 1) ? -c : c) * (float)m;
+      store_bf16x3(ct * (h == 0 ? sj0 : sj1), Gp + row * a.k_pad + t, ps);
+      if (jm != j) store_bf16x3(ct * (h == 0 ? sm0 : sm1), Gp + rowm * a.k_pad + t, ps);
+    }
+  }
+  if (lane == 0) {
+    a.add[3][row] = 0.f;
+    if (jm != j) a.add[3][rowm] = 0.f;
+  }
+}
+
 template <int S, bool STAGE>
 size_t theta_smem(const yy_grid *g) {
   return ((size_t)3 * S + (STAGE ? 16 : 0)) * g->n_lm * sizeof(float);
@@ -1081,6 +1211,7 @@ struct yy_tc_tables {
   int sp_ok, sp_kpad, sp_rows, sp_rows_pad, sp_bn, sp_row_tiles, sp_b_rows_pad, sp_stages;
   void *sp_G[4], *sp_trig;
   float *sp_ones, *sp_ga[4], *sp_trigs_f;   // unit cell scales, slot-0 terms, trig row scales
+  float *sp_inv_sin, *sp_inv_r;             // 1 / sin theta_j, 1 / r_(n+1) (g_phi of the polar stage)
   double *sp_trigs;
   yy::PairMaps sp_maps;                   // a[field]: G, b[0]: trig table
   // separable analysis: rows (shell, j) of rho w as operand A, the azimuthal
@@ -1215,7 +1346,7 @@ static yy_status prepare_separable_synthesis(yy_grid *g, yy_tc_tables *t) {
       cudaFuncSetAttribute(k_theta_g<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kThetaSmemMax) != cudaSuccess ||
       cudaFuncSetAttribute(k_theta_g<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kThetaSmemMax) != cudaSuccess)
     return YY_ERR_NOT_SUPPORTED;
-  if (theta_smem<2, false>(g) > (size_t)kThetaSmemMax) return YY_OK;
+  if (nt > 128 && theta_smem<2, false>(g) > (size_t)kThetaSmemMax) return YY_OK;
   const size_t g_bytes = (size_t)F::kPA * t->sp_rows_pad * t->sp_kpad * F::kElem;
   cudaError_t e = cudaSuccess;
   auto A = [&](void **ptr, size_t bytes) {
@@ -1229,6 +1360,9 @@ static yy_status prepare_separable_synthesis(yy_grid *g, yy_tc_tables *t) {
   A(&t->sp_trig, (size_t)F::kPB * t->sp_b_rows_pad * t->sp_kpad * F::kElem);
   A((void **)&t->sp_trigs, t->sp_b_rows_pad * sizeof(double));
   A((void **)&t->sp_trigs_f, t->sp_b_rows_pad * sizeof(float));
+  A((void **)&t->sp_inv_sin, g->n_theta * sizeof(float));
+  A((void **)&t->sp_inv_r, g->n_r * sizeof(float));
+  if (!g->Q32) A((void **)&g->Q32, 3 * (size_t)grid_rows(g) * g->n_lm * sizeof(float));   // the scan's fp32 copy
   double *trig_rows = nullptr;
   A((void **)&trig_rows, (size_t)g->n_phi * nt * sizeof(double));
   if (e != cudaSuccess) {
@@ -1236,6 +1370,16 @@ static yy_status prepare_separable_synthesis(yy_grid *g, yy_tc_tables *t) {
     return e == cudaErrorMemoryAllocation ? YY_ERR_OOM : YY_ERR_CUDA;
   }
   for (int f = 0; f < 4 && e == cudaSuccess; ++f) e = cudaMemset(t->sp_G[f], 0, g_bytes);
+  if (e == cudaSuccess) {
+    // the polar cell centres of the tables and the scan's 1 / r
+    std::vector<float> is(g->n_theta), ir(g->n_r);
+    std::vector<double> re(g->n_r + 1);
+    for (int j = 0; j < g->n_theta; ++j) is[j] = (float)(1.0 / sin(g->th0 + g->dth * (j + 0.5)));
+    e = cudaMemcpy(re.data(), g->r_edges, re.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    for (int n = 0; n < g->n_r; ++n) ir[n] = (float)(1.0 / re[n + 1]);
+    if (e == cudaSuccess) e = cudaMemcpy(t->sp_inv_sin, is.data(), is.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(t->sp_inv_r, ir.data(), ir.size() * sizeof(float), cudaMemcpyHostToDevice);
+  }
   k_fill_ones<<<(t->sp_rows_pad + 255) / 256, 256>>>(t->sp_rows_pad, t->sp_ones);
   k_transpose_trig<<<(nt * g->n_phi + 255) / 256, 256>>>(nt, g->n_phi, g->sep_tr, trig_rows);
   PackBatch b = {};
@@ -1458,6 +1602,7 @@ static void release_separable(yy_tc_tables *t) {
     t->sp_ga[f] = nullptr;
   }
   void **sp[] = {&t->sp_trig, (void **)&t->sp_trigs_f, (void **)&t->sp_trigs, (void **)&t->sp_ones,
+                 (void **)&t->sp_inv_sin, (void **)&t->sp_inv_r,
                  &t->san_x, &t->san_az, (void **)&t->san_rs, (void **)&t->san_mean, (void **)&t->san_F0,
                  (void **)&t->san_azs, (void **)&t->san_rsf, (void **)&t->san_azsf, (void **)&t->san_colsum,
                  (void **)&t->san_ones, (void **)&t->san_part};
@@ -1727,6 +1872,39 @@ cudaError_t tc_analysis(yy_grid *g, yy_precision prec, const double *ry, const d
 }
 
 static cudaError_t theta_form(yy_grid *g, yy_tc_tables *t, bool grad, cudaStream_t s) {
+  if (t->sp_kpad <= 128 && g->Q32) {
+    ThetaF32Args b = {};
+    b.n_shells = grid_rows(g);
+    b.n_theta = g->n_theta;
+    b.n_r = g->n_r;
+    b.lmax = g->lmax;
+    b.n_lm = g->n_lm;
+    b.nt = 2 * g->lmax + 1;
+    b.k_pad = t->sp_kpad;
+    b.n_jobs = grad ? 4 : 1;
+    b.rows_pad = t->sp_rows_pad;
+    b.Q32 = g->Q32;
+    b.Q = g->Q;
+    b.tab[0] = g->sep_P32;
+    b.tab[1] = g->sep_dP32;
+    b.tab[2] = g->sep_Qs32;
+    b.tab64[0] = g->sep_P;
+    b.tab64[1] = g->sep_dP;
+    b.inv_sin = t->sp_inv_sin;
+    b.inv_r = t->sp_inv_r;
+    for (int f = 0; f < 4; ++f) {
+      b.G[f] = t->sp_G[f];
+      b.add[f] = t->sp_ga[f];
+    }
+    const size_t warps = (size_t)b.n_shells * ((g->n_theta + 1) / 2) * (grad ? 3 : 1);
+    const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
+    if (t->sp_kpad <= 64)
+      k_theta_f32<1><<<blocks, 256, 0, s>>>(b);
+    else
+      k_theta_f32<2><<<blocks, 256, 0, s>>>(b);
+    note_launch(g, "k_theta_f32", s);
+    return cudaGetLastError();
+  }
   ThetaArgs a = {};
   a.n_shells = grid_rows(g);
   a.n_theta = g->n_theta;
