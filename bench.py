@@ -740,6 +740,15 @@ def run_batched(args, gradient, dev, stream, flush):
     for (py, pg), o in zip(phi, outs):
         for got, ref in ((py, o[0]), (pg, o[1])):
             err = max(err, float(((got - ref).abs() / ref.abs()).max()))
+    ref64 = [[t.clone() for t in o] for o in outs]
+    # the same batch at float64 accuracy on the tensor cores (Ozaki digits)
+    b.prepare("fp64_ozaki")
+    b.tune("fp64_ozaki", gradient=gradient, reps=1)
+    ms_oz = timed("fp64_ozaki", args.batch_steps, max(3, args.warmup))
+    err_oz = 0.0
+    for r, o in zip(ref64, outs):
+        for got, ref in ((o[0], r[0]), (o[1], r[1])):
+            err_oz = max(err_oz, float(((got - ref).abs() / ref.abs()).max()))
     cells = sum(2 * sp.n_r * sp.n_ang for sp in specs)   # both patches
     res = {
         "workload": "64 fields, n_r ~ U{100..600}, 2 / 1.5 / 1 degree cells, l_max ~ U{10..40}, "
@@ -760,6 +769,9 @@ def run_batched(args, gradient, dev, stream, flush):
         "sum_of_solo_solves_ms": solo_ms,
         "fp64_gpu_path": {"value": len(specs) * 1e3 / ms64, "unit": "field solves/s", "ms_per_step": ms64},
         "speedup_vs_fp64": ms64 / ms,
+        "fp64_ozaki": {"value": len(specs) * 1e3 / ms_oz, "unit": "field solves/s", "ms_per_step": ms_oz,
+                       "speedup_vs_fp64": ms64 / ms_oz,
+                       "phi_rel_max_pointwise_vs_fp64_worst_field": err_oz},
         "phi_rel_max_pointwise_vs_fp64_worst_field": err,
         "l2": "L2 flushed (252 MB write) before every timed step",
     }

@@ -85,7 +85,10 @@ typedef enum {
  *             combination of the patches and the scans are float64 on CUDA
  *             cores as for YY_FP64 (and so is the analysis with
  *             YY_ANALYSIS_DENSE, or with more than 640 cells per row).
- *             Needs yy_grid_prepare and 2 l_max + 1 <= 64 (l_max <= 31).    */
+ *             Needs yy_grid_prepare and 2 l_max + 1 <= 127 (l_max <= 63);
+ *             above l_max 30 the contractions take their general kernels
+ *             (no spare bias columns in G rows of 64 slots, rows of 128
+ *             slots past l_max 31, the analysis in tiles of 32 slots). */
 typedef enum {
   YY_FP64 = 0,
   YY_FP32 = 1,
@@ -222,7 +225,7 @@ yy_status yy_grid_set_analysis_splits(yy_grid *g, yy_precision prec, int splits)
 /* Build the operand tables of a reduced-precision form or of YY_FP64_OZAKI
  * (allocates device memory; synchronises).  YY_FP64 is always ready.
  * Returns YY_ERR_NOT_SUPPORTED if the device cannot run the form, or for
- * YY_FP64_OZAKI when l_max > 31. */
+ * YY_FP64_OZAKI when l_max > 63. */
 yy_status yy_grid_prepare(yy_grid *g, yy_precision prec);
 
 /* One solve on `cuda_stream` (a cudaStream_t, NULL = legacy default stream).

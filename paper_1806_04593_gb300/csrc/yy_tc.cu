@@ -2108,17 +2108,19 @@ cudaError_t tc_synthesis(yy_grid *g, yy_precision prec, double *py, double *pg, 
 // j) and field and cuts each row into FormOzaki's six fixed-point slices
 // under the row's power-of-two scale; k_tc_pair (out_mode 3) contracts them
 // with the slices of the trig table (scaled by 1/2: cos 0 = 1 must lie inside
-// (-1, 1)) over K = 2 l_max + 1 <= 64, exact per level, and rounds each value
-// once.  The monopole slot t = 0 is part of the contraction: it is exact too.
+// (-1, 1)) over K = 2 l_max + 1 <= 127 (rows of 64 or 128 slots, one fill),
+// exact per level, and rounds each value once.  The monopole slot t = 0 is
+// part of the contraction: it is exact too.
 
 struct OzThetaArgs {
   int n_shells, n_theta, lmax, n_lm, nt, n_jobs, rows_pad;
+  int gk;                       // slots of a G row (64 or 128: 64 NG)
   int n_r;                      // shells of one patch
   const double *inv_sin;        // [n_theta]: 1 / sin theta_j at the polar cell centres
   const double *inv_r;          // [n_r]: the angular coefficients are -Q inv_r[n]
   const double *Q;              // [3][n_shells][n_lm]: Phi, g_r and angular coefficients
   const double *tab[3];         // [n_theta][n_lm]: P, dP/dtheta, m P / sin theta (float64)
-  __nv_bfloat16 *G[4];          // per field: slices [6][rows_pad][kMaxK]
+  __nv_bfloat16 *G[4];          // per field: slices [6][rows_pad][gk]
   int *gexp[4];                 // per field: [rows_pad] power of two of a unit level-5 sum
   int bias;                     // write the bias digits of output mode 4 in slots nt and nt + 1
 };
@@ -2140,56 +2142,45 @@ __host__ __device__ __forceinline__ void oz_digits(unsigned long long X, int (&d
   d[0] = (int)X;
 }
 
-// One row's digits (row slots t0 = lane and t1 = 63 - lane hold G0 and G1,
-// passed as their float64 bit patterns b0 and b1):
-// the row's scale 2^e (e from the largest |G|: every |G| 2^-e < 1/2) and the
+// One row's digits: this lane's slots 64 g + lane and 64 g + 63 - lane
+// (g < NG) hold the float64 bit patterns b[g][0] and b[g][1].  The row's
+// scale 2^e (e from the largest |G| of the row: every |G| 2^-e < 1/2) and the
 // digits of X = round(|G| 2^(48 - e)) <= 2^47, taken from the float64 bits,
 // each with the sign of G.  A row of zeros (or of values below the normal
 // range) gets zero digits.
-__device__ __forceinline__ void oz_theta_row(unsigned long long b0, unsigned long long b1, int lane,
-                                             __nv_bfloat16 *dst, size_t stride, int *gexp, int nt, int bias) {
-  unsigned long long mb = max(b0 & 0x7FFFFFFFFFFFFFFFull, b1 & 0x7FFFFFFFFFFFFFFFull);
+template <int NG>
+__device__ __forceinline__ void oz_theta_row(const unsigned long long (&b)[NG][2], int lane, __nv_bfloat16 *dst,
+                                             size_t stride, int *gexp, int nt, int bias) {
+  unsigned long long mb = 0ull;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) mb = max(mb, max(b[g][0] & 0x7FFFFFFFFFFFFFFFull, b[g][1] & 0x7FFFFFFFFFFFFFFFull));
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
   const int exm = (int)(mb >> 52);                 // biased exponent of the largest |G|
   const int e = exm - 1021;                        // |G| < 2^(exm - 1022) = 2^(e - 1)
-  int d[2][6];
-  const unsigned long long bits[2] = {b0, b1};
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int ex = (int)((bits[h] >> 52) & 0x7FFu);
-    const int sh = 1027 - ex + e;                  // |G| 2^(48 - e) = significand >> sh, sh >= 6
-    unsigned long long X = 0ull;
-    if (exm != 0 && ex != 0 && sh < 64)
-      X = ((((bits[h] & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> (sh - 1)) + 1ull) >> 1;   // round half up
-    oz_digits(X, d[h]);
-  }
-  // the bias digits of output mode 4 (slots nt and nt + 1 hold G = 0)
-  const int t1 = 63 - lane;
-  const int bias0 = bias ? (lane == nt ? 0 : lane == nt + 1 ? 1 : -1) : -1;
-  const int bias1 = bias ? (t1 == nt ? 0 : t1 == nt + 1 ? 1 : -1) : -1;
+  for (int g = 0; g < NG; ++g)
 #pragma unroll
-  for (int sl = 0; sl < 6; ++sl) {
-    const float v0 = sl == bias0 ? kOzBiasG : ((b0 >> 63) ? -(float)d[0][sl] : (float)d[0][sl]);
-    const float v1 = sl == bias1 ? kOzBiasG : ((b1 >> 63) ? -(float)d[1][sl] : (float)d[1][sl]);
-    dst[sl * stride + lane] = __float2bfloat16_rn(v0);
-    dst[sl * stride + t1] = __float2bfloat16_rn(v1);
-  }
+    for (int h = 0; h < 2; ++h) {
+      const unsigned long long bits = b[g][h];
+      const int t = 64 * g + (h == 0 ? lane : 63 - lane);
+      const int ex = (int)((bits >> 52) & 0x7FFu);
+      const int sh = 1027 - ex + e;                // |G| 2^(48 - e) = significand >> sh, sh >= 6
+      unsigned long long X = 0ull;
+      if (exm != 0 && ex != 0 && sh < 64)
+        X = ((((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> (sh - 1)) + 1ull) >> 1;   // round half up
+      int d[6];
+      oz_digits(X, d);
+      // the bias digits of output mode 4 (slots nt and nt + 1 hold G = 0)
+      const int bias_sl = bias ? (t == nt ? 0 : t == nt + 1 ? 1 : -1) : -1;
+#pragma unroll
+      for (int sl = 0; sl < 6; ++sl) {
+        const float v = sl == bias_sl ? kOzBiasG : ((bits >> 63) ? -(float)d[sl] : (float)d[sl]);
+        dst[sl * stride + t] = __float2bfloat16_rn(v);
+      }
+    }
   // value = 2^(e + 1 - 64) (digit sums): trig scale 2^1, digit weights 2^-64
   if (lane == 0) *gexp = exm == 0 ? 0 : e + 1 - 64;
-}
-
-// The float64 value of a G bit pattern from another lane: slot t0 = lane
-// takes slot t0 + 1 (t0 odd) or t0 - 1 (t0 even), slot t1 = 63 - lane slot
-// t1 - 1 (t1 even) or t1 + 1 (t1 odd), i.e. the other slot of the same m.
-__device__ __forceinline__ void oz_swap_slots(unsigned long long b0, unsigned long long b1, int lane,
-                                              unsigned long long &s0, unsigned long long &s1) {
-  const int src0 = (lane & 1) ? lane + 1 : lane - 1;   // holds slot swap(t0) as its t0 (lane 31: own t1)
-  const int src1 = (lane & 1) ? lane + 1 : lane - 1;   // holds slot swap(t1) as its t1 (lane 31: own t0)
-  const unsigned long long x0 = __shfl_sync(0xffffffffu, b0, src0 & 31);
-  const unsigned long long x1 = __shfl_sync(0xffffffffu, b1, src1 & 31);
-  s0 = lane == 31 ? b1 : x0;
-  s1 = lane == 31 ? b0 : x1;
 }
 
 // One warp per (field, shell, mirrored row pair j, j' = n_theta - 1 - j).
@@ -2198,11 +2189,13 @@ __device__ __forceinline__ void oz_swap_slots(unsigned long long b0, unsigned lo
 // (-1)^(l + m) P_l^m(cos theta): with E and O the sums over the terms of even
 // and of odd l + m at row j, G = E + O at j and E - O at j' (for P and
 // m P / sin theta; dP/dtheta has the opposite parity, -(E - O) at j').  So one
-// pass over the coefficients gives both rows.  Lane L takes the slots t = L
-// and 63 - L (slot t sums l_max + 1 - (t + 1) / 2 terms, so every lane does
-// about the same work), l from l_max down in steps of two (terms l and l - 1:
+// pass over the coefficients gives both rows.  Lane L takes the slots
+// t = 64 g + L and 64 g + 63 - L, g < NG (G rows of 64 NG slots; slot t sums
+// l_max + 1 - (t + 1) / 2 terms, so the pair's counts add up to about the
+// same in every lane), l from l_max down in steps of two (terms l and l - 1:
 // one of each parity), g_phi with the cos / sin slots swapped, one pair of
 // accumulators that moves from slot t0 to t1 by register moves.
+template <int NG>
 __global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
   const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   const int half = (a.n_theta + 1) >> 1;
@@ -2217,69 +2210,73 @@ __global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
   const double *tab = f <= 1 ? a.tab[0] : (f == 2 ? a.tab[1] : a.tab[2]);
   const double *tj = tab + (size_t)j * a.n_lm;
   const int L = a.lmax;
-  const int t0 = lane, t1 = 63 - lane;
-  const int m0 = (t0 + 1) / 2, m1 = (t1 + 1) / 2;
-  int s0 = t0, s1 = t1;                               // coefficient slots
-  if (f == 3) {                                       // cos slot <- sin coefficient, sin slot <- cos
-    s0 = (t0 & 1) ? t0 + 1 : t0 - 1;
-    s1 = (t1 & 1) ? t1 + 1 : t1 - 1;
-  }
-  const int n0 = (t0 < a.nt && (f < 3 || t0 > 0)) ? L + 1 - m0 : 0;
-  const int n1 = (t1 < a.nt && (f < 3 || t1 > 0)) ? L + 1 - m1 : 0;
-  const int k0 = (n0 + 1) >> 1, k1 = (n1 + 1) >> 1;  // steps of two terms per slot
-  // a1: terms with l = l_max, l_max - 2, ...; a2: l = l_max - 1, l_max - 3, ...
-  double a1 = 0.0, a2 = 0.0, h1 = 0.0, h2 = 0.0;
-  const double *pq = q + L * L + s0, *pt = tj + L * L + t0;
-  int l = L, m = m0;
-  for (int it = 0; it < k0 + k1; ++it) {
-    if (it == k0) {
-      h1 = a1;
-      h2 = a2;
-      a1 = 0.0;
-      a2 = 0.0;
-      l = L;
-      m = m1;
-      pq = q + L * L + s1;
-      pt = tj + L * L + t1;
+  unsigned long long gb[NG][2], rb[NG][2];   // this lane's slots at rows j and j'
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    const int t0 = 64 * g + lane, t1 = 64 * g + 63 - lane;
+    const int m0 = (t0 + 1) / 2, m1 = (t1 + 1) / 2;
+    int s0 = t0, s1 = t1;                             // coefficient slots
+    if (f == 3) {                                     // cos slot <- sin coefficient, sin slot <- cos
+      s0 = (t0 & 1) ? t0 + 1 : t0 - 1;
+      s1 = (t1 & 1) ? t1 + 1 : t1 - 1;
     }
-    a1 = fma(pq[0], pt[0], a1);
-    const int d1 = 2 * l - 1;                        // l^2 - (l - 1)^2
-    if (l > m) a2 = fma(pq[-d1], pt[-d1], a2);
-    pq -= 4 * l - 4;                                 // l^2 - (l - 2)^2
-    pt -= 4 * l - 4;
-    l -= 2;
+    const int n0 = (t0 < a.nt && (f < 3 || t0 > 0)) ? L + 1 - m0 : 0;
+    const int n1 = (t1 < a.nt && (f < 3 || t1 > 0)) ? L + 1 - m1 : 0;
+    const int k0 = (n0 + 1) >> 1, k1 = (n1 + 1) >> 1;  // steps of two terms per slot
+    // a1: terms with l = l_max, l_max - 2, ...; a2: l = l_max - 1, l_max - 3, ...
+    double a1 = 0.0, a2 = 0.0, h1 = 0.0, h2 = 0.0;
+    const double *pq = q + L * L + s0, *pt = tj + L * L + t0;
+    int l = L, m = m0;
+    for (int it = 0; it < k0 + k1; ++it) {
+      if (it == k0) {
+        h1 = a1;
+        h2 = a2;
+        a1 = 0.0;
+        a2 = 0.0;
+        l = L;
+        m = m1;
+        pq = q + L * L + s1;
+        pt = tj + L * L + t1;
+      }
+      a1 = fma(pq[0], pt[0], a1);
+      const int d1 = 2 * l - 1;                        // l^2 - (l - 1)^2
+      if (l > m) a2 = fma(pq[-d1], pt[-d1], a2);
+      pq -= 4 * l - 4;                                 // l^2 - (l - 2)^2
+      pt -= 4 * l - 4;
+      l -= 2;
+    }
+    double x0[2], x1[2];                               // (a1, a2) of slots t0 and t1
+    if (k1 > 0) {
+      x0[0] = h1; x0[1] = h2; x1[0] = a1; x1[1] = a2;
+    } else {
+      x0[0] = a1; x0[1] = a2; x1[0] = 0.0; x1[1] = 0.0;
+    }
+    // Row j: E + O = a1 + a2.  Row j': E - O, which is a1 - a2 when a1 holds
+    // the terms of even l + m (l_max + m even), else a2 - a1.  Every sign change
+    // (that one, dP/dtheta's parity, g_phi's swapped slots) flips the sign bit
+    // of the bit pattern on the integer units: four float64 additions per lane.
+    const unsigned long long SB = 0x8000000000000000ull;
+    unsigned long long fg0 = 0ull, fg1 = 0ull;
+    unsigned long long fr0 = ((L + m0) & 1) ? SB : 0ull, fr1 = ((L + m1) & 1) ? SB : 0ull;
+    if (f == 2) {
+      fr0 ^= SB;
+      fr1 ^= SB;
+    }
+    if (f == 3) {
+      if (!(t0 & 1)) { fg0 = SB; fr0 ^= SB; }
+      if (!(t1 & 1)) { fg1 = SB; fr1 ^= SB; }
+    }
+    gb[g][0] = (unsigned long long)__double_as_longlong(x0[0] + x0[1]) ^ fg0;
+    gb[g][1] = (unsigned long long)__double_as_longlong(x1[0] + x1[1]) ^ fg1;
+    rb[g][0] = (unsigned long long)__double_as_longlong(x0[0] - x0[1]) ^ fr0;
+    rb[g][1] = (unsigned long long)__double_as_longlong(x1[0] - x1[1]) ^ fr1;
   }
-  double x0[2], x1[2];                               // (a1, a2) of slots t0 and t1
-  if (k1 > 0) {
-    x0[0] = h1; x0[1] = h2; x1[0] = a1; x1[1] = a2;
-  } else {
-    x0[0] = a1; x0[1] = a2; x1[0] = 0.0; x1[1] = 0.0;
-  }
-  // Row j: E + O = a1 + a2.  Row j': E - O, which is a1 - a2 when a1 holds
-  // the terms of even l + m (l_max + m even), else a2 - a1.  Every sign change
-  // (that one, dP/dtheta's parity, g_phi's swapped slots) flips the sign bit
-  // of the bit pattern on the integer units: four float64 additions per lane.
-  const unsigned long long SB = 0x8000000000000000ull;
-  unsigned long long fg0 = 0ull, fg1 = 0ull;
-  unsigned long long fr0 = ((L + m0) & 1) ? SB : 0ull, fr1 = ((L + m1) & 1) ? SB : 0ull;
-  if (f == 2) {
-    fr0 ^= SB;
-    fr1 ^= SB;
-  }
-  if (f == 3) {
-    if (!(t0 & 1)) { fg0 = SB; fr0 ^= SB; }
-    if (!(t1 & 1)) { fg1 = SB; fr1 ^= SB; }
-  }
-  const unsigned long long g0 = (unsigned long long)__double_as_longlong(x0[0] + x0[1]) ^ fg0;
-  const unsigned long long g1 = (unsigned long long)__double_as_longlong(x1[0] + x1[1]) ^ fg1;
-  const unsigned long long r0 = (unsigned long long)__double_as_longlong(x0[0] - x0[1]) ^ fr0;
-  const unsigned long long r1 = (unsigned long long)__double_as_longlong(x1[0] - x1[1]) ^ fr1;
-  const size_t stride = (size_t)a.rows_pad * FormOzaki::kMaxK;
+  const size_t stride = (size_t)a.rows_pad * a.gk;
   __nv_bfloat16 *const Gf = f == 0 ? a.G[0] : f == 1 ? a.G[1] : f == 2 ? a.G[2] : a.G[3];
   int *const gexp = f == 0 ? a.gexp[0] : f == 1 ? a.gexp[1] : f == 2 ? a.gexp[2] : a.gexp[3];
   const size_t row = (size_t)shell * a.n_theta + j, rowm = (size_t)shell * a.n_theta + jm;
-  oz_theta_row(g0, g1, lane, Gf + row * FormOzaki::kMaxK, stride, gexp + row, a.nt, a.bias);
-  if (jm != j) oz_theta_row(r0, r1, lane, Gf + rowm * FormOzaki::kMaxK, stride, gexp + rowm, a.nt, a.bias);
+  oz_theta_row<NG>(gb, lane, Gf + row * a.gk, stride, gexp + row, a.nt, a.bias);
+  if (jm != j) oz_theta_row<NG>(rb, lane, Gf + rowm * a.gk, stride, gexp + rowm, a.nt, a.bias);
   if (f != 0 || a.n_jobs < 4) return;
   // g_phi from Phi's values: its coefficients are the angular set, -Q / r
   // (r the shell's outer edge), and its table m P / sin theta is m / sin
@@ -2287,20 +2284,34 @@ __global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
   //   G_phi[t] = (+1 for t even, -1 for t odd) (m / (r sin theta)) G_Phi[swap t]
   // at both rows (sin theta_j' = sin theta_j); slot 0 (m = 0) and the slots
   // past nt are zero.  This takes the place of a fourth pass over the terms.
-  unsigned long long sg0, sg1, sr0, sr1;
-  oz_swap_slots(g0, g1, lane, sg0, sg1);
-  oz_swap_slots(r0, r1, lane, sr0, sr1);
+  // The other slot of the same m is the neighbouring lane's slot in the same
+  // half of the group, or for lanes 0 and 31 one of their own.
   const double c = a.inv_r[shell % a.n_r] * a.inv_sin[j];
-  const double c0 = (t0 >= 1 && t0 < a.nt) ? ((t0 & 1) ? -c : c) * (double)m0 : 0.0;
-  const double c1 = (t1 >= 1 && t1 < a.nt) ? ((t1 & 1) ? -c : c) * (double)m1 : 0.0;
-  const unsigned long long p0 = (unsigned long long)__double_as_longlong(c0 * __longlong_as_double((long long)sg0));
-  const unsigned long long p1 = (unsigned long long)__double_as_longlong(c1 * __longlong_as_double((long long)sg1));
-  oz_theta_row(p0, p1, lane, a.G[3] + row * FormOzaki::kMaxK, stride, a.gexp[3] + row, a.nt, a.bias);
-  if (jm != j) {
-    const unsigned long long q0 = (unsigned long long)__double_as_longlong(c0 * __longlong_as_double((long long)sr0));
-    const unsigned long long q1 = (unsigned long long)__double_as_longlong(c1 * __longlong_as_double((long long)sr1));
-    oz_theta_row(q0, q1, lane, a.G[3] + rowm * FormOzaki::kMaxK, stride, a.gexp[3] + rowm, a.nt, a.bias);
+  const int src = ((lane & 1) ? lane + 1 : lane - 1) & 31;
+  unsigned long long pg[NG][2], prm[NG][2];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    unsigned long long sg0 = __shfl_sync(0xffffffffu, gb[g][0], src), sr0 = __shfl_sync(0xffffffffu, rb[g][0], src);
+    unsigned long long sg1 = __shfl_sync(0xffffffffu, gb[g][1], src), sr1 = __shfl_sync(0xffffffffu, rb[g][1], src);
+    if (lane == 31) {
+      sg0 = gb[g][1]; sr0 = rb[g][1];
+      sg1 = gb[g][0]; sr1 = rb[g][0];
+    } else if (lane == 0) {
+      sg0 = g > 0 ? gb[g > 0 ? g - 1 : 0][1] : 0ull;       // slot 64 g - 1
+      sr0 = g > 0 ? rb[g > 0 ? g - 1 : 0][1] : 0ull;
+      sg1 = g + 1 < NG ? gb[g + 1 < NG ? g + 1 : g][0] : 0ull;   // slot 64 g + 64
+      sr1 = g + 1 < NG ? rb[g + 1 < NG ? g + 1 : g][0] : 0ull;
+    }
+    const int t0 = 64 * g + lane, t1 = 64 * g + 63 - lane;
+    const double c0 = (t0 >= 1 && t0 < a.nt) ? ((t0 & 1) ? -c : c) * (double)((t0 + 1) / 2) : 0.0;
+    const double c1 = (t1 >= 1 && t1 < a.nt) ? ((t1 & 1) ? -c : c) * (double)((t1 + 1) / 2) : 0.0;
+    pg[g][0] = (unsigned long long)__double_as_longlong(c0 * __longlong_as_double((long long)sg0));
+    pg[g][1] = (unsigned long long)__double_as_longlong(c1 * __longlong_as_double((long long)sg1));
+    prm[g][0] = (unsigned long long)__double_as_longlong(c0 * __longlong_as_double((long long)sr0));
+    prm[g][1] = (unsigned long long)__double_as_longlong(c1 * __longlong_as_double((long long)sr1));
   }
+  oz_theta_row<NG>(pg, lane, a.G[3] + row * a.gk, stride, a.gexp[3] + row, a.nt, a.bias);
+  if (jm != j) oz_theta_row<NG>(prm, lane, a.G[3] + rowm * a.gk, stride, a.gexp[3] + rowm, a.nt, a.bias);
 }
 
 // The weighted densities of the separable analysis, rho w, as digit rows for
@@ -2411,6 +2422,7 @@ __global__ void __launch_bounds__(256) k_rhow_ozaki(OzRhoArgs a) {
 
 struct yy_oz_tables {
   int rows, rows_pad, bn, row_tiles, b_rows_pad, stages, pair_slots;
+  int gk;                       // slots of a G row and of a trig digit row: 64 (l_max <= 31) or 128
   int bias;                     // synthesis with biased level sums (one fill): k_oz_synth
   int synth_slots;              // resident clusters of k_oz_synth (0: use k_tc_pair output mode 4)
   yy::OzSynthMaps synth_maps;   // its G maps (those of `maps`) and the trig map with 48-row boxes
@@ -2528,7 +2540,7 @@ static yy_status ozaki_prepare_analysis(yy_grid *g, yy_oz_tables *o) {
   o->an_ok = 1;
   // the analysis kernel with all slots in one MMA
   o->an_slots2 = 0;
-  if (make_map<F>(&o->an_maps2.a, o->an_x, o->an_kpad, F::kPA * o->rows_pad, kPairRows) &&
+  if (nt <= kOzAnBN && make_map<F>(&o->an_maps2.a, o->an_x, o->an_kpad, F::kPA * o->rows_pad, kPairRows) &&
       make_map<F>(&o->an_maps2.b, o->an_az, o->an_kpad, F::kPB * o->an_b_rows_pad, kOzAnBN / 2) &&
       cudaFuncSetAttribute(k_oz_analysis, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzAnSmem) == cudaSuccess) {
     cudaLaunchAttribute attr[1];
@@ -2624,9 +2636,10 @@ yy_status ozaki_prepare(yy_grid *g) {
   typedef FormOzaki F;
   if (g->oz) return YY_OK;
   const int nt = 2 * g->lmax + 1;
-  if (nt > F::kMaxK || !g->sep_tr || !g->sep_P || !g->sep_dP || !g->sep_Qs) return YY_ERR_NOT_SUPPORTED;
+  if (nt > 2 * F::kMaxK || !g->sep_tr || !g->sep_P || !g->sep_dP || !g->sep_Qs) return YY_ERR_NOT_SUPPORTED;
   yy_oz_tables *o = new (std::nothrow) yy_oz_tables();
   if (!o) return YY_ERR_OOM;
+  o->gk = nt <= F::kMaxK ? F::kMaxK : 2 * F::kMaxK;   // K of the synthesis contraction: one fill either way
   o->rows = grid_rows(g) * g->n_theta;
   o->rows_pad = round_up(o->rows, 2 * kPairRows);
   o->bn = 32;   // eight accumulators of bn columns fill one 256-column TMEM buffer
@@ -2656,8 +2669,8 @@ yy_status ozaki_prepare(yy_grid *g) {
   auto A = [&](void **ptr, size_t bytes) {
     if (e == cudaSuccess) e = dmalloc(ptr, bytes);
   };
-  const size_t g_bytes = (size_t)F::kPA * o->rows_pad * F::kMaxK * F::kElem;
-  const size_t t_elems = (size_t)F::kPB * o->b_rows_pad * F::kMaxK;
+  const size_t g_bytes = (size_t)F::kPA * o->rows_pad * o->gk * F::kElem;
+  const size_t t_elems = (size_t)F::kPB * o->b_rows_pad * o->gk;
   if (st == YY_OK) {
     for (int f = 0; f < 4; ++f) {
       A(&o->G[f], g_bytes);
@@ -2689,7 +2702,7 @@ yy_status ozaki_prepare(yy_grid *g) {
     // output mode 4 needs two spare K columns and |S_L| < 2^22 for every
     // level and longitude: |S_L| <= 128 sum over the level's products (s, u)
     // of sum_t |trig digit u at t| (G digits are at most 128 in magnitude)
-    bool bias = nt + 2 <= F::kMaxK;
+    bool bias = nt + 2 <= o->gk;
     for (int k = 0; k < g->n_phi && st == YY_OK; ++k) {
       long long asum[6] = {0, 0, 0, 0, 0, 0};
       for (int t = 0; t < nt; ++t) {
@@ -2697,7 +2710,7 @@ yy_status ozaki_prepare(yy_grid *g) {
         int d[6];
         oz_digits((unsigned long long)floor(ldexp(fabs(y), 48) + 0.5), d);
         for (int s2 = 0; s2 < F::kPB; ++s2) {
-          sl[((size_t)s2 * o->b_rows_pad + k) * F::kMaxK + t] = bf16_int(y < 0 ? -d[s2] : d[s2]);
+          sl[((size_t)s2 * o->b_rows_pad + k) * o->gk + t] = bf16_int(y < 0 ? -d[s2] : d[s2]);
           asum[s2] += d[s2] < 0 ? -d[s2] : d[s2];
         }
       }
@@ -2711,8 +2724,8 @@ yy_status ozaki_prepare(yy_grid *g) {
       // the trig side of the bias columns: 2^11 in every slice at nt, in slice 5 at nt + 1
       const uint16_t two11 = bf16_int(2048);   // a power of two: exact in bf16
       for (int k = 0; k < o->b_rows_pad; ++k) {
-        for (int s2 = 0; s2 < F::kPB; ++s2) sl[((size_t)s2 * o->b_rows_pad + k) * F::kMaxK + nt] = two11;
-        sl[((size_t)5 * o->b_rows_pad + k) * F::kMaxK + nt + 1] = two11;
+        for (int s2 = 0; s2 < F::kPB; ++s2) sl[((size_t)s2 * o->b_rows_pad + k) * o->gk + nt] = two11;
+        sl[((size_t)5 * o->b_rows_pad + k) * o->gk + nt + 1] = two11;
       }
     }
     o->bias = bias ? 1 : 0;
@@ -2720,17 +2733,17 @@ yy_status ozaki_prepare(yy_grid *g) {
       st = YY_ERR_CUDA;
   }
   if (st == YY_OK) {
-    bool ok = make_map<F>(&o->maps.b[0], o->trig, F::kMaxK, F::kPB * o->b_rows_pad, o->bn / 2);
+    bool ok = make_map<F>(&o->maps.b[0], o->trig, o->gk, F::kPB * o->b_rows_pad, o->bn / 2);
     for (int f = 0; f < 4 && ok; ++f)
-      ok = make_map<F>(&o->maps.a[f], o->G[f], F::kMaxK, F::kPA * o->rows_pad, kPairRows);
+      ok = make_map<F>(&o->maps.a[f], o->G[f], o->gk, F::kPA * o->rows_pad, kPairRows);
     if (!ok) st = YY_ERR_NOT_SUPPORTED;
   }
-  if (st == YY_OK && o->bias && F::kMaxK == kOzSynthKB * 32) {
+  if (st == YY_OK && o->bias && o->gk == kOzSynthKB * 32) {
     // the synthesis kernel with the G tile resident (falls back to the pair
     // kernel's output mode 4 where it cannot run)
     int n = 0;
     for (int f = 0; f < 4; ++f) o->synth_maps.a[f] = o->maps.a[f];
-    if (make_map<F>(&o->synth_maps.b, o->trig, F::kMaxK, F::kPB * o->b_rows_pad, kOzSynthBN / 2) &&
+    if (make_map<F>(&o->synth_maps.b, o->trig, o->gk, F::kPB * o->b_rows_pad, kOzSynthBN / 2) &&
         cudaFuncSetAttribute(k_oz_synth, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSynthSmem) == cudaSuccess) {
       cudaLaunchAttribute attr[1];
       cudaLaunchConfig_t cfg = pair_config(64, kOzSynthSmem, 0, attr);
@@ -2761,6 +2774,7 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
   ta.nt = 2 * g->lmax + 1;
   ta.n_jobs = n_jobs;
   ta.rows_pad = o->rows_pad;
+  ta.gk = o->gk;
   ta.bias = o->bias;
   ta.n_r = g->n_r;
   ta.inv_sin = o->inv_sin;
@@ -2775,7 +2789,10 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
   }
   // mirrored row pairs of Phi, g_r and g_theta (Phi's warps also write g_phi)
   const size_t warps = (size_t)ta.n_shells * ((g->n_theta + 1) / 2) * (n_jobs == 4 ? 3 : n_jobs);
-  k_theta_ozaki<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(ta);
+  if (o->gk == 64)
+    k_theta_ozaki<1><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(ta);
+  else
+    k_theta_ozaki<2><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(ta);
   note_launch(g, "k_theta_ozaki", s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -2815,7 +2832,7 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
   a.rows = g->n_phi;
   a.row_tiles = o->row_tiles;
   a.bn = o->bn;
-  a.kb_total = F::kMaxK * F::kElem / kRowBytes;
+  a.kb_total = o->gk * F::kElem / kRowBytes;   // one fill (level sums below 2^24 up to K = 160)
   a.k_splits = 1;
   a.kb_per_split = a.kb_total;
   a.a_rows = o->rows_pad;

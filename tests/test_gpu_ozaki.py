@@ -119,9 +119,13 @@ def test_ozaki_analysis_in_several_fills(yy, oracle_grid):
 def test_ozaki_ragged_and_highest_degree(yy):
     """Sizes that are multiples of no tile (17 x 41 cells, 131 zones; an odd
     n_theta, whose middle polar row is its own mirror in the polar synthesis
-    stage), and l_max = 31, the largest with 2 l_max + 1 <= 64."""
+    stage); l_max = 31, the last in G rows of 64 slots (no room for the bias
+    columns: the general synthesis kernel); l_max = 40 and 63, in rows of 128
+    slots (the polar stage's second slot group, the analysis in tiles of 32
+    slots), 63 the largest."""
     from oracle import OracleGrid
-    for n_r, nt, npp, lmax, seed in ((131, 17, 41, 13, 45), (40, 20, 60, 31, 46)):
+    for n_r, nt, npp, lmax, seed in ((131, 17, 41, 13, 45), (40, 20, 60, 31, 46), (36, 22, 66, 40, 47),
+                                     (20, 24, 70, 63, 48)):
         spec = inputs.GridSpec(f"ragged_oz_{lmax}", np.logspace(-2, 0, n_r + 1), nt, npp, 0.03, 0.05, lmax, 1.0)
         rng = np.random.default_rng(seed)
         ry = rng.uniform(0.5, 1.5, (n_r, nt, npp))
@@ -183,7 +187,7 @@ def test_ozaki_needs_prepare_and_low_degree(yy):
         assert st == yy.YY_ERR_NOT_SUPPORTED
     finally:
         g.close()
-    big = inputs.GridSpec("oz_lmax40", np.logspace(-2, 0, 9), 12, 36, 0.05, 0.05, 40, 1.0)
+    big = inputs.GridSpec("oz_lmax64", np.logspace(-2, 0, 9), 12, 36, 0.05, 0.05, 64, 1.0)   # 2 l_max + 1 > 127
     g = yy.Grid.from_spec(big)
     try:
         assert yy.yy_grid_prepare(g.handle, yy.YY_FP64_OZAKI) == yy.YY_ERR_NOT_SUPPORTED
