@@ -49,6 +49,9 @@ L2_BYTES = 126 * 1024 * 1024
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # fp32 pipe: 152 SMs x 128 FFMA per clock x 2 flop x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# fp32 operations of one float-float multiply-add (TwoProduct by FMA with the
+# cross terms, TwoSum into the high part, the low parts added)
+FF_OPS = 12
 FORMS = ("fp64_ozaki", "fp16x2", "bf16x3", "tf32", "fp32", "fp64")
 DTYPE = {"fp64": "f64", "fp32": "f32", "fp16x2": "fp16x2 (fp32 accumulate, f64 scans)",
          "bf16x3": "bf16x3 (fp32 accumulate, f64 scans)", "tf32": "tf32 (fp32 accumulate, f64 scans)",
@@ -339,13 +342,15 @@ def kernel_work(name, spec, n_lm, gradient, prec):
         k_pad = -(-spec.n_phi // 64) * 64
         w = {"flop": 2.0 * rows * spec.n_phi * nt, "flop_kind": "tensor", "products": "ozaki",
              "bytes": rows * k_pad * 6 * 2}
-    elif name == "k_theta_ozaki":
-        dfma = 0
-        for t in range(nt):
-            m = (t + 1) // 2
-            dfma += (L + 1 - m) * (J if t > 0 else min(J, 3))
-        w = {"flop": 2.0 * n_r2 * half * dfma, "flop_kind": "fp64",
-             "bytes": J * rows * (-(-nt // 32) * 32) * 6 * 2 + 3 * n_r2 * n_lm * f64}
+    elif name == "k_theta_ff":
+        # float-float multiply-adds of Phi, g_r and g_theta (g_phi is formed
+        # from Phi's sums), one per term and mirrored row pair
+        ffma = sum(L + 1 - (t + 1) // 2 for t in range(nt)) * min(J, 3)
+        gk = 64 if nt <= 64 else 128
+        w = {"flop": 2.0 * n_r2 * half * ffma, "flop_kind": "ff",
+             "bytes": J * rows * gk * 6 * 2 + min(J, 3) * n_r2 * n_lm * f64}
+    elif name == "k_q_ff":
+        w = {"bytes": 2 * min(J, 3) * n_r2 * n_lm * f64}
     elif name == "k_rhow_ozaki":
         k_pad = -(-spec.n_phi // 64) * 64
         w = {"bytes": n_r2 * spec.n_ang * f64 + rows * k_pad * 6 * 2}
@@ -391,6 +396,12 @@ def roofline_of(name, ms, spec, n_lm, gradient, prec, peaks, ozaki_products):
                                    f"(algorithmic float64 work {w['flop'] / 1e9:.2f} GFLOP)"),
                           "peak_source": ("measured bf16 burst" + (" x 0.5 (tf32 nominal ratio)" if ratio < 1 else "")
                                           + f", {peaks['source']}")})
+        elif kind == "ff":
+            cands.append({"bound": "alu", "achieved": w["flop"] / s / 1e12, "peak": FP32_PEAK_TFLOPS / FF_OPS,
+                          "unit": "TFLOP/s",
+                          "work": f"float-float multiply-adds x 2 = {w['flop'] / 1e9:.2f} GFLOP per launch",
+                          "peak_source": (f"derived: 152 SMs x 128 FFMA per clock x 2 flop x 2070 MHz, divided by "
+                                          f"the {FF_OPS} fp32 operations of one float-float multiply-add")})
         else:
             peak = FP64_PEAK_TFLOPS if kind == "fp64" else FP32_PEAK_TFLOPS
             cands.append({"bound": "alu", "achieved": w["flop"] / s / 1e12, "peak": peak, "unit": "TFLOP/s",

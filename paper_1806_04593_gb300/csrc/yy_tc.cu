@@ -2314,6 +2314,379 @@ __global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
   if (jm != j) oz_theta_row<NG>(prm, lane, a.G[3] + rowm * a.gk, stride, a.gexp[3] + rowm, a.nt, a.bias);
 }
 
+// ---- the polar stage in float-float arithmetic (k_q_ff, k_theta_ff) --------
+//
+// The same sums as k_theta_ozaki, G[t] = sum_l Q[l^2 + t] T_j[l^2 + t] with
+// the even / odd split over the mirrored rows, on the fp32 pipe in
+// float-float arithmetic: a value is the unevaluated sum hi + lo of two fp32
+// numbers (about 48 significant bits, the precision of the digits the sums
+// are cut into next).  A product is exact as x + fma(a, b, -x) (Dekker's
+// TwoProduct with a fused multiply-add), a sum as s + err (Knuth's TwoSum);
+// the cross terms hi lo' + lo hi' go into the low part and lo lo' (2^-48 of
+// the product) is dropped -- the accurate dot product of Ogita, Rump and
+// Oishi (2005) with split inputs.  Every step is an explicitly rounded
+// intrinsic so that the compiler neither fuses nor reorders it.
+//
+// The stage is a small product per slot t (m = (t + 1) / 2): the polar table
+// T_j[l, t] (rows j, l = m..l_max) times the coefficients Q[l, t] of every
+// shell.  So a block takes 32 shells (the lanes: coefficient loads from a
+// shell-minor copy of Q are coalesced) and TP mirrored row pairs (their
+// table rows in shared memory: every lane of a warp reads the same entry),
+// each warp the slots of one or two orders m with about the same number of
+// terms (m and l_max + 1 - m), and stages the sums in shared memory; then
+// each warp cuts whole rows into digits as k_theta_ozaki does (lanes on
+// slots 2 L and 2 L + 1: one 4-byte store per slice and lane), Phi's rows
+// giving g_phi's as well.
+
+// (hi, lo) of Q 2^-qexp per (field, shell), the scale from the row's largest
+// |Q| (|Q| 2^-qexp < 1), in a shell-minor layout [field][n_lm][shells_pad];
+// entries below 2^-126 of the scale (and the padding shells) are zero.
+struct OzQffArgs {
+  int n_shells, shells_pad, n_lm;
+  const double *Q;              // [n_q][n_shells][n_lm]
+  float2 *Qf;                   // [n_q][n_lm][shells_pad]
+  int *qexp;                    // [n_q][n_shells]
+};
+
+__device__ __forceinline__ float2 ff_split(double x, int qe) {
+  const uint32_t lo = (uint32_t)__double2loint(x), hi = (uint32_t)__double2hiint(x);
+  const int ex0 = (int)((hi >> 20) & 0x7FFu);
+  const int ex = ex0 - qe;                             // biased exponent of x 2^-qe
+  if (ex0 == 0 || ex < 897) return make_float2(0.f, 0.f);   // zero, subnormal, or below 2^-126 of the scale
+  const double y = __hiloint2double((int)(hi - ((uint32_t)qe << 20)), (int)lo);   // |y| < 1: exact
+  const float h = f64_to_f32_rn(y);
+  // y - h: the 29 bits below h's last, less h's rounding step; times 2^(ex - 1075)
+  const uint32_t r29 = lo & 0x1FFFFFFFu;
+  const uint32_t m23 = (lo >> 29) & 1u;
+  const int up = (r29 > 0x10000000u || (r29 == 0x10000000u && m23)) ? 1 : 0;
+  const int r = (int)r29 - (up << 29);                 // |r| <= 2^28
+  float l = __fmul_rn(__fmul_rn(__int2float_rn(r), __uint_as_float(63u << 23)),   // 2^-64
+                      __uint_as_float((uint32_t)(ex - 1011 + 127) << 23));        // 2^(ex - 1011)
+  if (hi >> 31) l = -l;
+  return make_float2(h, l);
+}
+
+// One block per (field, 8 shells), a warp per shell: the row's scale, then
+// the row through a shared tile (chunks of kQffChunk coefficients) so that
+// the stores are 64-byte runs of the 8 shells.
+constexpr int kQffShells = 8, kQffChunk = 512;
+
+__global__ void __launch_bounds__(256) k_q_ff(OzQffArgs a) {
+  __shared__ float2 tile[kQffChunk][kQffShells + 1];
+  const int n_sb = a.shells_pad / kQffShells;
+  const int f = (int)blockIdx.x / n_sb, s0 = ((int)blockIdx.x % n_sb) * kQffShells;
+  const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+  const int s = s0 + warp;
+  const double *row = a.Q + ((size_t)f * a.n_shells + (s < a.n_shells ? s : 0)) * a.n_lm;
+  unsigned long long mb = 0ull;
+  if (s < a.n_shells)
+    for (int k = lane; k < a.n_lm; k += 32)
+      mb = max(mb, (unsigned long long)__double_as_longlong(row[k]) & 0x7FFFFFFFFFFFFFFFull);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
+  const int exm = (int)(mb >> 52);
+  const int qe = exm == 0 ? 0 : exm - 1022;
+  if (lane == 0 && s < a.n_shells) a.qexp[(size_t)f * a.n_shells + s] = qe;
+  float2 *Qfb = a.Qf + (size_t)f * a.n_lm * a.shells_pad + s0;
+  for (int k0 = 0; k0 < a.n_lm; k0 += kQffChunk) {
+    const int kn = min(kQffChunk, a.n_lm - k0);
+    for (int k = lane; k < kn; k += 32)
+      tile[k][warp] = s < a.n_shells ? ff_split(row[k0 + k], qe) : make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int i = (int)threadIdx.x; i < kn * kQffShells; i += (int)blockDim.x) {
+      const int k = i / kQffShells, c = i - k * kQffShells;
+      Qfb[(size_t)(k0 + k) * a.shells_pad + c] = tile[k][c];
+    }
+    __syncthreads();
+  }
+}
+
+// acc += q p (q, p, acc float-float)
+__device__ __forceinline__ void ff_fma(float2 q, float2 p, float2 &acc) {
+  const float x = __fmul_rn(q.x, p.x);
+  const float xe = __fmaf_rn(q.x, p.y, __fmaf_rn(q.y, p.x, __fmaf_rn(q.x, p.x, -x)));
+  const float s = __fadd_rn(acc.x, x);
+  const float bb = __fsub_rn(s, acc.x);
+  const float err = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  acc.y = __fadd_rn(acc.y, __fadd_rn(err, xe));
+  acc.x = s;
+}
+
+// a + sg b, renormalised (|lo| <= half an ulp of hi)
+__device__ __forceinline__ float2 ff_sum(float2 a, float2 b, float sg) {
+  const float bx = sg * b.x, by = sg * b.y;
+  const float s = __fadd_rn(a.x, bx);
+  const float bb = __fsub_rn(s, a.x);
+  const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(bx, bb));
+  const float lo = __fadd_rn(err, __fadd_rn(a.y, by));
+  const float h = __fadd_rn(s, lo);
+  return make_float2(h, __fsub_rn(lo, __fsub_rn(h, s)));
+}
+
+// x 2^(64 - e) truncated to an integer, for |x| < 2^(e - 1)
+__device__ __forceinline__ long long ff_fixed_part(float x, int e) {
+  const uint32_t u = __float_as_uint(x);
+  const int ex = (int)((u >> 23) & 0xFFu);
+  const uint32_t sig = ex ? ((u & 0x7FFFFFu) | 0x800000u) : (u & 0x7FFFFFu);
+  const int sh = (ex ? ex : 1) - 86 - e;                // x 2^(64 - e) = sig 2^sh, sh <= 39
+  unsigned long long m = 0ull;
+  if (sh >= 0)
+    m = (unsigned long long)sig << sh;
+  else if (sh > -32)
+    m = sig >> -sh;
+  return (u >> 31) ? -(long long)m : (long long)m;
+}
+
+// One row of float-float values cut into digits: lane L holds slots
+// 64 g + 2 L and 64 g + 2 L + 1.  The row's scale 2^e: the largest |hi|
+// stepped up by one ulp bounds every |hi + lo| (|lo| is at most half an ulp),
+// so every value is below 2^(e - 1); X = round(|value| 2^(48 - e)) <= 2^47
+// from 16 guard bits, and its balanced base-256 digits in one step: with
+// Y = X + 127 (1 + 2^8 + ... + 2^32), the low five digits are Y's bytes less
+// 127 (each in [-127, 128], the carries done by the addition) and the top
+// one is Y >> 40.  qe: the power of two the values carry.
+template <int NG>
+__device__ __forceinline__ void ff_row(const float2 (&v)[NG][2], int lane, __nv_bfloat16 *dst, size_t stride,
+                                       int *gexp, int nt, int bias, int qe) {
+  uint32_t mb = 0u;
+#pragma unroll
+  for (int g = 0; g < NG; ++g)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t u = __float_as_uint(v[g][h].x) & 0x7FFFFFFFu;
+      mb = max(mb, u == 0u ? 0u : u + 1u);
+    }
+  mb = __reduce_max_sync(0xffffffffu, mb);
+  const int exm = (int)(mb >> 23);
+  const int e = exm - 125;                              // every |value| < 2^(exm - 126) = 2^(e - 1)
+  constexpr uint32_t kBiasBits = 0x45C0u;               // bf16 of kOzBiasG (6144)
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    uint32_t bits[2][6], sgn[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const long long V = ff_fixed_part(v[g][h].x, e) + ff_fixed_part(v[g][h].y, e);
+      const unsigned long long A = (unsigned long long)(V < 0 ? -V : V);
+      const unsigned long long Y = ((A + 32768ull) >> 16) + 0x7F7F7F7F7Full;
+      const uint32_t ylo = (uint32_t)Y, yhi = (uint32_t)(Y >> 32);
+      sgn[h] = V < 0 ? 1u : 0u;
+      bits[h][0] = __float_as_uint(__fsub_rn(__uint_as_float(0x4B000000u | (yhi >> 8)), 8388608.f));
+      bits[h][1] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(yhi, 0x4B000000u, 0x7540)), 8388735.f));
+      bits[h][2] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7543)), 8388735.f));
+      bits[h][3] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7542)), 8388735.f));
+      bits[h][4] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7541)), 8388735.f));
+      bits[h][5] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7540)), 8388735.f));
+    }
+    const int t = 64 * g + 2 * lane;
+    const uint32_t sm = (sgn[0] << 15) | (sgn[1] << 31);
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst + t);
+#pragma unroll
+    for (int sl = 0; sl < 6; ++sl) {
+      uint32_t w = __byte_perm(bits[0][sl], bits[1][sl], 0x7632) ^ sm;
+      if (bias) {
+        // the bias digits of output mode 4 (slots nt and nt + 1 hold G = 0)
+        if (sl == 0 && t == nt) w |= kBiasBits;
+        if (sl == 0 && t + 1 == nt) w |= kBiasBits << 16;
+        if (sl == 1 && t == nt + 1) w |= kBiasBits;
+        if (sl == 1 && t + 1 == nt + 1) w |= kBiasBits << 16;
+      }
+      d32[sl * (stride / 2)] = w;
+    }
+  }
+  // value = 2^(e + qe + 1 - 64) (digit sums): trig scale 2^1, digit weights 2^-64
+  if (lane == 0) *gexp = exm == 0 ? 0 : e + qe + 1 - 64;
+}
+
+struct OzThetaFFArgs {
+  int n_shells, shells_pad, n_theta, half, lmax, n_lm, nt, gphi, rows_pad, gk, n_r, bias;
+  const float2 *Qf;             // [3][n_lm][shells_pad] (k_q_ff)
+  const int *qexp;              // [3][n_shells]
+  const float2 *Pf[2];          // [n_theta][n_lm]: P and dP/dtheta as (hi, lo)
+  const double *inv_sin, *inv_r;
+  __nv_bfloat16 *G[4];
+  int *gexp[4];
+};
+
+// Shared memory of k_theta_ff: TP table rows (rounded to an even count of
+// float2) and the staged sums, 32 shells x (2 TP rows of gk slots + 1).
+__host__ __device__ constexpr int theta_ff_tp(int gk) { return gk == 64 ? 2 : 1; }
+__host__ __device__ inline int theta_ff_tab(int n_lm, int gk) { return (theta_ff_tp(gk) * n_lm + 1) & ~1; }
+__host__ __device__ inline int theta_ff_pitch(int gk) { return 2 * theta_ff_tp(gk) * gk + 1; }
+inline size_t theta_ff_smem(int n_lm, int gk) {
+  return ((size_t)theta_ff_tab(n_lm, gk) + 32 * (size_t)theta_ff_pitch(gk)) * sizeof(float2);
+}
+
+// Blocks: (field, 32 shells, TP mirrored row pairs); warps: one or two
+// orders m at a time (m and l_max + 1 - m, about 2 (l_max + 1) terms).
+template <int NG>
+__global__ void __launch_bounds__(512, 2) k_theta_ff(OzThetaFFArgs a) {
+  constexpr int TP = NG == 1 ? 2 : 1;
+  constexpr int R = 2 * TP;
+  extern __shared__ float2 ffsm[];
+  float2 *ptab = ffsm;                                   // [TP][n_lm]
+  float2 *stg = ffsm + theta_ff_tab(a.n_lm, a.gk);       // [32][pitch]
+  const int pitch = theta_ff_pitch(a.gk);
+  const int W = (int)(blockDim.x >> 5), warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+  const int n_pt = (a.half + TP - 1) / TP, n_st = a.shells_pad >> 5;
+  const int pt = (int)blockIdx.x % n_pt, st = ((int)blockIdx.x / n_pt) % n_st, f = (int)blockIdx.x / (n_pt * n_st);
+  const int pair0 = pt * TP, shell0 = st * 32;
+  const float2 *tsrc = f == 2 ? a.Pf[1] : a.Pf[0];
+  for (int i = (int)threadIdx.x; i < TP * a.n_lm; i += (int)blockDim.x) {
+    const int r = i / a.n_lm;
+    ptab[i] = pair0 + r < a.half ? tsrc[(size_t)(pair0 + r) * a.n_lm + (i - r * a.n_lm)] : make_float2(0.f, 0.f);
+  }
+  // the rows' scales, and g_phi's factor 1 / (r sin theta_j) as an fp32 pair
+  __shared__ int qe_s[32];
+  __shared__ float2 cphi[32][R];
+  if (threadIdx.x < 32) {
+    const int sh = shell0 + (int)threadIdx.x;
+    qe_s[threadIdx.x] = sh < a.n_shells ? a.qexp[(size_t)f * a.n_shells + sh] : 0;
+  }
+  if (f == 0 && a.gphi)
+    for (int i = (int)threadIdx.x; i < 32 * R; i += (int)blockDim.x) {
+      const int sl = i / R, ri = i - sl * R;
+      const int sh = shell0 + sl, p = pair0 + (ri >> 1);
+      float2 c2 = make_float2(0.f, 0.f);
+      if (sh < a.n_shells && p < a.half) {
+        const int j = (ri & 1) ? a.n_theta - 1 - p : p;
+        const double c = a.inv_r[sh % a.n_r] * a.inv_sin[j];
+        const float ch = f64_to_f32_rn(c);
+        c2 = make_float2(ch, f64_to_f32_rn(c - f32_to_f64(ch)));
+      }
+      cphi[sl][ri] = c2;
+    }
+  __syncthreads();
+  const int L = a.lmax, n_groups = L / 2 + 1;
+  const float2 *qf = a.Qf + (size_t)f * a.n_lm * a.shells_pad + shell0 + lane;
+  const size_t qs = (size_t)a.shells_pad;
+  float2 *srow = stg + lane * pitch;
+  for (int gi = warp; gi < n_groups; gi += W) {
+#pragma unroll 1
+    for (int k = 0; k < 2; ++k) {
+      int m;
+      if (gi == 0) {
+        if (k == 1 && !(L & 1)) break;
+        m = k == 0 ? 0 : (L + 1) / 2;
+      } else {
+        m = k == 0 ? gi : L + 1 - gi;
+      }
+      const int t0 = m == 0 ? 0 : 2 * m - 1;
+      const bool two_slots = m > 0;
+      // a[s][i][0]: terms l = l_max, l_max - 2, ...; [1]: l = l_max - 1, ...
+      float2 acc[2][TP][2];
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int i = 0; i < TP; ++i) acc[s][i][0] = acc[s][i][1] = make_float2(0.f, 0.f);
+      // terms l and l - 1 per step; the next step's coefficients are loaded
+      // before this step's multiply-adds
+      const float2 z2 = make_float2(0.f, 0.f);
+      int b1 = L * L + t0;                               // l^2 + t0 at l
+      float2 q1[2], q2[2];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const bool on = s == 0 || two_slots;
+        q1[s] = on ? qf[(size_t)(b1 + s) * qs] : z2;
+        q2[s] = on && L - 1 >= m ? qf[(size_t)(b1 - (2 * L - 1) + s) * qs] : z2;
+      }
+#pragma unroll 1
+      for (int l = L; l >= m; l -= 2) {
+        const bool second = l - 1 >= m;
+        const int b2 = b1 - (2 * l - 1);                 // (l - 1)^2 + t0
+        const int b1n = b1 - (4 * l - 4);                // (l - 2)^2 + t0
+        const int b2n = b1n - (2 * l - 5);               // (l - 3)^2 + t0
+        float2 n1[2], n2[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const bool on = s == 0 || two_slots;
+          n1[s] = on && l - 2 >= m ? qf[(size_t)(b1n + s) * qs] : z2;
+          n2[s] = on && l - 3 >= m ? qf[(size_t)(b2n + s) * qs] : z2;
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          if (s == 1 && !two_slots) break;
+#pragma unroll
+          for (int i = 0; i < TP; ++i) {
+            ff_fma(q1[s], ptab[i * a.n_lm + b1 + s], acc[s][i][0]);
+            if (second) ff_fma(q2[s], ptab[i * a.n_lm + b2 + s], acc[s][i][1]);
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          q1[s] = n1[s];
+          q2[s] = n2[s];
+        }
+        b1 = b1n;
+      }
+      // row j: E + O = a0 + a1; row j': E - O, which is a0 - a1 when a0
+      // holds the terms of even l + m (l_max + m even), else a1 - a0;
+      // dP/dtheta has the opposite parity
+      const float sg = (((L + m) & 1) ^ (f == 2 ? 1 : 0)) ? -1.f : 1.f;
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        if (s == 1 && !two_slots) break;
+#pragma unroll
+        for (int i = 0; i < TP; ++i) {
+          srow[(2 * i) * a.gk + t0 + s] = ff_sum(acc[s][i][0], acc[s][i][1], 1.f);
+          const float2 d = ff_sum(acc[s][i][0], acc[s][i][1], -1.f);
+          srow[(2 * i + 1) * a.gk + t0 + s] = make_float2(sg * d.x, sg * d.y);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // rows: digits of each staged row; Phi's rows also give g_phi's from its
+  // values: its coefficients are the angular set, -Q / r (r the shell's
+  // outer edge), and its table m P / sin theta is m / sin theta times Phi's
+  // P in the other slot of the same m, so
+  //   G_phi[t] = (+1 for t even, -1 for t odd) (m / (r sin theta)) G_Phi[swap t]
+  // (sin theta_j' = sin theta_j); slot 0 and the slots past nt are zero.
+  const size_t stride = (size_t)a.rows_pad * a.gk;
+  __nv_bfloat16 *const Gf = f == 0 ? a.G[0] : f == 1 ? a.G[1] : a.G[2];
+  int *const gexp = f == 0 ? a.gexp[0] : f == 1 ? a.gexp[1] : a.gexp[2];
+  for (int rr = warp; rr < 32 * R; rr += W) {
+    const int sl = rr / R, ri = rr - sl * R;
+    const int shell = shell0 + sl, p = pair0 + (ri >> 1);
+    if (shell >= a.n_shells || p >= a.half) continue;
+    const int j = (ri & 1) ? a.n_theta - 1 - p : p;
+    if ((ri & 1) && j == p) continue;                    // the middle row is its own mirror
+    const float2 *src = stg + sl * pitch + ri * a.gk;
+    float2 v[NG][2];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int t = 64 * g + 2 * lane + h;
+        v[g][h] = t < a.nt ? src[t] : make_float2(0.f, 0.f);
+      }
+    const size_t row = (size_t)shell * a.n_theta + j;
+    const int qe = qe_s[sl];
+    ff_row<NG>(v, lane, Gf + row * a.gk, stride, gexp + row, a.nt, a.bias, qe);
+    if (f != 0 || !a.gphi) continue;
+    const float ch = cphi[sl][ri].x, cl = cphi[sl][ri].y;
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int t = 64 * g + 2 * lane + h;
+        float2 w = make_float2(0.f, 0.f);
+        if (t >= 1 && t < a.nt) {
+          const float2 x = src[(t & 1) ? t + 1 : t - 1];
+          const float mf = (float)((t + 1) >> 1);
+          const float c0 = __fmul_rn(ch, mf);
+          const float c1 = __fmaf_rn(cl, mf, __fmaf_rn(ch, mf, -c0));   // c m = c0 + c1
+          const float y = __fmul_rn(x.x, c0);
+          const float ye = __fmaf_rn(x.x, c1, __fmaf_rn(x.y, c0, __fmaf_rn(x.x, c0, -y)));
+          const float hs = __fadd_rn(y, ye);
+          w = make_float2(hs, __fsub_rn(ye, __fsub_rn(hs, y)));
+          if (t & 1) w = make_float2(-w.x, -w.y);
+        }
+        v[g][h] = w;
+      }
+    ff_row<NG>(v, lane, a.G[3] + row * a.gk, stride, a.gexp[3] + row, a.nt, a.bias, qe);
+  }
+}
+
 // The weighted densities of the separable analysis, rho w, as digit rows for
 // the analysis: one warp per row (shell, j); lane L takes the pairs
 // k = 2 L + 64 c.  rho w is the float64 product of the CUDA-core path; the
@@ -2429,6 +2802,10 @@ struct yy_oz_tables {
   void *G[4];                   // per field: slices [6][rows_pad][64]
   int *gexp[4];                 // per field: [rows_pad]
   double *inv_sin, *inv_r;      // 1 / sin theta_j at the polar cell centres, 1 / r_(n+1) per shell
+  int shells_pad;               // shells rounded up to 32 (k_theta_ff's tiles)
+  float2 *Qf;                   // [3][n_lm][shells_pad]: scaled coefficients as fp32 pairs (k_q_ff)
+  int *qexp;                    // [3][n_shells]: their scales
+  float2 *Pf[2];                // [n_theta][n_lm]: P and dP/dtheta as fp32 pairs
   void *trig;                   // slices of trig / 2: [6][b_rows_pad][64]
   yy::PairMaps maps;
   // analysis (FormOzaki in fills of kFillK): rho w digit rows as operand A, the azimuthal table as operand B
@@ -2452,6 +2829,10 @@ static void free_oz(yy_oz_tables *o) {
   if (o->trig) cudaFree(o->trig);
   if (o->inv_sin) cudaFree(o->inv_sin);
   if (o->inv_r) cudaFree(o->inv_r);
+  if (o->Qf) cudaFree(o->Qf);
+  if (o->qexp) cudaFree(o->qexp);
+  for (int k = 0; k < 2; ++k)
+    if (o->Pf[k]) cudaFree(o->Pf[k]);
   if (o->an_x) cudaFree(o->an_x);
   if (o->an_exp) cudaFree(o->an_exp);
   if (o->an_az) cudaFree(o->an_az);
@@ -2679,6 +3060,10 @@ yy_status ozaki_prepare(yy_grid *g) {
     A(&o->trig, t_elems * F::kElem);
     A((void **)&o->inv_sin, g->n_theta * sizeof(double));
     A((void **)&o->inv_r, g->n_r * sizeof(double));
+    o->shells_pad = round_up(grid_rows(g), 32);
+    A((void **)&o->Qf, (size_t)3 * g->n_lm * o->shells_pad * sizeof(float2));
+    A((void **)&o->qexp, (size_t)3 * grid_rows(g) * sizeof(int));
+    for (int k = 0; k < 2; ++k) A((void **)&o->Pf[k], (size_t)g->n_theta * g->n_lm * sizeof(float2));
     for (int f = 0; f < 4 && e == cudaSuccess; ++f) e = cudaMemset(o->G[f], 0, g_bytes);
     if (e == cudaSuccess) {
       // g_phi's polar factors (k_theta_ozaki): the same cell centres as the
@@ -2689,6 +3074,27 @@ yy_status ozaki_prepare(yy_grid *g) {
       for (int n = 0; n < g->n_r; ++n) ir[n] = 1.0 / re[n + 1];
       if (e == cudaSuccess) e = cudaMemcpy(o->inv_sin, is.data(), is.size() * sizeof(double), cudaMemcpyHostToDevice);
       if (e == cudaSuccess) e = cudaMemcpy(o->inv_r, ir.data(), ir.size() * sizeof(double), cudaMemcpyHostToDevice);
+      // the polar tables as fp32 pairs: hi = fl32(x), lo = fl32(x - hi)
+      const size_t ne = (size_t)g->n_theta * g->n_lm;
+      std::vector<double> tb(ne);
+      std::vector<float2> tf(ne);
+      const double *tsrc[2] = {g->sep_P, g->sep_dP};
+      for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMemcpy(tb.data(), tsrc[k], ne * sizeof(double), cudaMemcpyDeviceToHost);
+        for (size_t i = 0; i < ne; ++i) {
+          const float h = (float)tb[i];
+          tf[i] = make_float2(h, (float)(tb[i] - (double)h));
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(o->Pf[k], tf.data(), ne * sizeof(float2), cudaMemcpyHostToDevice);
+      }
+      if (e == cudaSuccess) e = cudaMemset(o->Qf, 0, (size_t)3 * g->n_lm * o->shells_pad * sizeof(float2));
+      // the largest dynamic shared memory of any supported degree (l_max 63),
+      // the same for every grid
+      const int ff_max = (int)theta_ff_smem(64 * 64, 128);
+      if (e == cudaSuccess &&
+          (cudaFuncSetAttribute(k_theta_ff<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ff_max) != cudaSuccess ||
+           cudaFuncSetAttribute(k_theta_ff<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, ff_max) != cudaSuccess))
+        e = cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? YY_ERR_OOM : YY_ERR_CUDA;
   }
@@ -2787,13 +3193,50 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
     ta.G[f] = (__nv_bfloat16 *)o->G[f];
     ta.gexp[f] = o->gexp[f];
   }
-  // mirrored row pairs of Phi, g_r and g_theta (Phi's warps also write g_phi)
-  const size_t warps = (size_t)ta.n_shells * ((g->n_theta + 1) / 2) * (n_jobs == 4 ? 3 : n_jobs);
+  // the coefficients as scaled fp32 pairs, then the polar stage of Phi, g_r
+  // and g_theta (Phi's blocks also write g_phi)
+  const int n_q = n_jobs == 4 ? 3 : 1;
+  OzQffArgs qa = {};
+  qa.n_shells = ta.n_shells;
+  qa.shells_pad = o->shells_pad;
+  qa.n_lm = g->n_lm;
+  qa.Q = g->Q;
+  qa.Qf = o->Qf;
+  qa.qexp = o->qexp;
+  k_q_ff<<<(unsigned)(n_q * (o->shells_pad / kQffShells)), 32 * kQffShells, 0, s>>>(qa);
+  note_launch(g, "k_q_ff", s);
+  OzThetaFFArgs fa = {};
+  fa.n_shells = ta.n_shells;
+  fa.shells_pad = o->shells_pad;
+  fa.n_theta = g->n_theta;
+  fa.half = (g->n_theta + 1) / 2;
+  fa.lmax = g->lmax;
+  fa.n_lm = g->n_lm;
+  fa.nt = ta.nt;
+  fa.gphi = n_jobs == 4 ? 1 : 0;
+  fa.rows_pad = o->rows_pad;
+  fa.gk = o->gk;
+  fa.n_r = g->n_r;
+  fa.bias = o->bias;
+  fa.Qf = o->Qf;
+  fa.qexp = o->qexp;
+  fa.Pf[0] = o->Pf[0];
+  fa.Pf[1] = o->Pf[1];
+  fa.inv_sin = o->inv_sin;
+  fa.inv_r = o->inv_r;
+  for (int f = 0; f < 4; ++f) {
+    fa.G[f] = ta.G[f];
+    fa.gexp[f] = ta.gexp[f];
+  }
+  const int n_groups = g->lmax / 2 + 1, tp = theta_ff_tp(o->gk);
+  const unsigned ff_blocks = (unsigned)(n_q * (o->shells_pad / 32) * ((fa.half + tp - 1) / tp));
+  const unsigned ff_threads = (unsigned)(32 * (n_groups < 16 ? n_groups : 16));
+  const size_t ff_smem = theta_ff_smem(g->n_lm, o->gk);
   if (o->gk == 64)
-    k_theta_ozaki<1><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(ta);
+    k_theta_ff<1><<<ff_blocks, ff_threads, ff_smem, s>>>(fa);
   else
-    k_theta_ozaki<2><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(ta);
-  note_launch(g, "k_theta_ozaki", s);
+    k_theta_ff<2><<<ff_blocks, ff_threads, ff_smem, s>>>(fa);
+  note_launch(g, "k_theta_ff", s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t comp = (size_t)g->n_r * g->n_ang;

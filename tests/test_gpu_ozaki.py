@@ -59,9 +59,10 @@ def test_ozaki_matches_oracle_and_fp64_path(yy, oracle_grid, name, analysis):
         g.set_analysis("auto")
     assert yy.yy_last_device_status(g.handle) == yy.YY_OK
     if analysis == "auto":
-        # separable both ways; the emulated analysis and synthesis each launch
-        # one kernel more (the digit rows) than their float64 counterparts
-        assert n_oz == n_64 + 2, (n_oz, n_64)
+        # separable both ways; the emulated analysis launches one kernel more
+        # (the digit rows) than its float64 counterpart, the synthesis two
+        # (the coefficients as fp32 pairs, the digit products)
+        assert n_oz == n_64 + 3, (n_oz, n_64)
     ref = oracle_grid(spec).solve(ry, rg, gradient=True)
     for q in ("yin", "yang"):
         assert phi_err(oz["phi_" + q], ref["phi_" + q]) <= TOL_FP64, q
@@ -102,8 +103,9 @@ def test_ozaki_analysis_in_several_fills(yy, oracle_grid):
         torch.cuda.synchronize()
         assert yy.yy_last_device_status(g.handle) == yy.YY_OK
         # polar grid: emulated analysis (digit rows, digit products, polar
-        # stage), scans, synthesis (polar stage, digit products)
-        assert n_oz == 6, n_oz
+        # stage), scans, synthesis (coefficient pairs, polar stage, digit
+        # products)
+        assert n_oz == 7, n_oz
         for key in ("phi", "grad"):
             assert field_err(key, out[key].cpu().numpy(), f64[key].cpu().numpy()) <= TOL_VS_FP64_PATH, key
         rng = np.random.default_rng(48)
@@ -211,9 +213,9 @@ def test_ozaki_long_rows_keep_the_float64_analysis(yy, oracle_grid):
         n_oz = yy.yy_last_launch_count(g.handle)
         assert yy.yy_last_device_status(g.handle) == yy.YY_OK
         # polar grid: analysis (float64: one or two launches), scans (one),
-        # synthesis (polar stage and digit products: two); the emulated
-        # analysis would take three
-        assert n_oz in (4, 5), n_oz
+        # synthesis (coefficient pairs, polar stage and digit products:
+        # three); the emulated analysis would take three
+        assert n_oz in (5, 6), n_oz
         rng = np.random.default_rng(47)
         cells = np.sort(rng.choice(spec.n_ang, 64, replace=False))
         ref = oracle_grid(spec).solve(rho, gradient=True, cells=cells)
