@@ -354,6 +354,10 @@ def kernel_work(name, spec, n_lm, gradient, prec):
     elif name == "k_rhow_ozaki":
         k_pad = -(-spec.n_phi // 64) * 64
         w = {"bytes": n_r2 * spec.n_ang * f64 + rows * k_pad * 6 * 2}
+    elif name == "k_sep_theta_ff":
+        nt_pad = -(-nt // 4) * 4
+        w = {"flop": 2.0 * n_r2 * n_lm * half, "flop_kind": "ff",
+             "bytes": rows * nt_pad * f64 + n_r2 * n_lm * f64}
     elif name.startswith("k_sep_theta"):
         w = {"flop": 2.0 * n_r2 * n_lm * half, "flop_kind": "fp64" if "double" in name or prec == "fp64" else "fp32",
              "bytes": rows * (-(-nt // 4) * 4) * f64 + n_r2 * n_lm * f64}
@@ -625,7 +629,8 @@ def run_ours(args, dist):
                    "gradient": gradient, "precision": prec, "parallelism": f"replicas x{dist.world}",
                    "l2": "L2 flushed (252 MB write) before every timed step"},
         "precision_note": ("float64 results: the azimuthal stages of analysis and synthesis as bf16 digit "
-                           "products on tcgen05 (exact per level, rounded once to float64), polar stages, "
+                           "products on tcgen05 (48-bit operands, exact per level, rounded once to float64), "
+                           "the polar stages in float-float arithmetic on the fp32 pipe (about 48 bits), "
                            "combination and radial scans in float64") if prec == "fp64_ozaki" else None,
         "gemm_tflops": grid.flops(gradient) / (dev_s_max / args.steps) / 1e12,
         "stage_ms": stage_ms,

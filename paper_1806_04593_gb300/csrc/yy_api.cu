@@ -360,7 +360,7 @@ yy_status yy_potential(yy_grid *g, const double *rho_yin, const double *rho_yang
   const bool sep_synth = ozaki || (simt ? (g->analysis_method != YY_ANALYSIS_DENSE && (g->sep_syn_ok & (f32 ? 1 : 2)) != 0)
                                         : (g->analysis_method == YY_ANALYSIS_SEPARABLE && tc_separable_synthesis_ready(g, prec)));
   g->last_sep_synthesis = sep_synth ? 1 : 0;
-  if (e == cudaSuccess && !g->atot_done) e = rotate_moments(g, prec == YY_FP64, s);
+  if (e == cudaSuccess && !g->atot_done) e = ozaki ? ozaki_rotate(g, s) : rotate_moments(g, prec == YY_FP64, s);
   // the separable tensor-core synthesis reads the coefficients in fp32 (the scan's copy)
   if (e == cudaSuccess) e = radial_scan(g, f32 || (sep_synth && !simt && !ozaki), true, s);
   if (e == cudaSuccess && !simt)

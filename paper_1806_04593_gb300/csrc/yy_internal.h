@@ -277,6 +277,8 @@ void ozaki_free(yy_grid *g);
 bool ozaki_ready(const yy_grid *g);
 // the separable analysis with its azimuthal stage by the same scheme (n_phi <= 640)
 bool ozaki_analysis_ready(const yy_grid *g);
+// the other patch's moments in each frame, float-float arithmetic (k_rotate_ff)
+cudaError_t ozaki_rotate(yy_grid *g, cudaStream_t s);
 cudaError_t ozaki_analysis(yy_grid *g, const double *rho_yin, const double *rho_yang, cudaStream_t s);
 cudaError_t ozaki_synthesis(yy_grid *g, double *phi_yin, double *phi_yang, double *grad_yin, double *grad_yang,
                             cudaStream_t s);

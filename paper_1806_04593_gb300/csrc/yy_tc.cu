@@ -2343,6 +2343,7 @@ __global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
 // entries below 2^-126 of the scale (and the padding shells) are zero.
 struct OzQffArgs {
   int n_shells, shells_pad, n_lm;
+  int one_pass;                 // the block's 8 rows fit in dynamic shared memory
   const double *Q;              // [n_q][n_shells][n_lm]
   float2 *Qf;                   // [n_q][n_lm][shells_pad]
   int *qexp;                    // [n_q][n_shells]
@@ -2367,31 +2368,58 @@ __device__ __forceinline__ float2 ff_split(double x, int qe) {
 }
 
 // One block per (field, 8 shells), a warp per shell: the row's scale, then
-// the row through a shared tile (chunks of kQffChunk coefficients) so that
-// the stores are 64-byte runs of the 8 shells.
+// its pairs, and the 8 rows written out shell-minor as 64-byte runs.  Rows
+// that fit in shared memory (one_pass) are read once: the loads of a lane
+// all in flight, the values staged in place of their pairs.
 constexpr int kQffShells = 8, kQffChunk = 512;
+constexpr size_t kQffOnePassSmem = 200 * 1024;
 
 __global__ void __launch_bounds__(256) k_q_ff(OzQffArgs a) {
-  __shared__ float2 tile[kQffChunk][kQffShells + 1];
+  extern __shared__ float2 qrow[];                         // one_pass: [8][n_lm]; else [kQffChunk][8 + 1]
+  float2 (*tile)[kQffShells + 1] = reinterpret_cast<float2 (*)[kQffShells + 1]>(qrow);
   const int n_sb = a.shells_pad / kQffShells;
   const int f = (int)blockIdx.x / n_sb, s0 = ((int)blockIdx.x % n_sb) * kQffShells;
   const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
   const int s = s0 + warp;
-  const double *row = a.Q + ((size_t)f * a.n_shells + (s < a.n_shells ? s : 0)) * a.n_lm;
+  const bool on = s < a.n_shells;
+  const double *row = a.Q + ((size_t)f * a.n_shells + (on ? s : 0)) * a.n_lm;
+  float2 *Qfb = a.Qf + (size_t)f * a.n_lm * a.shells_pad + s0;
   unsigned long long mb = 0ull;
-  if (s < a.n_shells)
+  if (a.one_pass) {
+    float2 *mine = qrow + (size_t)warp * a.n_lm;
+#pragma unroll 8
+    for (int k = lane; k < a.n_lm; k += 32) {
+      const double x = on ? row[k] : 0.0;
+      mb = max(mb, (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull);
+      mine[k] = *reinterpret_cast<const float2 *>(&x);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
+    const int exm = (int)(mb >> 52);
+    const int qe = exm == 0 ? 0 : exm - 1022;
+    if (lane == 0 && on) a.qexp[(size_t)f * a.n_shells + s] = qe;
+    for (int k = lane; k < a.n_lm; k += 32) {
+      const float2 b = mine[k];
+      mine[k] = ff_split(*reinterpret_cast<const double *>(&b), qe);
+    }
+    __syncthreads();
+    for (int i = (int)threadIdx.x; i < a.n_lm * kQffShells; i += (int)blockDim.x) {
+      const int k = i / kQffShells, c = i - k * kQffShells;
+      Qfb[(size_t)k * a.shells_pad + c] = qrow[(size_t)c * a.n_lm + k];
+    }
+    return;
+  }
+  if (on)
     for (int k = lane; k < a.n_lm; k += 32)
       mb = max(mb, (unsigned long long)__double_as_longlong(row[k]) & 0x7FFFFFFFFFFFFFFFull);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
   const int exm = (int)(mb >> 52);
   const int qe = exm == 0 ? 0 : exm - 1022;
-  if (lane == 0 && s < a.n_shells) a.qexp[(size_t)f * a.n_shells + s] = qe;
-  float2 *Qfb = a.Qf + (size_t)f * a.n_lm * a.shells_pad + s0;
+  if (lane == 0 && on) a.qexp[(size_t)f * a.n_shells + s] = qe;
   for (int k0 = 0; k0 < a.n_lm; k0 += kQffChunk) {
     const int kn = min(kQffChunk, a.n_lm - k0);
-    for (int k = lane; k < kn; k += 32)
-      tile[k][warp] = s < a.n_shells ? ff_split(row[k0 + k], qe) : make_float2(0.f, 0.f);
+    for (int k = lane; k < kn; k += 32) tile[k][warp] = on ? ff_split(row[k0 + k], qe) : make_float2(0.f, 0.f);
     __syncthreads();
     for (int i = (int)threadIdx.x; i < kn * kQffShells; i += (int)blockDim.x) {
       const int k = i / kQffShells, c = i - k * kQffShells;
@@ -2423,28 +2451,21 @@ __device__ __forceinline__ float2 ff_sum(float2 a, float2 b, float sg) {
   return make_float2(h, __fsub_rn(lo, __fsub_rn(h, s)));
 }
 
-// x 2^(64 - e) truncated to an integer, for |x| < 2^(e - 1)
-__device__ __forceinline__ long long ff_fixed_part(float x, int e) {
-  const uint32_t u = __float_as_uint(x);
-  const int ex = (int)((u >> 23) & 0xFFu);
-  const uint32_t sig = ex ? ((u & 0x7FFFFFu) | 0x800000u) : (u & 0x7FFFFFu);
-  const int sh = (ex ? ex : 1) - 86 - e;                // x 2^(64 - e) = sig 2^sh, sh <= 39
-  unsigned long long m = 0ull;
-  if (sh >= 0)
-    m = (unsigned long long)sig << sh;
-  else if (sh > -32)
-    m = sig >> -sh;
-  return (u >> 31) ? -(long long)m : (long long)m;
-}
-
 // One row of float-float values cut into digits: lane L holds slots
 // 64 g + 2 L and 64 g + 2 L + 1.  The row's scale 2^e: the largest |hi|
 // stepped up by one ulp bounds every |hi + lo| (|lo| is at most half an ulp),
-// so every value is below 2^(e - 1); X = round(|value| 2^(48 - e)) <= 2^47
-// from 16 guard bits, and its balanced base-256 digits in one step: with
-// Y = X + 127 (1 + 2^8 + ... + 2^32), the low five digits are Y's bytes less
-// 127 (each in [-127, 128], the carries done by the addition) and the top
-// one is Y >> 40.  qe: the power of two the values carry.
+// so every value is below 2^(e - 1).  X = round(|value| 2^(48 - e)) <= 2^47
+// on the fp32 pipe, 16 bits at a time: A = |hi| 2^(48 - e) and B = +-lo
+// 2^(48 - e) (exact power-of-two scalings), T2 = rint(A 2^-32), T1 =
+// rint((A - T2 2^32) 2^-16) (the remainders exact by fused multiply-add), T0
+// = rint(remainder + B), each rint by adding and removing 1.5 2^23 (whose
+// bit pattern then holds the integer), X = T2 2^32 + T1 2^16 + T0.  The last
+// addition rounds only where the remainder and B span more than 24 bits, so
+// X is the nearest integer except within 2^-9 of a tie.  Then the balanced
+// base-256 digits in one step: with Y = X + 127 (1 + 2^8 + ... + 2^32), the
+// low five digits are Y's bytes less 127 (each in [-127, 128], the carries
+// done by the addition) and the top one is Y >> 40.  qe: the power of two
+// the values carry.
 template <int NG>
 __device__ __forceinline__ void ff_row(const float2 (&v)[NG][2], int lane, __nv_bfloat16 *dst, size_t stride,
                                        int *gexp, int nt, int bias, int qe) {
@@ -2459,17 +2480,30 @@ __device__ __forceinline__ void ff_row(const float2 (&v)[NG][2], int lane, __nv_
   mb = __reduce_max_sync(0xffffffffu, mb);
   const int exm = (int)(mb >> 23);
   const int e = exm - 125;                              // every |value| < 2^(exm - 126) = 2^(e - 1)
+  const int K = 48 - e, K1 = K >> 1, K2 = K - K1;       // 2^K as two normal factors
+  const float p1 = __uint_as_float((uint32_t)(K1 + 127) << 23), p2 = __uint_as_float((uint32_t)(K2 + 127) << 23);
+  constexpr float kM = 12582912.f;                      // 1.5 2^23
+  constexpr uint32_t kMBits = 0x4B400000u;
   constexpr uint32_t kBiasBits = 0x45C0u;               // bf16 of kOzBiasG (6144)
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
     uint32_t bits[2][6], sgn[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const long long V = ff_fixed_part(v[g][h].x, e) + ff_fixed_part(v[g][h].y, e);
-      const unsigned long long A = (unsigned long long)(V < 0 ? -V : V);
-      const unsigned long long Y = ((A + 32768ull) >> 16) + 0x7F7F7F7F7Full;
+      const float hi = v[g][h].x, lo = v[g][h].y;
+      sgn[h] = __float_as_uint(hi) >> 31;
+      const float A = __fmul_rn(__fmul_rn(fabsf(hi), p1), p2);
+      const float B = __fmul_rn(__fmul_rn(sgn[h] ? -lo : lo, p1), p2);
+      const float s2 = __fadd_rn(__fmul_rn(A, 0x1p-32f), kM);
+      const float R1 = __fmaf_rn(-__fsub_rn(s2, kM), 0x1p32f, A);
+      const float s1 = __fadd_rn(__fmul_rn(R1, 0x1p-16f), kM);
+      const float R2 = __fmaf_rn(-__fsub_rn(s1, kM), 0x1p16f, R1);
+      const float s0 = __fadd_rn(__fadd_rn(R2, B), kM);
+      const long long X = ((long long)(int)(__float_as_uint(s2) - kMBits) << 32) +
+                          ((long long)(int)(__float_as_uint(s1) - kMBits) << 16) +
+                          (long long)(int)(__float_as_uint(s0) - kMBits);
+      const unsigned long long Y = (unsigned long long)X + 0x7F7F7F7F7Full;
       const uint32_t ylo = (uint32_t)Y, yhi = (uint32_t)(Y >> 32);
-      sgn[h] = V < 0 ? 1u : 0u;
       bits[h][0] = __float_as_uint(__fsub_rn(__uint_as_float(0x4B000000u | (yhi >> 8)), 8388608.f));
       bits[h][1] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(yhi, 0x4B000000u, 0x7540)), 8388735.f));
       bits[h][2] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7543)), 8388735.f));
@@ -2687,6 +2721,235 @@ __global__ void __launch_bounds__(512, 2) k_theta_ff(OzThetaFFArgs a) {
   }
 }
 
+// The polar stage of the analysis in float-float arithmetic (the Ozaki
+// path): A[lm] = sum_{j < ceil(n_theta / 2)} T_j[lm] (F_j + s F_j')[t], with
+// s = +1 for even l + m and -1 for odd (the cell integrals of P_l^m sin theta
+// have the parity of l + m; a middle row enters once), as in k_sep_theta.
+// One block per shell: its F rows scaled by a power of two (the shell's
+// largest |F| below 1) and split into fp32 pairs, the mirrored sums and
+// differences formed in float-float and staged in shared memory, then one
+// thread per mode with the pair-split table; the result widened to float64
+// and scaled back.
+constexpr int kSepFFRegs = 8;    // mirrored (F_j, F_j') pairs per thread held in registers
+constexpr int kSepFFShells = 2;  // shells per block: each table value read serves them all
+
+__global__ void __launch_bounds__(512) k_sep_theta_ff(int n_shells, int n_theta, int n_lm, int nt, int nt_pad,
+                                                      const float2 *__restrict__ tbf, const double *__restrict__ F,
+                                                      double *__restrict__ A) {
+  extern __shared__ float2 sdf[];                          // per shell [2][half][nt_pad]: S, then D
+  __shared__ unsigned long long red[16];
+  __shared__ int qes[kSepFFShells];
+  const int half = (n_theta + 1) >> 1;
+  const int shell0 = (int)blockIdx.x * kSepFFShells;
+  const int tid = (int)threadIdx.x, nthr = (int)blockDim.x;
+  const size_t per_shell = (size_t)2 * half * nt_pad;
+  // pair e = j nt + t (j < half, t < nt): F_j[t] and F_j'[t], all loads in
+  // flight together when the shell fits in registers
+  const int n_pairs = half * nt;
+  const bool in_regs = n_pairs <= kSepFFRegs * nthr;
+  for (int sh = 0; sh < kSepFFShells; ++sh) {
+    float2 *sd = sdf + sh * per_shell;
+    if (shell0 + sh >= n_shells) {
+      for (int e = tid; e < (int)per_shell; e += nthr) sd[e] = make_float2(0.f, 0.f);
+      continue;
+    }
+    const double *Fs = F + (size_t)(shell0 + sh) * n_theta * nt_pad;
+    double fa[kSepFFRegs], fb[kSepFFRegs];
+    unsigned long long mb = 0ull;
+    if (in_regs) {
+#pragma unroll
+      for (int i = 0; i < kSepFFRegs; ++i) {
+        const int e = tid + i * nthr;
+        const int j = e / nt, t = e - j * nt, jm = n_theta - 1 - j;
+        const bool ok = e < n_pairs;
+        fa[i] = ok ? Fs[(size_t)j * nt_pad + t] : 0.0;
+        fb[i] = ok && jm != j ? Fs[(size_t)jm * nt_pad + t] : 0.0;
+      }
+#pragma unroll
+      for (int i = 0; i < kSepFFRegs; ++i)
+        mb = max(mb, max((unsigned long long)__double_as_longlong(fa[i]) & 0x7FFFFFFFFFFFFFFFull,
+                         (unsigned long long)__double_as_longlong(fb[i]) & 0x7FFFFFFFFFFFFFFFull));
+    } else {
+      for (int e = tid; e < n_pairs; e += nthr) {
+        const int j = e / nt, t = e - j * nt, jm = n_theta - 1 - j;
+        mb = max(mb, (unsigned long long)__double_as_longlong(Fs[(size_t)j * nt_pad + t]) & 0x7FFFFFFFFFFFFFFFull);
+        mb = max(mb, (unsigned long long)__double_as_longlong(Fs[(size_t)jm * nt_pad + t]) & 0x7FFFFFFFFFFFFFFFull);
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
+    if ((tid & 31) == 0) red[tid >> 5] = mb;
+    __syncthreads();
+    mb = 0ull;
+    for (int w = 0; w < (nthr >> 5); ++w) mb = max(mb, red[w]);
+    const int exm = (int)(mb >> 52);
+    const int qe = exm == 0 ? 0 : exm - 1022;              // |F| 2^-qe < 1
+    if (tid == 0) qes[sh] = qe;
+    if (in_regs) {
+#pragma unroll
+      for (int i = 0; i < kSepFFRegs; ++i) {
+        const int e = tid + i * nthr;
+        if (e >= n_pairs) continue;
+        const int j = e / nt, t = e - j * nt, jm = n_theta - 1 - j;
+        const float2 a = ff_split(fa[i], qe);
+        float2 S = a, D = a;
+        if (jm != j) {
+          const float2 b = ff_split(fb[i], qe);
+          S = ff_sum(a, b, 1.f);
+          D = ff_sum(a, b, -1.f);
+        }
+        sd[j * nt_pad + t] = S;
+        sd[(size_t)(half + j) * nt_pad + t] = D;
+      }
+    } else {
+      for (int e = tid; e < n_pairs; e += nthr) {
+        const int j = e / nt, t = e - j * nt, jm = n_theta - 1 - j;
+        const float2 a = ff_split(Fs[(size_t)j * nt_pad + t], qe);
+        float2 S = a, D = a;
+        if (jm != j) {
+          const float2 b = ff_split(Fs[(size_t)jm * nt_pad + t], qe);
+          S = ff_sum(a, b, 1.f);
+          D = ff_sum(a, b, -1.f);
+        }
+        sd[j * nt_pad + t] = S;
+        sd[(size_t)(half + j) * nt_pad + t] = D;
+      }
+    }
+    __syncthreads();                                         // red[] is read before the next shell writes it
+  }
+  for (int idx = tid; idx < n_lm; idx += nthr) {
+    const int l = degree_of_mode(idx);
+    const int t = idx - l * l;
+    const size_t coff = ((((l + ((t + 1) >> 1)) & 1) != 0) ? (size_t)half * nt_pad : 0) + t;
+    const float2 *p = tbf + idx;
+    float2 acc[kSepFFShells];
+#pragma unroll
+    for (int sh = 0; sh < kSepFFShells; ++sh) acc[sh] = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int j = 0; j < half; ++j) {
+      const float2 tv = __ldg(p + (size_t)j * n_lm);
+#pragma unroll
+      for (int sh = 0; sh < kSepFFShells; ++sh) ff_fma(sdf[sh * per_shell + coff + (size_t)j * nt_pad], tv, acc[sh]);
+    }
+#pragma unroll
+    for (int sh = 0; sh < kSepFFShells; ++sh) {
+      if (shell0 + sh >= n_shells) break;
+      const int qe = qes[sh];
+      double v = f32_to_f64(acc[sh].x) + f32_to_f64(acc[sh].y);
+      // times 2^qe on the exponent field (a normal result), else by ldexp
+      const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+      const int ex = (int)((u >> 52) & 0x7FFu);
+      if (ex != 0) {
+        if (ex + qe > 0 && ex + qe < 2047)
+          v = __longlong_as_double((long long)(u + ((unsigned long long)(long long)qe << 52)));
+        else
+          v = ldexp(v, qe);
+      }
+      A[(size_t)(shell0 + sh) * n_lm + idx] = v;
+    }
+  }
+}
+
+// threads of k_sep_theta_ff: the modes in as few rounds of at most 512
+// threads as possible, whole warps
+static int sep_theta_ff_threads(int n_lm) {
+  const int rounds = (n_lm + 511) / 512;
+  const int per = (n_lm + rounds - 1) / rounds;
+  return (per + 31) / 32 * 32;
+}
+
+// The other patch's moments in each frame (the combination of the two
+// patches, as k_rotate_moments) in float-float arithmetic for the Ozaki path:
+//   Atot[p][n][j] = A[p][n][j] + sum_i D^l_ij A[1-p][n][i],  i, j of degree l,
+// the sum over the x-reflection parity class of j (the other class of D^l is
+// zero).  Per radius and degree, both patches' moments are scaled by one
+// power of two (the largest |A| of the degree below 1: D^l maps a degree
+// onto itself) and split into fp32 pairs; the rotated sum is widened to
+// float64, scaled back and added to the own moment.  One block per (degree,
+// kRotRadii radii), the highest degrees first: D^l staged in shared memory
+// once, a warp per radius stages the moments (raw, then their pairs in
+// place), then a thread per (radius, mode) for both patches.
+constexpr int kRotRadii = 4;
+
+__global__ void __launch_bounds__(256) k_rotate_ff(int n_r, int n_lm, int lmax, const float2 *__restrict__ Df,
+                                                   const double *__restrict__ A, double *__restrict__ Atot) {
+  extern __shared__ float2 rsm[];                          // [w][w] D^l, then [kRotRadii][2 w] moment pairs
+  __shared__ int rexp[kRotRadii];
+  const int tiles = (n_r + kRotRadii - 1) / kRotRadii;
+  const int l = lmax - (int)blockIdx.x / tiles;
+  const int n0 = ((int)blockIdx.x % tiles) * kRotRadii;
+  const int w = 2 * l + 1, base = l * l;
+  const int tid = (int)threadIdx.x, nthr = (int)blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+  const float2 *Dl = Df + (size_t)l * (4 * l * l - 1) / 3;
+  for (int i = tid; i < w * w; i += nthr) rsm[i] = Dl[i];
+  float2 *xs = rsm + w * w;
+  for (int r = warp; r < kRotRadii; r += nw) {
+    const int n = n0 + r;
+    if (n >= n_r) continue;
+    const double *a0 = A + (size_t)n * n_lm + base, *a1 = A + ((size_t)n_r + n) * n_lm + base;
+    float2 *x = xs + r * 2 * w;
+    unsigned long long mb = 0ull;
+    for (int i = lane; i < 2 * w; i += 32) {
+      const double v = i < w ? a0[i] : a1[i - w];
+      mb = max(mb, (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull);
+      x[i] = *reinterpret_cast<const float2 *>(&v);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
+    const int exm = (int)(mb >> 52);
+    const int qe = exm == 0 ? 0 : exm - 1022;
+    if (lane == 0) rexp[r] = qe;
+    for (int i = lane; i < 2 * w; i += 32) {
+      const float2 b = x[i];
+      x[i] = ff_split(*reinterpret_cast<const double *>(&b), qe);
+    }
+  }
+  __syncthreads();
+  for (int o = tid; o < kRotRadii * w; o += nthr) {
+    const int r = o / w, jj = o - r * w, n = n0 + r;
+    if (n >= n_r) continue;
+    const float2 *x0 = xs + r * 2 * w, *x1 = x0 + w;
+    float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);   // into patch 0, into patch 1
+    // the class of jj: index 0 and i % 4 in {2, 3} (even), or 1 and i % 4 in {0, 1}
+    const bool even = jj == 0 || (jj & 3) >= 2;
+    int i = even ? 0 : 1;
+    {
+      const float2 d = rsm[i * w + jj];
+      ff_fma(x1[i], d, s0);
+      ff_fma(x0[i], d, s1);
+    }
+#pragma unroll 2
+    for (i = even ? 2 : 4; i < w; i += 4) {
+      const float2 d = rsm[i * w + jj];
+      ff_fma(x1[i], d, s0);
+      ff_fma(x0[i], d, s1);
+      if (i + 1 < w) {
+        const float2 e = rsm[(i + 1) * w + jj];
+        ff_fma(x1[i + 1], e, s0);
+        ff_fma(x0[i + 1], e, s1);
+      }
+    }
+    const int qe = rexp[r];
+    double rr[2] = {f32_to_f64(s0.x) + f32_to_f64(s0.y), f32_to_f64(s1.x) + f32_to_f64(s1.y)};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      // times 2^qe on the exponent field (a normal result), else by ldexp
+      const unsigned long long u = (unsigned long long)__double_as_longlong(rr[k]);
+      const int ex = (int)((u >> 52) & 0x7FFu);
+      if (ex != 0) {
+        if (ex + qe > 0 && ex + qe < 2047)
+          rr[k] = __longlong_as_double((long long)(u + ((unsigned long long)(long long)qe << 52)));
+        else
+          rr[k] = ldexp(rr[k], qe);
+      }
+    }
+    const size_t j0 = (size_t)n * n_lm + base + jj, j1 = ((size_t)n_r + n) * n_lm + base + jj;
+    Atot[j0] = A[j0] + rr[0];
+    Atot[j1] = A[j1] + rr[1];
+  }
+}
+
 // The weighted densities of the separable analysis, rho w, as digit rows for
 // the analysis: one warp per row (shell, j); lane L takes the pairs
 // k = 2 L + 64 c.  rho w is the float64 product of the CUDA-core path; the
@@ -2806,6 +3069,8 @@ struct yy_oz_tables {
   float2 *Qf;                   // [3][n_lm][shells_pad]: scaled coefficients as fp32 pairs (k_q_ff)
   int *qexp;                    // [3][n_shells]: their scales
   float2 *Pf[2];                // [n_theta][n_lm]: P and dP/dtheta as fp32 pairs
+  float2 *tbf;                  // [ceil(n_theta / 2)][n_lm]: the analysis table T as fp32 pairs
+  float2 *Df;                   // [sum_l (2l+1)^2]: the rotation D^l as fp32 pairs (two patches)
   void *trig;                   // slices of trig / 2: [6][b_rows_pad][64]
   yy::PairMaps maps;
   // analysis (FormOzaki in fills of kFillK): rho w digit rows as operand A, the azimuthal table as operand B
@@ -2833,6 +3098,8 @@ static void free_oz(yy_oz_tables *o) {
   if (o->qexp) cudaFree(o->qexp);
   for (int k = 0; k < 2; ++k)
     if (o->Pf[k]) cudaFree(o->Pf[k]);
+  if (o->tbf) cudaFree(o->tbf);
+  if (o->Df) cudaFree(o->Df);
   if (o->an_x) cudaFree(o->an_x);
   if (o->an_exp) cudaFree(o->an_exp);
   if (o->an_az) cudaFree(o->an_az);
@@ -2933,6 +3200,18 @@ static yy_status ozaki_prepare_analysis(yy_grid *g, yy_oz_tables *o) {
   return YY_OK;
 }
 
+// the polar stage of the analysis after the Ozaki azimuthal stage
+static cudaError_t ozaki_theta_analysis(yy_grid *g, cudaStream_t s) {
+  const int half = (g->n_theta + 1) / 2;
+  const size_t smem = (size_t)kSepFFShells * 2 * half * g->sep_nt_pad * sizeof(float2);
+  if (smem > 200 * 1024) return separable_theta_f64(g, s);
+  const int shells = grid_rows(g);
+  k_sep_theta_ff<<<(unsigned)((shells + kSepFFShells - 1) / kSepFFShells), sep_theta_ff_threads(g->n_lm), smem, s>>>(
+      shells, g->n_theta, g->n_lm, 2 * g->lmax + 1, g->sep_nt_pad, g->oz->tbf, g->sep_F, g->A);
+  note_launch(g, "k_sep_theta_ff", s);
+  return cudaGetLastError();
+}
+
 cudaError_t ozaki_analysis(yy_grid *g, const double *ry, const double *rg, cudaStream_t s) {
   typedef FormOzaki F;
   yy_oz_tables *o = g->oz;
@@ -2977,7 +3256,7 @@ cudaError_t ozaki_analysis(yy_grid *g, const double *ry, const double *rg, cudaS
     e = cudaLaunchKernelEx(&cfg, k_oz_analysis, o->an_maps2, z);
     note_launch(g, "k_oz_analysis", s);
     if (e != cudaSuccess) return e;
-    return separable_theta_f64(g, s);
+    return ozaki_theta_analysis(g, s);
   }
   PairArgs a = {};
   a.stages = o->an_stages;
@@ -3010,7 +3289,17 @@ cudaError_t ozaki_analysis(yy_grid *g, const double *ry, const double *rg, cudaS
   e = cudaLaunchKernelEx(&cfg, k_tc_pair<F, 3>, o->an_maps, a);
   note_launch(g, "k_tc_pair<FormOzaki,3>/analysis", s);
   if (e != cudaSuccess) return e;
-  return separable_theta_f64(g, s);
+  return ozaki_theta_analysis(g, s);
+}
+
+cudaError_t ozaki_rotate(yy_grid *g, cudaStream_t s) {
+  if (g->n_patch == 1) return cudaSuccess;   // polar grid: the scans read A itself
+  const int w = 2 * g->lmax + 1;
+  const size_t smem = ((size_t)w * w + (size_t)kRotRadii * 2 * w) * sizeof(float2);
+  const unsigned blocks = (unsigned)((g->lmax + 1) * ((g->n_r + kRotRadii - 1) / kRotRadii));
+  k_rotate_ff<<<blocks, 256, smem, s>>>(g->n_r, g->n_lm, g->lmax, g->oz->Df, g->A, g->Atot);
+  note_launch(g, "k_rotate_ff", s);
+  return cudaGetLastError();
 }
 
 yy_status ozaki_prepare(yy_grid *g) {
@@ -3064,6 +3353,8 @@ yy_status ozaki_prepare(yy_grid *g) {
     A((void **)&o->Qf, (size_t)3 * g->n_lm * o->shells_pad * sizeof(float2));
     A((void **)&o->qexp, (size_t)3 * grid_rows(g) * sizeof(int));
     for (int k = 0; k < 2; ++k) A((void **)&o->Pf[k], (size_t)g->n_theta * g->n_lm * sizeof(float2));
+    A((void **)&o->tbf, (size_t)((g->n_theta + 1) / 2) * g->n_lm * sizeof(float2));
+    if (g->n_patch == 2) A((void **)&o->Df, rotation_table_size(g->lmax) * sizeof(float2));
     for (int f = 0; f < 4 && e == cudaSuccess; ++f) e = cudaMemset(o->G[f], 0, g_bytes);
     if (e == cudaSuccess) {
       // g_phi's polar factors (k_theta_ozaki): the same cell centres as the
@@ -3078,14 +3369,21 @@ yy_status ozaki_prepare(yy_grid *g) {
       const size_t ne = (size_t)g->n_theta * g->n_lm;
       std::vector<double> tb(ne);
       std::vector<float2> tf(ne);
-      const double *tsrc[2] = {g->sep_P, g->sep_dP};
-      for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-        e = cudaMemcpy(tb.data(), tsrc[k], ne * sizeof(double), cudaMemcpyDeviceToHost);
-        for (size_t i = 0; i < ne; ++i) {
+      const double *tsrc[4] = {g->sep_P, g->sep_dP, g->tbar, g->rot};
+      float2 *tdst[4] = {o->Pf[0], o->Pf[1], o->tbf, o->Df};
+      const size_t tn[4] = {ne, ne, (size_t)((g->n_theta + 1) / 2) * g->n_lm,
+                            g->n_patch == 2 ? rotation_table_size(g->lmax) : 0};
+      const size_t tmax = std::max(ne, tn[3]);
+      tb.resize(tmax);
+      tf.resize(tmax);
+      for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+        if (tn[k] == 0) continue;
+        e = cudaMemcpy(tb.data(), tsrc[k], tn[k] * sizeof(double), cudaMemcpyDeviceToHost);
+        for (size_t i = 0; i < tn[k]; ++i) {
           const float h = (float)tb[i];
           tf[i] = make_float2(h, (float)(tb[i] - (double)h));
         }
-        if (e == cudaSuccess) e = cudaMemcpy(o->Pf[k], tf.data(), ne * sizeof(float2), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(tdst[k], tf.data(), tn[k] * sizeof(float2), cudaMemcpyHostToDevice);
       }
       if (e == cudaSuccess) e = cudaMemset(o->Qf, 0, (size_t)3 * g->n_lm * o->shells_pad * sizeof(float2));
       // the largest dynamic shared memory of any supported degree (l_max 63),
@@ -3093,7 +3391,10 @@ yy_status ozaki_prepare(yy_grid *g) {
       const int ff_max = (int)theta_ff_smem(64 * 64, 128);
       if (e == cudaSuccess &&
           (cudaFuncSetAttribute(k_theta_ff<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ff_max) != cudaSuccess ||
-           cudaFuncSetAttribute(k_theta_ff<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, ff_max) != cudaSuccess))
+           cudaFuncSetAttribute(k_theta_ff<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, ff_max) != cudaSuccess ||
+           cudaFuncSetAttribute(k_sep_theta_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess ||
+           cudaFuncSetAttribute(k_rotate_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess ||
+           cudaFuncSetAttribute(k_q_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQffOnePassSmem) != cudaSuccess))
         e = cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? YY_ERR_OOM : YY_ERR_CUDA;
@@ -3203,7 +3504,10 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
   qa.Q = g->Q;
   qa.Qf = o->Qf;
   qa.qexp = o->qexp;
-  k_q_ff<<<(unsigned)(n_q * (o->shells_pad / kQffShells)), 32 * kQffShells, 0, s>>>(qa);
+  const size_t qff_smem = (size_t)kQffShells * g->n_lm * sizeof(float2);
+  qa.one_pass = qff_smem <= kQffOnePassSmem ? 1 : 0;
+  k_q_ff<<<(unsigned)(n_q * (o->shells_pad / kQffShells)), 32 * kQffShells,
+           qa.one_pass ? qff_smem : (size_t)kQffChunk * (kQffShells + 1) * sizeof(float2), s>>>(qa);
   note_launch(g, "k_q_ff", s);
   OzThetaFFArgs fa = {};
   fa.n_shells = ta.n_shells;
