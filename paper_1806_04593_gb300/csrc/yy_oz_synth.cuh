@@ -272,6 +272,7 @@ k_oz_synth(const __grid_constant__ OzSynthMaps maps, const __grid_constant__ OzS
       const int cell = (2 * ct + rank) * kPairRows + quarter * 32 + lane;
       const bool cell_ok = cell < a.cells;
       const int ce = cell_ok ? J.cell_exp[cell] : 0;
+      const bool row_ok = i64_ldexp_row_ok(ce + 16);
       __syncwarp();   // the previous tile's row pointers are no longer read
       rowp[lane] = !cell_ok ? nullptr
                    : (cell < a.out_split) ? J.out0 + (size_t)cell * a.ldo
@@ -330,7 +331,7 @@ k_oz_synth(const __grid_constant__ OzSynthMaps maps, const __grid_constant__ OzS
             for (int j = 0; j < 8; ++j) {
               const long long V = ((long long)(int)(u0[j] - kOzBiasBits) << 32) +
                                   ((long long)mid[c0 + j] << 16) + (long long)lo[c0 + j];
-              ebuf[lane * kOzEpiPad + j] = i64_ldexp(V, ce + 16);
+              ebuf[lane * kOzEpiPad + j] = row_ok ? i64_ldexp_row(V, ce + 16) : i64_ldexp(V, ce + 16);
             }
             __syncwarp();
             const int col0 = col_base + c0;

@@ -799,7 +799,7 @@ __global__ void __launch_bounds__(256) k_theta_g(ThetaArgs a) {
   }
 }
 
-// The same polar stage in the layout of k_theta_ozaki: one warp per (field,
+// The polar stage of the separable tensor-core synthesis: one warp per (field,
 // shell, mirrored row pair j, j' = n_theta - 1 - j), the terms of even and of
 // odd l + m summed apart so that one pass gives both rows (P and m P / sin
 // theta keep the parity of l + m across the equator, dP/dtheta takes the
@@ -809,7 +809,7 @@ __global__ void __launch_bounds__(256) k_theta_g(ThetaArgs a) {
 // in float64 into add[] (its operand column stays zero).  g_phi needs no sum
 // of its own: its coefficients are -Q / r and its table m / sin theta times
 // Phi's, so Phi's warps form it from their values of the other slot of the
-// same m (as in k_theta_ozaki).
+// same m.
 struct ThetaF32Args {
   int n_shells, n_theta, n_r, lmax, n_lm, nt, k_pad, n_jobs, rows_pad;
   const float *Q32;             // [3][n_shells][n_lm]: Phi, g_r and angular coefficients in fp32
@@ -2112,19 +2112,6 @@ cudaError_t tc_synthesis(yy_grid *g, yy_precision prec, double *py, double *pg, 
 // exact per level, and rounds each value once.  The monopole slot t = 0 is
 // part of the contraction: it is exact too.
 
-struct OzThetaArgs {
-  int n_shells, n_theta, lmax, n_lm, nt, n_jobs, rows_pad;
-  int gk;                       // slots of a G row (64 or 128: 64 NG)
-  int n_r;                      // shells of one patch
-  const double *inv_sin;        // [n_theta]: 1 / sin theta_j at the polar cell centres
-  const double *inv_r;          // [n_r]: the angular coefficients are -Q inv_r[n]
-  const double *Q;              // [3][n_shells][n_lm]: Phi, g_r and angular coefficients
-  const double *tab[3];         // [n_theta][n_lm]: P, dP/dtheta, m P / sin theta (float64)
-  __nv_bfloat16 *G[4];          // per field: slices [6][rows_pad][gk]
-  int *gexp[4];                 // per field: [rows_pad] power of two of a unit level-5 sum
-  int bias;                     // write the bias digits of output mode 4 in slots nt and nt + 1
-};
-
 // Balanced base-256 digits of X < 2^48 (most significant first): each
 // digit taken in [-127, 128] with a carry into the next; the top one is at
 // most 128 for X <= 2^47.
@@ -2142,182 +2129,14 @@ __host__ __device__ __forceinline__ void oz_digits(unsigned long long X, int (&d
   d[0] = (int)X;
 }
 
-// One row's digits: this lane's slots 64 g + lane and 64 g + 63 - lane
-// (g < NG) hold the float64 bit patterns b[g][0] and b[g][1].  The row's
-// scale 2^e (e from the largest |G| of the row: every |G| 2^-e < 1/2) and the
-// digits of X = round(|G| 2^(48 - e)) <= 2^47, taken from the float64 bits,
-// each with the sign of G.  A row of zeros (or of values below the normal
-// range) gets zero digits.
-template <int NG>
-__device__ __forceinline__ void oz_theta_row(const unsigned long long (&b)[NG][2], int lane, __nv_bfloat16 *dst,
-                                             size_t stride, int *gexp, int nt, int bias) {
-  unsigned long long mb = 0ull;
-#pragma unroll
-  for (int g = 0; g < NG; ++g) mb = max(mb, max(b[g][0] & 0x7FFFFFFFFFFFFFFFull, b[g][1] & 0x7FFFFFFFFFFFFFFFull));
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
-  const int exm = (int)(mb >> 52);                 // biased exponent of the largest |G|
-  const int e = exm - 1021;                        // |G| < 2^(exm - 1022) = 2^(e - 1)
-#pragma unroll
-  for (int g = 0; g < NG; ++g)
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const unsigned long long bits = b[g][h];
-      const int t = 64 * g + (h == 0 ? lane : 63 - lane);
-      const int ex = (int)((bits >> 52) & 0x7FFu);
-      const int sh = 1027 - ex + e;                // |G| 2^(48 - e) = significand >> sh, sh >= 6
-      unsigned long long X = 0ull;
-      if (exm != 0 && ex != 0 && sh < 64)
-        X = ((((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> (sh - 1)) + 1ull) >> 1;   // round half up
-      int d[6];
-      oz_digits(X, d);
-      // the bias digits of output mode 4 (slots nt and nt + 1 hold G = 0)
-      const int bias_sl = bias ? (t == nt ? 0 : t == nt + 1 ? 1 : -1) : -1;
-#pragma unroll
-      for (int sl = 0; sl < 6; ++sl) {
-        const float v = sl == bias_sl ? kOzBiasG : ((bits >> 63) ? -(float)d[sl] : (float)d[sl]);
-        dst[sl * stride + t] = __float2bfloat16_rn(v);
-      }
-    }
-  // value = 2^(e + 1 - 64) (digit sums): trig scale 2^1, digit weights 2^-64
-  if (lane == 0) *gexp = exm == 0 ? 0 : e + 1 - 64;
-}
-
-// One warp per (field, shell, mirrored row pair j, j' = n_theta - 1 - j).
-// The polar cells are symmetric about the equator (theta_j + theta_j' = pi on
-// the Yin-Yang patch and on the polar grid), and P_l^m(cos(pi - theta)) =
-// (-1)^(l + m) P_l^m(cos theta): with E and O the sums over the terms of even
-// and of odd l + m at row j, G = E + O at j and E - O at j' (for P and
-// m P / sin theta; dP/dtheta has the opposite parity, -(E - O) at j').  So one
-// pass over the coefficients gives both rows.  Lane L takes the slots
-// t = 64 g + L and 64 g + 63 - L, g < NG (G rows of 64 NG slots; slot t sums
-// l_max + 1 - (t + 1) / 2 terms, so the pair's counts add up to about the
-// same in every lane), l from l_max down in steps of two (terms l and l - 1:
-// one of each parity), g_phi with the cos / sin slots swapped, one pair of
-// accumulators that moves from slot t0 to t1 by register moves.
-template <int NG>
-__global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
-  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  const int half = (a.n_theta + 1) >> 1;
-  const int pairs = a.n_shells * half;
-  if (warp >= pairs * a.n_jobs) return;
-  const int f = warp / pairs, pr = warp % pairs;
-  const int shell = pr / half, j = pr % half, jm = a.n_theta - 1 - j;
-  const int qb = f < 2 ? f : 2;
-  const double *q = a.Q + ((size_t)qb * a.n_shells + shell) * a.n_lm;
-  // parameter arrays read at constant indexes (a dynamic index copies the
-  // whole argument block to local memory)
-  const double *tab = f <= 1 ? a.tab[0] : (f == 2 ? a.tab[1] : a.tab[2]);
-  const double *tj = tab + (size_t)j * a.n_lm;
-  const int L = a.lmax;
-  unsigned long long gb[NG][2], rb[NG][2];   // this lane's slots at rows j and j'
-#pragma unroll
-  for (int g = 0; g < NG; ++g) {
-    const int t0 = 64 * g + lane, t1 = 64 * g + 63 - lane;
-    const int m0 = (t0 + 1) / 2, m1 = (t1 + 1) / 2;
-    int s0 = t0, s1 = t1;                             // coefficient slots
-    if (f == 3) {                                     // cos slot <- sin coefficient, sin slot <- cos
-      s0 = (t0 & 1) ? t0 + 1 : t0 - 1;
-      s1 = (t1 & 1) ? t1 + 1 : t1 - 1;
-    }
-    const int n0 = (t0 < a.nt && (f < 3 || t0 > 0)) ? L + 1 - m0 : 0;
-    const int n1 = (t1 < a.nt && (f < 3 || t1 > 0)) ? L + 1 - m1 : 0;
-    const int k0 = (n0 + 1) >> 1, k1 = (n1 + 1) >> 1;  // steps of two terms per slot
-    // a1: terms with l = l_max, l_max - 2, ...; a2: l = l_max - 1, l_max - 3, ...
-    double a1 = 0.0, a2 = 0.0, h1 = 0.0, h2 = 0.0;
-    const double *pq = q + L * L + s0, *pt = tj + L * L + t0;
-    int l = L, m = m0;
-    for (int it = 0; it < k0 + k1; ++it) {
-      if (it == k0) {
-        h1 = a1;
-        h2 = a2;
-        a1 = 0.0;
-        a2 = 0.0;
-        l = L;
-        m = m1;
-        pq = q + L * L + s1;
-        pt = tj + L * L + t1;
-      }
-      a1 = fma(pq[0], pt[0], a1);
-      const int d1 = 2 * l - 1;                        // l^2 - (l - 1)^2
-      if (l > m) a2 = fma(pq[-d1], pt[-d1], a2);
-      pq -= 4 * l - 4;                                 // l^2 - (l - 2)^2
-      pt -= 4 * l - 4;
-      l -= 2;
-    }
-    double x0[2], x1[2];                               // (a1, a2) of slots t0 and t1
-    if (k1 > 0) {
-      x0[0] = h1; x0[1] = h2; x1[0] = a1; x1[1] = a2;
-    } else {
-      x0[0] = a1; x0[1] = a2; x1[0] = 0.0; x1[1] = 0.0;
-    }
-    // Row j: E + O = a1 + a2.  Row j': E - O, which is a1 - a2 when a1 holds
-    // the terms of even l + m (l_max + m even), else a2 - a1.  Every sign change
-    // (that one, dP/dtheta's parity, g_phi's swapped slots) flips the sign bit
-    // of the bit pattern on the integer units: four float64 additions per lane.
-    const unsigned long long SB = 0x8000000000000000ull;
-    unsigned long long fg0 = 0ull, fg1 = 0ull;
-    unsigned long long fr0 = ((L + m0) & 1) ? SB : 0ull, fr1 = ((L + m1) & 1) ? SB : 0ull;
-    if (f == 2) {
-      fr0 ^= SB;
-      fr1 ^= SB;
-    }
-    if (f == 3) {
-      if (!(t0 & 1)) { fg0 = SB; fr0 ^= SB; }
-      if (!(t1 & 1)) { fg1 = SB; fr1 ^= SB; }
-    }
-    gb[g][0] = (unsigned long long)__double_as_longlong(x0[0] + x0[1]) ^ fg0;
-    gb[g][1] = (unsigned long long)__double_as_longlong(x1[0] + x1[1]) ^ fg1;
-    rb[g][0] = (unsigned long long)__double_as_longlong(x0[0] - x0[1]) ^ fr0;
-    rb[g][1] = (unsigned long long)__double_as_longlong(x1[0] - x1[1]) ^ fr1;
-  }
-  const size_t stride = (size_t)a.rows_pad * a.gk;
-  __nv_bfloat16 *const Gf = f == 0 ? a.G[0] : f == 1 ? a.G[1] : f == 2 ? a.G[2] : a.G[3];
-  int *const gexp = f == 0 ? a.gexp[0] : f == 1 ? a.gexp[1] : f == 2 ? a.gexp[2] : a.gexp[3];
-  const size_t row = (size_t)shell * a.n_theta + j, rowm = (size_t)shell * a.n_theta + jm;
-  oz_theta_row<NG>(gb, lane, Gf + row * a.gk, stride, gexp + row, a.nt, a.bias);
-  if (jm != j) oz_theta_row<NG>(rb, lane, Gf + rowm * a.gk, stride, gexp + rowm, a.nt, a.bias);
-  if (f != 0 || a.n_jobs < 4) return;
-  // g_phi from Phi's values: its coefficients are the angular set, -Q / r
-  // (r the shell's outer edge), and its table m P / sin theta is m / sin
-  // theta times Phi's P in the other slot of the same m, so
-  //   G_phi[t] = (+1 for t even, -1 for t odd) (m / (r sin theta)) G_Phi[swap t]
-  // at both rows (sin theta_j' = sin theta_j); slot 0 (m = 0) and the slots
-  // past nt are zero.  This takes the place of a fourth pass over the terms.
-  // The other slot of the same m is the neighbouring lane's slot in the same
-  // half of the group, or for lanes 0 and 31 one of their own.
-  const double c = a.inv_r[shell % a.n_r] * a.inv_sin[j];
-  const int src = ((lane & 1) ? lane + 1 : lane - 1) & 31;
-  unsigned long long pg[NG][2], prm[NG][2];
-#pragma unroll
-  for (int g = 0; g < NG; ++g) {
-    unsigned long long sg0 = __shfl_sync(0xffffffffu, gb[g][0], src), sr0 = __shfl_sync(0xffffffffu, rb[g][0], src);
-    unsigned long long sg1 = __shfl_sync(0xffffffffu, gb[g][1], src), sr1 = __shfl_sync(0xffffffffu, rb[g][1], src);
-    if (lane == 31) {
-      sg0 = gb[g][1]; sr0 = rb[g][1];
-      sg1 = gb[g][0]; sr1 = rb[g][0];
-    } else if (lane == 0) {
-      sg0 = g > 0 ? gb[g > 0 ? g - 1 : 0][1] : 0ull;       // slot 64 g - 1
-      sr0 = g > 0 ? rb[g > 0 ? g - 1 : 0][1] : 0ull;
-      sg1 = g + 1 < NG ? gb[g + 1 < NG ? g + 1 : g][0] : 0ull;   // slot 64 g + 64
-      sr1 = g + 1 < NG ? rb[g + 1 < NG ? g + 1 : g][0] : 0ull;
-    }
-    const int t0 = 64 * g + lane, t1 = 64 * g + 63 - lane;
-    const double c0 = (t0 >= 1 && t0 < a.nt) ? ((t0 & 1) ? -c : c) * (double)((t0 + 1) / 2) : 0.0;
-    const double c1 = (t1 >= 1 && t1 < a.nt) ? ((t1 & 1) ? -c : c) * (double)((t1 + 1) / 2) : 0.0;
-    pg[g][0] = (unsigned long long)__double_as_longlong(c0 * __longlong_as_double((long long)sg0));
-    pg[g][1] = (unsigned long long)__double_as_longlong(c1 * __longlong_as_double((long long)sg1));
-    prm[g][0] = (unsigned long long)__double_as_longlong(c0 * __longlong_as_double((long long)sr0));
-    prm[g][1] = (unsigned long long)__double_as_longlong(c1 * __longlong_as_double((long long)sr1));
-  }
-  oz_theta_row<NG>(pg, lane, a.G[3] + row * a.gk, stride, a.gexp[3] + row, a.nt, a.bias);
-  if (jm != j) oz_theta_row<NG>(prm, lane, a.G[3] + rowm * a.gk, stride, a.gexp[3] + rowm, a.nt, a.bias);
-}
-
 // ---- the polar stage in float-float arithmetic (k_q_ff, k_theta_ff) --------
 //
-// The same sums as k_theta_ozaki, G[t] = sum_l Q[l^2 + t] T_j[l^2 + t] with
-// the even / odd split over the mirrored rows, on the fp32 pipe in
+// The polar stage of the synthesis, G[t] = sum_l Q[l^2 + t] T_j[l^2 + t]
+// per output row (shell, j) and slot t (m = (t + 1) / 2), with the even / odd
+// split over the mirrored rows (cells j and n_theta - 1 - j are reflections
+// about the equator and P_l^m(-x) = (-1)^(l + m) P_l^m(x): with E and O the
+// sums over even and odd l + m, row j gets E + O and its mirror E - O;
+// dP/dtheta has the opposite parity), on the fp32 pipe in
 // float-float arithmetic: a value is the unevaluated sum hi + lo of two fp32
 // numbers (about 48 significant bits, the precision of the digits the sums
 // are cut into next).  A product is exact as x + fma(a, b, -x) (Dekker's
@@ -2334,9 +2153,8 @@ __global__ void __launch_bounds__(256) k_theta_ozaki(OzThetaArgs a) {
 // table rows in shared memory: every lane of a warp reads the same entry),
 // each warp the slots of one or two orders m with about the same number of
 // terms (m and l_max + 1 - m), and stages the sums in shared memory; then
-// each warp cuts whole rows into digits as k_theta_ozaki does (lanes on
-// slots 2 L and 2 L + 1: one 4-byte store per slice and lane), Phi's rows
-// giving g_phi's as well.
+// each warp cuts whole rows into digits (lanes on slots 2 L and 2 L + 1: one
+// 4-byte store per slice and lane), Phi's rows giving g_phi's as well.
 
 // (hi, lo) of Q 2^-qexp per (field, shell), the scale from the row's largest
 // |Q| (|Q| 2^-qexp < 1), in a shell-minor layout [field][n_lm][shells_pad];
@@ -2451,6 +2269,42 @@ __device__ __forceinline__ float2 ff_sum(float2 a, float2 b, float sg) {
   return make_float2(h, __fsub_rn(lo, __fsub_rn(h, s)));
 }
 
+// The six digit slices of one float-float value (hi, lo), as fp32 bit
+// patterns whose upper halves are the bf16 digits of |value| (the sign is
+// returned): X = round(|value| 2^K), 2^K = p1 p2 the row's scale, and its
+// balanced base-256 digits, as described below for ff_row.
+__device__ __forceinline__ uint32_t ff_digit_bits(float hi, float lo, float p1, float p2, uint32_t (&bits)[6]) {
+  constexpr float kM = 12582912.f;                      // 1.5 2^23
+  constexpr uint32_t kMBits = 0x4B400000u;
+  const uint32_t sgn = __float_as_uint(hi) >> 31;
+  const float A = __fmul_rn(__fmul_rn(fabsf(hi), p1), p2);
+  const float B = __fmul_rn(__fmul_rn(sgn ? -lo : lo, p1), p2);
+  const float s2 = __fadd_rn(__fmul_rn(A, 0x1p-32f), kM);
+  const float R1 = __fmaf_rn(-__fsub_rn(s2, kM), 0x1p32f, A);
+  const float s1 = __fadd_rn(__fmul_rn(R1, 0x1p-16f), kM);
+  const float R2 = __fmaf_rn(-__fsub_rn(s1, kM), 0x1p16f, R1);
+  const float s0 = __fadd_rn(__fadd_rn(R2, B), kM);
+  const long long X = ((long long)(int)(__float_as_uint(s2) - kMBits) << 32) +
+                      ((long long)(int)(__float_as_uint(s1) - kMBits) << 16) +
+                      (long long)(int)(__float_as_uint(s0) - kMBits);
+  const unsigned long long Y = (unsigned long long)X + 0x7F7F7F7F7Full;
+  const uint32_t ylo = (uint32_t)Y, yhi = (uint32_t)(Y >> 32);
+  bits[0] = __float_as_uint(__fsub_rn(__uint_as_float(0x4B000000u | (yhi >> 8)), 8388608.f));
+  bits[1] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(yhi, 0x4B000000u, 0x7540)), 8388735.f));
+  bits[2] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7543)), 8388735.f));
+  bits[3] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7542)), 8388735.f));
+  bits[4] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7541)), 8388735.f));
+  bits[5] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7540)), 8388735.f));
+  return sgn;
+}
+
+// the row scale of ff_row: 2^K with K = 48 - e as two normal fp32 factors
+__device__ __forceinline__ void ff_row_scale(int e, float &p1, float &p2) {
+  const int K = 48 - e, K1 = K >> 1, K2 = K - K1;
+  p1 = __uint_as_float((uint32_t)(K1 + 127) << 23);
+  p2 = __uint_as_float((uint32_t)(K2 + 127) << 23);
+}
+
 // One row of float-float values cut into digits: lane L holds slots
 // 64 g + 2 L and 64 g + 2 L + 1.  The row's scale 2^e: the largest |hi|
 // stepped up by one ulp bounds every |hi + lo| (|lo| is at most half an ulp),
@@ -2480,37 +2334,14 @@ __device__ __forceinline__ void ff_row(const float2 (&v)[NG][2], int lane, __nv_
   mb = __reduce_max_sync(0xffffffffu, mb);
   const int exm = (int)(mb >> 23);
   const int e = exm - 125;                              // every |value| < 2^(exm - 126) = 2^(e - 1)
-  const int K = 48 - e, K1 = K >> 1, K2 = K - K1;       // 2^K as two normal factors
-  const float p1 = __uint_as_float((uint32_t)(K1 + 127) << 23), p2 = __uint_as_float((uint32_t)(K2 + 127) << 23);
-  constexpr float kM = 12582912.f;                      // 1.5 2^23
-  constexpr uint32_t kMBits = 0x4B400000u;
+  float p1, p2;
+  ff_row_scale(e, p1, p2);
   constexpr uint32_t kBiasBits = 0x45C0u;               // bf16 of kOzBiasG (6144)
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
     uint32_t bits[2][6], sgn[2];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const float hi = v[g][h].x, lo = v[g][h].y;
-      sgn[h] = __float_as_uint(hi) >> 31;
-      const float A = __fmul_rn(__fmul_rn(fabsf(hi), p1), p2);
-      const float B = __fmul_rn(__fmul_rn(sgn[h] ? -lo : lo, p1), p2);
-      const float s2 = __fadd_rn(__fmul_rn(A, 0x1p-32f), kM);
-      const float R1 = __fmaf_rn(-__fsub_rn(s2, kM), 0x1p32f, A);
-      const float s1 = __fadd_rn(__fmul_rn(R1, 0x1p-16f), kM);
-      const float R2 = __fmaf_rn(-__fsub_rn(s1, kM), 0x1p16f, R1);
-      const float s0 = __fadd_rn(__fadd_rn(R2, B), kM);
-      const long long X = ((long long)(int)(__float_as_uint(s2) - kMBits) << 32) +
-                          ((long long)(int)(__float_as_uint(s1) - kMBits) << 16) +
-                          (long long)(int)(__float_as_uint(s0) - kMBits);
-      const unsigned long long Y = (unsigned long long)X + 0x7F7F7F7F7Full;
-      const uint32_t ylo = (uint32_t)Y, yhi = (uint32_t)(Y >> 32);
-      bits[h][0] = __float_as_uint(__fsub_rn(__uint_as_float(0x4B000000u | (yhi >> 8)), 8388608.f));
-      bits[h][1] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(yhi, 0x4B000000u, 0x7540)), 8388735.f));
-      bits[h][2] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7543)), 8388735.f));
-      bits[h][3] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7542)), 8388735.f));
-      bits[h][4] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7541)), 8388735.f));
-      bits[h][5] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7540)), 8388735.f));
-    }
+    for (int h = 0; h < 2; ++h) sgn[h] = ff_digit_bits(v[g][h].x, v[g][h].y, p1, p2, bits[h]);
     const int t = 64 * g + 2 * lane;
     const uint32_t sm = (sgn[0] << 15) | (sgn[1] << 31);
     uint32_t *d32 = reinterpret_cast<uint32_t *>(dst + t);
@@ -2953,8 +2784,9 @@ __global__ void __launch_bounds__(256) k_rotate_ff(int n_r, int n_lm, int lmax, 
 // The weighted densities of the separable analysis, rho w, as digit rows for
 // the analysis: one warp per row (shell, j); lane L takes the pairs
 // k = 2 L + 64 c.  rho w is the float64 product of the CUDA-core path; the
-// row's scale and digits as in k_theta_ozaki, and the row exponent of a unit
-// level-6 sum includes the table's scale 2^eb.
+// row's scale 2^e from its largest |rho w| (every value below 2^(e - 1)),
+// the digits of X = round(|rho w| 2^(48 - e)) taken from the float64 bits,
+// and the row exponent of a unit level-6 sum includes the table's scale 2^eb.
 struct OzRhoArgs {
   int n_r, n_theta, n_phi, rows, k_pad, rows_pad, eb;
   const double *rho0, *rho1;    // [n_r][n_theta][n_phi] per patch (rho1 NULL on a polar grid)
@@ -3357,7 +3189,7 @@ yy_status ozaki_prepare(yy_grid *g) {
     if (g->n_patch == 2) A((void **)&o->Df, rotation_table_size(g->lmax) * sizeof(float2));
     for (int f = 0; f < 4 && e == cudaSuccess; ++f) e = cudaMemset(o->G[f], 0, g_bytes);
     if (e == cudaSuccess) {
-      // g_phi's polar factors (k_theta_ozaki): the same cell centres as the
+      // g_phi's polar factors (k_theta_ff): the same cell centres as the
       // tables and the same 1 / r as the scan coefficients
       std::vector<double> is(g->n_theta), ir(g->n_r), re(g->n_r + 1);
       for (int j = 0; j < g->n_theta; ++j) is[j] = 1.0 / sin(g->th0 + g->dth * (j + 0.5));
@@ -3372,7 +3204,7 @@ yy_status ozaki_prepare(yy_grid *g) {
       const double *tsrc[4] = {g->sep_P, g->sep_dP, g->tbar, g->rot};
       float2 *tdst[4] = {o->Pf[0], o->Pf[1], o->tbf, o->Df};
       const size_t tn[4] = {ne, ne, (size_t)((g->n_theta + 1) / 2) * g->n_lm,
-                            g->n_patch == 2 ? rotation_table_size(g->lmax) : 0};
+                            g->n_patch == 2 ? (size_t)rotation_table_size(g->lmax) : (size_t)0};
       const size_t tmax = std::max(ne, tn[3]);
       tb.resize(tmax);
       tf.resize(tmax);
@@ -3473,32 +3305,12 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
   typedef FormOzaki F;
   yy_oz_tables *o = g->oz;
   const int n_jobs = gy ? 4 : 1;
-  OzThetaArgs ta = {};
-  ta.n_shells = grid_rows(g);
-  ta.n_theta = g->n_theta;
-  ta.lmax = g->lmax;
-  ta.n_lm = g->n_lm;
-  ta.nt = 2 * g->lmax + 1;
-  ta.n_jobs = n_jobs;
-  ta.rows_pad = o->rows_pad;
-  ta.gk = o->gk;
-  ta.bias = o->bias;
-  ta.n_r = g->n_r;
-  ta.inv_sin = o->inv_sin;
-  ta.inv_r = o->inv_r;
-  ta.Q = g->Q;
-  ta.tab[0] = g->sep_P;
-  ta.tab[1] = g->sep_dP;
-  ta.tab[2] = g->sep_Qs;
-  for (int f = 0; f < 4; ++f) {
-    ta.G[f] = (__nv_bfloat16 *)o->G[f];
-    ta.gexp[f] = o->gexp[f];
-  }
+  const int n_shells = grid_rows(g);
   // the coefficients as scaled fp32 pairs, then the polar stage of Phi, g_r
   // and g_theta (Phi's blocks also write g_phi)
   const int n_q = n_jobs == 4 ? 3 : 1;
   OzQffArgs qa = {};
-  qa.n_shells = ta.n_shells;
+  qa.n_shells = n_shells;
   qa.shells_pad = o->shells_pad;
   qa.n_lm = g->n_lm;
   qa.Q = g->Q;
@@ -3510,13 +3322,13 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
            qa.one_pass ? qff_smem : (size_t)kQffChunk * (kQffShells + 1) * sizeof(float2), s>>>(qa);
   note_launch(g, "k_q_ff", s);
   OzThetaFFArgs fa = {};
-  fa.n_shells = ta.n_shells;
+  fa.n_shells = n_shells;
   fa.shells_pad = o->shells_pad;
   fa.n_theta = g->n_theta;
   fa.half = (g->n_theta + 1) / 2;
   fa.lmax = g->lmax;
   fa.n_lm = g->n_lm;
-  fa.nt = ta.nt;
+  fa.nt = 2 * g->lmax + 1;
   fa.gphi = n_jobs == 4 ? 1 : 0;
   fa.rows_pad = o->rows_pad;
   fa.gk = o->gk;
@@ -3529,8 +3341,8 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
   fa.inv_sin = o->inv_sin;
   fa.inv_r = o->inv_r;
   for (int f = 0; f < 4; ++f) {
-    fa.G[f] = ta.G[f];
-    fa.gexp[f] = ta.gexp[f];
+    fa.G[f] = (__nv_bfloat16 *)o->G[f];
+    fa.gexp[f] = o->gexp[f];
   }
   const int n_groups = g->lmax / 2 + 1, tp = theta_ff_tp(o->gk);
   const unsigned ff_blocks = (unsigned)(n_q * (o->shells_pad / 32) * ((fa.half + tp - 1) / tp));

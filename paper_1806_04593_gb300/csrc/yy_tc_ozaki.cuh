@@ -45,18 +45,31 @@ static_assert(FormOzaki::start(7) == 26 && FormOzaki::level(25) == 6 && FormOzak
                   FormOzaki::pa(20) == 5 && FormOzaki::pb(20) == 0 && !FormOzaki::first(20),
               "Ozaki product table");
 
-// v 2^e exactly, for |v| < 2^53 and a result in the normal range (built from
-// the bits: the top bit's position gives the exponent, the bits below it the
-// fraction); anything else takes ldexp.
+// v 2^e exactly, for |v| < 2^53 and a result in the normal range, built
+// from the bits: |v| shifted so that its top bit lands on bit 52 (the
+// implicit one), then the biased exponent less one added above it (the
+// implicit one carries it up by one) and the sign bit set; anything else
+// takes ldexp.
 __device__ __forceinline__ double i64_ldexp(long long v, int e) {
-  if (v == 0) return 0.0;
-  const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ull;
-  const unsigned long long u = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const unsigned long long s = (unsigned long long)(v >> 63);          // 0 or all ones
+  const unsigned long long u = ((unsigned long long)v ^ s) - s;        // |v|
+  const int lz = __clzll((long long)u);                                // 64 for v = 0
+  const int be = 1086 - lz + e;                                        // (63 - lz) + 1023 + e
+  if (lz < 11 || lz == 64 || be <= 0 || be >= 2047) return lz == 64 ? 0.0 : ldexp((double)v, e);
+  const unsigned long long m = u << (lz - 11);
+  return __longlong_as_double((long long)((m + ((unsigned long long)(be - 1) << 52)) | (s << 63)));
+}
+
+// i64_ldexp for callers that checked e once per row: |v| < 2^53 and
+// e in [-1022, 971] keep every nonzero result normal, so the range checks go.
+__device__ __forceinline__ bool i64_ldexp_row_ok(int e) { return e >= -1022 && e <= 971; }
+__device__ __forceinline__ double i64_ldexp_row(long long v, int e) {
+  const unsigned long long s = (unsigned long long)(v >> 63);
+  const unsigned long long u = ((unsigned long long)v ^ s) - s;
   const int lz = __clzll((long long)u);
-  const int be = 1086 - lz + e;   // (63 - lz) + 1023 + e
-  if (lz < 11 || be <= 0 || be >= 2047) return ldexp((double)v, e);
-  const unsigned long long frac = ((u << lz) << 1) >> 12;
-  return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | frac));
+  const unsigned long long m = u << ((lz - 11) & 63);
+  const unsigned long long b = (m + ((unsigned long long)(1085 - lz + e) << 52)) | (s << 63);
+  return __longlong_as_double((long long)(u == 0ull ? 0ull : b));
 }
 
 // An accumulator value of the Ozaki forms: an integer below 2^24 held in fp32.
