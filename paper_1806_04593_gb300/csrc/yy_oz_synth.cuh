@@ -335,8 +335,18 @@ k_oz_synth(const __grid_constant__ OzSynthMaps maps, const __grid_constant__ OzS
             }
             __syncwarp();
             const int col0 = col_base + c0;
-            if (vec) {
-              // lanes 4 c' + e: row 8 q + c', values 2 e and 2 e + 1 of the run
+            if (vec && col0 + 8 <= a.cols) {
+              // the whole run inside the row; lanes 4 c' + e: row 8 q + c', values
+              // 2 e and 2 e + 1 of the run
+              const int e = lane & 3, col = col0 + 2 * e;
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const int r = 8 * q + (lane >> 2);
+                double *orow = rowp[r];
+                const double2 val = *reinterpret_cast<const double2 *>(ebuf + r * kOzEpiPad + 2 * e);
+                if (orow != nullptr) *reinterpret_cast<double2 *>(orow + col) = val;
+              }
+            } else if (vec) {
               const int e = lane & 3, col = col0 + 2 * e;
 #pragma unroll
               for (int q = 0; q < 4; ++q) {

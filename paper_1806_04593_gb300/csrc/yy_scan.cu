@@ -408,12 +408,15 @@ void scan_geometry(const yy_grid *g, int *nc, int *ch) {
 
 cudaError_t radial_scan(yy_grid *g, bool want_f32, bool f64_out, cudaStream_t st) {
   float *q32 = want_f32 ? g->Q32 : nullptr;
-  const unsigned wblocks = (unsigned)((g->n_patch * g->n_lm * 32 + 127) / 128);
+  // one warp per block: the SMs get the warps in equal numbers (with four per
+  // block, 1352 warps left some SMs three blocks and most two, and the
+  // three-block SMs set the time)
+  const unsigned wblocks = (unsigned)(g->n_patch * g->n_lm);
   const double *At = moments_total(g);
   if (g->n_r <= 32 * 24) {
 #define YY_SCAN_WARP(CH)                                                                               \
-  (f64_out ? (k_scan_warp<CH, true><<<wblocks, 128, 0, st>>>(g->n_patch, g->n_r, g->lmax, g->n_lm, At, g->scan, g->Q, q32), 0) \
-           : (k_scan_warp<CH, false><<<wblocks, 128, 0, st>>>(g->n_patch, g->n_r, g->lmax, g->n_lm, At, g->scan, g->Q, q32), 0))
+  (f64_out ? (k_scan_warp<CH, true><<<wblocks, 32, 0, st>>>(g->n_patch, g->n_r, g->lmax, g->n_lm, At, g->scan, g->Q, q32), 0) \
+           : (k_scan_warp<CH, false><<<wblocks, 32, 0, st>>>(g->n_patch, g->n_r, g->lmax, g->n_lm, At, g->scan, g->Q, q32), 0))
     if (g->n_r <= 32 * 8)
       YY_SCAN_WARP(8);
     else if (g->n_r <= 32 * 12)
