@@ -224,3 +224,49 @@ def test_ozaki_long_rows_keep_the_float64_analysis(yy, oracle_grid):
         assert grad_err(out["grad"].cpu().numpy()[:, :, j, k], ref["grad"]) <= TOL_FP64
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("name", ["mid", "polar"])
+def test_ozaki_is_homogeneous_in_the_density(yy, name):
+    """The potential is linear in rho.  Every scale the Ozaki path takes
+    (the digit rows' powers of two, the float-float splits' scales per
+    coefficient row, per shell and per degree) follows the data, and float64
+    multiplication by a power of two is exact, so rho 2^k gives exactly 2^k
+    times the result: bitwise, for k = +-100 (far outside the fp32 range of
+    the float-float stages).  rho 1e30 and 1e-30 stay within the float64 bar
+    of the scaled result."""
+    import torch
+    if name == "mid":
+        spec = inputs.GRIDS["mid"]()
+        ry, rg = inputs.density_for(spec)
+        g = _grid(yy, spec)
+        solve = lambda s: gpu_solve(g, ry * s, rg * s, gradient=True, prec="fp64_ozaki")
+        closer = None
+    else:
+        spec = inputs.mid_polar_grid()
+        g = yy.Grid.from_spec(spec)
+        g.prepare("fp64_ozaki")
+        rho, _ = inputs.pns_density(spec, 3, 0.05)
+
+        def solve(s):
+            r = torch.as_tensor(np.ascontiguousarray(rho * s), device="cuda")
+            out = g.solve(r, gradient=True, prec="fp64_ozaki")
+            torch.cuda.synchronize()
+            return {k: v.cpu().numpy() for k, v in out.items()}
+        closer = g
+    try:
+        base = solve(1.0)
+        assert yy.yy_last_device_status(g.handle) == yy.YY_OK
+        for k in (100, -100):
+            out = solve(2.0 ** k)
+            assert yy.yy_last_device_status(g.handle) == yy.YY_OK
+            for key in base:
+                assert np.array_equal(out[key], np.ldexp(base[key], k)), (k, key)
+        for s in (1e30, 1e-30):
+            out = solve(s)
+            for key in base:
+                assert np.all(np.isfinite(out[key])), (s, key)
+                assert field_err(key, out[key] / s, base[key]) <= TOL_FP64, (s, key)
+    finally:
+        if closer is not None:
+            closer.close()
