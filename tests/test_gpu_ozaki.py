@@ -270,3 +270,27 @@ def test_ozaki_is_homogeneous_in_the_density(yy, name):
     finally:
         if closer is not None:
             closer.close()
+
+
+def test_ozaki_long_polar_rows_at_high_degree(yy):
+    """l_max 60 on 90 polar rows: the float-float analysis stage holds more
+    mirrored row pairs than its registers (45 x 121 > 8 per thread) and the
+    coefficient rows (3721 of them) are longer than one shared-memory pass of
+    the split, so both take their looping forms; against the CUDA-core
+    float64 path on all cells."""
+    import torch
+    spec = inputs.polar_grid(np.logspace(-2, 0, 9), 90, 180, 60, "polar_l60_oz")
+    g = yy.Grid.from_spec(spec)
+    try:
+        g.prepare("fp64_ozaki")
+        rho, _ = inputs.pns_density(spec, 5, 0.05)
+        r = torch.as_tensor(np.ascontiguousarray(rho), device="cuda")
+        out = g.solve(r, gradient=True, prec="fp64_ozaki")
+        torch.cuda.synchronize()
+        assert yy.yy_last_device_status(g.handle) == yy.YY_OK
+        f64 = g.solve(r, gradient=True, prec="fp64")
+        torch.cuda.synchronize()
+        for key in ("phi", "grad"):
+            assert field_err(key, out[key].cpu().numpy(), f64[key].cpu().numpy()) <= TOL_VS_FP64_PATH, key
+    finally:
+        g.close()
