@@ -331,7 +331,13 @@ k_oz_synth(const __grid_constant__ OzSynthMaps maps, const __grid_constant__ OzS
             for (int j = 0; j < 8; ++j) {
               const long long V = ((long long)(int)(u0[j] - kOzBiasBits) << 32) +
                                   ((long long)mid[c0 + j] << 16) + (long long)lo[c0 + j];
-              ebuf[lane * kOzEpiPad + j] = row_ok ? i64_ldexp_row(V, ce + 16) : i64_ldexp(V, ce + 16);
+              // the even columns through the float64 pipe's conversion, the
+              // odd ones by integer formatting: the epilogue's issue slots are
+              // its limit and the float64 pipe is otherwise idle (three of
+              // eight: 526 -> 515 us, four: 511, six: 510, the pipe near full)
+              ebuf[lane * kOzEpiPad + j] = !row_ok       ? i64_ldexp(V, ce + 16)
+                                           : (j % 2 == 0) ? i64_ldexp_row_cvt(V, ce + 16)
+                                                          : i64_ldexp_row(V, ce + 16);
             }
             __syncwarp();
             const int col0 = col_base + c0;

@@ -72,6 +72,14 @@ __device__ __forceinline__ double i64_ldexp_row(long long v, int e) {
   return __longlong_as_double((long long)(u == 0ull ? 0ull : b));
 }
 
+// The same through the float64 pipe's conversion (exact: |v| < 2^53) and an
+// exponent add: a few issue slots instead of the integer formatting, for
+// callers that spread their values over both pipes.
+__device__ __forceinline__ double i64_ldexp_row_cvt(long long v, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(__ll2double_rn(v));
+  return __longlong_as_double((long long)(v == 0 ? 0ull : b + ((unsigned long long)(long long)e << 52)));
+}
+
 // An accumulator value of the Ozaki forms: an integer below 2^24 held in fp32.
 __device__ __forceinline__ int oz_int(uint32_t v) { return __float2int_rn(__uint_as_float(v)); }
 
