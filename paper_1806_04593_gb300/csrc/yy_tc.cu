@@ -2269,6 +2269,23 @@ __device__ __forceinline__ float2 ff_sum(float2 a, float2 b, float sg) {
   return make_float2(h, __fsub_rn(lo, __fsub_rn(h, s)));
 }
 
+// The balanced base-256 digits of 0 <= X <= 2^47 in one step: with
+// Y = X + 127 (1 + 2^8 + ... + 2^32), the low five digits are Y's bytes less
+// 127 (each in [-127, 128], the carries done by the addition) and the top
+// one is Y >> 40.  Each digit comes out as the fp32 bit pattern of its
+// value, whose upper half is the bf16 pattern (an integer below 2^8 in
+// magnitude has sixteen zero low bits), most significant digit first.
+__device__ __forceinline__ void x_digit_bits(unsigned long long X, uint32_t (&bits)[6]) {
+  const unsigned long long Y = X + 0x7F7F7F7F7Full;
+  const uint32_t ylo = (uint32_t)Y, yhi = (uint32_t)(Y >> 32);
+  bits[0] = __float_as_uint(__fsub_rn(__uint_as_float(0x4B000000u | (yhi >> 8)), 8388608.f));
+  bits[1] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(yhi, 0x4B000000u, 0x7540)), 8388735.f));
+  bits[2] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7543)), 8388735.f));
+  bits[3] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7542)), 8388735.f));
+  bits[4] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7541)), 8388735.f));
+  bits[5] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7540)), 8388735.f));
+}
+
 // The six digit slices of one float-float value (hi, lo), as fp32 bit
 // patterns whose upper halves are the bf16 digits of |value| (the sign is
 // returned): X = round(|value| 2^K), 2^K = p1 p2 the row's scale, and its
@@ -2287,14 +2304,7 @@ __device__ __forceinline__ uint32_t ff_digit_bits(float hi, float lo, float p1, 
   const long long X = ((long long)(int)(__float_as_uint(s2) - kMBits) << 32) +
                       ((long long)(int)(__float_as_uint(s1) - kMBits) << 16) +
                       (long long)(int)(__float_as_uint(s0) - kMBits);
-  const unsigned long long Y = (unsigned long long)X + 0x7F7F7F7F7Full;
-  const uint32_t ylo = (uint32_t)Y, yhi = (uint32_t)(Y >> 32);
-  bits[0] = __float_as_uint(__fsub_rn(__uint_as_float(0x4B000000u | (yhi >> 8)), 8388608.f));
-  bits[1] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(yhi, 0x4B000000u, 0x7540)), 8388735.f));
-  bits[2] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7543)), 8388735.f));
-  bits[3] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7542)), 8388735.f));
-  bits[4] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7541)), 8388735.f));
-  bits[5] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7540)), 8388735.f));
+  x_digit_bits((unsigned long long)X, bits);
   return sgn;
 }
 
@@ -2795,33 +2805,6 @@ struct OzRhoArgs {
   int *rexp;                    // [rows_pad]
 };
 
-// Balanced base-256 digits of a signed X, |X| <= 2^47, as fp32 integers:
-// the low 24 bits taken as a signed number in [-2^23, 2^23) (with a carry
-// into the high part), then three digits of each 24-bit half, each digit the
-// remainder rounded to the nearest multiple of 2^16 or 2^8 by one fused
-// multiply-add against 1.5 2^23 (every value below 2^24: all exact).  Each
-// digit lies in [-128, 128]; its fp32 bit pattern has sixteen zero low bits,
-// so the upper half is the digit in bf16.
-__device__ __forceinline__ void oz_digits_f(long long X, float (&d)[6]) {
-  constexpr float kRound = 12582912.0f;   // 1.5 2^23: the sum's last place is 1
-  int lo = (int)((unsigned)X & 0xFFFFFFu);
-  int hi = (int)(X >> 24);
-  const int carry = lo >= 0x800000 ? 1 : 0;
-  lo -= carry << 24;
-  hi += carry;
-  const float half[2] = {(float)hi, (float)lo};
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const float r0 = half[h];
-    const float d0 = __fsub_rn(__fmaf_rn(r0, 1.0f / 65536.0f, kRound), kRound);
-    const float r1 = __fmaf_rn(-d0, 65536.0f, r0);
-    const float d1 = __fsub_rn(__fmaf_rn(r1, 1.0f / 256.0f, kRound), kRound);
-    d[3 * h] = d0;
-    d[3 * h + 1] = d1;
-    d[3 * h + 2] = __fmaf_rn(-d1, 256.0f, r1);
-  }
-}
-
 // C: 64-wide pieces of a row held per lane (k_pad <= 64 C).  Two cells'
 // digits of one slice go out as one 32-bit store of their bf16 patterns.
 template <int C>
@@ -2868,20 +2851,21 @@ __global__ void __launch_bounds__(256) k_rhow_ozaki(OzRhoArgs a) {
   for (int c = 0; c < C; ++c) {
     const int k0 = 2 * lane + 64 * c;
     if (k0 >= a.k_pad) break;
-    float d[2][6];
+    uint32_t d[2][6];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int ex = (int)((bits[c][h] >> 52) & 0x7FFu);
       const int sh = 1027 - ex + e;
-      long long X = 0;
+      unsigned long long X = 0;
       if (exm != 0 && ex != 0 && sh < 64)
-        X = (long long)(((((bits[c][h] & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> (sh - 1)) + 1ull) >> 1);
-      oz_digits_f((bits[c][h] >> 63) ? -X : X, d[h]);
+        X = ((((bits[c][h] & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> (sh - 1)) + 1ull) >> 1;
+      x_digit_bits(X, d[h]);
     }
+    // the signs on the bf16 patterns
+    const uint32_t sm = ((uint32_t)(bits[c][0] >> 63) << 15) | ((uint32_t)(bits[c][1] >> 63) << 31);
     uint32_t *dst = reinterpret_cast<uint32_t *>(a.X + (size_t)row * a.k_pad + k0);
 #pragma unroll
-    for (int sl = 0; sl < 6; ++sl)
-      dst[sl * (stride / 2)] = __byte_perm(__float_as_uint(d[0][sl]), __float_as_uint(d[1][sl]), 0x7632);
+    for (int sl = 0; sl < 6; ++sl) dst[sl * (stride / 2)] = __byte_perm(d[0][sl], d[1][sl], 0x7632) ^ sm;
   }
   if (lane == 0) a.rexp[row] = exm == 0 ? 0 : e + a.eb - 64;
 }
