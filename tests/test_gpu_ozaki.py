@@ -294,3 +294,26 @@ def test_ozaki_long_polar_rows_at_high_degree(yy):
             assert field_err(key, out[key].cpu().numpy(), f64[key].cpu().numpy()) <= TOL_VS_FP64_PATH, key
     finally:
         g.close()
+
+
+def test_ozaki_polar_grid_with_odd_shell_count(yy):
+    """A polar grid of 9 zones (an odd number of shells: the last block of the
+    float-float analysis stage, two shells per block, has one) and 17 polar
+    rows (an odd count: the middle row is its own mirror); against the
+    CUDA-core float64 path on all cells."""
+    import torch
+    spec = inputs.polar_grid(np.logspace(-2, 0, 10), 17, 48, 11, "polar_odd_oz")
+    g = yy.Grid.from_spec(spec)
+    try:
+        g.prepare("fp64_ozaki")
+        rho, _ = inputs.pns_density(spec, 4, 0.05)
+        r = torch.as_tensor(np.ascontiguousarray(rho), device="cuda")
+        out = g.solve(r, gradient=True, prec="fp64_ozaki")
+        torch.cuda.synchronize()
+        assert yy.yy_last_device_status(g.handle) == yy.YY_OK
+        f64 = g.solve(r, gradient=True, prec="fp64")
+        torch.cuda.synchronize()
+        for key in ("phi", "grad"):
+            assert field_err(key, out[key].cpu().numpy(), f64[key].cpu().numpy()) <= TOL_VS_FP64_PATH, key
+    finally:
+        g.close()
