@@ -3005,7 +3005,7 @@ static yy_status ozaki_prepare_analysis(yy_grid *g, yy_oz_tables *o) {
   // the analysis kernel with all slots in one MMA
   o->an_slots2 = 0;
   if (nt <= kOzAnBN && make_map<F>(&o->an_maps2.a, o->an_x, o->an_kpad, F::kPA * o->rows_pad, kPairRows) &&
-      make_map<F>(&o->an_maps2.b, o->an_az, o->an_kpad, F::kPB * o->an_b_rows_pad, kOzAnBN / 2) &&
+      make_map<F>(&o->an_maps2.b, o->an_az, o->an_kpad, F::kPB * o->an_b_rows_pad, kOzAnBN) &&
       cudaFuncSetAttribute(k_oz_analysis, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzAnSmem) == cudaSuccess) {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = pair_config(64, kOzAnSmem, 0, attr);

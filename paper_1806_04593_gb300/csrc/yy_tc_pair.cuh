@@ -220,6 +220,19 @@ __device__ __forceinline__ void tmem_ld8_async(uint32_t taddr, uint32_t (&v)[8])
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Zeros into 16 columns of this warp's 32 TMEM lanes, and the wait for a
+// thread's TMEM stores.
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+  const uint32_t z = 0u;
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+      "r"(z)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // ---- CTA-pair (cta_group::2) forms -------------------------------------
 //
 // Two CTAs of a cluster share one MMA of M = 256: the even CTA issues it; each
