@@ -108,17 +108,17 @@ k_gemm_tn(int M, int N, int K, int k_chunk, int seg,
     if (t + 1 < nk) store(buf ^ 1);
     __syncthreads();
   }
-  if (PARTIAL) return;
-
+  if constexpr (!PARTIAL) {
 #pragma unroll
-  for (int i = 0; i < TM; ++i) {
-    const int m = bm + ty * TM + i;
-    if (m >= M) continue;
-    double *crow = (m < c_split) ? C0 + (size_t)m * ldc : C1 + (size_t)(m - c_split) * ldc;
+    for (int i = 0; i < TM; ++i) {
+      const int m = bm + ty * TM + i;
+      if (m >= M) continue;
+      double *crow = (m < c_split) ? C0 + (size_t)m * ldc : C1 + (size_t)(m - c_split) * ldc;
 #pragma unroll
-    for (int j = 0; j < TN; ++j) {
-      const int n = bn + tx * TN + j;
-      if (n < N) crow[n] = (double)acc[i][j];
+      for (int j = 0; j < TN; ++j) {
+        const int n = bn + tx * TN + j;
+        if (n < N) crow[n] = (double)acc[i][j];
+      }
     }
   }
 }
