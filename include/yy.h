@@ -81,10 +81,15 @@ typedef enum {
  *             six balanced 8-bit digits (integers exact in bf16) under a
  *             power-of-two scale per row, the 26 digit products of levels
  *             <= 6 accumulated exactly in fp32 per level, levels combined in
- *             integers and rounded once to float64.  The polar stages, the
- *             combination of the patches and the scans are float64 on CUDA
- *             cores as for YY_FP64 (and so is the analysis with
- *             YY_ANALYSIS_DENSE, or with more than 640 cells per row).
+ *             integers and rounded once to float64.  The polar stages and
+ *             the combination of the patches run in float-float arithmetic
+ *             (unevaluated pairs of fp32 values, about 48 bits: exact
+ *             products by fused multiply-add and exact sums by TwoSum) on the
+ *             CUDA cores' fp32 pipe, each input scaled by a power of two that
+ *             follows the data; the radial scans are float64 as for YY_FP64
+ *             (and so is the analysis with YY_ANALYSIS_DENSE, or with more
+ *             than 640 cells per row).  Multiplying rho by a power of two
+ *             multiplies every result by the same power exactly.
  *             Needs yy_grid_prepare and 2 l_max + 1 <= 127 (l_max <= 63);
  *             above l_max 30 the contractions take their general kernels
  *             (no spare bias columns in G rows of 64 slots, rows of 128
