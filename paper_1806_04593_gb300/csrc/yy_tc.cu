@@ -2185,38 +2185,45 @@ __device__ __forceinline__ float2 ff_split(double x, int qe) {
   return make_float2(h, l);
 }
 
-// One block per (field, 8 shells), a warp per shell: the row's scale, then
-// its pairs, and the 8 rows written out shell-minor as 64-byte runs.  Rows
-// that fit in shared memory (one_pass) are read once: the loads of a lane
-// all in flight, the values staged in place of their pairs.
+// One block per (field, 8 shells), two warps per shell: the row's scale,
+// then its pairs, and the 8 rows written out shell-minor as 64-byte runs.
+// Rows that fit in shared memory (one_pass) are read once: the loads of a
+// lane all in flight, the values staged in place of their pairs, each warp
+// of a row taking alternate 32-value pieces.  Longer rows take a warp each,
+// in chunks through a shared tile.
 constexpr int kQffShells = 8, kQffChunk = 512;
 constexpr size_t kQffOnePassSmem = 200 * 1024;
 
-__global__ void __launch_bounds__(256) k_q_ff(OzQffArgs a) {
+__global__ void __launch_bounds__(512) k_q_ff(OzQffArgs a) {
   extern __shared__ float2 qrow[];                         // one_pass: [8][n_lm]; else [kQffChunk][8 + 1]
+  __shared__ unsigned long long part[2][kQffShells];
   float2 (*tile)[kQffShells + 1] = reinterpret_cast<float2 (*)[kQffShells + 1]>(qrow);
   const int n_sb = a.shells_pad / kQffShells;
   const int f = (int)blockIdx.x / n_sb, s0 = ((int)blockIdx.x % n_sb) * kQffShells;
   const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
-  const int s = s0 + warp;
+  const int r = warp % kQffShells, h = warp / kQffShells;  // the row, and which of its two warps
+  const int s = s0 + r;
   const bool on = s < a.n_shells;
   const double *row = a.Q + ((size_t)f * a.n_shells + (on ? s : 0)) * a.n_lm;
   float2 *Qfb = a.Qf + (size_t)f * a.n_lm * a.shells_pad + s0;
   unsigned long long mb = 0ull;
   if (a.one_pass) {
-    float2 *mine = qrow + (size_t)warp * a.n_lm;
+    float2 *mine = qrow + (size_t)r * a.n_lm;
 #pragma unroll 8
-    for (int k = lane; k < a.n_lm; k += 32) {
+    for (int k = lane + 32 * h; k < a.n_lm; k += 64) {
       const double x = on ? row[k] : 0.0;
       mb = max(mb, (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull);
       mine[k] = *reinterpret_cast<const float2 *>(&x);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
+    if (lane == 0) part[h][r] = mb;
+    __syncthreads();
+    mb = max(part[0][r], part[1][r]);
     const int exm = (int)(mb >> 52);
     const int qe = exm == 0 ? 0 : exm - 1022;
-    if (lane == 0 && on) a.qexp[(size_t)f * a.n_shells + s] = qe;
-    for (int k = lane; k < a.n_lm; k += 32) {
+    if (lane == 0 && h == 0 && on) a.qexp[(size_t)f * a.n_shells + s] = qe;
+    for (int k = lane + 32 * h; k < a.n_lm; k += 64) {
       const float2 b = mine[k];
       mine[k] = ff_split(*reinterpret_cast<const double *>(&b), qe);
     }
@@ -2227,17 +2234,21 @@ __global__ void __launch_bounds__(256) k_q_ff(OzQffArgs a) {
     }
     return;
   }
-  if (on)
-    for (int k = lane; k < a.n_lm; k += 32)
-      mb = max(mb, (unsigned long long)__double_as_longlong(row[k]) & 0x7FFFFFFFFFFFFFFFull);
+  int qe = 0;
+  if (h == 0) {
+    if (on)
+      for (int k = lane; k < a.n_lm; k += 32)
+        mb = max(mb, (unsigned long long)__double_as_longlong(row[k]) & 0x7FFFFFFFFFFFFFFFull);
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
-  const int exm = (int)(mb >> 52);
-  const int qe = exm == 0 ? 0 : exm - 1022;
-  if (lane == 0 && on) a.qexp[(size_t)f * a.n_shells + s] = qe;
+    for (int off = 16; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
+    const int exm = (int)(mb >> 52);
+    qe = exm == 0 ? 0 : exm - 1022;
+    if (lane == 0 && on) a.qexp[(size_t)f * a.n_shells + s] = qe;
+  }
   for (int k0 = 0; k0 < a.n_lm; k0 += kQffChunk) {
     const int kn = min(kQffChunk, a.n_lm - k0);
-    for (int k = lane; k < kn; k += 32) tile[k][warp] = on ? ff_split(row[k0 + k], qe) : make_float2(0.f, 0.f);
+    if (h == 0)
+      for (int k = lane; k < kn; k += 32) tile[k][r] = on ? ff_split(row[k0 + k], qe) : make_float2(0.f, 0.f);
     __syncthreads();
     for (int i = (int)threadIdx.x; i < kn * kQffShells; i += (int)blockDim.x) {
       const int k = i / kQffShells, c = i - k * kQffShells;
@@ -3302,7 +3313,7 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
   qa.qexp = o->qexp;
   const size_t qff_smem = (size_t)kQffShells * g->n_lm * sizeof(float2);
   qa.one_pass = qff_smem <= kQffOnePassSmem ? 1 : 0;
-  k_q_ff<<<(unsigned)(n_q * (o->shells_pad / kQffShells)), 32 * kQffShells,
+  k_q_ff<<<(unsigned)(n_q * (o->shells_pad / kQffShells)), 64 * kQffShells,
            qa.one_pass ? qff_smem : (size_t)kQffChunk * (kQffShells + 1) * sizeof(float2), s>>>(qa);
   note_launch(g, "k_q_ff", s);
   OzThetaFFArgs fa = {};
