@@ -2157,15 +2157,38 @@ __host__ __device__ __forceinline__ void oz_digits(unsigned long long X, int (&d
 // 4-byte store per slice and lane), Phi's rows giving g_phi's as well.
 
 // (hi, lo) of Q 2^-qexp per (field, shell), the scale from the row's largest
-// |Q| (|Q| 2^-qexp < 1), in a shell-minor layout [field][n_lm][shells_pad];
-// entries below 2^-126 of the scale (and the padding shells) are zero.
+// |Q| (|Q| 2^-qexp < 1), in a shell-minor layout of the two slots of each
+// (l, m) side by side: [field][l (l + 1) / 2 + m][shells_pad] as
+// (hi_cos, hi_sin, lo_cos, lo_sin), the slots l^2 + 2m - 1 and l^2 + 2m
+// (m = 0: the slot l^2 and zeros); entries below 2^-126 of the scale (and the
+// padding shells) are zero.
 struct OzQffArgs {
-  int n_shells, shells_pad, n_lm;
+  int n_shells, shells_pad, lmax, n_lm, n_pm;
   int one_pass;                 // the block's 8 rows fit in dynamic shared memory
   const double *Q;              // [n_q][n_shells][n_lm]
-  float2 *Qf;                   // [n_q][n_lm][shells_pad]
+  float4 *Qf;                   // [n_q][n_pm][shells_pad]
   int *qexp;                    // [n_q][n_shells]
 };
+
+// pairs (l, m), 0 <= m <= l <= lmax
+__host__ __device__ constexpr int n_pm_of(int lmax) { return (lmax + 1) * (lmax + 2) / 2; }
+
+// (l, m) of the triangular index pm = l (l + 1) / 2 + m, 0 <= m <= l
+__device__ __forceinline__ void pm_decode(int pm, int &l, int &m) {
+  int x = (int)((sqrtf(8.f * (float)pm + 1.f) - 1.f) * 0.5f);
+  while (x > 0 && x * (x + 1) / 2 > pm) --x;
+  while ((x + 1) * (x + 2) / 2 <= pm) ++x;
+  l = x;
+  m = pm - x * (x + 1) / 2;
+}
+
+// the slot pair of (l, m) from per-slot pairs, slot k at row[(k - k0) stride]
+__device__ __forceinline__ float4 slot_pair(const float2 *row, int k0, int l, int m, int stride) {
+  const int k = l * l + (m == 0 ? 0 : 2 * m - 1) - k0;
+  const float2 c = row[(size_t)k * stride];
+  const float2 sn = m == 0 ? make_float2(0.f, 0.f) : row[(size_t)(k + 1) * stride];
+  return make_float4(c.x, sn.x, c.y, sn.y);
+}
 
 __device__ __forceinline__ float2 ff_split(double x, int qe) {
   const uint32_t lo = (uint32_t)__double2loint(x), hi = (uint32_t)__double2hiint(x);
@@ -2186,11 +2209,11 @@ __device__ __forceinline__ float2 ff_split(double x, int qe) {
 }
 
 // One block per (field, 8 shells), two warps per shell: the row's scale,
-// then its pairs, and the 8 rows written out shell-minor as 64-byte runs.
+// then its pairs, and the 8 rows written out shell-minor as 128-byte runs.
 // Rows that fit in shared memory (one_pass) are read once: the loads of a
 // lane all in flight, the values staged in place of their pairs, each warp
 // of a row taking alternate 32-value pieces.  Longer rows take a warp each,
-// in chunks through a shared tile.
+// in chunks of whole degrees through a shared tile.
 constexpr int kQffShells = 8, kQffChunk = 512;
 constexpr size_t kQffOnePassSmem = 200 * 1024;
 
@@ -2205,7 +2228,7 @@ __global__ void __launch_bounds__(512) k_q_ff(OzQffArgs a) {
   const int s = s0 + r;
   const bool on = s < a.n_shells;
   const double *row = a.Q + ((size_t)f * a.n_shells + (on ? s : 0)) * a.n_lm;
-  float2 *Qfb = a.Qf + (size_t)f * a.n_lm * a.shells_pad + s0;
+  float4 *Qfb = a.Qf + (size_t)f * a.n_pm * a.shells_pad + s0;
   unsigned long long mb = 0ull;
   if (a.one_pass) {
     float2 *mine = qrow + (size_t)r * a.n_lm;
@@ -2228,9 +2251,13 @@ __global__ void __launch_bounds__(512) k_q_ff(OzQffArgs a) {
       mine[k] = ff_split(*reinterpret_cast<const double *>(&b), qe);
     }
     __syncthreads();
-    for (int i = (int)threadIdx.x; i < a.n_lm * kQffShells; i += (int)blockDim.x) {
-      const int k = i / kQffShells, c = i - k * kQffShells;
-      Qfb[(size_t)k * a.shells_pad + c] = qrow[(size_t)c * a.n_lm + k];
+    // thread: shell c, pairs pm, pm + step, ...; (l, m) walked along
+    const int c = (int)threadIdx.x % kQffShells, step = (int)blockDim.x / kQffShells;
+    int pm = (int)threadIdx.x / kQffShells, l, m;
+    pm_decode(pm, l, m);
+    for (; pm < a.n_pm; pm += step) {
+      Qfb[(size_t)pm * a.shells_pad + c] = slot_pair(qrow + (size_t)c * a.n_lm, 0, l, m, 1);
+      for (m += step; m > l;) m -= ++l;
     }
     return;
   }
@@ -2245,16 +2272,24 @@ __global__ void __launch_bounds__(512) k_q_ff(OzQffArgs a) {
     qe = exm == 0 ? 0 : exm - 1022;
     if (lane == 0 && on) a.qexp[(size_t)f * a.n_shells + s] = qe;
   }
-  for (int k0 = 0; k0 < a.n_lm; k0 += kQffChunk) {
-    const int kn = min(kQffChunk, a.n_lm - k0);
+  // degrees la..lb per chunk: their slots [la^2, (lb + 1)^2) and pairs
+  // [la (la + 1) / 2, (lb + 1) (lb + 2) / 2)  (2 l_max + 1 <= kQffChunk)
+  for (int la = 0; la <= a.lmax;) {
+    int lb = la;
+    while (lb < a.lmax && (lb + 2) * (lb + 2) - la * la <= kQffChunk) ++lb;
+    const int k0 = la * la, kn = (lb + 1) * (lb + 1) - k0;
     if (h == 0)
       for (int k = lane; k < kn; k += 32) tile[k][r] = on ? ff_split(row[k0 + k], qe) : make_float2(0.f, 0.f);
     __syncthreads();
-    for (int i = (int)threadIdx.x; i < kn * kQffShells; i += (int)blockDim.x) {
-      const int k = i / kQffShells, c = i - k * kQffShells;
-      Qfb[(size_t)(k0 + k) * a.shells_pad + c] = tile[k][c];
+    const int p0 = la * (la + 1) / 2, pn = (lb + 1) * (lb + 2) / 2 - p0;
+    for (int i = (int)threadIdx.x; i < pn * kQffShells; i += (int)blockDim.x) {
+      const int pm = p0 + i / kQffShells, c = i % kQffShells;
+      int l, m;
+      pm_decode(pm, l, m);
+      Qfb[(size_t)pm * a.shells_pad + c] = slot_pair(&tile[0][c], k0, l, m, kQffShells + 1);
     }
     __syncthreads();
+    la = lb + 1;
   }
 }
 
@@ -2280,12 +2315,69 @@ __device__ __forceinline__ float2 ff_sum(float2 a, float2 b, float sg) {
   return make_float2(h, __fsub_rn(lo, __fsub_rn(h, s)));
 }
 
+// Two float-float values at once, on the packed fp32 instructions (each
+// half rounded exactly as the scalar instruction rounds it): a 64-bit
+// register holds two fp32 numbers, the lower address's in its low half.
+typedef unsigned long long ffx2;
+
+__device__ __forceinline__ ffx2 mul_x2(ffx2 a, ffx2 b) {
+  ffx2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ ffx2 fma_x2(ffx2 a, ffx2 b, ffx2 c) {
+  ffx2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ ffx2 add_x2(ffx2 a, ffx2 b) {
+  ffx2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ ffx2 sub_x2(ffx2 a, ffx2 b) {
+  ffx2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ float x2_half(ffx2 a, int h) {
+  return __uint_as_float(h ? (uint32_t)(a >> 32) : (uint32_t)a);
+}
+
+// (aH, aL) += q p for two slots at once, ff_fma's steps in its order: q =
+// (hi of both slots, lo of both slots), qn_hi = -(q's hi), p = (hi, hi),
+// (lo, lo) of one table value.  With xn = -x the error of the product is
+// q_hi p_hi + xn, the sum a + x is a - xn, and x - bb is -(xn + bb): every
+// rounding is the scalar one's (up to the sign of a zero low part).
+__device__ __forceinline__ void ff_fma_x2(ulonglong2 q, ffx2 qn_hi, ulonglong2 p, ffx2 &aH, ffx2 &aL) {
+  const ffx2 xn = mul_x2(qn_hi, p.x);
+  const ffx2 xe = fma_x2(q.x, p.y, fma_x2(q.y, p.x, fma_x2(q.x, p.x, xn)));
+  const ffx2 s = sub_x2(aH, xn);
+  const ffx2 bb = sub_x2(s, aH);
+  const ffx2 err = sub_x2(sub_x2(aH, sub_x2(s, bb)), add_x2(xn, bb));
+  aL = add_x2(aL, add_x2(err, xe));
+  aH = s;
+}
+
 // The balanced base-256 digits of 0 <= X <= 2^47 in one step: with
 // Y = X + 127 (1 + 2^8 + ... + 2^32), the low five digits are Y's bytes less
 // 127 (each in [-127, 128], the carries done by the addition) and the top
 // one is Y >> 40.  Each digit comes out as the fp32 bit pattern of its
 // value, whose upper half is the bf16 pattern (an integer below 2^8 in
-// magnitude has sixteen zero low bits), most significant digit first.
+// magnitude has sixteen zero low bits), most significant digit first:
+// x_digit_pre gives the patterns of 2^23 + digit + 127 (the top one's of
+// 2^23 + digit), from which one fp32 subtraction each leaves the digit.
+__device__ __forceinline__ void x_digit_pre(unsigned long long X, uint32_t (&pre)[6]) {
+  const unsigned long long Y = X + 0x7F7F7F7F7Full;
+  const uint32_t ylo = (uint32_t)Y, yhi = (uint32_t)(Y >> 32);
+  pre[0] = 0x4B000000u | (yhi >> 8);
+  pre[1] = __byte_perm(yhi, 0x4B000000u, 0x7540);
+  pre[2] = __byte_perm(ylo, 0x4B000000u, 0x7543);
+  pre[3] = __byte_perm(ylo, 0x4B000000u, 0x7542);
+  pre[4] = __byte_perm(ylo, 0x4B000000u, 0x7541);
+  pre[5] = __byte_perm(ylo, 0x4B000000u, 0x7540);
+}
+
 __device__ __forceinline__ void x_digit_bits(unsigned long long X, uint32_t (&bits)[6]) {
   const unsigned long long Y = X + 0x7F7F7F7F7Full;
   const uint32_t ylo = (uint32_t)Y, yhi = (uint32_t)(Y >> 32);
@@ -2297,26 +2389,32 @@ __device__ __forceinline__ void x_digit_bits(unsigned long long X, uint32_t (&bi
   bits[5] = __float_as_uint(__fsub_rn(__uint_as_float(__byte_perm(ylo, 0x4B000000u, 0x7540)), 8388735.f));
 }
 
-// The six digit slices of one float-float value (hi, lo), as fp32 bit
-// patterns whose upper halves are the bf16 digits of |value| (the sign is
-// returned): X = round(|value| 2^K), 2^K = p1 p2 the row's scale, and its
-// balanced base-256 digits, as described below for ff_row.
-__device__ __forceinline__ uint32_t ff_digit_bits(float hi, float lo, float p1, float p2, uint32_t (&bits)[6]) {
-  constexpr float kM = 12582912.f;                      // 1.5 2^23
+__device__ __forceinline__ ffx2 x2_pack(uint32_t lo, uint32_t hi) { return ((ffx2)hi << 32) | lo; }
+
+// The digit patterns (x_digit_pre) of two float-float values (hi, lo) at
+// once, both halves of each packed register: X = round(|value| 2^K), 2^K =
+// p1 p2 the row's scale, as described below for ff_row.  The scalings by
+// 2^-32 and 2^-16 are exact (or leave a sum of 1.5 2^23 that rounds to it
+// either way), so each multiply-and-add is one fused operation.
+__device__ __forceinline__ void ff_digit_pre_x2(ffx2 hi, ffx2 lo, ffx2 p1, ffx2 p2, uint32_t (&pre)[2][6]) {
+  constexpr ffx2 kSign = 0x8000000080000000ull;
+  constexpr ffx2 kM = 0x4B4000004B400000ull;             // 1.5 2^23 in both halves
   constexpr uint32_t kMBits = 0x4B400000u;
-  const uint32_t sgn = __float_as_uint(hi) >> 31;
-  const float A = __fmul_rn(__fmul_rn(fabsf(hi), p1), p2);
-  const float B = __fmul_rn(__fmul_rn(sgn ? -lo : lo, p1), p2);
-  const float s2 = __fadd_rn(__fmul_rn(A, 0x1p-32f), kM);
-  const float R1 = __fmaf_rn(-__fsub_rn(s2, kM), 0x1p32f, A);
-  const float s1 = __fadd_rn(__fmul_rn(R1, 0x1p-16f), kM);
-  const float R2 = __fmaf_rn(-__fsub_rn(s1, kM), 0x1p16f, R1);
-  const float s0 = __fadd_rn(__fadd_rn(R2, B), kM);
-  const long long X = ((long long)(int)(__float_as_uint(s2) - kMBits) << 32) +
-                      ((long long)(int)(__float_as_uint(s1) - kMBits) << 16) +
-                      (long long)(int)(__float_as_uint(s0) - kMBits);
-  x_digit_bits((unsigned long long)X, bits);
-  return sgn;
+  const ffx2 sg = hi & kSign;
+  const ffx2 A = mul_x2(mul_x2(hi ^ sg, p1), p2);        // |hi| 2^K
+  const ffx2 B = mul_x2(mul_x2(lo ^ sg, p1), p2);        // +-lo 2^K, the sign of |value|
+  const ffx2 s2 = fma_x2(A, 0x2F8000002F800000ull, kM);                              // A 2^-32 + M
+  const ffx2 R1 = fma_x2(sub_x2(s2, kM), 0xCF800000CF800000ull, A);                  // A - T2 2^32
+  const ffx2 s1 = fma_x2(R1, 0x3780000037800000ull, kM);                             // R1 2^-16 + M
+  const ffx2 R2 = fma_x2(sub_x2(s1, kM), 0xC7800000C7800000ull, R1);                 // R1 - T1 2^16
+  const ffx2 s0 = add_x2(add_x2(R2, B), kM);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const long long X = ((long long)(int)((uint32_t)(s2 >> (32 * h)) - kMBits) << 32) +
+                        ((long long)(int)((uint32_t)(s1 >> (32 * h)) - kMBits) << 16) +
+                        (long long)(int)((uint32_t)(s0 >> (32 * h)) - kMBits);
+    x_digit_pre((unsigned long long)X, pre[h]);
+  }
 }
 
 // the row scale of ff_row: 2^K with K = 48 - e as two normal fp32 factors
@@ -2324,6 +2422,21 @@ __device__ __forceinline__ void ff_row_scale(int e, float &p1, float &p2) {
   const int K = 48 - e, K1 = K >> 1, K2 = K - K1;
   p1 = __uint_as_float((uint32_t)(K1 + 127) << 23);
   p2 = __uint_as_float((uint32_t)(K2 + 127) << 23);
+}
+
+// The bias digits of output mode 4 in a lane's two slots of each 64-slot
+// group (slots nt and nt + 1 hold G = 0): the top digit slice gets bf16 6144
+// (kOzBiasG) at slot nt, the next one at slot nt + 1; zero without a bias.
+template <int NG>
+__device__ __forceinline__ void ff_bias_masks(int lane, int nt, int bias, uint32_t (&bmask)[NG][2]) {
+  constexpr uint32_t kBiasBits = 0x45C0u;               // bf16 of kOzBiasG (6144)
+#pragma unroll
+  for (int g = 0; g < NG; ++g)
+#pragma unroll
+    for (int sl = 0; sl < 2; ++sl) {
+      const int t = 64 * g + 2 * lane, tb = nt + sl;
+      bmask[g][sl] = !bias ? 0u : (t == tb ? kBiasBits : 0u) | (t + 1 == tb ? kBiasBits << 16 : 0u);
+    }
 }
 
 // One row of float-float values cut into digits: lane L holds slots
@@ -2343,7 +2456,7 @@ __device__ __forceinline__ void ff_row_scale(int e, float &p1, float &p2) {
 // the values carry.
 template <int NG>
 __device__ __forceinline__ void ff_row(const float2 (&v)[NG][2], int lane, __nv_bfloat16 *dst, size_t stride,
-                                       int *gexp, int nt, int bias, int qe) {
+                                       int *gexp, const uint32_t (&bmask)[NG][2], int qe) {
   uint32_t mb = 0u;
 #pragma unroll
   for (int g = 0; g < NG; ++g)
@@ -2357,25 +2470,24 @@ __device__ __forceinline__ void ff_row(const float2 (&v)[NG][2], int lane, __nv_
   const int e = exm - 125;                              // every |value| < 2^(exm - 126) = 2^(e - 1)
   float p1, p2;
   ff_row_scale(e, p1, p2);
-  constexpr uint32_t kBiasBits = 0x45C0u;               // bf16 of kOzBiasG (6144)
+  const ffx2 p1x = x2_pack(__float_as_uint(p1), __float_as_uint(p1));
+  const ffx2 p2x = x2_pack(__float_as_uint(p2), __float_as_uint(p2));
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
-    uint32_t bits[2][6], sgn[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) sgn[h] = ff_digit_bits(v[g][h].x, v[g][h].y, p1, p2, bits[h]);
+    // the lane's two values, one in each half
+    const uint32_t h0 = __float_as_uint(v[g][0].x), h1 = __float_as_uint(v[g][1].x);
+    uint32_t pre[2][6];
+    ff_digit_pre_x2(x2_pack(h0, h1), x2_pack(__float_as_uint(v[g][0].y), __float_as_uint(v[g][1].y)), p1x, p2x,
+                    pre);
     const int t = 64 * g + 2 * lane;
-    const uint32_t sm = (sgn[0] << 15) | (sgn[1] << 31);
+    const uint32_t sm = ((h0 >> 31) << 15) | (h1 & 0x80000000u);
     uint32_t *d32 = reinterpret_cast<uint32_t *>(dst + t);
 #pragma unroll
     for (int sl = 0; sl < 6; ++sl) {
-      uint32_t w = __byte_perm(bits[0][sl], bits[1][sl], 0x7632) ^ sm;
-      if (bias) {
-        // the bias digits of output mode 4 (slots nt and nt + 1 hold G = 0)
-        if (sl == 0 && t == nt) w |= kBiasBits;
-        if (sl == 0 && t + 1 == nt) w |= kBiasBits << 16;
-        if (sl == 1 && t == nt + 1) w |= kBiasBits;
-        if (sl == 1 && t + 1 == nt + 1) w |= kBiasBits << 16;
-      }
+      // 2^23 + 127 (the top digit: 2^23) off both halves: the digits' fp32 patterns
+      const ffx2 d = sub_x2(x2_pack(pre[0][sl], pre[1][sl]), sl == 0 ? 0x4B0000004B000000ull : 0x4B00007F4B00007Full);
+      uint32_t w = __byte_perm((uint32_t)d, (uint32_t)(d >> 32), 0x7632) ^ sm;
+      if (sl < 2) w |= bmask[g][sl];                    // the bias digits (ff_bias_masks)
       d32[sl * (stride / 2)] = w;
     }
   }
@@ -2384,8 +2496,8 @@ __device__ __forceinline__ void ff_row(const float2 (&v)[NG][2], int lane, __nv_
 }
 
 struct OzThetaFFArgs {
-  int n_shells, shells_pad, n_theta, half, lmax, n_lm, nt, gphi, rows_pad, gk, n_r, bias;
-  const float2 *Qf;             // [3][n_lm][shells_pad] (k_q_ff)
+  int n_shells, shells_pad, n_theta, half, lmax, n_lm, n_pm, nt, gphi, rows_pad, gk, n_r, bias;
+  const float4 *Qf;             // [3][n_pm][shells_pad] (k_q_ff)
   const int *qexp;              // [3][n_shells]
   const float2 *Pf[2];          // [n_theta][n_lm]: P and dP/dtheta as (hi, lo)
   const double *inv_sin, *inv_r;
@@ -2393,13 +2505,16 @@ struct OzThetaFFArgs {
   int *gexp[4];
 };
 
-// Shared memory of k_theta_ff: TP table rows (rounded to an even count of
-// float2) and the staged sums, 32 shells x (2 TP rows of gk slots + 1).
+// Shared memory of k_theta_ff: TP table rows of (l, m) entries (hi, hi, lo,
+// lo), in float2 units, and the staged sums, 32 shells x (2 TP rows of gk
+// slots + 1).
 __host__ __device__ constexpr int theta_ff_tp(int gk) { return gk == 64 ? 2 : 1; }
-__host__ __device__ inline int theta_ff_tab(int n_lm, int gk) { return (theta_ff_tp(gk) * n_lm + 1) & ~1; }
+__host__ __device__ inline int theta_ff_tab(int lmax, int gk) {
+  return 2 * theta_ff_tp(gk) * ((lmax + 1) * (lmax + 2) / 2);
+}
 __host__ __device__ inline int theta_ff_pitch(int gk) { return 2 * theta_ff_tp(gk) * gk + 1; }
-inline size_t theta_ff_smem(int n_lm, int gk) {
-  return ((size_t)theta_ff_tab(n_lm, gk) + 32 * (size_t)theta_ff_pitch(gk)) * sizeof(float2);
+inline size_t theta_ff_smem(int lmax, int gk) {
+  return ((size_t)theta_ff_tab(lmax, gk) + 32 * (size_t)theta_ff_pitch(gk)) * sizeof(float2);
 }
 
 // Blocks: (field, 32 shells, TP mirrored row pairs); warps: one or two
@@ -2408,18 +2523,24 @@ template <int NG>
 __global__ void __launch_bounds__(512, 2) k_theta_ff(OzThetaFFArgs a) {
   constexpr int TP = NG == 1 ? 2 : 1;
   constexpr int R = 2 * TP;
-  extern __shared__ float2 ffsm[];
-  float2 *ptab = ffsm;                                   // [TP][n_lm]
-  float2 *stg = ffsm + theta_ff_tab(a.n_lm, a.gk);       // [32][pitch]
+  extern __shared__ float4 ffsm4[];
+  float2 *const ffsm = reinterpret_cast<float2 *>(ffsm4);
+  float4 *ptab = ffsm4;                                  // [TP][n_pm]: (hi, hi, lo, lo)
+  float2 *stg = ffsm + theta_ff_tab(a.lmax, a.gk);       // [32][pitch]
   const int pitch = theta_ff_pitch(a.gk);
   const int W = (int)(blockDim.x >> 5), warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
   const int n_pt = (a.half + TP - 1) / TP, n_st = a.shells_pad >> 5;
   const int pt = (int)blockIdx.x % n_pt, st = ((int)blockIdx.x / n_pt) % n_st, f = (int)blockIdx.x / (n_pt * n_st);
   const int pair0 = pt * TP, shell0 = st * 32;
   const float2 *tsrc = f == 2 ? a.Pf[1] : a.Pf[0];
-  for (int i = (int)threadIdx.x; i < TP * a.n_lm; i += (int)blockDim.x) {
-    const int r = i / a.n_lm;
-    ptab[i] = pair0 + r < a.half ? tsrc[(size_t)(pair0 + r) * a.n_lm + (i - r * a.n_lm)] : make_float2(0.f, 0.f);
+  // the table value of (l, m), the same in both of its slots, twice
+  for (int i = (int)threadIdx.x; i < TP * a.n_pm; i += (int)blockDim.x) {
+    const int r = i / a.n_pm;
+    int l, m;
+    pm_decode(i - r * a.n_pm, l, m);
+    const float2 v = pair0 + r < a.half ? tsrc[(size_t)(pair0 + r) * a.n_lm + l * l + (m == 0 ? 0 : 2 * m - 1)]
+                                        : make_float2(0.f, 0.f);
+    ptab[i] = make_float4(v.x, v.x, v.y, v.y);
   }
   // the rows' scales, and g_phi's factor 1 / (r sin theta_j) as an fp32 pair
   __shared__ int qe_s[32];
@@ -2443,9 +2564,10 @@ __global__ void __launch_bounds__(512, 2) k_theta_ff(OzThetaFFArgs a) {
     }
   __syncthreads();
   const int L = a.lmax, n_groups = L / 2 + 1;
-  const float2 *qf = a.Qf + (size_t)f * a.n_lm * a.shells_pad + shell0 + lane;
-  const size_t qs = (size_t)a.shells_pad;
+  const ulonglong2 *qf = reinterpret_cast<const ulonglong2 *>(a.Qf + (size_t)f * a.n_pm * a.shells_pad + shell0 + lane);
+  const int qs = a.shells_pad;
   float2 *srow = stg + lane * pitch;
+  constexpr ffx2 kSign2 = 0x8000000080000000ull;
   for (int gi = warp; gi < n_groups; gi += W) {
 #pragma unroll 1
     for (int k = 0; k < 2; ++k) {
@@ -2458,50 +2580,38 @@ __global__ void __launch_bounds__(512, 2) k_theta_ff(OzThetaFFArgs a) {
       }
       const int t0 = m == 0 ? 0 : 2 * m - 1;
       const bool two_slots = m > 0;
-      // a[s][i][0]: terms l = l_max, l_max - 2, ...; [1]: l = l_max - 1, ...
-      float2 acc[2][TP][2];
+      // both slots of m at once (m = 0: the second is zero); aH[i][0], aL[i][0]:
+      // terms l = l_max, l_max - 2, ...; [1]: l = l_max - 1, ...
+      ffx2 aH[TP][2], aL[TP][2];
 #pragma unroll
-      for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int i = 0; i < TP; ++i) acc[s][i][0] = acc[s][i][1] = make_float2(0.f, 0.f);
-      // terms l and l - 1 per step; the next step's coefficients are loaded
-      // before this step's multiply-adds
-      const float2 z2 = make_float2(0.f, 0.f);
-      int b1 = L * L + t0;                               // l^2 + t0 at l
-      float2 q1[2], q2[2];
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const bool on = s == 0 || two_slots;
-        q1[s] = on ? qf[(size_t)(b1 + s) * qs] : z2;
-        q2[s] = on && L - 1 >= m ? qf[(size_t)(b1 - (2 * L - 1) + s) * qs] : z2;
-      }
+      for (int i = 0; i < TP; ++i) aH[i][0] = aH[i][1] = aL[i][0] = aL[i][1] = 0ull;
+      // terms l and l - 1 per step, the pairs index (l, m) -> l (l + 1) / 2 + m;
+      // the next step's coefficients are loaded before this step's
+      // multiply-adds.  Past the last term the same index steps stay in
+      // [0, n_pm) (at l = m: b2 = m (m + 1) / 2, b1n = (m^2 - m + 2) / 2, b2n
+      // = (m^2 - 3m + 6) / 2), so every load is unconditional; a value is
+      // used only where its term exists.  (l_max = 0 reaches rows 1 and 3:
+      // the allocation has four spare rows after the last field.)
+      int b1 = L * (L + 1) / 2 + m;
+      ulonglong2 q1 = qf[b1 * qs];
+      ulonglong2 q2 = qf[(b1 - L) * qs];
 #pragma unroll 1
       for (int l = L; l >= m; l -= 2) {
         const bool second = l - 1 >= m;
-        const int b2 = b1 - (2 * l - 1);                 // (l - 1)^2 + t0
-        const int b1n = b1 - (4 * l - 4);                // (l - 2)^2 + t0
-        const int b2n = b1n - (2 * l - 5);               // (l - 3)^2 + t0
-        float2 n1[2], n2[2];
+        const int b2 = b1 - l;                           // (l - 1, m)
+        const int b1n = b2 - (l - 1);                    // (l - 2, m)
+        const int b2n = b1n - (l - 2);                   // (l - 3, m)
+        const ulonglong2 n1 = qf[b1n * qs];
+        const ulonglong2 n2 = qf[b2n * qs];
+        const ffx2 qn1 = q1.x ^ kSign2, qn2 = q2.x ^ kSign2;
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          const bool on = s == 0 || two_slots;
-          n1[s] = on && l - 2 >= m ? qf[(size_t)(b1n + s) * qs] : z2;
-          n2[s] = on && l - 3 >= m ? qf[(size_t)(b2n + s) * qs] : z2;
+        for (int i = 0; i < TP; ++i) {
+          ff_fma_x2(q1, qn1, *reinterpret_cast<const ulonglong2 *>(ptab + i * a.n_pm + b1), aH[i][0], aL[i][0]);
+          if (second)
+            ff_fma_x2(q2, qn2, *reinterpret_cast<const ulonglong2 *>(ptab + i * a.n_pm + b2), aH[i][1], aL[i][1]);
         }
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          if (s == 1 && !two_slots) break;
-#pragma unroll
-          for (int i = 0; i < TP; ++i) {
-            ff_fma(q1[s], ptab[i * a.n_lm + b1 + s], acc[s][i][0]);
-            if (second) ff_fma(q2[s], ptab[i * a.n_lm + b2 + s], acc[s][i][1]);
-          }
-        }
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          q1[s] = n1[s];
-          q2[s] = n2[s];
-        }
+        q1 = n1;
+        q2 = n2;
         b1 = b1n;
       }
       // row j: E + O = a0 + a1; row j': E - O, which is a0 - a1 when a0
@@ -2513,8 +2623,10 @@ __global__ void __launch_bounds__(512, 2) k_theta_ff(OzThetaFFArgs a) {
         if (s == 1 && !two_slots) break;
 #pragma unroll
         for (int i = 0; i < TP; ++i) {
-          srow[(2 * i) * a.gk + t0 + s] = ff_sum(acc[s][i][0], acc[s][i][1], 1.f);
-          const float2 d = ff_sum(acc[s][i][0], acc[s][i][1], -1.f);
+          const float2 a0 = make_float2(x2_half(aH[i][0], s), x2_half(aL[i][0], s));
+          const float2 a1 = make_float2(x2_half(aH[i][1], s), x2_half(aL[i][1], s));
+          srow[(2 * i) * a.gk + t0 + s] = ff_sum(a0, a1, 1.f);
+          const float2 d = ff_sum(a0, a1, -1.f);
           srow[(2 * i + 1) * a.gk + t0 + s] = make_float2(sg * d.x, sg * d.y);
         }
       }
@@ -2528,6 +2640,8 @@ __global__ void __launch_bounds__(512, 2) k_theta_ff(OzThetaFFArgs a) {
   //   G_phi[t] = (+1 for t even, -1 for t odd) (m / (r sin theta)) G_Phi[swap t]
   // (sin theta_j' = sin theta_j); slot 0 and the slots past nt are zero.
   const size_t stride = (size_t)a.rows_pad * a.gk;
+  uint32_t bmask[NG][2];
+  ff_bias_masks<NG>(lane, a.nt, a.bias, bmask);
   __nv_bfloat16 *const Gf = f == 0 ? a.G[0] : f == 1 ? a.G[1] : a.G[2];
   int *const gexp = f == 0 ? a.gexp[0] : f == 1 ? a.gexp[1] : a.gexp[2];
   for (int rr = warp; rr < 32 * R; rr += W) {
@@ -2547,7 +2661,7 @@ __global__ void __launch_bounds__(512, 2) k_theta_ff(OzThetaFFArgs a) {
       }
     const size_t row = (size_t)shell * a.n_theta + j;
     const int qe = qe_s[sl];
-    ff_row<NG>(v, lane, Gf + row * a.gk, stride, gexp + row, a.nt, a.bias, qe);
+    ff_row<NG>(v, lane, Gf + row * a.gk, stride, gexp + row, bmask, qe);
     if (f != 0 || !a.gphi) continue;
     const float ch = cphi[sl][ri].x, cl = cphi[sl][ri].y;
 #pragma unroll
@@ -2569,7 +2683,7 @@ __global__ void __launch_bounds__(512, 2) k_theta_ff(OzThetaFFArgs a) {
         }
         v[g][h] = w;
       }
-    ff_row<NG>(v, lane, a.G[3] + row * a.gk, stride, a.gexp[3] + row, a.nt, a.bias, qe);
+    ff_row<NG>(v, lane, a.G[3] + row * a.gk, stride, a.gexp[3] + row, bmask, qe);
   }
 }
 
@@ -2893,7 +3007,7 @@ struct yy_oz_tables {
   int *gexp[4];                 // per field: [rows_pad]
   double *inv_sin, *inv_r;      // 1 / sin theta_j at the polar cell centres, 1 / r_(n+1) per shell
   int shells_pad;               // shells rounded up to 32 (k_theta_ff's tiles)
-  float2 *Qf;                   // [3][n_lm][shells_pad]: scaled coefficients as fp32 pairs (k_q_ff)
+  float4 *Qf;                   // [3][n_pm][shells_pad]: scaled coefficients as fp32 pairs (k_q_ff)
   int *qexp;                    // [3][n_shells]: their scales
   float2 *Pf[2];                // [n_theta][n_lm]: P and dP/dtheta as fp32 pairs
   float2 *tbf;                  // [ceil(n_theta / 2)][n_lm]: the analysis table T as fp32 pairs
@@ -3177,7 +3291,8 @@ yy_status ozaki_prepare(yy_grid *g) {
     A((void **)&o->inv_sin, g->n_theta * sizeof(double));
     A((void **)&o->inv_r, g->n_r * sizeof(double));
     o->shells_pad = round_up(grid_rows(g), 32);
-    A((void **)&o->Qf, (size_t)3 * g->n_lm * o->shells_pad * sizeof(float2));
+    // four spare rows: k_theta_ff's unconditional loads past a degree-0 row
+    A((void **)&o->Qf, ((size_t)3 * n_pm_of(g->lmax) + 4) * o->shells_pad * sizeof(float4));
     A((void **)&o->qexp, (size_t)3 * grid_rows(g) * sizeof(int));
     for (int k = 0; k < 2; ++k) A((void **)&o->Pf[k], (size_t)g->n_theta * g->n_lm * sizeof(float2));
     A((void **)&o->tbf, (size_t)((g->n_theta + 1) / 2) * g->n_lm * sizeof(float2));
@@ -3212,10 +3327,11 @@ yy_status ozaki_prepare(yy_grid *g) {
         }
         if (e == cudaSuccess) e = cudaMemcpy(tdst[k], tf.data(), tn[k] * sizeof(float2), cudaMemcpyHostToDevice);
       }
-      if (e == cudaSuccess) e = cudaMemset(o->Qf, 0, (size_t)3 * g->n_lm * o->shells_pad * sizeof(float2));
+      if (e == cudaSuccess)
+        e = cudaMemset(o->Qf, 0, ((size_t)3 * n_pm_of(g->lmax) + 4) * o->shells_pad * sizeof(float4));
       // the largest dynamic shared memory of any supported degree (l_max 63),
       // the same for every grid
-      const int ff_max = (int)theta_ff_smem(64 * 64, 128);
+      const int ff_max = (int)theta_ff_smem(63, 128);
       if (e == cudaSuccess &&
           (cudaFuncSetAttribute(k_theta_ff<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ff_max) != cudaSuccess ||
            cudaFuncSetAttribute(k_theta_ff<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, ff_max) != cudaSuccess ||
@@ -3307,7 +3423,9 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
   OzQffArgs qa = {};
   qa.n_shells = n_shells;
   qa.shells_pad = o->shells_pad;
+  qa.lmax = g->lmax;
   qa.n_lm = g->n_lm;
+  qa.n_pm = n_pm_of(g->lmax);
   qa.Q = g->Q;
   qa.Qf = o->Qf;
   qa.qexp = o->qexp;
@@ -3323,6 +3441,7 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
   fa.half = (g->n_theta + 1) / 2;
   fa.lmax = g->lmax;
   fa.n_lm = g->n_lm;
+  fa.n_pm = n_pm_of(g->lmax);
   fa.nt = 2 * g->lmax + 1;
   fa.gphi = n_jobs == 4 ? 1 : 0;
   fa.rows_pad = o->rows_pad;
@@ -3342,7 +3461,7 @@ cudaError_t ozaki_synthesis(yy_grid *g, double *py, double *pg, double *gy, doub
   const int n_groups = g->lmax / 2 + 1, tp = theta_ff_tp(o->gk);
   const unsigned ff_blocks = (unsigned)(n_q * (o->shells_pad / 32) * ((fa.half + tp - 1) / tp));
   const unsigned ff_threads = (unsigned)(32 * (n_groups < 16 ? n_groups : 16));
-  const size_t ff_smem = theta_ff_smem(g->n_lm, o->gk);
+  const size_t ff_smem = theta_ff_smem(g->lmax, o->gk);
   if (o->gk == 64)
     k_theta_ff<1><<<ff_blocks, ff_threads, ff_smem, s>>>(fa);
   else
