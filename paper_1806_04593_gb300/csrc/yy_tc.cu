@@ -2343,6 +2343,11 @@ __device__ __forceinline__ ffx2 sub_x2(ffx2 a, ffx2 b) {
 __device__ __forceinline__ float x2_half(ffx2 a, int h) {
   return __uint_as_float(h ? (uint32_t)(a >> 32) : (uint32_t)a);
 }
+// (hi, hi), (lo, lo) of one float-float value
+__device__ __forceinline__ ulonglong2 ff_dup(float2 v) {
+  const ffx2 h = __float_as_uint(v.x), l = __float_as_uint(v.y);
+  return make_ulonglong2((h << 32) | h, (l << 32) | l);
+}
 
 // (aH, aL) += q p for two slots at once, ff_fma's steps in its order: q =
 // (hi of both slots, lo of both slots), qn_hi = -(q's hi), p = (hi, hi),
@@ -2694,29 +2699,34 @@ __global__ void __launch_bounds__(512, 2) k_theta_ff(OzThetaFFArgs a) {
 // One block per shell: its F rows scaled by a power of two (the shell's
 // largest |F| below 1) and split into fp32 pairs, the mirrored sums and
 // differences formed in float-float and staged in shared memory, then one
-// thread per mode with the pair-split table; the result widened to float64
-// and scaled back.
+// thread per mode with the pair-split table, both shells' multiply-adds as
+// one on the packed fp32 instructions; the result widened to float64 and
+// scaled back.
 constexpr int kSepFFRegs = 8;    // mirrored (F_j, F_j') pairs per thread held in registers
-constexpr int kSepFFShells = 2;  // shells per block: each table value read serves them all
+constexpr int kSepFFShells = 2;  // shells per block: each table value read serves both halves of a pair
+static_assert(kSepFFShells == 2, "k_sep_theta_ff packs its two shells into one fp32 pair");
 
 __global__ void __launch_bounds__(512) k_sep_theta_ff(int n_shells, int n_theta, int n_lm, int nt, int nt_pad,
                                                       const float2 *__restrict__ tbf, const double *__restrict__ F,
                                                       double *__restrict__ A) {
-  extern __shared__ float2 sdf[];                          // per shell [2][half][nt_pad]: S, then D
+  // [2][half][nt_pad]: S, then D, both shells' values as one packed pair
+  // (hi of shell 0, hi of shell 1, lo of shell 0, lo of shell 1)
+  extern __shared__ float4 sdf[];
   __shared__ unsigned long long red[16];
   __shared__ int qes[kSepFFShells];
   const int half = (n_theta + 1) >> 1;
   const int shell0 = (int)blockIdx.x * kSepFFShells;
   const int tid = (int)threadIdx.x, nthr = (int)blockDim.x;
-  const size_t per_shell = (size_t)2 * half * nt_pad;
+  const int per_shell = 2 * half * nt_pad;
   // pair e = j nt + t (j < half, t < nt): F_j[t] and F_j'[t], all loads in
   // flight together when the shell fits in registers
   const int n_pairs = half * nt;
   const bool in_regs = n_pairs <= kSepFFRegs * nthr;
   for (int sh = 0; sh < kSepFFShells; ++sh) {
-    float2 *sd = sdf + sh * per_shell;
+    // shell sh's value of entry e: components sh (hi) and 2 + sh (lo)
+    float *sd = reinterpret_cast<float *>(sdf) + sh;
     if (shell0 + sh >= n_shells) {
-      for (int e = tid; e < (int)per_shell; e += nthr) sd[e] = make_float2(0.f, 0.f);
+      for (int e = tid; e < per_shell; e += nthr) sd[4 * e] = sd[4 * e + 2] = 0.f;
       continue;
     }
     const double *Fs = F + (size_t)(shell0 + sh) * n_theta * nt_pad;
@@ -2764,8 +2774,11 @@ __global__ void __launch_bounds__(512) k_sep_theta_ff(int n_shells, int n_theta,
           S = ff_sum(a, b, 1.f);
           D = ff_sum(a, b, -1.f);
         }
-        sd[j * nt_pad + t] = S;
-        sd[(size_t)(half + j) * nt_pad + t] = D;
+        const int es = j * nt_pad + t, ed = (half + j) * nt_pad + t;
+        sd[4 * es] = S.x;
+        sd[4 * es + 2] = S.y;
+        sd[4 * ed] = D.x;
+        sd[4 * ed + 2] = D.y;
       }
     } else {
       for (int e = tid; e < n_pairs; e += nthr) {
@@ -2777,8 +2790,11 @@ __global__ void __launch_bounds__(512) k_sep_theta_ff(int n_shells, int n_theta,
           S = ff_sum(a, b, 1.f);
           D = ff_sum(a, b, -1.f);
         }
-        sd[j * nt_pad + t] = S;
-        sd[(size_t)(half + j) * nt_pad + t] = D;
+        const int es = j * nt_pad + t, ed = (half + j) * nt_pad + t;
+        sd[4 * es] = S.x;
+        sd[4 * es + 2] = S.y;
+        sd[4 * ed] = D.x;
+        sd[4 * ed + 2] = D.y;
       }
     }
     __syncthreads();                                         // red[] is read before the next shell writes it
@@ -2786,17 +2802,19 @@ __global__ void __launch_bounds__(512) k_sep_theta_ff(int n_shells, int n_theta,
   for (int idx = tid; idx < n_lm; idx += nthr) {
     const int l = degree_of_mode(idx);
     const int t = idx - l * l;
-    const size_t coff = ((((l + ((t + 1) >> 1)) & 1) != 0) ? (size_t)half * nt_pad : 0) + t;
+    const int coff = ((((l + ((t + 1) >> 1)) & 1) != 0) ? half * nt_pad : 0) + t;
     const float2 *p = tbf + idx;
-    float2 acc[kSepFFShells];
-#pragma unroll
-    for (int sh = 0; sh < kSepFFShells; ++sh) acc[sh] = make_float2(0.f, 0.f);
-#pragma unroll 4
+    const ulonglong2 *sq = reinterpret_cast<const ulonglong2 *>(sdf) + coff;
+    ffx2 aH = 0ull, aL = 0ull;
+#pragma unroll 8
     for (int j = 0; j < half; ++j) {
       const float2 tv = __ldg(p + (size_t)j * n_lm);
-#pragma unroll
-      for (int sh = 0; sh < kSepFFShells; ++sh) ff_fma(sdf[sh * per_shell + coff + (size_t)j * nt_pad], tv, acc[sh]);
+      const ulonglong2 q = sq[j * nt_pad];
+      ff_fma_x2(q, q.x ^ 0x8000000080000000ull, ff_dup(tv), aH, aL);
     }
+    float2 acc[kSepFFShells];
+#pragma unroll
+    for (int sh = 0; sh < kSepFFShells; ++sh) acc[sh] = make_float2(x2_half(aH, sh), x2_half(aL, sh));
 #pragma unroll
     for (int sh = 0; sh < kSepFFShells; ++sh) {
       if (shell0 + sh >= n_shells) break;
