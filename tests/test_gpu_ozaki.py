@@ -145,6 +145,29 @@ def test_ozaki_ragged_and_highest_degree(yy):
             assert grad_err(out["grad_" + q], ref["grad_" + q]) <= TOL_FP64, (lmax, q)
 
 
+def test_ozaki_lowest_degrees(yy):
+    """l_max = 0 (the monopole alone: one slot and one polar order, the polar
+    stage's loads past the degree-0 coefficient row landing in the spare rows
+    after the last field), 1 and 2, against the oracle."""
+    from oracle import OracleGrid
+    for lmax, seed in ((0, 51), (1, 52), (2, 53)):
+        spec = inputs.GridSpec(f"oz_low_{lmax}", np.logspace(-2, 0, 10), 12, 36, 0.03, 0.05, lmax, 1.0)
+        rng = np.random.default_rng(seed)
+        ry = rng.uniform(0.5, 1.5, (9, 12, 36))
+        rg = rng.uniform(0.5, 1.5, (9, 12, 36))
+        g = yy.Grid.from_spec(spec)
+        try:
+            g.prepare("fp64_ozaki")
+            out = gpu_solve(g, ry, rg, gradient=True, prec="fp64_ozaki")
+            assert yy.yy_last_device_status(g.handle) == yy.YY_OK
+        finally:
+            g.close()
+        ref = OracleGrid(spec.r_edges, 12, 36, 0.03, 0.05, lmax).solve(ry, rg, gradient=True)
+        for q in ("yin", "yang"):
+            assert phi_err(out["phi_" + q], ref["phi_" + q]) <= TOL_FP64, (lmax, q)
+            assert grad_err(out["grad_" + q], ref["grad_" + q]) <= TOL_FP64, (lmax, q)
+
+
 def test_ozaki_polar_grid(yy, oracle_grid):
     import torch
     spec = inputs.mid_polar_grid()
