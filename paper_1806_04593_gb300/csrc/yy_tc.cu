@@ -2144,7 +2144,8 @@ __host__ __device__ __forceinline__ void oz_digits(unsigned long long X, int (&d
 // the cross terms hi lo' + lo hi' go into the low part and lo lo' (2^-48 of
 // the product) is dropped -- the accurate dot product of Ogita, Rump and
 // Oishi (2005) with split inputs.  Every step is an explicitly rounded
-// intrinsic so that the compiler neither fuses nor reorders it.
+// intrinsic or packed instruction (inline PTX with .rn) so that the compiler
+// neither fuses nor reorders it.
 //
 // The stage is a small product per slot t (m = (t + 1) / 2): the polar table
 // T_j[l, t] (rows j, l = m..l_max) times the coefficients Q[l, t] of every
@@ -2154,7 +2155,10 @@ __host__ __device__ __forceinline__ void oz_digits(unsigned long long X, int (&d
 // each warp the slots of one or two orders m with about the same number of
 // terms (m and l_max + 1 - m), and stages the sums in shared memory; then
 // each warp cuts whole rows into digits (lanes on slots 2 L and 2 L + 1: one
-// 4-byte store per slice and lane), Phi's rows giving g_phi's as well.
+// 4-byte store per slice and lane), Phi's rows giving g_phi's as well.  The
+// cos and sin slots of an order share their table value, so their
+// multiply-adds run as one on the packed fp32 instructions (ff_fma_x2), the
+// coefficients stored as slot pairs by k_q_ff.
 
 // (hi, lo) of Q 2^-qexp per (field, shell), the scale from the row's largest
 // |Q| (|Q| 2^-qexp < 1), in a shell-minor layout of the two slots of each
